@@ -1,0 +1,213 @@
+"""FP64 CPU oracle for the SOP bake and query/shade (test infrastructure).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+import this package. The product path (the CUDA library and its binding)
+never does. The C source (sop_oracle.c) is compiled with gcc by `build()`
+into oracle/_build/liboracle.so and driven here through ctypes; the
+surrogate MLP part of the oracle is plain NumPy in `mlp.py`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "sop_oracle.c")
+LIB = os.path.join(HERE, "_build", "liboracle.so")
+
+MODE_SHADE, MODE_SHADOW = 0, 1
+FLAG_ALPHA_MIN, FLAG_ORDER, FLAG_TNEAR, FLAG_TSTOP = 1, 2, 4, 8
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE double, no FMA contraction)."""
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+    tmp = LIB + f".tmp{os.getpid()}"
+    try:
+        subprocess.run(base + ["-fopenmp", SRC, "-o", tmp, "-lm"], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + [SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(LIB)
+        _lib.orc_num_threads.restype = C.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a, shape_last=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+# ----------------------------------------------------------------------------
+# octahedral map, frame, environment, BRDF
+# ----------------------------------------------------------------------------
+def oct_encode(d):
+    d = _f64(d).reshape(-1, 3)
+    uv = np.empty((len(d), 2))
+    lib().orc_oct_encode_n(C.c_int64(len(d)), _p(d), _p(uv))
+    return uv
+
+
+def oct_decode(uv, l1_only=False):
+    uv = _f64(uv).reshape(-1, 2)
+    d = np.empty((len(uv), 3))
+    lib().orc_oct_decode_n(C.c_int64(len(uv)), _p(uv), _p(d), C.c_int(1 if l1_only else 0))
+    return d
+
+
+def oct_wrap(R, i, j):
+    si, sj = C.c_int(), C.c_int()
+    lib().orc_oct_wrap(C.c_int(R), C.c_int(i), C.c_int(j), C.byref(si), C.byref(sj))
+    return si.value, sj.value
+
+
+def oct_bilerp(map_, uv):
+    """map_: [R, R, C] float64 compact map; uv: [n, 2]."""
+    map_ = _f64(map_)
+    R, _, Ch = map_.shape
+    uv = _f64(uv).reshape(-1, 2)
+    out = np.empty((len(uv), Ch))
+    lib().orc_oct_bilerp_n(C.c_int64(len(uv)), _p(map_), C.c_int(R), C.c_int(Ch), _p(uv), _p(out))
+    return out
+
+
+def hammersley(S):
+    out = np.empty((S, 3))
+    lib().orc_hammersley(C.c_int32(S), _p(out))
+    return out
+
+
+def onb(n):
+    n = _f64(n).reshape(-1, 3)
+    t, b = np.empty_like(n), np.empty_like(n)
+    lib().orc_onb_n(C.c_int64(len(n)), _p(n), _p(t), _p(b))
+    return t, b
+
+
+def env_lookup(env, w):
+    env = _f32(env)
+    He, We, _ = env.shape
+    w = _f64(w).reshape(-1, 3)
+    out = np.empty((len(w), 3))
+    lib().orc_env_lookup_n(C.c_int64(len(w)), _p(env), C.c_int32(He), C.c_int32(We), _p(w), _p(out))
+    return out
+
+
+def brdf(n, wo, wi, albedo, rough, metal, spec=0.5):
+    n, wo, wi, albedo = (_f64(v).reshape(-1, 3) for v in (n, wo, wi, albedo))
+    rough, metal = _f64(rough).reshape(-1), _f64(metal).reshape(-1)
+    f = np.empty((len(n), 3))
+    lib().orc_brdf_n(C.c_int64(len(n)), _p(n), _p(wo), _p(wi), _p(albedo), _p(rough), _p(metal),
+                     C.c_double(spec), _p(f))
+    return f
+
+
+# ----------------------------------------------------------------------------
+# bake
+# ----------------------------------------------------------------------------
+DEFAULT_BAKE = dict(t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4)
+
+
+def bake_rays(gauss, probe_pos, R, probe_of, ti, tj, t_near=0.0, alpha_min=1.0 / 255.0,
+              alpha_max=0.99, t_stop=1e-4):
+    """Bake the listed texel rays. Returns rgb [n,3], occ [n], depth [n], flags [n]."""
+    mean, scale, quat, op, rgb = (_f32(gauss[k]) for k in ("mean", "scale", "quat", "opacity", "rgb"))
+    pp = _f32(probe_pos)
+    probe_of, ti, tj = (np.ascontiguousarray(v, dtype=np.int32) for v in (probe_of, ti, tj))
+    n = len(probe_of)
+    o_rgb, o_occ, o_d = np.empty((n, 3)), np.empty(n), np.empty(n)
+    o_fl = np.empty(n, np.int32)
+    lib().orc_bake_rays(C.c_int64(len(mean)), _p(mean), _p(scale), _p(quat), _p(op), _p(rgb), _p(pp),
+                        C.c_int(R), C.c_int64(n), _p(probe_of), _p(ti), _p(tj), C.c_double(t_near),
+                        C.c_double(alpha_min), C.c_double(alpha_max), C.c_double(t_stop),
+                        _p(o_rgb), _p(o_occ), _p(o_d), _p(o_fl))
+    return o_rgb, o_occ, o_d, o_fl
+
+
+def bake(gauss, probe_pos, R, probes=None, **kw):
+    """Bake whole probes (all R*R texels). Returns maps [P',R,R,3], [P',R,R],
+    [P',R,R] and flags [P',R,R] for the probes listed (default: all)."""
+    probes = np.arange(len(probe_pos)) if probes is None else np.asarray(probes)
+    jj, ii = np.meshgrid(np.arange(R), np.arange(R), indexing="ij")
+    po = np.repeat(probes, R * R)
+    ti = np.tile(ii.reshape(-1), len(probes))
+    tj = np.tile(jj.reshape(-1), len(probes))
+    rgb, occ, dep, fl = bake_rays(gauss, probe_pos, R, po, ti, tj, **kw)
+    P = len(probes)
+    return (rgb.reshape(P, R, R, 3), occ.reshape(P, R, R), dep.reshape(P, R, R), fl.reshape(P, R, R))
+
+
+# ----------------------------------------------------------------------------
+# query / shade
+# ----------------------------------------------------------------------------
+def snap_key_for(eps_snap=1e-6):
+    """Largest quantised squared distance (units of 2^-40) within eps_snap."""
+    return int(np.floor((eps_snap * 1048576.0) ** 2))
+
+
+def knn(x, probe_pos, K):
+    x, pp = _f32(x), _f32(probe_pos)
+    M = len(x)
+    idx = np.empty((M, K), np.int32)
+    key = np.empty((M, K), np.uint64)
+    lib().orc_knn(C.c_int64(M), _p(x), C.c_int32(len(pp)), _p(pp), C.c_int32(K), _p(idx), _p(key))
+    return idx, key
+
+
+def weights(x, n, probe_pos, idx, key, snap_key=None):
+    x, n, pp = _f32(x), _f32(n), _f32(probe_pos)
+    idx = np.ascontiguousarray(idx, np.int32)
+    key = np.ascontiguousarray(key, np.uint64)
+    M, K = idx.shape
+    W = np.empty((M, K))
+    sk = snap_key_for() if snap_key is None else snap_key
+    lib().orc_weights(C.c_int64(M), _p(x), _p(n), _p(pp), C.c_int32(K), _p(idx), _p(key),
+                      C.c_uint64(sk), _p(W))
+    return W
+
+
+def query_shade(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S,
+                mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None):
+    """FP64 query + shade. Returns out [M,3], idx [M,K], W [M,K]."""
+    x, n, wo, albedo, rough, metal = (_f32(v) for v in (x, n, wo, albedo, rough, metal))
+    pp, mr, mo, env = _f32(probe_pos), _f32(maps_rgb), _f32(maps_occ), _f32(env)
+    P, R = mr.shape[0], mr.shape[1]
+    He, We, _ = env.shape
+    M = len(x)
+    out = np.empty((M, 3))
+    idx = np.empty((M, K), np.int32)
+    W = np.empty((M, K))
+    dp = None if dirs is None else _f64(dirs)
+    sk = snap_key_for() if snap_key is None else snap_key
+    lib().orc_query_shade(C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal),
+                          C.c_int32(P), _p(pp), C.c_int32(R), _p(mr), _p(mo), C.c_int32(He), C.c_int32(We),
+                          _p(env), C.c_int32(S), None if dp is None else _p(dp), C.c_int32(K),
+                          C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), _p(out), _p(idx), _p(W))
+    return out, idx, W

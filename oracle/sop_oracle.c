@@ -1,0 +1,563 @@
+/*
+ * FP64 CPU oracle for the Surface Octahedral Probe (SOP) bake and query/shade
+ * of ComGS (arXiv 2510.07729).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or
+ * load this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it. It shares no code, header or constant table
+ * with the CUDA library: every step below is written out plainly, in double
+ * precision, in the order the paper states it, with no blocking, fusion or
+ * culling that the definition does not contain.
+ *
+ * Where the paper is silent the readings used are (each one also tested):
+ *   - octahedral map: Cigolle et al. 2014 ("A Survey of Efficient
+ *     Representations for Independent Unit Vectors"), z-up, world frame
+ *     (Sec. 3.1.2 only names octahedral textures [Praun & Hoppe 2003]);
+ *   - bilinear fetch across the octahedral folds: the DDGI border rule of
+ *     Majercik et al. 2019 (the work the back-face weight of Sec. 3.1.2 cites);
+ *   - ray-Gaussian response: the 3D Gaussian's maximum along the ray,
+ *     alpha = min(alpha_max, o exp(-m^2/2)), kept when alpha >= alpha_min,
+ *     composited front to back by Eq. 1 (T_i = prod (1 - alpha_j));
+ *   - K nearest probes (Eq. 4) by an exact integer squared distance on
+ *     positions quantised to 2^-20, ties to the lower probe index;
+ *   - weights w_s = 1/|d_k| (Eq. 5), w_b = 0.5 (1 + d_k/|d_k| . n) + 0.01
+ *     (Eq. 6) with n the shading normal, one-hot on the nearest probe when it
+ *     coincides with the shading point;
+ *   - S_r directions: Hammersley with centred first coordinate,
+ *     z_i = (i + 1/2)/S, phi_i = 2 pi radical_inverse_2(i), uniform on the
+ *     hemisphere, rotated by the branchless ONB of Duff et al. 2017;
+ *   - "simplified Disney" BRDF (Sec. 3.1.2): Lambert (1-m) a/pi plus GGX
+ *     specular D F G / (4 NdotL NdotV), alpha = r^2, Schlick-GGX k=(r+1)^2/8,
+ *     F0 = 0.08 spec (1-m) + a m, Schlick Fresnel;
+ *   - equirectangular environment, z-up, u = (phi + pi)/(2 pi),
+ *     v = theta/pi, bilinear with u wrapping and v clamped.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Octahedral map (Sec. 3.1.2, octahedral textures).                         */
+/* ------------------------------------------------------------------------ */
+static double sgn_nz(double v) { return v >= 0.0 ? 1.0 : -1.0; }
+
+/* Unit direction -> uv in [0,1]^2. */
+void orc_oct_encode(const double* d, double* uv)
+{
+    double l1 = fabs(d[0]) + fabs(d[1]) + fabs(d[2]);
+    double px = d[0] / l1, py = d[1] / l1;
+    if (d[2] < 0.0) {
+        double qx = (1.0 - fabs(py)) * sgn_nz(px);
+        double qy = (1.0 - fabs(px)) * sgn_nz(py);
+        px = qx;
+        py = qy;
+    }
+    uv[0] = 0.5 * (px + 1.0);
+    uv[1] = 0.5 * (py + 1.0);
+}
+
+/* uv -> the point of the L1 unit octahedron (not normalised). */
+void orc_oct_decode_l1(const double* uv, double* d)
+{
+    double px = 2.0 * uv[0] - 1.0, py = 2.0 * uv[1] - 1.0;
+    double z = 1.0 - fabs(px) - fabs(py);
+    if (z < 0.0) {
+        double qx = (1.0 - fabs(py)) * sgn_nz(px);
+        double qy = (1.0 - fabs(px)) * sgn_nz(py);
+        px = qx;
+        py = qy;
+    }
+    d[0] = px;
+    d[1] = py;
+    d[2] = z;
+}
+
+/* uv -> unit direction. */
+void orc_oct_decode(const double* uv, double* d)
+{
+    orc_oct_decode_l1(uv, d);
+    double n = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    d[0] /= n;
+    d[1] /= n;
+    d[2] /= n;
+}
+
+/* Texel (i = column along u, j = row along v) centre direction. */
+void orc_texel_dir(int R, int i, int j, double* d)
+{
+    double uv[2] = {(i + 0.5) / R, (j + 0.5) / R};
+    orc_oct_decode(uv, d);
+}
+
+/* Border rule: a texel index pair in [-1, R]^2 -> the texel it stands for.
+ * Crossing an edge of the square mirrors the index along that edge; the
+ * four corners map to the diagonally opposite corner. */
+void orc_oct_wrap(int R, int i, int j, int* si, int* sj)
+{
+    int oi = (i < 0) || (i >= R), oj = (j < 0) || (j >= R);
+    if (oi && oj) {
+        *si = (i < 0) ? R - 1 : 0;
+        *sj = (j < 0) ? R - 1 : 0;
+    } else if (oi) {
+        *si = (i < 0) ? 0 : R - 1;
+        *sj = R - 1 - j;
+    } else if (oj) {
+        *si = R - 1 - i;
+        *sj = (j < 0) ? 0 : R - 1;
+    } else {
+        *si = i;
+        *sj = j;
+    }
+}
+
+/* Bilinear read of a compact map [R][R][C] (row j, column i) at uv. */
+void orc_oct_bilerp(const double* map, int R, int C, const double* uv, double* out)
+{
+    double s = uv[0] * R - 0.5, t = uv[1] * R - 0.5;
+    double fi = floor(s), fj = floor(t);
+    double fu = s - fi, fv = t - fj;
+    int i0 = (int)fi, j0 = (int)fj;
+    for (int c = 0; c < C; ++c) out[c] = 0.0;
+    for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+            double w = (di ? fu : 1.0 - fu) * (dj ? fv : 1.0 - fv);
+            int si, sj;
+            orc_oct_wrap(R, i0 + di, j0 + dj, &si, &sj);
+            const double* tex = map + ((size_t)sj * R + si) * C;
+            for (int c = 0; c < C; ++c) out[c] += w * tex[c];
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Probe bake (Sec. 3.1.2 "initialised via ray tracing"; Sec. 3.2.2 occlusion */
+/* caching; compositing of Eq. 1; depth normalisation D/W of Sec. 3.1).       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double t, alpha;
+    int64_t idx;
+} orc_hit;
+
+static int hit_cmp(const void* a, const void* b)
+{
+    const orc_hit* x = (const orc_hit*)a;
+    const orc_hit* y = (const orc_hit*)b;
+    if (x->t < y->t) return -1;
+    if (x->t > y->t) return 1;
+    return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
+}
+
+/* Rotation matrix of a unit quaternion (w, x, y, z); columns are the
+ * Gaussian's local axes in world space. */
+static void quat_to_rot(const float* q4, double Rm[3][3])
+{
+    double w = q4[0], x = q4[1], y = q4[2], z = q4[3];
+    double n = sqrt(w * w + x * x + y * y + z * z);
+    w /= n; x /= n; y /= n; z /= n;
+    Rm[0][0] = 1 - 2 * (y * y + z * z); Rm[0][1] = 2 * (x * y - w * z);     Rm[0][2] = 2 * (x * z + w * y);
+    Rm[1][0] = 2 * (x * y + w * z);     Rm[1][1] = 1 - 2 * (x * x + z * z); Rm[1][2] = 2 * (y * z - w * x);
+    Rm[2][0] = 2 * (x * z - w * y);     Rm[2][1] = 2 * (y * z + w * x);     Rm[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+/* Flags a texel whose FP32 result may legitimately differ from this FP64
+ * one because a floating-point comparison is within rounding of flipping. */
+enum {
+    ORC_FLAG_ALPHA_MIN = 1, /* a response within 1e-4 relative of alpha_min  */
+    ORC_FLAG_ORDER = 2,     /* two kept hits whose t* differ by <= 1e-6 rel.  */
+    ORC_FLAG_TNEAR = 4,     /* a t* within rounding of t_near                 */
+    ORC_FLAG_TSTOP = 8,     /* transmittance within 1e-3 relative of T_stop   */
+};
+
+/* Bake n_rays texel rays. Ray r starts at probe probe_of[r] and points at the
+ * centre of texel (ti[r], tj[r]) of an R x R map. Outputs per ray: RGB
+ * indirect radiance L, occlusion O = 1 - T, depth D = sum(T a t*)/sum(T a)
+ * (0 when nothing is hit) and ambiguity flags. */
+void orc_bake_rays(int64_t N, const float* mean, const float* scale, const float* quat,
+                   const float* opacity, const float* rgb, const float* probe_pos, int R,
+                   int64_t n_rays, const int32_t* probe_of, const int32_t* ti, const int32_t* tj,
+                   double t_near, double alpha_min, double alpha_max, double t_stop,
+                   double* out_rgb, double* out_occ, double* out_depth, int32_t* out_flags)
+{
+    /* Per-Gaussian M = diag(1/s) R^T, so that m^2(x) = |M (x - mu)|^2. */
+    double* Mg = (double*)malloc(sizeof(double) * 9 * (size_t)(N > 0 ? N : 1));
+    for (int64_t g = 0; g < N; ++g) {
+        double Rm[3][3];
+        quat_to_rot(quat + 4 * g, Rm);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Mg[9 * g + 3 * a + b] = Rm[b][a] / (double)scale[3 * g + a];
+    }
+#pragma omp parallel
+    {
+        size_t cap = 1024;
+        orc_hit* hits = (orc_hit*)malloc(sizeof(orc_hit) * cap);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t r = 0; r < n_rays; ++r) {
+            const float* p = probe_pos + 3 * (size_t)probe_of[r];
+            double d[3];
+            orc_texel_dir(R, ti[r], tj[r], d);
+            size_t nh = 0;
+            int flags = 0;
+            for (int64_t g = 0; g < N; ++g) {
+                const double* M = Mg + 9 * g;
+                double del[3] = {(double)p[0] - mean[3 * g], (double)p[1] - mean[3 * g + 1],
+                                 (double)p[2] - mean[3 * g + 2]};
+                double u[3], w[3];
+                for (int a = 0; a < 3; ++a) {
+                    u[a] = M[3 * a] * del[0] + M[3 * a + 1] * del[1] + M[3 * a + 2] * del[2];
+                    w[a] = M[3 * a] * d[0] + M[3 * a + 1] * d[1] + M[3 * a + 2] * d[2];
+                }
+                double A = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+                double B = w[0] * u[0] + w[1] * u[1] + w[2] * u[2];
+                double ts = -B / A;
+                double m2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    double e = u[a] + ts * w[a];
+                    m2 += e * e;
+                }
+                double resp = opacity[g] * exp(-0.5 * m2);
+                double dl = sqrt(del[0] * del[0] + del[1] * del[1] + del[2] * del[2]);
+                if (fabs(resp - alpha_min) <= 1e-4 * alpha_min && ts > t_near) flags |= ORC_FLAG_ALPHA_MIN;
+                if (resp >= alpha_min && fabs(ts - t_near) <= 1e-5 * (dl + 1e-3)) flags |= ORC_FLAG_TNEAR;
+                if (ts <= t_near) continue;
+                if (resp < alpha_min) continue;
+                if (nh == cap) {
+                    cap *= 2;
+                    hits = (orc_hit*)realloc(hits, sizeof(orc_hit) * cap);
+                }
+                hits[nh].t = ts;
+                hits[nh].alpha = resp < alpha_max ? resp : alpha_max;
+                hits[nh].idx = g;
+                ++nh;
+            }
+            qsort(hits, nh, sizeof(orc_hit), hit_cmp);
+            double T = 1.0, L[3] = {0, 0, 0}, Dacc = 0.0, W = 0.0;
+            for (size_t k = 0; k < nh; ++k) {
+                if (k + 1 < nh && hits[k + 1].t - hits[k].t <= 1e-6 * fabs(hits[k + 1].t)) flags |= ORC_FLAG_ORDER;
+                double wk = T * hits[k].alpha;
+                const float* c = rgb + 3 * hits[k].idx;
+                L[0] += wk * c[0];
+                L[1] += wk * c[1];
+                L[2] += wk * c[2];
+                Dacc += wk * hits[k].t;
+                W += wk;
+                T *= (1.0 - hits[k].alpha);
+                if (t_stop > 0.0 && fabs(T - t_stop) <= 1e-3 * t_stop) flags |= ORC_FLAG_TSTOP;
+                if (T < t_stop) break;
+            }
+            out_rgb[3 * r] = L[0];
+            out_rgb[3 * r + 1] = L[1];
+            out_rgb[3 * r + 2] = L[2];
+            out_occ[r] = 1.0 - T;
+            out_depth[r] = (W > 1e-8) ? Dacc / W : 0.0;
+            out_flags[r] = flags;
+        }
+        free(hits);
+    }
+    free(Mg);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Query: K nearest probes and blend weights (Sec. 3.1.2, Eq. 4-6).           */
+/* ------------------------------------------------------------------------ */
+static int64_t quantise(float v) { return (int64_t)nearbyint((double)v * 1048576.0); }
+
+/* Exact K nearest probes of each point, by the integer squared distance of
+ * positions quantised to 2^-20, ties to the lower probe index. */
+void orc_knn(int64_t M, const float* x, int32_t P, const float* probe_pos, int32_t K,
+             int32_t* out_idx, uint64_t* out_key)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < M; ++m) {
+        int64_t qx = quantise(x[3 * m]), qy = quantise(x[3 * m + 1]), qz = quantise(x[3 * m + 2]);
+        int32_t* bi = out_idx + (size_t)m * K;
+        uint64_t* bk = out_key + (size_t)m * K;
+        int n = 0;
+        for (int32_t p = 0; p < P; ++p) {
+            int64_t dx = quantise(probe_pos[3 * p]) - qx;
+            int64_t dy = quantise(probe_pos[3 * p + 1]) - qy;
+            int64_t dz = quantise(probe_pos[3 * p + 2]) - qz;
+            uint64_t key = (uint64_t)(dx * dx) + (uint64_t)(dy * dy) + (uint64_t)(dz * dz);
+            /* insertion into the sorted list of the best K (key, index) */
+            if (n == K && key >= bk[K - 1]) continue; /* equal key: larger index loses */
+            int pos = (n < K) ? n++ : K - 1;
+            while (pos > 0 && bk[pos - 1] > key) {
+                bk[pos] = bk[pos - 1];
+                bi[pos] = bi[pos - 1];
+                --pos;
+            }
+            bk[pos] = key;
+            bi[pos] = p;
+        }
+    }
+}
+
+/* Normalised blend weights W_k = w_s w_b / sum_j w_s w_b (Eq. 4-6) for the
+ * neighbours found by orc_knn. When the nearest probe's quantised squared
+ * distance is <= snap_key the point sits on that probe: W is one-hot. */
+void orc_weights(int64_t M, const float* x, const float* n, const float* probe_pos, int32_t K,
+                 const int32_t* idx, const uint64_t* key, uint64_t snap_key, double* out_w)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < M; ++m) {
+        double* W = out_w + (size_t)m * K;
+        if (key[(size_t)m * K] <= snap_key) {
+            for (int k = 0; k < K; ++k) W[k] = (k == 0) ? 1.0 : 0.0;
+            continue;
+        }
+        double nn[3] = {n[3 * m], n[3 * m + 1], n[3 * m + 2]};
+        double nl = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+        double sum = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const float* p = probe_pos + 3 * (size_t)idx[(size_t)m * K + k];
+            double d[3] = {(double)p[0] - x[3 * m], (double)p[1] - x[3 * m + 1], (double)p[2] - x[3 * m + 2]};
+            double dl = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double ws = 1.0 / dl;
+            double wb = 0.5 * (1.0 + (d[0] * nn[0] + d[1] * nn[1] + d[2] * nn[2]) / (dl * nl)) + 0.01;
+            W[k] = ws * wb;
+            sum += W[k];
+        }
+        for (int k = 0; k < K; ++k) W[k] /= sum;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Light directions, frame, environment and BRDF (Sec. 3.1.2, Eq. 2-3).        */
+/* ------------------------------------------------------------------------ */
+static double radical_inverse2(uint32_t i)
+{
+    double r = 0.0, f = 0.5;
+    while (i) {
+        if (i & 1u) r += f;
+        f *= 0.5;
+        i >>= 1;
+    }
+    return r;
+}
+
+/* The S_r local directions (z = cos theta about the normal). */
+void orc_hammersley(int32_t S, double* out)
+{
+    for (int32_t i = 0; i < S; ++i) {
+        double z = (i + 0.5) / S;
+        double phi = 2.0 * M_PI * radical_inverse2((uint32_t)i);
+        double s = sqrt(1.0 - z * z);
+        out[3 * i] = s * cos(phi);
+        out[3 * i + 1] = s * sin(phi);
+        out[3 * i + 2] = z;
+    }
+}
+
+/* Orthonormal frame (t, b, n) of a unit normal (Duff et al. 2017). */
+void orc_onb(const double* n, double* t, double* b)
+{
+    double sg = n[2] >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sg + n[2]);
+    double c = n[0] * n[1] * a;
+    t[0] = 1.0 + sg * n[0] * n[0] * a;
+    t[1] = sg * c;
+    t[2] = -sg * n[0];
+    b[0] = c;
+    b[1] = sg + n[1] * n[1] * a;
+    b[2] = -n[1];
+}
+
+/* Equirectangular environment lookup L_dir(w), bilinear, u wraps, v clamps. */
+void orc_env_lookup(const float* env, int32_t He, int32_t We, const double* w, double* out)
+{
+    double theta = atan2(sqrt(w[0] * w[0] + w[1] * w[1]), w[2]);
+    double phi = atan2(w[1], w[0]);
+    double u = (phi + M_PI) / (2.0 * M_PI), v = theta / M_PI;
+    double s = u * We - 0.5, t = v * He - 0.5;
+    double fs = floor(s), ft = floor(t);
+    double a = s - fs, b = t - ft;
+    int c0 = (int)fs, r0 = (int)ft;
+    out[0] = out[1] = out[2] = 0.0;
+    for (int dr = 0; dr < 2; ++dr)
+        for (int dc = 0; dc < 2; ++dc) {
+            int r = r0 + dr, c = c0 + dc;
+            r = r < 0 ? 0 : (r > He - 1 ? He - 1 : r);
+            c = ((c % We) + We) % We;
+            double wgt = (dc ? a : 1.0 - a) * (dr ? b : 1.0 - b);
+            const float* e = env + ((size_t)r * We + c) * 3;
+            out[0] += wgt * e[0];
+            out[1] += wgt * e[1];
+            out[2] += wgt * e[2];
+        }
+}
+
+/* GGX / Trowbridge-Reitz normal distribution D(h) for alpha = r^2, written
+ * with sin^2 = |n x h|^2 so that it stays accurate near n . h = 1. */
+double orc_ggx_D(double NdotH, double sin2, double rough)
+{
+    double al = rough * rough, a2 = al * al;
+    double den = NdotH * NdotH * a2 + sin2;
+    return a2 / (M_PI * den * den);
+}
+
+/* Schlick-GGX masking term of one direction, k = (r + 1)^2 / 8. */
+double orc_smith_G1(double NdotX, double rough)
+{
+    double k = (rough + 1.0) * (rough + 1.0) / 8.0;
+    return NdotX / (NdotX * (1.0 - k) + k);
+}
+
+/* Schlick Fresnel. */
+double orc_fresnel(double F0, double VdotH) { return F0 + (1.0 - F0) * pow(1.0 - VdotH, 5.0); }
+
+/* Simplified Disney BRDF value f(wo, wi) per channel (Sec. 3.1.2). */
+void orc_brdf(const double* n, const double* wo, const double* wi, const double* albedo, double rough,
+              double metal, double spec, double* f)
+{
+    double h[3] = {wi[0] + wo[0], wi[1] + wo[1], wi[2] + wo[2]};
+    double hl = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    if (hl < 1e-30) {
+        h[0] = n[0]; h[1] = n[1]; h[2] = n[2];
+    } else {
+        h[0] /= hl; h[1] /= hl; h[2] /= hl;
+    }
+    double NdotL = n[0] * wi[0] + n[1] * wi[1] + n[2] * wi[2];
+    double NdotV = n[0] * wo[0] + n[1] * wo[1] + n[2] * wo[2];
+    if (NdotV < 1e-4) NdotV = 1e-4;
+    double NdotH = n[0] * h[0] + n[1] * h[1] + n[2] * h[2];
+    double VdotH = wo[0] * h[0] + wo[1] * h[1] + wo[2] * h[2];
+    double cx = n[1] * h[2] - n[2] * h[1], cy = n[2] * h[0] - n[0] * h[2], cz = n[0] * h[1] - n[1] * h[0];
+    double D = orc_ggx_D(NdotH, cx * cx + cy * cy + cz * cz, rough);
+    double G = orc_smith_G1(NdotL, rough) * orc_smith_G1(NdotV, rough);
+    for (int c = 0; c < 3; ++c) {
+        double F0 = 0.08 * spec * (1.0 - metal) + albedo[c] * metal;
+        double F = orc_fresnel(F0, VdotH);
+        f[c] = (1.0 - metal) * albedo[c] / M_PI + D * F * G / (4.0 * NdotL * NdotV);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Query + shade (Sec. 3.1.2 Eq. 2-6; shadow ratio of Sec. 3.2.2, Eq. 7-9).    */
+/* ------------------------------------------------------------------------ */
+enum { ORC_MODE_SHADE = 0, ORC_MODE_SHADOW = 1 };
+
+/* For each shading point: K nearest probes, weights, then the Monte Carlo sum
+ * over the S directions of
+ *   shade : C = 2pi/S sum f ((1 - O) L_dir + L_in) (n . w_i)      (Eq. 3, 4)
+ *   shadow: S_c = sum L_dir (1 - O) (n . w_i) / sum L_dir (n . w_i) (Eq. 7-9)
+ * with O and L_in blended from the probes' octahedral maps. maps_rgb is the
+ * compact [P][R][R][3] radiance, maps_occ the [P][R][R] occlusion. dirs is the
+ * local direction set [S][3]; NULL selects orc_hammersley(S). */
+void orc_query_shade(int64_t M, const float* x, const float* n, const float* wo, const float* albedo,
+                     const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
+                     const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We, const float* env,
+                     int32_t S, const double* dirs, int32_t K, int32_t mode, double spec, uint64_t snap_key,
+                     double* out, int32_t* out_idx, double* out_w)
+{
+    double* dl = (double*)malloc(sizeof(double) * 3 * (size_t)S);
+    if (dirs) memcpy(dl, dirs, sizeof(double) * 3 * (size_t)S);
+    else orc_hammersley(S, dl);
+    size_t RR = (size_t)R * R;
+    double* mrgb = (double*)malloc(sizeof(double) * 3 * RR * (size_t)P);
+    double* mocc = (double*)malloc(sizeof(double) * RR * (size_t)P);
+    for (size_t i = 0; i < 3 * RR * (size_t)P; ++i) mrgb[i] = maps_rgb[i];
+    for (size_t i = 0; i < RR * (size_t)P; ++i) mocc[i] = maps_occ[i];
+    uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)M * K);
+    orc_knn(M, x, P, probe_pos, K, out_idx, key);
+    orc_weights(M, x, n, probe_pos, K, out_idx, key, snap_key, out_w);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < M; ++m) {
+        double nn[3] = {n[3 * m], n[3 * m + 1], n[3 * m + 2]};
+        double nl = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+        nn[0] /= nl; nn[1] /= nl; nn[2] /= nl;
+        double vo[3] = {wo[3 * m], wo[3 * m + 1], wo[3 * m + 2]};
+        double a[3] = {albedo[3 * m], albedo[3 * m + 1], albedo[3 * m + 2]};
+        double t[3], b[3];
+        orc_onb(nn, t, b);
+        double acc[3] = {0, 0, 0}, den[3] = {0, 0, 0};
+        for (int32_t i = 0; i < S; ++i) {
+            const double* l = dl + 3 * i;
+            double w[3];
+            for (int c = 0; c < 3; ++c) w[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
+            double uv[2];
+            orc_oct_encode(w, uv);
+            double O = 0.0, Lin[3] = {0, 0, 0};
+            for (int k = 0; k < K; ++k) {
+                int32_t p = out_idx[(size_t)m * K + k];
+                double Wk = out_w[(size_t)m * K + k];
+                double o1, l3[3];
+                orc_oct_bilerp(mocc + RR * p, R, 1, uv, &o1);
+                orc_oct_bilerp(mrgb + 3 * RR * p, R, 3, uv, l3);
+                O += Wk * o1;
+                for (int c = 0; c < 3; ++c) Lin[c] += Wk * l3[c];
+            }
+            double Ld[3];
+            orc_env_lookup(env, He, We, w, Ld);
+            double NdotL = nn[0] * w[0] + nn[1] * w[1] + nn[2] * w[2];
+            if (mode == ORC_MODE_SHADE) {
+                double f[3];
+                orc_brdf(nn, vo, w, a, rough[m], metal[m], spec, f);
+                for (int c = 0; c < 3; ++c) acc[c] += f[c] * ((1.0 - O) * Ld[c] + Lin[c]) * NdotL;
+            } else {
+                for (int c = 0; c < 3; ++c) {
+                    acc[c] += Ld[c] * (1.0 - O) * NdotL;
+                    den[c] += Ld[c] * NdotL;
+                }
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (mode == ORC_MODE_SHADE) out[3 * m + c] = 2.0 * M_PI / S * acc[c];
+            else out[3 * m + c] = (den[c] < 1e-20) ? 1.0 : acc[c] / den[c];
+        }
+    }
+    free(key);
+    free(mocc);
+    free(mrgb);
+    free(dl);
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Batched entry points for the tests (loops over the single-item routines).  */
+/* ------------------------------------------------------------------------ */
+void orc_oct_encode_n(int64_t n, const double* d, double* uv)
+{
+    for (int64_t i = 0; i < n; ++i) orc_oct_encode(d + 3 * i, uv + 2 * i);
+}
+
+void orc_oct_decode_n(int64_t n, const double* uv, double* d, int l1_only)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        if (l1_only) orc_oct_decode_l1(uv + 2 * i, d + 3 * i);
+        else orc_oct_decode(uv + 2 * i, d + 3 * i);
+    }
+}
+
+void orc_oct_bilerp_n(int64_t n, const double* map, int R, int C, const double* uv, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) orc_oct_bilerp(map, R, C, uv + 2 * i, out + (size_t)C * i);
+}
+
+void orc_env_lookup_n(int64_t n, const float* env, int32_t He, int32_t We, const double* w, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) orc_env_lookup(env, He, We, w + 3 * i, out + 3 * i);
+}
+
+void orc_brdf_n(int64_t n, const double* nrm, const double* wo, const double* wi, const double* albedo,
+                const double* rough, const double* metal, double spec, double* f)
+{
+    for (int64_t i = 0; i < n; ++i)
+        orc_brdf(nrm + 3 * i, wo + 3 * i, wi + 3 * i, albedo + 3 * i, rough[i], metal[i], spec, f + 3 * i);
+}
+
+void orc_onb_n(int64_t n, const double* nrm, double* t, double* b)
+{
+    for (int64_t i = 0; i < n; ++i) orc_onb(nrm + 3 * i, t + 3 * i, b + 3 * i);
+}
