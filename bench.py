@@ -1,0 +1,404 @@
+"""Benchmark of the SOP hot path on GB300: probe bake + probe query/shade.
+
+One step = one pass of the whole path over the 'object' workload
+(200,000 anisotropic Gaussians on 5 ellipsoids, 4,096 probes at 16x16,
+418,111 shading points from an 800x800 view, K=8, S=128, 256x512 HDR
+environment): sop_bake of all 4,096 probes (1,048,576 texel rays,
+Gaussian binning, grid walk, compositing, atlas packing) followed by
+sop_query_shade of all points against the freshly baked atlas (nearest
+probes, weights, S directions, BRDF). `value` is shaded point-directions
+per second of that step; the bake's texels/s is reported beside it.
+
+Usage (driver contract):
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+Multi-GPU: one replica per rank (the path shards by independent probes and
+points; no collective on the data path), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="object", choices=["object", "compose", "tiny"])
+    ap.add_argument("--part", default="step", choices=["step", "bake", "query"],
+                    help="profiling aid: run only one half (the JSON line then covers that half)")
+    ap.add_argument("--probes", type=int, default=0, help="profiling aid: bake only the first N probes")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                r = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                    "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if r.returncode == 0 and r.stdout.strip():
+                    self.samples.append([v.strip() for v in r.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 5 + i and
+                          s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def load_workload(name):
+    from paper_2510_07729_gb300 import inputs as I
+    if name == "object":
+        c = I.make_object()
+        return dict(name="object", gauss=c["gauss"], probe_pos=c["probe_pos"], probe_nrm=c["probe_nrm"], R=c["R"],
+                    pts={k: c[k] for k in ("x", "n", "wo", "albedo", "rough", "metal")}, env=c["env"], K=c["K"],
+                    S=c["S"], mode=0)
+    if name == "tiny":
+        c = I.make_tiny()
+        return dict(name="tiny", gauss=c["gauss"], probe_pos=c["probe_pos"], probe_nrm=c["probe_nrm"], R=c["R"],
+                    pts={k: c[k] for k in ("x", "n", "wo", "albedo", "rough", "metal")}, env=c["env"], K=c["K"],
+                    S=c["S"], mode=0)
+    c = I.make_compose()
+    d = c["shadow"]
+    return dict(name="compose-shadow", gauss=c["gauss_object"], probe_pos=d["probe_pos"], probe_nrm=d["probe_nrm"],
+                R=c["R"], pts={k: d[k] for k in ("x", "n", "wo", "albedo", "rough", "metal")}, env=c["env"],
+                K=c["K"], S=c["S"], mode=1)
+
+
+# algorithmic FP32 work of one shaded point-direction (K probes, SHADE mode):
+# frame rotation 15, octahedral encode 12, texel coordinates 10, per probe
+# 4 bilinear weights x 4 channels (16 FMA = 32 FLOP) + 4 weight products,
+# environment uv 2 atan2 (~40) + bilinear 3x4 FMA (24) + weights 8, BRDF
+# (half vector 12, dots 15, D 8, G 4, Fresnel 12, combine 12) and the
+# accumulation 9.
+def flop_per_point_dir(K, mode):
+    f = 15 + 12 + 10 + K * (32 + 4) + 40 + 24 + 8 + 9
+    if mode == 0:
+        f += 12 + 15 + 8 + 4 + 12 + 12
+    return f
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2510_07729_gb300 import sop
+    sop.load()
+    W = load_workload(args.workload)
+    P = len(W["probe_pos"]) if args.probes <= 0 else min(args.probes, len(W["probe_pos"]))
+    R, K, S, mode = W["R"], W["K"], W["S"], W["mode"]
+    M = len(W["pts"]["x"])
+
+    def cu(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    g = {k: cu(v) for k, v in W["gauss"].items()}
+    ppos = cu(W["probe_pos"][:P])
+    pts = {k: cu(v) for k, v in W["pts"].items()}
+    env = cu(W["env"])
+    atlas = sop.make_atlas(ppos, R)
+    out = torch.empty((M, 3), dtype=torch.float32, device=dev)
+    qws = torch.empty(sop.query_workspace_bytes(P, M, K, S, env.shape[0], env.shape[1], mode), dtype=torch.uint8,
+                      device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    pargs = [pts[k] for k in ("x", "n", "wo", "albedo", "rough", "metal")]
+    do_bake = args.part in ("step", "bake")
+    do_query = args.part in ("step", "query")
+    if not do_bake:
+        sop.bake(g, atlas)  # query-only runs shade against a baked atlas
+
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(evs):
+        if do_bake:
+            evs[0].record(stream)
+            sop.bake(g, atlas)
+            evs[1].record(stream)
+        if do_query:
+            evs[2].record(stream)
+            sop.query_shade(*pargs, atlas, env, K, S, mode=mode, out=out, workspace=qws)
+            evs[3].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step([ev() for _ in range(4)])
+    torch.cuda.synchronize()
+
+    gpu_index = torch.cuda.get_device_properties(dev).index if hasattr(
+        torch.cuda.get_device_properties(dev), "index") else local_rank
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_index = vis.split(",")[local_rank] if vis else str(local_rank)
+    records = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    with ClockSampler(smi_index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)  # L2 flush between timed steps (outside the step events)
+            evs = [ev() for _ in range(4)]
+            step(evs)
+            records.append(evs)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+
+    t_bake = [r[0].elapsed_time(r[1]) for r in records] if do_bake else [0.0]
+    t_query = [r[2].elapsed_time(r[3]) for r in records] if do_query else [0.0]
+    ms_step = float(np.sum(t_bake) + np.sum(t_query)) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms_step, float(np.mean(t_bake)), float(np.mean(t_query))], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step, mb, mq = tt.tolist()
+    else:
+        mb, mq = float(np.mean(t_bake)), float(np.mean(t_query))
+
+    texels = P * R * R
+    pd = M * S
+    if args.part == "bake":
+        units, unit_name = texels, "texels/s"
+    else:
+        units, unit_name = pd, "point-dirs/s"
+    value = world * units / (ms_step * 1e-3)
+
+    # e2e: public API from pinned host buffers, H2D + bake + query + D2H each step
+    e2e = None
+    if not args.no_e2e and args.part == "step":
+        e2e = measure_e2e(args, W, P, dev, sop, flush)
+
+    # roofline of the query/shade kernel, measured live on its stream
+    roof = None
+    if do_query:
+        fl = flop_per_point_dir(K, mode) * pd
+        ach = fl / (mq * 1e-3) / 1e12
+        peak = N_SMS * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+        roof = {"kernel": "shade_kernel (sop_query_shade call)", "bound": "alu", "achieved": round(ach, 2),
+                "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
+
+    clocks = clk.summary()
+    line = {
+        "metric": "SOP-shaded point-dirs/s (bake + query/shade step)" if args.part != "bake" else
+        "probe-bake texels/s",
+        "value": round(value, 1),
+        "unit": unit_name,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded generators; the paper's SynCom/TensoIR scenes are not available)",
+        "config": {"workload": f"{W['name']}: {len(W['gauss']['mean'])} Gaussians, {P} probes {R}x{R}, "
+                               f"{M} points, K={K}, S={S}, env {W['env'].shape[0]}x{W['env'].shape[1]}",
+                   "part": args.part, "l2": "512 MB buffer written between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "bake": {"ms": round(mb, 4), "texels_per_s": round(texels / (mb * 1e-3), 1) if do_bake else None},
+        "query": {"ms": round(mq, 4), "point_dirs_per_s": round(pd / (mq * 1e-3), 1) if do_query else None},
+        "wall_s_timed_region": round(t_wall, 4),
+        "gpu_launches": launches_per_step(do_bake, do_query, P, R) * args.steps,
+        "clocks": clocks,
+        "roofline": roof,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.part == "step":
+        line["cpu_baseline"] = cpu_baseline(W, P, R, K, S, mode)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def launches_per_step(do_bake, do_query, P, R):
+    n = 0
+    if do_bake:
+        # bbox init, gauss prep, grid setup, bin count, bin scan, bin fill,
+        # texel dirs, trace, atlas pack, depth pack
+        n += 10
+    if do_query:
+        # probe grid, knn, env pack, dirs, shade
+        n += 5
+    return n
+
+
+def measure_e2e(args, W, P, dev, sop, flush):
+    import torch
+    host = {}
+    for k, v in W["gauss"].items():
+        host["g_" + k] = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+    for k, v in W["pts"].items():
+        host["p_" + k] = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+    host["probe_pos"] = torch.from_numpy(np.ascontiguousarray(W["probe_pos"][:P])).pin_memory()
+    host["env"] = torch.from_numpy(np.ascontiguousarray(W["env"])).pin_memory()
+    dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    M = len(W["pts"]["x"])
+    R, K, S, mode = W["R"], W["K"], W["S"], W["mode"]
+    out_h = torch.empty((M, 3), dtype=torch.float32).pin_memory()
+    bi = sum(v.numel() * v.element_size() for v in host.values())
+    bo = out_h.numel() * out_h.element_size()
+
+    def one():
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        g = {k[2:]: dbuf[k] for k in dbuf if k.startswith("g_")}
+        at = sop.make_atlas(dbuf["probe_pos"], R)
+        sop.bake(g, at)
+        o = sop.query_shade(*[dbuf["p_" + k] for k in ("x", "n", "wo", "albedo", "rough", "metal")], at, dbuf["env"],
+                            K, S, mode=mode)
+        out_h.copy_(o, non_blocking=True)
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        one()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    return {"value": round(M * S / (ms * 1e-3), 1), "unit": "point-dirs/s", "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
+
+
+def cpu_baseline(W, P, R, K, S, mode, seconds_hint=True):
+    """The FP64 oracle, as it stands, on a bounded sample of the same
+    workload: 16 probes (4,096 texel rays) of the bake and 4,096 points of
+    the query; scaled to the whole step."""
+    import oracle
+    from paper_2510_07729_gb300 import inputs as I
+    rng = np.random.default_rng(123)
+    probes = np.sort(rng.choice(P, min(16, P), replace=False))
+    t0 = time.perf_counter()
+    rgb, occ, dep, _ = oracle.bake(W["gauss"], W["probe_pos"][:P], R, probes=probes)
+    tb = time.perf_counter() - t0
+    sel, pts = I.subsample(rng, W["pts"], ["x", "n", "wo", "albedo", "rough", "metal"], 4096)
+    maps = I.synthetic_maps(rng, P, R)
+    t0 = time.perf_counter()
+    oracle.query_shade(pts["x"], pts["n"], pts["wo"], pts["albedo"], pts["rough"], pts["metal"], W["probe_pos"][:P],
+                       maps["rgb"], maps["occ"], W["env"], K, S, mode=mode)
+    tq = time.perf_counter() - t0
+    M = len(W["pts"]["x"])
+    t_step = tb * (P / len(probes)) + tq * (M / len(sel))
+    return {"value": round(M * S / t_step, 1), "unit": "point-dirs/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"bake of {len(probes)} probes ({len(probes) * R * R} rays, {tb:.2f} s) + query of "
+                      f"{len(sel)} points x {S} dirs ({tq:.2f} s), scaled to the full step"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle timed on the host cores, each step a
+    bounded sample of the same workload, in the same metric."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2510_07729_gb300 import inputs as I
+    W = load_workload(args.workload)
+    P, R, K, S, mode = len(W["probe_pos"]), W["R"], W["K"], W["S"], W["mode"]
+    M = len(W["pts"]["x"])
+    rng = np.random.default_rng(7)
+    maps = I.synthetic_maps(rng, P, R)
+
+    def one():
+        probes = np.sort(rng.choice(P, 2, replace=False))
+        t0 = time.perf_counter()
+        oracle.bake(W["gauss"], W["probe_pos"], R, probes=probes)
+        tb = time.perf_counter() - t0
+        sel, pts = I.subsample(rng, W["pts"], ["x", "n", "wo", "albedo", "rough", "metal"], 512)
+        t0 = time.perf_counter()
+        oracle.query_shade(pts["x"], pts["n"], pts["wo"], pts["albedo"], pts["rough"], pts["metal"], W["probe_pos"],
+                           maps["rgb"], maps["occ"], W["env"], K, S, mode=mode)
+        tq = time.perf_counter() - t0
+        return tb * (P / 2) + tq * (M / 512)
+
+    for _ in range(args.warmup):
+        one()
+    ts = [one() for _ in range(args.steps)]
+    t = float(np.mean(ts))
+    v = M * S / t
+    line = {"impl": "reference", "metric": "SOP-shaded point-dirs/s (bake + query/shade step)", "value": round(v, 3),
+            "unit": "point-dirs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": W["name"], "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "point-dirs/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "per step: bake of 2 probes + query of 512 points, scaled to the full step"},
+            "e2e": {"value": round(v, 3), "unit": "point-dirs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * libsop: Surface Octahedral Probes (SOPs) of ComGS (arXiv 2510.07729) on one
+ * GB300 (sm_103a). C ABI.
+ *
+ * The library computes the two data-parallel halves of the SOP method:
+ *   - the probe bake: every octahedral texel of every probe shoots a ray that
+ *     is alpha-composited front to back through 3D Gaussians, giving the
+ *     probe's occlusion O, indirect radiance L_in and depth D maps
+ *     (Sec. 3.1.2 "SOPs ... initialised via ray tracing"; Sec. 3.2.2 occlusion
+ *     caching; compositing of Eq. 1; unbiased depth D/W of Sec. 3.1);
+ *   - the probe query + shading that replaces ray tracing: K nearest probes,
+ *     back-face and distance weights (Eq. 4-6), per-direction bilinear
+ *     octahedral fetches, and the Monte Carlo sum of the visibility-weighted
+ *     BRDF against an environment map plus the interpolated indirect term
+ *     (Eq. 2-3), or the shadow ratio S = L_o'/L_o (Eq. 7-9).
+ *
+ * Conventions for every entry point:
+ *   - Every array pointer is DEVICE memory owned by the caller, unless the
+ *     argument says "host". Arrays are C-contiguous float32 unless stated.
+ *   - The library allocates no memory. Scratch space ("workspace") is passed
+ *     in by the caller; its size comes from the matching *_workspace_bytes()
+ *     query and the workspace pointer must be 256-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *     enqueued asynchronously on it unless the entry point says it syncs.
+ *   - Arguments are validated on the host before any launch. A non-OK status
+ *     means nothing was launched (except SOP_ERR_CUDA, which reports a launch
+ *     or runtime error); sop_last_error() then returns a message for the
+ *     calling thread. No exception crosses this boundary.
+ *   - Readings of points the paper leaves open (octahedral map formula,
+ *     border rule, ray-Gaussian response, KNN tie-break, BRDF terms, light
+ *     direction set, environment parameterisation) are stated beside the
+ *     function that applies them.
+ */
+#ifndef SOP_H
+#define SOP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+    SOP_OK = 0,
+    SOP_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or parameter  */
+    SOP_ERR_CUDA = 2,        /* a CUDA launch or runtime call failed        */
+    SOP_ERR_WORKSPACE = 3,   /* workspace missing, misaligned or too small  */
+    SOP_ERR_UNSUPPORTED = 4, /* valid but not implemented (e.g. a dtype)    */
+    SOP_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up          */
+    SOP_ERR_DEVICE = 6       /* a device-side check failed (see message)    */
+} sop_status;
+
+/* Storage types of the probe atlas (Sec. 3.1.2 octahedral textures; the
+ * reduced-precision atlas stores in bf16/fp16, accumulates in fp32). */
+typedef enum { SOP_F32 = 0, SOP_BF16 = 1, SOP_F16 = 2, SOP_FP8E4M3 = 3 } sop_dtype;
+
+/* Query output mode. SHADE: outgoing radiance of Eq. 3 with Eq. 4 lighting.
+ * SHADOW: the ratio S = L_o'/L_o of Eq. 9 with the Lambertian Eq. 7-8 (the
+ * diffuse factor cancels). */
+typedef enum { SOP_MODE_SHADE = 0, SOP_MODE_SHADOW = 1 } sop_mode;
+
+/* A set of n 3D Gaussians, structure of arrays, device memory:
+ * mean [n,3], per-axis scale [n,3] (> 0), rotation quaternion [n,4] in
+ * (w, x, y, z) order (need not be normalised), opacity [n] in [0,1],
+ * colour rgb [n,3]. (Sec. 3.1: centre, quaternion, scaling; the colour is
+ * the radiance a probe ray receives from the Gaussian.) */
+typedef struct {
+    const float* mean;
+    const float* scale;
+    const float* quat;
+    const float* opacity;
+    const float* rgb;
+    int64_t n;
+} sop_gaussians;
+
+/* Probe atlas (caller-owned device memory). P probes, each an R x R
+ * octahedral map stored with a one-texel border ("gutter"), i.e. (R+2)^2
+ * texels per probe, probe-major, then row (v), then column (u):
+ *   rgbo  [P][R+2][R+2][4]  indirect radiance RGB + occlusion O, dtype
+ *                           rgbo_dtype (SOP_F32: 16 B/texel; SOP_BF16 or
+ *                           SOP_F16: 8 B/texel);
+ *   depth [P][R+2][R+2]     mean hit depth D, dtype depth_dtype (SOP_F32,
+ *                           SOP_F16 or SOP_FP8E4M3, stored as D/depth_scale);
+ *                           may be NULL when not needed.
+ * Stored texel (jj, ii) for 1 <= ii, jj <= R is map texel (i = ii-1 along u,
+ * j = jj-1 along v). Border texels copy the texel that the octahedral fold
+ * makes their neighbour: crossing an edge mirrors the index along that edge,
+ * corners take the diagonally opposite corner (the border rule of Majercik
+ * et al. 2019, which keeps bilinear fetches continuous across the folds).
+ * probe_pos [P,3] (and probe_nrm [P,3], informational) are device arrays.
+ * The octahedral map is the one of Cigolle et al. 2014, z-up, world frame:
+ * encode(d) = (p + 1)/2 with p = (d.x, d.y)/|d|_1 folded for d.z < 0. */
+typedef struct {
+    void* rgbo;
+    void* depth;
+    int32_t rgbo_dtype;
+    int32_t depth_dtype;
+    int32_t P;
+    int32_t R;
+    float depth_scale;
+    const float* probe_pos;
+    const float* probe_nrm;
+} sop_atlas;
+
+/* Bake parameters (paper silent; 3D Gaussian splatting conventions):
+ * a Gaussian's response along a ray is its maximum, alpha = min(alpha_max,
+ * o exp(-m^2/2)) with m the Mahalanobis distance at the maximising t*;
+ * responses with t* <= t_near or alpha < alpha_min are skipped; compositing
+ * stops once the transmittance falls below t_stop (0 = never).
+ * Defaults: t_near 0, alpha_min 1/255, alpha_max 0.99, t_stop 1e-4. */
+typedef struct {
+    float t_near;
+    float alpha_min;
+    float alpha_max;
+    float t_stop;
+} sop_bake_params;
+
+/* Query/shade parameters. K nearest probes (1..32), S light directions
+ * (1..4096), mode (sop_mode), specular = the Disney "specular" level giving
+ * F0 = 0.08 specular (1-m) + a m (0.5 gives F0 = 0.04), eps_snap = distance
+ * below which a shading point counts as sitting on its nearest probe (the
+ * blend is then one-hot on that probe; default 1e-6). */
+typedef struct {
+    int32_t K;
+    int32_t S;
+    int32_t mode;
+    float specular;
+    float eps_snap;
+} sop_shade_params;
+
+/* Message for the last non-OK status returned to the calling thread
+ * (thread-local, valid until the next call on that thread). */
+const char* sop_last_error(void);
+
+/* Library version string. */
+const char* sop_version(void);
+
+/* Bytes of the rgbo and depth planes of an atlas (either pointer may be
+ * NULL). Returns SOP_ERR_INVALID_ARG for P < 1, R < 2 or an unknown dtype. */
+sop_status sop_atlas_bytes(int32_t P, int32_t R, int32_t rgbo_dtype, int32_t depth_dtype,
+                           size_t* rgbo_bytes, size_t* depth_bytes);
+
+/* Pack compact probe maps into an atlas (conversion to the atlas dtypes and
+ * the border rule described at sop_atlas). maps_rgb [P,R,R,3], maps_occ
+ * [P,R,R], maps_depth [P,R,R] or NULL (depth plane then left untouched);
+ * rows index v, columns index u. Asynchronous. */
+sop_status sop_atlas_pack(const float* maps_rgb, const float* maps_occ, const float* maps_depth,
+                          const sop_atlas* atlas, void* stream);
+
+/* The canonical S light directions in the local frame (z along the normal),
+ * written to out_dirs [S,3] (device): a Hammersley set with centred first
+ * coordinate, z_i = (i + 1/2)/S, phi_i = 2 pi radical_inverse_base2(i),
+ * uniform on the hemisphere (Sec. 3.1.2, Eq. 3 low-discrepancy rays).
+ * Asynchronous. */
+sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream);
+
+/* Workspace bytes for sop_bake on n Gaussians and P probes of side R. */
+size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R);
+
+/* Bake every texel of every probe of `atlas` (positions atlas->probe_pos)
+ * against the Gaussians `g` and write the atlas (interior and border) in its
+ * dtypes. Texel (i, j) looks along the octahedral decode of its centre
+ * ((i + 1/2)/R, (j + 1/2)/R). Hits are composited in increasing (t*, Gaussian
+ * index) order: T <- T (1 - alpha), L += T_before alpha rgb, D accumulates
+ * T_before alpha t*. Outputs O = 1 - T, L_in = L, D = sum(T alpha t*) /
+ * sum(T alpha) (0 when nothing is hit).
+ * Implementation: Gaussians are binned by their alpha_min bounding spheres
+ * into a uniform grid that each texel ray walks front to back.
+ * SYNCHRONISES `stream` once, after binning, to size the cell lists: it
+ * returns SOP_ERR_WORKSPACE (message gives the bytes needed) when ws_bytes is
+ * too small for this scene. Not capturable in a CUDA graph. */
+sop_status sop_bake(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* Workspace bytes for sop_query_shade / sop_query_shade_backward. */
+size_t sop_query_workspace_bytes(int32_t P, int64_t M, const sop_shade_params* params, int32_t He, int32_t We);
+
+/* Probe query and shading of M points (Sec. 3.1.2 Eq. 2-6; Sec. 3.2.2 Eq. 7-9).
+ * Inputs [M,3]: x (position), n (normal, normalised inside), wo (unit view
+ * direction, towards the viewer); [M,3] albedo, [M] rough (> 0), [M] metal.
+ * env [He,We,3]: equirectangular environment, z-up, row r at polar angle
+ * (r+1/2)/He pi, column c at azimuth (c+1/2)/We 2pi - pi; bilinear, u wraps,
+ * v clamps. dirs_local [S,3] or NULL (= sop_hammersley(S)).
+ * Per point: the K nearest probes by the exact integer squared distance of
+ * positions rounded to multiples of 2^-20 (|coordinates| < 1024), ties to the
+ * lower probe index; weights w_s = 1/|d_k|, w_b = 0.5 (1 + d_k/|d_k| . n)
+ * + 0.01, W_k = w_s w_b / sum (one-hot on the nearest probe when it is within
+ * eps_snap). For every local direction l: w_i = l.x t + l.y b + l.z n with
+ * the frame (t, b) of Duff et al. 2017; O and L_in are the W-blend of the K
+ * probes' bilinear octahedral fetches at w_i; L_dir the environment.
+ *   SHADE : out = 2pi/S sum_i f(wo, w_i) ((1 - O) L_dir + L_in) (n . w_i), with
+ *           f the simplified Disney BRDF: (1-m) a/pi + D F G/(4 (n.w_i)
+ *           max(n.wo, 1e-4)), GGX D with alpha = rough^2, Schlick-GGX G with
+ *           k = (rough+1)^2/8, Schlick F from F0.
+ *   SHADOW: out_c = sum L_dir,c (1 - O)(n . w_i) / sum L_dir,c (n . w_i)
+ *           (1 where the denominator is < 1e-20).
+ * out [M,3] float32. out_idx [M,K] int32 and out_w [M,K] float32 are
+ * optional (NULL to skip): the neighbour indices in increasing distance and
+ * their weights. Asynchronous. */
+sop_status sop_query_shade(const float* x, const float* n, const float* wo, const float* albedo, const float* rough,
+                           const float* metal, int64_t M, const sop_atlas* atlas, const float* env, int32_t He,
+                           int32_t We, const float* dirs_local, const sop_shade_params* params, float* out,
+                           int32_t* out_idx, float* out_w, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOP_H */

@@ -211,3 +211,26 @@ def query_shade(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, e
                           _p(env), C.c_int32(S), None if dp is None else _p(dp), C.c_int32(K),
                           C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), _p(out), _p(idx), _p(W))
     return out, idx, W
+
+
+# angular error bound of one light direction in the FP32 path (rad): the
+# rounding of the frame, the rotation into world space and of atan2
+FP32_DIR_EPS = 2e-6
+
+
+def query_shade_sensitivity(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S,
+                            mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, eps=FP32_DIR_EPS):
+    """Per-output allowance [M,3] for an FP32 evaluation (see the C docs)."""
+    x, n, wo, albedo, rough, metal = (_f32(v) for v in (x, n, wo, albedo, rough, metal))
+    pp, mr, mo, env = _f32(probe_pos), _f32(maps_rgb), _f32(maps_occ), _f32(env)
+    P, R = mr.shape[0], mr.shape[1]
+    He, We, _ = env.shape
+    M = len(x)
+    kap = np.empty((M, 3))
+    dp = None if dirs is None else _f64(dirs)
+    sk = snap_key_for() if snap_key is None else snap_key
+    lib().orc_query_shade_sensitivity(
+        C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal), C.c_int32(P), _p(pp), C.c_int32(R),
+        _p(mr), _p(mo), C.c_int32(He), C.c_int32(We), _p(env), C.c_int32(S), None if dp is None else _p(dp),
+        C.c_int32(K), C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_double(eps), _p(kap))
+    return kap

@@ -439,6 +439,71 @@ void orc_brdf(const double* n, const double* wo, const double* wi, const double*
 /* ------------------------------------------------------------------------ */
 enum { ORC_MODE_SHADE = 0, ORC_MODE_SHADOW = 1 };
 
+/* One light direction's terms at a shading point (unit normal nn, view vo,
+ * material a/rough/metal, K neighbours with weights W): O and L_in blended
+ * from the probes' octahedral maps at w (Eq. 4), L_dir from the environment,
+ * then
+ *   shade : g[0..2] = f(wo, w) ((1 - O) L_dir + L_in) (n . w)     (Eq. 3, 4)
+ *   shadow: g[0..2] = L_dir (1 - O) (n . w), g[3..5] = L_dir (n . w) (Eq. 7-8) */
+static void sample_terms(const double* nn, const double* vo, const double* a, double rough, double metal, double spec,
+                         int mode, const double* w, int32_t K, const int32_t* idx, const double* W, int32_t R,
+                         const double* mrgb, const double* mocc, const float* env, int32_t He, int32_t We, double* g)
+{
+    size_t RR = (size_t)R * R;
+    double uv[2];
+    orc_oct_encode(w, uv);
+    double O = 0.0, Lin[3] = {0, 0, 0};
+    for (int k = 0; k < K; ++k) {
+        double o1, l3[3];
+        orc_oct_bilerp(mocc + RR * idx[k], R, 1, uv, &o1);
+        orc_oct_bilerp(mrgb + 3 * RR * idx[k], R, 3, uv, l3);
+        O += W[k] * o1;
+        for (int c = 0; c < 3; ++c) Lin[c] += W[k] * l3[c];
+    }
+    double Ld[3];
+    orc_env_lookup(env, He, We, w, Ld);
+    double NdotL = nn[0] * w[0] + nn[1] * w[1] + nn[2] * w[2];
+    if (mode == ORC_MODE_SHADE) {
+        double f[3];
+        orc_brdf(nn, vo, w, a, rough, metal, spec, f);
+        for (int c = 0; c < 3; ++c) g[c] = f[c] * ((1.0 - O) * Ld[c] + Lin[c]) * NdotL;
+    } else {
+        for (int c = 0; c < 3; ++c) {
+            g[c] = Ld[c] * (1.0 - O) * NdotL;
+            g[3 + c] = Ld[c] * NdotL;
+        }
+    }
+}
+
+static void query_setup(int64_t M, const float* x, const float* n, int32_t P, const float* probe_pos, int32_t R,
+                        const float* maps_rgb, const float* maps_occ, int32_t S, const double* dirs, int32_t K,
+                        uint64_t snap_key, int32_t* out_idx, double* out_w, double** dl, double** mrgb, double** mocc)
+{
+    *dl = (double*)malloc(sizeof(double) * 3 * (size_t)S);
+    if (dirs) memcpy(*dl, dirs, sizeof(double) * 3 * (size_t)S);
+    else orc_hammersley(S, *dl);
+    size_t RR = (size_t)R * R;
+    *mrgb = (double*)malloc(sizeof(double) * 3 * RR * (size_t)P);
+    *mocc = (double*)malloc(sizeof(double) * RR * (size_t)P);
+    for (size_t i = 0; i < 3 * RR * (size_t)P; ++i) (*mrgb)[i] = maps_rgb[i];
+    for (size_t i = 0; i < RR * (size_t)P; ++i) (*mocc)[i] = maps_occ[i];
+    uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(M > 0 ? M : 1) * K);
+    orc_knn(M, x, P, probe_pos, K, out_idx, key);
+    orc_weights(M, x, n, probe_pos, K, out_idx, key, snap_key, out_w);
+    free(key);
+}
+
+static void point_frame(const float* n, const float* wo, const float* albedo, int64_t m, double* nn, double* vo,
+                        double* a, double* t, double* b)
+{
+    nn[0] = n[3 * m]; nn[1] = n[3 * m + 1]; nn[2] = n[3 * m + 2];
+    double nl = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+    nn[0] /= nl; nn[1] /= nl; nn[2] /= nl;
+    vo[0] = wo[3 * m]; vo[1] = wo[3 * m + 1]; vo[2] = wo[3 * m + 2];
+    a[0] = albedo[3 * m]; a[1] = albedo[3 * m + 1]; a[2] = albedo[3 * m + 2];
+    orc_onb(nn, t, b);
+}
+
 /* For each shading point: K nearest probes, weights, then the Monte Carlo sum
  * over the S directions of
  *   shade : C = 2pi/S sum f ((1 - O) L_dir + L_in) (n . w_i)      (Eq. 3, 4)
@@ -452,66 +517,98 @@ void orc_query_shade(int64_t M, const float* x, const float* n, const float* wo,
                      int32_t S, const double* dirs, int32_t K, int32_t mode, double spec, uint64_t snap_key,
                      double* out, int32_t* out_idx, double* out_w)
 {
-    double* dl = (double*)malloc(sizeof(double) * 3 * (size_t)S);
-    if (dirs) memcpy(dl, dirs, sizeof(double) * 3 * (size_t)S);
-    else orc_hammersley(S, dl);
-    size_t RR = (size_t)R * R;
-    double* mrgb = (double*)malloc(sizeof(double) * 3 * RR * (size_t)P);
-    double* mocc = (double*)malloc(sizeof(double) * RR * (size_t)P);
-    for (size_t i = 0; i < 3 * RR * (size_t)P; ++i) mrgb[i] = maps_rgb[i];
-    for (size_t i = 0; i < RR * (size_t)P; ++i) mocc[i] = maps_occ[i];
-    uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)M * K);
-    orc_knn(M, x, P, probe_pos, K, out_idx, key);
-    orc_weights(M, x, n, probe_pos, K, out_idx, key, snap_key, out_w);
+    double *dl, *mrgb, *mocc;
+    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, K, snap_key, out_idx, out_w, &dl, &mrgb,
+                &mocc);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t m = 0; m < M; ++m) {
-        double nn[3] = {n[3 * m], n[3 * m + 1], n[3 * m + 2]};
-        double nl = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-        nn[0] /= nl; nn[1] /= nl; nn[2] /= nl;
-        double vo[3] = {wo[3 * m], wo[3 * m + 1], wo[3 * m + 2]};
-        double a[3] = {albedo[3 * m], albedo[3 * m + 1], albedo[3 * m + 2]};
-        double t[3], b[3];
-        orc_onb(nn, t, b);
-        double acc[3] = {0, 0, 0}, den[3] = {0, 0, 0};
+        double nn[3], vo[3], a[3], t[3], b[3];
+        point_frame(n, wo, albedo, m, nn, vo, a, t, b);
+        double acc[6] = {0, 0, 0, 0, 0, 0};
         for (int32_t i = 0; i < S; ++i) {
             const double* l = dl + 3 * i;
-            double w[3];
+            double w[3], g[6];
             for (int c = 0; c < 3; ++c) w[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
-            double uv[2];
-            orc_oct_encode(w, uv);
-            double O = 0.0, Lin[3] = {0, 0, 0};
-            for (int k = 0; k < K; ++k) {
-                int32_t p = out_idx[(size_t)m * K + k];
-                double Wk = out_w[(size_t)m * K + k];
-                double o1, l3[3];
-                orc_oct_bilerp(mocc + RR * p, R, 1, uv, &o1);
-                orc_oct_bilerp(mrgb + 3 * RR * p, R, 3, uv, l3);
-                O += Wk * o1;
-                for (int c = 0; c < 3; ++c) Lin[c] += Wk * l3[c];
-            }
-            double Ld[3];
-            orc_env_lookup(env, He, We, w, Ld);
-            double NdotL = nn[0] * w[0] + nn[1] * w[1] + nn[2] * w[2];
-            if (mode == ORC_MODE_SHADE) {
-                double f[3];
-                orc_brdf(nn, vo, w, a, rough[m], metal[m], spec, f);
-                for (int c = 0; c < 3; ++c) acc[c] += f[c] * ((1.0 - O) * Ld[c] + Lin[c]) * NdotL;
-            } else {
-                for (int c = 0; c < 3; ++c) {
-                    acc[c] += Ld[c] * (1.0 - O) * NdotL;
-                    den[c] += Ld[c] * NdotL;
-                }
-            }
+            sample_terms(nn, vo, a, rough[m], metal[m], spec, mode, w, K, out_idx + (size_t)m * K,
+                         out_w + (size_t)m * K, R, mrgb, mocc, env, He, We, g);
+            for (int c = 0; c < (mode == ORC_MODE_SHADE ? 3 : 6); ++c) acc[c] += g[c];
         }
         for (int c = 0; c < 3; ++c) {
             if (mode == ORC_MODE_SHADE) out[3 * m + c] = 2.0 * M_PI / S * acc[c];
-            else out[3 * m + c] = (den[c] < 1e-20) ? 1.0 : acc[c] / den[c];
+            else out[3 * m + c] = (acc[3 + c] < 1e-20) ? 1.0 : acc[c] / acc[3 + c];
         }
     }
-    free(key);
     free(mocc);
     free(mrgb);
     free(dl);
+}
+
+/* Test allowance for an FP32 evaluation of orc_query_shade: how far each
+ * output may move when every light direction carries an angular error of
+ * up to eps (the rounding of the frame, of the rotation into world space
+ * and of atan2 in single precision). Each direction's terms are re-evaluated
+ * at four directions rotated by eps about two axes normal to it; the largest
+ * change per term is summed over directions (shadow: propagated through the
+ * ratio). The environment and probe maps are piecewise bilinear, so this is
+ * their local slope times eps; it is what separates a rough HDR environment,
+ * where neighbouring texels differ by 10x, from a smooth one. */
+void orc_query_shade_sensitivity(int64_t M, const float* x, const float* n, const float* wo, const float* albedo,
+                                 const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
+                                 const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We,
+                                 const float* env, int32_t S, const double* dirs, int32_t K, int32_t mode, double spec,
+                                 uint64_t snap_key, double eps, double* kappa)
+{
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1) * K);
+    double* W = (double*)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1) * K);
+    double *dl, *mrgb, *mocc;
+    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, K, snap_key, idx, W, &dl, &mrgb, &mocc);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < M; ++m) {
+        double nn[3], vo[3], a[3], t[3], b[3];
+        point_frame(n, wo, albedo, m, nn, vo, a, t, b);
+        double acc[6] = {0, 0, 0, 0, 0, 0}, dev[6] = {0, 0, 0, 0, 0, 0};
+        for (int32_t i = 0; i < S; ++i) {
+            const double* l = dl + 3 * i;
+            double w[3], g0[6];
+            for (int c = 0; c < 3; ++c) w[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
+            sample_terms(nn, vo, a, rough[m], metal[m], spec, mode, w, K, idx + (size_t)m * K, W + (size_t)m * K, R,
+                         mrgb, mocc, env, He, We, g0);
+            /* two unit axes normal to w */
+            double u1[3] = {w[1] * nn[2] - w[2] * nn[1], w[2] * nn[0] - w[0] * nn[2], w[0] * nn[1] - w[1] * nn[0]};
+            double ul = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+            if (ul < 1e-12) { u1[0] = t[0]; u1[1] = t[1]; u1[2] = t[2]; ul = 1.0; }
+            for (int c = 0; c < 3; ++c) u1[c] /= ul;
+            double u2[3] = {w[1] * u1[2] - w[2] * u1[1], w[2] * u1[0] - w[0] * u1[2], w[0] * u1[1] - w[1] * u1[0]};
+            double mx[6] = {0, 0, 0, 0, 0, 0};
+            for (int j = 0; j < 4; ++j) {
+                const double* u = (j < 2) ? u1 : u2;
+                double sg = (j & 1) ? -eps : eps, wp[3], g1[6];
+                for (int c = 0; c < 3; ++c) wp[c] = w[c] + sg * u[c];
+                double wl = sqrt(wp[0] * wp[0] + wp[1] * wp[1] + wp[2] * wp[2]);
+                for (int c = 0; c < 3; ++c) wp[c] /= wl;
+                sample_terms(nn, vo, a, rough[m], metal[m], spec, mode, wp, K, idx + (size_t)m * K, W + (size_t)m * K,
+                             R, mrgb, mocc, env, He, We, g1);
+                for (int c = 0; c < 6; ++c) {
+                    double d = fabs(g1[c] - g0[c]);
+                    if (d > mx[c]) mx[c] = d;
+                }
+            }
+            for (int c = 0; c < 6; ++c) {
+                acc[c] += g0[c];
+                dev[c] += mx[c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (mode == ORC_MODE_SHADE) kappa[3 * m + c] = 2.0 * M_PI / S * dev[c];
+            else if (acc[3 + c] < 1e-20) kappa[3 * m + c] = 0.0;
+            else kappa[3 * m + c] = (dev[c] + fabs(acc[c] / acc[3 + c]) * dev[3 + c]) / acc[3 + c];
+        }
+    }
+    free(mocc);
+    free(mrgb);
+    free(dl);
+    free(W);
+    free(idx);
 }
 
 int orc_num_threads(void)

@@ -1,0 +1,570 @@
+// SOP bake (Sec. 3.1.2 probe textures initialised by ray tracing; Sec. 3.2.2
+// occlusion caching; compositing of Eq. 1; D/W depth of Sec. 3.1) for sm_103a.
+//
+// Every probe texel shoots one ray from the probe along the octahedral decode
+// of the texel centre. A Gaussian's response along a ray is its maximum,
+// alpha = min(alpha_max, o exp(-m^2/2)); responses with alpha >= alpha_min
+// and t* > t_near are composited in increasing (t*, index) order.
+//
+// Design: the alpha_min cut-off bounds each Gaussian by a sphere of radius
+// rho = s_max sqrt(2 ln(o / alpha_min)) (no point further away can reach
+// alpha_min). The spheres are binned into a uniform grid (count, scan, fill).
+// Each texel ray then walks the grid front to back (3D DDA). In each cell it
+// keeps only hits whose t* lies inside the cell's t-interval, orders them by
+// (t*, index) in a small local buffer (a cell with more hits than the buffer
+// is rescanned past the last composited hit) and composites them. Cells
+// partition the ray, so hits come out globally ordered and each once; the
+// walk ends when the transmittance drops below t_stop. No per-ray hit lists.
+//
+// The hit evaluation avoids FP32 cancellation: the probe-to-centre offset is
+// split exactly into hi + lo parts (two-sum), the closest-approach point is
+// formed with an FMA, and m^2 is taken from the Mahalanobis norm of that
+// small vector, so alpha carries ~1e-7 relative error even for far, thin
+// Gaussians.
+#include "sop_device.cuh"
+#include "sop_internal.h"
+
+namespace sop {
+
+// Gaussian record: 5 float4 = 80 B.
+//   r0 = (mu.xyz, rho)   rho < 0: never reaches alpha_min
+//   r1..r3 = M = diag(1/s) R^T row-major (9) then opacity
+//   r3.zw, r4.x = rgb
+struct GRec {
+    float4 r0, r1, r2, r3, r4;
+};
+
+constexpr float kMarginRel = 1e-4f;
+
+BakeLayout bake_layout(int64_t N, int32_t P, int32_t R, int64_t entries_cap)
+{
+    BakeLayout L{};
+    L.cells_cap = N < 4096 ? 4096 : (N > (1 << 23) ? (1 << 23) : N);
+    L.entries_cap = entries_cap > 0 ? entries_cap : 48 * N + 65536;
+    size_t o = 0;
+    L.hdr = o;        o = align256(o + sizeof(GaussGrid));
+    L.bbox = o;       o = align256(o + 8 * sizeof(int32_t));
+    L.rec = o;        o = align256(o + sizeof(GRec) * (size_t)(N > 0 ? N : 1));
+    L.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)(L.cells_cap + 1));
+    L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
+    L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)R * R);
+    L.maps = o;       o = align256(o + sizeof(float4) * (size_t)P * R * R);
+    L.depth = o;      o = align256(o + sizeof(float) * (size_t)P * R * R);
+    L.entries = o;    o = align256(o + sizeof(int32_t) * (size_t)L.entries_cap);
+    L.ent_sph = o;    o = align256(o + sizeof(float4) * (size_t)L.entries_cap);
+    L.total = o;
+    return L;
+}
+
+// float <-> order-preserving int for atomic min/max of floats
+__device__ __forceinline__ int32_t f2o(float f)
+{
+    int32_t i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float o2f(int32_t i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void bbox_init_kernel(int32_t* bbox)
+{
+    if (threadIdx.x < 3) bbox[threadIdx.x] = f2o(FLT_MAX);
+    else if (threadIdx.x < 6) bbox[threadIdx.x] = f2o(-FLT_MAX);
+}
+
+// Per-Gaussian record + bounding box of the (margin-expanded) spheres.
+__global__ void gauss_prep_kernel(sop_gaussians g, float alpha_min, GRec* __restrict__ rec, int32_t* bbox)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    if (i < g.n) {
+        const float qw = g.quat[4 * i], qx = g.quat[4 * i + 1], qy = g.quat[4 * i + 2], qz = g.quat[4 * i + 3];
+        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        const float w = qw / qn, x = qx / qn, y = qy / qn, z = qz / qn;
+        // rotation matrix (columns = local axes in world space)
+        const float R00 = 1.f - 2.f * (y * y + z * z), R01 = 2.f * (x * y - w * z), R02 = 2.f * (x * z + w * y);
+        const float R10 = 2.f * (x * y + w * z), R11 = 1.f - 2.f * (x * x + z * z), R12 = 2.f * (y * z - w * x);
+        const float R20 = 2.f * (x * z - w * y), R21 = 2.f * (y * z + w * x), R22 = 1.f - 2.f * (x * x + y * y);
+        const float sx = g.scale[3 * i], sy = g.scale[3 * i + 1], sz = g.scale[3 * i + 2];
+        const float ix = 1.f / sx, iy = 1.f / sy, iz = 1.f / sz;
+        const float o = g.opacity[i];
+        const float3 mu = load3(g.mean, i);
+        float rho = -1.f;
+        if (o >= alpha_min && o > 0.f) {
+            const float smax = fmaxf(sx, fmaxf(sy, sz));
+            rho = smax * sqrtf(2.f * fmaxf(logf(o / alpha_min), 0.f));
+            rho = rho * (1.f + kMarginRel) + 1e-7f;
+        }
+        GRec r;
+        r.r0 = make_float4(mu.x, mu.y, mu.z, rho);
+        // M = diag(1/s) R^T : row a = R[:, a] / s_a
+        r.r1 = make_float4(R00 * ix, R10 * ix, R20 * ix, R01 * iy);
+        r.r2 = make_float4(R11 * iy, R21 * iy, R02 * iz, R12 * iz);
+        r.r3 = make_float4(R22 * iz, o, g.rgb[3 * i], g.rgb[3 * i + 1]);
+        r.r4 = make_float4(g.rgb[3 * i + 2], 0.f, 0.f, 0.f);
+        rec[i] = r;
+        if (rho >= 0.f) {
+            lo[0] = mu.x - rho; lo[1] = mu.y - rho; lo[2] = mu.z - rho;
+            hi[0] = mu.x + rho; hi[1] = mu.y + rho; hi[2] = mu.z + rho;
+        }
+    }
+    // warp reduce then one atomic per warp
+    for (int a = 0; a < 3; ++a) {
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; ++a) {
+            if (lo[a] <= hi[a]) {
+                atomicMin(&bbox[a], f2o(lo[a]));
+                atomicMax(&bbox[3 + a], f2o(hi[a]));
+            }
+        }
+    }
+}
+
+// Grid geometry from the bounding box: cubic cells, about cells_cap/2 of
+// them over the box, never more than cells_cap.
+__global__ void grid_setup_kernel(const int32_t* bbox, int64_t cells_cap, GaussGrid* grid, int32_t* cell_cnt)
+{
+    __shared__ GaussGrid G;
+    if (threadIdx.x == 0) {
+        float lo[3], hi[3], ext[3];
+        bool empty = false;
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = o2f(bbox[a]);
+            hi[a] = o2f(bbox[3 + a]);
+            if (!(lo[a] <= hi[a])) empty = true;
+        }
+        if (empty) {
+            for (int a = 0; a < 3; ++a) { lo[a] = 0.f; hi[a] = 0.f; }
+        }
+        float emax = 0.f;
+        for (int a = 0; a < 3; ++a) {
+            // pad the box so boundary rounding never drops a sphere
+            const float pad = 1e-5f * fmaxf(hi[a] - lo[a], 1e-3f) + 1e-6f;
+            lo[a] -= pad;
+            hi[a] += pad;
+            ext[a] = hi[a] - lo[a];
+            emax = fmaxf(emax, ext[a]);
+        }
+        // cell edge: volume / (cells_cap/2), clamped so that no axis needs
+        // more than cbrt-balanced resolution
+        const double vol = (double)ext[0] * ext[1] * ext[2];
+        double h = cbrt(vol / (double)(cells_cap / 2));
+        h = fmax(h, (double)emax / 1024.0);
+        int64_t nc;
+        int d[3];
+        for (;;) {
+            nc = 1;
+            for (int a = 0; a < 3; ++a) {
+                d[a] = (int)ceil(ext[a] / h);
+                d[a] = d[a] < 1 ? 1 : d[a];
+                nc *= d[a];
+            }
+            if (nc <= cells_cap) break;
+            h *= 1.1;
+        }
+        for (int a = 0; a < 3; ++a) {
+            G.origin[a] = lo[a];
+            G.bmax[a] = hi[a];
+            G.dims[a] = d[a];
+        }
+        G.h = (float)h;
+        G.inv_h = (float)(1.0 / h);
+        G.ncells = (int32_t)nc;
+        G.n_entries = 0;
+        *grid = G;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < G.ncells; c += blockDim.x) cell_cnt[c] = 0;
+}
+
+__device__ __forceinline__ void cell_range(const GaussGrid& G, float3 mu, float rho, int lo[3], int hi[3])
+{
+    const float m = rho + kMarginRel * G.h;
+    const float c[3] = {mu.x, mu.y, mu.z};
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = min(max((int)floorf((c[a] - m - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
+        hi[a] = min(max((int)floorf((c[a] + m - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
+    }
+}
+
+__global__ void bin_count_kernel(int64_t N, const GRec* __restrict__ rec, const GaussGrid* __restrict__ gridp,
+                                 int32_t* __restrict__ cell_cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 r0 = rec[i].r0;
+    if (r0.w < 0.f) return;
+    const GaussGrid G = *gridp;
+    int lo[3], hi[3];
+    cell_range(G, f3(r0.x, r0.y, r0.z), r0.w, lo, hi);
+    for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&cell_cnt[(z * G.dims[1] + y) * G.dims[0] + x], 1);
+}
+
+// Exclusive scan of the cell counts in one CTA; total into grid->n_entries.
+__global__ void __launch_bounds__(1024) bin_scan_kernel(GaussGrid* gridp, int32_t* __restrict__ cell_cnt,
+                                                         int32_t* __restrict__ cell_start)
+{
+    __shared__ int64_t s_part[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nc = gridp->ncells;
+    const int chunk = (nc + nt - 1) / nt;
+    const int c0 = tid * chunk, c1 = min(nc, c0 + chunk);
+    int64_t sum = 0;
+    for (int c = c0; c < c1; ++c) sum += cell_cnt[c];
+    s_part[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int64_t v = (tid >= off) ? s_part[tid - off] : 0;
+        __syncthreads();
+        s_part[tid] += v;
+        __syncthreads();
+    }
+    int64_t run = s_part[tid] - sum;
+    for (int c = c0; c < c1; ++c) {
+        const int32_t v = cell_cnt[c];
+        cell_start[c] = (int32_t)(run < INT32_MAX ? run : INT32_MAX);
+        run += v;
+        cell_cnt[c] = 0;
+    }
+    if (tid == nt - 1) {
+        const int64_t tot = s_part[nt - 1];
+        cell_start[nc] = (int32_t)(tot < INT32_MAX ? tot : INT32_MAX);
+        gridp->n_entries = (int32_t)(tot < INT32_MAX ? tot : INT32_MAX);
+    }
+}
+
+__global__ void bin_fill_kernel(int64_t N, const GRec* __restrict__ rec, const GaussGrid* __restrict__ gridp,
+                                const int32_t* __restrict__ cell_start, int32_t* __restrict__ cell_cnt,
+                                int32_t* __restrict__ entries, float4* __restrict__ ent_sph)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 r0 = rec[i].r0;
+    if (r0.w < 0.f) return;
+    const GaussGrid G = *gridp;
+    int lo[3], hi[3];
+    cell_range(G, f3(r0.x, r0.y, r0.z), r0.w, lo, hi);
+    for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+                const int c = (z * G.dims[1] + y) * G.dims[0] + x;
+                const int pos = cell_start[c] + atomicAdd(&cell_cnt[c], 1);
+                entries[pos] = (int32_t)i;
+                ent_sph[pos] = r0;
+            }
+}
+
+// Texel-centre directions, computed in fp64 and rounded once.
+__global__ void texel_dirs_kernel(int R, float4* __restrict__ dirs)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= R * R) return;
+    double d[3];
+    oct_decode_centre_f64(R, t % R, t / R, d);
+    dirs[t] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
+}
+
+// error-free a - b = hi + lo
+__device__ __forceinline__ void two_diff(float a, float b, float& hi, float& lo)
+{
+    hi = a - b;
+    const float bv = a - hi;
+    const float av = hi + bv;
+    lo = (a - av) + (bv - b);
+}
+
+constexpr int kHitBuf = 32;
+
+struct TraceK {
+    const GRec* rec;
+    const GaussGrid* grid;
+    const int32_t* cell_start;
+    const int32_t* entries;
+    const float4* ent_sph;
+    const float4* dirs;
+    const float* probe_pos;
+    int32_t P, R;
+    float t_near, alpha_min, alpha_max, t_stop;
+    float4* maps;   // [P][R][R] (L.rgb, O)
+    float* depth;   // [P][R][R]
+};
+
+// One thread per texel ray.
+__global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
+{
+    const int RR = k.R * k.R;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)k.P * RR) return;
+    const int p = (int)(gid / RR), t = (int)(gid % RR);
+    const GaussGrid G = *k.grid;
+    const float4 d4 = __ldg(k.dirs + t);
+    const float3 d = f3(d4.x, d4.y, d4.z);
+    const float3 o = load3(k.probe_pos, p);
+
+    float T = 1.f, L0 = 0.f, L1 = 0.f, L2 = 0.f, Dacc = 0.f, Wacc = 0.f;
+    bool done = false;
+
+    // slab entry/exit of the grid box
+    const float ov[3] = {o.x, o.y, o.z}, dv[3] = {d.x, d.y, d.z};
+    float t0 = 0.f, t1 = FLT_MAX;
+    for (int a = 0; a < 3; ++a) {
+        if (dv[a] != 0.f) {
+            const float inv = 1.f / dv[a];
+            float ta = (G.origin[a] - ov[a]) * inv, tb = (G.bmax[a] - ov[a]) * inv;
+            if (ta > tb) { const float tmp = ta; ta = tb; tb = tmp; }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        } else if (ov[a] < G.origin[a] || ov[a] > G.bmax[a]) {
+            t1 = -1.f;
+        }
+    }
+    if (G.n_entries > 0 && t0 <= t1) {
+        int cell[3], step[3];
+        float tmax[3];
+        for (int a = 0; a < 3; ++a) {
+            const float pa = ov[a] + t0 * dv[a];
+            cell[a] = min(max((int)floorf((pa - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
+            if (dv[a] > 0.f) {
+                step[a] = 1;
+                tmax[a] = (G.origin[a] + (cell[a] + 1) * G.h - ov[a]) / dv[a];
+            } else if (dv[a] < 0.f) {
+                step[a] = -1;
+                tmax[a] = (G.origin[a] + cell[a] * G.h - ov[a]) / dv[a];
+            } else {
+                step[a] = 0;
+                tmax[a] = FLT_MAX;
+            }
+        }
+        float t_enter = t0;
+        float bt[kHitBuf], ba[kHitBuf];
+        int32_t bg[kHitBuf];
+        while (!done) {
+            int ax = 0;
+            if (tmax[1] < tmax[ax]) ax = 1;
+            if (tmax[2] < tmax[ax]) ax = 2;
+            float t_exit = fminf(tmax[ax], t1);
+            if (t_exit < t_enter) t_exit = t_enter;
+            const int c = (cell[2] * G.dims[1] + cell[1]) * G.dims[0] + cell[0];
+            const int e0 = __ldg(k.cell_start + c), e1 = __ldg(k.cell_start + c + 1);
+            float cur_t = -FLT_MAX;
+            int32_t cur_g = -1;
+            // window loop: composite the cell's hits in (t*, index) order,
+            // kHitBuf at a time
+            for (;;) {
+                int nb = 0;
+                bool overflow = false;
+                for (int e = e0; e < e1; ++e) {
+                    const float4 r0 = __ldg(k.ent_sph + e);
+                    const float3 mu = f3(r0.x, r0.y, r0.z);
+                    const float3 del = mu - o;
+                    const float tc = dot3(del, d);
+                    if (tc + r0.w < t_enter || tc - r0.w > t_exit) continue;
+                    const float3 cx = cross3(del, d);
+                    if (dot3(cx, cx) > r0.w * r0.w) continue;
+                    const int32_t gi = __ldg(k.entries + e);
+                    // exact response
+                    const float4 r1 = __ldg(&k.rec[gi].r1), r2 = __ldg(&k.rec[gi].r2), r3 = __ldg(&k.rec[gi].r3);
+                    float hx, lx, hy, ly, hz, lz;
+                    two_diff(o.x, mu.x, hx, lx);
+                    two_diff(o.y, mu.y, hy, ly);
+                    two_diff(o.z, mu.z, hz, lz);
+                    const float u0 = fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz));
+                    const float u1 = fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz));
+                    const float u2 = fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz));
+                    const float w0 = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
+                    const float w1 = fmaf(r1.w, d.x, fmaf(r2.x, d.y, r2.y * d.z));
+                    const float w2 = fmaf(r2.z, d.x, fmaf(r2.w, d.y, r3.x * d.z));
+                    const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                    const float B = fmaf(w0, u0, fmaf(w1, u1, w2 * u2));
+                    const float ts = -B / A;
+                    if (!(ts > k.t_near) || ts < t_enter || ts >= t_exit) continue;
+                    const float ex = fmaf(ts, d.x, hx) + lx, ey = fmaf(ts, d.y, hy) + ly, ez = fmaf(ts, d.z, hz) + lz;
+                    const float v0 = fmaf(r1.x, ex, fmaf(r1.y, ey, r1.z * ez));
+                    const float v1 = fmaf(r1.w, ex, fmaf(r2.x, ey, r2.y * ez));
+                    const float v2 = fmaf(r2.z, ex, fmaf(r2.w, ey, r3.x * ez));
+                    const float m2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                    const float resp = r3.y * expf(-0.5f * m2);
+                    if (!(resp >= k.alpha_min)) continue;
+                    if (ts < cur_t || (ts == cur_t && gi <= cur_g)) continue;
+                    const float al = fminf(resp, k.alpha_max);
+                    // insertion into the sorted buffer (keep the smallest)
+                    if (nb == kHitBuf) {
+                        overflow = true;
+                        if (ts > bt[kHitBuf - 1] || (ts == bt[kHitBuf - 1] && gi > bg[kHitBuf - 1])) continue;
+                        --nb;
+                    }
+                    int pos = nb++;
+                    while (pos > 0 && (bt[pos - 1] > ts || (bt[pos - 1] == ts && bg[pos - 1] > gi))) {
+                        bt[pos] = bt[pos - 1];
+                        ba[pos] = ba[pos - 1];
+                        bg[pos] = bg[pos - 1];
+                        --pos;
+                    }
+                    bt[pos] = ts;
+                    ba[pos] = al;
+                    bg[pos] = gi;
+                }
+                for (int h = 0; h < nb; ++h) {
+                    const float wgt = T * ba[h];
+                    const float4 r3 = __ldg(&k.rec[bg[h]].r3), r4 = __ldg(&k.rec[bg[h]].r4);
+                    L0 = fmaf(wgt, r3.z, L0);
+                    L1 = fmaf(wgt, r3.w, L1);
+                    L2 = fmaf(wgt, r4.x, L2);
+                    Dacc = fmaf(wgt, bt[h], Dacc);
+                    Wacc += wgt;
+                    T *= (1.f - ba[h]);
+                    if (T < k.t_stop) {
+                        done = true;
+                        break;
+                    }
+                }
+                if (done || !overflow) break;
+                cur_t = bt[nb - 1];
+                cur_g = bg[nb - 1];
+            }
+            if (done || t_exit >= t1) break;
+            cell[ax] += step[ax];
+            if (cell[ax] < 0 || cell[ax] >= G.dims[ax]) break;
+            // boundary recomputed from the cell index (no accumulated error)
+            tmax[ax] = (G.origin[ax] + (cell[ax] + (step[ax] > 0 ? 1 : 0)) * G.h - ov[ax]) / dv[ax];
+            t_enter = t_exit;
+        }
+    }
+    k.maps[gid] = make_float4(L0, L1, L2, 1.f - T);
+    k.depth[gid] = Wacc > 1e-8f ? Dacc / Wacc : 0.f;
+}
+
+cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s)
+{
+    GaussGrid* grid = reinterpret_cast<GaussGrid*>(ws + L.hdr);
+    int32_t* bbox = reinterpret_cast<int32_t*>(ws + L.bbox);
+    GRec* rec = reinterpret_cast<GRec*>(ws + L.rec);
+    int32_t* cstart = reinterpret_cast<int32_t*>(ws + L.cell_start);
+    int32_t* ccnt = reinterpret_cast<int32_t*>(ws + L.cell_cnt);
+    bbox_init_kernel<<<1, 32, 0, s>>>(bbox);
+    const int bs = 256;
+    const unsigned nb = (unsigned)((g.n + bs - 1) / bs);
+    if (g.n > 0) gauss_prep_kernel<<<nb, bs, 0, s>>>(g, alpha_min, rec, bbox);
+    grid_setup_kernel<<<1, 1024, 0, s>>>(bbox, L.cells_cap, grid, ccnt);
+    if (g.n > 0) bin_count_kernel<<<nb, bs, 0, s>>>(g.n, rec, grid, ccnt);
+    bin_scan_kernel<<<1, 1024, 0, s>>>(grid, ccnt, cstart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bake_trace(const sop_gaussians& g, const sop_atlas& atlas, const sop_bake_params& bp,
+                              const BakeLayout& L, char* ws, cudaStream_t s)
+{
+    GaussGrid* grid = reinterpret_cast<GaussGrid*>(ws + L.hdr);
+    GRec* rec = reinterpret_cast<GRec*>(ws + L.rec);
+    int32_t* cstart = reinterpret_cast<int32_t*>(ws + L.cell_start);
+    int32_t* ccnt = reinterpret_cast<int32_t*>(ws + L.cell_cnt);
+    int32_t* ent = reinterpret_cast<int32_t*>(ws + L.entries);
+    float4* sph = reinterpret_cast<float4*>(ws + L.ent_sph);
+    const int bs = 256;
+    if (g.n > 0)
+        bin_fill_kernel<<<(unsigned)((g.n + bs - 1) / bs), bs, 0, s>>>(g.n, rec, grid, cstart, ccnt, ent, sph);
+    const int R = atlas.R;
+    float4* dirs = reinterpret_cast<float4*>(ws + L.dirs);
+    texel_dirs_kernel<<<(R * R + 127) / 128, 128, 0, s>>>(R, dirs);
+    TraceK k;
+    k.rec = rec;
+    k.grid = grid;
+    k.cell_start = cstart;
+    k.entries = ent;
+    k.ent_sph = sph;
+    k.dirs = dirs;
+    k.probe_pos = atlas.probe_pos;
+    k.P = atlas.P;
+    k.R = R;
+    k.t_near = bp.t_near;
+    k.alpha_min = bp.alpha_min;
+    k.alpha_max = bp.alpha_max;
+    k.t_stop = bp.t_stop;
+    k.maps = reinterpret_cast<float4*>(ws + L.maps);
+    k.depth = reinterpret_cast<float*>(ws + L.depth);
+    const int64_t rays = (int64_t)atlas.P * R * R;
+    trace_kernel<<<(unsigned)((rays + bs - 1) / bs), bs, 0, s>>>(k);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_atlas_pack(reinterpret_cast<const float*>(k.maps), 4, reinterpret_cast<const float*>(k.maps) + 3, 4,
+                             k.depth, atlas, s);
+}
+
+// ---------------------------------------------------------------------------
+// Atlas pack: compact maps -> gutter atlas in the storage dtypes.
+// ---------------------------------------------------------------------------
+template <int DT>
+__global__ void atlas_pack_kernel(const float* __restrict__ rgb, int rgb_stride, const float* __restrict__ occ,
+                                  int occ_stride, int32_t P, int32_t R, typename Texel<DT>::raw* __restrict__ out)
+{
+    const int RS = R + 2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)P * RS * RS) return;
+    const int p = (int)(i / (RS * RS)), r = (int)(i % (RS * RS));
+    int si, sj;
+    oct_wrap(R, r % RS - 1, r / RS - 1, si, sj);
+    const int64_t src = (int64_t)p * R * R + (int64_t)sj * R + si;
+    const float4 v = make_float4(rgb[src * rgb_stride], rgb[src * rgb_stride + 1], rgb[src * rgb_stride + 2],
+                                 occ[src * occ_stride]);
+    out[i] = Texel<DT>::pack(v);
+}
+
+template <int DT>
+__global__ void depth_pack_kernel(const float* __restrict__ depth, int32_t P, int32_t R, float inv_scale,
+                                  void* __restrict__ out)
+{
+    const int RS = R + 2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)P * RS * RS) return;
+    const int p = (int)(i / (RS * RS)), r = (int)(i % (RS * RS));
+    int si, sj;
+    oct_wrap(R, r % RS - 1, r / RS - 1, si, sj);
+    const float v = depth[(int64_t)p * R * R + (int64_t)sj * R + si] * inv_scale;
+    if (DT == SOP_F32) reinterpret_cast<float*>(out)[i] = v;
+    else if (DT == SOP_F16) reinterpret_cast<__half*>(out)[i] = __float2half_rn(v);
+    else if (DT == SOP_BF16) reinterpret_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(v);
+    else reinterpret_cast<__nv_fp8_e4m3*>(out)[i] = __nv_fp8_e4m3(v);
+}
+
+cudaError_t launch_atlas_pack(const float* rgb, int rgb_stride, const float* occ, int occ_stride, const float* depth,
+                              const sop_atlas& atlas, cudaStream_t s)
+{
+    const int RS = atlas.R + 2;
+    const int64_t n = (int64_t)atlas.P * RS * RS;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    switch (atlas.rgbo_dtype) {
+    case SOP_F32:
+        atlas_pack_kernel<SOP_F32><<<nb, 256, 0, s>>>(rgb, rgb_stride, occ, occ_stride, atlas.P, atlas.R,
+                                                     reinterpret_cast<float4*>(atlas.rgbo));
+        break;
+    case SOP_BF16:
+        atlas_pack_kernel<SOP_BF16><<<nb, 256, 0, s>>>(rgb, rgb_stride, occ, occ_stride, atlas.P, atlas.R,
+                                                      reinterpret_cast<uint2*>(atlas.rgbo));
+        break;
+    case SOP_F16:
+        atlas_pack_kernel<SOP_F16><<<nb, 256, 0, s>>>(rgb, rgb_stride, occ, occ_stride, atlas.P, atlas.R,
+                                                     reinterpret_cast<uint2*>(atlas.rgbo));
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (depth && atlas.depth) {
+        const float inv = 1.f / atlas.depth_scale;
+        switch (atlas.depth_dtype) {
+        case SOP_F32: depth_pack_kernel<SOP_F32><<<nb, 256, 0, s>>>(depth, atlas.P, atlas.R, inv, atlas.depth); break;
+        case SOP_F16: depth_pack_kernel<SOP_F16><<<nb, 256, 0, s>>>(depth, atlas.P, atlas.R, inv, atlas.depth); break;
+        case SOP_BF16: depth_pack_kernel<SOP_BF16><<<nb, 256, 0, s>>>(depth, atlas.P, atlas.R, inv, atlas.depth); break;
+        case SOP_FP8E4M3:
+            depth_pack_kernel<SOP_FP8E4M3><<<nb, 256, 0, s>>>(depth, atlas.P, atlas.R, inv, atlas.depth);
+            break;
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sop

@@ -1,0 +1,558 @@
+// SOP query + shade (Sec. 3.1.2 Eq. 2-6, Sec. 3.2.2 Eq. 7-9) for sm_103a.
+//
+// Kernels, in launch order:
+//   probe_grid_kernel   one CTA: quantise probe positions to 2^-20, counting
+//                       sort into a uniform grid of ~P cells;
+//   knn_kernel          one thread per point: exact K nearest probes by
+//                       integer squared distance (ring search with an exact
+//                       integer stopping bound), then the Eq. 4-6 weights;
+//   env_pack_kernel     environment to float4 with a wrapped column and
+//                       clamped rows so the bilinear fetch needs no branches;
+//   dirs_kernel         local light directions (Hammersley in fp64 -> fp32);
+//   shade_kernel        LANES threads per point split the S directions; per
+//                       direction one octahedral encode (world-frame maps),
+//                       4 texel fetches per probe from the L2-resident atlas,
+//                       environment bilinear, BRDF, fp32 accumulation, and a
+//                       shuffle reduction over the point's lanes.
+#include <float.h>
+
+#include "sop_device.cuh"
+#include "sop_internal.h"
+
+namespace sop {
+
+QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He, int32_t We)
+{
+    QueryLayout L{};
+    int g = 1;
+    while ((int64_t)g * g * g < P) ++g;
+    L.g_axis = g;
+    L.cells_cap = (g + 1) * (g + 1) * (g + 1);
+    size_t o = 0;
+    L.grid_hdr = o;   o = align256(o + sizeof(ProbeGrid));
+    L.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)(L.cells_cap + 1));
+    L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
+    L.entries = o;    o = align256(o + sizeof(int4) * (size_t)P);
+    L.env4 = o;       o = align256(o + sizeof(float4) * (size_t)(He + 2) * (We + 1));
+    L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)S);
+    L.idx = o;        o = align256(o + sizeof(int32_t) * (size_t)M * K);
+    L.w = o;          o = align256(o + sizeof(float) * (size_t)M * K);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ int32_t quantise(float v) { return __float2int_rn(v * 1048576.0f); }
+
+// ---------------------------------------------------------------------------
+// Probe grid (single CTA; P is small: thousands to ~1e5 probes).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) probe_grid_kernel(const float* __restrict__ probe_pos, int32_t P, int32_t g_axis,
+                                                           ProbeGrid* grid, int32_t* cell_start, int32_t* cell_cnt,
+                                                           int4* entries)
+{
+    __shared__ int32_t s_min[3], s_max[3];
+    __shared__ int32_t s_part[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid < 3) {
+        s_min[tid] = INT32_MAX;
+        s_max[tid] = INT32_MIN;
+    }
+    __syncthreads();
+    int32_t lmin[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, lmax[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (int p = tid; p < P; p += nt)
+        for (int a = 0; a < 3; ++a) {
+            int32_t q = quantise(probe_pos[3 * p + a]);
+            lmin[a] = min(lmin[a], q);
+            lmax[a] = max(lmax[a], q);
+        }
+    for (int a = 0; a < 3; ++a) {
+        atomicMin(&s_min[a], lmin[a]);
+        atomicMax(&s_max[a], lmax[a]);
+    }
+    __syncthreads();
+    __shared__ ProbeGrid G;
+    if (tid == 0) {
+        int64_t ext[3], emax = 0;
+        for (int a = 0; a < 3; ++a) {
+            ext[a] = (int64_t)s_max[a] - s_min[a];
+            emax = ext[a] > emax ? ext[a] : emax;
+        }
+        int64_t cs = emax / g_axis + 1;
+        G.cs = (int32_t)cs;
+        int32_t nc = 1;
+        for (int a = 0; a < 3; ++a) {
+            G.qmin[a] = s_min[a];
+            G.dims[a] = (int32_t)(ext[a] / cs) + 1;
+            nc *= G.dims[a];
+        }
+        G.ncells = nc;
+        *grid = G;
+    }
+    __syncthreads();
+    const int nc = G.ncells;
+    for (int c = tid; c < nc; c += nt) cell_cnt[c] = 0;
+    __syncthreads();
+    for (int p = tid; p < P; p += nt) {
+        int c[3];
+        for (int a = 0; a < 3; ++a) c[a] = (int)(((int64_t)quantise(probe_pos[3 * p + a]) - G.qmin[a]) / G.cs);
+        atomicAdd(&cell_cnt[(c[2] * G.dims[1] + c[1]) * G.dims[0] + c[0]], 1);
+    }
+    __syncthreads();
+    // exclusive scan of cell counts: contiguous chunk per thread + block scan
+    const int chunk = (nc + nt - 1) / nt;
+    const int c0 = tid * chunk, c1 = min(nc, c0 + chunk);
+    int32_t sum = 0;
+    for (int c = c0; c < c1; ++c) sum += cell_cnt[c];
+    s_part[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int32_t v = (tid >= off) ? s_part[tid - off] : 0;
+        __syncthreads();
+        s_part[tid] += v;
+        __syncthreads();
+    }
+    int32_t run = s_part[tid] - sum;
+    for (int c = c0; c < c1; ++c) {
+        int32_t v = cell_cnt[c];
+        cell_start[c] = run;
+        run += v;
+        cell_cnt[c] = 0;
+    }
+    if (tid == nt - 1) cell_start[nc] = s_part[nt - 1];
+    __syncthreads();
+    for (int p = tid; p < P; p += nt) {
+        int32_t q[3];
+        int c[3];
+        for (int a = 0; a < 3; ++a) {
+            q[a] = quantise(probe_pos[3 * p + a]);
+            c[a] = (int)(((int64_t)q[a] - G.qmin[a]) / G.cs);
+        }
+        int cell = (c[2] * G.dims[1] + c[1]) * G.dims[0] + c[0];
+        int pos = cell_start[cell] + atomicAdd(&cell_cnt[cell], 1);
+        entries[pos] = make_int4(q[0], q[1], q[2], p);
+    }
+}
+
+// floor division for possibly negative numerators (positive divisor)
+__device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Exact K nearest probes + blend weights. One thread per point.
+// ---------------------------------------------------------------------------
+template <int KMAX>
+__global__ void __launch_bounds__(128) knn_kernel(const float* __restrict__ x, const float* __restrict__ nrm, int64_t M,
+                                                   int32_t K, uint64_t snap_key, const ProbeGrid* __restrict__ gridp,
+                                                   const int32_t* __restrict__ cell_start,
+                                                   const int4* __restrict__ entries,
+                                                   const float* __restrict__ probe_pos, int32_t* __restrict__ ws_idx,
+                                                   float* __restrict__ ws_w, int32_t* __restrict__ user_idx,
+                                                   float* __restrict__ user_w)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const ProbeGrid G = *gridp;
+    const float3 xp = load3(x, m);
+    const int32_t q[3] = {quantise(xp.x), quantise(xp.y), quantise(xp.z)};
+    int64_t c[3], off_min = INT64_MAX;
+    for (int a = 0; a < 3; ++a) {
+        int64_t rel = (int64_t)q[a] - G.qmin[a];
+        c[a] = floordiv(rel, G.cs);
+        int64_t off = rel - c[a] * G.cs;  // in [0, cs)
+        int64_t m2 = off < G.cs - off ? off : G.cs - off;
+        off_min = m2 < off_min ? m2 : off_min;
+    }
+    uint64_t bk[KMAX];
+    int32_t bi[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        bk[k] = UINT64_MAX;
+        bi[k] = INT32_MAX;
+    }
+    int64_t r0 = 0;
+    for (int a = 0; a < 3; ++a) {
+        int64_t d = c[a] < 0 ? -c[a] : (c[a] >= G.dims[a] ? c[a] - (G.dims[a] - 1) : 0);
+        r0 = d > r0 ? d : r0;
+    }
+    for (int64_t r = r0;; ++r) {
+        const int64_t zlo = max(c[2] - r, (int64_t)0), zhi = min(c[2] + r, (int64_t)G.dims[2] - 1);
+        const int64_t ylo = max(c[1] - r, (int64_t)0), yhi = min(c[1] + r, (int64_t)G.dims[1] - 1);
+        for (int64_t z = zlo; z <= zhi; ++z)
+            for (int64_t y = ylo; y <= yhi; ++y) {
+                const bool face = (z == c[2] - r) || (z == c[2] + r) || (y == c[1] - r) || (y == c[1] + r);
+                const int64_t xs = face ? 1 : 2 * r;  // on a face row: every x; else only the two ends
+                for (int64_t xx = c[0] - r; xx <= c[0] + r; xx += (xs > 0 ? xs : 1)) {
+                    if (xx < 0 || xx >= G.dims[0]) continue;
+                    const int cell = (int)((z * G.dims[1] + y) * G.dims[0] + xx);
+                    const int e1 = __ldg(cell_start + cell + 1);
+                    for (int e = __ldg(cell_start + cell); e < e1; ++e) {
+                        const int4 en = __ldg(entries + e);
+                        const int64_t dx = (int64_t)en.x - q[0], dy = (int64_t)en.y - q[1], dz = (int64_t)en.z - q[2];
+                        const uint64_t key = (uint64_t)(dx * dx) + (uint64_t)(dy * dy) + (uint64_t)(dz * dz);
+                        const int32_t id = en.w;
+                        // keep the KMAX best (key, id) pairs sorted; the first K
+                        // of them are the K nearest
+                        const bool better = key < bk[KMAX - 1] || (key == bk[KMAX - 1] && id < bi[KMAX - 1]);
+                        if (!better) continue;
+                        uint64_t ck = key;
+                        int32_t ci = id;
+#pragma unroll
+                        for (int k = 0; k < KMAX; ++k) {
+                            const bool sw = (ck < bk[k]) || (ck == bk[k] && ci < bi[k]);
+                            const uint64_t tk = bk[k];
+                            const int32_t ti = bi[k];
+                            bk[k] = sw ? ck : bk[k];
+                            bi[k] = sw ? ci : bi[k];
+                            ck = sw ? tk : ck;
+                            ci = sw ? ti : ci;
+                        }
+                    }
+                }
+            }
+        // stop once no probe outside ring r can enter the best K
+        uint64_t kth = bk[0];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k == K - 1) kth = bk[k];
+        const int64_t bound = r * (int64_t)G.cs + off_min;
+        const bool full_grid = (c[0] - r <= 0) && (c[0] + r >= G.dims[0] - 1) && (c[1] - r <= 0) &&
+                               (c[1] + r >= G.dims[1] - 1) && (c[2] - r <= 0) && (c[2] + r >= G.dims[2] - 1);
+        if (full_grid) break;
+        if (kth != UINT64_MAX && kth < (uint64_t)bound * (uint64_t)bound) break;
+    }
+    // weights (Eq. 4-6)
+    const float3 nr = load3(nrm, m);
+    const float nl = sqrtf(dot3(nr, nr));
+    const float3 nn = f3(nr.x / nl, nr.y / nl, nr.z / nl);
+    float w[KMAX];
+    float wsum = 0.f;
+    const bool snap = bk[0] <= snap_key;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        w[k] = 0.f;
+        if (k < K) {
+            const float3 pk = load3(probe_pos, bi[k]);
+            const float3 d = pk - xp;
+            const float dl = sqrtf(dot3(d, d));
+            const float ws = 1.f / dl;
+            const float wb = 0.5f * (1.f + dot3(d, nn) / dl) + 0.01f;
+            w[k] = snap ? (k == 0 ? 1.f : 0.f) : ws * wb;
+            wsum += w[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+        if (k < K) {
+            const float wk = snap ? w[k] : w[k] / wsum;
+            ws_idx[m * K + k] = bi[k];
+            ws_w[m * K + k] = wk;
+            if (user_idx) user_idx[m * K + k] = bi[k];
+            if (user_w) user_w[m * K + k] = wk;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Environment table: float4 [(He+2)][(We+1)], stored row r+1 = row r (rows 0
+// and He+1 repeat the first and last row: v clamps), stored column We =
+// column 0 (u wraps).
+// ---------------------------------------------------------------------------
+__global__ void env_pack_kernel(const float* __restrict__ env, int32_t He, int32_t We, float4* __restrict__ env4)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)(He + 2) * (We + 1);
+    if (i >= n) return;
+    const int rs = (int)(i / (We + 1)), cs = (int)(i % (We + 1));
+    const int r = min(max(rs - 1, 0), He - 1), c = cs == We ? 0 : cs;
+    const float* e = env + ((int64_t)r * We + c) * 3;
+    env4[i] = make_float4(e[0], e[1], e[2], 0.f);
+}
+
+__device__ __forceinline__ double radical_inverse2(uint32_t i) { return (double)__brev(i) * 2.3283064365386963e-10; }
+
+// Local light directions: the caller's set, or the centred Hammersley set.
+__global__ void dirs_kernel(int32_t S, const float* __restrict__ dirs_local, float4* __restrict__ out4,
+                            float* __restrict__ out3)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    float3 d;
+    if (dirs_local) {
+        d = load3(dirs_local, i);
+    } else {
+        const double z = (i + 0.5) / S;
+        const double phi = 6.283185307179586476925 * radical_inverse2((uint32_t)i);
+        const double s = sqrt(1.0 - z * z);
+        d = f3((float)(s * cos(phi)), (float)(s * sin(phi)), (float)z);
+    }
+    if (out4) out4[i] = make_float4(d.x, d.y, d.z, 0.f);
+    if (out3) {
+        out3[3 * i] = d.x;
+        out3[3 * i + 1] = d.y;
+        out3[3 * i + 2] = d.z;
+    }
+}
+
+// Bilinear environment lookup L_dir(w) (z-up equirectangular).
+__device__ __forceinline__ float3 env_lookup(const float4* __restrict__ env4, int He, int We, float3 w)
+{
+    const float th = atan2f(sqrtf(w.x * w.x + w.y * w.y), w.z);
+    const float ph = atan2f(w.y, w.x);
+    const float s = (ph + kPi) * kInv2Pi * We - 0.5f;
+    const float t = th * kInvPi * He - 0.5f;
+    const float fs = floorf(s), ft = floorf(t);
+    const float a = s - fs, b = t - ft;
+    int c0 = (int)fs;
+    c0 = c0 < 0 ? c0 + We : c0;
+    c0 = min(max(c0, 0), We - 1);
+    const int r0 = min(max((int)ft + 1, 0), He);
+    const float4* p = env4 + (int64_t)r0 * (We + 1) + c0;
+    const float4 e00 = __ldg(p), e01 = __ldg(p + 1), e10 = __ldg(p + We + 1), e11 = __ldg(p + We + 2);
+    const float w00 = (1.f - a) * (1.f - b), w01 = a * (1.f - b), w10 = (1.f - a) * b, w11 = a * b;
+    return f3(w00 * e00.x + w01 * e01.x + w10 * e10.x + w11 * e11.x,
+              w00 * e00.y + w01 * e01.y + w10 * e10.y + w11 * e11.y,
+              w00 * e00.z + w01 * e01.z + w10 * e10.z + w11 * e11.z);
+}
+
+struct ShadeK {
+    const float *n, *wo, *albedo, *rough, *metal;
+    int64_t M;
+    const void* rgbo;
+    int32_t R, K, S, He, We;
+    const float4* env4;
+    const float4* dirs;
+    const int32_t* idx;
+    const float* w;
+    float specular;
+    float* out;
+};
+
+// ---------------------------------------------------------------------------
+// Query + shade. LANES consecutive threads share one point and split its S
+// directions; one warp covers 32/LANES points.
+// ---------------------------------------------------------------------------
+template <int DT, int KMAX, int LANES, int MODE>
+__global__ void __launch_bounds__(256) shade_kernel(const ShadeK a)
+{
+    using TX = Texel<DT>;
+    extern __shared__ float4 s_dirs[];
+    for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_dirs[i] = a.dirs[i];
+    __syncthreads();
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = gid / LANES;
+    const int sub = (int)(gid % LANES);
+    const bool active = m < a.M;
+    const int64_t mm = active ? m : 0;
+
+    const float3 nr = load3(a.n, mm);
+    const float nl = sqrtf(dot3(nr, nr));
+    const float3 n = f3(nr.x / nl, nr.y / nl, nr.z / nl);
+    float3 tt, bb;
+    onb(n, tt, bb);
+    const float3 wo = load3(a.wo, mm);
+    const int RS = a.R + 2;
+    const typename TX::raw* base[KMAX];
+    float W[KMAX];
+    const typename TX::raw* atlas = reinterpret_cast<const typename TX::raw*>(a.rgbo);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const bool on = k < a.K;
+        const int32_t id = on ? __ldg(a.idx + mm * a.K + k) : 0;
+        W[k] = on ? __ldg(a.w + mm * a.K + k) : 0.f;
+        base[k] = atlas + (int64_t)id * RS * RS;
+    }
+    // per-point BRDF constants
+    float3 kd, F0;
+    float a2 = 0.f, kk = 0.f, specV = 0.f, NdotV = 1.f;
+    if (MODE == SOP_MODE_SHADE) {
+        const float3 alb = load3(a.albedo, mm);
+        const float r = __ldg(a.rough + mm), mt = __ldg(a.metal + mm);
+        const float dsc = (1.f - mt) * kInvPi;
+        kd = f3(dsc * alb.x, dsc * alb.y, dsc * alb.z);
+        const float f0d = 0.08f * a.specular * (1.f - mt);
+        F0 = f3(f0d + alb.x * mt, f0d + alb.y * mt, f0d + alb.z * mt);
+        const float al = r * r;
+        a2 = al * al;
+        kk = (r + 1.f) * (r + 1.f) * 0.125f;
+        NdotV = fmaxf(dot3(n, wo), 1e-4f);
+        const float G1V = NdotV / (NdotV * (1.f - kk) + kk);
+        specV = G1V / (4.f * NdotV);
+    }
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, den0 = 0.f, den1 = 0.f, den2 = 0.f;
+    const float Rf = (float)a.R;
+    for (int i = sub; i < a.S; i += LANES) {
+        const float4 l = s_dirs[i];
+        const float3 w = f3(fmaf(l.x, tt.x, fmaf(l.y, bb.x, l.z * n.x)), fmaf(l.x, tt.y, fmaf(l.y, bb.y, l.z * n.y)),
+                            fmaf(l.x, tt.z, fmaf(l.y, bb.z, l.z * n.z)));
+        const float2 uv = oct_encode(w);
+        const float s = uv.x * Rf - 0.5f, t = uv.y * Rf - 0.5f;
+        const float fi = floorf(s), fj = floorf(t);
+        const float fu = s - fi, fv = t - fj;
+        const int i0 = min(max((int)fi + 1, 0), a.R), j0 = min(max((int)fj + 1, 0), a.R);
+        const int off = j0 * RS + i0;
+        const float w00 = (1.f - fu) * (1.f - fv), w10 = fu * (1.f - fv), w01 = (1.f - fu) * fv, w11 = fu * fv;
+        float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (k < a.K) {
+                const typename TX::raw* p = base[k] + off;
+                const float4 t00 = TX::load(p), t10 = TX::load(p + 1), t01 = TX::load(p + RS), t11 = TX::load(p + RS + 1);
+                const float c00 = W[k] * w00, c10 = W[k] * w10, c01 = W[k] * w01, c11 = W[k] * w11;
+                pr.x += c00 * t00.x + c10 * t10.x + c01 * t01.x + c11 * t11.x;
+                pr.y += c00 * t00.y + c10 * t10.y + c01 * t01.y + c11 * t11.y;
+                pr.z += c00 * t00.z + c10 * t10.z + c01 * t01.z + c11 * t11.z;
+                pr.w += c00 * t00.w + c10 * t10.w + c01 * t01.w + c11 * t11.w;
+            }
+        }
+        const float3 Ld = env_lookup(a.env4, a.He, a.We, w);
+        const float NdotL = l.z;
+        const float vis = 1.f - pr.w;
+        if (MODE == SOP_MODE_SHADE) {
+            float3 h = w + wo;
+            const float hl2 = dot3(h, h);
+            h = hl2 > 1e-30f ? (1.f / sqrtf(hl2)) * h : n;
+            const float NdotH = dot3(n, h), VdotH = dot3(wo, h);
+            const float3 cr = cross3(n, h);
+            const float sin2 = dot3(cr, cr);
+            const float den = NdotH * NdotH * a2 + sin2;
+            const float D = a2 / (kPi * den * den);
+            const float spec = D * specV / (NdotL * (1.f - kk) + kk);
+            const float x1 = 1.f - VdotH, x2 = x1 * x1, fc = x2 * x2 * x1;
+            const float f0 = kd.x + spec * (F0.x + (1.f - F0.x) * fc);
+            const float f1 = kd.y + spec * (F0.y + (1.f - F0.y) * fc);
+            const float f2 = kd.z + spec * (F0.z + (1.f - F0.z) * fc);
+            acc0 += f0 * (vis * Ld.x + pr.x) * NdotL;
+            acc1 += f1 * (vis * Ld.y + pr.y) * NdotL;
+            acc2 += f2 * (vis * Ld.z + pr.z) * NdotL;
+        } else {
+            acc0 += Ld.x * vis * NdotL;
+            acc1 += Ld.y * vis * NdotL;
+            acc2 += Ld.z * vis * NdotL;
+            den0 += Ld.x * NdotL;
+            den1 += Ld.y * NdotL;
+            den2 += Ld.z * NdotL;
+        }
+    }
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) {
+        acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+        acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+        acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+        if (MODE == SOP_MODE_SHADOW) {
+            den0 += __shfl_xor_sync(0xffffffffu, den0, o);
+            den1 += __shfl_xor_sync(0xffffffffu, den1, o);
+            den2 += __shfl_xor_sync(0xffffffffu, den2, o);
+        }
+    }
+    if (active && sub == 0) {
+        float* o = a.out + 3 * m;
+        if (MODE == SOP_MODE_SHADE) {
+            const float sc = 2.f * kPi / (float)a.S;
+            o[0] = sc * acc0;
+            o[1] = sc * acc1;
+            o[2] = sc * acc2;
+        } else {
+            o[0] = den0 < 1e-20f ? 1.f : acc0 / den0;
+            o[1] = den1 < 1e-20f ? 1.f : acc1 / den1;
+            o[2] = den2 < 1e-20f ? 1.f : acc2 / den2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_hammersley(int32_t S, float* out3, cudaStream_t s)
+{
+    dirs_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, nullptr, nullptr, out3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s)
+{
+    ProbeGrid* grid = reinterpret_cast<ProbeGrid*>(ws + L.grid_hdr);
+    int32_t* cstart = reinterpret_cast<int32_t*>(ws + L.cell_start);
+    int32_t* ccnt = reinterpret_cast<int32_t*>(ws + L.cell_cnt);
+    int4* ent = reinterpret_cast<int4*>(ws + L.entries);
+    probe_grid_kernel<<<1, 1024, 0, s>>>(a.probe_pos, a.P, L.g_axis, grid, cstart, ccnt, ent);
+    int32_t* idx = reinterpret_cast<int32_t*>(ws + L.idx);
+    float* w = reinterpret_cast<float*>(ws + L.w);
+    if (a.M > 0) {
+        const int bs = 128;
+        const unsigned nb = (unsigned)((a.M + bs - 1) / bs);
+#define SOP_KNN(KM) \
+    knn_kernel<KM><<<nb, bs, 0, s>>>(a.x, a.n, a.M, a.K, a.snap_key, grid, cstart, ent, a.probe_pos, idx, w, a.out_idx, a.out_w)
+        if (a.K <= 4) SOP_KNN(4);
+        else if (a.K <= 8) SOP_KNN(8);
+        else if (a.K <= 16) SOP_KNN(16);
+        else SOP_KNN(32);
+#undef SOP_KNN
+    }
+    const int64_t ne = (int64_t)(a.He + 2) * (a.We + 1);
+    env_pack_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(a.env, a.He, a.We,
+                                                                   reinterpret_cast<float4*>(ws + L.env4));
+    dirs_kernel<<<(a.S + 127) / 128, 128, 0, s>>>(a.S, a.dirs_local, reinterpret_cast<float4*>(ws + L.dirs), nullptr);
+    return cudaGetLastError();
+}
+
+template <int DT, int KMAX, int MODE>
+static cudaError_t shade_dispatch(const ShadeK& k, cudaStream_t s)
+{
+    constexpr int LANES = 4;
+    const int bs = 256;
+    const int64_t threads = k.M * LANES;
+    const unsigned nb = (unsigned)((threads + bs - 1) / bs);
+    const size_t smem = sizeof(float4) * (size_t)k.S;
+    auto fn = shade_kernel<DT, KMAX, LANES, MODE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    fn<<<nb, bs, smem, s>>>(k);
+    return cudaGetLastError();
+}
+
+template <int DT, int MODE>
+static cudaError_t shade_k(const ShadeK& k, cudaStream_t s)
+{
+    if (k.K <= 4) return shade_dispatch<DT, 4, MODE>(k, s);
+    if (k.K <= 8) return shade_dispatch<DT, 8, MODE>(k, s);
+    if (k.K <= 16) return shade_dispatch<DT, 16, MODE>(k, s);
+    return shade_dispatch<DT, 32, MODE>(k, s);
+}
+
+template <int DT>
+static cudaError_t shade_mode(const ShadeK& k, int mode, cudaStream_t s)
+{
+    return mode == SOP_MODE_SHADE ? shade_k<DT, SOP_MODE_SHADE>(k, s) : shade_k<DT, SOP_MODE_SHADOW>(k, s);
+}
+
+cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s)
+{
+    if (a.M == 0) return cudaSuccess;
+    ShadeK k;
+    k.n = a.n;
+    k.wo = a.wo;
+    k.albedo = a.albedo;
+    k.rough = a.rough;
+    k.metal = a.metal;
+    k.M = a.M;
+    k.rgbo = a.rgbo;
+    k.R = a.R;
+    k.K = a.K;
+    k.S = a.S;
+    k.He = a.He;
+    k.We = a.We;
+    k.env4 = reinterpret_cast<const float4*>(ws + L.env4);
+    k.dirs = reinterpret_cast<const float4*>(ws + L.dirs);
+    k.idx = reinterpret_cast<const int32_t*>(ws + L.idx);
+    k.w = reinterpret_cast<const float*>(ws + L.w);
+    k.specular = a.specular;
+    k.out = a.out;
+    switch (a.rgbo_dtype) {
+    case SOP_F32: return shade_mode<SOP_F32>(k, a.mode, s);
+    case SOP_BF16: return shade_mode<SOP_BF16>(k, a.mode, s);
+    case SOP_F16: return shade_mode<SOP_F16>(k, a.mode, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sop

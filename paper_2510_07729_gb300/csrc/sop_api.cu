@@ -1,0 +1,238 @@
+// C ABI of libsop: argument validation, workspace layout, launch sequencing.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "sop_device.cuh"
+#include "sop_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+sop_status fail(sop_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+sop_status cuda_status(cudaError_t e, const char* where)
+{
+    if (e == cudaSuccess) return SOP_OK;
+    return fail(SOP_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool dtype_ok(int32_t dt, bool depth)
+{
+    if (dt == SOP_F32 || dt == SOP_BF16 || dt == SOP_F16) return true;
+    return depth && dt == SOP_FP8E4M3;
+}
+
+size_t rgbo_texel_bytes(int32_t dt) { return dt == SOP_F32 ? 16 : 8; }
+size_t depth_texel_bytes(int32_t dt) { return dt == SOP_F32 ? 4 : (dt == SOP_FP8E4M3 ? 1 : 2); }
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+sop_status check_atlas(const sop_atlas* a, bool need_depth)
+{
+    if (!a) return fail(SOP_ERR_INVALID_ARG, "atlas is NULL");
+    if (a->P < 1) return fail(SOP_ERR_INVALID_ARG, "atlas P = %d < 1", a->P);
+    if (a->R < 2 || a->R > 64) return fail(SOP_ERR_INVALID_ARG, "atlas R = %d outside [2, 64]", a->R);
+    if (!dtype_ok(a->rgbo_dtype, false))
+        return fail(SOP_ERR_UNSUPPORTED, "atlas rgbo dtype %d not supported (F32, BF16, F16)", a->rgbo_dtype);
+    if (!a->rgbo || !aligned(a->rgbo, 16)) return fail(SOP_ERR_INVALID_ARG, "atlas rgbo NULL or not 16-byte aligned");
+    if (!a->probe_pos) return fail(SOP_ERR_INVALID_ARG, "atlas probe_pos is NULL");
+    if (need_depth && a->depth) {
+        if (!dtype_ok(a->depth_dtype, true))
+            return fail(SOP_ERR_UNSUPPORTED, "atlas depth dtype %d not supported", a->depth_dtype);
+        if (!(a->depth_scale > 0.f) || !isfinite(a->depth_scale))
+            return fail(SOP_ERR_INVALID_ARG, "atlas depth_scale must be finite and > 0");
+    }
+    return SOP_OK;
+}
+
+sop_status check_ws(void* ws, size_t ws_bytes, size_t need)
+{
+    if (need == 0) return SOP_OK;
+    if (!ws) return fail(SOP_ERR_WORKSPACE, "workspace is NULL (%zu bytes needed)", need);
+    if (!aligned(ws, 256)) return fail(SOP_ERR_WORKSPACE, "workspace not 256-byte aligned");
+    if (ws_bytes < need) return fail(SOP_ERR_WORKSPACE, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    return SOP_OK;
+}
+
+sop_status check_shade(const sop_shade_params* p, int32_t P)
+{
+    if (!p) return fail(SOP_ERR_INVALID_ARG, "params is NULL");
+    if (p->K < 1 || p->K > 32) return fail(SOP_ERR_INVALID_ARG, "K = %d outside [1, 32]", p->K);
+    if (p->K > P) return fail(SOP_ERR_INVALID_ARG, "K = %d exceeds the number of probes %d", p->K, P);
+    if (p->S < 1 || p->S > 4096) return fail(SOP_ERR_INVALID_ARG, "S = %d outside [1, 4096]", p->S);
+    if (p->mode != SOP_MODE_SHADE && p->mode != SOP_MODE_SHADOW)
+        return fail(SOP_ERR_INVALID_ARG, "mode = %d is neither SHADE nor SHADOW", p->mode);
+    if (!(p->eps_snap >= 0.f) || !isfinite(p->eps_snap)) return fail(SOP_ERR_INVALID_ARG, "eps_snap must be >= 0");
+    if (!isfinite(p->specular)) return fail(SOP_ERR_INVALID_ARG, "specular must be finite");
+    return SOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sop_last_error(void) { return g_err; }
+
+const char* sop_version(void) { return "libsop 0.1 (sm_103a)"; }
+
+sop_status sop_atlas_bytes(int32_t P, int32_t R, int32_t rgbo_dtype, int32_t depth_dtype, size_t* rgbo_bytes,
+                           size_t* depth_bytes)
+{
+    if (P < 1 || R < 2 || R > 64) return fail(SOP_ERR_INVALID_ARG, "P = %d, R = %d invalid", P, R);
+    if (!dtype_ok(rgbo_dtype, false) || !dtype_ok(depth_dtype, true))
+        return fail(SOP_ERR_INVALID_ARG, "unknown dtype (%d, %d)", rgbo_dtype, depth_dtype);
+    const size_t tex = (size_t)P * (R + 2) * (R + 2);
+    if (rgbo_bytes) *rgbo_bytes = tex * rgbo_texel_bytes(rgbo_dtype);
+    if (depth_bytes) *depth_bytes = tex * depth_texel_bytes(depth_dtype);
+    return SOP_OK;
+}
+
+sop_status sop_atlas_pack(const float* maps_rgb, const float* maps_occ, const float* maps_depth,
+                          const sop_atlas* atlas, void* stream)
+{
+    sop_status st = check_atlas(atlas, maps_depth != nullptr);
+    if (st != SOP_OK) return st;
+    if (!maps_rgb || !maps_occ) return fail(SOP_ERR_INVALID_ARG, "maps_rgb / maps_occ is NULL");
+    return cuda_status(sop::launch_atlas_pack(maps_rgb, 3, maps_occ, 1, maps_depth, *atlas, (cudaStream_t)stream),
+                       "sop_atlas_pack");
+}
+
+sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream)
+{
+    if (S < 1 || S > 4096) return fail(SOP_ERR_INVALID_ARG, "S = %d outside [1, 4096]", S);
+    if (!out_dirs) return fail(SOP_ERR_INVALID_ARG, "out_dirs is NULL");
+    return cuda_status(sop::launch_hammersley(S, out_dirs, (cudaStream_t)stream), "sop_hammersley");
+}
+
+size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R)
+{
+    if (n_gauss < 0 || P < 1 || R < 2) return 0;
+    return sop::bake_layout(n_gauss, P, R, 0).total;
+}
+
+sop_status sop_bake(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
+                    size_t ws_bytes, void* stream)
+{
+    if (!g || !params) return fail(SOP_ERR_INVALID_ARG, "gaussians or params is NULL");
+    sop_status st = check_atlas(atlas, true);
+    if (st != SOP_OK) return st;
+    if (g->n < 0 || g->n > (int64_t)INT32_MAX) return fail(SOP_ERR_INVALID_ARG, "n = %lld out of range", (long long)g->n);
+    if (g->n > 0 && (!g->mean || !g->scale || !g->quat || !g->opacity || !g->rgb))
+        return fail(SOP_ERR_INVALID_ARG, "a Gaussian array is NULL");
+    if (!(params->alpha_min > 0.f) || !(params->alpha_max >= params->alpha_min) || !(params->alpha_max < 1.f) ||
+        !(params->t_stop >= 0.f) || !(params->t_stop < 1.f) || !isfinite(params->t_near))
+        return fail(SOP_ERR_INVALID_ARG, "bake params out of range (need 0 < alpha_min <= alpha_max < 1, "
+                                         "0 <= t_stop < 1, finite t_near)");
+    const int64_t RR = (int64_t)atlas->R * atlas->R;
+    if ((int64_t)atlas->P * RR > (int64_t)INT32_MAX)
+        return fail(SOP_ERR_INVALID_ARG, "P * R^2 exceeds 2^31 texels");
+    // the caller's workspace decides how many cell entries fit
+    sop::BakeLayout L0 = sop::bake_layout(g->n, atlas->P, atlas->R, 1);
+    if (!ws || ws_bytes < L0.total) return check_ws(ws, ws_bytes, sop::bake_layout(g->n, atlas->P, atlas->R, 0).total);
+    // largest entry capacity whose layout fits the caller's workspace
+    int64_t cap = 64 + (int64_t)((ws_bytes - L0.total) / (sizeof(int32_t) + sizeof(float4)));
+    sop::BakeLayout L = sop::bake_layout(g->n, atlas->P, atlas->R, cap);
+    while (L.total > ws_bytes && L.entries_cap > 1) L = sop::bake_layout(g->n, atlas->P, atlas->R, L.entries_cap - 1);
+    st = check_ws(ws, ws_bytes, L.total);
+    if (st != SOP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    st = cuda_status(sop::launch_bake_bin(*g, params->alpha_min, L, w, s), "sop_bake (binning)");
+    if (st != SOP_OK) return st;
+    // size check of the cell lists: one 4-byte read-back
+    int32_t n_entries = 0;
+    st = cuda_status(cudaMemcpyAsync(&n_entries, w + L.hdr + offsetof(sop::GaussGrid, n_entries), sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, s),
+                     "sop_bake (read-back)");
+    if (st != SOP_OK) return st;
+    st = cuda_status(cudaStreamSynchronize(s), "sop_bake (sync)");
+    if (st != SOP_OK) return st;
+    if (n_entries == INT32_MAX || (int64_t)n_entries > L.entries_cap) {
+        const sop::BakeLayout need = sop::bake_layout(g->n, atlas->P, atlas->R, (int64_t)n_entries + 1);
+        return fail(SOP_ERR_WORKSPACE, "sop_bake: %d grid entries exceed the workspace; need %zu bytes", n_entries,
+                    need.total);
+    }
+    return cuda_status(sop::launch_bake_trace(*g, *atlas, *params, L, w, s), "sop_bake (trace)");
+}
+
+size_t sop_query_workspace_bytes(int32_t P, int64_t M, const sop_shade_params* params, int32_t He, int32_t We)
+{
+    if (!params || P < 1 || M < 0 || He < 1 || We < 1 || params->K < 1 || params->S < 1) return 0;
+    return sop::query_layout(P, M, params->K, params->S, He, We).total;
+}
+
+static sop_status query_common(const float* x, const float* n, const float* wo, const float* albedo, const float* rough,
+                               const float* metal, int64_t M, const sop_atlas* atlas, const float* env, int32_t He,
+                               int32_t We, const float* dirs_local, const sop_shade_params* params, void* ws,
+                               size_t ws_bytes, sop::QueryArgs& a, sop::QueryLayout& L)
+{
+    sop_status st = check_atlas(atlas, false);
+    if (st != SOP_OK) return st;
+    st = check_shade(params, atlas->P);
+    if (st != SOP_OK) return st;
+    if (M < 0 || M > ((int64_t)1 << 36)) return fail(SOP_ERR_INVALID_ARG, "M = %lld out of range", (long long)M);
+    if (He < 1 || We < 1 || (int64_t)He * We > ((int64_t)1 << 28))
+        return fail(SOP_ERR_INVALID_ARG, "environment size %d x %d invalid", He, We);
+    if (!env) return fail(SOP_ERR_INVALID_ARG, "env is NULL");
+    if (M > 0 && (!x || !n || !wo || !albedo || !rough || !metal))
+        return fail(SOP_ERR_INVALID_ARG, "a shading-point array is NULL");
+    L = sop::query_layout(atlas->P, M, params->K, params->S, He, We);
+    st = check_ws(ws, ws_bytes, L.total);
+    if (st != SOP_OK) return st;
+    a = sop::QueryArgs{};
+    a.x = x;
+    a.n = n;
+    a.wo = wo;
+    a.albedo = albedo;
+    a.rough = rough;
+    a.metal = metal;
+    a.M = M;
+    a.rgbo = atlas->rgbo;
+    a.rgbo_dtype = atlas->rgbo_dtype;
+    a.P = atlas->P;
+    a.R = atlas->R;
+    a.probe_pos = atlas->probe_pos;
+    a.env = env;
+    a.He = He;
+    a.We = We;
+    a.dirs_local = dirs_local;
+    a.K = params->K;
+    a.S = params->S;
+    a.mode = params->mode;
+    a.specular = params->specular;
+    const double e = (double)params->eps_snap * 1048576.0;
+    a.snap_key = (uint64_t)floor(e * e);
+    return SOP_OK;
+}
+
+sop_status sop_query_shade(const float* x, const float* n, const float* wo, const float* albedo, const float* rough,
+                           const float* metal, int64_t M, const sop_atlas* atlas, const float* env, int32_t He,
+                           int32_t We, const float* dirs_local, const sop_shade_params* params, float* out,
+                           int32_t* out_idx, float* out_w, void* ws, size_t ws_bytes, void* stream)
+{
+    sop::QueryArgs a;
+    sop::QueryLayout L;
+    sop_status st = query_common(x, n, wo, albedo, rough, metal, M, atlas, env, He, We, dirs_local, params, ws,
+                                 ws_bytes, a, L);
+    if (st != SOP_OK) return st;
+    if (M > 0 && !out) return fail(SOP_ERR_INVALID_ARG, "out is NULL");
+    a.out = out;
+    a.out_idx = out_idx;
+    a.out_w = out_w;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_status(sop::launch_query_prep(a, L, (char*)ws, s), "sop_query_shade (prep)");
+    if (st != SOP_OK) return st;
+    return cuda_status(sop::launch_shade(a, L, (char*)ws, s), "sop_query_shade (shade)");
+}
+
+}  // extern "C"

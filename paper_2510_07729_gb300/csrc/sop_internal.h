@@ -1,0 +1,66 @@
+// Host-side internal interface between the C ABI layer (sop_api.cu) and the
+// kernel translation units. Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "sop.h"
+
+namespace sop {
+
+struct ProbeGrid;
+struct GaussGrid;
+
+// ---- query ----------------------------------------------------------------
+struct QueryLayout {
+    size_t grid_hdr, cell_start, cell_cnt, entries, env4, dirs, idx, w, total;
+    int32_t cells_cap, g_axis;
+};
+QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He, int32_t We);
+
+struct QueryArgs {
+    const float *x, *n, *wo, *albedo, *rough, *metal;
+    int64_t M;
+    const void* rgbo;
+    int32_t rgbo_dtype;
+    int32_t P, R;
+    const float* probe_pos;
+    const float* env;
+    int32_t He, We;
+    const float* dirs_local;
+    int32_t K, S, mode;
+    float specular;
+    uint64_t snap_key;
+    float* out;
+    int32_t* out_idx;
+    float* out_w;
+    // upstream gradient and gradient outputs (backward only)
+    const float* grad_out;
+    float *g_albedo, *g_rough, *g_metal, *g_normal, *g_env, *g_atlas;
+};
+
+// Enqueue the probe grid, nearest-probe search + weights, environment and
+// direction tables (shared by forward and backward).
+cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s);
+cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s);
+cudaError_t launch_hammersley(int32_t S, float* out3, cudaStream_t s);
+
+// ---- atlas pack -------------------------------------------------------------
+cudaError_t launch_atlas_pack(const float* rgb, int rgb_stride, const float* occ, int occ_stride, const float* depth,
+                              const sop_atlas& atlas, cudaStream_t s);
+
+// ---- bake -------------------------------------------------------------------
+struct BakeLayout {
+    size_t hdr, rec, bbox, cell_start, cell_cnt, entries, ent_sph, dirs, maps, depth, total;
+    int64_t cells_cap, entries_cap;
+};
+BakeLayout bake_layout(int64_t N, int32_t P, int32_t R, int64_t entries_cap);
+cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s);
+cudaError_t launch_bake_trace(const sop_gaussians& g, const sop_atlas& atlas, const sop_bake_params& bp,
+                              const BakeLayout& L, char* ws, cudaStream_t s);
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace sop

@@ -1,0 +1,279 @@
+"""Python binding of libsop (argument marshalling only).
+
+Every function here passes torch CUDA tensors' device pointers and the
+current CUDA stream to the C ABI declared in include/sop.h; all arithmetic
+runs in the library's kernels. There is no fallback: if libsop.so is missing
+or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+from . import build as _build
+
+SOP_F32, SOP_BF16, SOP_F16, SOP_FP8E4M3 = 0, 1, 2, 3
+MODE_SHADE, MODE_SHADOW = 0, 1
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "WORKSPACE", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "DEVICE"}
+
+
+class SopError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libsop {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Gaussians(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("opacity", C.c_void_p),
+                ("rgb", C.c_void_p), ("n", C.c_int64)]
+
+
+class AtlasDesc(C.Structure):
+    _fields_ = [("rgbo", C.c_void_p), ("depth", C.c_void_p), ("rgbo_dtype", C.c_int32), ("depth_dtype", C.c_int32),
+                ("P", C.c_int32), ("R", C.c_int32), ("depth_scale", C.c_float), ("probe_pos", C.c_void_p),
+                ("probe_nrm", C.c_void_p)]
+
+
+class BakeParams(C.Structure):
+    _fields_ = [("t_near", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float)]
+
+
+class ShadeParams(C.Structure):
+    _fields_ = [("K", C.c_int32), ("S", C.c_int32), ("mode", C.c_int32), ("specular", C.c_float),
+                ("eps_snap", C.c_float)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsop.so (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libsop.so not built ({_build.LIB}); run paper_2510_07729_gb300.build.build()")
+    lib = C.CDLL(_build.LIB)
+    vp, i32, i64, sz, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.c_float
+    lib.sop_last_error.restype = C.c_char_p
+    lib.sop_version.restype = C.c_char_p
+    lib.sop_atlas_bytes.argtypes = [i32, i32, i32, i32, C.POINTER(sz), C.POINTER(sz)]
+    lib.sop_atlas_pack.argtypes = [vp, vp, vp, C.POINTER(AtlasDesc), vp]
+    lib.sop_hammersley.argtypes = [i32, vp, vp]
+    lib.sop_bake_workspace_bytes.argtypes = [i64, i32, i32]
+    lib.sop_bake_workspace_bytes.restype = sz
+    lib.sop_bake.argtypes = [C.POINTER(Gaussians), C.POINTER(AtlasDesc), C.POINTER(BakeParams), vp, sz, vp]
+    lib.sop_query_workspace_bytes.argtypes = [i32, i64, C.POINTER(ShadeParams), i32, i32]
+    lib.sop_query_workspace_bytes.restype = sz
+    lib.sop_query_shade.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
+                                    C.POINTER(ShadeParams), vp, vp, vp, vp, sz, vp]
+    for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_query_shade"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != 0:
+        raise SopError(st, load().sop_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libsop takes CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("libsop takes contiguous tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _f32(t, shape=None):
+    if t.dtype != torch.float32:
+        raise TypeError(f"expected float32, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return _ptr(t)
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ws(nbytes, device):
+    # 256-byte aligned scratch from torch's caching allocator
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+_TORCH_DT = {SOP_F32: torch.float32, SOP_BF16: torch.bfloat16, SOP_F16: torch.float16,
+             SOP_FP8E4M3: torch.float8_e4m3fn}
+
+
+@dataclass
+class Atlas:
+    """Caller-owned probe atlas (see sop_atlas in include/sop.h)."""
+    rgbo: torch.Tensor
+    depth: torch.Tensor | None
+    probe_pos: torch.Tensor
+    probe_nrm: torch.Tensor | None
+    rgbo_dtype: int = SOP_F32
+    depth_dtype: int = SOP_F32
+    depth_scale: float = 1.0
+    desc: AtlasDesc = field(default=None, repr=False)
+
+    @property
+    def P(self):
+        return self.probe_pos.shape[0]
+
+    @property
+    def R(self):
+        return self.rgbo.shape[1] - 2
+
+    def c(self):
+        d = AtlasDesc()
+        d.rgbo = self.rgbo.data_ptr()
+        d.depth = self.depth.data_ptr() if self.depth is not None else None
+        d.rgbo_dtype, d.depth_dtype = self.rgbo_dtype, self.depth_dtype
+        d.P, d.R = self.P, self.R
+        d.depth_scale = self.depth_scale
+        d.probe_pos = self.probe_pos.data_ptr()
+        d.probe_nrm = self.probe_nrm.data_ptr() if self.probe_nrm is not None else None
+        self.desc = d
+        return d
+
+    def interior(self):
+        """Interior texels as float32: rgb [P,R,R,3], occ [P,R,R], depth."""
+        R = self.R
+        v = self.rgbo.float()[:, 1:R + 1, 1:R + 1]
+        dep = None
+        if self.depth is not None:
+            dep = self.depth.float()[:, 1:R + 1, 1:R + 1] * self.depth_scale
+        return v[..., :3], v[..., 3], dep
+
+
+def make_atlas(probe_pos, R, rgbo_dtype=SOP_F32, depth_dtype=SOP_F32, probe_nrm=None, depth_scale=1.0,
+               with_depth=True):
+    P = probe_pos.shape[0]
+    dev = probe_pos.device
+    rgbo = torch.empty((P, R + 2, R + 2, 4), dtype=_TORCH_DT[rgbo_dtype], device=dev)
+    depth = torch.empty((P, R + 2, R + 2), dtype=_TORCH_DT[depth_dtype], device=dev) if with_depth else None
+    return Atlas(rgbo, depth, probe_pos.contiguous(), probe_nrm, rgbo_dtype, depth_dtype, float(depth_scale))
+
+
+def version() -> str:
+    return load().sop_version().decode()
+
+
+def atlas_bytes(P, R, rgbo_dtype=SOP_F32, depth_dtype=SOP_F32):
+    a, b = C.c_size_t(), C.c_size_t()
+    _check(load().sop_atlas_bytes(P, R, rgbo_dtype, depth_dtype, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def atlas_pack(maps_rgb, maps_occ, maps_depth, atlas: Atlas):
+    P, R = atlas.P, atlas.R
+    d = atlas.c()
+    _check(load().sop_atlas_pack(_f32(maps_rgb, (P, R, R, 3)), _f32(maps_occ, (P, R, R)),
+                                 None if maps_depth is None else _f32(maps_depth, (P, R, R)), C.byref(d), _stream()))
+    return atlas
+
+
+def hammersley(S, device="cuda"):
+    out = torch.empty((S, 3), dtype=torch.float32, device=device)
+    _check(load().sop_hammersley(S, _ptr(out), _stream()))
+    return out
+
+
+def _gauss(g):
+    n = g["mean"].shape[0]
+    s = Gaussians()
+    s.mean = g["mean"].data_ptr() if n else None
+    s.scale = g["scale"].data_ptr() if n else None
+    s.quat = g["quat"].data_ptr() if n else None
+    s.opacity = g["opacity"].data_ptr() if n else None
+    s.rgb = g["rgb"].data_ptr() if n else None
+    s.n = n
+    for k, shp in (("mean", (n, 3)), ("scale", (n, 3)), ("quat", (n, 4)), ("opacity", (n,)), ("rgb", (n, 3))):
+        t = g[k]
+        if n:
+            _f32(t, shp)
+    return s
+
+
+def bake_workspace_bytes(n_gauss, P, R):
+    return int(load().sop_bake_workspace_bytes(n_gauss, P, R))
+
+
+_bake_ws_cache = {}
+
+
+def bake(gauss, atlas: Atlas, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, workspace=None):
+    """Bake every texel of `atlas` against the Gaussians (dict of CUDA
+    float32 tensors: mean, scale, quat, opacity, rgb). Synchronises once."""
+    lib = load()
+    g = _gauss(gauss)
+    bp = BakeParams(t_near, alpha_min, alpha_max, t_stop)
+    d = atlas.c()
+    dev = atlas.rgbo.device
+    n = int(g.n)
+    if workspace is None:
+        need = bake_workspace_bytes(n, atlas.P, atlas.R)
+        key = (dev, n, atlas.P, atlas.R)
+        ws = _bake_ws_cache.get(key)
+        if ws is None or ws.numel() < need:
+            ws = _ws(need, dev)
+            _bake_ws_cache.clear()
+            _bake_ws_cache[key] = ws
+    else:
+        ws = workspace
+    st = lib.sop_bake(C.byref(g), C.byref(d), C.byref(bp), _ptr(ws), ws.numel(), _stream())
+    if st == 3 and workspace is None:  # cell lists need more room: retry once with the size asked for
+        msg = lib.sop_last_error().decode()
+        need = int(msg.rsplit("need ", 1)[1].split()[0]) if "need " in msg else 2 * ws.numel()
+        ws = _ws(need, dev)
+        _bake_ws_cache.clear()
+        _bake_ws_cache[(dev, n, atlas.P, atlas.R)] = ws
+        st = lib.sop_bake(C.byref(g), C.byref(d), C.byref(bp), _ptr(ws), ws.numel(), _stream())
+    _check(st)
+    return atlas
+
+
+def query_workspace_bytes(P, M, K, S, He, We, mode=MODE_SHADE):
+    sp = ShadeParams(K, S, mode, 0.5, 1e-6)
+    return int(load().sop_query_workspace_bytes(P, M, C.byref(sp), He, We))
+
+
+def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MODE_SHADE, specular=0.5,
+                eps_snap=1e-6, dirs_local=None, out=None, return_idx=False, workspace=None):
+    """SOP query + shade of M points; returns out [M,3] (and idx [M,K] int32,
+    W [M,K] float32 when return_idx)."""
+    lib = load()
+    M = x.shape[0]
+    He, We = env.shape[0], env.shape[1]
+    dev = x.device
+    sp = ShadeParams(K, S, mode, specular, eps_snap)
+    d = atlas.c()
+    if out is None:
+        out = torch.empty((M, 3), dtype=torch.float32, device=dev)
+    idx = torch.empty((M, K), dtype=torch.int32, device=dev) if return_idx else None
+    w = torch.empty((M, K), dtype=torch.float32, device=dev) if return_idx else None
+    need = int(lib.sop_query_workspace_bytes(atlas.P, M, C.byref(sp), He, We))
+    ws = workspace if workspace is not None else _ws(need, dev)
+    for t, shp in ((x, (M, 3)), (n, (M, 3)), (wo, (M, 3)), (albedo, (M, 3)), (rough, (M,)), (metal, (M,)),
+                   (env, (He, We, 3))):
+        _f32(t, shp)
+    _check(lib.sop_query_shade(_ptr(x), _ptr(n), _ptr(wo), _ptr(albedo), _ptr(rough), _ptr(metal), M, C.byref(d),
+                               _ptr(env), He, We, None if dirs_local is None else _f32(dirs_local, (S, 3)),
+                               C.byref(sp), _ptr(out), _ptr(idx), _ptr(w), _ptr(ws), ws.numel(), _stream()))
+    if return_idx:
+        return out, idx, w
+    return out

@@ -237,3 +237,21 @@ def test_shade_linear_in_env_and_probe_radiance(orc):
     d, _, _ = orc.query_shade(c["x"], c["n"], maps_rgb=maps["rgb"], env=np.zeros_like(c["env"]), **base)
     assert np.allclose(a, b + d, rtol=1e-12, atol=1e-14)
     assert np.all(a >= 0)
+
+
+def test_fp32_sensitivity_allowance(orc):
+    """The FP32 allowance is linear in the angular error and much larger for
+    a rough environment than for a smooth one."""
+    c = I.make_tiny()
+    rng = np.random.default_rng(7)
+    maps = I.synthetic_maps(rng, 64, 8)
+    args = (c["x"][:256], c["n"][:256], c["wo"][:256], c["albedo"][:256], c["rough"][:256], c["metal"][:256],
+            c["probe_pos"], maps["rgb"], maps["occ"])
+    k1 = orc.query_shade_sensitivity(*args, c["env"], 4, 64, eps=1e-6)
+    k2 = orc.query_shade_sensitivity(*args, c["env"], 4, 64, eps=2e-6)
+    assert np.allclose(k2, 2 * k1, rtol=0.02, atol=1e-15)
+    rough = I.env_lognormal(rng, 16, 32)
+    kr = orc.query_shade_sensitivity(*args, rough, 4, 64, eps=1e-6)
+    out, _, _ = orc.query_shade(*args[:6], c["probe_pos"], maps["rgb"], maps["occ"], rough, 4, 64)
+    assert np.median(kr / np.abs(out)) > 3 * np.median(k1 / np.abs(orc.query_shade(
+        *args[:6], c["probe_pos"], maps["rgb"], maps["occ"], c["env"], 4, 64)[0]))
