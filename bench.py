@@ -163,7 +163,7 @@ def main():
     env = cu(W["env"])
     atlas = sop.make_atlas(ppos, R)
     out = torch.empty((M, 3), dtype=torch.float32, device=dev)
-    qws = torch.empty(sop.query_workspace_bytes(P, M, K, S, env.shape[0], env.shape[1], mode), dtype=torch.uint8,
+    qws = torch.empty(sop.query_workspace_bytes(atlas, M, K, S, env.shape[0], env.shape[1], mode), dtype=torch.uint8,
                       device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     pargs = [pts[k] for k in ("x", "n", "wo", "albedo", "rough", "metal")]

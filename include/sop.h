@@ -174,8 +174,11 @@ size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R);
 sop_status sop_bake(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
                     size_t ws_bytes, void* stream);
 
-/* Workspace bytes for sop_query_shade / sop_query_shade_backward. */
-size_t sop_query_workspace_bytes(int32_t P, int64_t M, const sop_shade_params* params, int32_t He, int32_t We);
+/* Workspace bytes for sop_query_shade / sop_query_shade_backward on M
+ * points with this atlas (its P, R and rgbo_dtype) and a He x We
+ * environment; 0 for invalid arguments. */
+size_t sop_query_workspace_bytes(const sop_atlas* atlas, int64_t M, const sop_shade_params* params, int32_t He,
+                                 int32_t We);
 
 /* Probe query and shading of M points (Sec. 3.1.2 Eq. 2-6; Sec. 3.2.2 Eq. 7-9).
  * Inputs [M,3]: x (position), n (normal, normalised inside), wo (unit view

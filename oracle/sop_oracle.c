@@ -611,6 +611,303 @@ void orc_query_shade_sensitivity(int64_t M, const float* x, const float* n, cons
     free(idx);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the SHADE output (Sec. 3.1.2: environment, materials and SOP   */
+/* textures are the learnable quantities of the decomposition; Eq. 3-6).     */
+/* ------------------------------------------------------------------------ */
+
+/* d uv / d w of orc_oct_encode (uv = (p + 1)/2), 2x3 row-major. */
+static void oct_encode_jac(const double* w, double* J)
+{
+    double ax = fabs(w[0]), ay = fabs(w[1]), az = fabs(w[2]);
+    double l1 = ax + ay + az;
+    double sx = sgn_nz(w[0]), sy = sgn_nz(w[1]), sz = w[2] >= 0.0 ? 1.0 : -1.0;
+    double px = w[0] / l1, py = w[1] / l1;
+    /* dp/dw for p = w.xy / |w|_1 */
+    double dpx[3] = {(l1 - ax) / (l1 * l1), -w[0] * sy / (l1 * l1), -w[0] * sz / (l1 * l1)};
+    double dpy[3] = {-w[1] * sx / (l1 * l1), (l1 - ay) / (l1 * l1), -w[1] * sz / (l1 * l1)};
+    if (w[2] < 0.0) {
+        /* q = ((1 - |py|) sgn px, (1 - |px|) sgn py) */
+        double spx = sgn_nz(px), spy = sgn_nz(py);
+        for (int c = 0; c < 3; ++c) {
+            double qx = -spy * dpy[c] * spx, qy = -spx * dpx[c] * spy;
+            J[c] = 0.5 * qx;
+            J[3 + c] = 0.5 * qy;
+        }
+    } else {
+        for (int c = 0; c < 3; ++c) {
+            J[c] = 0.5 * dpx[c];
+            J[3 + c] = 0.5 * dpy[c];
+        }
+    }
+}
+
+/* Bilinear read of a compact [R][R][C] map with its uv-gradient and the
+ * four (source texel, weight) pairs the read used. */
+static void bilerp_grad(const double* map, int R, int C, const double* uv, double* out, double* duv, int* texel,
+                        double* wt)
+{
+    double s = uv[0] * R - 0.5, t = uv[1] * R - 0.5;
+    double fi = floor(s), fj = floor(t);
+    double fu = s - fi, fv = t - fj;
+    int i0 = (int)fi, j0 = (int)fj;
+    const double* tx[4];
+    for (int q = 0; q < 4; ++q) {
+        int di = q & 1, dj = q >> 1, si, sj;
+        orc_oct_wrap(R, i0 + di, j0 + dj, &si, &sj);
+        texel[q] = sj * R + si;
+        tx[q] = map + (size_t)texel[q] * C;
+        wt[q] = (di ? fu : 1.0 - fu) * (dj ? fv : 1.0 - fv);
+    }
+    for (int c = 0; c < C; ++c) {
+        out[c] = wt[0] * tx[0][c] + wt[1] * tx[1][c] + wt[2] * tx[2][c] + wt[3] * tx[3][c];
+        duv[2 * c] = R * ((1.0 - fv) * (tx[1][c] - tx[0][c]) + fv * (tx[3][c] - tx[2][c]));
+        duv[2 * c + 1] = R * ((1.0 - fu) * (tx[2][c] - tx[0][c]) + fu * (tx[3][c] - tx[1][c]));
+    }
+}
+
+/* Environment read with dL/dw (3x3, row = channel) and the four
+ * (texel, weight) pairs. */
+static void env_grad(const float* env, int32_t He, int32_t We, const double* w, double* L, double* dL, int* texel,
+                     double* wt)
+{
+    double rho2 = w[0] * w[0] + w[1] * w[1], rho = sqrt(rho2);
+    double theta = atan2(rho, w[2]), phi = atan2(w[1], w[0]);
+    double u = (phi + M_PI) / (2.0 * M_PI), v = theta / M_PI;
+    double s = u * We - 0.5, t = v * He - 0.5;
+    double fs = floor(s), ft = floor(t);
+    double a = s - fs, b = t - ft;
+    int c0 = (int)fs, r0 = (int)ft;
+    const float* e[4];
+    for (int q = 0; q < 4; ++q) {
+        int dc = q & 1, dr = q >> 1;
+        int r = r0 + dr, c = c0 + dc;
+        r = r < 0 ? 0 : (r > He - 1 ? He - 1 : r);
+        c = ((c % We) + We) % We;
+        texel[q] = r * We + c;
+        e[q] = env + (size_t)texel[q] * 3;
+        wt[q] = (dc ? a : 1.0 - a) * (dr ? b : 1.0 - b);
+    }
+    /* ds/dw and dt/dw */
+    double ds[3] = {0, 0, 0}, dt[3] = {0, 0, 0};
+    if (rho2 > 0.0) {
+        double k = We / (2.0 * M_PI);
+        ds[0] = -k * w[1] / rho2;
+        ds[1] = k * w[0] / rho2;
+        double r2 = rho2 + w[2] * w[2], kt = He / M_PI;
+        /* dtheta/dx = z x / (rho r2), dtheta/dy = z y / (rho r2), dtheta/dz = -rho / r2 */
+        dt[0] = kt * w[2] * w[0] / (rho * r2);
+        dt[1] = kt * w[2] * w[1] / (rho * r2);
+        dt[2] = -kt * rho / r2;
+    }
+    for (int c = 0; c < 3; ++c) {
+        L[c] = wt[0] * e[0][c] + wt[1] * e[1][c] + wt[2] * e[2][c] + wt[3] * e[3][c];
+        double dLs = (1.0 - b) * (e[1][c] - e[0][c]) + b * (e[3][c] - e[2][c]);
+        double dLt = (1.0 - a) * (e[2][c] - e[0][c]) + a * (e[3][c] - e[1][c]);
+        for (int j = 0; j < 3; ++j) dL[3 * c + j] = dLs * ds[j] + dLt * dt[j];
+    }
+}
+
+/* Gradients of L = sum_m grad_out[m] . C[m] (SHADE mode) with respect to
+ * albedo [M,3], roughness [M], metallic [M], the raw normal [M,3] (these
+ * four overwrite), the environment texels [He,We,3] and the compact probe
+ * maps [P,R,R,3] radiance and [P,R,R] occlusion (these three accumulate).
+ * The chain follows the forward pass term by term; NdotL is l_z, which does
+ * not move with the normal. */
+void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float* wo, const float* albedo,
+                          const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
+                          const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We, const float* env,
+                          int32_t S, const double* dirs, int32_t K, double spec, uint64_t snap_key,
+                          const double* grad_out, double* g_albedo, double* g_rough, double* g_metal,
+                          double* g_normal, double* g_env, double* g_maps_rgb, double* g_maps_occ)
+{
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1) * K);
+    double* W = (double*)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1) * K);
+    uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(M > 0 ? M : 1) * K);
+    double *dl, *mrgb, *mocc;
+    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, K, snap_key, idx, W, &dl, &mrgb, &mocc);
+    orc_knn(M, x, P, probe_pos, K, idx, key);
+    size_t RR = (size_t)R * R;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < M; ++m) {
+        double nn[3], vo[3], a[3], t[3], b[3];
+        point_frame(n, wo, albedo, m, nn, vo, a, t, b);
+        const int32_t* id = idx + (size_t)m * K;
+        const double* Wk = W + (size_t)m * K;
+        double r = rough[m], mt = metal[m];
+        double al = r * r, a2 = al * al, kk = (r + 1.0) * (r + 1.0) / 8.0;
+        double NdotVraw = nn[0] * vo[0] + nn[1] * vo[1] + nn[2] * vo[2];
+        int vclamp = NdotVraw < 1e-4;
+        double NdotV = vclamp ? 1e-4 : NdotVraw;
+        double G1V = NdotV / (NdotV * (1.0 - kk) + kk);
+        double F0[3];
+        for (int c = 0; c < 3; ++c) F0[c] = 0.08 * spec * (1.0 - mt) + a[c] * mt;
+        double ga[3] = {0, 0, 0}, gr = 0, gm = 0, gn[3] = {0, 0, 0}, gW[32];
+        for (int k = 0; k < K; ++k) gW[k] = 0.0;
+        const double sc = 2.0 * M_PI / S;
+        for (int32_t i = 0; i < S; ++i) {
+            const double* l = dl + 3 * i;
+            double w[3];
+            for (int c = 0; c < 3; ++c) w[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
+            double NdotL = l[2];
+            /* probe terms */
+            double uv[2];
+            orc_oct_encode(w, uv);
+            double O = 0, Lin[3] = {0, 0, 0}, dO_duv[2] = {0, 0}, dLin_duv[6] = {0, 0, 0, 0, 0, 0};
+            double ok[32], lk[32][3], dok[32][2], dlk[32][6], wto[32][4];
+            int txo[32][4];
+            for (int k = 0; k < K; ++k) {
+                double wt[4];
+                int tx[4];
+                bilerp_grad(mocc + RR * id[k], R, 1, uv, &ok[k], dok[k], tx, wt);
+                bilerp_grad(mrgb + 3 * RR * id[k], R, 3, uv, lk[k], dlk[k], txo[k], wto[k]);
+                O += Wk[k] * ok[k];
+                for (int c = 0; c < 3; ++c) Lin[c] += Wk[k] * lk[k][c];
+                for (int j = 0; j < 2; ++j) dO_duv[j] += Wk[k] * dok[k][j];
+                for (int c = 0; c < 6; ++c) dLin_duv[c] += Wk[k] * dlk[k][c];
+            }
+            double Ld[3], dLd[9], ewt[4];
+            int etx[4];
+            env_grad(env, He, We, w, Ld, dLd, etx, ewt);
+            /* BRDF pieces */
+            double hv[3] = {w[0] + vo[0], w[1] + vo[1], w[2] + vo[2]};
+            double hl = sqrt(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
+            double h[3];
+            for (int c = 0; c < 3; ++c) h[c] = hl < 1e-30 ? nn[c] : hv[c] / hl;
+            double NdotH = nn[0] * h[0] + nn[1] * h[1] + nn[2] * h[2];
+            double VdotH = vo[0] * h[0] + vo[1] * h[1] + vo[2] * h[2];
+            double cx = nn[1] * h[2] - nn[2] * h[1], cy = nn[2] * h[0] - nn[0] * h[2], cz = nn[0] * h[1] - nn[1] * h[0];
+            double sin2 = cx * cx + cy * cy + cz * cz;
+            double den = NdotH * NdotH * a2 + sin2;
+            double D = a2 / (M_PI * den * den);
+            double gl = NdotL * (1.0 - kk) + kk;
+            double G1L = NdotL / gl;
+            double spec_t = D * G1L * G1V / (4.0 * NdotL * NdotV);
+            double x1 = 1.0 - VdotH, fc = pow(x1, 5.0);
+            double f[3], F[3], Lmix[3], gam[3];
+            for (int c = 0; c < 3; ++c) {
+                F[c] = F0[c] + (1.0 - F0[c]) * fc;
+                f[c] = (1.0 - mt) * a[c] / M_PI + spec_t * F[c];
+                Lmix[c] = (1.0 - O) * Ld[c] + Lin[c];
+                gam[c] = sc * grad_out[3 * m + c] * NdotL;
+            }
+            /* materials */
+            double dD_da2 = (den - 2.0 * a2 * NdotH * NdotH) / (M_PI * den * den * den);
+            double dG1L_dk = -NdotL * (1.0 - NdotL) / (gl * gl);
+            double gvv = NdotV * (1.0 - kk) + kk;
+            double dG1V_dk = -NdotV * (1.0 - NdotV) / (gvv * gvv);
+            double dspec_dr = (dD_da2 * 4.0 * r * r * r * G1L * G1V +
+                               D * (dG1L_dk * G1V + G1L * dG1V_dk) * (r + 1.0) / 4.0) /
+                              (4.0 * NdotL * NdotV);
+            double GN = 0, GS = 0, GVH = 0, GNV = 0; /* dL/d(NdotH), d(sin2), d(VdotH), d(NdotV) */
+            double gOt = 0, gLin[3], gLd[3];
+            for (int c = 0; c < 3; ++c) {
+                double u = gam[c] * Lmix[c];
+                ga[c] += u * ((1.0 - mt) / M_PI + spec_t * (1.0 - fc) * mt);
+                gm += u * (-a[c] / M_PI + spec_t * (1.0 - fc) * (-0.08 * spec + a[c]));
+                gr += u * dspec_dr * F[c];
+                double fsp = F[c] * G1L * G1V / (4.0 * NdotL * NdotV);
+                GN += u * fsp * (-4.0 * a2 * a2 * NdotH / (M_PI * den * den * den));
+                GS += u * fsp * (-2.0 * a2 / (M_PI * den * den * den));
+                GVH += u * spec_t * (1.0 - F0[c]) * (-5.0 * x1 * x1 * x1 * x1);
+                if (!vclamp) {
+                    double gv = NdotV * (1.0 - kk) + kk;
+                    GNV += u * F[c] * D * G1L / (4.0 * NdotL) * (-(1.0 - kk) / (gv * gv));
+                }
+                gOt += -gam[c] * f[c] * Ld[c];
+                gLin[c] = gam[c] * f[c];
+                gLd[c] = gam[c] * f[c] * (1.0 - O);
+            }
+            /* texel scatter and weight gradients */
+            for (int k = 0; k < K; ++k) {
+                gW[k] += gOt * ok[k] + gLin[0] * lk[k][0] + gLin[1] * lk[k][1] + gLin[2] * lk[k][2];
+                for (int q = 0; q < 4; ++q) {
+                    size_t tix = RR * id[k] + txo[k][q];
+                    double wq = Wk[k] * wto[k][q];
+#pragma omp atomic
+                    g_maps_occ[tix] += gOt * wq;
+                    for (int c = 0; c < 3; ++c) {
+#pragma omp atomic
+                        g_maps_rgb[3 * tix + c] += gLin[c] * wq;
+                    }
+                }
+            }
+            for (int q = 0; q < 4; ++q)
+                for (int c = 0; c < 3; ++c) {
+#pragma omp atomic
+                    g_env[3 * (size_t)etx[q] + c] += gLd[c] * ewt[q];
+                }
+            /* d/dw */
+            double gw[3] = {0, 0, 0}, guv[2];
+            guv[0] = gOt * dO_duv[0] + gLin[0] * dLin_duv[0] + gLin[1] * dLin_duv[2] + gLin[2] * dLin_duv[4];
+            guv[1] = gOt * dO_duv[1] + gLin[0] * dLin_duv[1] + gLin[1] * dLin_duv[3] + gLin[2] * dLin_duv[5];
+            double J[6];
+            oct_encode_jac(w, J);
+            for (int j = 0; j < 3; ++j) gw[j] += guv[0] * J[j] + guv[1] * J[3 + j];
+            for (int c = 0; c < 3; ++c)
+                for (int j = 0; j < 3; ++j) gw[j] += gLd[c] * dLd[3 * c + j];
+            /* BRDF geometry: through h (and directly through n) */
+            double gh[3], gnd[3];
+            for (int j = 0; j < 3; ++j) {
+                gh[j] = GN * nn[j] + GS * 2.0 * (h[j] - NdotH * nn[j]) + GVH * vo[j];
+                gnd[j] = GN * h[j] + GS * 2.0 * (nn[j] - NdotH * h[j]) + GNV * vo[j];
+            }
+            if (hl >= 1e-30) {
+                double hg = h[0] * gh[0] + h[1] * gh[1] + h[2] * gh[2];
+                for (int j = 0; j < 3; ++j) gw[j] += (gh[j] - hg * h[j]) / hl;
+            }
+            /* w = l.x t(n) + l.y b(n) + l.z n */
+            double sg = nn[2] >= 0.0 ? 1.0 : -1.0, aa = -1.0 / (sg + nn[2]), a2n = aa * aa;
+            double dt[3][3] = {{2.0 * sg * nn[0] * aa, 0.0, sg * nn[0] * nn[0] * a2n},
+                               {sg * nn[1] * aa, sg * nn[0] * aa, sg * nn[0] * nn[1] * a2n},
+                               {-sg, 0.0, 0.0}};
+            double db[3][3] = {{nn[1] * aa, nn[0] * aa, nn[0] * nn[1] * a2n},
+                               {0.0, 2.0 * nn[1] * aa, nn[1] * nn[1] * a2n},
+                               {0.0, -1.0, 0.0}};
+            for (int j = 0; j < 3; ++j) {
+                double v = l[2] * gw[j] + gnd[j];
+                for (int c = 0; c < 3; ++c) v += l[0] * gw[c] * dt[c][j] + l[1] * gw[c] * db[c][j];
+                gn[j] += v;
+            }
+        }
+        /* blend weights W_k = w_s w_b / sum (Eq. 4-6): w_b moves with n */
+        if (key[(size_t)m * K] > snap_key) {
+            double u[32], U = 0, ws[32], dh[32][3];
+            for (int k = 0; k < K; ++k) {
+                const float* p = probe_pos + 3 * (size_t)id[k];
+                double d[3] = {(double)p[0] - x[3 * m], (double)p[1] - x[3 * m + 1], (double)p[2] - x[3 * m + 2]};
+                double dlen = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                ws[k] = 1.0 / dlen;
+                for (int j = 0; j < 3; ++j) dh[k][j] = d[j] / dlen;
+                u[k] = ws[k] * (0.5 * (1.0 + dh[k][0] * nn[0] + dh[k][1] * nn[1] + dh[k][2] * nn[2]) + 0.01);
+                U += u[k];
+            }
+            double gu_dot = 0;
+            for (int k = 0; k < K; ++k) gu_dot += gW[k] * Wk[k];
+            for (int j = 0; j < K; ++j) {
+                double gu = (gW[j] - gu_dot) / U; /* dL/du_j */
+                for (int c = 0; c < 3; ++c) gn[c] += gu * ws[j] * 0.5 * dh[j][c];
+            }
+        }
+        /* through the normalisation n = n_raw / |n_raw| */
+        double nr[3] = {n[3 * m], n[3 * m + 1], n[3 * m + 2]};
+        double nl = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+        double ng = gn[0] * nn[0] + gn[1] * nn[1] + gn[2] * nn[2];
+        for (int c = 0; c < 3; ++c) {
+            g_normal[3 * m + c] = (gn[c] - ng * nn[c]) / nl;
+            g_albedo[3 * m + c] = ga[c];
+        }
+        g_rough[m] = gr;
+        g_metal[m] = gm;
+    }
+    free(mocc);
+    free(mrgb);
+    free(dl);
+    free(key);
+    free(W);
+    free(idx);
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

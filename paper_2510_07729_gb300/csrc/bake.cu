@@ -29,7 +29,8 @@ namespace sop {
 // Gaussian record: 5 float4 = 80 B.
 //   r0 = (mu.xyz, rho)   rho < 0: never reaches alpha_min
 //   r1..r3 = M = diag(1/s) R^T row-major (9) then opacity
-//   r3.zw, r4.x = rgb
+//   r3.zw, r4.x = rgb; r4.yzw = half extents of the alpha_min ellipsoid's
+//   axis-aligned box (used to bin the Gaussian into grid cells)
 struct GRec {
     float4 r0, r1, r2, r3, r4;
 };
@@ -39,8 +40,8 @@ constexpr float kMarginRel = 1e-4f;
 BakeLayout bake_layout(int64_t N, int32_t P, int32_t R, int64_t entries_cap)
 {
     BakeLayout L{};
-    L.cells_cap = N < 4096 ? 4096 : (N > (1 << 23) ? (1 << 23) : N);
-    L.entries_cap = entries_cap > 0 ? entries_cap : 48 * N + 65536;
+    L.cells_cap = N / 2 < 4096 ? 4096 : (N / 2 > (1 << 23) ? (1 << 23) : N / 2);
+    L.entries_cap = entries_cap > 0 ? entries_cap : 24 * N + 65536;
     size_t o = 0;
     L.hdr = o;        o = align256(o + sizeof(GaussGrid));
     L.bbox = o;       o = align256(o + 8 * sizeof(int32_t));
@@ -68,6 +69,7 @@ __global__ void bbox_init_kernel(int32_t* bbox)
 {
     if (threadIdx.x < 3) bbox[threadIdx.x] = f2o(FLT_MAX);
     else if (threadIdx.x < 6) bbox[threadIdx.x] = f2o(-FLT_MAX);
+    else if (threadIdx.x < 8) bbox[threadIdx.x] = 0;  // [6]: trace status word
 }
 
 // Per-Gaussian record + bounding box of the (margin-expanded) spheres.
@@ -87,11 +89,20 @@ __global__ void gauss_prep_kernel(sop_gaussians g, float alpha_min, GRec* __rest
         const float ix = 1.f / sx, iy = 1.f / sy, iz = 1.f / sz;
         const float o = g.opacity[i];
         const float3 mu = load3(g.mean, i);
-        float rho = -1.f;
+        float rho = -1.f, ex = 0.f, ey = 0.f, ez = 0.f;
         if (o >= alpha_min && o > 0.f) {
+            // {x : o exp(-m^2(x)/2) >= alpha_min} is the ellipsoid m^2 <= kk^2
+            const float kk = sqrtf(2.f * fmaxf(logf(o / alpha_min), 0.f));
             const float smax = fmaxf(sx, fmaxf(sy, sz));
-            rho = smax * sqrtf(2.f * fmaxf(logf(o / alpha_min), 0.f));
-            rho = rho * (1.f + kMarginRel) + 1e-7f;
+            rho = smax * kk * (1.f + kMarginRel) + 1e-7f;
+            // axis-aligned half extents: kk sqrt(Sigma_aa), Sigma = R diag(s^2) R^T
+            const float sx2 = sx * sx, sy2 = sy * sy, sz2 = sz * sz;
+            ex = kk * sqrtf(R00 * R00 * sx2 + R01 * R01 * sy2 + R02 * R02 * sz2) * (1.f + kMarginRel) + 1e-7f;
+            ey = kk * sqrtf(R10 * R10 * sx2 + R11 * R11 * sy2 + R12 * R12 * sz2) * (1.f + kMarginRel) + 1e-7f;
+            ez = kk * sqrtf(R20 * R20 * sx2 + R21 * R21 * sy2 + R22 * R22 * sz2) * (1.f + kMarginRel) + 1e-7f;
+            ex = fminf(ex, rho);
+            ey = fminf(ey, rho);
+            ez = fminf(ez, rho);
         }
         GRec r;
         r.r0 = make_float4(mu.x, mu.y, mu.z, rho);
@@ -99,11 +110,11 @@ __global__ void gauss_prep_kernel(sop_gaussians g, float alpha_min, GRec* __rest
         r.r1 = make_float4(R00 * ix, R10 * ix, R20 * ix, R01 * iy);
         r.r2 = make_float4(R11 * iy, R21 * iy, R02 * iz, R12 * iz);
         r.r3 = make_float4(R22 * iz, o, g.rgb[3 * i], g.rgb[3 * i + 1]);
-        r.r4 = make_float4(g.rgb[3 * i + 2], 0.f, 0.f, 0.f);
+        r.r4 = make_float4(g.rgb[3 * i + 2], ex, ey, ez);
         rec[i] = r;
         if (rho >= 0.f) {
-            lo[0] = mu.x - rho; lo[1] = mu.y - rho; lo[2] = mu.z - rho;
-            hi[0] = mu.x + rho; hi[1] = mu.y + rho; hi[2] = mu.z + rho;
+            lo[0] = mu.x - ex; lo[1] = mu.y - ey; lo[2] = mu.z - ez;
+            hi[0] = mu.x + ex; hi[1] = mu.y + ey; hi[2] = mu.z + ez;
         }
     }
     // warp reduce then one atomic per warp
@@ -180,13 +191,15 @@ __global__ void grid_setup_kernel(const int32_t* bbox, int64_t cells_cap, GaussG
     for (int c = threadIdx.x; c < G.ncells; c += blockDim.x) cell_cnt[c] = 0;
 }
 
-__device__ __forceinline__ void cell_range(const GaussGrid& G, float3 mu, float rho, int lo[3], int hi[3])
+// Cells overlapped by the Gaussian's axis-aligned box (plus a margin that
+// covers the rounding of the grid walk's cell boundaries).
+__device__ __forceinline__ void cell_range(const GaussGrid& G, float3 mu, float4 r4, int lo[3], int hi[3])
 {
-    const float m = rho + kMarginRel * G.h;
-    const float c[3] = {mu.x, mu.y, mu.z};
+    const float mg = kMarginRel * G.h;
+    const float c[3] = {mu.x, mu.y, mu.z}, e[3] = {r4.y + mg, r4.z + mg, r4.w + mg};
     for (int a = 0; a < 3; ++a) {
-        lo[a] = min(max((int)floorf((c[a] - m - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
-        hi[a] = min(max((int)floorf((c[a] + m - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
+        lo[a] = min(max((int)floorf((c[a] - e[a] - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
+        hi[a] = min(max((int)floorf((c[a] + e[a] - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
     }
 }
 
@@ -199,7 +212,7 @@ __global__ void bin_count_kernel(int64_t N, const GRec* __restrict__ rec, const 
     if (r0.w < 0.f) return;
     const GaussGrid G = *gridp;
     int lo[3], hi[3];
-    cell_range(G, f3(r0.x, r0.y, r0.z), r0.w, lo, hi);
+    cell_range(G, f3(r0.x, r0.y, r0.z), rec[i].r4, lo, hi);
     for (int z = lo[2]; z <= hi[2]; ++z)
         for (int y = lo[1]; y <= hi[1]; ++y)
             for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&cell_cnt[(z * G.dims[1] + y) * G.dims[0] + x], 1);
@@ -248,7 +261,7 @@ __global__ void bin_fill_kernel(int64_t N, const GRec* __restrict__ rec, const G
     if (r0.w < 0.f) return;
     const GaussGrid G = *gridp;
     int lo[3], hi[3];
-    cell_range(G, f3(r0.x, r0.y, r0.z), r0.w, lo, hi);
+    cell_range(G, f3(r0.x, r0.y, r0.z), rec[i].r4, lo, hi);
     for (int z = lo[2]; z <= hi[2]; ++z)
         for (int y = lo[1]; y <= hi[1]; ++y)
             for (int x = lo[0]; x <= hi[0]; ++x) {
@@ -278,8 +291,6 @@ __device__ __forceinline__ void two_diff(float a, float b, float& hi, float& lo)
     lo = (a - av) + (bv - b);
 }
 
-constexpr int kHitBuf = 32;
-
 struct TraceK {
     const GRec* rec;
     const GaussGrid* grid;
@@ -292,15 +303,34 @@ struct TraceK {
     float t_near, alpha_min, alpha_max, t_stop;
     float4* maps;   // [P][R][R] (L.rgb, O)
     float* depth;   // [P][R][R]
+    int32_t* status;  // device status word: bit 0 = a cell window could not be split
 };
 
-// One thread per texel ray.
+constexpr int kWarpsPerCta = 8;
+constexpr int kHitCap = 256;  // per-warp hit buffer (shared memory)
+
+// order-preserving 64-bit key of (t*, Gaussian index)
+__device__ __forceinline__ uint64_t hit_key(float t, int32_t g)
+{
+    const uint32_t o = (uint32_t)f2o(t) ^ 0x80000000u;
+    return ((uint64_t)o << 32) | (uint32_t)g;
+}
+
+// One warp per texel ray. Lanes share the grid walk (uniform control flow),
+// split each cell's entries, append hits to the warp's shared buffer, sort
+// them by (t*, index) with a bitonic network and composite 32 at a time with
+// a prefix product of (1 - alpha).
 __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
 {
+    __shared__ uint64_t s_key[kWarpsPerCta][kHitCap];
+    __shared__ float s_alpha[kWarpsPerCta][kHitCap];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t* key = s_key[wib];
+    float* alp = s_alpha[wib];
     const int RR = k.R * k.R;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)k.P * RR) return;
-    const int p = (int)(gid / RR), t = (int)(gid % RR);
+    const int64_t ray = (int64_t)blockIdx.x * kWarpsPerCta + wib;
+    if (ray >= (int64_t)k.P * RR) return;  // whole warp leaves together
+    const int p = (int)(ray / RR), t = (int)(ray % RR);
     const GaussGrid G = *k.grid;
     const float4 d4 = __ldg(k.dirs + t);
     const float3 d = f3(d4.x, d4.y, d4.z);
@@ -309,7 +339,6 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
     float T = 1.f, L0 = 0.f, L1 = 0.f, L2 = 0.f, Dacc = 0.f, Wacc = 0.f;
     bool done = false;
 
-    // slab entry/exit of the grid box
     const float ov[3] = {o.x, o.y, o.z}, dv[3] = {d.x, d.y, d.z};
     float t0 = 0.f, t1 = FLT_MAX;
     for (int a = 0; a < 3; ++a) {
@@ -323,26 +352,19 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
             t1 = -1.f;
         }
     }
+    // exact (hi + lo) split of the probe position relative to nothing: the
+    // per-Gaussian offsets are split in the hit test below
     if (G.n_entries > 0 && t0 <= t1) {
         int cell[3], step[3];
         float tmax[3];
         for (int a = 0; a < 3; ++a) {
             const float pa = ov[a] + t0 * dv[a];
             cell[a] = min(max((int)floorf((pa - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
-            if (dv[a] > 0.f) {
-                step[a] = 1;
-                tmax[a] = (G.origin[a] + (cell[a] + 1) * G.h - ov[a]) / dv[a];
-            } else if (dv[a] < 0.f) {
-                step[a] = -1;
-                tmax[a] = (G.origin[a] + cell[a] * G.h - ov[a]) / dv[a];
-            } else {
-                step[a] = 0;
-                tmax[a] = FLT_MAX;
-            }
+            step[a] = dv[a] > 0.f ? 1 : (dv[a] < 0.f ? -1 : 0);
+            tmax[a] = step[a] == 0 ? FLT_MAX
+                                   : (G.origin[a] + (cell[a] + (step[a] > 0 ? 1 : 0)) * G.h - ov[a]) / dv[a];
         }
         float t_enter = t0;
-        float bt[kHitBuf], ba[kHitBuf];
-        int32_t bg[kHitBuf];
         while (!done) {
             int ax = 0;
             if (tmax[1] < tmax[ax]) ax = 1;
@@ -351,81 +373,181 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
             if (t_exit < t_enter) t_exit = t_enter;
             const int c = (cell[2] * G.dims[1] + cell[1]) * G.dims[0] + cell[0];
             const int e0 = __ldg(k.cell_start + c), e1 = __ldg(k.cell_start + c + 1);
-            float cur_t = -FLT_MAX;
-            int32_t cur_g = -1;
-            // window loop: composite the cell's hits in (t*, index) order,
-            // kHitBuf at a time
-            for (;;) {
-                int nb = 0;
-                bool overflow = false;
-                for (int e = e0; e < e1; ++e) {
-                    const float4 r0 = __ldg(k.ent_sph + e);
-                    const float3 mu = f3(r0.x, r0.y, r0.z);
-                    const float3 del = mu - o;
-                    const float tc = dot3(del, d);
-                    if (tc + r0.w < t_enter || tc - r0.w > t_exit) continue;
-                    const float3 cx = cross3(del, d);
-                    if (dot3(cx, cx) > r0.w * r0.w) continue;
-                    const int32_t gi = __ldg(k.entries + e);
-                    // exact response
-                    const float4 r1 = __ldg(&k.rec[gi].r1), r2 = __ldg(&k.rec[gi].r2), r3 = __ldg(&k.rec[gi].r3);
-                    float hx, lx, hy, ly, hz, lz;
-                    two_diff(o.x, mu.x, hx, lx);
-                    two_diff(o.y, mu.y, hy, ly);
-                    two_diff(o.z, mu.z, hz, lz);
-                    const float u0 = fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz));
-                    const float u1 = fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz));
-                    const float u2 = fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz));
-                    const float w0 = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
-                    const float w1 = fmaf(r1.w, d.x, fmaf(r2.x, d.y, r2.y * d.z));
-                    const float w2 = fmaf(r2.z, d.x, fmaf(r2.w, d.y, r3.x * d.z));
-                    const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-                    const float B = fmaf(w0, u0, fmaf(w1, u1, w2 * u2));
-                    const float ts = -B / A;
-                    if (!(ts > k.t_near) || ts < t_enter || ts >= t_exit) continue;
-                    const float ex = fmaf(ts, d.x, hx) + lx, ey = fmaf(ts, d.y, hy) + ly, ez = fmaf(ts, d.z, hz) + lz;
-                    const float v0 = fmaf(r1.x, ex, fmaf(r1.y, ey, r1.z * ez));
-                    const float v1 = fmaf(r1.w, ex, fmaf(r2.x, ey, r2.y * ez));
-                    const float v2 = fmaf(r2.z, ex, fmaf(r2.w, ey, r3.x * ez));
-                    const float m2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-                    const float resp = r3.y * expf(-0.5f * m2);
-                    if (!(resp >= k.alpha_min)) continue;
-                    if (ts < cur_t || (ts == cur_t && gi <= cur_g)) continue;
-                    const float al = fminf(resp, k.alpha_max);
-                    // insertion into the sorted buffer (keep the smallest)
-                    if (nb == kHitBuf) {
-                        overflow = true;
-                        if (ts > bt[kHitBuf - 1] || (ts == bt[kHitBuf - 1] && gi > bg[kHitBuf - 1])) continue;
-                        --nb;
+            float tl = t_enter, th = t_exit;
+            int splits = 0;
+            while (e1 > e0) {
+                // ---- collect the hits with t* in [tl, th) -----------------
+                int n = 0;
+                for (int eb = e0; eb < e1; eb += 32) {
+                    const int e = eb + lane;
+                    bool hit = false;
+                    float ts = 0.f, al = 0.f;
+                    int32_t gi = 0;
+                    if (e < e1) {
+                        const float4 r0 = __ldg(k.ent_sph + e);
+                        const float3 mu = f3(r0.x, r0.y, r0.z);
+                        const float3 del = mu - o;
+                        const float tc = dot3(del, d);
+                        const float3 cx = cross3(del, d);
+                        if (tc + r0.w >= tl && tc - r0.w <= th && dot3(cx, cx) <= r0.w * r0.w) {
+                            gi = __ldg(k.entries + e);
+                            const float4 r1 = __ldg(&k.rec[gi].r1), r2 = __ldg(&k.rec[gi].r2),
+                                         r3 = __ldg(&k.rec[gi].r3);
+                            float hx, lx, hy, ly, hz, lz;
+                            two_diff(o.x, mu.x, hx, lx);
+                            two_diff(o.y, mu.y, hy, ly);
+                            two_diff(o.z, mu.z, hz, lz);
+                            const float u0 = fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz));
+                            const float u1 = fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz));
+                            const float u2 = fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz));
+                            const float w0 = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
+                            const float w1 = fmaf(r1.w, d.x, fmaf(r2.x, d.y, r2.y * d.z));
+                            const float w2 = fmaf(r2.z, d.x, fmaf(r2.w, d.y, r3.x * d.z));
+                            const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                            const float B = fmaf(w0, u0, fmaf(w1, u1, w2 * u2));
+                            ts = -B / A;
+                            if (ts > k.t_near && ts >= tl && ts < th) {
+                                const float ex = fmaf(ts, d.x, hx) + lx, ey = fmaf(ts, d.y, hy) + ly,
+                                            ez = fmaf(ts, d.z, hz) + lz;
+                                const float v0 = fmaf(r1.x, ex, fmaf(r1.y, ey, r1.z * ez));
+                                const float v1 = fmaf(r1.w, ex, fmaf(r2.x, ey, r2.y * ez));
+                                const float v2 = fmaf(r2.z, ex, fmaf(r2.w, ey, r3.x * ez));
+                                const float m2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                                const float resp = r3.y * expf(-0.5f * m2);
+                                if (resp >= k.alpha_min) {
+                                    hit = true;
+                                    al = fminf(resp, k.alpha_max);
+                                }
+                            }
+                        }
                     }
-                    int pos = nb++;
-                    while (pos > 0 && (bt[pos - 1] > ts || (bt[pos - 1] == ts && bg[pos - 1] > gi))) {
-                        bt[pos] = bt[pos - 1];
-                        ba[pos] = ba[pos - 1];
-                        bg[pos] = bg[pos - 1];
-                        --pos;
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (hit) {
+                        const int pos = n + __popc(m & ((1u << lane) - 1u));
+                        if (pos < kHitCap) {
+                            key[pos] = hit_key(ts, gi);
+                            alp[pos] = al;
+                        }
                     }
-                    bt[pos] = ts;
-                    ba[pos] = al;
-                    bg[pos] = gi;
+                    n += __popc(m);
                 }
-                for (int h = 0; h < nb; ++h) {
-                    const float wgt = T * ba[h];
-                    const float4 r3 = __ldg(&k.rec[bg[h]].r3), r4 = __ldg(&k.rec[bg[h]].r4);
-                    L0 = fmaf(wgt, r3.z, L0);
-                    L1 = fmaf(wgt, r3.w, L1);
-                    L2 = fmaf(wgt, r4.x, L2);
-                    Dacc = fmaf(wgt, bt[h], Dacc);
-                    Wacc += wgt;
-                    T *= (1.f - ba[h]);
-                    if (T < k.t_stop) {
-                        done = true;
+                if (n > kHitCap) {
+                    // too many hits in this window: halve it and rescan
+                    if (++splits > 40 || !(th > tl)) {
+                        if (lane == 0) atomicOr(k.status, 1);
                         break;
                     }
+                    th = tl + 0.5f * (th - tl);
+                    continue;
                 }
-                if (done || !overflow) break;
-                cur_t = bt[nb - 1];
-                cur_g = bg[nb - 1];
+                // ---- sort the n hits by (t*, index) --------------------------
+                if (n > 32) {
+                    int P2 = 64;
+                    while (P2 < n) P2 <<= 1;
+                    for (int i = n + lane; i < P2; i += 32) {
+                        key[i] = ~0ull;
+                        alp[i] = 0.f;
+                    }
+                    __syncwarp();
+                    for (int kk = 2; kk <= P2; kk <<= 1) {
+                        for (int j = kk >> 1; j > 0; j >>= 1) {
+                            for (int i = lane; i < P2; i += 32) {
+                                const int ixj = i ^ j;
+                                if (ixj > i) {
+                                    const uint64_t a = key[i], b = key[ixj];
+                                    const bool up = (i & kk) == 0;
+                                    if ((a > b) == up) {
+                                        key[i] = b;
+                                        key[ixj] = a;
+                                        const float ta = alp[i];
+                                        alp[i] = alp[ixj];
+                                        alp[ixj] = ta;
+                                    }
+                                }
+                            }
+                            __syncwarp();
+                        }
+                    }
+                } else if (n > 1) {
+                    // one hit per lane, bitonic network over the 32 lanes
+                    __syncwarp();
+                    uint64_t kv = lane < n ? key[lane] : ~0ull;
+                    float av = lane < n ? alp[lane] : 0.f;
+#pragma unroll
+                    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+                        for (int j = kk >> 1; j > 0; j >>= 1) {
+                            const uint64_t ko = __shfl_xor_sync(0xffffffffu, kv, j);
+                            const float ao = __shfl_xor_sync(0xffffffffu, av, j);
+                            const bool lower = (lane & j) == 0;
+                            const bool up = (lane & kk) == 0;
+                            // keep the smaller key on the lower lane of an ascending pair
+                            const bool take = (lower == up) ? (ko < kv) : (ko > kv);
+                            if (take) {
+                                kv = ko;
+                                av = ao;
+                            }
+                        }
+                    }
+                    if (lane < n) {
+                        key[lane] = kv;
+                        alp[lane] = av;
+                    }
+                }
+                __syncwarp();
+                // ---- composite 32 hits at a time ------------------------------
+                for (int cb = 0; cb < n && !done; cb += 32) {
+                    const int h = cb + lane;
+                    const bool on = h < n;
+                    const uint64_t kh = on ? key[h] : 0ull;
+                    const float a = on ? alp[h] : 0.f;
+                    const int32_t gh = (int32_t)(uint32_t)(kh & 0xffffffffu);
+                    const float th_hit = o2f((int32_t)((uint32_t)(kh >> 32) ^ 0x80000000u));
+                    // inclusive prefix product of (1 - alpha)
+                    float pin = 1.f - a;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const float v = __shfl_up_sync(0xffffffffu, pin, off);
+                        if (lane >= off) pin *= v;
+                    }
+                    float pex = __shfl_up_sync(0xffffffffu, pin, 1);
+                    if (lane == 0) pex = 1.f;
+                    const float Tb = T * pex, Ta = T * pin;
+                    // first lane whose transmittance after its hit is below t_stop
+                    const unsigned stopm = __ballot_sync(0xffffffffu, on && Ta < k.t_stop);
+                    const int stop_lane = stopm ? __ffs(stopm) - 1 : 32;
+                    const bool use = on && lane <= stop_lane;
+                    const float w = use ? Tb * a : 0.f;
+                    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+                    if (use) {
+                        const float4 r3 = __ldg(&k.rec[gh].r3), r4 = __ldg(&k.rec[gh].r4);
+                        c0 = w * r3.z;
+                        c1 = w * r3.w;
+                        c2 = w * r4.x;
+                    }
+                    float wd = w * th_hit, ww = w;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        c0 += __shfl_xor_sync(0xffffffffu, c0, off);
+                        c1 += __shfl_xor_sync(0xffffffffu, c1, off);
+                        c2 += __shfl_xor_sync(0xffffffffu, c2, off);
+                        wd += __shfl_xor_sync(0xffffffffu, wd, off);
+                        ww += __shfl_xor_sync(0xffffffffu, ww, off);
+                    }
+                    L0 += c0;
+                    L1 += c1;
+                    L2 += c2;
+                    Dacc += wd;
+                    Wacc += ww;
+                    const int last = stop_lane < 32 ? stop_lane : min(31, n - cb - 1);
+                    T = __shfl_sync(0xffffffffu, Ta, last);
+                    if (stop_lane < 32) done = true;
+                }
+                __syncwarp();
+                if (done || !(th < t_exit)) break;
+                tl = th;
+                th = t_exit;
+                splits = 0;
             }
             if (done || t_exit >= t1) break;
             cell[ax] += step[ax];
@@ -435,8 +557,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
             t_enter = t_exit;
         }
     }
-    k.maps[gid] = make_float4(L0, L1, L2, 1.f - T);
-    k.depth[gid] = Wacc > 1e-8f ? Dacc / Wacc : 0.f;
+    if (lane == 0) {
+        k.maps[ray] = make_float4(L0, L1, L2, 1.f - T);
+        k.depth[ray] = Wacc > 1e-8f ? Dacc / Wacc : 0.f;
+    }
 }
 
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s)
@@ -487,8 +611,9 @@ cudaError_t launch_bake_trace(const sop_gaussians& g, const sop_atlas& atlas, co
     k.t_stop = bp.t_stop;
     k.maps = reinterpret_cast<float4*>(ws + L.maps);
     k.depth = reinterpret_cast<float*>(ws + L.depth);
+    k.status = reinterpret_cast<int32_t*>(ws + L.bbox) + 6;
     const int64_t rays = (int64_t)atlas.P * R * R;
-    trace_kernel<<<(unsigned)((rays + bs - 1) / bs), bs, 0, s>>>(k);
+    trace_kernel<<<(unsigned)((rays + kWarpsPerCta - 1) / kWarpsPerCta), kWarpsPerCta * 32, 0, s>>>(k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_atlas_pack(reinterpret_cast<const float*>(k.maps), 4, reinterpret_cast<const float*>(k.maps) + 3, 4,

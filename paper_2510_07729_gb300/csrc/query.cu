@@ -15,13 +15,15 @@
 //                       environment bilinear, BRDF, fp32 accumulation, and a
 //                       shuffle reduction over the point's lanes.
 #include <float.h>
+#include <stdlib.h>
 
 #include "sop_device.cuh"
 #include "sop_internal.h"
 
 namespace sop {
 
-QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He, int32_t We)
+QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He, int32_t We, int32_t R,
+                         int32_t rgbo_dtype)
 {
     QueryLayout L{};
     int g = 1;
@@ -34,6 +36,8 @@ QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He,
     L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
     L.entries = o;    o = align256(o + sizeof(int4) * (size_t)P);
     L.env4 = o;       o = align256(o + sizeof(float4) * (size_t)(He + 2) * (We + 1));
+    L.envq = o;       o = align256(o + 64 * (size_t)(He + 1) * We);
+    L.quads = o;      o = align256(o + (rgbo_dtype == SOP_F32 ? 64 : 32) * (size_t)P * (R + 1) * (R + 1));
     L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)S);
     L.idx = o;        o = align256(o + sizeof(int32_t) * (size_t)M * K);
     L.w = o;          o = align256(o + sizeof(float) * (size_t)M * K);
@@ -266,6 +270,44 @@ __global__ void env_pack_kernel(const float* __restrict__ env, int32_t He, int32
     env4[i] = make_float4(e[0], e[1], e[2], 0.f);
 }
 
+// Environment footprints: for base (r0, c0), r0 in [0, He], c0 in [0, We),
+// the 2x2 bilinear footprint of the padded table, RGB x 4 = 12 floats in a
+// 64-byte slot: (e00, e01, e10, e11) with e01 = column c0+1, e10 = row r0+1.
+__global__ void env_quad_kernel(const float4* __restrict__ env4, int32_t He, int32_t We, float4* __restrict__ envq)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)(He + 1) * We) return;
+    const int r0 = (int)(i / We), c0 = (int)(i % We);
+    const float4* p = env4 + (int64_t)r0 * (We + 1) + c0;
+    const float4 a = p[0], b = p[1], c = p[We + 1], d = p[We + 2];
+    float4* q = envq + 4 * i;
+    q[0] = make_float4(a.x, a.y, a.z, b.x);
+    q[1] = make_float4(b.y, b.z, c.x, c.y);
+    q[2] = make_float4(c.z, d.x, d.y, d.z);
+    q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Atlas footprints: for probe p and base (a, b) in [0, R]^2 of the stored
+// (gutter) map, the texels (a,b), (a+1,b), (a,b+1), (a+1,b+1) stored
+// contiguously, so one bilinear fetch reads one aligned 32/64-byte block.
+template <int DT>
+__global__ void atlas_quad_kernel(const typename Texel<DT>::raw* __restrict__ atlas, int32_t P, int32_t R,
+                                  typename Texel<DT>::raw* __restrict__ quads)
+{
+    const int RS = R + 2, RQ = R + 1;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)P * RQ * RQ) return;
+    const int64_t pr = i / (RQ * RQ);
+    const int r = (int)(i % (RQ * RQ));
+    const int b = r / RQ, a = r % RQ;
+    const typename Texel<DT>::raw* src = atlas + pr * RS * RS + (int64_t)b * RS + a;
+    typename Texel<DT>::raw* dst = quads + 4 * i;
+    dst[0] = src[0];
+    dst[1] = src[1];
+    dst[2] = src[RS];
+    dst[3] = src[RS + 1];
+}
+
 __device__ __forceinline__ double radical_inverse2(uint32_t i) { return (double)__brev(i) * 2.3283064365386963e-10; }
 
 // Local light directions: the caller's set, or the centred Hammersley set.
@@ -291,8 +333,19 @@ __global__ void dirs_kernel(int32_t S, const float* __restrict__ dirs_local, flo
     }
 }
 
-// Bilinear environment lookup L_dir(w) (z-up equirectangular).
-__device__ __forceinline__ float3 env_lookup(const float4* __restrict__ env4, int He, int We, float3 w)
+// 256-bit read-only global load (sm_100+); p must be 32-byte aligned.
+__device__ __forceinline__ void ldg256(const void* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d)
+{
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+        : "l"(p));
+}
+__device__ __forceinline__ float lo32f(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi32f(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
+// Bilinear environment lookup L_dir(w) (z-up equirectangular) from the
+// footprint table: three 16-byte loads of one 64-byte slot.
+__device__ __forceinline__ float3 env_lookup(const float4* __restrict__ envq, int He, int We, float3 w)
 {
     const float th = atan2f(sqrtf(w.x * w.x + w.y * w.y), w.z);
     const float ph = atan2f(w.y, w.x);
@@ -304,20 +357,76 @@ __device__ __forceinline__ float3 env_lookup(const float4* __restrict__ env4, in
     c0 = c0 < 0 ? c0 + We : c0;
     c0 = min(max(c0, 0), We - 1);
     const int r0 = min(max((int)ft + 1, 0), He);
-    const float4* p = env4 + (int64_t)r0 * (We + 1) + c0;
-    const float4 e00 = __ldg(p), e01 = __ldg(p + 1), e10 = __ldg(p + We + 1), e11 = __ldg(p + We + 2);
+    const float4* q = envq + 4 * ((int64_t)r0 * We + c0);
+    uint64_t x0, x1, x2, x3;
+    ldg256(q, x0, x1, x2, x3);
+    const float4 q0 = make_float4(lo32f(x0), hi32f(x0), lo32f(x1), hi32f(x1));
+    const float4 q1 = make_float4(lo32f(x2), hi32f(x2), lo32f(x3), hi32f(x3));
+    const float4 q2 = __ldg(q + 2);
     const float w00 = (1.f - a) * (1.f - b), w01 = a * (1.f - b), w10 = (1.f - a) * b, w11 = a * b;
-    return f3(w00 * e00.x + w01 * e01.x + w10 * e10.x + w11 * e11.x,
-              w00 * e00.y + w01 * e01.y + w10 * e10.y + w11 * e11.y,
-              w00 * e00.z + w01 * e01.z + w10 * e10.z + w11 * e11.z);
+    return f3(w00 * q0.x + w01 * q0.w + w10 * q1.z + w11 * q2.y, w00 * q0.y + w01 * q1.x + w10 * q1.w + w11 * q2.z,
+              w00 * q0.z + w01 * q1.y + w10 * q2.x + w11 * q2.w);
 }
+
+// One bilinear footprint of the atlas: four texels as float4 (RGB, O).
+template <int DT> struct Quad;
+template <> struct Quad<SOP_F32> {
+    static __device__ __forceinline__ void load(const void* base, int64_t qi, float4& t00, float4& t10, float4& t01,
+                                                float4& t11)
+    {
+        const float4* p = reinterpret_cast<const float4*>(base) + 4 * qi;
+        uint64_t a, b, c, d, e, f, g, h;
+        ldg256(p, a, b, c, d);
+        ldg256(p + 2, e, f, g, h);
+        t00 = make_float4(lo32f(a), hi32f(a), lo32f(b), hi32f(b));
+        t10 = make_float4(lo32f(c), hi32f(c), lo32f(d), hi32f(d));
+        t01 = make_float4(lo32f(e), hi32f(e), lo32f(f), hi32f(f));
+        t11 = make_float4(lo32f(g), hi32f(g), lo32f(h), hi32f(h));
+    }
+};
+__device__ __forceinline__ float4 h4(uint32_t x, uint32_t y)
+{
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 b4(uint32_t x, uint32_t y)
+{
+    return make_float4(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u), __uint_as_float(y << 16),
+                       __uint_as_float(y & 0xffff0000u));
+}
+template <> struct Quad<SOP_F16> {
+    static __device__ __forceinline__ void load(const void* base, int64_t qi, float4& t00, float4& t10, float4& t01,
+                                                float4& t11)
+    {
+        uint64_t a, b, c, d;
+        ldg256(reinterpret_cast<const uint4*>(base) + 2 * qi, a, b, c, d);
+        t00 = h4((uint32_t)a, (uint32_t)(a >> 32));
+        t10 = h4((uint32_t)b, (uint32_t)(b >> 32));
+        t01 = h4((uint32_t)c, (uint32_t)(c >> 32));
+        t11 = h4((uint32_t)d, (uint32_t)(d >> 32));
+    }
+};
+template <> struct Quad<SOP_BF16> {
+    static __device__ __forceinline__ void load(const void* base, int64_t qi, float4& t00, float4& t10, float4& t01,
+                                                float4& t11)
+    {
+        uint64_t a, b, c, d;
+        ldg256(reinterpret_cast<const uint4*>(base) + 2 * qi, a, b, c, d);
+        t00 = b4((uint32_t)a, (uint32_t)(a >> 32));
+        t10 = b4((uint32_t)b, (uint32_t)(b >> 32));
+        t01 = b4((uint32_t)c, (uint32_t)(c >> 32));
+        t11 = b4((uint32_t)d, (uint32_t)(d >> 32));
+    }
+};
 
 struct ShadeK {
     const float *n, *wo, *albedo, *rough, *metal;
     int64_t M;
     const void* rgbo;
     int32_t R, K, S, He, We;
-    const float4* env4;
+    const float4* envq;
+    const void* quads;
     const float4* dirs;
     const int32_t* idx;
     const float* w;
@@ -329,10 +438,9 @@ struct ShadeK {
 // Query + shade. LANES consecutive threads share one point and split its S
 // directions; one warp covers 32/LANES points.
 // ---------------------------------------------------------------------------
-template <int DT, int KMAX, int LANES, int MODE>
-__global__ void __launch_bounds__(256) shade_kernel(const ShadeK a)
+template <int DT, int KMAX, int MODE>
+__global__ void __launch_bounds__(256) shade_kernel(const ShadeK a, const int LANES)
 {
-    using TX = Texel<DT>;
     extern __shared__ float4 s_dirs[];
     for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_dirs[i] = a.dirs[i];
     __syncthreads();
@@ -348,17 +456,33 @@ __global__ void __launch_bounds__(256) shade_kernel(const ShadeK a)
     float3 tt, bb;
     onb(n, tt, bb);
     const float3 wo = load3(a.wo, mm);
-    const int RS = a.R + 2;
-    const typename TX::raw* base[KMAX];
+    const int RQ = a.R + 1;
+    int32_t base[KMAX];
     float W[KMAX];
-    const typename TX::raw* atlas = reinterpret_cast<const typename TX::raw*>(a.rgbo);
+    int32_t ids[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
         const bool on = k < a.K;
-        const int32_t id = on ? __ldg(a.idx + mm * a.K + k) : 0;
+        ids[k] = on ? __ldg(a.idx + mm * a.K + k) : INT32_MAX;
         W[k] = on ? __ldg(a.w + mm * a.K + k) : 0.f;
-        base[k] = atlas + (int64_t)id * RS * RS;
     }
+    // visit the probes in index order: neighbouring points, which share most
+    // of their probes, then read the same footprints at the same time
+    if (KMAX <= 8)
+#pragma unroll
+    for (int i = 1; i < KMAX; ++i)
+#pragma unroll
+        for (int j = KMAX - 1; j >= i; --j) {
+            const bool sw = ids[j - 1] > ids[j];
+            const int32_t ti = ids[j - 1];
+            const float tw = W[j - 1];
+            ids[j - 1] = sw ? ids[j] : ids[j - 1];
+            W[j - 1] = sw ? W[j] : W[j - 1];
+            ids[j] = sw ? ti : ids[j];
+            W[j] = sw ? tw : W[j];
+        }
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) base[k] = (k < a.K) ? ids[k] * RQ * RQ : 0;
     // per-point BRDF constants
     float3 kd, F0;
     float a2 = 0.f, kk = 0.f, specV = 0.f, NdotV = 1.f;
@@ -387,14 +511,14 @@ __global__ void __launch_bounds__(256) shade_kernel(const ShadeK a)
         const float fi = floorf(s), fj = floorf(t);
         const float fu = s - fi, fv = t - fj;
         const int i0 = min(max((int)fi + 1, 0), a.R), j0 = min(max((int)fj + 1, 0), a.R);
-        const int off = j0 * RS + i0;
+        const int off = j0 * RQ + i0;
         const float w00 = (1.f - fu) * (1.f - fv), w10 = fu * (1.f - fv), w01 = (1.f - fu) * fv, w11 = fu * fv;
         float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             if (k < a.K) {
-                const typename TX::raw* p = base[k] + off;
-                const float4 t00 = TX::load(p), t10 = TX::load(p + 1), t01 = TX::load(p + RS), t11 = TX::load(p + RS + 1);
+                float4 t00, t10, t01, t11;
+                Quad<DT>::load(a.quads, (int64_t)(base[k] + off), t00, t10, t01, t11);
                 const float c00 = W[k] * w00, c10 = W[k] * w10, c01 = W[k] * w01, c11 = W[k] * w11;
                 pr.x += c00 * t00.x + c10 * t10.x + c01 * t01.x + c11 * t11.x;
                 pr.y += c00 * t00.y + c10 * t10.y + c01 * t01.y + c11 * t11.y;
@@ -402,7 +526,7 @@ __global__ void __launch_bounds__(256) shade_kernel(const ShadeK a)
                 pr.w += c00 * t00.w + c10 * t10.w + c01 * t01.w + c11 * t11.w;
             }
         }
-        const float3 Ld = env_lookup(a.env4, a.He, a.We, w);
+        const float3 Ld = env_lookup(a.envq, a.He, a.We, w);
         const float NdotL = l.z;
         const float vis = 1.f - pr.w;
         if (MODE == SOP_MODE_SHADE) {
@@ -431,7 +555,6 @@ __global__ void __launch_bounds__(256) shade_kernel(const ShadeK a)
             den2 += Ld.z * NdotL;
         }
     }
-#pragma unroll
     for (int o = LANES / 2; o > 0; o >>= 1) {
         acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
         acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
@@ -489,25 +612,61 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
     const int64_t ne = (int64_t)(a.He + 2) * (a.We + 1);
     env_pack_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(a.env, a.He, a.We,
                                                                    reinterpret_cast<float4*>(ws + L.env4));
+    const int64_t nq = (int64_t)(a.He + 1) * a.We;
+    env_quad_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(ws + L.env4), a.He,
+                                                                   a.We, reinterpret_cast<float4*>(ws + L.envq));
+    const int64_t na = (int64_t)a.P * (a.R + 1) * (a.R + 1);
+    const unsigned nba = (unsigned)((na + 255) / 256);
+    switch (a.rgbo_dtype) {
+    case SOP_F32:
+        atlas_quad_kernel<SOP_F32><<<nba, 256, 0, s>>>(reinterpret_cast<const float4*>(a.rgbo), a.P, a.R,
+                                                      reinterpret_cast<float4*>(ws + L.quads));
+        break;
+    case SOP_BF16:
+        atlas_quad_kernel<SOP_BF16><<<nba, 256, 0, s>>>(reinterpret_cast<const uint2*>(a.rgbo), a.P, a.R,
+                                                       reinterpret_cast<uint2*>(ws + L.quads));
+        break;
+    default:
+        atlas_quad_kernel<SOP_F16><<<nba, 256, 0, s>>>(reinterpret_cast<const uint2*>(a.rgbo), a.P, a.R,
+                                                      reinterpret_cast<uint2*>(ws + L.quads));
+        break;
+    }
     dirs_kernel<<<(a.S + 127) / 128, 128, 0, s>>>(a.S, a.dirs_local, reinterpret_cast<float4*>(ws + L.dirs), nullptr);
     return cudaGetLastError();
 }
 
 template <int DT, int KMAX, int MODE>
-static cudaError_t shade_dispatch(const ShadeK& k, cudaStream_t s)
+static cudaError_t shade_launch(const ShadeK& k, int LANES, cudaStream_t s)
 {
-    constexpr int LANES = 4;
     const int bs = 256;
     const int64_t threads = k.M * LANES;
     const unsigned nb = (unsigned)((threads + bs - 1) / bs);
     const size_t smem = sizeof(float4) * (size_t)k.S;
-    auto fn = shade_kernel<DT, KMAX, LANES, MODE>;
+    auto fn = shade_kernel<DT, KMAX, MODE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    fn<<<nb, bs, smem, s>>>(k);
+    fn<<<nb, bs, smem, s>>>(k, LANES);
     return cudaGetLastError();
+}
+
+// Threads per shading point (they split the S directions); SOP_SHADE_LANES
+// overrides the default for tuning.
+static int shade_lanes()
+{
+    static int lanes = [] {
+        const char* e = getenv("SOP_SHADE_LANES");
+        const int v = e ? atoi(e) : 0;
+        return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 4;
+    }();
+    return lanes;
+}
+
+template <int DT, int KMAX, int MODE>
+static cudaError_t shade_dispatch(const ShadeK& k, cudaStream_t s)
+{
+    return shade_launch<DT, KMAX, MODE>(k, shade_lanes(), s);
 }
 
 template <int DT, int MODE>
@@ -541,7 +700,8 @@ cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cud
     k.S = a.S;
     k.He = a.He;
     k.We = a.We;
-    k.env4 = reinterpret_cast<const float4*>(ws + L.env4);
+    k.envq = reinterpret_cast<const float4*>(ws + L.envq);
+    k.quads = ws + L.quads;
     k.dirs = reinterpret_cast<const float4*>(ws + L.dirs);
     k.idx = reinterpret_cast<const int32_t*>(ws + L.idx);
     k.w = reinterpret_cast<const float*>(ws + L.w);

@@ -165,10 +165,13 @@ sop_status sop_bake(const sop_gaussians* g, const sop_atlas* atlas, const sop_ba
     return cuda_status(sop::launch_bake_trace(*g, *atlas, *params, L, w, s), "sop_bake (trace)");
 }
 
-size_t sop_query_workspace_bytes(int32_t P, int64_t M, const sop_shade_params* params, int32_t He, int32_t We)
+size_t sop_query_workspace_bytes(const sop_atlas* atlas, int64_t M, const sop_shade_params* params, int32_t He,
+                                 int32_t We)
 {
-    if (!params || P < 1 || M < 0 || He < 1 || We < 1 || params->K < 1 || params->S < 1) return 0;
-    return sop::query_layout(P, M, params->K, params->S, He, We).total;
+    if (!atlas || !params || atlas->P < 1 || atlas->R < 2 || M < 0 || He < 1 || We < 1 || params->K < 1 ||
+        params->S < 1)
+        return 0;
+    return sop::query_layout(atlas->P, M, params->K, params->S, He, We, atlas->R, atlas->rgbo_dtype).total;
 }
 
 static sop_status query_common(const float* x, const float* n, const float* wo, const float* albedo, const float* rough,
@@ -186,7 +189,7 @@ static sop_status query_common(const float* x, const float* n, const float* wo, 
     if (!env) return fail(SOP_ERR_INVALID_ARG, "env is NULL");
     if (M > 0 && (!x || !n || !wo || !albedo || !rough || !metal))
         return fail(SOP_ERR_INVALID_ARG, "a shading-point array is NULL");
-    L = sop::query_layout(atlas->P, M, params->K, params->S, He, We);
+    L = sop::query_layout(atlas->P, M, params->K, params->S, He, We, atlas->R, atlas->rgbo_dtype);
     st = check_ws(ws, ws_bytes, L.total);
     if (st != SOP_OK) return st;
     a = sop::QueryArgs{};

@@ -72,7 +72,7 @@ def load(build_if_missing: bool = True):
     lib.sop_bake_workspace_bytes.argtypes = [i64, i32, i32]
     lib.sop_bake_workspace_bytes.restype = sz
     lib.sop_bake.argtypes = [C.POINTER(Gaussians), C.POINTER(AtlasDesc), C.POINTER(BakeParams), vp, sz, vp]
-    lib.sop_query_workspace_bytes.argtypes = [i32, i64, C.POINTER(ShadeParams), i32, i32]
+    lib.sop_query_workspace_bytes.argtypes = [C.POINTER(AtlasDesc), i64, C.POINTER(ShadeParams), i32, i32]
     lib.sop_query_workspace_bytes.restype = sz
     lib.sop_query_shade.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
                                     C.POINTER(ShadeParams), vp, vp, vp, vp, sz, vp]
@@ -247,9 +247,10 @@ def bake(gauss, atlas: Atlas, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99,
     return atlas
 
 
-def query_workspace_bytes(P, M, K, S, He, We, mode=MODE_SHADE):
+def query_workspace_bytes(atlas: Atlas, M, K, S, He, We, mode=MODE_SHADE):
     sp = ShadeParams(K, S, mode, 0.5, 1e-6)
-    return int(load().sop_query_workspace_bytes(P, M, C.byref(sp), He, We))
+    d = atlas.c()
+    return int(load().sop_query_workspace_bytes(C.byref(d), M, C.byref(sp), He, We))
 
 
 def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MODE_SHADE, specular=0.5,
@@ -266,7 +267,7 @@ def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MO
         out = torch.empty((M, 3), dtype=torch.float32, device=dev)
     idx = torch.empty((M, K), dtype=torch.int32, device=dev) if return_idx else None
     w = torch.empty((M, K), dtype=torch.float32, device=dev) if return_idx else None
-    need = int(lib.sop_query_workspace_bytes(atlas.P, M, C.byref(sp), He, We))
+    need = int(lib.sop_query_workspace_bytes(C.byref(d), M, C.byref(sp), He, We))
     ws = workspace if workspace is not None else _ws(need, dev)
     for t, shp in ((x, (M, 3)), (n, (M, 3)), (wo, (M, 3)), (albedo, (M, 3)), (rough, (M,)), (metal, (M,)),
                    (env, (He, We, 3))):
