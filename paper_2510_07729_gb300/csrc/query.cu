@@ -653,20 +653,22 @@ static cudaError_t shade_launch(const ShadeK& k, int LANES, cudaStream_t s)
 
 // Threads per shading point (they split the S directions); SOP_SHADE_LANES
 // overrides the default for tuning.
-static int shade_lanes()
+// Default (measured on GB300, 'object' workload): one thread per point for a
+// float32 atlas, two for 16-bit atlases.
+static int shade_lanes(int dtype)
 {
     static int lanes = [] {
         const char* e = getenv("SOP_SHADE_LANES");
         const int v = e ? atoi(e) : 0;
-        return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 4;
+        return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 0;
     }();
-    return lanes;
+    return lanes ? lanes : (dtype == SOP_F32 ? 1 : 2);
 }
 
 template <int DT, int KMAX, int MODE>
 static cudaError_t shade_dispatch(const ShadeK& k, cudaStream_t s)
 {
-    return shade_launch<DT, KMAX, MODE>(k, shade_lanes(), s);
+    return shade_launch<DT, KMAX, MODE>(k, shade_lanes(DT), s);
 }
 
 template <int DT, int MODE>
@@ -714,5 +716,6 @@ cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cud
     default: return cudaErrorInvalidValue;
     }
 }
+
 
 }  // namespace sop

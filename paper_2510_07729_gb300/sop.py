@@ -278,3 +278,4 @@ def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MO
     if return_idx:
         return out, idx, w
     return out
+
