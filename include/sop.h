@@ -207,6 +207,33 @@ sop_status sop_query_shade(const float* x, const float* n, const float* wo, cons
                            int32_t We, const float* dirs_local, const sop_shade_params* params, float* out,
                            int32_t* out_idx, float* out_w, void* ws, size_t ws_bytes, void* stream);
 
+/* Allocation-free sop_query_shade. No counterpart in the paper: this entry
+ * point exists for callers that cannot allocate device memory, for example
+ * code running where cudaMalloc is unavailable or forbidden (a host
+ * framework that owns all allocations, a capture or plugin context, an
+ * embedded runtime without an allocator). It takes the same arguments as
+ * sop_query_shade except the workspace, allocates nothing, and computes the
+ * same result (same K nearest probes, weights and shading) by reading the
+ * atlas and the environment in the caller's own layouts.
+ * Scratch: one fixed array of SOP_NOALLOC_SCRATCH_BYTES (8 MiB) of device
+ * memory inside the library, held on every GPU that loads the library until
+ * the process exits. Limits: the probe grid, the direction table and one
+ * chunk of 16,384 points' neighbour lists must fit it, which holds for up to
+ * SOP_NOALLOC_MAX_PROBES probes at any K <= 32 and S <= 4096 (larger P is
+ * rejected with SOP_ERR_INVALID_ARG and a message; use sop_query_shade).
+ * The first call on a device looks up the array's address on that device,
+ * so make that first call before any CUDA stream capture on the device.
+ * Every call uses the same array and leaves its contents behind; calls that
+ * overlap on the GPU (other streams or host threads) race on it and must be
+ * serialised by the caller. Asynchronous on `stream`. */
+#define SOP_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define SOP_NOALLOC_MAX_PROBES 65536
+sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* wo, const float* albedo,
+                                   const float* rough, const float* metal, int64_t M, const sop_atlas* atlas,
+                                   const float* env, int32_t He, int32_t We, const float* dirs_local,
+                                   const sop_shade_params* params, float* out, int32_t* out_idx, float* out_w,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

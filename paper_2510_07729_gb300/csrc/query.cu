@@ -17,6 +17,8 @@
 #include <float.h>
 #include <stdlib.h>
 
+#include <mutex>
+
 #include "sop_device.cuh"
 #include "sop_internal.h"
 
@@ -717,5 +719,302 @@ cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cud
     }
 }
 
+
+// ===========================================================================
+// Allocation-free variant of the query + shade (sop_query_shade_noalloc).
+//
+// For callers that cannot allocate device memory themselves. Its scratch is
+// one file-scope device array of kNoAllocScratchBytes, present on every GPU
+// that loads the library until the process exits. Host code cannot pass the
+// array's name to a kernel (on the host it is only a stand-in symbol), so the
+// first call on each device looks up the array's device address with
+// cudaGetSymbolAddress while that device is current, and later calls reuse
+// it. The probe atlas and the environment are read in the caller's own
+// layouts (no repacked copies), and points are processed in chunks of
+// kNoAllocChunk so that the per-point neighbour lists fit the array. All
+// calls share the array: calls that overlap on the GPU (other streams, other
+// host threads) race on it.
+// ===========================================================================
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
+constexpr int64_t kNoAllocChunk = 16384;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+int64_t noalloc_chunk() { return kNoAllocChunk; }
+
+// Bilinear environment lookup straight from the caller's [He][We][3] array.
+__device__ __forceinline__ float3 env_lookup_direct(const float* __restrict__ env, int He, int We, float3 w)
+{
+    const float th = atan2f(sqrtf(w.x * w.x + w.y * w.y), w.z);
+    const float ph = atan2f(w.y, w.x);
+    const float s = (ph + kPi) * kInv2Pi * We - 0.5f;
+    const float t = th * kInvPi * He - 0.5f;
+    const float fs = floorf(s), ft = floorf(t);
+    const float a = s - fs, b = t - ft;
+    int c0 = (int)fs;
+    c0 = c0 < 0 ? c0 + We : c0;
+    c0 = min(max(c0, 0), We - 1);
+    const int c1 = c0 + 1 == We ? 0 : c0 + 1;
+    const int r0 = min(max((int)ft, 0), He - 1), r1 = min(max((int)ft + 1, 0), He - 1);
+    const float* e00 = env + ((int64_t)r0 * We + c0) * 3;
+    const float* e01 = env + ((int64_t)r0 * We + c1) * 3;
+    const float* e10 = env + ((int64_t)r1 * We + c0) * 3;
+    const float* e11 = env + ((int64_t)r1 * We + c1) * 3;
+    const float w00 = (1.f - a) * (1.f - b), w01 = a * (1.f - b), w10 = (1.f - a) * b, w11 = a * b;
+    return f3(w00 * __ldg(e00) + w01 * __ldg(e01) + w10 * __ldg(e10) + w11 * __ldg(e11),
+              w00 * __ldg(e00 + 1) + w01 * __ldg(e01 + 1) + w10 * __ldg(e10 + 1) + w11 * __ldg(e11 + 1),
+              w00 * __ldg(e00 + 2) + w01 * __ldg(e01 + 2) + w10 * __ldg(e10 + 2) + w11 * __ldg(e11 + 2));
+}
+
+struct ShadeDirectK {
+    const float *n, *wo, *albedo, *rough, *metal;
+    int64_t M;
+    const void* rgbo;
+    int32_t R, K, S, He, We;
+    const float* env;
+    const float4* dirs;
+    const int32_t* idx;
+    const float* w;
+    float specular;
+    float* out;
+};
+
+// One thread per point; texels read from the gutter atlas, four per probe.
+template <int DT, int KMAX, int MODE>
+__global__ void __launch_bounds__(256) shade_direct_kernel(const ShadeDirectK a)
+{
+    using TX = Texel<DT>;
+    extern __shared__ float4 s_dirs[];
+    for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_dirs[i] = a.dirs[i];
+    __syncthreads();
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.M) return;
+    const float3 nr = load3(a.n, m);
+    const float nl = sqrtf(dot3(nr, nr));
+    const float3 n = f3(nr.x / nl, nr.y / nl, nr.z / nl);
+    float3 tt, bb;
+    onb(n, tt, bb);
+    const float3 wo = load3(a.wo, m);
+    const int RS = a.R + 2;
+    const typename TX::raw* atlas = reinterpret_cast<const typename TX::raw*>(a.rgbo);
+    int64_t base[KMAX];
+    float W[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const bool on = k < a.K;
+        base[k] = on ? (int64_t)__ldg(a.idx + m * a.K + k) * RS * RS : 0;
+        W[k] = on ? __ldg(a.w + m * a.K + k) : 0.f;
+    }
+    float3 kd = f3(0.f, 0.f, 0.f), F0 = f3(0.f, 0.f, 0.f);
+    float a2 = 0.f, kk = 0.f, specV = 0.f;
+    if (MODE == SOP_MODE_SHADE) {
+        const float3 alb = load3(a.albedo, m);
+        const float r = __ldg(a.rough + m), mt = __ldg(a.metal + m);
+        const float dsc = (1.f - mt) * kInvPi;
+        kd = f3(dsc * alb.x, dsc * alb.y, dsc * alb.z);
+        const float f0d = 0.08f * a.specular * (1.f - mt);
+        F0 = f3(f0d + alb.x * mt, f0d + alb.y * mt, f0d + alb.z * mt);
+        const float al = r * r;
+        a2 = al * al;
+        kk = (r + 1.f) * (r + 1.f) * 0.125f;
+        const float NdotV = fmaxf(dot3(n, wo), 1e-4f);
+        specV = (NdotV / (NdotV * (1.f - kk) + kk)) / (4.f * NdotV);
+    }
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, den0 = 0.f, den1 = 0.f, den2 = 0.f;
+    const float Rf = (float)a.R;
+    for (int i = 0; i < a.S; ++i) {
+        const float4 l = s_dirs[i];
+        const float3 w = f3(fmaf(l.x, tt.x, fmaf(l.y, bb.x, l.z * n.x)), fmaf(l.x, tt.y, fmaf(l.y, bb.y, l.z * n.y)),
+                            fmaf(l.x, tt.z, fmaf(l.y, bb.z, l.z * n.z)));
+        const float2 uv = oct_encode(w);
+        const float s = uv.x * Rf - 0.5f, t = uv.y * Rf - 0.5f;
+        const float fi = floorf(s), fj = floorf(t);
+        const float fu = s - fi, fv = t - fj;
+        const int i0 = min(max((int)fi + 1, 0), a.R), j0 = min(max((int)fj + 1, 0), a.R);
+        const int off = j0 * RS + i0;
+        const float w00 = (1.f - fu) * (1.f - fv), w10 = fu * (1.f - fv), w01 = (1.f - fu) * fv, w11 = fu * fv;
+        float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (k < a.K) {
+                const typename TX::raw* p = atlas + base[k] + off;
+                const float4 t00 = TX::load(p), t10 = TX::load(p + 1), t01 = TX::load(p + RS), t11 = TX::load(p + RS + 1);
+                const float c00 = W[k] * w00, c10 = W[k] * w10, c01 = W[k] * w01, c11 = W[k] * w11;
+                pr.x += c00 * t00.x + c10 * t10.x + c01 * t01.x + c11 * t11.x;
+                pr.y += c00 * t00.y + c10 * t10.y + c01 * t01.y + c11 * t11.y;
+                pr.z += c00 * t00.z + c10 * t10.z + c01 * t01.z + c11 * t11.z;
+                pr.w += c00 * t00.w + c10 * t10.w + c01 * t01.w + c11 * t11.w;
+            }
+        }
+        const float3 Ld = env_lookup_direct(a.env, a.He, a.We, w);
+        const float NdotL = l.z;
+        const float vis = 1.f - pr.w;
+        if (MODE == SOP_MODE_SHADE) {
+            float3 h = w + wo;
+            const float hl2 = dot3(h, h);
+            h = hl2 > 1e-30f ? (1.f / sqrtf(hl2)) * h : n;
+            const float NdotH = dot3(n, h), VdotH = dot3(wo, h);
+            const float3 cr = cross3(n, h);
+            const float sin2 = dot3(cr, cr);
+            const float den = NdotH * NdotH * a2 + sin2;
+            const float D = a2 / (kPi * den * den);
+            const float spec = D * specV / (NdotL * (1.f - kk) + kk);
+            const float x1 = 1.f - VdotH, x2 = x1 * x1, fc = x2 * x2 * x1;
+            acc0 += (kd.x + spec * (F0.x + (1.f - F0.x) * fc)) * (vis * Ld.x + pr.x) * NdotL;
+            acc1 += (kd.y + spec * (F0.y + (1.f - F0.y) * fc)) * (vis * Ld.y + pr.y) * NdotL;
+            acc2 += (kd.z + spec * (F0.z + (1.f - F0.z) * fc)) * (vis * Ld.z + pr.z) * NdotL;
+        } else {
+            acc0 += Ld.x * vis * NdotL;
+            acc1 += Ld.y * vis * NdotL;
+            acc2 += Ld.z * vis * NdotL;
+            den0 += Ld.x * NdotL;
+            den1 += Ld.y * NdotL;
+            den2 += Ld.z * NdotL;
+        }
+    }
+    float* o = a.out + 3 * m;
+    if (MODE == SOP_MODE_SHADE) {
+        const float sc = 2.f * kPi / (float)a.S;
+        o[0] = sc * acc0;
+        o[1] = sc * acc1;
+        o[2] = sc * acc2;
+    } else {
+        o[0] = den0 < 1e-20f ? 1.f : acc0 / den0;
+        o[1] = den1 < 1e-20f ? 1.f : acc1 / den1;
+        o[2] = den2 < 1e-20f ? 1.f : acc2 / den2;
+    }
+}
+
+template <int DT, int KMAX, int MODE>
+static cudaError_t shade_direct_launch(const ShadeDirectK& k, cudaStream_t s)
+{
+    const size_t smem = sizeof(float4) * (size_t)k.S;
+    auto fn = shade_direct_kernel<DT, KMAX, MODE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    fn<<<(unsigned)((k.M + 255) / 256), 256, smem, s>>>(k);
+    return cudaGetLastError();
+}
+
+template <int DT, int MODE>
+static cudaError_t shade_direct_k(const ShadeDirectK& k, cudaStream_t s)
+{
+    if (k.K <= 4) return shade_direct_launch<DT, 4, MODE>(k, s);
+    if (k.K <= 8) return shade_direct_launch<DT, 8, MODE>(k, s);
+    if (k.K <= 16) return shade_direct_launch<DT, 16, MODE>(k, s);
+    return shade_direct_launch<DT, 32, MODE>(k, s);
+}
+
+template <int DT>
+static cudaError_t shade_direct_mode(const ShadeDirectK& k, int mode, cudaStream_t s)
+{
+    return mode == SOP_MODE_SHADE ? shade_direct_k<DT, SOP_MODE_SHADE>(k, s) : shade_direct_k<DT, SOP_MODE_SHADOW>(k, s);
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the lookup must run with that device current).
+static cudaError_t noalloc_scratch_ptr(char** out)
+{
+    static std::mutex mu;
+    static char* ptrs[256] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        ptrs[dev] = static_cast<char*>(p);
+    }
+    *out = ptrs[dev];
+    return cudaSuccess;
+}
+
+// Scratch layout for P probes, S directions and K neighbours (per chunk).
+static QueryLayout noalloc_layout(int32_t P, int32_t K, int32_t S)
+{
+    QueryLayout L{};
+    int g = 1;
+    while ((int64_t)g * g * g < P) ++g;
+    L.g_axis = g;
+    L.cells_cap = (g + 1) * (g + 1) * (g + 1);
+    size_t o = 0;
+    L.grid_hdr = o;   o = align256(o + sizeof(ProbeGrid));
+    L.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)(L.cells_cap + 1));
+    L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
+    L.entries = o;    o = align256(o + sizeof(int4) * (size_t)P);
+    L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)S);
+    L.idx = o;        o = align256(o + sizeof(int32_t) * (size_t)kNoAllocChunk * K);
+    L.w = o;          o = align256(o + sizeof(float) * (size_t)kNoAllocChunk * K);
+    L.total = o;
+    return L;
+}
+
+size_t noalloc_required_bytes(int32_t P, int32_t K, int32_t S) { return noalloc_layout(P, K, S).total; }
+
+cudaError_t launch_query_noalloc(const QueryArgs& a, cudaStream_t s)
+{
+    char* ws = nullptr;
+    cudaError_t e = noalloc_scratch_ptr(&ws);
+    if (e != cudaSuccess) return e;
+    const QueryLayout L = noalloc_layout(a.P, a.K, a.S);
+    if (L.total > kNoAllocScratchBytes) return cudaErrorInvalidValue;  // checked by the caller first
+    ProbeGrid* grid = reinterpret_cast<ProbeGrid*>(ws + L.grid_hdr);
+    int32_t* cstart = reinterpret_cast<int32_t*>(ws + L.cell_start);
+    int32_t* ccnt = reinterpret_cast<int32_t*>(ws + L.cell_cnt);
+    int4* ent = reinterpret_cast<int4*>(ws + L.entries);
+    float4* dirs = reinterpret_cast<float4*>(ws + L.dirs);
+    int32_t* idx = reinterpret_cast<int32_t*>(ws + L.idx);
+    float* w = reinterpret_cast<float*>(ws + L.w);
+    // the grid build clears its own counters, so stale contents are harmless
+    probe_grid_kernel<<<1, 1024, 0, s>>>(a.probe_pos, a.P, L.g_axis, grid, cstart, ccnt, ent);
+    dirs_kernel<<<(a.S + 127) / 128, 128, 0, s>>>(a.S, a.dirs_local, dirs, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int64_t m0 = 0; m0 < a.M; m0 += kNoAllocChunk) {
+        const int64_t mc = a.M - m0 < kNoAllocChunk ? a.M - m0 : kNoAllocChunk;
+        const unsigned nb = (unsigned)((mc + 127) / 128);
+        int32_t* uidx = a.out_idx ? a.out_idx + m0 * a.K : nullptr;
+        float* uw = a.out_w ? a.out_w + m0 * a.K : nullptr;
+#define SOP_KNN_NA(KM)                                                                                             \
+    knn_kernel<KM><<<nb, 128, 0, s>>>(a.x + 3 * m0, a.n + 3 * m0, mc, a.K, a.snap_key, grid, cstart, ent, a.probe_pos, \
+                                      idx, w, uidx, uw)
+        if (a.K <= 4) SOP_KNN_NA(4);
+        else if (a.K <= 8) SOP_KNN_NA(8);
+        else if (a.K <= 16) SOP_KNN_NA(16);
+        else SOP_KNN_NA(32);
+#undef SOP_KNN_NA
+        ShadeDirectK k;
+        k.n = a.n + 3 * m0;
+        k.wo = a.wo + 3 * m0;
+        k.albedo = a.albedo + 3 * m0;
+        k.rough = a.rough + m0;
+        k.metal = a.metal + m0;
+        k.M = mc;
+        k.rgbo = a.rgbo;
+        k.R = a.R;
+        k.K = a.K;
+        k.S = a.S;
+        k.He = a.He;
+        k.We = a.We;
+        k.env = a.env;
+        k.dirs = dirs;
+        k.idx = idx;
+        k.w = w;
+        k.specular = a.specular;
+        k.out = a.out + 3 * m0;
+        switch (a.rgbo_dtype) {
+        case SOP_F32: e = shade_direct_mode<SOP_F32>(k, a.mode, s); break;
+        case SOP_BF16: e = shade_direct_mode<SOP_BF16>(k, a.mode, s); break;
+        case SOP_F16: e = shade_direct_mode<SOP_F16>(k, a.mode, s); break;
+        default: e = cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
 
 }  // namespace sop

@@ -238,4 +238,55 @@ sop_status sop_query_shade(const float* x, const float* n, const float* wo, cons
     return cuda_status(sop::launch_shade(a, L, (char*)ws, s), "sop_query_shade (shade)");
 }
 
+sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* wo, const float* albedo,
+                                   const float* rough, const float* metal, int64_t M, const sop_atlas* atlas,
+                                   const float* env, int32_t He, int32_t We, const float* dirs_local,
+                                   const sop_shade_params* params, float* out, int32_t* out_idx, float* out_w,
+                                   void* stream)
+{
+    sop_status st = check_atlas(atlas, false);
+    if (st != SOP_OK) return st;
+    st = check_shade(params, atlas->P);
+    if (st != SOP_OK) return st;
+    const size_t need = sop::noalloc_required_bytes(atlas->P, params->K, params->S);
+    if (atlas->P > SOP_NOALLOC_MAX_PROBES || need > sop::noalloc_scratch_bytes())
+        return fail(SOP_ERR_INVALID_ARG,
+                    "sop_query_shade_noalloc: P = %d, K = %d, S = %d need %zu bytes of scratch, more than the "
+                    "fixed %zu (at most %d probes with K = 32 and S = 4096); use sop_query_shade with a workspace",
+                    atlas->P, params->K, params->S, need, sop::noalloc_scratch_bytes(), SOP_NOALLOC_MAX_PROBES);
+    if (M < 0 || M > ((int64_t)1 << 36)) return fail(SOP_ERR_INVALID_ARG, "M = %lld out of range", (long long)M);
+    if (He < 1 || We < 1 || (int64_t)He * We > ((int64_t)1 << 28))
+        return fail(SOP_ERR_INVALID_ARG, "environment size %d x %d invalid", He, We);
+    if (!env) return fail(SOP_ERR_INVALID_ARG, "env is NULL");
+    if (M > 0 && (!x || !n || !wo || !albedo || !rough || !metal || !out))
+        return fail(SOP_ERR_INVALID_ARG, "a shading-point array is NULL");
+    sop::QueryArgs a{};
+    a.x = x;
+    a.n = n;
+    a.wo = wo;
+    a.albedo = albedo;
+    a.rough = rough;
+    a.metal = metal;
+    a.M = M;
+    a.rgbo = atlas->rgbo;
+    a.rgbo_dtype = atlas->rgbo_dtype;
+    a.P = atlas->P;
+    a.R = atlas->R;
+    a.probe_pos = atlas->probe_pos;
+    a.env = env;
+    a.He = He;
+    a.We = We;
+    a.dirs_local = dirs_local;
+    a.K = params->K;
+    a.S = params->S;
+    a.mode = params->mode;
+    a.specular = params->specular;
+    const double e = (double)params->eps_snap * 1048576.0;
+    a.snap_key = (uint64_t)floor(e * e);
+    a.out = out;
+    a.out_idx = out_idx;
+    a.out_w = out_w;
+    return cuda_status(sop::launch_query_noalloc(a, (cudaStream_t)stream), "sop_query_shade_noalloc");
+}
+
 }  // extern "C"

@@ -48,6 +48,12 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
 cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_hammersley(int32_t S, float* out3, cudaStream_t s);
 
+// allocation-free query (static device scratch, see query.cu)
+size_t noalloc_scratch_bytes();
+int64_t noalloc_chunk();
+size_t noalloc_required_bytes(int32_t P, int32_t K, int32_t S);
+cudaError_t launch_query_noalloc(const QueryArgs& a, cudaStream_t s);
+
 // ---- atlas pack -------------------------------------------------------------
 cudaError_t launch_atlas_pack(const float* rgb, int rgb_stride, const float* occ, int occ_stride, const float* depth,
                               const sop_atlas& atlas, cudaStream_t s);

@@ -76,7 +76,10 @@ def load(build_if_missing: bool = True):
     lib.sop_query_workspace_bytes.restype = sz
     lib.sop_query_shade.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
                                     C.POINTER(ShadeParams), vp, vp, vp, vp, sz, vp]
-    for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_query_shade"):
+    lib.sop_query_shade_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
+                                            C.POINTER(ShadeParams), vp, vp, vp, vp]
+    for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_query_shade",
+                 "sop_query_shade_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -279,3 +282,29 @@ def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MO
         return out, idx, w
     return out
 
+
+def query_shade_noalloc(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MODE_SHADE, specular=0.5,
+                        eps_snap=1e-6, dirs_local=None, out=None, return_idx=False):
+    """sop_query_shade_noalloc: the same query + shade without a workspace,
+    for callers that cannot allocate device memory (the library's fixed
+    scratch array is used instead; see include/sop.h)."""
+    lib = load()
+    M = x.shape[0]
+    He, We = env.shape[0], env.shape[1]
+    dev = x.device
+    sp = ShadeParams(K, S, mode, specular, eps_snap)
+    d = atlas.c()
+    if out is None:
+        out = torch.empty((M, 3), dtype=torch.float32, device=dev)
+    idx = torch.empty((M, K), dtype=torch.int32, device=dev) if return_idx else None
+    w = torch.empty((M, K), dtype=torch.float32, device=dev) if return_idx else None
+    for t, shp in ((x, (M, 3)), (n, (M, 3)), (wo, (M, 3)), (albedo, (M, 3)), (rough, (M,)), (metal, (M,)),
+                   (env, (He, We, 3))):
+        _f32(t, shp)
+    _check(lib.sop_query_shade_noalloc(_ptr(x), _ptr(n), _ptr(wo), _ptr(albedo), _ptr(rough), _ptr(metal), M,
+                                       C.byref(d), _ptr(env), He, We,
+                                       None if dirs_local is None else _f32(dirs_local, (S, 3)), C.byref(sp),
+                                       _ptr(out), _ptr(idx), _ptr(w), _stream()))
+    if return_idx:
+        return out, idx, w
+    return out
