@@ -44,7 +44,7 @@ BakeLayout bake_layout(int64_t N, int32_t P, int32_t R, int64_t entries_cap)
     L.entries_cap = entries_cap > 0 ? entries_cap : 24 * N + 65536;
     size_t o = 0;
     L.hdr = o;        o = align256(o + sizeof(GaussGrid));
-    L.bbox = o;       o = align256(o + 8 * sizeof(int32_t));
+    L.bbox = o;       o = align256(o + 16 * sizeof(int32_t));
     L.rec = o;        o = align256(o + sizeof(GRec) * (size_t)(N > 0 ? N : 1));
     L.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)(L.cells_cap + 1));
     L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
@@ -69,7 +69,7 @@ __global__ void bbox_init_kernel(int32_t* bbox)
 {
     if (threadIdx.x < 3) bbox[threadIdx.x] = f2o(FLT_MAX);
     else if (threadIdx.x < 6) bbox[threadIdx.x] = f2o(-FLT_MAX);
-    else if (threadIdx.x < 8) bbox[threadIdx.x] = 0;  // [6]: trace status word
+    else if (threadIdx.x < 12) bbox[threadIdx.x] = 0;  // [6]: trace status word, [8..9]: ray counter
 }
 
 // Per-Gaussian record + bounding box of the (margin-expanded) spheres.
@@ -304,6 +304,7 @@ struct TraceK {
     float4* maps;   // [P][R][R] (L.rgb, O)
     float* depth;   // [P][R][R]
     int32_t* status;  // device status word: bit 0 = a cell window could not be split
+    unsigned long long* counter;  // next texel ray to trace
 };
 
 constexpr int kWarpsPerCta = 8;
@@ -324,103 +325,145 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
 {
     __shared__ uint64_t s_key[kWarpsPerCta][kHitCap];
     __shared__ float s_alpha[kWarpsPerCta][kHitCap];
+    __shared__ int32_t s_que[kWarpsPerCta][64];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t* key = s_key[wib];
     float* alp = s_alpha[wib];
+    int32_t* que = s_que[wib];
     const int RR = k.R * k.R;
-    const int64_t ray = (int64_t)blockIdx.x * kWarpsPerCta + wib;
-    if (ray >= (int64_t)k.P * RR) return;  // whole warp leaves together
+    const int64_t total = (int64_t)k.P * RR;
+    // persistent warps: each takes the next texel ray from a global counter,
+    // so long rays (escaping the object) do not hold up short ones
+    for (;;) {
+    unsigned long long rr = 0;
+    if (lane == 0) rr = atomicAdd(k.counter, 1ull);
+    const int64_t ray = (int64_t)__shfl_sync(0xffffffffu, rr, 0);
+    if (ray >= total) break;
     const int p = (int)(ray / RR), t = (int)(ray % RR);
     const GaussGrid G = *k.grid;
     const float4 d4 = __ldg(k.dirs + t);
     const float3 d = f3(d4.x, d4.y, d4.z);
     const float3 o = load3(k.probe_pos, p);
 
+    // per-lane partial sums of the composited terms, reduced once per ray
     float T = 1.f, L0 = 0.f, L1 = 0.f, L2 = 0.f, Dacc = 0.f, Wacc = 0.f;
     bool done = false;
 
-    const float ov[3] = {o.x, o.y, o.z}, dv[3] = {d.x, d.y, d.z};
+    // grid box entry/exit (slab test), per axis in scalars so that nothing
+    // is indexed by a run-time axis (which would put it in local memory)
+    const float gox = G.origin[0], goy = G.origin[1], goz = G.origin[2];
+    const float gmx = G.bmax[0], gmy = G.bmax[1], gmz = G.bmax[2];
+    const int gdx = G.dims[0], gdy = G.dims[1], gdz = G.dims[2];
+    const float gh = G.h, gih = G.inv_h;
     float t0 = 0.f, t1 = FLT_MAX;
-    for (int a = 0; a < 3; ++a) {
-        if (dv[a] != 0.f) {
-            const float inv = 1.f / dv[a];
-            float ta = (G.origin[a] - ov[a]) * inv, tb = (G.bmax[a] - ov[a]) * inv;
-            if (ta > tb) { const float tmp = ta; ta = tb; tb = tmp; }
-            t0 = fmaxf(t0, ta);
-            t1 = fminf(t1, tb);
-        } else if (ov[a] < G.origin[a] || ov[a] > G.bmax[a]) {
-            t1 = -1.f;
-        }
+#define SOP_SLAB(OA, DA, LO, HI)                                     \
+    if (DA != 0.f) {                                                 \
+        const float inv = 1.f / DA;                                  \
+        float ta = (LO - OA) * inv, tb = (HI - OA) * inv;            \
+        if (ta > tb) {                                               \
+            const float tmp = ta;                                    \
+            ta = tb;                                                 \
+            tb = tmp;                                                \
+        }                                                            \
+        t0 = fmaxf(t0, ta);                                          \
+        t1 = fminf(t1, tb);                                          \
+    } else if (OA < LO || OA > HI) {                                 \
+        t1 = -1.f;                                                   \
     }
-    // exact (hi + lo) split of the probe position relative to nothing: the
-    // per-Gaussian offsets are split in the hit test below
+    SOP_SLAB(o.x, d.x, gox, gmx)
+    SOP_SLAB(o.y, d.y, goy, gmy)
+    SOP_SLAB(o.z, d.z, goz, gmz)
+#undef SOP_SLAB
     if (G.n_entries > 0 && t0 <= t1) {
-        int cell[3], step[3];
-        float tmax[3];
-        for (int a = 0; a < 3; ++a) {
-            const float pa = ov[a] + t0 * dv[a];
-            cell[a] = min(max((int)floorf((pa - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
-            step[a] = dv[a] > 0.f ? 1 : (dv[a] < 0.f ? -1 : 0);
-            tmax[a] = step[a] == 0 ? FLT_MAX
-                                   : (G.origin[a] + (cell[a] + (step[a] > 0 ? 1 : 0)) * G.h - ov[a]) / dv[a];
-        }
+        int cx = min(max((int)floorf((o.x + t0 * d.x - gox) * gih), 0), gdx - 1);
+        int cy = min(max((int)floorf((o.y + t0 * d.y - goy) * gih), 0), gdy - 1);
+        int cz = min(max((int)floorf((o.z + t0 * d.z - goz) * gih), 0), gdz - 1);
+        const int sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
+        const int sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
+        const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
+        // t at the next cell boundary along each axis, from the cell index
+#define SOP_TNEXT(S, C, GO, OA, DA) ((S) == 0 ? FLT_MAX : ((GO) + ((C) + ((S) > 0 ? 1 : 0)) * gh - (OA)) / (DA))
+        float tmx = SOP_TNEXT(sx, cx, gox, o.x, d.x);
+        float tmy = SOP_TNEXT(sy, cy, goy, o.y, d.y);
+        float tmz = SOP_TNEXT(sz, cz, goz, o.z, d.z);
         float t_enter = t0;
         while (!done) {
-            int ax = 0;
-            if (tmax[1] < tmax[ax]) ax = 1;
-            if (tmax[2] < tmax[ax]) ax = 2;
-            float t_exit = fminf(tmax[ax], t1);
+            const int ax = (tmx <= tmy && tmx <= tmz) ? 0 : (tmy <= tmz ? 1 : 2);
+            const float tm = ax == 0 ? tmx : (ax == 1 ? tmy : tmz);
+            float t_exit = fminf(tm, t1);
             if (t_exit < t_enter) t_exit = t_enter;
-            const int c = (cell[2] * G.dims[1] + cell[1]) * G.dims[0] + cell[0];
+            const int c = (cz * gdy + cy) * gdx + cx;
             const int e0 = __ldg(k.cell_start + c), e1 = __ldg(k.cell_start + c + 1);
             float tl = t_enter, th = t_exit;
             int splits = 0;
             while (e1 > e0) {
                 // ---- collect the hits with t* in [tl, th) -----------------
-                int n = 0;
-                for (int eb = e0; eb < e1; eb += 32) {
-                    const int e = eb + lane;
+                // cheap sphere test on every entry; survivors are queued and
+                // evaluated exactly 32 at a time so that all lanes are busy
+                int n = 0, qn = 0;
+                for (int eb = e0; eb < e1 || qn > 0; eb += 32) {
+                    if (eb < e1) {
+                        const int e = eb + lane;
+                        bool pass = false;
+                        if (e < e1) {
+                            const float4 r0 = __ldg(k.ent_sph + e);
+                            const float3 del = f3(r0.x, r0.y, r0.z) - o;
+                            const float tc = dot3(del, d);
+                            const float dd = dot3(del, del);
+                            // squared ray-centre distance |del|^2 - tc^2, with a
+                            // margin larger than its rounding (filter only)
+                            pass = tc + r0.w >= tl && tc - r0.w <= th &&
+                                   fmaf(-tc, tc, dd) <= fmaf(r0.w, r0.w, 1e-6f * dd);
+                        }
+                        const unsigned pm = __ballot_sync(0xffffffffu, pass);
+                        if (pass) que[qn + __popc(pm & ((1u << lane) - 1u))] = e;
+                        qn += __popc(pm);
+                        __syncwarp();
+                        if (qn < 32 && eb + 32 < e1) continue;  // batch up more candidates
+                    }
+                    // exact responses of up to 32 queued candidates, one per lane
+                    const int take = qn < 32 ? qn : 32;
                     bool hit = false;
                     float ts = 0.f, al = 0.f;
                     int32_t gi = 0;
-                    if (e < e1) {
+                    if (lane < take) {
+                        const int e = que[lane];
                         const float4 r0 = __ldg(k.ent_sph + e);
                         const float3 mu = f3(r0.x, r0.y, r0.z);
-                        const float3 del = mu - o;
-                        const float tc = dot3(del, d);
-                        const float3 cx = cross3(del, d);
-                        if (tc + r0.w >= tl && tc - r0.w <= th && dot3(cx, cx) <= r0.w * r0.w) {
-                            gi = __ldg(k.entries + e);
-                            const float4 r1 = __ldg(&k.rec[gi].r1), r2 = __ldg(&k.rec[gi].r2),
-                                         r3 = __ldg(&k.rec[gi].r3);
-                            float hx, lx, hy, ly, hz, lz;
-                            two_diff(o.x, mu.x, hx, lx);
-                            two_diff(o.y, mu.y, hy, ly);
-                            two_diff(o.z, mu.z, hz, lz);
-                            const float u0 = fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz));
-                            const float u1 = fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz));
-                            const float u2 = fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz));
-                            const float w0 = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
-                            const float w1 = fmaf(r1.w, d.x, fmaf(r2.x, d.y, r2.y * d.z));
-                            const float w2 = fmaf(r2.z, d.x, fmaf(r2.w, d.y, r3.x * d.z));
-                            const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-                            const float B = fmaf(w0, u0, fmaf(w1, u1, w2 * u2));
-                            ts = -B / A;
-                            if (ts > k.t_near && ts >= tl && ts < th) {
-                                const float ex = fmaf(ts, d.x, hx) + lx, ey = fmaf(ts, d.y, hy) + ly,
-                                            ez = fmaf(ts, d.z, hz) + lz;
-                                const float v0 = fmaf(r1.x, ex, fmaf(r1.y, ey, r1.z * ez));
-                                const float v1 = fmaf(r1.w, ex, fmaf(r2.x, ey, r2.y * ez));
-                                const float v2 = fmaf(r2.z, ex, fmaf(r2.w, ey, r3.x * ez));
-                                const float m2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-                                const float resp = r3.y * expf(-0.5f * m2);
-                                if (resp >= k.alpha_min) {
-                                    hit = true;
-                                    al = fminf(resp, k.alpha_max);
-                                }
+                        gi = __ldg(k.entries + e);
+                        const float4 r1 = __ldg(&k.rec[gi].r1), r2 = __ldg(&k.rec[gi].r2), r3 = __ldg(&k.rec[gi].r3);
+                        float hx, lx, hy, ly, hz, lz;
+                        two_diff(o.x, mu.x, hx, lx);
+                        two_diff(o.y, mu.y, hy, ly);
+                        two_diff(o.z, mu.z, hz, lz);
+                        const float u0 = fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz));
+                        const float u1 = fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz));
+                        const float u2 = fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz));
+                        const float w0 = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
+                        const float w1 = fmaf(r1.w, d.x, fmaf(r2.x, d.y, r2.y * d.z));
+                        const float w2 = fmaf(r2.z, d.x, fmaf(r2.w, d.y, r3.x * d.z));
+                        const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+                        const float B = fmaf(w0, u0, fmaf(w1, u1, w2 * u2));
+                        ts = -B / A;
+                        if (ts > k.t_near && ts >= tl && ts < th) {
+                            const float ex = fmaf(ts, d.x, hx) + lx, ey = fmaf(ts, d.y, hy) + ly,
+                                        ez = fmaf(ts, d.z, hz) + lz;
+                            const float v0 = fmaf(r1.x, ex, fmaf(r1.y, ey, r1.z * ez));
+                            const float v1 = fmaf(r1.w, ex, fmaf(r2.x, ey, r2.y * ez));
+                            const float v2 = fmaf(r2.z, ex, fmaf(r2.w, ey, r3.x * ez));
+                            const float m2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                            const float resp = r3.y * expf(-0.5f * m2);
+                            if (resp >= k.alpha_min) {
+                                hit = true;
+                                al = fminf(resp, k.alpha_max);
                             }
                         }
                     }
+                    __syncwarp();
+                    // drop the evaluated candidates from the queue
+                    if (lane < qn - take) que[lane] = que[lane + take];
+                    qn -= take;
+                    __syncwarp();
                     const unsigned m = __ballot_sync(0xffffffffu, hit);
                     if (hit) {
                         const int pos = n + __popc(m & ((1u << lane) - 1u));
@@ -467,6 +510,18 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
                             }
                             __syncwarp();
                         }
+                    }
+                } else if (n > 1 && n <= 12) {
+                    // few hits: each lane's rank is the number of smaller keys
+                    __syncwarp();
+                    const uint64_t kv = lane < n ? key[lane] : ~0ull;
+                    const float av = lane < n ? alp[lane] : 0.f;
+                    int rank = 0;
+                    for (int j = 0; j < n; ++j) rank += __shfl_sync(0xffffffffu, kv, j) < kv ? 1 : 0;
+                    __syncwarp();
+                    if (lane < n) {
+                        key[rank] = kv;
+                        alp[rank] = av;
                     }
                 } else if (n > 1) {
                     // one hit per lane, bitonic network over the 32 lanes
@@ -518,27 +573,14 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
                     const int stop_lane = stopm ? __ffs(stopm) - 1 : 32;
                     const bool use = on && lane <= stop_lane;
                     const float w = use ? Tb * a : 0.f;
-                    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
                     if (use) {
                         const float4 r3 = __ldg(&k.rec[gh].r3), r4 = __ldg(&k.rec[gh].r4);
-                        c0 = w * r3.z;
-                        c1 = w * r3.w;
-                        c2 = w * r4.x;
+                        L0 = fmaf(w, r3.z, L0);
+                        L1 = fmaf(w, r3.w, L1);
+                        L2 = fmaf(w, r4.x, L2);
+                        Dacc = fmaf(w, th_hit, Dacc);
+                        Wacc += w;
                     }
-                    float wd = w * th_hit, ww = w;
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        c0 += __shfl_xor_sync(0xffffffffu, c0, off);
-                        c1 += __shfl_xor_sync(0xffffffffu, c1, off);
-                        c2 += __shfl_xor_sync(0xffffffffu, c2, off);
-                        wd += __shfl_xor_sync(0xffffffffu, wd, off);
-                        ww += __shfl_xor_sync(0xffffffffu, ww, off);
-                    }
-                    L0 += c0;
-                    L1 += c1;
-                    L2 += c2;
-                    Dacc += wd;
-                    Wacc += ww;
                     const int last = stop_lane < 32 ? stop_lane : min(31, n - cb - 1);
                     T = __shfl_sync(0xffffffffu, Ta, last);
                     if (stop_lane < 32) done = true;
@@ -550,17 +592,38 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
                 splits = 0;
             }
             if (done || t_exit >= t1) break;
-            cell[ax] += step[ax];
-            if (cell[ax] < 0 || cell[ax] >= G.dims[ax]) break;
-            // boundary recomputed from the cell index (no accumulated error)
-            tmax[ax] = (G.origin[ax] + (cell[ax] + (step[ax] > 0 ? 1 : 0)) * G.h - ov[ax]) / dv[ax];
+            // step one cell; the boundary is recomputed from the cell index
+            // (no accumulated error)
+            if (ax == 0) {
+                cx += sx;
+                if (cx < 0 || cx >= gdx) break;
+                tmx = SOP_TNEXT(sx, cx, gox, o.x, d.x);
+            } else if (ax == 1) {
+                cy += sy;
+                if (cy < 0 || cy >= gdy) break;
+                tmy = SOP_TNEXT(sy, cy, goy, o.y, d.y);
+            } else {
+                cz += sz;
+                if (cz < 0 || cz >= gdz) break;
+                tmz = SOP_TNEXT(sz, cz, goz, o.z, d.z);
+            }
             t_enter = t_exit;
         }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        L0 += __shfl_xor_sync(0xffffffffu, L0, off);
+        L1 += __shfl_xor_sync(0xffffffffu, L1, off);
+        L2 += __shfl_xor_sync(0xffffffffu, L2, off);
+        Dacc += __shfl_xor_sync(0xffffffffu, Dacc, off);
+        Wacc += __shfl_xor_sync(0xffffffffu, Wacc, off);
     }
     if (lane == 0) {
         k.maps[ray] = make_float4(L0, L1, L2, 1.f - T);
         k.depth[ray] = Wacc > 1e-8f ? Dacc / Wacc : 0.f;
     }
+    }  // next ray
+#undef SOP_TNEXT
 }
 
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s)
@@ -612,8 +675,20 @@ cudaError_t launch_bake_trace(const sop_gaussians& g, const sop_atlas& atlas, co
     k.maps = reinterpret_cast<float4*>(ws + L.maps);
     k.depth = reinterpret_cast<float*>(ws + L.depth);
     k.status = reinterpret_cast<int32_t*>(ws + L.bbox) + 6;
+    k.counter = reinterpret_cast<unsigned long long*>(ws + L.bbox + 8 * sizeof(int32_t));
     const int64_t rays = (int64_t)atlas.P * R * R;
-    trace_kernel<<<(unsigned)((rays + kWarpsPerCta - 1) / kWarpsPerCta), kWarpsPerCta * 32, 0, s>>>(k);
+    // persistent grid: as many CTAs as fit on the device at once
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, kWarpsPerCta * 32, 0);
+        resident = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+    }
+    const int64_t need = (rays + kWarpsPerCta - 1) / kWarpsPerCta;
+    const unsigned nb = (unsigned)(need < resident ? need : resident);
+    trace_kernel<<<nb, kWarpsPerCta * 32, 0, s>>>(k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_atlas_pack(reinterpret_cast<const float*>(k.maps), 4, reinterpret_cast<const float*>(k.maps) + 3, 4,

@@ -441,7 +441,7 @@ struct ShadeK {
 // directions; one warp covers 32/LANES points.
 // ---------------------------------------------------------------------------
 template <int DT, int KMAX, int MODE>
-__global__ void __launch_bounds__(256) shade_kernel(const ShadeK a, const int LANES)
+__global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int LANES)
 {
     extern __shared__ float4 s_dirs[];
     for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_dirs[i] = a.dirs[i];
@@ -534,13 +534,13 @@ __global__ void __launch_bounds__(256) shade_kernel(const ShadeK a, const int LA
         if (MODE == SOP_MODE_SHADE) {
             float3 h = w + wo;
             const float hl2 = dot3(h, h);
-            h = hl2 > 1e-30f ? (1.f / sqrtf(hl2)) * h : n;
+            h = hl2 > 1e-30f ? rsqrtf(hl2) * h : n;
             const float NdotH = dot3(n, h), VdotH = dot3(wo, h);
             const float3 cr = cross3(n, h);
             const float sin2 = dot3(cr, cr);
             const float den = NdotH * NdotH * a2 + sin2;
-            const float D = a2 / (kPi * den * den);
-            const float spec = D * specV / (NdotL * (1.f - kk) + kk);
+            const float D = __fdividef(a2, kPi * den * den);
+            const float spec = __fdividef(D * specV, NdotL * (1.f - kk) + kk);
             const float x1 = 1.f - VdotH, x2 = x1 * x1, fc = x2 * x2 * x1;
             const float f0 = kd.x + spec * (F0.x + (1.f - F0.x) * fc);
             const float f1 = kd.y + spec * (F0.y + (1.f - F0.y) * fc);

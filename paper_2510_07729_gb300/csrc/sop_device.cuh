@@ -38,7 +38,8 @@ __device__ __forceinline__ float3 load3(const float* p, int64_t i)
 __device__ __forceinline__ float2 oct_encode(float3 d)
 {
     float l1 = fabsf(d.x) + fabsf(d.y) + fabsf(d.z);
-    float px = d.x / l1, py = d.y / l1;
+    const float inv = __fdividef(1.f, l1);
+    float px = d.x * inv, py = d.y * inv;
     if (d.z < 0.f) {
         float qx = (1.f - fabsf(py)) * (px >= 0.f ? 1.f : -1.f);
         float qy = (1.f - fabsf(px)) * (py >= 0.f ? 1.f : -1.f);
