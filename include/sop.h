@@ -207,6 +207,27 @@ sop_status sop_query_shade(const float* x, const float* n, const float* wo, cons
                            int32_t We, const float* dirs_local, const sop_shade_params* params, float* out,
                            int32_t* out_idx, float* out_w, void* ws, size_t ws_bytes, void* stream);
 
+/* Adjoint of sop_query_shade in SOP_MODE_SHADE (the environment, the
+ * materials and the SOP textures are the learnable quantities of the
+ * paper's decomposition step, Sec. 3.1.2; Eq. 3-6). Given grad_out = dL/dC
+ * [M,3], writes (overwriting) g_albedo [M,3], g_rough [M], g_metal [M] and
+ * g_normal [M,3] (w.r.t. the raw, unnormalised input normal), and ADDS
+ * dL/d(environment texel) into g_env [He,We,3] and dL/d(probe texel) into
+ * g_maps [P,R,R,4] (compact maps: RGB radiance then occlusion, border texels
+ * folded onto the texels they copy; 16-byte aligned). The caller zeroes the
+ * accumulated arrays. Every per-direction term is recomputed rather than
+ * stored; the K nearest probes do not depend on the differentiated inputs.
+ * Bilinear fetches are piecewise linear: at a texel edge the gradient is
+ * one of the one-sided derivatives. Accumulation uses float atomics, so sums
+ * are order-nondeterministic. SOP_MODE_SHADOW returns SOP_ERR_UNSUPPORTED.
+ * Same workspace as sop_query_shade. Asynchronous. */
+sop_status sop_query_shade_backward(const float* x, const float* n, const float* wo, const float* albedo,
+                                    const float* rough, const float* metal, int64_t M, const sop_atlas* atlas,
+                                    const float* env, int32_t He, int32_t We, const float* dirs_local,
+                                    const sop_shade_params* params, const float* grad_out, float* g_albedo,
+                                    float* g_rough, float* g_metal, float* g_normal, float* g_env, float* g_maps,
+                                    void* ws, size_t ws_bytes, void* stream);
+
 /* Allocation-free sop_query_shade. No counterpart in the paper: this entry
  * point exists for callers that cannot allocate device memory, for example
  * code running where cudaMalloc is unavailable or forbidden (a host

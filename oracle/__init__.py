@@ -240,7 +240,9 @@ def query_shade_grad(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_o
                      spec=0.5, dirs=None, snap_key=None):
     """Analytic FP64 gradients of sum(grad_out * C) (SHADE mode). Returns a
     dict: albedo [M,3], rough [M], metal [M], normal [M,3] (w.r.t. the raw
-    normal), env [He,We,3], maps_rgb [P,R,R,3], maps_occ [P,R,R]."""
+    normal), env [He,We,3], maps_rgb [P,R,R,3], maps_occ [P,R,R], and the
+    sums of the magnitudes of the per-direction terms of each per-point
+    gradient (abs_albedo, abs_rough, abs_metal, abs_normal)."""
     x, n, wo, albedo, rough, metal = (_f32(v) for v in (x, n, wo, albedo, rough, metal))
     pp, mr, mo, env = _f32(probe_pos), _f32(maps_rgb), _f32(maps_occ), _f32(env)
     P, R = mr.shape[0], mr.shape[1]
@@ -248,12 +250,14 @@ def query_shade_grad(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_o
     M = len(x)
     go = _f64(grad_out).reshape(M, 3)
     out = dict(albedo=np.empty((M, 3)), rough=np.empty(M), metal=np.empty(M), normal=np.empty((M, 3)),
-               env=np.zeros((He, We, 3)), maps_rgb=np.zeros((P, R, R, 3)), maps_occ=np.zeros((P, R, R)))
+               env=np.zeros((He, We, 3)), maps_rgb=np.zeros((P, R, R, 3)), maps_occ=np.zeros((P, R, R)),
+               abs_albedo=np.empty((M, 3)), abs_rough=np.empty(M), abs_metal=np.empty(M), abs_normal=np.empty(M))
     dp = None if dirs is None else _f64(dirs)
     sk = snap_key_for() if snap_key is None else snap_key
     lib().orc_query_shade_grad(
         C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal), C.c_int32(P), _p(pp), C.c_int32(R),
         _p(mr), _p(mo), C.c_int32(He), C.c_int32(We), _p(env), C.c_int32(S), None if dp is None else _p(dp),
         C.c_int32(K), C.c_double(spec), C.c_uint64(sk), _p(go), _p(out["albedo"]), _p(out["rough"]),
-        _p(out["metal"]), _p(out["normal"]), _p(out["env"]), _p(out["maps_rgb"]), _p(out["maps_occ"]))
+        _p(out["metal"]), _p(out["normal"]), _p(out["env"]), _p(out["maps_rgb"]), _p(out["maps_occ"]),
+        _p(out["abs_albedo"]), _p(out["abs_rough"]), _p(out["abs_metal"]), _p(out["abs_normal"]))
     return out

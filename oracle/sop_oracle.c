@@ -719,7 +719,8 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
                           const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We, const float* env,
                           int32_t S, const double* dirs, int32_t K, double spec, uint64_t snap_key,
                           const double* grad_out, double* g_albedo, double* g_rough, double* g_metal,
-                          double* g_normal, double* g_env, double* g_maps_rgb, double* g_maps_occ)
+                          double* g_normal, double* g_env, double* g_maps_rgb, double* g_maps_occ,
+                          double* abs_albedo, double* abs_rough, double* abs_metal, double* abs_normal)
 {
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1) * K);
     double* W = (double*)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1) * K);
@@ -743,6 +744,9 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
         double F0[3];
         for (int c = 0; c < 3; ++c) F0[c] = 0.08 * spec * (1.0 - mt) + a[c] * mt;
         double ga[3] = {0, 0, 0}, gr = 0, gm = 0, gn[3] = {0, 0, 0}, gW[32];
+        /* sums of the magnitudes of the per-direction terms (the scale of the
+         * rounding error of each gradient, which may cancel to near zero) */
+        double sa[3] = {0, 0, 0}, sr = 0, sm = 0, sn = 0;
         for (int k = 0; k < K; ++k) gW[k] = 0.0;
         const double sc = 2.0 * M_PI / S;
         for (int32_t i = 0; i < S; ++i) {
@@ -803,9 +807,15 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
             double gOt = 0, gLin[3], gLd[3];
             for (int c = 0; c < 3; ++c) {
                 double u = gam[c] * Lmix[c];
-                ga[c] += u * ((1.0 - mt) / M_PI + spec_t * (1.0 - fc) * mt);
-                gm += u * (-a[c] / M_PI + spec_t * (1.0 - fc) * (-0.08 * spec + a[c]));
-                gr += u * dspec_dr * F[c];
+                double ta = u * ((1.0 - mt) / M_PI + spec_t * (1.0 - fc) * mt);
+                double tm = u * (-a[c] / M_PI + spec_t * (1.0 - fc) * (-0.08 * spec + a[c]));
+                double tr = u * dspec_dr * F[c];
+                ga[c] += ta;
+                gm += tm;
+                gr += tr;
+                sa[c] += fabs(ta);
+                sm += fabs(tm);
+                sr += fabs(tr);
                 double fsp = F[c] * G1L * G1V / (4.0 * NdotL * NdotV);
                 GN += u * fsp * (-4.0 * a2 * a2 * NdotH / (M_PI * den * den * den));
                 GS += u * fsp * (-2.0 * a2 / (M_PI * den * den * den));
@@ -864,11 +874,14 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
             double db[3][3] = {{nn[1] * aa, nn[0] * aa, nn[0] * nn[1] * a2n},
                                {0.0, 2.0 * nn[1] * aa, nn[1] * nn[1] * a2n},
                                {0.0, -1.0, 0.0}};
+            double vn[3];
             for (int j = 0; j < 3; ++j) {
                 double v = l[2] * gw[j] + gnd[j];
                 for (int c = 0; c < 3; ++c) v += l[0] * gw[c] * dt[c][j] + l[1] * gw[c] * db[c][j];
                 gn[j] += v;
+                vn[j] = v;
             }
+            sn += sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
         }
         /* blend weights W_k = w_s w_b / sum (Eq. 4-6): w_b moves with n */
         if (key[(size_t)m * K] > snap_key) {
@@ -887,6 +900,7 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
             for (int j = 0; j < K; ++j) {
                 double gu = (gW[j] - gu_dot) / U; /* dL/du_j */
                 for (int c = 0; c < 3; ++c) gn[c] += gu * ws[j] * 0.5 * dh[j][c];
+                sn += fabs(gu * ws[j] * 0.5);
             }
         }
         /* through the normalisation n = n_raw / |n_raw| */
@@ -899,6 +913,12 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
         }
         g_rough[m] = gr;
         g_metal[m] = gm;
+        if (abs_albedo) {
+            for (int c = 0; c < 3; ++c) abs_albedo[3 * m + c] = sa[c];
+            abs_rough[m] = sr;
+            abs_metal[m] = sm;
+            abs_normal[m] = sn / nl;
+        }
     }
     free(mocc);
     free(mrgb);

@@ -238,6 +238,37 @@ sop_status sop_query_shade(const float* x, const float* n, const float* wo, cons
     return cuda_status(sop::launch_shade(a, L, (char*)ws, s), "sop_query_shade (shade)");
 }
 
+sop_status sop_query_shade_backward(const float* x, const float* n, const float* wo, const float* albedo,
+                                    const float* rough, const float* metal, int64_t M, const sop_atlas* atlas,
+                                    const float* env, int32_t He, int32_t We, const float* dirs_local,
+                                    const sop_shade_params* params, const float* grad_out, float* g_albedo,
+                                    float* g_rough, float* g_metal, float* g_normal, float* g_env, float* g_maps,
+                                    void* ws, size_t ws_bytes, void* stream)
+{
+    sop::QueryArgs a;
+    sop::QueryLayout L;
+    sop_status st = query_common(x, n, wo, albedo, rough, metal, M, atlas, env, He, We, dirs_local, params, ws,
+                                 ws_bytes, a, L);
+    if (st != SOP_OK) return st;
+    if (params->mode != SOP_MODE_SHADE)
+        return fail(SOP_ERR_UNSUPPORTED, "sop_query_shade_backward: only SOP_MODE_SHADE has an adjoint");
+    if (M > 0 && (!grad_out || !g_albedo || !g_rough || !g_metal || !g_normal))
+        return fail(SOP_ERR_INVALID_ARG, "a per-point gradient array is NULL");
+    if (!g_env || !g_maps) return fail(SOP_ERR_INVALID_ARG, "g_env / g_maps is NULL");
+    if (!aligned(g_maps, 16)) return fail(SOP_ERR_INVALID_ARG, "g_maps must be 16-byte aligned");
+    a.grad_out = grad_out;
+    a.g_albedo = g_albedo;
+    a.g_rough = g_rough;
+    a.g_metal = g_metal;
+    a.g_normal = g_normal;
+    a.g_env = g_env;
+    a.g_atlas = g_maps;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_status(sop::launch_query_prep(a, L, (char*)ws, s), "sop_query_shade_backward (prep)");
+    if (st != SOP_OK) return st;
+    return cuda_status(sop::launch_adjoint(a, L, (char*)ws, s), "sop_query_shade_backward");
+}
+
 sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* wo, const float* albedo,
                                    const float* rough, const float* metal, int64_t M, const sop_atlas* atlas,
                                    const float* env, int32_t He, int32_t We, const float* dirs_local,

@@ -46,6 +46,7 @@ struct QueryArgs {
 // direction tables (shared by forward and backward).
 cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s);
+cudaError_t launch_adjoint(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_hammersley(int32_t S, float* out3, cudaStream_t s);
 
 // allocation-free query (static device scratch, see query.cu)

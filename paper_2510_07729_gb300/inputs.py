@@ -404,3 +404,16 @@ def subsample(rng, arrays, keys, m):
     n = len(arrays[keys[0]])
     idx = np.sort(rng.choice(n, size=min(m, n), replace=False))
     return idx, {k: np.ascontiguousarray(arrays[k][idx]) for k in keys}
+
+
+def smooth_maps(rng, P, R):
+    """Probe maps that vary slowly with the texel index (random phases per
+    probe): O in [0.2, 0.8], RGB in [0.1, 0.4]."""
+    jj, ii = np.meshgrid(np.arange(R) / R, np.arange(R) / R, indexing="ij")
+    ph = rng.uniform(0, 2 * np.pi, (P, 4, 2))
+    wave = lambda k: np.sin(2 * np.pi * ii[None] + ph[:, k, 0, None, None]) * \
+        np.cos(2 * np.pi * jj[None] + ph[:, k, 1, None, None])  # noqa: E731
+    occ = 0.5 + 0.3 * wave(3)
+    rgb = np.stack([0.25 + 0.15 * wave(c) for c in range(3)], axis=-1)
+    return dict(rgb=rgb.astype(F32), occ=occ.astype(F32),
+                depth=np.full((P, R, R), 0.5, F32))

@@ -76,10 +76,12 @@ def load(build_if_missing: bool = True):
     lib.sop_query_workspace_bytes.restype = sz
     lib.sop_query_shade.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
                                     C.POINTER(ShadeParams), vp, vp, vp, vp, sz, vp]
+    lib.sop_query_shade_backward.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
+                                             C.POINTER(ShadeParams), vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.sop_query_shade_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
                                             C.POINTER(ShadeParams), vp, vp, vp, vp]
     for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_query_shade",
-                 "sop_query_shade_noalloc"):
+                 "sop_query_shade_backward", "sop_query_shade_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -281,6 +283,63 @@ def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MO
     if return_idx:
         return out, idx, w
     return out
+
+
+def query_shade_backward(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, grad_out, g_env=None, g_maps=None,
+                         specular=0.5, eps_snap=1e-6, dirs_local=None, workspace=None):
+    """sop_query_shade_backward (SHADE mode). Returns a dict of gradients:
+    albedo, rough, metal, normal (fresh tensors) and env [He,We,3], maps
+    [P,R,R,4] (accumulated into g_env / g_maps when given, else zeros)."""
+    lib = load()
+    M = x.shape[0]
+    He, We = env.shape[0], env.shape[1]
+    dev = x.device
+    P, R = atlas.P, atlas.R
+    sp = ShadeParams(K, S, MODE_SHADE, specular, eps_snap)
+    d = atlas.c()
+    g = dict(albedo=torch.empty((M, 3), dtype=torch.float32, device=dev),
+             rough=torch.empty((M,), dtype=torch.float32, device=dev),
+             metal=torch.empty((M,), dtype=torch.float32, device=dev),
+             normal=torch.empty((M, 3), dtype=torch.float32, device=dev),
+             env=g_env if g_env is not None else torch.zeros((He, We, 3), dtype=torch.float32, device=dev),
+             maps=g_maps if g_maps is not None else torch.zeros((P, R, R, 4), dtype=torch.float32, device=dev))
+    _f32(grad_out, (M, 3))
+    _f32(g["env"], (He, We, 3))
+    _f32(g["maps"], (P, R, R, 4))
+    need = int(lib.sop_query_workspace_bytes(C.byref(d), M, C.byref(sp), He, We))
+    ws = workspace if workspace is not None else _ws(need, dev)
+    _check(lib.sop_query_shade_backward(
+        _ptr(x), _ptr(n), _ptr(wo), _ptr(albedo), _ptr(rough), _ptr(metal), M, C.byref(d), _ptr(env), He, We,
+        None if dirs_local is None else _f32(dirs_local, (S, 3)), C.byref(sp), _ptr(grad_out), _ptr(g["albedo"]),
+        _ptr(g["rough"]), _ptr(g["metal"]), _ptr(g["normal"]), _ptr(g["env"]), _ptr(g["maps"]), _ptr(ws),
+        ws.numel(), _stream()))
+    return g
+
+
+class SopQueryShade(torch.autograd.Function):
+    """Differentiable SOP query + shade (SHADE mode) over compact probe maps.
+
+    forward(x, n, wo, albedo, rough, metal, maps [P,R,R,4] (RGB, O), env
+    [He,We,3], probe_pos [P,3], K, S) packs the maps into a float32 atlas and
+    shades; backward calls the hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, x, n, wo, albedo, rough, metal, maps, env, probe_pos, K, S):
+        P, R = maps.shape[0], maps.shape[1]
+        at = make_atlas(probe_pos, R, with_depth=False)
+        m = maps.contiguous()
+        atlas_pack(m[..., :3].contiguous(), m[..., 3].contiguous(), None, at)
+        out = query_shade(x, n, wo, albedo, rough, metal, at, env, K, S)
+        ctx.save_for_backward(x, n, wo, albedo, rough, metal, env)
+        ctx.at, ctx.K, ctx.S = at, K, S
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        x, n, wo, albedo, rough, metal, env = ctx.saved_tensors
+        g = query_shade_backward(x, n, wo, albedo, rough, metal, ctx.at, env, ctx.K, ctx.S,
+                                 grad_out.contiguous().float())
+        return None, g["normal"], None, g["albedo"], g["rough"], g["metal"], g["maps"], g["env"], None, None, None
 
 
 def query_shade_noalloc(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MODE_SHADE, specular=0.5,

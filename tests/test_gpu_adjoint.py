@@ -1,0 +1,182 @@
+"""GPU parity of the hand-written adjoint of query/shade (SHADE mode)
+against the FP64 oracle's analytic adjoint (itself pinned by finite
+differences in test_oracle_grad.py), through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2510_07729_gb300 import inputs as I
+from tests.tolerance import assert_close
+
+pytestmark = pytest.mark.gpu
+KEYS = ("x", "n", "wo", "albedo", "rough", "metal")
+
+
+@pytest.fixture(scope="module")
+def sop():
+    from paper_2510_07729_gb300 import sop as S
+    S.load()
+    return S
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def atlas(sop, pp, maps):
+    R = maps["occ"].shape[1]
+    at = sop.make_atlas(cuda(pp), R)
+    sop.atlas_pack(cuda(maps["rgb"]), cuda(maps["occ"]), None, at)
+    return at
+
+
+def gpu_grads(sop, pts, at, env, K, S, go):
+    g = sop.query_shade_backward(*[cuda(pts[k]) for k in KEYS], at, cuda(env), K, S, cuda(go.astype(np.float32)))
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in g.items()}
+
+
+def orc_grads(orc, pts, pp, maps, env, K, S, go):
+    return orc.query_shade_grad(*[pts[k] for k in KEYS], pp, maps["rgb"], maps["occ"], env, K, S,
+                                go.astype(np.float32).astype(np.float64))
+
+
+def tilted(pts, rng):
+    """View directions off the normal so every BRDF term is exercised."""
+    M = len(pts["n"])
+    wo = pts["n"] + 0.4 * rng.standard_normal((M, 3)).astype(np.float32)
+    wo /= np.linalg.norm(wo, axis=1, keepdims=True)
+    ok = np.sum(wo * pts["n"], 1) > 0.2
+    return dict(pts, wo=np.where(ok[:, None], wo, pts["n"]).astype(np.float32))
+
+
+def maps_of(g):
+    return np.concatenate([g["maps_rgb"], g["maps_occ"][..., None]], axis=-1)
+
+
+# A per-point gradient is a sum over light directions of terms that can
+# cancel (widening the GGX lobe lowers its peak and raises its tail), and
+# each term is evaluated at an FP32 direction whose angular error (~1e-6 rad)
+# a sharp lobe (alpha = r^2 >= 0.01) amplifies by up to ~2/alpha: so beside
+# the relative bound each element may also differ by a fraction of the sum of
+# the magnitudes of its terms, which the oracle reports.
+TERM_FRAC = 2e-4
+
+
+def test_adjoint_smooth_inputs_strict(sop, orc):
+    """Smooth environment and smooth probe maps: every gradient within
+    1e-4 relative (floors: 1e-3 of the mean magnitude per point, 1e-6 of
+    the largest entry for the atomically summed env/probe gradients), plus
+    TERM_FRAC of the sum of its terms' magnitudes."""
+    c = I.make_tiny()
+    rng = np.random.default_rng(50)
+    pts = tilted({k: c[k] for k in KEYS}, rng)
+    maps = I.smooth_maps(rng, 64, 8)
+    go = rng.standard_normal((len(pts["x"]), 3))
+    at = atlas(sop, c["probe_pos"], maps)
+    g = gpu_grads(sop, pts, at, c["env"], 4, 64, go)
+    o = orc_grads(orc, pts, c["probe_pos"], maps, c["env"], 4, 64, go)
+    for k in ("albedo", "rough", "metal"):
+        assert_close(g[k], o[k], rtol=1e-4, absolute=TERM_FRAC * o["abs_" + k], what=k)
+    assert_close(g["normal"], o["normal"], rtol=1e-4, absolute=TERM_FRAC * o["abs_normal"][:, None], what="normal")
+    assert_close(g["env"], o["env"], rtol=1e-4, floor=0, absolute=1e-6 * np.abs(o["env"]).max(), what="env")
+    om = maps_of(o)
+    assert_close(g["maps"], om, rtol=1e-4, floor=0, absolute=1e-6 * np.abs(om).max(), what="maps")
+
+
+def diff_subset(n=4096, seed=51):
+    c = I.make_diff()
+    sel, pts = I.subsample(np.random.default_rng(seed), c, list(KEYS), n)
+    return c, sel, pts
+
+
+def test_adjoint_rough_workload_subset(sop, orc):
+    """The differentiation workload (rough HDR environment, independent
+    per-texel maps, K=8, S=128) on 4,096 points. Materials, environment and
+    probe gradients within 2e-3 relative: the same FP32 direction
+    conditioning as the forward pass (up to ~1e-4 relative there) enters
+    here multiplied by the texture slopes. Normal gradients cross bilinear
+    kinks whenever an FP32 direction lands on the other side of a texel
+    edge (the derivative is one-sided there), so they are checked by
+    distribution: median within 1e-4, 99% within 1e-3."""
+    c, sel, pts = diff_subset()
+    rng = np.random.default_rng(52)
+    maps = I.synthetic_maps(rng, 4096, 16)
+    go = (rng.uniform(0, 1, (len(sel), 3)) - c["target"][sel]).astype(np.float64)
+    at = atlas(sop, c["probe_pos"], maps)
+    g = gpu_grads(sop, pts, at, c["env"], 8, 128, go)
+    o = orc_grads(orc, pts, c["probe_pos"], maps, c["env"], 8, 128, go)
+    for k in ("albedo", "rough", "metal"):
+        assert_close(g[k], o[k], rtol=2e-3, absolute=TERM_FRAC * o["abs_" + k], what=k)
+    assert_close(g["env"], o["env"], rtol=2e-3, floor=0, absolute=1e-5 * np.abs(o["env"]).max(), what="env")
+    om = maps_of(o)
+    assert_close(g["maps"], om, rtol=2e-3, floor=0, absolute=1e-5 * np.abs(om).max(), what="maps")
+    rel = np.linalg.norm(g["normal"] - o["normal"], axis=1) / np.maximum(
+        np.linalg.norm(o["normal"], axis=1), 1e-3 * np.linalg.norm(o["normal"], axis=1).mean())
+    print("normal grad rel err: median %.2e p99 %.2e max %.2e" % (np.median(rel), np.percentile(rel, 99), rel.max()))
+    assert np.median(rel) < 1e-4
+    assert np.percentile(rel, 99) < 1e-3
+
+
+def test_adjoint_full_size_identities(sop, orc):
+    """All 1,586,082 points of the 4-view differentiation workload. The
+    loss <g, C> is linear in the environment and in the probe radiance and
+    affine in the probe occlusion, so <dL/d env, env> = <g, C(L_in = 0)>,
+    <dL/d L_in, L_in> = <g, C(env = 0)> and <dL/d O, O> = <g, C - C(O = 0)>
+    at any size. Per-point gradients of 4,096 sampled points are compared
+    with the oracle (they depend on their own point only)."""
+    c = I.make_diff()
+    rng = np.random.default_rng(53)
+    maps = I.synthetic_maps(rng, 4096, 16)
+    M = len(c["x"])
+    go = (rng.uniform(0, 1, (M, 3)) - c["target"]).astype(np.float32)
+    pts = [cuda(c[k]) for k in KEYS]
+    env = cuda(c["env"])
+
+    def fwd(mp, e):
+        at = atlas(sop, c["probe_pos"], mp)
+        return sop.query_shade(*pts, at, e, 8, 128).double()
+
+    at = atlas(sop, c["probe_pos"], maps)
+    g = sop.query_shade_backward(*pts, at, env, 8, 128, cuda(go))
+    gt = cuda(go).double()
+    zero_rgb = dict(maps, rgb=np.zeros_like(maps["rgb"]))
+    zero_occ = dict(maps, occ=np.zeros_like(maps["occ"]))
+    C = fwd(maps, env)
+    lhs_env = (g["env"].double() * env.double()).sum().item()
+    rhs_env = (gt * fwd(zero_rgb, env)).sum().item()
+    lhs_rgb = (g["maps"][..., :3].double() * cuda(maps["rgb"]).double()).sum().item()
+    rhs_rgb = (gt * fwd(maps, torch.zeros_like(env))).sum().item()
+    lhs_occ = (g["maps"][..., 3].double() * cuda(maps["occ"]).double()).sum().item()
+    rhs_occ = (gt * (C - fwd(zero_occ, env))).sum().item()
+    for lhs, rhs, what in ((lhs_env, rhs_env, "env"), (lhs_rgb, rhs_rgb, "L_in"), (lhs_occ, rhs_occ, "O")):
+        assert lhs == pytest.approx(rhs, rel=2e-4), what
+    sel = np.sort(np.random.default_rng(54).choice(M, 4096, replace=False))
+    sub = {k: c[k][sel] for k in KEYS}
+    o = orc_grads(orc, sub, c["probe_pos"], maps, c["env"], 8, 128, go[sel].astype(np.float64))
+    for k in ("albedo", "rough", "metal"):
+        assert_close(g[k].cpu().numpy()[sel], o[k], rtol=2e-3, absolute=TERM_FRAC * o["abs_" + k], what=k)
+
+
+def test_autograd_function(sop):
+    """torch.autograd through SopQueryShade gives the adjoint's gradients."""
+    c = I.make_tiny()
+    rng = np.random.default_rng(55)
+    maps = I.smooth_maps(rng, 64, 8)
+    m4 = np.concatenate([maps["rgb"], maps["occ"][..., None]], axis=-1)
+    x, n, wo, a, r, mt = (cuda(c[k]) for k in KEYS)
+    n = n.clone().requires_grad_(True)
+    a = a.clone().requires_grad_(True)
+    r = r.clone().requires_grad_(True)
+    mt = mt.clone().requires_grad_(True)
+    mp = cuda(m4).requires_grad_(True)
+    env = cuda(c["env"]).requires_grad_(True)
+    out = sop.SopQueryShade.apply(x, n, wo, a, r, mt, mp, env, cuda(c["probe_pos"]), 4, 64)
+    target = torch.rand_like(out)
+    loss = 0.5 * ((out - target) ** 2).sum()
+    loss.backward()
+    at = atlas(sop, c["probe_pos"], maps)
+    g = sop.query_shade_backward(x, n.detach(), wo, a.detach(), r.detach(), mt.detach(), at, env.detach(), 4, 64,
+                                 (out - target).detach().contiguous())
+    for t, k in ((a, "albedo"), (r, "rough"), (mt, "metal"), (n, "normal"), (env, "env"), (mp, "maps")):
+        assert torch.allclose(t.grad, g[k], rtol=1e-5, atol=1e-7 * g[k].abs().max().item()), k
