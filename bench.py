@@ -124,6 +124,65 @@ def load_workload(name):
 # environment uv 2 atan2 (~40) + bilinear 3x4 FMA (24) + weights 8, BRDF
 # (half vector 12, dots 15, D 8, G 4, Fresnel 12, combine 12) and the
 # accumulation 9.
+# algorithmic FP32 work of the bake: an exact ray-Gaussian evaluation (the
+# probe offset split into two parts 18, M*offset 15, M*direction 15, A and B
+# 10, t* 2, closest point 9, M*point 15, m^2 5, response 4: ~93) and one
+# composited hit (1 - alpha, transmittance, weight, 3 colour, depth and
+# weight sums: ~15)
+FLOP_PER_EVAL = 93
+FLOP_PER_COMPOSITE = 15
+
+
+def traffic_for(kernel, P):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = tab.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2510_07729_gb300", "csrc", e["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if h != e.get("source_sha256_16"):
+        return None
+    return round(e["bytes_per_probe"] * P) if "bytes_per_probe" in e else e.get("bytes")
+
+
+def chosen_variant(sop, g, ppos, R, pargs, env, K, S, mode, out_ref, flush, steps):
+    """The reduced-precision atlas (FP16 RGBO, FP32 accumulation): query
+    throughput and its relative L1 difference from the FP32-atlas output."""
+    import torch
+    at16 = sop.make_atlas(ppos, R, rgbo_dtype=sop.SOP_F16, depth_dtype=sop.SOP_F16)
+    sop.bake(g, at16)
+    M = pargs[0].shape[0]
+    out = torch.empty((M, 3), dtype=torch.float32, device=pargs[0].device)
+    ws = torch.empty(sop.query_workspace_bytes(at16, M, K, S, env.shape[0], env.shape[1], mode), dtype=torch.uint8,
+                     device=pargs[0].device)
+    for _ in range(3):
+        sop.query_shade(*pargs, at16, env, K, S, mode=mode, out=out, workspace=ws)
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sop.query_shade(*pargs, at16, env, K, S, mode=mode, out=out, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    rel = ((out - out_ref).abs().sum() / out_ref.abs().sum()).item()
+    return {"atlas": "fp16 RGBO + fp16 depth, fp32 accumulation", "query_ms": round(ms, 4),
+            "query_point_dirs_per_s": round(M * S / (ms * 1e-3), 1), "rel_l1_vs_fp32_atlas": rel}
+
+
 def flop_per_point_dir(K, mode):
     f = 15 + 12 + 10 + K * (32 + 4) + 40 + 24 + 8 + 9
     if mode == 0:
@@ -175,10 +234,14 @@ def main():
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
+    bws = sop.BakeWorkspace(len(W["gauss"]["mean"]), dev)
+
     def step(evs):
         if do_bake:
             evs[0].record(stream)
-            sop.bake(g, atlas)
+            sop.bake_bin(g, bws)
+            evs[4].record(stream)
+            sop.bake_trace(g, atlas, bws)
             evs[1].record(stream)
         if do_query:
             evs[2].record(stream)
@@ -187,7 +250,7 @@ def main():
 
     for _ in range(args.warmup):
         flush.fill_(1)
-        step([ev() for _ in range(4)])
+        step([ev() for _ in range(5)])
     torch.cuda.synchronize()
 
     gpu_index = torch.cuda.get_device_properties(dev).index if hasattr(
@@ -202,7 +265,7 @@ def main():
     with ClockSampler(smi_index) as clk:
         for _ in range(args.steps):
             flush.fill_(1)  # L2 flush between timed steps (outside the step events)
-            evs = [ev() for _ in range(4)]
+            evs = [ev() for _ in range(5)]
             step(evs)
             records.append(evs)
         torch.cuda.synchronize()
@@ -212,6 +275,7 @@ def main():
     t_wall = time.perf_counter() - t_wall0
 
     t_bake = [r[0].elapsed_time(r[1]) for r in records] if do_bake else [0.0]
+    t_trace = [r[4].elapsed_time(r[1]) for r in records] if do_bake else [0.0]
     t_query = [r[2].elapsed_time(r[3]) for r in records] if do_query else [0.0]
     ms_step = float(np.sum(t_bake) + np.sum(t_query)) / args.steps
     if world > 1:
@@ -234,15 +298,34 @@ def main():
     if not args.no_e2e and args.part == "step":
         e2e = measure_e2e(args, W, P, dev, sop, flush)
 
-    # roofline of the query/shade kernel, measured live on its stream
-    roof = None
+    # rooflines, from the timed region: the bake's trace kernel (the step's
+    # dominant kernel) and the query/shade kernel
+    roof = roof_q = None
+    peak_fp32 = N_SMS * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    if do_bake:
+        n_eval, n_comp, status = sop.bake_stats(bws)
+        fl = n_eval * FLOP_PER_EVAL + n_comp * FLOP_PER_COMPOSITE
+        mt = float(np.mean(t_trace))
+        ach = fl / (mt * 1e-3) / 1e12
+        roof = {"kernel": "trace_kernel (sop_bake_trace)", "bound": "alu", "achieved": round(ach, 3),
+                "peak": round(peak_fp32, 1), "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
+                "traffic": traffic_for("trace_kernel", P),
+                "work": {"exact_evaluations": n_eval, "composited_hits": n_comp, "status_bits": status,
+                         "flop_per_evaluation": FLOP_PER_EVAL, "flop_per_composite": FLOP_PER_COMPOSITE},
+                "ms": round(mt, 4),
+                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
     if do_query:
         fl = flop_per_point_dir(K, mode) * pd
         ach = fl / (mq * 1e-3) / 1e12
-        peak = N_SMS * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
-        roof = {"kernel": "shade_kernel (sop_query_shade call)", "bound": "alu", "achieved": round(ach, 2),
-                "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
-                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
+        roof_q = {"kernel": "shade_kernel (sop_query_shade call)", "bound": "alu", "achieved": round(ach, 3),
+                  "peak": round(peak_fp32, 1), "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
+                  "traffic": traffic_for("shade_kernel", P),
+                  "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
+        if roof is None:
+            roof = roof_q
+    chosen = None
+    if do_query and args.part == "step":
+        chosen = chosen_variant(sop, g, ppos, R, pargs, env, K, S, mode, out, flush, args.steps)
 
     clocks = clk.summary()
     line = {
@@ -269,6 +352,8 @@ def main():
         "gpu_launches": launches_per_step(do_bake, do_query, P, R) * args.steps,
         "clocks": clocks,
         "roofline": roof,
+        "roofline_query": roof_q,
+        "chosen": chosen,
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.part == "step":

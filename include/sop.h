@@ -156,7 +156,8 @@ sop_status sop_atlas_pack(const float* maps_rgb, const float* maps_occ, const fl
  * Asynchronous. */
 sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream);
 
-/* Workspace bytes for sop_bake on n Gaussians and P probes of side R. */
+/* Workspace bytes for sop_bake / sop_bake_bin / sop_bake_trace on n
+ * Gaussians (the size does not depend on P or R; they are only checked). */
 size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R);
 
 /* Bake every texel of every probe of `atlas` (positions atlas->probe_pos)
@@ -166,13 +167,31 @@ size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R);
  * index) order: T <- T (1 - alpha), L += T_before alpha rgb, D accumulates
  * T_before alpha t*. Outputs O = 1 - T, L_in = L, D = sum(T alpha t*) /
  * sum(T alpha) (0 when nothing is hit).
- * Implementation: Gaussians are binned by their alpha_min bounding spheres
- * into a uniform grid that each texel ray walks front to back.
- * SYNCHRONISES `stream` once, after binning, to size the cell lists: it
- * returns SOP_ERR_WORKSPACE (message gives the bytes needed) when ws_bytes is
- * too small for this scene. Not capturable in a CUDA graph. */
+ * Implementation: Gaussians are binned by the bounding boxes of their
+ * alpha_min ellipsoids into a uniform grid that each texel ray walks front
+ * to back. Equivalent to sop_bake_bin followed by sop_bake_trace: it
+ * SYNCHRONISES `stream` once, after binning, and returns SOP_ERR_WORKSPACE
+ * (the message gives the bytes needed) when ws_bytes is too small for this
+ * scene's cell lists. Not capturable in a CUDA graph. */
 sop_status sop_bake(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
                     size_t ws_bytes, void* stream);
+
+/* First half of sop_bake: bin the Gaussians into the grid kept in `ws`.
+ * Synchronises `stream` once (see sop_bake). */
+sop_status sop_bake_bin(const sop_gaussians* g, const sop_bake_params* params, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/* Second half of sop_bake: trace every texel of `atlas` through the grid
+ * that sop_bake_bin left in `ws` (same g, params and ws_bytes). May be called
+ * any number of times, for any probe set, after one binning. Asynchronous. */
+sop_status sop_bake_trace(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
+                          size_t ws_bytes, void* stream);
+
+/* Work counters of the last sop_bake_trace on `ws` (synchronises stream):
+ * out[0] = exact ray-Gaussian evaluations, out[1] = composited hits,
+ * out[2] = status bits (bit 0: a grid cell held more hits with equal t* than
+ * the hit buffer; that cell's later hits were dropped). */
+sop_status sop_bake_stats(const void* ws, size_t ws_bytes, int64_t n_gauss, int64_t* out, void* stream);
 
 /* Workspace bytes for sop_query_shade / sop_query_shade_backward on M
  * points with this atlas (its P, R and rgbo_dtype) and a He x We

@@ -36,8 +36,9 @@ struct GRec {
 };
 
 constexpr float kMarginRel = 1e-4f;
+constexpr int kMaxR = 64;
 
-BakeLayout bake_layout(int64_t N, int32_t P, int32_t R, int64_t entries_cap)
+BakeLayout bake_layout(int64_t N, int64_t entries_cap)
 {
     BakeLayout L{};
     L.cells_cap = N / 2 < 4096 ? 4096 : (N / 2 > (1 << 23) ? (1 << 23) : N / 2);
@@ -45,12 +46,11 @@ BakeLayout bake_layout(int64_t N, int32_t P, int32_t R, int64_t entries_cap)
     size_t o = 0;
     L.hdr = o;        o = align256(o + sizeof(GaussGrid));
     L.bbox = o;       o = align256(o + 16 * sizeof(int32_t));
+    L.stats = o;      o = align256(o + 4 * sizeof(unsigned long long));
     L.rec = o;        o = align256(o + sizeof(GRec) * (size_t)(N > 0 ? N : 1));
     L.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)(L.cells_cap + 1));
     L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
-    L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)R * R);
-    L.maps = o;       o = align256(o + sizeof(float4) * (size_t)P * R * R);
-    L.depth = o;      o = align256(o + sizeof(float) * (size_t)P * R * R);
+    L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)kMaxR * kMaxR);
     L.entries = o;    o = align256(o + sizeof(int32_t) * (size_t)L.entries_cap);
     L.ent_sph = o;    o = align256(o + sizeof(float4) * (size_t)L.entries_cap);
     L.total = o;
@@ -69,7 +69,7 @@ __global__ void bbox_init_kernel(int32_t* bbox)
 {
     if (threadIdx.x < 3) bbox[threadIdx.x] = f2o(FLT_MAX);
     else if (threadIdx.x < 6) bbox[threadIdx.x] = f2o(-FLT_MAX);
-    else if (threadIdx.x < 12) bbox[threadIdx.x] = 0;  // [6]: trace status word, [8..9]: ray counter
+    else if (threadIdx.x < 8) bbox[threadIdx.x] = 0;  // [6]: binning status word
 }
 
 // Per-Gaussian record + bounding box of the (margin-expanded) spheres.
@@ -301,10 +301,13 @@ struct TraceK {
     const float* probe_pos;
     int32_t P, R;
     float t_near, alpha_min, alpha_max, t_stop;
-    float4* maps;   // [P][R][R] (L.rgb, O)
-    float* depth;   // [P][R][R]
-    int32_t* status;  // device status word: bit 0 = a cell window could not be split
-    unsigned long long* counter;  // next texel ray to trace
+    void* rgbo;       // atlas [P][R+2][R+2] in rgbo_dtype (interior written here)
+    void* depth;      // atlas depth plane or NULL
+    int32_t rgbo_dtype, depth_dtype;
+    float inv_depth_scale;
+    // stats[0]: next texel ray to trace; [1]: exact evaluations; [2]:
+    // composited hits; [3] bit 0: a cell window could not be split
+    unsigned long long* stats;
 };
 
 constexpr int kWarpsPerCta = 8;
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
     // so long rays (escaping the object) do not hold up short ones
     for (;;) {
     unsigned long long rr = 0;
-    if (lane == 0) rr = atomicAdd(k.counter, 1ull);
+    if (lane == 0) rr = atomicAdd(k.stats, 1ull);
     const int64_t ray = (int64_t)__shfl_sync(0xffffffffu, rr, 0);
     if (ray >= total) break;
     const int p = (int)(ray / RR), t = (int)(ray % RR);
@@ -348,6 +351,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
     // per-lane partial sums of the composited terms, reduced once per ray
     float T = 1.f, L0 = 0.f, L1 = 0.f, L2 = 0.f, Dacc = 0.f, Wacc = 0.f;
     bool done = false;
+    int n_eval = 0, n_comp = 0;  // warp-uniform work counters
 
     // grid box entry/exit (slab test), per axis in scalars so that nothing
     // is indexed by a run-time axis (which would put it in local memory)
@@ -423,6 +427,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
                     }
                     // exact responses of up to 32 queued candidates, one per lane
                     const int take = qn < 32 ? qn : 32;
+                    n_eval += take;
                     bool hit = false;
                     float ts = 0.f, al = 0.f;
                     int32_t gi = 0;
@@ -477,7 +482,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
                 if (n > kHitCap) {
                     // too many hits in this window: halve it and rescan
                     if (++splits > 40 || !(th > tl)) {
-                        if (lane == 0) atomicOr(k.status, 1);
+                        if (lane == 0) atomicOr(k.stats + 3, 1ull);
                         break;
                     }
                     th = tl + 0.5f * (th - tl);
@@ -582,6 +587,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
                         Wacc += w;
                     }
                     const int last = stop_lane < 32 ? stop_lane : min(31, n - cb - 1);
+                    n_comp += last + 1;
                     T = __shfl_sync(0xffffffffu, Ta, last);
                     if (stop_lane < 32) done = true;
                 }
@@ -619,8 +625,26 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
         Wacc += __shfl_xor_sync(0xffffffffu, Wacc, off);
     }
     if (lane == 0) {
-        k.maps[ray] = make_float4(L0, L1, L2, 1.f - T);
-        k.depth[ray] = Wacc > 1e-8f ? Dacc / Wacc : 0.f;
+        // interior texel (t % R, t / R) of probe p, stored at (+1, +1)
+        const int RS = k.R + 2;
+        const int64_t ti = (int64_t)p * RS * RS + (int64_t)(t / k.R + 1) * RS + (t % k.R + 1);
+        const float4 v = make_float4(L0, L1, L2, 1.f - T);
+        switch (k.rgbo_dtype) {
+        case SOP_F32: reinterpret_cast<float4*>(k.rgbo)[ti] = v; break;
+        case SOP_BF16: reinterpret_cast<uint2*>(k.rgbo)[ti] = Texel<SOP_BF16>::pack(v); break;
+        default: reinterpret_cast<uint2*>(k.rgbo)[ti] = Texel<SOP_F16>::pack(v); break;
+        }
+        if (k.depth) {
+            const float dv = (Wacc > 1e-8f ? Dacc / Wacc : 0.f) * k.inv_depth_scale;
+            switch (k.depth_dtype) {
+            case SOP_F32: reinterpret_cast<float*>(k.depth)[ti] = dv; break;
+            case SOP_F16: reinterpret_cast<__half*>(k.depth)[ti] = __float2half_rn(dv); break;
+            case SOP_BF16: reinterpret_cast<__nv_bfloat16*>(k.depth)[ti] = __float2bfloat16_rn(dv); break;
+            default: reinterpret_cast<__nv_fp8_e4m3*>(k.depth)[ti] = __nv_fp8_e4m3(dv); break;
+            }
+        }
+        atomicAdd(k.stats + 1, (unsigned long long)n_eval);
+        atomicAdd(k.stats + 2, (unsigned long long)n_comp);
     }
     }  // next ray
 #undef SOP_TNEXT
@@ -643,8 +667,39 @@ cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeL
     return cudaGetLastError();
 }
 
-cudaError_t launch_bake_trace(const sop_gaussians& g, const sop_atlas& atlas, const sop_bake_params& bp,
-                              const BakeLayout& L, char* ws, cudaStream_t s)
+// Border texels of an atlas copied from the texels the border rule names.
+__global__ void gutter_fill_kernel(int32_t P, int32_t R, void* __restrict__ rgbo, int rgbo_bytes,
+                                   void* __restrict__ depth, int depth_bytes)
+{
+    const int RS = R + 2, NB = 4 * (R + 1);  // border texels per probe
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)P * NB) return;
+    const int64_t p = i / NB;
+    const int b = (int)(i % NB);
+    int ii, jj;  // stored coordinates of this border texel
+    if (b < RS) { ii = b; jj = 0; }
+    else if (b < 2 * RS) { ii = b - RS; jj = RS - 1; }
+    else if (b < 2 * RS + R) { ii = 0; jj = b - 2 * RS + 1; }
+    else { ii = RS - 1; jj = b - 2 * RS - R + 1; }
+    int si, sj;
+    oct_wrap(R, ii - 1, jj - 1, si, sj);
+    const int64_t dst = p * RS * RS + (int64_t)jj * RS + ii, src = p * RS * RS + (int64_t)(sj + 1) * RS + (si + 1);
+    if (rgbo_bytes == 16) reinterpret_cast<float4*>(rgbo)[dst] = reinterpret_cast<const float4*>(rgbo)[src];
+    else reinterpret_cast<uint2*>(rgbo)[dst] = reinterpret_cast<const uint2*>(rgbo)[src];
+    if (depth) {
+        if (depth_bytes == 4) reinterpret_cast<float*>(depth)[dst] = reinterpret_cast<const float*>(depth)[src];
+        else if (depth_bytes == 2)
+            reinterpret_cast<uint16_t*>(depth)[dst] = reinterpret_cast<const uint16_t*>(depth)[src];
+        else reinterpret_cast<uint8_t*>(depth)[dst] = reinterpret_cast<const uint8_t*>(depth)[src];
+    }
+}
+
+__global__ void trace_reset_kernel(unsigned long long* stats)
+{
+    if (threadIdx.x < 4) stats[threadIdx.x] = 0ull;
+}
+
+cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s)
 {
     GaussGrid* grid = reinterpret_cast<GaussGrid*>(ws + L.hdr);
     GRec* rec = reinterpret_cast<GRec*>(ws + L.rec);
@@ -655,15 +710,24 @@ cudaError_t launch_bake_trace(const sop_gaussians& g, const sop_atlas& atlas, co
     const int bs = 256;
     if (g.n > 0)
         bin_fill_kernel<<<(unsigned)((g.n + bs - 1) / bs), bs, 0, s>>>(g.n, rec, grid, cstart, ccnt, ent, sph);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp, const BakeLayout& L, char* ws,
+                              cudaStream_t s)
+{
+    GaussGrid* grid = reinterpret_cast<GaussGrid*>(ws + L.hdr);
     const int R = atlas.R;
     float4* dirs = reinterpret_cast<float4*>(ws + L.dirs);
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(ws + L.stats);
+    trace_reset_kernel<<<1, 32, 0, s>>>(stats);
     texel_dirs_kernel<<<(R * R + 127) / 128, 128, 0, s>>>(R, dirs);
     TraceK k;
-    k.rec = rec;
+    k.rec = reinterpret_cast<GRec*>(ws + L.rec);
     k.grid = grid;
-    k.cell_start = cstart;
-    k.entries = ent;
-    k.ent_sph = sph;
+    k.cell_start = reinterpret_cast<int32_t*>(ws + L.cell_start);
+    k.entries = reinterpret_cast<int32_t*>(ws + L.entries);
+    k.ent_sph = reinterpret_cast<float4*>(ws + L.ent_sph);
     k.dirs = dirs;
     k.probe_pos = atlas.probe_pos;
     k.P = atlas.P;
@@ -672,10 +736,12 @@ cudaError_t launch_bake_trace(const sop_gaussians& g, const sop_atlas& atlas, co
     k.alpha_min = bp.alpha_min;
     k.alpha_max = bp.alpha_max;
     k.t_stop = bp.t_stop;
-    k.maps = reinterpret_cast<float4*>(ws + L.maps);
-    k.depth = reinterpret_cast<float*>(ws + L.depth);
-    k.status = reinterpret_cast<int32_t*>(ws + L.bbox) + 6;
-    k.counter = reinterpret_cast<unsigned long long*>(ws + L.bbox + 8 * sizeof(int32_t));
+    k.rgbo = atlas.rgbo;
+    k.depth = atlas.depth;
+    k.rgbo_dtype = atlas.rgbo_dtype;
+    k.depth_dtype = atlas.depth_dtype;
+    k.inv_depth_scale = 1.f / atlas.depth_scale;
+    k.stats = stats;
     const int64_t rays = (int64_t)atlas.P * R * R;
     // persistent grid: as many CTAs as fit on the device at once
     static int resident = 0;
@@ -689,10 +755,11 @@ cudaError_t launch_bake_trace(const sop_gaussians& g, const sop_atlas& atlas, co
     const int64_t need = (rays + kWarpsPerCta - 1) / kWarpsPerCta;
     const unsigned nb = (unsigned)(need < resident ? need : resident);
     trace_kernel<<<nb, kWarpsPerCta * 32, 0, s>>>(k);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_atlas_pack(reinterpret_cast<const float*>(k.maps), 4, reinterpret_cast<const float*>(k.maps) + 3, 4,
-                             k.depth, atlas, s);
+    const int64_t nbord = (int64_t)atlas.P * 4 * (R + 1);
+    const int db = atlas.depth_dtype == SOP_F32 ? 4 : (atlas.depth_dtype == SOP_FP8E4M3 ? 1 : 2);
+    gutter_fill_kernel<<<(unsigned)((nbord + 255) / 256), 256, 0, s>>>(
+        atlas.P, R, atlas.rgbo, atlas.rgbo_dtype == SOP_F32 ? 16 : 8, atlas.depth, db);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

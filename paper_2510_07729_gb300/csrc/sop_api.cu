@@ -117,15 +117,12 @@ sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream)
 size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R)
 {
     if (n_gauss < 0 || P < 1 || R < 2) return 0;
-    return sop::bake_layout(n_gauss, P, R, 0).total;
+    return sop::bake_layout(n_gauss, 0).total;
 }
 
-sop_status sop_bake(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
-                    size_t ws_bytes, void* stream)
+static sop_status check_bake_args(const sop_gaussians* g, const sop_bake_params* params)
 {
     if (!g || !params) return fail(SOP_ERR_INVALID_ARG, "gaussians or params is NULL");
-    sop_status st = check_atlas(atlas, true);
-    if (st != SOP_OK) return st;
     if (g->n < 0 || g->n > (int64_t)INT32_MAX) return fail(SOP_ERR_INVALID_ARG, "n = %lld out of range", (long long)g->n);
     if (g->n > 0 && (!g->mean || !g->scale || !g->quat || !g->opacity || !g->rgb))
         return fail(SOP_ERR_INVALID_ARG, "a Gaussian array is NULL");
@@ -133,36 +130,89 @@ sop_status sop_bake(const sop_gaussians* g, const sop_atlas* atlas, const sop_ba
         !(params->t_stop >= 0.f) || !(params->t_stop < 1.f) || !isfinite(params->t_near))
         return fail(SOP_ERR_INVALID_ARG, "bake params out of range (need 0 < alpha_min <= alpha_max < 1, "
                                          "0 <= t_stop < 1, finite t_near)");
-    const int64_t RR = (int64_t)atlas->R * atlas->R;
-    if ((int64_t)atlas->P * RR > (int64_t)INT32_MAX)
-        return fail(SOP_ERR_INVALID_ARG, "P * R^2 exceeds 2^31 texels");
-    // the caller's workspace decides how many cell entries fit
-    sop::BakeLayout L0 = sop::bake_layout(g->n, atlas->P, atlas->R, 1);
-    if (!ws || ws_bytes < L0.total) return check_ws(ws, ws_bytes, sop::bake_layout(g->n, atlas->P, atlas->R, 0).total);
-    // largest entry capacity whose layout fits the caller's workspace
+    return SOP_OK;
+}
+
+// The layout with the largest cell-entry capacity that fits ws_bytes.
+static sop_status bake_fit(int64_t n, void* ws, size_t ws_bytes, sop::BakeLayout& L)
+{
+    const sop::BakeLayout L0 = sop::bake_layout(n, 1);
+    if (!ws || ws_bytes < L0.total) return check_ws(ws, ws_bytes, sop::bake_layout(n, 0).total);
     int64_t cap = 64 + (int64_t)((ws_bytes - L0.total) / (sizeof(int32_t) + sizeof(float4)));
-    sop::BakeLayout L = sop::bake_layout(g->n, atlas->P, atlas->R, cap);
-    while (L.total > ws_bytes && L.entries_cap > 1) L = sop::bake_layout(g->n, atlas->P, atlas->R, L.entries_cap - 1);
-    st = check_ws(ws, ws_bytes, L.total);
+    L = sop::bake_layout(n, cap);
+    while (L.total > ws_bytes && L.entries_cap > 1) L = sop::bake_layout(n, L.entries_cap - 1);
+    return check_ws(ws, ws_bytes, L.total);
+}
+
+sop_status sop_bake_bin(const sop_gaussians* g, const sop_bake_params* params, void* ws, size_t ws_bytes,
+                        void* stream)
+{
+    sop_status st = check_bake_args(g, params);
     if (st != SOP_OK) return st;
+    sop::BakeLayout L;
+    if ((st = bake_fit(g->n, ws, ws_bytes, L)) != SOP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     char* w = (char*)ws;
-    st = cuda_status(sop::launch_bake_bin(*g, params->alpha_min, L, w, s), "sop_bake (binning)");
+    st = cuda_status(sop::launch_bake_bin(*g, params->alpha_min, L, w, s), "sop_bake_bin (binning)");
     if (st != SOP_OK) return st;
     // size check of the cell lists: one 4-byte read-back
     int32_t n_entries = 0;
     st = cuda_status(cudaMemcpyAsync(&n_entries, w + L.hdr + offsetof(sop::GaussGrid, n_entries), sizeof(int32_t),
                                      cudaMemcpyDeviceToHost, s),
-                     "sop_bake (read-back)");
+                     "sop_bake_bin (read-back)");
     if (st != SOP_OK) return st;
-    st = cuda_status(cudaStreamSynchronize(s), "sop_bake (sync)");
+    st = cuda_status(cudaStreamSynchronize(s), "sop_bake_bin (sync)");
     if (st != SOP_OK) return st;
     if (n_entries == INT32_MAX || (int64_t)n_entries > L.entries_cap) {
-        const sop::BakeLayout need = sop::bake_layout(g->n, atlas->P, atlas->R, (int64_t)n_entries + 1);
+        const sop::BakeLayout need = sop::bake_layout(g->n, (int64_t)n_entries + 1);
         return fail(SOP_ERR_WORKSPACE, "sop_bake: %d grid entries exceed the workspace; need %zu bytes", n_entries,
                     need.total);
     }
-    return cuda_status(sop::launch_bake_trace(*g, *atlas, *params, L, w, s), "sop_bake (trace)");
+    return cuda_status(sop::launch_bake_fill(*g, L, w, s), "sop_bake_bin (fill)");
+}
+
+sop_status sop_bake_trace(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
+                          size_t ws_bytes, void* stream)
+{
+    sop_status st = check_bake_args(g, params);
+    if (st != SOP_OK) return st;
+    if ((st = check_atlas(atlas, true)) != SOP_OK) return st;
+    if ((int64_t)atlas->P * atlas->R * atlas->R > (int64_t)INT32_MAX)
+        return fail(SOP_ERR_INVALID_ARG, "P * R^2 exceeds 2^31 texels");
+    sop::BakeLayout L;
+    if ((st = bake_fit(g->n, ws, ws_bytes, L)) != SOP_OK) return st;
+    return cuda_status(sop::launch_bake_trace(*atlas, *params, L, (char*)ws, (cudaStream_t)stream), "sop_bake_trace");
+}
+
+sop_status sop_bake(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
+                    size_t ws_bytes, void* stream)
+{
+    sop_status st = check_bake_args(g, params);
+    if (st != SOP_OK) return st;
+    if ((st = check_atlas(atlas, true)) != SOP_OK) return st;
+    if ((int64_t)atlas->P * atlas->R * atlas->R > (int64_t)INT32_MAX)
+        return fail(SOP_ERR_INVALID_ARG, "P * R^2 exceeds 2^31 texels");
+    if ((st = sop_bake_bin(g, params, ws, ws_bytes, stream)) != SOP_OK) return st;
+    return sop_bake_trace(g, atlas, params, ws, ws_bytes, stream);
+}
+
+sop_status sop_bake_stats(const void* ws, size_t ws_bytes, int64_t n_gauss, int64_t* out, void* stream)
+{
+    if (!out) return fail(SOP_ERR_INVALID_ARG, "out is NULL");
+    sop::BakeLayout L;
+    sop_status st = bake_fit(n_gauss, const_cast<void*>(ws), ws_bytes, L);
+    if (st != SOP_OK) return st;
+    unsigned long long v[4];
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_status(cudaMemcpyAsync(v, (const char*)ws + L.stats, sizeof(v), cudaMemcpyDeviceToHost, s),
+                     "sop_bake_stats");
+    if (st != SOP_OK) return st;
+    st = cuda_status(cudaStreamSynchronize(s), "sop_bake_stats (sync)");
+    if (st != SOP_OK) return st;
+    out[0] = (int64_t)v[1];
+    out[1] = (int64_t)v[2];
+    out[2] = (int64_t)v[3];
+    return SOP_OK;
 }
 
 size_t sop_query_workspace_bytes(const sop_atlas* atlas, int64_t M, const sop_shade_params* params, int32_t He,

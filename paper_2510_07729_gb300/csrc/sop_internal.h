@@ -61,13 +61,15 @@ cudaError_t launch_atlas_pack(const float* rgb, int rgb_stride, const float* occ
 
 // ---- bake -------------------------------------------------------------------
 struct BakeLayout {
-    size_t hdr, rec, bbox, cell_start, cell_cnt, entries, ent_sph, dirs, maps, depth, total;
+    size_t hdr, bbox, stats, rec, cell_start, cell_cnt, dirs, entries, ent_sph, total;
     int64_t cells_cap, entries_cap;
 };
-BakeLayout bake_layout(int64_t N, int32_t P, int32_t R, int64_t entries_cap);
+// bake workspace layout for N Gaussians (independent of the atlas)
+BakeLayout bake_layout(int64_t N, int64_t entries_cap);
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s);
-cudaError_t launch_bake_trace(const sop_gaussians& g, const sop_atlas& atlas, const sop_bake_params& bp,
-                              const BakeLayout& L, char* ws, cudaStream_t s);
+cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s);
+cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp, const BakeLayout& L, char* ws,
+                              cudaStream_t s);
 
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 

@@ -72,6 +72,9 @@ def load(build_if_missing: bool = True):
     lib.sop_bake_workspace_bytes.argtypes = [i64, i32, i32]
     lib.sop_bake_workspace_bytes.restype = sz
     lib.sop_bake.argtypes = [C.POINTER(Gaussians), C.POINTER(AtlasDesc), C.POINTER(BakeParams), vp, sz, vp]
+    lib.sop_bake_bin.argtypes = [C.POINTER(Gaussians), C.POINTER(BakeParams), vp, sz, vp]
+    lib.sop_bake_trace.argtypes = [C.POINTER(Gaussians), C.POINTER(AtlasDesc), C.POINTER(BakeParams), vp, sz, vp]
+    lib.sop_bake_stats.argtypes = [vp, sz, i64, C.POINTER(i64), vp]
     lib.sop_query_workspace_bytes.argtypes = [C.POINTER(AtlasDesc), i64, C.POINTER(ShadeParams), i32, i32]
     lib.sop_query_workspace_bytes.restype = sz
     lib.sop_query_shade.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
@@ -80,7 +83,8 @@ def load(build_if_missing: bool = True):
                                              C.POINTER(ShadeParams), vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.sop_query_shade_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
                                             C.POINTER(ShadeParams), vp, vp, vp, vp]
-    for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_query_shade",
+    for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_bake_bin", "sop_bake_trace",
+                 "sop_bake_stats", "sop_query_shade",
                  "sop_query_shade_backward", "sop_query_shade_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -218,37 +222,74 @@ def bake_workspace_bytes(n_gauss, P, R):
     return int(load().sop_bake_workspace_bytes(n_gauss, P, R))
 
 
-_bake_ws_cache = {}
+class BakeWorkspace:
+    """Scratch for the bake of one Gaussian set (grows on demand)."""
+
+    def __init__(self, n_gauss, device):
+        self.n = int(n_gauss)
+        self.buf = _ws(bake_workspace_bytes(self.n, 1, 2), device)
+
+    def grow(self, nbytes):
+        self.buf = _ws(nbytes, self.buf.device)
+
+
+def _bake_params(t_near, alpha_min, alpha_max, t_stop):
+    return BakeParams(t_near, alpha_min, alpha_max, t_stop)
+
+
+def bake_bin(gauss, workspace: BakeWorkspace, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4):
+    """Bin the Gaussians into the grid kept in the workspace (syncs once);
+    grows the workspace once if the scene needs more cell entries."""
+    lib = load()
+    g = _gauss(gauss)
+    bp = _bake_params(t_near, alpha_min, alpha_max, t_stop)
+    ws = workspace
+    st = lib.sop_bake_bin(C.byref(g), C.byref(bp), _ptr(ws.buf), ws.buf.numel(), _stream())
+    if st == 3:
+        msg = lib.sop_last_error().decode()
+        need = int(msg.rsplit("need ", 1)[1].split()[0]) if "need " in msg else 2 * ws.buf.numel()
+        ws.grow(need)
+        st = lib.sop_bake_bin(C.byref(g), C.byref(bp), _ptr(ws.buf), ws.buf.numel(), _stream())
+    _check(st)
+    return ws
+
+
+def bake_trace(gauss, atlas: Atlas, workspace: BakeWorkspace, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99,
+               t_stop=1e-4):
+    """Trace every texel of the atlas through the binned grid (async)."""
+    lib = load()
+    g = _gauss(gauss)
+    bp = _bake_params(t_near, alpha_min, alpha_max, t_stop)
+    d = atlas.c()
+    _check(lib.sop_bake_trace(C.byref(g), C.byref(d), C.byref(bp), _ptr(workspace.buf), workspace.buf.numel(),
+                              _stream()))
+    return atlas
+
+
+def bake_stats(workspace: BakeWorkspace):
+    """(exact evaluations, composited hits, status bits) of the last trace."""
+    out = (C.c_int64 * 3)()
+    _check(load().sop_bake_stats(_ptr(workspace.buf), workspace.buf.numel(), workspace.n, out, _stream()))
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+_bake_ws = {}
 
 
 def bake(gauss, atlas: Atlas, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, workspace=None):
     """Bake every texel of `atlas` against the Gaussians (dict of CUDA
-    float32 tensors: mean, scale, quat, opacity, rgb). Synchronises once."""
-    lib = load()
-    g = _gauss(gauss)
-    bp = BakeParams(t_near, alpha_min, alpha_max, t_stop)
-    d = atlas.c()
+    float32 tensors: mean, scale, quat, opacity, rgb): bin + trace.
+    Synchronises once."""
+    n = int(gauss["mean"].shape[0])
     dev = atlas.rgbo.device
-    n = int(g.n)
-    if workspace is None:
-        need = bake_workspace_bytes(n, atlas.P, atlas.R)
-        key = (dev, n, atlas.P, atlas.R)
-        ws = _bake_ws_cache.get(key)
-        if ws is None or ws.numel() < need:
-            ws = _ws(need, dev)
-            _bake_ws_cache.clear()
-            _bake_ws_cache[key] = ws
-    else:
-        ws = workspace
-    st = lib.sop_bake(C.byref(g), C.byref(d), C.byref(bp), _ptr(ws), ws.numel(), _stream())
-    if st == 3 and workspace is None:  # cell lists need more room: retry once with the size asked for
-        msg = lib.sop_last_error().decode()
-        need = int(msg.rsplit("need ", 1)[1].split()[0]) if "need " in msg else 2 * ws.numel()
-        ws = _ws(need, dev)
-        _bake_ws_cache.clear()
-        _bake_ws_cache[(dev, n, atlas.P, atlas.R)] = ws
-        st = lib.sop_bake(C.byref(g), C.byref(d), C.byref(bp), _ptr(ws), ws.numel(), _stream())
-    _check(st)
+    ws = workspace
+    if ws is None:
+        ws = _bake_ws.get((dev, n))
+        if ws is None:
+            _bake_ws.clear()
+            ws = _bake_ws[(dev, n)] = BakeWorkspace(n, dev)
+    bake_bin(gauss, ws, t_near, alpha_min, alpha_max, t_stop)
+    bake_trace(gauss, atlas, ws, t_near, alpha_min, alpha_max, t_stop)
     return atlas
 
 
