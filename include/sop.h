@@ -247,6 +247,58 @@ sop_status sop_query_shade_backward(const float* x, const float* n, const float*
                                     float* g_rough, float* g_metal, float* g_normal, float* g_env, float* g_maps,
                                     void* ws, size_t ws_bytes, void* stream);
 
+/* ---- Learned bake surrogate ------------------------------------------------
+ * A small MLP predicts a probe's maps (O, D/depth_scale, RGB) from its
+ * neighbourhood, to rebake probes quickly after an object moves; the
+ * ray-traced sop_bake is its fallback and its judge (the paper has no
+ * surrogate: it initialises SOPs by ray tracing, Sec. 3.1.2 / 3.2.2).
+ *   probe features f_p (416 floats): the 32 Gaussians nearest to the probe
+ *     (exact integer-key search, ties to the lower index), nearest first,
+ *     each as (centre - probe) * 10, log(scale) + 5, opacity, rgb; then
+ *     sin and cos of pi 2^(f/3) p for f = 0..15 and each axis;
+ *   per texel: h1 = relu(W1p f_p + W1d d_t + b1), h2 = relu(W2 h1 + b2),
+ *     h3 = relu(W3 h2 + b3), y = W4 h3 + b4 with d_t the texel direction and
+ *     y = (O, D / depth_scale, R, G, B); written to an atlas as O clamped to
+ *     [0,1] and D, RGB clamped at 0.
+ * Parameters: one float32 vector of sop_surrogate_param_count() values, in
+ * the order W1p [64][416], W1d [64][3], b1 [64], W2 [64][64], b2, W3 [64][64],
+ * b3, W4 [5][64], b4 [5] (row-major, out x in). Weights are used as bfloat16
+ * with float32 accumulation; the 64x64 layers run on the tensor cores.
+ * Training: mean absolute error over the 5 outputs, Adam (0.9, 0.999, 1e-8,
+ * bias-corrected), float32 master weights. The caller owns the state buffer
+ * (sop_surrogate_state_bytes(), 256-byte aligned). */
+int32_t sop_surrogate_param_count(void);
+size_t sop_surrogate_state_bytes(void);
+/* Load parameters (device [count] float32) into the state; resets Adam. */
+sop_status sop_surrogate_set_params(void* state, const float* params, void* stream);
+sop_status sop_surrogate_get_params(const void* state, float* params, void* stream);
+/* The gradient summed by the last sop_surrogate_train_step (device [count]). */
+sop_status sop_surrogate_get_grad(const void* state, float* grad, void* stream);
+/* Workspace for features / train / infer on n Gaussians, P probes of side R. */
+size_t sop_surrogate_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R);
+/* Probe features: feats [P][416] float32 (device). Needs n >= 32. */
+sop_status sop_surrogate_features(const sop_gaussians* g, const float* probe_pos, int32_t P, float* feats, void* ws,
+                                  size_t ws_bytes, void* stream);
+/* One Adam step on B probes: probe_ids [B] (device; NULL = 0..B-1) index both
+ * feats and the target atlas (baked maps, R x R texels each). loss_out
+ * (device float, may be NULL) receives the mean absolute error of the batch
+ * before the step. */
+sop_status sop_surrogate_train_step(void* state, const float* feats, const int32_t* probe_ids, int32_t B,
+                                    const sop_atlas* targets, float lr, float* loss_out, void* ws, size_t ws_bytes,
+                                    void* stream);
+/* Predict the maps of B probes (probe_ids as above) into `out` (interior
+ * and border texels). */
+sop_status sop_surrogate_infer(const void* state, const float* feats, const int32_t* probe_ids, int32_t B,
+                               const sop_atlas* out, void* ws, size_t ws_bytes, void* stream);
+/* Spot-check helpers: out[0] = sum |O_a - O_b| and out[1] = sum of |RGB_a -
+ * RGB_b| over the interior texels of n probe pairs (a_probes[i],
+ * b_probes[i]; NULL = 0..n-1), written to device out[2]. */
+sop_status sop_atlas_compare(const sop_atlas* a, const int32_t* a_probes, const sop_atlas* b, const int32_t* b_probes,
+                             int32_t n, float* out, void* stream);
+/* Copy whole probes (all (R+2)^2 texels) src_probes[i] -> dst_probes[i]. */
+sop_status sop_atlas_copy(const sop_atlas* src, const int32_t* src_probes, const sop_atlas* dst,
+                          const int32_t* dst_probes, int32_t n, void* stream);
+
 /* Allocation-free sop_query_shade. No counterpart in the paper: this entry
  * point exists for callers that cannot allocate device memory, for example
  * code running where cudaMalloc is unavailable or forbidden (a host

@@ -755,10 +755,15 @@ cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp,
     const int64_t need = (rays + kWarpsPerCta - 1) / kWarpsPerCta;
     const unsigned nb = (unsigned)(need < resident ? need : resident);
     trace_kernel<<<nb, kWarpsPerCta * 32, 0, s>>>(k);
-    const int64_t nbord = (int64_t)atlas.P * 4 * (R + 1);
+    return launch_gutter_fill(atlas, s);
+}
+
+cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s)
+{
+    const int64_t nbord = (int64_t)atlas.P * 4 * (atlas.R + 1);
     const int db = atlas.depth_dtype == SOP_F32 ? 4 : (atlas.depth_dtype == SOP_FP8E4M3 ? 1 : 2);
     gutter_fill_kernel<<<(unsigned)((nbord + 255) / 256), 256, 0, s>>>(
-        atlas.P, R, atlas.rgbo, atlas.rgbo_dtype == SOP_F32 ? 16 : 8, atlas.depth, db);
+        atlas.P, atlas.R, atlas.rgbo, atlas.rgbo_dtype == SOP_F32 ? 16 : 8, atlas.depth, db);
     return cudaGetLastError();
 }
 

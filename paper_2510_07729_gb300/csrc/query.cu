@@ -720,6 +720,51 @@ cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cud
 }
 
 
+// ---------------------------------------------------------------------------
+// K nearest sites (e.g. Gaussian centres) of M query points, exact, with the
+// same integer keys and tie rule as the probe search.
+// ---------------------------------------------------------------------------
+size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K)
+{
+    int g = 1;
+    while ((int64_t)g * g * g < N) ++g;
+    const int64_t cells = (int64_t)(g + 1) * (g + 1) * (g + 1);
+    size_t o = align256(sizeof(ProbeGrid));
+    o = align256(o + sizeof(int32_t) * (size_t)(cells + 1));
+    o = align256(o + sizeof(int32_t) * (size_t)cells);
+    o = align256(o + sizeof(int4) * (size_t)N);
+    o = align256(o + sizeof(float) * (size_t)M * K);
+    return o;
+}
+
+cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,
+                             char* ws, cudaStream_t s)
+{
+    int g = 1;
+    while ((int64_t)g * g * g < N) ++g;
+    const int64_t cells = (int64_t)(g + 1) * (g + 1) * (g + 1);
+    size_t o = 0;
+    ProbeGrid* grid = reinterpret_cast<ProbeGrid*>(ws + o);
+    o = align256(sizeof(ProbeGrid));
+    int32_t* cstart = reinterpret_cast<int32_t*>(ws + o);
+    o = align256(o + sizeof(int32_t) * (size_t)(cells + 1));
+    int32_t* ccnt = reinterpret_cast<int32_t*>(ws + o);
+    o = align256(o + sizeof(int32_t) * (size_t)cells);
+    int4* ent = reinterpret_cast<int4*>(ws + o);
+    o = align256(o + sizeof(int4) * (size_t)N);
+    float* w = reinterpret_cast<float*>(ws + o);
+    probe_grid_kernel<<<1, 1024, 0, s>>>(sites, N, g, grid, cstart, ccnt, ent);
+    if (M > 0) {
+        const unsigned nb = (unsigned)((M + 127) / 128);
+        // the blend weights are not needed here; the points stand in for normals
+        if (K <= 4) knn_kernel<4><<<nb, 128, 0, s>>>(pts, pts, M, K, 0, grid, cstart, ent, sites, idx, w, nullptr, nullptr);
+        else if (K <= 8) knn_kernel<8><<<nb, 128, 0, s>>>(pts, pts, M, K, 0, grid, cstart, ent, sites, idx, w, nullptr, nullptr);
+        else if (K <= 16) knn_kernel<16><<<nb, 128, 0, s>>>(pts, pts, M, K, 0, grid, cstart, ent, sites, idx, w, nullptr, nullptr);
+        else knn_kernel<32><<<nb, 128, 0, s>>>(pts, pts, M, K, 0, grid, cstart, ent, sites, idx, w, nullptr, nullptr);
+    }
+    return cudaGetLastError();
+}
+
 // ===========================================================================
 // Allocation-free variant of the query + shade (sop_query_shade_noalloc).
 //

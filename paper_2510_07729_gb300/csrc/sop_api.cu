@@ -370,4 +370,114 @@ sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* 
     return cuda_status(sop::launch_query_noalloc(a, (cudaStream_t)stream), "sop_query_shade_noalloc");
 }
 
+// ---- learned bake surrogate ----------------------------------------------------
+int32_t sop_surrogate_param_count(void) { return sop::surr_n_params(); }
+
+size_t sop_surrogate_state_bytes(void) { return sop::surr_state_bytes(); }
+
+sop_status sop_surrogate_set_params(void* state, const float* params, void* stream)
+{
+    if (!state || !params) return fail(SOP_ERR_INVALID_ARG, "state / params is NULL");
+    if (!aligned(state, 256)) return fail(SOP_ERR_INVALID_ARG, "state must be 256-byte aligned");
+    return cuda_status(sop::surr_set_params((char*)state, params, (cudaStream_t)stream), "sop_surrogate_set_params");
+}
+
+sop_status sop_surrogate_get_params(const void* state, float* params, void* stream)
+{
+    if (!state || !params) return fail(SOP_ERR_INVALID_ARG, "state / params is NULL");
+    return cuda_status(sop::surr_get_params((const char*)state, params, (cudaStream_t)stream),
+                       "sop_surrogate_get_params");
+}
+
+sop_status sop_surrogate_get_grad(const void* state, float* grad, void* stream)
+{
+    if (!state || !grad) return fail(SOP_ERR_INVALID_ARG, "state / grad is NULL");
+    return cuda_status(sop::surr_get_grad((const char*)state, grad, (cudaStream_t)stream), "sop_surrogate_get_grad");
+}
+
+size_t sop_surrogate_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R)
+{
+    if (n_gauss < 32 || P < 1 || R < 2) return 0;
+    const size_t a = sop::surr_features_ws_bytes(n_gauss, P), b = sop::surr_run_ws_bytes(P, R);
+    return a > b ? a : b;
+}
+
+sop_status sop_surrogate_features(const sop_gaussians* g, const float* probe_pos, int32_t P, float* feats, void* ws,
+                                  size_t ws_bytes, void* stream)
+{
+    if (!g || !probe_pos || !feats) return fail(SOP_ERR_INVALID_ARG, "a pointer is NULL");
+    if (P < 1) return fail(SOP_ERR_INVALID_ARG, "P = %d < 1", P);
+    if (g->n < 32 || g->n > (int64_t)INT32_MAX)
+        return fail(SOP_ERR_INVALID_ARG, "the surrogate needs at least 32 Gaussians (n = %lld)", (long long)g->n);
+    if (!g->mean || !g->scale || !g->opacity || !g->rgb) return fail(SOP_ERR_INVALID_ARG, "a Gaussian array is NULL");
+    sop_status st = check_ws(ws, ws_bytes, sop::surr_features_ws_bytes(g->n, P));
+    if (st != SOP_OK) return st;
+    return cuda_status(sop::surr_features(*g, probe_pos, P, feats, (char*)ws, (cudaStream_t)stream),
+                       "sop_surrogate_features");
+}
+
+sop_status sop_surrogate_train_step(void* state, const float* feats, const int32_t* probe_ids, int32_t B,
+                                    const sop_atlas* targets, float lr, float* loss_out, void* ws, size_t ws_bytes,
+                                    void* stream)
+{
+    if (!state || !feats) return fail(SOP_ERR_INVALID_ARG, "state / feats is NULL");
+    sop_status st = check_atlas(targets, true);
+    if (st != SOP_OK) return st;
+    if (B < 1) return fail(SOP_ERR_INVALID_ARG, "B = %d < 1", B);
+    if (!probe_ids && B > targets->P) return fail(SOP_ERR_INVALID_ARG, "B exceeds the target atlas' probes");
+    if (!(lr > 0.f) || !isfinite(lr)) return fail(SOP_ERR_INVALID_ARG, "lr must be finite and > 0");
+    st = check_ws(ws, ws_bytes, sop::surr_run_ws_bytes(B, targets->R));
+    if (st != SOP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_status(sop::surr_train_step((char*)state, feats, probe_ids, B, *targets, lr, (char*)ws, s),
+                     "sop_surrogate_train_step");
+    if (st != SOP_OK || !loss_out) return st;
+    const float scale = 1.f / ((float)B * targets->R * targets->R * 5.f);
+    return cuda_status(sop::surr_loss_out((const char*)state, scale, loss_out, s), "sop_surrogate_train_step (loss)");
+}
+
+sop_status sop_surrogate_infer(const void* state, const float* feats, const int32_t* probe_ids, int32_t B,
+                               const sop_atlas* out, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!state || !feats) return fail(SOP_ERR_INVALID_ARG, "state / feats is NULL");
+    sop_status st = check_atlas(out, true);
+    if (st != SOP_OK) return st;
+    if (B < 1) return fail(SOP_ERR_INVALID_ARG, "B = %d < 1", B);
+    if (!probe_ids && B > out->P) return fail(SOP_ERR_INVALID_ARG, "B exceeds the atlas' probes");
+    st = check_ws(ws, ws_bytes, sop::surr_run_ws_bytes(B, out->R));
+    if (st != SOP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_status(sop::surr_infer((const char*)state, feats, probe_ids, B, *out, (char*)ws, s),
+                     "sop_surrogate_infer");
+    if (st != SOP_OK) return st;
+    // border texels from the predicted interior
+    return cuda_status(sop::launch_gutter_fill(*out, s), "sop_surrogate_infer (border)");
+}
+
+sop_status sop_atlas_compare(const sop_atlas* a, const int32_t* a_probes, const sop_atlas* b, const int32_t* b_probes,
+                             int32_t n, float* out, void* stream)
+{
+    sop_status st = check_atlas(a, false);
+    if (st != SOP_OK) return st;
+    if ((st = check_atlas(b, false)) != SOP_OK) return st;
+    if (a->R != b->R) return fail(SOP_ERR_INVALID_ARG, "atlases of different R");
+    if (n < 0 || !out) return fail(SOP_ERR_INVALID_ARG, "n < 0 or out is NULL");
+    return cuda_status(sop::launch_atlas_compare(*a, a_probes, *b, b_probes, n, out, (cudaStream_t)stream),
+                       "sop_atlas_compare");
+}
+
+sop_status sop_atlas_copy(const sop_atlas* src, const int32_t* src_probes, const sop_atlas* dst,
+                          const int32_t* dst_probes, int32_t n, void* stream)
+{
+    sop_status st = check_atlas(src, false);
+    if (st != SOP_OK) return st;
+    if ((st = check_atlas(dst, false)) != SOP_OK) return st;
+    if (src->R != dst->R || src->rgbo_dtype != dst->rgbo_dtype ||
+        ((src->depth && dst->depth) && src->depth_dtype != dst->depth_dtype))
+        return fail(SOP_ERR_INVALID_ARG, "atlases differ in R or dtype");
+    if (n < 0) return fail(SOP_ERR_INVALID_ARG, "n < 0");
+    return cuda_status(sop::launch_atlas_copy(*src, src_probes, *dst, dst_probes, n, (cudaStream_t)stream),
+                       "sop_atlas_copy");
+}
+
 }  // extern "C"

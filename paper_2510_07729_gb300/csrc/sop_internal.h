@@ -49,6 +49,11 @@ cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cud
 cudaError_t launch_adjoint(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_hammersley(int32_t S, float* out3, cudaStream_t s);
 
+// K nearest sites of M points (surrogate features)
+size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K);
+cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,
+                             char* ws, cudaStream_t s);
+
 // allocation-free query (static device scratch, see query.cu)
 size_t noalloc_scratch_bytes();
 int64_t noalloc_chunk();
@@ -68,8 +73,30 @@ struct BakeLayout {
 BakeLayout bake_layout(int64_t N, int64_t entries_cap);
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s);
+cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s);
 cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp, const BakeLayout& L, char* ws,
                               cudaStream_t s);
+
+// ---- learned bake surrogate ---------------------------------------------------
+struct SurrState;
+int surr_n_params();
+size_t surr_state_bytes();
+cudaError_t surr_set_params(char* state, const float* params, cudaStream_t s);
+cudaError_t surr_get_params(const char* state, float* params, cudaStream_t s);
+cudaError_t surr_get_grad(const char* state, float* grad, cudaStream_t s);
+size_t surr_features_ws_bytes(int64_t N, int32_t P);
+size_t surr_run_ws_bytes(int32_t B, int32_t R);
+cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_t P, float* feats, char* ws,
+                          cudaStream_t s);
+cudaError_t surr_train_step(char* state, const float* feats, const int32_t* pid, int32_t B, const sop_atlas& tgt,
+                            float lr, char* ws, cudaStream_t s);
+cudaError_t surr_infer(const char* state, const float* feats, const int32_t* pid, int32_t B, const sop_atlas& out,
+                       char* ws, cudaStream_t s);
+cudaError_t surr_loss_out(const char* state, float scale, float* out, cudaStream_t s);
+cudaError_t launch_atlas_compare(const sop_atlas& a, const int32_t* ap, const sop_atlas& b, const int32_t* bp,
+                                 int32_t n, float* out, cudaStream_t s);
+cudaError_t launch_atlas_copy(const sop_atlas& src, const int32_t* sp, const sop_atlas& dst, const int32_t* dp,
+                              int32_t n, cudaStream_t s);
 
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 

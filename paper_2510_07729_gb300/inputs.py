@@ -417,3 +417,57 @@ def smooth_maps(rng, P, R):
     rgb = np.stack([0.25 + 0.15 * wave(c) for c in range(3)], axis=-1)
     return dict(rgb=rgb.astype(F32), occ=occ.astype(F32),
                 depth=np.full((P, R, R), 0.5, F32))
+
+
+# --------------------------------------------------------------------------
+# learned bake surrogate: initial parameters and training / evaluation scenes
+# --------------------------------------------------------------------------
+SURR_BLOCKS = [("W1p", (64, 416)), ("W1d", (64, 3)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
+               ("W3", (64, 64)), ("b3", (64,)), ("W4", (5, 64)), ("b4", (5,))]
+
+
+def surrogate_init(seed):
+    """Initial surrogate parameters (flat float32, block order above):
+    weights uniform in +-sqrt(6 / fan_in), biases zero."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, shp in SURR_BLOCKS:
+        if name.startswith("b"):
+            out.append(np.zeros(shp))
+        else:
+            fan_in = 419 if name in ("W1p", "W1d") else shp[1]
+            b = np.sqrt(6.0 / fan_in)
+            out.append(rng.uniform(-b, b, shp))
+    return np.concatenate([o.reshape(-1) for o in out]).astype(F32)
+
+
+def surrogate_scene(seed, n_gauss=200_000, n_probes=4096):
+    """A randomised 'object'-style scene (5 random ellipsoids) with probes at
+    random surface samples offset by 1% of the size along the normal."""
+    rng = np.random.default_rng(seed)
+    ells = Ellipsoids(rng.uniform(-0.6, 0.6, (5, 3)), rng.uniform(0.2, 0.6, (5, 3)), _random_rotations(rng, 5))
+    g = gaussians_on_surface(rng, ells, n_gauss)
+    samp, snrm = ells.sample_surface(rng, n_probes)
+    diag = float(np.linalg.norm(g["mean"].max(0) - g["mean"].min(0)))
+    ppos = samp + 0.01 * diag * snrm
+    return dict(gauss=g, probe_pos=ppos.astype(F32), probe_nrm=snrm.astype(F32), R=16)
+
+
+def moved_object(seed=4):
+    """The 'object' scene after its first ellipsoid's Gaussians move by a
+    U(-0.5, 0.5)^3 translation; 4,096 probes re-placed on the new surface
+    (random samples, offset 1% of the size along the normal)."""
+    _, ells, g, _, _, _, diag = _object(1)
+    rng = np.random.default_rng(seed)
+    shift = rng.uniform(-0.5, 0.5, 3)
+    mean = g["mean"].astype(np.float64)
+    # Gaussians of ellipsoid 0: those lying on its surface
+    loc = (mean - ells.c[0]) @ ells.R[0]
+    on0 = np.abs(np.sum((loc / ells.a[0]) ** 2, axis=1) - 1.0) < 1e-6
+    mean[on0] += shift
+    g2 = dict(g, mean=mean.astype(F32))
+    moved = Ellipsoids(ells.c + np.where(np.arange(5)[:, None] == 0, shift, 0.0), ells.a, ells.R)
+    samp, snrm = moved.sample_surface(rng, 4096)
+    ppos = samp + 0.01 * diag * snrm
+    return dict(gauss=g2, probe_pos=ppos.astype(F32), probe_nrm=snrm.astype(F32), R=16, moved=int(on0.sum()),
+                shift=shift)

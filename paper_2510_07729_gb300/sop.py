@@ -83,6 +83,22 @@ def load(build_if_missing: bool = True):
                                              C.POINTER(ShadeParams), vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.sop_query_shade_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, i64, C.POINTER(AtlasDesc), vp, i32, i32, vp,
                                             C.POINTER(ShadeParams), vp, vp, vp, vp]
+    lib.sop_surrogate_param_count.restype = i32
+    lib.sop_surrogate_state_bytes.restype = sz
+    lib.sop_surrogate_set_params.argtypes = [vp, vp, vp]
+    lib.sop_surrogate_get_params.argtypes = [vp, vp, vp]
+    lib.sop_surrogate_get_grad.argtypes = [vp, vp, vp]
+    lib.sop_surrogate_workspace_bytes.argtypes = [i64, i32, i32]
+    lib.sop_surrogate_workspace_bytes.restype = sz
+    lib.sop_surrogate_features.argtypes = [C.POINTER(Gaussians), vp, i32, vp, vp, sz, vp]
+    lib.sop_surrogate_train_step.argtypes = [vp, vp, vp, i32, C.POINTER(AtlasDesc), f32, vp, vp, sz, vp]
+    lib.sop_surrogate_infer.argtypes = [vp, vp, vp, i32, C.POINTER(AtlasDesc), vp, sz, vp]
+    lib.sop_atlas_compare.argtypes = [C.POINTER(AtlasDesc), vp, C.POINTER(AtlasDesc), vp, i32, vp, vp]
+    lib.sop_atlas_copy.argtypes = [C.POINTER(AtlasDesc), vp, C.POINTER(AtlasDesc), vp, i32, vp]
+    for name in ("sop_surrogate_set_params", "sop_surrogate_get_params", "sop_surrogate_get_grad",
+                 "sop_surrogate_features", "sop_surrogate_train_step", "sop_surrogate_infer", "sop_atlas_compare",
+                 "sop_atlas_copy"):
+        getattr(lib, name).restype = C.c_int
     for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_bake_bin", "sop_bake_trace",
                  "sop_bake_stats", "sop_query_shade",
                  "sop_query_shade_backward", "sop_query_shade_noalloc"):
@@ -408,3 +424,119 @@ def query_shade_noalloc(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S,
     if return_idx:
         return out, idx, w
     return out
+
+
+# ----------------------------------------------------------------------------
+# learned bake surrogate
+# ----------------------------------------------------------------------------
+def _i32(t):
+    if t is None:
+        return None
+    if t.dtype != torch.int32:
+        raise TypeError(f"expected int32, got {t.dtype}")
+    return _ptr(t)
+
+
+class Surrogate:
+    """Caller-owned surrogate state (parameters, Adam moments, gradient)."""
+
+    def __init__(self, params, device="cuda"):
+        lib = load()
+        self.n_params = int(lib.sop_surrogate_param_count())
+        self.state = _ws(int(lib.sop_surrogate_state_bytes()), device)
+        self.device = torch.device(device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.set_params(params)
+
+    def set_params(self, params):
+        p = torch.as_tensor(params, dtype=torch.float32).to(self.device).contiguous()
+        if p.numel() != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check(load().sop_surrogate_set_params(_ptr(self.state), _ptr(p), _stream()))
+        self._keep = p
+
+    def params(self):
+        out = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        _check(load().sop_surrogate_get_params(_ptr(self.state), _ptr(out), _stream()))
+        return out
+
+    def grad(self):
+        out = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        _check(load().sop_surrogate_get_grad(_ptr(self.state), _ptr(out), _stream()))
+        return out
+
+    def _ws(self, n_gauss, P, R):
+        return _ws(int(load().sop_surrogate_workspace_bytes(max(int(n_gauss), 32), int(P), int(R))), self.device)
+
+    def features(self, gauss, probe_pos, workspace=None):
+        P = probe_pos.shape[0]
+        g = _gauss(gauss)
+        feats = torch.empty((P, 416), dtype=torch.float32, device=self.device)
+        ws = workspace if workspace is not None else self._ws(g.n, P, 2)
+        _check(load().sop_surrogate_features(C.byref(g), _f32(probe_pos, (P, 3)), P, _ptr(feats), _ptr(ws),
+                                             ws.numel(), _stream()))
+        return feats
+
+    def train_step(self, feats, targets: Atlas, lr=1e-3, probe_ids=None, workspace=None):
+        """One Adam step; returns the batch's mean absolute error (device)."""
+        B = probe_ids.shape[0] if probe_ids is not None else targets.P
+        d = targets.c()
+        ws = workspace if workspace is not None else self._ws(32, B, targets.R)
+        _check(load().sop_surrogate_train_step(_ptr(self.state), _ptr(feats), _i32(probe_ids), B, C.byref(d),
+                                               C.c_float(lr), _ptr(self.loss), _ptr(ws), ws.numel(), _stream()))
+        return self.loss
+
+    def infer(self, feats, out: Atlas, probe_ids=None, workspace=None):
+        B = probe_ids.shape[0] if probe_ids is not None else out.P
+        d = out.c()
+        ws = workspace if workspace is not None else self._ws(32, B, out.R)
+        _check(load().sop_surrogate_infer(_ptr(self.state), _ptr(feats), _i32(probe_ids), B, C.byref(d), _ptr(ws),
+                                          ws.numel(), _stream()))
+        return out
+
+
+def atlas_compare(a: Atlas, b: Atlas, a_probes=None, b_probes=None, n=None):
+    """(sum |dO|, sum |dRGB|) over the interior texels of n probe pairs."""
+    n = n if n is not None else (a_probes.shape[0] if a_probes is not None else a.P)
+    out = torch.empty(2, dtype=torch.float32, device=a.rgbo.device)
+    da, db = a.c(), b.c()
+    _check(load().sop_atlas_compare(C.byref(da), _i32(a_probes), C.byref(db), _i32(b_probes), n, _ptr(out),
+                                    _stream()))
+    return out
+
+
+def atlas_copy(src: Atlas, dst: Atlas, src_probes=None, dst_probes=None, n=None):
+    n = n if n is not None else (src_probes.shape[0] if src_probes is not None else src.P)
+    ds, dd = src.c(), dst.c()
+    _check(load().sop_atlas_copy(C.byref(ds), _i32(src_probes), C.byref(dd), _i32(dst_probes), n, _stream()))
+
+
+def surrogate_rebake(surr: Surrogate, gauss, out: Atlas, spot_frac=0.01, tau=0.05, seed=0, bake_workspace=None):
+    """Rebake all probes of `out` with the surrogate, then spot-check
+    ceil(spot_frac * P) random probes against the ray-traced bake: if their
+    mean |dO| exceeds tau, bake every probe with the ray-traced bake instead
+    (fallback); otherwise the checked probes keep their exact bake. Returns
+    (mean |dO| of the spot-check, fell_back). Synchronises once for the
+    decision."""
+    import math
+
+    import numpy as np
+    P, R = out.P, out.R
+    feats = surr.features(gauss, out.probe_pos)
+    surr.infer(feats, out)
+    n_spot = max(1, math.ceil(spot_frac * P))
+    sel = np.sort(np.random.default_rng(seed).choice(P, n_spot, replace=False)).astype(np.int32)
+    sel_t = torch.from_numpy(sel).to(out.rgbo.device)
+    spot = make_atlas(out.probe_pos[sel_t.long()].contiguous(), R, out.rgbo_dtype, out.depth_dtype,
+                      depth_scale=out.depth_scale, with_depth=out.depth is not None)
+    n = int(gauss["mean"].shape[0])
+    ws = bake_workspace if bake_workspace is not None else BakeWorkspace(n, out.rgbo.device)
+    bake_bin(gauss, ws)
+    bake_trace(gauss, spot, ws)
+    diff = atlas_compare(spot, out, None, sel_t, n_spot)
+    err = float(diff[0].item()) / (n_spot * R * R)
+    if err > tau:
+        bake_trace(gauss, out, ws)
+        return err, True
+    atlas_copy(spot, out, None, sel_t, n_spot)
+    return err, False
