@@ -721,6 +721,118 @@ cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cud
 
 
 // ---------------------------------------------------------------------------
+// Multi-CTA build of the same quantised grid for large site sets (the
+// single-CTA probe_grid_kernel is meant for thousands of probes).
+// ---------------------------------------------------------------------------
+__global__ void sites_bbox_kernel(const float* __restrict__ pos, int32_t N, int32_t* __restrict__ mm)
+{
+    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            const int32_t q = quantise(pos[3 * i + a]);
+            lo[a] = min(lo[a], q);
+            hi[a] = max(hi[a], q);
+        }
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&mm[a], lo[a]);
+            atomicMax(&mm[3 + a], hi[a]);
+        }
+    }
+}
+
+__global__ void sites_setup_kernel(int32_t* mm, int32_t g_axis, ProbeGrid* grid)
+{
+    if (threadIdx.x == 0) {
+        ProbeGrid G;
+        int64_t ext[3], emax = 0;
+        for (int a = 0; a < 3; ++a) {
+            ext[a] = (int64_t)mm[3 + a] - mm[a];
+            emax = ext[a] > emax ? ext[a] : emax;
+        }
+        const int64_t cs = emax / g_axis + 1;
+        G.cs = (int32_t)cs;
+        int32_t nc = 1;
+        for (int a = 0; a < 3; ++a) {
+            G.qmin[a] = mm[a];
+            G.dims[a] = (int32_t)(ext[a] / cs) + 1;
+            nc *= G.dims[a];
+        }
+        G.ncells = nc;
+        *grid = G;
+    }
+}
+
+__global__ void sites_zero_kernel(int32_t* __restrict__ cnt, int64_t n, int32_t* mm)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cnt[i] = 0;
+    if (i < 3) mm[i] = INT32_MAX;
+    else if (i < 6) mm[i] = INT32_MIN;
+}
+
+__device__ __forceinline__ int site_cell(const ProbeGrid& G, const float* pos, int64_t i, int32_t q[3])
+{
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+        q[a] = quantise(pos[3 * i + a]);
+        c[a] = (int)(((int64_t)q[a] - G.qmin[a]) / G.cs);
+    }
+    return (c[2] * G.dims[1] + c[1]) * G.dims[0] + c[0];
+}
+
+__global__ void sites_count_kernel(const float* __restrict__ pos, int32_t N, const ProbeGrid* __restrict__ gp,
+                                   int32_t* __restrict__ cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const ProbeGrid G = *gp;
+    int32_t q[3];
+    atomicAdd(&cnt[site_cell(G, pos, i, q)], 1);
+}
+
+__global__ void __launch_bounds__(1024) sites_scan_kernel(const ProbeGrid* __restrict__ gp, int32_t* __restrict__ cnt,
+                                                           int32_t* __restrict__ start)
+{
+    __shared__ int32_t s_part[1024];
+    const int tid = threadIdx.x, nt = blockDim.x, nc = gp->ncells;
+    const int chunk = (nc + nt - 1) / nt, c0 = tid * chunk, c1 = min(nc, c0 + chunk);
+    int32_t sum = 0;
+    for (int c = c0; c < c1; ++c) sum += cnt[c];
+    s_part[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        const int32_t v = tid >= off ? s_part[tid - off] : 0;
+        __syncthreads();
+        s_part[tid] += v;
+        __syncthreads();
+    }
+    int32_t run = s_part[tid] - sum;
+    for (int c = c0; c < c1; ++c) {
+        const int32_t v = cnt[c];
+        start[c] = run;
+        run += v;
+        cnt[c] = 0;
+    }
+    if (tid == nt - 1) start[nc] = s_part[nt - 1];
+}
+
+__global__ void sites_fill_kernel(const float* __restrict__ pos, int32_t N, const ProbeGrid* __restrict__ gp,
+                                  const int32_t* __restrict__ start, int32_t* __restrict__ cnt, int4* __restrict__ ent)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const ProbeGrid G = *gp;
+    int32_t q[3];
+    const int cell = site_cell(G, pos, i, q);
+    ent[start[cell] + atomicAdd(&cnt[cell], 1)] = make_int4(q[0], q[1], q[2], (int)i);
+}
+
+// ---------------------------------------------------------------------------
 // K nearest sites (e.g. Gaussian centres) of M query points, exact, with the
 // same integer keys and tie rule as the probe search.
 // ---------------------------------------------------------------------------
@@ -734,6 +846,7 @@ size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K)
     o = align256(o + sizeof(int32_t) * (size_t)cells);
     o = align256(o + sizeof(int4) * (size_t)N);
     o = align256(o + sizeof(float) * (size_t)M * K);
+    o = align256(o + 8 * sizeof(int32_t));
     return o;
 }
 
@@ -753,7 +866,19 @@ cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, in
     int4* ent = reinterpret_cast<int4*>(ws + o);
     o = align256(o + sizeof(int4) * (size_t)N);
     float* w = reinterpret_cast<float*>(ws + o);
-    probe_grid_kernel<<<1, 1024, 0, s>>>(sites, N, g, grid, cstart, ccnt, ent);
+    o = align256(o + sizeof(float) * (size_t)M * K);
+    int32_t* mm = reinterpret_cast<int32_t*>(ws + o);
+    if (N <= 16384) {
+        probe_grid_kernel<<<1, 1024, 0, s>>>(sites, N, g, grid, cstart, ccnt, ent);
+    } else {
+        const unsigned nb = (unsigned)((N + 255) / 256);
+        sites_zero_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(ccnt, cells, mm);
+        sites_bbox_kernel<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(sites, N, mm);
+        sites_setup_kernel<<<1, 32, 0, s>>>(mm, g, grid);
+        sites_count_kernel<<<nb, 256, 0, s>>>(sites, N, grid, ccnt);
+        sites_scan_kernel<<<1, 1024, 0, s>>>(grid, ccnt, cstart);
+        sites_fill_kernel<<<nb, 256, 0, s>>>(sites, N, grid, cstart, ccnt, ent);
+    }
     if (M > 0) {
         const unsigned nb = (unsigned)((M + 127) / 128);
         // the blend weights are not needed here; the points stand in for normals

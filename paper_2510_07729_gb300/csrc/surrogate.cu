@@ -106,22 +106,23 @@ __global__ void surr_features_kernel(sop_gaussians g, const float* __restrict__ 
     if (i >= (int64_t)P * kFP) return;
     const int64_t p = i / kFP;
     const int f = (int)(i % kFP);
-    const float3 pp = load3(probe_pos, p);
-    float v;
+    // computed in double and rounded once, so that the bf16 rounding the
+    // network applies to each feature sees the correctly rounded value
+    const double pp[3] = {probe_pos[3 * p], probe_pos[3 * p + 1], probe_pos[3 * p + 2]};
+    double v;
     if (f < kNeigh * 10) {
         const int j = f / 10, c = f % 10;
         const int64_t gi = idx[p * kNeigh + j];
-        if (c < 3) v = (g.mean[3 * gi + c] - (c == 0 ? pp.x : (c == 1 ? pp.y : pp.z))) * 10.f;
-        else if (c < 6) v = logf(g.scale[3 * gi + c - 3]) + 5.f;
+        if (c < 3) v = ((double)g.mean[3 * gi + c] - pp[c]) * 10.0;
+        else if (c < 6) v = log((double)g.scale[3 * gi + c - 3]) + 5.0;
         else if (c == 6) v = g.opacity[gi];
         else v = g.rgb[3 * gi + c - 7];
     } else {
         const int e = f - kNeigh * 10, ax = e / 32, r = e % 32, fr = r % 16;
-        const double freq = 3.14159265358979323846 * exp2((double)fr / 3.0);
-        const float arg = (float)((double)(ax == 0 ? pp.x : (ax == 1 ? pp.y : pp.z)) * freq);
-        v = r < 16 ? sinf(arg) : cosf(arg);
+        const double arg = pp[ax] * (3.14159265358979323846 * exp2((double)fr / 3.0));
+        v = r < 16 ? sin(arg) : cos(arg);
     }
-    feats[i] = v;
+    feats[i] = (float)v;
 }
 
 // h1p[b] = W1p bf16(f_{pid[b]}) + b1, one thread per (probe, output).
