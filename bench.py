@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--probes", type=int, default=0, help="profiling aid: bake only the first N probes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-rebake measurement")
     return ap.parse_args()
 
 
@@ -183,11 +184,90 @@ def chosen_variant(sop, g, ppos, R, pargs, env, K, S, mode, out_ref, flush, step
             "query_point_dirs_per_s": round(M * S / (ms * 1e-3), 1), "rel_l1_vs_fp32_atlas": rel}
 
 
+def surrogate_variant(sop, dev, flush, steps, n_scenes=6, train_steps=4000):
+    """The learned rebake after the object's first ellipsoid moves: train on
+    bakes of random scenes (untimed), then time the rebake of the moved
+    scene's 4,096 probes (features, inference, 1% spot-check against the
+    ray-traced bake, fallback when the check fails) beside the plain bake."""
+    import torch
+    from paper_2510_07729_gb300 import inputs as I
+
+    def cu(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    surr = sop.Surrogate(I.surrogate_init(0), device=dev)
+    feats, atl = [], []
+    for s in range(n_scenes):
+        sc = I.surrogate_scene(1000 + s)
+        gt = {k: cu(v) for k, v in sc["gauss"].items()}
+        at = sop.make_atlas(cu(sc["probe_pos"]), 16)
+        sop.bake(gt, at)
+        atl.append(at)
+        feats.append(surr.features(gt, cu(sc["probe_pos"])))
+    rng = np.random.default_rng(0)
+    for it in range(train_steps):
+        j = int(rng.integers(n_scenes))
+        ids = cu(np.sort(rng.choice(4096, 64, replace=False)).astype(np.int32))
+        surr.train_step(feats[j], atl[j], lr=2e-3 if it < 0.7 * train_steps else 5e-4, probe_ids=ids)
+    mv = I.moved_object()
+    gt = {k: cu(v) for k, v in mv["gauss"].items()}
+    pp = cu(mv["probe_pos"])
+    exact = sop.make_atlas(pp, 16)
+    bws = sop.BakeWorkspace(len(mv["gauss"]["mean"]), dev)
+    out = sop.make_atlas(pp, 16)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(max(3, steps // 2)):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.mean(ts)), r
+
+    t_plain, _ = timed(lambda: sop.bake(gt, exact, workspace=bws))
+    t_rebake, (err, fell) = timed(lambda: sop.surrogate_rebake(surr, gt, out, spot_frac=0.01, tau=0.05, seed=3,
+                                                               bake_workspace=bws))
+    pred = sop.make_atlas(pp, 16)
+    surr.infer(surr.features(gt, pp), pred)
+    true_err = sop.atlas_compare(exact, pred)[0].item() / (4096 * 256)
+    texels = 4096 * 256
+    return {"what": "learned rebake (MLP surrogate, 1% spot-check, fallback to the ray-traced bake above "
+                    "mean |dO| 0.05) of 4,096 probes after the object's first ellipsoid moved",
+            "train": f"{n_scenes} random scenes x 4096 probes, {train_steps} Adam steps of 64 probes",
+            "rebake_ms": round(t_rebake, 4), "plain_bake_ms": round(t_plain, 4),
+            "rebake_texels_per_s": round(texels / (t_rebake * 1e-3), 1),
+            "speedup_vs_plain": round(t_plain / t_rebake, 3), "surrogate_mean_abs_dO": round(true_err, 5),
+            "spot_check_mean_abs_dO": round(err, 5), "fell_back": bool(fell)}
+
+
 def flop_per_point_dir(K, mode):
     f = 15 + 12 + 10 + K * (32 + 4) + 40 + 24 + 8 + 9
     if mode == 0:
         f += 12 + 15 + 8 + 4 + 12 + 12
     return f
+
+
+def reduce_max(vals, world, device):
+    """Per-rank timings -> their maximum over ranks (the slowest rank sets
+    the time of a weak-scaling step)."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_value(units_per_rank, ms_step, world):
+    """Units processed by all ranks per second of the (max-over-ranks) step."""
+    return world * units_per_rank / (ms_step * 1e-3)
 
 
 def main():
@@ -278,12 +358,7 @@ def main():
     t_trace = [r[4].elapsed_time(r[1]) for r in records] if do_bake else [0.0]
     t_query = [r[2].elapsed_time(r[3]) for r in records] if do_query else [0.0]
     ms_step = float(np.sum(t_bake) + np.sum(t_query)) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms_step, float(np.mean(t_bake)), float(np.mean(t_query))], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step, mb, mq = tt.tolist()
-    else:
-        mb, mq = float(np.mean(t_bake)), float(np.mean(t_query))
+    ms_step, mb, mq = reduce_max([ms_step, float(np.mean(t_bake)), float(np.mean(t_query))], world, dev)
 
     texels = P * R * R
     pd = M * S
@@ -291,7 +366,7 @@ def main():
         units, unit_name = texels, "texels/s"
     else:
         units, unit_name = pd, "point-dirs/s"
-    value = world * units / (ms_step * 1e-3)
+    value = whole_job_value(units, ms_step, world)
 
     # e2e: public API from pinned host buffers, H2D + bake + query + D2H each step
     e2e = None
@@ -323,9 +398,11 @@ def main():
                   "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
         if roof is None:
             roof = roof_q
-    chosen = None
+    chosen = surr = None
     if do_query and args.part == "step":
         chosen = chosen_variant(sop, g, ppos, R, pargs, env, K, S, mode, out, flush, args.steps)
+        if not args.no_surrogate and args.workload == "object":
+            surr = surrogate_variant(sop, dev, flush, args.steps)
 
     clocks = clk.summary()
     line = {
@@ -354,6 +431,7 @@ def main():
         "roofline": roof,
         "roofline_query": roof_q,
         "chosen": chosen,
+        "chosen_bake": surr,
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.part == "step":

@@ -1022,13 +1022,13 @@ __global__ void __launch_bounds__(256) shade_direct_kernel(const ShadeDirectK a)
         if (MODE == SOP_MODE_SHADE) {
             float3 h = w + wo;
             const float hl2 = dot3(h, h);
-            h = hl2 > 1e-30f ? (1.f / sqrtf(hl2)) * h : n;
+            h = hl2 > 1e-30f ? rsqrtf(hl2) * h : n;
             const float NdotH = dot3(n, h), VdotH = dot3(wo, h);
             const float3 cr = cross3(n, h);
             const float sin2 = dot3(cr, cr);
             const float den = NdotH * NdotH * a2 + sin2;
-            const float D = a2 / (kPi * den * den);
-            const float spec = D * specV / (NdotL * (1.f - kk) + kk);
+            const float D = __fdividef(a2, kPi * den * den);
+            const float spec = __fdividef(D * specV, NdotL * (1.f - kk) + kk);
             const float x1 = 1.f - VdotH, x2 = x1 * x1, fc = x2 * x2 * x1;
             acc0 += (kd.x + spec * (F0.x + (1.f - F0.x) * fc)) * (vis * Ld.x + pr.x) * NdotL;
             acc1 += (kd.y + spec * (F0.y + (1.f - F0.y) * fc)) * (vis * Ld.y + pr.y) * NdotL;
