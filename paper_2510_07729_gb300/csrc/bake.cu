@@ -51,8 +51,8 @@ BakeLayout bake_layout(int64_t N, int64_t entries_cap)
     L.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)(L.cells_cap + 1));
     L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
     L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)kMaxR * kMaxR);
-    L.entries = o;    o = align256(o + sizeof(int32_t) * (size_t)L.entries_cap);
     L.ent_sph = o;    o = align256(o + sizeof(float4) * (size_t)L.entries_cap);
+    L.ent_box = o;    o = align256(o + sizeof(float4) * (size_t)L.entries_cap);
     L.total = o;
     return L;
 }
@@ -191,11 +191,15 @@ __global__ void grid_setup_kernel(const int32_t* bbox, int64_t cells_cap, GaussG
     for (int c = threadIdx.x; c < G.ncells; c += blockDim.x) cell_cnt[c] = 0;
 }
 
-// Cells overlapped by the Gaussian's axis-aligned box (plus a margin that
-// covers the rounding of the grid walk's cell boundaries).
+// Cells overlapped by the Gaussian's axis-aligned box plus a margin. The
+// margin is far larger than the rounding of the grid walk's cell boundaries
+// and of the ray's entry into the box, so the cell in which the walk finds
+// the box entry always lists the Gaussian.
 __device__ __forceinline__ void cell_range(const GaussGrid& G, float3 mu, float4 r4, int lo[3], int hi[3])
 {
-    const float mg = kMarginRel * G.h;
+    float amax = 0.f;
+    for (int a = 0; a < 3; ++a) amax = fmaxf(amax, fmaxf(fabsf(G.origin[a]), fabsf(G.bmax[a])));
+    const float mg = 1e-3f * G.h + 16.f * FLT_EPSILON * amax;
     const float c[3] = {mu.x, mu.y, mu.z}, e[3] = {r4.y + mg, r4.z + mg, r4.w + mg};
     for (int a = 0; a < 3; ++a) {
         lo[a] = min(max((int)floorf((c[a] - e[a] - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
@@ -253,22 +257,24 @@ __global__ void __launch_bounds__(1024) bin_scan_kernel(GaussGrid* gridp, int32_
 
 __global__ void bin_fill_kernel(int64_t N, const GRec* __restrict__ rec, const GaussGrid* __restrict__ gridp,
                                 const int32_t* __restrict__ cell_start, int32_t* __restrict__ cell_cnt,
-                                int32_t* __restrict__ entries, float4* __restrict__ ent_sph)
+                                float4* __restrict__ ent_sph, float4* __restrict__ ent_box)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float4 r0 = rec[i].r0;
     if (r0.w < 0.f) return;
     const GaussGrid G = *gridp;
+    const float4 r4 = rec[i].r4;
+    const float4 box = make_float4(r4.y, r4.z, r4.w, __int_as_float((int32_t)i));
     int lo[3], hi[3];
-    cell_range(G, f3(r0.x, r0.y, r0.z), rec[i].r4, lo, hi);
+    cell_range(G, f3(r0.x, r0.y, r0.z), r4, lo, hi);
     for (int z = lo[2]; z <= hi[2]; ++z)
         for (int y = lo[1]; y <= hi[1]; ++y)
             for (int x = lo[0]; x <= hi[0]; ++x) {
                 const int c = (z * G.dims[1] + y) * G.dims[0] + x;
                 const int pos = cell_start[c] + atomicAdd(&cell_cnt[c], 1);
-                entries[pos] = (int32_t)i;
                 ent_sph[pos] = r0;
+                ent_box[pos] = box;
             }
 }
 
@@ -295,8 +301,8 @@ struct TraceK {
     const GRec* rec;
     const GaussGrid* grid;
     const int32_t* cell_start;
-    const int32_t* entries;
-    const float4* ent_sph;
+    const float4* ent_sph;  // per cell entry: centre, bounding-sphere radius
+    const float4* ent_box;  // per cell entry: box half extents, Gaussian index (bits)
     const float4* dirs;
     const float* probe_pos;
     int32_t P, R;
@@ -320,38 +326,336 @@ __device__ __forceinline__ uint64_t hit_key(float t, int32_t g)
     return ((uint64_t)o << 32) | (uint32_t)g;
 }
 
-// One warp per texel ray. Lanes share the grid walk (uniform control flow),
-// split each cell's entries, append hits to the warp's shared buffer, sort
-// them by (t*, index) with a bitonic network and composite 32 at a time with
-// a prefix product of (1 - alpha).
-__global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
+// Warp-uniform state of one texel ray, plus each lane's partial sums of the
+// composited terms (reduced once per ray).
+struct RayAcc {
+    float T, L0, L1, L2, Dacc, Wacc;
+    int n_eval, n_comp;
+    bool done;
+};
+
+// Exact responses of up to 32 queued candidates (one per lane). Hits are
+// appended to the warp's buffer key/alp[0, n); n keeps counting past
+// kHitCap, but nothing is written there.
+__device__ __forceinline__ void eval_batch(const TraceK& k, const float3 o, const float3 d, int32_t* que, int& qn,
+                                           uint64_t* key, float* alp, int& n, const int lane, RayAcc& acc)
+{
+    {
+        const int take = qn < 32 ? qn : 32;
+        acc.n_eval += take;
+        bool hit = false;
+        float ts = 0.f, al = 0.f;
+        int32_t gi = 0;
+        if (lane < take) {
+            gi = que[lane];
+            const GRec* gr = k.rec + gi;
+            const float4 r0 = __ldg(&gr->r0), r1 = __ldg(&gr->r1), r2 = __ldg(&gr->r2), r3 = __ldg(&gr->r3);
+            float hx, lx, hy, ly, hz, lz;
+            two_diff(o.x, r0.x, hx, lx);
+            two_diff(o.y, r0.y, hy, ly);
+            two_diff(o.z, r0.z, hz, lz);
+            const float u0 = fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz));
+            const float u1 = fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz));
+            const float u2 = fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz));
+            const float w0 = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
+            const float w1 = fmaf(r1.w, d.x, fmaf(r2.x, d.y, r2.y * d.z));
+            const float w2 = fmaf(r2.z, d.x, fmaf(r2.w, d.y, r3.x * d.z));
+            const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+            const float B = fmaf(w0, u0, fmaf(w1, u1, w2 * u2));
+            ts = -B / A;
+            if (ts > k.t_near) {
+                const float ex = fmaf(ts, d.x, hx) + lx, ey = fmaf(ts, d.y, hy) + ly, ez = fmaf(ts, d.z, hz) + lz;
+                const float v0 = fmaf(r1.x, ex, fmaf(r1.y, ey, r1.z * ez));
+                const float v1 = fmaf(r1.w, ex, fmaf(r2.x, ey, r2.y * ez));
+                const float v2 = fmaf(r2.z, ex, fmaf(r2.w, ey, r3.x * ez));
+                const float m2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
+                const float resp = r3.y * expf(-0.5f * m2);
+                if (resp >= k.alpha_min) {
+                    hit = true;
+                    al = fminf(resp, k.alpha_max);
+                }
+            }
+        }
+        __syncwarp();
+        // drop the evaluated candidates (with take == 32 the sources lie at
+        // 32 and above and the destinations below 32, so nothing overlaps)
+        if (lane < qn - take) que[lane] = que[lane + take];
+        qn -= take;
+        __syncwarp();
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int pos = n + __popc(m & ((1u << lane) - 1u));
+            if (pos < kHitCap) {
+                key[pos] = hit_key(ts, gi);
+                alp[pos] = al;
+            }
+        }
+        n += __popc(m);
+        __syncwarp();
+    }
+}
+
+// Sorts key/alp[0, n) (n <= kHitCap) by key: ranks for a few hits, a bitonic
+// network over the lanes up to 32, a shared-memory bitonic network above.
+__device__ __forceinline__ void sort_hits(uint64_t* key, float* alp, const int n, const int lane)
+{
+    __syncwarp();
+    if (n > 32) {
+        int P2 = 64;
+        while (P2 < n) P2 <<= 1;
+        for (int i = n + lane; i < P2; i += 32) {
+            key[i] = ~0ull;
+            alp[i] = 0.f;
+        }
+        __syncwarp();
+        for (int kk = 2; kk <= P2; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < P2; i += 32) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint64_t a = key[i], b = key[ixj];
+                        const bool up = (i & kk) == 0;
+                        if ((a > b) == up) {
+                            key[i] = b;
+                            key[ixj] = a;
+                            const float ta = alp[i];
+                            alp[i] = alp[ixj];
+                            alp[ixj] = ta;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    } else if (n > 1 && n <= 12) {
+        // each lane's rank is the number of smaller keys
+        const uint64_t kv = lane < n ? key[lane] : ~0ull;
+        const float av = lane < n ? alp[lane] : 0.f;
+        int rank = 0;
+        for (int j = 0; j < n; ++j) rank += __shfl_sync(0xffffffffu, kv, j) < kv ? 1 : 0;
+        __syncwarp();
+        if (lane < n) {
+            key[rank] = kv;
+            alp[rank] = av;
+        }
+    } else if (n > 1) {
+        uint64_t kv = lane < n ? key[lane] : ~0ull;
+        float av = lane < n ? alp[lane] : 0.f;
+#pragma unroll
+        for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                const uint64_t ko = __shfl_xor_sync(0xffffffffu, kv, j);
+                const float ao = __shfl_xor_sync(0xffffffffu, av, j);
+                const bool lower = (lane & j) == 0;
+                const bool up = (lane & kk) == 0;
+                // keep the smaller key on the lower lane of an ascending pair
+                const bool tk = (lower == up) ? (ko < kv) : (ko > kv);
+                if (tk) {
+                    kv = ko;
+                    av = ao;
+                }
+            }
+        }
+        if (lane < n) {
+            key[lane] = kv;
+            alp[lane] = av;
+        }
+    }
+    __syncwarp();
+}
+
+// Composites the hits with t* < thr (every hit when `all`). They move to the
+// scratch buffer dkey/dalp (the others close up, in order, at the front of
+// key/alp, and n becomes their count), are sorted by (t*, index) and taken
+// front to back, 32 at a time, with a prefix product of (1 - alpha). The
+// ray stops once the transmittance falls below t_stop.
+__device__ __forceinline__ void composite_hits(const TraceK& k, uint64_t* key, float* alp, uint64_t* dkey,
+                                               float* dalp, int& n, const bool all, const float thr, const int lane,
+                                               RayAcc& acc)
+{
+    const unsigned below = (1u << lane) - 1u;
+    int nd = 0, nr = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const bool in = i < n;
+        const uint64_t kv = in ? key[i] : 0ull;
+        const float av = in ? alp[i] : 0.f;
+        const float tv = o2f((int32_t)((uint32_t)(kv >> 32) ^ 0x80000000u));
+        const bool due = in && (all || tv < thr);
+        const unsigned dm = __ballot_sync(0xffffffffu, due), rm = __ballot_sync(0xffffffffu, in && !due);
+        __syncwarp();
+        if (due) {
+            const int j = nd + __popc(dm & below);
+            dkey[j] = kv;
+            dalp[j] = av;
+        } else if (in) {
+            // j <= i: the chunk was read before any of it is overwritten
+            const int j = nr + __popc(rm & below);
+            key[j] = kv;
+            alp[j] = av;
+        }
+        nd += __popc(dm);
+        nr += __popc(rm);
+        __syncwarp();
+    }
+    n = nr;
+    if (nd == 0) return;
+    sort_hits(dkey, dalp, nd, lane);
+    int used = 0;
+    for (int cb = 0; cb < nd && !acc.done; cb += 32) {
+        const int h = cb + lane;
+        const bool on = h < nd;
+        const uint64_t kh = on ? dkey[h] : 0ull;
+        const float th_hit = o2f((int32_t)((uint32_t)(kh >> 32) ^ 0x80000000u));
+        const float a = on ? dalp[h] : 0.f;
+        const int32_t gh = (int32_t)(uint32_t)(kh & 0xffffffffu);
+        // inclusive prefix product of (1 - alpha)
+        float pin = 1.f - a;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float v = __shfl_up_sync(0xffffffffu, pin, off);
+            if (lane >= off) pin *= v;
+        }
+        float pex = __shfl_up_sync(0xffffffffu, pin, 1);
+        if (lane == 0) pex = 1.f;
+        const float Tb = acc.T * pex, Ta = acc.T * pin;
+        // first lane whose transmittance after its hit is below t_stop
+        const unsigned stopm = __ballot_sync(0xffffffffu, on && Ta < k.t_stop);
+        const int stop_lane = stopm ? __ffs(stopm) - 1 : 32;
+        const bool use = on && lane <= stop_lane;
+        const float w = use ? Tb * a : 0.f;
+        if (use) {
+            const float4 r3 = __ldg(&k.rec[gh].r3), r4 = __ldg(&k.rec[gh].r4);
+            acc.L0 = fmaf(w, r3.z, acc.L0);
+            acc.L1 = fmaf(w, r3.w, acc.L1);
+            acc.L2 = fmaf(w, r4.x, acc.L2);
+            acc.Dacc = fmaf(w, th_hit, acc.Dacc);
+            acc.Wacc += w;
+        }
+        const int cnt = stop_lane < 32 ? stop_lane + 1 : min(32, nd - cb);
+        used += cnt;
+        acc.T = __shfl_sync(0xffffffffu, Ta, cnt - 1);
+        if (stop_lane < 32) acc.done = true;
+    }
+    acc.n_comp += used;
+    if (acc.done) n = 0;
+    __syncwarp();
+}
+
+// Tests the cell entries [e0, e1) against the ray: bounding sphere, then the
+// ray's entry E into the Gaussian's box (not before the walk's start t0).
+// Gaussians with E in [tl, th_e) are queued. Queued candidates are evaluated
+// 32 at a time as the queue fills, and at the end while at least `least`
+// remain. Entries are loaded 32 ahead of the ones being tested: ps/pb hold
+// entries pe + lane, and the last batch of the range loads the first one of
+// the next range [nf, ne) (the next cell's, when the walk knows it).
+__device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const float3 d, const float3 iv,
+                                          const float t0, const int e0, const int e1, const int nf, const int ne,
+                                          const float tl, const float th_e, const int least, float4& ps,
+                                          float4& pb, int& pe, int32_t* que, int& qn, uint64_t* key, float* alp,
+                                          int& n, const int lane, RayAcc& acc)
+{
+    int eb = e0;
+    if (eb < e1 && pe != eb) {
+        pe = eb;
+        if (eb + lane < e1) {
+            ps = __ldg(k.ent_sph + eb + lane);
+            pb = __ldg(k.ent_box + eb + lane);
+        }
+    }
+    while (eb < e1 || (qn >= least && qn > 0)) {
+        if (eb < e1) {
+            const float4 r0 = ps, bx = pb;
+            const bool valid = eb + lane < e1;
+            eb += 32;
+            pe = eb < e1 ? eb : (ne > nf ? nf : -1);
+            const int pl = eb < e1 ? e1 : ne;
+            if (pe + lane < pl) {
+                ps = __ldg(k.ent_sph + pe + lane);
+                pb = __ldg(k.ent_box + pe + lane);
+            }
+            const float3 del = f3(r0.x, r0.y, r0.z) - o;
+            const float tc = dot3(del, d);
+            const float dd = dot3(del, del);
+            // sphere: squared ray-centre distance |del|^2 - tc^2 with a margin
+            // larger than its rounding (filter only)
+            const bool sph = tc + r0.w >= tl && fmaf(-tc, tc, dd) <= fmaf(r0.w, r0.w, 1e-6f * dd);
+            float ta = (del.x - bx.x) * iv.x, tb = (del.x + bx.x) * iv.x;
+            float tin = fminf(ta, tb), tout = fmaxf(ta, tb);
+            ta = (del.y - bx.y) * iv.y;
+            tb = (del.y + bx.y) * iv.y;
+            tin = fmaxf(tin, fminf(ta, tb));
+            tout = fminf(tout, fmaxf(ta, tb));
+            ta = (del.z - bx.z) * iv.z;
+            tb = (del.z + bx.z) * iv.z;
+            tin = fmaxf(tin, fminf(ta, tb));
+            tout = fminf(tout, fmaxf(ta, tb));
+            const float E = fmaxf(tin, t0);
+            const bool pass = valid && sph && tout >= E && E >= tl && E < th_e;
+            const unsigned pm = __ballot_sync(0xffffffffu, pass);
+            if (pass) que[qn + __popc(pm & ((1u << lane) - 1u))] = __float_as_int(bx.w);
+            qn += __popc(pm);
+            __syncwarp();
+            if (qn < 32) continue;
+        }
+        eval_batch(k, o, d, que, qn, key, alp, n, lane, acc);
+    }
+}
+
+// hits (plus queued candidates) that make the walk stop to composite
+constexpr int kCompositeAt = 16;
+
+// One warp per texel ray. Lanes share the grid walk (uniform control flow)
+// and split each cell's entries. Every Gaussian is evaluated once per ray:
+// in the cell window that holds the ray's entry into its axis-aligned box.
+// Candidates queue across cells and are evaluated 32 at a time; their hits
+// (t*, alpha) wait in the warp's shared buffer. Once enough have gathered,
+// the buffer is sorted by (t*, index) and the hits whose t* the walk has
+// passed are composited, so that hits are taken in (t*, index) order even
+// when a box spans several cells. A cell whose entries alone could overflow
+// the buffer is taken in halves of its window until each part fits.
+__global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
 {
     __shared__ uint64_t s_key[kWarpsPerCta][kHitCap];
     __shared__ float s_alpha[kWarpsPerCta][kHitCap];
+    __shared__ uint64_t s_dkey[kWarpsPerCta][kHitCap];
+    __shared__ float s_dalpha[kWarpsPerCta][kHitCap];
     __shared__ int32_t s_que[kWarpsPerCta][64];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t* key = s_key[wib];
     float* alp = s_alpha[wib];
+    uint64_t* dkey = s_dkey[wib];
+    float* dalp = s_dalpha[wib];
     int32_t* que = s_que[wib];
     const int RR = k.R * k.R;
     const int64_t total = (int64_t)k.P * RR;
+    const GaussGrid G = *k.grid;
     // persistent warps: each takes the next texel ray from a global counter,
-    // so long rays (escaping the object) do not hold up short ones
-    for (;;) {
+    // so long rays (escaping the object) do not hold up short ones; the next
+    // ray's number is fetched while the current ray is traced
     unsigned long long rr = 0;
     if (lane == 0) rr = atomicAdd(k.stats, 1ull);
+    for (;;) {
     const int64_t ray = (int64_t)__shfl_sync(0xffffffffu, rr, 0);
     if (ray >= total) break;
+    if (lane == 0) rr = atomicAdd(k.stats, 1ull);
     const int p = (int)(ray / RR), t = (int)(ray % RR);
-    const GaussGrid G = *k.grid;
     const float4 d4 = __ldg(k.dirs + t);
     const float3 d = f3(d4.x, d4.y, d4.z);
     const float3 o = load3(k.probe_pos, p);
-
-    // per-lane partial sums of the composited terms, reduced once per ray
-    float T = 1.f, L0 = 0.f, L1 = 0.f, L2 = 0.f, Dacc = 0.f, Wacc = 0.f;
-    bool done = false;
-    int n_eval = 0, n_comp = 0;  // warp-uniform work counters
+    // reciprocal direction for the box entries (a zero component becomes a
+    // tiny one: the slab along that axis is then all or nothing)
+    const float3 iv = f3(1.f / (fabsf(d.x) > 1e-30f ? d.x : 1e-30f), 1.f / (fabsf(d.y) > 1e-30f ? d.y : 1e-30f),
+                         1.f / (fabsf(d.z) > 1e-30f ? d.z : 1e-30f));
+    RayAcc acc;
+    acc.T = 1.f;
+    acc.L0 = acc.L1 = acc.L2 = acc.Dacc = acc.Wacc = 0.f;
+    acc.n_eval = acc.n_comp = 0;
+    acc.done = false;
+    int n = 0, qn = 0;  // hits in key/alp[0, n) (unsorted); candidates in que[0, qn)
+    float4 ps = make_float4(0.f, 0.f, 0.f, 0.f), pb = ps;  // entries pe + lane, loaded ahead
+    int pe = -1;
 
     // grid box entry/exit (slab test), per axis in scalars so that nothing
     // is indexed by a run-time axis (which would put it in local memory)
@@ -360,10 +664,9 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
     const int gdx = G.dims[0], gdy = G.dims[1], gdz = G.dims[2];
     const float gh = G.h, gih = G.inv_h;
     float t0 = 0.f, t1 = FLT_MAX;
-#define SOP_SLAB(OA, DA, LO, HI)                                     \
+#define SOP_SLAB(OA, DA, IA, LO, HI)                                 \
     if (DA != 0.f) {                                                 \
-        const float inv = 1.f / DA;                                  \
-        float ta = (LO - OA) * inv, tb = (HI - OA) * inv;            \
+        float ta = (LO - OA) * IA, tb = (HI - OA) * IA;              \
         if (ta > tb) {                                               \
             const float tmp = ta;                                    \
             ta = tb;                                                 \
@@ -374,9 +677,9 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
     } else if (OA < LO || OA > HI) {                                 \
         t1 = -1.f;                                                   \
     }
-    SOP_SLAB(o.x, d.x, gox, gmx)
-    SOP_SLAB(o.y, d.y, goy, gmy)
-    SOP_SLAB(o.z, d.z, goz, gmz)
+    SOP_SLAB(o.x, d.x, iv.x, gox, gmx)
+    SOP_SLAB(o.y, d.y, iv.y, goy, gmy)
+    SOP_SLAB(o.z, d.z, iv.z, goz, gmz)
 #undef SOP_SLAB
     if (G.n_entries > 0 && t0 <= t1) {
         int cx = min(max((int)floorf((o.x + t0 * d.x - gox) * gih), 0), gdx - 1);
@@ -386,236 +689,105 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
         const int sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
         const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
         // t at the next cell boundary along each axis, from the cell index
-#define SOP_TNEXT(S, C, GO, OA, DA) ((S) == 0 ? FLT_MAX : ((GO) + ((C) + ((S) > 0 ? 1 : 0)) * gh - (OA)) / (DA))
-        float tmx = SOP_TNEXT(sx, cx, gox, o.x, d.x);
-        float tmy = SOP_TNEXT(sy, cy, goy, o.y, d.y);
-        float tmz = SOP_TNEXT(sz, cz, goz, o.z, d.z);
+        // (no accumulated error; the bins' margin covers the rounding)
+#define SOP_TNEXT(S, C, GO, OA, IA) ((S) == 0 ? FLT_MAX : ((GO) + ((C) + ((S) > 0 ? 1 : 0)) * gh - (OA)) * (IA))
+        float tmx = SOP_TNEXT(sx, cx, gox, o.x, iv.x);
+        float tmy = SOP_TNEXT(sy, cy, goy, o.y, iv.y);
+        float tmz = SOP_TNEXT(sz, cz, goz, o.z, iv.z);
         float t_enter = t0;
-        while (!done) {
+        // entry range of the current cell; the next cell's range is loaded
+        // one cell ahead
+        int e0 = __ldg(k.cell_start + (cz * gdy + cy) * gdx + cx);
+        int e1 = __ldg(k.cell_start + (cz * gdy + cy) * gdx + cx + 1);
+        while (!acc.done) {
             const int ax = (tmx <= tmy && tmx <= tmz) ? 0 : (tmy <= tmz ? 1 : 2);
             const float tm = ax == 0 ? tmx : (ax == 1 ? tmy : tmz);
             float t_exit = fminf(tm, t1);
             if (t_exit < t_enter) t_exit = t_enter;
-            const int c = (cz * gdy + cy) * gdx + cx;
-            const int e0 = __ldg(k.cell_start + c), e1 = __ldg(k.cell_start + c + 1);
-            float tl = t_enter, th = t_exit;
+            // the last cell of the walk takes every box entry beyond it and
+            // composites every waiting hit
+            bool last = !(t_exit < t1);
+            if (!last) {
+                const int nx = ax == 0 ? cx + sx : (ax == 1 ? cy + sy : cz + sz);
+                const int nd = ax == 0 ? gdx : (ax == 1 ? gdy : gdz);
+                last = nx < 0 || nx >= nd;
+            }
+            int ne0 = 0, ne1 = 0;
+            if (!last) {
+                const int cn = (cz * gdy + cy) * gdx + cx + (ax == 0 ? sx : (ax == 1 ? sy * gdx : sz * gdx * gdy));
+                ne0 = __ldg(k.cell_start + cn);
+                ne1 = __ldg(k.cell_start + cn + 1);
+            }
+            const float tl = t_enter;
+            // mode 0: the cell cannot overflow the hit buffer; scan it, and
+            //   composite once enough hits have gathered (or at the end).
+            // mode 1: it could; first composite what lies before it, then go
+            //   on in mode 0 if the cell now fits, else in
+            // mode 2: take its window in parts [sl, sh), halving a part whose
+            //   hits overflow the buffer.
+            int mode = n + qn + (e1 - e0) <= kHitCap ? 0 : 1;
+            int from = mode == 0 ? e0 : e1, least = mode == 0 ? 32 : 1;
+            float sl = tl, sh = t_exit;
             int splits = 0;
-            while (e1 > e0) {
-                // ---- collect the hits with t* in [tl, th) -----------------
-                // cheap sphere test on every entry; survivors are queued and
-                // evaluated exactly 32 at a time so that all lanes are busy
-                int n = 0, qn = 0;
-                for (int eb = e0; eb < e1 || qn > 0; eb += 32) {
-                    if (eb < e1) {
-                        const int e = eb + lane;
-                        bool pass = false;
-                        if (e < e1) {
-                            const float4 r0 = __ldg(k.ent_sph + e);
-                            const float3 del = f3(r0.x, r0.y, r0.z) - o;
-                            const float tc = dot3(del, d);
-                            const float dd = dot3(del, del);
-                            // squared ray-centre distance |del|^2 - tc^2, with a
-                            // margin larger than its rounding (filter only)
-                            pass = tc + r0.w >= tl && tc - r0.w <= th &&
-                                   fmaf(-tc, tc, dd) <= fmaf(r0.w, r0.w, 1e-6f * dd);
-                        }
-                        const unsigned pm = __ballot_sync(0xffffffffu, pass);
-                        if (pass) que[qn + __popc(pm & ((1u << lane) - 1u))] = e;
-                        qn += __popc(pm);
-                        __syncwarp();
-                        if (qn < 32 && eb + 32 < e1) continue;  // batch up more candidates
-                    }
-                    // exact responses of up to 32 queued candidates, one per lane
-                    const int take = qn < 32 ? qn : 32;
-                    n_eval += take;
-                    bool hit = false;
-                    float ts = 0.f, al = 0.f;
-                    int32_t gi = 0;
-                    if (lane < take) {
-                        const int e = que[lane];
-                        const float4 r0 = __ldg(k.ent_sph + e);
-                        const float3 mu = f3(r0.x, r0.y, r0.z);
-                        gi = __ldg(k.entries + e);
-                        const float4 r1 = __ldg(&k.rec[gi].r1), r2 = __ldg(&k.rec[gi].r2), r3 = __ldg(&k.rec[gi].r3);
-                        float hx, lx, hy, ly, hz, lz;
-                        two_diff(o.x, mu.x, hx, lx);
-                        two_diff(o.y, mu.y, hy, ly);
-                        two_diff(o.z, mu.z, hz, lz);
-                        const float u0 = fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz));
-                        const float u1 = fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz));
-                        const float u2 = fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz));
-                        const float w0 = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
-                        const float w1 = fmaf(r1.w, d.x, fmaf(r2.x, d.y, r2.y * d.z));
-                        const float w2 = fmaf(r2.z, d.x, fmaf(r2.w, d.y, r3.x * d.z));
-                        const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-                        const float B = fmaf(w0, u0, fmaf(w1, u1, w2 * u2));
-                        ts = -B / A;
-                        if (ts > k.t_near && ts >= tl && ts < th) {
-                            const float ex = fmaf(ts, d.x, hx) + lx, ey = fmaf(ts, d.y, hy) + ly,
-                                        ez = fmaf(ts, d.z, hz) + lz;
-                            const float v0 = fmaf(r1.x, ex, fmaf(r1.y, ey, r1.z * ez));
-                            const float v1 = fmaf(r1.w, ex, fmaf(r2.x, ey, r2.y * ez));
-                            const float v2 = fmaf(r2.z, ex, fmaf(r2.w, ey, r3.x * ez));
-                            const float m2 = fmaf(v0, v0, fmaf(v1, v1, v2 * v2));
-                            const float resp = r3.y * expf(-0.5f * m2);
-                            if (resp >= k.alpha_min) {
-                                hit = true;
-                                al = fminf(resp, k.alpha_max);
-                            }
-                        }
-                    }
-                    __syncwarp();
-                    // drop the evaluated candidates from the queue
-                    if (lane < qn - take) que[lane] = que[lane + take];
-                    qn -= take;
-                    __syncwarp();
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (hit) {
-                        const int pos = n + __popc(m & ((1u << lane) - 1u));
-                        if (pos < kHitCap) {
-                            key[pos] = hit_key(ts, gi);
-                            alp[pos] = al;
-                        }
-                    }
-                    n += __popc(m);
-                }
-                if (n > kHitCap) {
-                    // too many hits in this window: halve it and rescan
-                    if (++splits > 40 || !(th > tl)) {
-                        if (lane == 0) atomicOr(k.stats + 3, 1ull);
-                        break;
-                    }
-                    th = tl + 0.5f * (th - tl);
+            for (;;) {
+                const bool sfin = last && !(sh < t_exit);
+                const float lo = mode == 2 ? sl : tl;
+                const float hi_e = (mode == 2 ? sfin : last) ? FLT_MAX : (mode == 2 ? sh : t_exit);
+                const int nb = n;
+                // in mode 0 the walk goes on to the next cell: load its first entries
+                scan_eval(k, o, d, iv, t0, from, e1, mode == 0 ? ne0 : 0, mode == 0 ? ne1 : 0, lo, hi_e, least, ps,
+                          pb, pe, que, qn, key, alp, n, lane, acc);
+                if (mode == 0 && least == 32) {
+                    if (!(last || n + qn >= kCompositeAt)) break;
+                    from = e1;  // evaluate what is still queued, then composite
+                    least = 1;
                     continue;
                 }
-                // ---- sort the n hits by (t*, index) --------------------------
-                if (n > 32) {
-                    int P2 = 64;
-                    while (P2 < n) P2 <<= 1;
-                    for (int i = n + lane; i < P2; i += 32) {
-                        key[i] = ~0ull;
-                        alp[i] = 0.f;
+                if (mode == 2 && n > kHitCap) {
+                    n = nb;
+                    if (++splits > 40 || !(sh > sl)) {
+                        if (lane == 0) atomicOr(k.stats + 3, 1ull);
+                        acc.done = true;
+                        break;
                     }
-                    __syncwarp();
-                    for (int kk = 2; kk <= P2; kk <<= 1) {
-                        for (int j = kk >> 1; j > 0; j >>= 1) {
-                            for (int i = lane; i < P2; i += 32) {
-                                const int ixj = i ^ j;
-                                if (ixj > i) {
-                                    const uint64_t a = key[i], b = key[ixj];
-                                    const bool up = (i & kk) == 0;
-                                    if ((a > b) == up) {
-                                        key[i] = b;
-                                        key[ixj] = a;
-                                        const float ta = alp[i];
-                                        alp[i] = alp[ixj];
-                                        alp[ixj] = ta;
-                                    }
-                                }
-                            }
-                            __syncwarp();
-                        }
-                    }
-                } else if (n > 1 && n <= 12) {
-                    // few hits: each lane's rank is the number of smaller keys
-                    __syncwarp();
-                    const uint64_t kv = lane < n ? key[lane] : ~0ull;
-                    const float av = lane < n ? alp[lane] : 0.f;
-                    int rank = 0;
-                    for (int j = 0; j < n; ++j) rank += __shfl_sync(0xffffffffu, kv, j) < kv ? 1 : 0;
-                    __syncwarp();
-                    if (lane < n) {
-                        key[rank] = kv;
-                        alp[rank] = av;
-                    }
-                } else if (n > 1) {
-                    // one hit per lane, bitonic network over the 32 lanes
-                    __syncwarp();
-                    uint64_t kv = lane < n ? key[lane] : ~0ull;
-                    float av = lane < n ? alp[lane] : 0.f;
-#pragma unroll
-                    for (int kk = 2; kk <= 32; kk <<= 1) {
-#pragma unroll
-                        for (int j = kk >> 1; j > 0; j >>= 1) {
-                            const uint64_t ko = __shfl_xor_sync(0xffffffffu, kv, j);
-                            const float ao = __shfl_xor_sync(0xffffffffu, av, j);
-                            const bool lower = (lane & j) == 0;
-                            const bool up = (lane & kk) == 0;
-                            // keep the smaller key on the lower lane of an ascending pair
-                            const bool take = (lower == up) ? (ko < kv) : (ko > kv);
-                            if (take) {
-                                kv = ko;
-                                av = ao;
-                            }
-                        }
-                    }
-                    if (lane < n) {
-                        key[lane] = kv;
-                        alp[lane] = av;
-                    }
+                    sh = sl + 0.5f * (sh - sl);
+                    continue;
                 }
-                __syncwarp();
-                // ---- composite 32 hits at a time ------------------------------
-                for (int cb = 0; cb < n && !done; cb += 32) {
-                    const int h = cb + lane;
-                    const bool on = h < n;
-                    const uint64_t kh = on ? key[h] : 0ull;
-                    const float a = on ? alp[h] : 0.f;
-                    const int32_t gh = (int32_t)(uint32_t)(kh & 0xffffffffu);
-                    const float th_hit = o2f((int32_t)((uint32_t)(kh >> 32) ^ 0x80000000u));
-                    // inclusive prefix product of (1 - alpha)
-                    float pin = 1.f - a;
-#pragma unroll
-                    for (int off = 1; off < 32; off <<= 1) {
-                        const float v = __shfl_up_sync(0xffffffffu, pin, off);
-                        if (lane >= off) pin *= v;
-                    }
-                    float pex = __shfl_up_sync(0xffffffffu, pin, 1);
-                    if (lane == 0) pex = 1.f;
-                    const float Tb = T * pex, Ta = T * pin;
-                    // first lane whose transmittance after its hit is below t_stop
-                    const unsigned stopm = __ballot_sync(0xffffffffu, on && Ta < k.t_stop);
-                    const int stop_lane = stopm ? __ffs(stopm) - 1 : 32;
-                    const bool use = on && lane <= stop_lane;
-                    const float w = use ? Tb * a : 0.f;
-                    if (use) {
-                        const float4 r3 = __ldg(&k.rec[gh].r3), r4 = __ldg(&k.rec[gh].r4);
-                        L0 = fmaf(w, r3.z, L0);
-                        L1 = fmaf(w, r3.w, L1);
-                        L2 = fmaf(w, r4.x, L2);
-                        Dacc = fmaf(w, th_hit, Dacc);
-                        Wacc += w;
-                    }
-                    const int last = stop_lane < 32 ? stop_lane : min(31, n - cb - 1);
-                    n_comp += last + 1;
-                    T = __shfl_sync(0xffffffffu, Ta, last);
-                    if (stop_lane < 32) done = true;
+                composite_hits(k, key, alp, dkey, dalp, n, mode == 0 ? last : (mode == 2 && sfin),
+                               mode == 0 ? t_exit : (mode == 1 ? tl : sh), lane, acc);
+                if (acc.done || mode == 0) break;
+                if (mode == 2) {
+                    if (!(sh < t_exit)) break;
+                    sl = sh;
+                    sh = t_exit;
+                    splits = 0;
+                } else {
+                    // the waiting hits are now those beyond tl: the cell may fit
+                    mode = n + (e1 - e0) <= kHitCap ? 0 : 2;
+                    least = mode == 0 ? 32 : 1;
                 }
-                __syncwarp();
-                if (done || !(th < t_exit)) break;
-                tl = th;
-                th = t_exit;
-                splits = 0;
+                from = e0;
             }
-            if (done || t_exit >= t1) break;
+            if (acc.done || last) break;
+            e0 = ne0;
+            e1 = ne1;
             // step one cell; the boundary is recomputed from the cell index
             // (no accumulated error)
             if (ax == 0) {
                 cx += sx;
-                if (cx < 0 || cx >= gdx) break;
-                tmx = SOP_TNEXT(sx, cx, gox, o.x, d.x);
+                tmx = SOP_TNEXT(sx, cx, gox, o.x, iv.x);
             } else if (ax == 1) {
                 cy += sy;
-                if (cy < 0 || cy >= gdy) break;
-                tmy = SOP_TNEXT(sy, cy, goy, o.y, d.y);
+                tmy = SOP_TNEXT(sy, cy, goy, o.y, iv.y);
             } else {
                 cz += sz;
-                if (cz < 0 || cz >= gdz) break;
-                tmz = SOP_TNEXT(sz, cz, goz, o.z, d.z);
+                tmz = SOP_TNEXT(sz, cz, goz, o.z, iv.z);
             }
             t_enter = t_exit;
         }
+#undef SOP_TNEXT
     }
+    float L0 = acc.L0, L1 = acc.L1, L2 = acc.L2, Dacc = acc.Dacc, Wacc = acc.Wacc;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         L0 += __shfl_xor_sync(0xffffffffu, L0, off);
@@ -628,7 +800,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
         // interior texel (t % R, t / R) of probe p, stored at (+1, +1)
         const int RS = k.R + 2;
         const int64_t ti = (int64_t)p * RS * RS + (int64_t)(t / k.R + 1) * RS + (t % k.R + 1);
-        const float4 v = make_float4(L0, L1, L2, 1.f - T);
+        const float4 v = make_float4(L0, L1, L2, 1.f - acc.T);
         switch (k.rgbo_dtype) {
         case SOP_F32: reinterpret_cast<float4*>(k.rgbo)[ti] = v; break;
         case SOP_BF16: reinterpret_cast<uint2*>(k.rgbo)[ti] = Texel<SOP_BF16>::pack(v); break;
@@ -643,11 +815,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceK k)
             default: reinterpret_cast<__nv_fp8_e4m3*>(k.depth)[ti] = __nv_fp8_e4m3(dv); break;
             }
         }
-        atomicAdd(k.stats + 1, (unsigned long long)n_eval);
-        atomicAdd(k.stats + 2, (unsigned long long)n_comp);
+        atomicAdd(k.stats + 1, (unsigned long long)acc.n_eval);
+        atomicAdd(k.stats + 2, (unsigned long long)acc.n_comp);
     }
     }  // next ray
-#undef SOP_TNEXT
 }
 
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s)
@@ -705,11 +876,11 @@ cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* 
     GRec* rec = reinterpret_cast<GRec*>(ws + L.rec);
     int32_t* cstart = reinterpret_cast<int32_t*>(ws + L.cell_start);
     int32_t* ccnt = reinterpret_cast<int32_t*>(ws + L.cell_cnt);
-    int32_t* ent = reinterpret_cast<int32_t*>(ws + L.entries);
     float4* sph = reinterpret_cast<float4*>(ws + L.ent_sph);
+    float4* box = reinterpret_cast<float4*>(ws + L.ent_box);
     const int bs = 256;
     if (g.n > 0)
-        bin_fill_kernel<<<(unsigned)((g.n + bs - 1) / bs), bs, 0, s>>>(g.n, rec, grid, cstart, ccnt, ent, sph);
+        bin_fill_kernel<<<(unsigned)((g.n + bs - 1) / bs), bs, 0, s>>>(g.n, rec, grid, cstart, ccnt, sph, box);
     return cudaGetLastError();
 }
 
@@ -726,8 +897,8 @@ cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp,
     k.rec = reinterpret_cast<GRec*>(ws + L.rec);
     k.grid = grid;
     k.cell_start = reinterpret_cast<int32_t*>(ws + L.cell_start);
-    k.entries = reinterpret_cast<int32_t*>(ws + L.entries);
     k.ent_sph = reinterpret_cast<float4*>(ws + L.ent_sph);
+    k.ent_box = reinterpret_cast<float4*>(ws + L.ent_box);
     k.dirs = dirs;
     k.probe_pos = atlas.probe_pos;
     k.P = atlas.P;

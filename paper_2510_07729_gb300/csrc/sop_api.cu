@@ -138,7 +138,7 @@ static sop_status bake_fit(int64_t n, void* ws, size_t ws_bytes, sop::BakeLayout
 {
     const sop::BakeLayout L0 = sop::bake_layout(n, 1);
     if (!ws || ws_bytes < L0.total) return check_ws(ws, ws_bytes, sop::bake_layout(n, 0).total);
-    int64_t cap = 64 + (int64_t)((ws_bytes - L0.total) / (sizeof(int32_t) + sizeof(float4)));
+    int64_t cap = 64 + (int64_t)((ws_bytes - L0.total) / sop::kBakeEntryBytes);
     L = sop::bake_layout(n, cap);
     while (L.total > ws_bytes && L.entries_cap > 1) L = sop::bake_layout(n, L.entries_cap - 1);
     return check_ws(ws, ws_bytes, L.total);
