@@ -318,6 +318,8 @@ struct TraceK {
 
 constexpr int kWarpsPerCta = 8;
 constexpr int kHitCap = 256;  // per-warp hit buffer (shared memory)
+// the bitonic sort pads a buffer to the next power of two within kHitCap
+static_assert((kHitCap & (kHitCap - 1)) == 0 && kHitCap >= 64, "kHitCap must be a power of two >= 64");
 
 // order-preserving 64-bit key of (t*, Gaussian index)
 __device__ __forceinline__ uint64_t hit_key(float t, int32_t g)
@@ -581,16 +583,11 @@ __device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const
             // sphere: squared ray-centre distance |del|^2 - tc^2 with a margin
             // larger than its rounding (filter only)
             const bool sph = tc + r0.w >= tl && fmaf(-tc, tc, dd) <= fmaf(r0.w, r0.w, 1e-6f * dd);
-            float ta = (del.x - bx.x) * iv.x, tb = (del.x + bx.x) * iv.x;
-            float tin = fminf(ta, tb), tout = fmaxf(ta, tb);
-            ta = (del.y - bx.y) * iv.y;
-            tb = (del.y + bx.y) * iv.y;
-            tin = fmaxf(tin, fminf(ta, tb));
-            tout = fminf(tout, fmaxf(ta, tb));
-            ta = (del.z - bx.z) * iv.z;
-            tb = (del.z + bx.z) * iv.z;
-            tin = fmaxf(tin, fminf(ta, tb));
-            tout = fminf(tout, fmaxf(ta, tb));
+            // box: slab entries/exits del*iv -+ e*|iv| per axis
+            const float px = del.x * iv.x, py = del.y * iv.y, pz = del.z * iv.z;
+            const float qx = bx.x * fabsf(iv.x), qy = bx.y * fabsf(iv.y), qz = bx.z * fabsf(iv.z);
+            const float tin = fmaxf(fmaxf(px - qx, py - qy), pz - qz);
+            const float tout = fminf(fminf(px + qx, py + qy), pz + qz);
             const float E = fmaxf(tin, t0);
             const bool pass = valid && sph && tout >= E && E >= tl && E < th_e;
             const unsigned pm = __ballot_sync(0xffffffffu, pass);
