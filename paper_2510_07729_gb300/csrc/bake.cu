@@ -51,8 +51,7 @@ BakeLayout bake_layout(int64_t N, int64_t entries_cap)
     L.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)(L.cells_cap + 1));
     L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
     L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)kMaxR * kMaxR);
-    L.ent_sph = o;    o = align256(o + sizeof(float4) * (size_t)L.entries_cap);
-    L.ent_box = o;    o = align256(o + sizeof(float4) * (size_t)L.entries_cap);
+    L.ent = o;        o = align256(o + sizeof(uint4) * (size_t)L.entries_cap);
     L.total = o;
     return L;
 }
@@ -191,16 +190,50 @@ __global__ void grid_setup_kernel(const int32_t* bbox, int64_t cells_cap, GaussG
     for (int c = threadIdx.x; c < G.ncells; c += blockDim.x) cell_cnt[c] = 0;
 }
 
-// Cells overlapped by the Gaussian's axis-aligned box plus a margin. The
-// margin is far larger than the rounding of the grid walk's cell boundaries
-// and of the ray's entry into the box, so the cell in which the walk finds
-// the box entry always lists the Gaussian.
-__device__ __forceinline__ void cell_range(const GaussGrid& G, float3 mu, float4 r4, int lo[3], int hi[3])
+// A cell entry is the Gaussian's box as the walk tests it, in 16 bytes: the
+// centre in 16-bit fixed point over the grid box (c = origin + q/65536 span),
+// the half extents in fp16, rounded up and widened by the centre's
+// quantisation error (so the box holds the alpha_min ellipsoid), and the
+// Gaussian's index. Binning and the walk decode it with the same arithmetic.
+__device__ __forceinline__ float qdecode(uint32_t q16, float span, float go)
+{
+    // q16 / 65536 exactly, from the bits of 1 + q16 / 65536
+    return fmaf(__uint_as_float(0x3f800000u | (q16 << 7)) - 1.f, span, go);
+}
+
+__device__ __forceinline__ float hdecode(uint32_t h16)
+{
+    return __half2float(__ushort_as_half((unsigned short)h16));
+}
+
+__device__ __forceinline__ uint4 make_entry(const GaussGrid& G, float3 mu, float4 r4, int32_t gi)
+{
+    const float m[3] = {mu.x, mu.y, mu.z}, e[3] = {r4.y, r4.z, r4.w};
+    uint32_t q[3], h[3];
+    for (int a = 0; a < 3; ++a) {
+        const float span = G.bmax[a] - G.origin[a];
+        const float v = rintf((m[a] - G.origin[a]) / span * 65536.f);
+        q[a] = (uint32_t)fminf(fmaxf(v, 0.f), 65535.f);
+        const float c = qdecode(q[a], span, G.origin[a]);
+        const float w = e[a] + fabsf(c - m[a]) + 1e-6f * (fabsf(m[a]) + span);
+        h[a] = __half_as_ushort(__float2half_ru(w));
+    }
+    return make_uint4(q[0] | (q[1] << 16), q[2] | (h[0] << 16), h[1] | (h[2] << 16), (uint32_t)gi);
+}
+
+// Cells overlapped by the entry's box plus a margin. The margin is far
+// larger than the rounding of the grid walk's cell boundaries and of the
+// ray's entry into the box, so the cell in which the walk finds the box
+// entry always lists the Gaussian.
+__device__ __forceinline__ void cell_range(const GaussGrid& G, const uint4 en, int lo[3], int hi[3])
 {
     float amax = 0.f;
     for (int a = 0; a < 3; ++a) amax = fmaxf(amax, fmaxf(fabsf(G.origin[a]), fabsf(G.bmax[a])));
     const float mg = 1e-3f * G.h + 16.f * FLT_EPSILON * amax;
-    const float c[3] = {mu.x, mu.y, mu.z}, e[3] = {r4.y + mg, r4.z + mg, r4.w + mg};
+    const float c[3] = {qdecode(en.x & 0xffffu, G.bmax[0] - G.origin[0], G.origin[0]),
+                        qdecode(en.x >> 16, G.bmax[1] - G.origin[1], G.origin[1]),
+                        qdecode(en.y & 0xffffu, G.bmax[2] - G.origin[2], G.origin[2])};
+    const float e[3] = {hdecode(en.y >> 16) + mg, hdecode(en.z & 0xffffu) + mg, hdecode(en.z >> 16) + mg};
     for (int a = 0; a < 3; ++a) {
         lo[a] = min(max((int)floorf((c[a] - e[a] - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
         hi[a] = min(max((int)floorf((c[a] + e[a] - G.origin[a]) * G.inv_h), 0), G.dims[a] - 1);
@@ -216,7 +249,7 @@ __global__ void bin_count_kernel(int64_t N, const GRec* __restrict__ rec, const 
     if (r0.w < 0.f) return;
     const GaussGrid G = *gridp;
     int lo[3], hi[3];
-    cell_range(G, f3(r0.x, r0.y, r0.z), rec[i].r4, lo, hi);
+    cell_range(G, make_entry(G, f3(r0.x, r0.y, r0.z), rec[i].r4, (int32_t)i), lo, hi);
     for (int z = lo[2]; z <= hi[2]; ++z)
         for (int y = lo[1]; y <= hi[1]; ++y)
             for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&cell_cnt[(z * G.dims[1] + y) * G.dims[0] + x], 1);
@@ -257,24 +290,22 @@ __global__ void __launch_bounds__(1024) bin_scan_kernel(GaussGrid* gridp, int32_
 
 __global__ void bin_fill_kernel(int64_t N, const GRec* __restrict__ rec, const GaussGrid* __restrict__ gridp,
                                 const int32_t* __restrict__ cell_start, int32_t* __restrict__ cell_cnt,
-                                float4* __restrict__ ent_sph, float4* __restrict__ ent_box)
+                                uint4* __restrict__ ent)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float4 r0 = rec[i].r0;
     if (r0.w < 0.f) return;
     const GaussGrid G = *gridp;
-    const float4 r4 = rec[i].r4;
-    const float4 box = make_float4(r4.y, r4.z, r4.w, __int_as_float((int32_t)i));
+    const uint4 en = make_entry(G, f3(r0.x, r0.y, r0.z), rec[i].r4, (int32_t)i);
     int lo[3], hi[3];
-    cell_range(G, f3(r0.x, r0.y, r0.z), r4, lo, hi);
+    cell_range(G, en, lo, hi);
     for (int z = lo[2]; z <= hi[2]; ++z)
         for (int y = lo[1]; y <= hi[1]; ++y)
             for (int x = lo[0]; x <= hi[0]; ++x) {
                 const int c = (z * G.dims[1] + y) * G.dims[0] + x;
                 const int pos = cell_start[c] + atomicAdd(&cell_cnt[c], 1);
-                ent_sph[pos] = r0;
-                ent_box[pos] = box;
+                ent[pos] = en;
             }
 }
 
@@ -301,8 +332,7 @@ struct TraceK {
     const GRec* rec;
     const GaussGrid* grid;
     const int32_t* cell_start;
-    const float4* ent_sph;  // per cell entry: centre, bounding-sphere radius
-    const float4* ent_box;  // per cell entry: box half extents, Gaussian index (bits)
+    const uint4* ent;  // cell entries (quantised box and Gaussian index)
     const float4* dirs;
     const float* probe_pos;
     int32_t P, R;
@@ -545,53 +575,46 @@ __device__ __forceinline__ void composite_hits(const TraceK& k, uint64_t* key, f
     __syncwarp();
 }
 
-// Tests the cell entries [e0, e1) against the ray: bounding sphere, then the
-// ray's entry E into the Gaussian's box (not before the walk's start t0).
+// Tests the cell entries [e0, e1) against the ray: the ray's entry E into
+// the entry's box (not before the walk's start t0).
 // Gaussians with E in [tl, th_e) are queued. Queued candidates are evaluated
 // 32 at a time as the queue fills, and at the end while at least `least`
-// remain. Entries are loaded 32 ahead of the ones being tested: ps/pb hold
-// entries pe + lane, and the last batch of the range loads the first one of
-// the next range [nf, ne) (the next cell's, when the walk knows it).
-__device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const float3 d, const float3 iv,
-                                          const float t0, const int e0, const int e1, const int nf, const int ne,
-                                          const float tl, const float th_e, const int least, float4& ps,
-                                          float4& pb, int& pe, int32_t* que, int& qn, uint64_t* key, float* alp,
-                                          int& n, const int lane, RayAcc& acc)
+// remain. Entries are loaded 32 ahead of the ones being tested: pv holds
+// entry pe + lane, and the last batch of the range loads the first one of
+// the next range [nf, ne) (the next cell's, when the walk knows it). go and
+// sp are the grid box's origin and span (the entries' fixed-point frame).
+__device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const float3 iv, const float3 go,
+                                          const float3 sp, const float t0, const int e0, const int e1,
+                                          const int nf, const int ne, const float tl, const float th_e,
+                                          const int least, uint4& pv, int& pe, int32_t* que, int& qn,
+                                          uint64_t* key, float* alp, int& n, const int lane, RayAcc& acc,
+                                          const float3 d)
 {
     int eb = e0;
     if (eb < e1 && pe != eb) {
         pe = eb;
-        if (eb + lane < e1) {
-            ps = __ldg(k.ent_sph + eb + lane);
-            pb = __ldg(k.ent_box + eb + lane);
-        }
+        if (eb + lane < e1) pv = __ldg(k.ent + eb + lane);
     }
     while (eb < e1 || (qn >= least && qn > 0)) {
         if (eb < e1) {
-            const float4 r0 = ps, bx = pb;
+            const uint4 en = pv;
             const bool valid = eb + lane < e1;
             eb += 32;
             pe = eb < e1 ? eb : (ne > nf ? nf : -1);
             const int pl = eb < e1 ? e1 : ne;
-            if (pe + lane < pl) {
-                ps = __ldg(k.ent_sph + pe + lane);
-                pb = __ldg(k.ent_box + pe + lane);
-            }
-            const float3 del = f3(r0.x, r0.y, r0.z) - o;
-            const float tc = dot3(del, d);
-            const float dd = dot3(del, del);
-            // sphere: squared ray-centre distance |del|^2 - tc^2 with a margin
-            // larger than its rounding (filter only)
-            const bool sph = tc + r0.w >= tl && fmaf(-tc, tc, dd) <= fmaf(r0.w, r0.w, 1e-6f * dd);
-            // box: slab entries/exits del*iv -+ e*|iv| per axis
-            const float px = del.x * iv.x, py = del.y * iv.y, pz = del.z * iv.z;
-            const float qx = bx.x * fabsf(iv.x), qy = bx.y * fabsf(iv.y), qz = bx.z * fabsf(iv.z);
+            if (pe + lane < pl) pv = __ldg(k.ent + pe + lane);
+            // box: slab entries/exits (c - o) iv -+ h |iv| per axis
+            const float px = (qdecode(en.x & 0xffffu, sp.x, go.x) - o.x) * iv.x;
+            const float py = (qdecode(en.x >> 16, sp.y, go.y) - o.y) * iv.y;
+            const float pz = (qdecode(en.y & 0xffffu, sp.z, go.z) - o.z) * iv.z;
+            const float qx = hdecode(en.y >> 16) * fabsf(iv.x), qy = hdecode(en.z & 0xffffu) * fabsf(iv.y),
+                        qz = hdecode(en.z >> 16) * fabsf(iv.z);
             const float tin = fmaxf(fmaxf(px - qx, py - qy), pz - qz);
             const float tout = fminf(fminf(px + qx, py + qy), pz + qz);
             const float E = fmaxf(tin, t0);
-            const bool pass = valid && sph && tout >= E && E >= tl && E < th_e;
+            const bool pass = valid && tout >= E && E >= tl && E < th_e;
             const unsigned pm = __ballot_sync(0xffffffffu, pass);
-            if (pass) que[qn + __popc(pm & ((1u << lane) - 1u))] = __float_as_int(bx.w);
+            if (pass) que[qn + __popc(pm & ((1u << lane) - 1u))] = (int32_t)en.w;
             qn += __popc(pm);
             __syncwarp();
             if (qn < 32) continue;
@@ -628,6 +651,8 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
     const int RR = k.R * k.R;
     const int64_t total = (int64_t)k.P * RR;
     const GaussGrid G = *k.grid;
+    const float3 go = f3(G.origin[0], G.origin[1], G.origin[2]);
+    const float3 sp = f3(G.bmax[0] - G.origin[0], G.bmax[1] - G.origin[1], G.bmax[2] - G.origin[2]);
     // persistent warps: each takes the next texel ray from a global counter,
     // so long rays (escaping the object) do not hold up short ones; the next
     // ray's number is fetched while the current ray is traced
@@ -651,7 +676,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
     acc.n_eval = acc.n_comp = 0;
     acc.done = false;
     int n = 0, qn = 0;  // hits in key/alp[0, n) (unsorted); candidates in que[0, qn)
-    float4 ps = make_float4(0.f, 0.f, 0.f, 0.f), pb = ps;  // entries pe + lane, loaded ahead
+    uint4 pv = make_uint4(0u, 0u, 0u, 0u);  // entry pe + lane, loaded ahead
     int pe = -1;
 
     // grid box entry/exit (slab test), per axis in scalars so that nothing
@@ -732,8 +757,8 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
                 const float hi_e = (mode == 2 ? sfin : last) ? FLT_MAX : (mode == 2 ? sh : t_exit);
                 const int nb = n;
                 // in mode 0 the walk goes on to the next cell: load its first entries
-                scan_eval(k, o, d, iv, t0, from, e1, mode == 0 ? ne0 : 0, mode == 0 ? ne1 : 0, lo, hi_e, least, ps,
-                          pb, pe, que, qn, key, alp, n, lane, acc);
+                scan_eval(k, o, iv, go, sp, t0, from, e1, mode == 0 ? ne0 : 0, mode == 0 ? ne1 : 0, lo, hi_e, least,
+                          pv, pe, que, qn, key, alp, n, lane, acc, d);
                 if (mode == 0 && least == 32) {
                     if (!(last || n + qn >= kCompositeAt)) break;
                     from = e1;  // evaluate what is still queued, then composite
@@ -873,11 +898,10 @@ cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* 
     GRec* rec = reinterpret_cast<GRec*>(ws + L.rec);
     int32_t* cstart = reinterpret_cast<int32_t*>(ws + L.cell_start);
     int32_t* ccnt = reinterpret_cast<int32_t*>(ws + L.cell_cnt);
-    float4* sph = reinterpret_cast<float4*>(ws + L.ent_sph);
-    float4* box = reinterpret_cast<float4*>(ws + L.ent_box);
+    uint4* ent = reinterpret_cast<uint4*>(ws + L.ent);
     const int bs = 256;
     if (g.n > 0)
-        bin_fill_kernel<<<(unsigned)((g.n + bs - 1) / bs), bs, 0, s>>>(g.n, rec, grid, cstart, ccnt, sph, box);
+        bin_fill_kernel<<<(unsigned)((g.n + bs - 1) / bs), bs, 0, s>>>(g.n, rec, grid, cstart, ccnt, ent);
     return cudaGetLastError();
 }
 
@@ -894,8 +918,7 @@ cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp,
     k.rec = reinterpret_cast<GRec*>(ws + L.rec);
     k.grid = grid;
     k.cell_start = reinterpret_cast<int32_t*>(ws + L.cell_start);
-    k.ent_sph = reinterpret_cast<float4*>(ws + L.ent_sph);
-    k.ent_box = reinterpret_cast<float4*>(ws + L.ent_box);
+    k.ent = reinterpret_cast<uint4*>(ws + L.ent);
     k.dirs = dirs;
     k.probe_pos = atlas.probe_pos;
     k.P = atlas.P;

@@ -66,11 +66,11 @@ cudaError_t launch_atlas_pack(const float* rgb, int rgb_stride, const float* occ
 
 // ---- bake -------------------------------------------------------------------
 struct BakeLayout {
-    size_t hdr, bbox, stats, rec, cell_start, cell_cnt, dirs, ent_sph, ent_box, total;
+    size_t hdr, bbox, stats, rec, cell_start, cell_cnt, dirs, ent, total;
     int64_t cells_cap, entries_cap;
 };
-// bytes per cell entry: (centre, sphere radius) and (box half extents, index)
-constexpr size_t kBakeEntryBytes = 32;
+// bytes per cell entry: quantised box and Gaussian index
+constexpr size_t kBakeEntryBytes = 16;
 // bake workspace layout for N Gaussians (independent of the atlas)
 BakeLayout bake_layout(int64_t N, int64_t entries_cap);
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s);
