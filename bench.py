@@ -125,11 +125,14 @@ def load_workload(name):
 # environment uv 2 atan2 (~40) + bilinear 3x4 FMA (24) + weights 8, BRDF
 # (half vector 12, dots 15, D 8, G 4, Fresnel 12, combine 12) and the
 # accumulation 9.
-# algorithmic FP32 work of the bake: an exact ray-Gaussian evaluation (the
-# probe offset split into two parts 18, M*offset 15, M*direction 15, A and B
-# 10, t* 2, closest point 9, M*point 15, m^2 5, response 4: ~93) and one
-# composited hit (1 - alpha, transmittance, weight, 3 colour, depth and
-# weight sums: ~15)
+# algorithmic FP32 work of the bake: a box test of one grid-cell entry
+# against a ray (centre decode 3 add + 3 FMA = 9, offset from the probe 3,
+# slab scaling 6, entries and exits 6, their max/min 4, the walk's start 1:
+# ~29), an exact ray-Gaussian evaluation (the probe offset split into two
+# parts 18, M*offset 15, M*direction 15, A and B 10, t* 2, closest point 9,
+# M*point 15, m^2 5, response 4: ~93) and one composited hit (1 - alpha,
+# transmittance, weight, 3 colour, depth and weight sums: ~15)
+FLOP_PER_TEST = 29
 FLOP_PER_EVAL = 93
 FLOP_PER_COMPOSITE = 15
 
@@ -378,14 +381,15 @@ def main():
     roof = roof_q = None
     peak_fp32 = N_SMS * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
     if do_bake:
-        n_eval, n_comp, status = sop.bake_stats(bws)
-        fl = n_eval * FLOP_PER_EVAL + n_comp * FLOP_PER_COMPOSITE
+        n_eval, n_comp, status, n_test = sop.bake_stats(bws)
+        fl = n_test * FLOP_PER_TEST + n_eval * FLOP_PER_EVAL + n_comp * FLOP_PER_COMPOSITE
         mt = float(np.mean(t_trace))
         ach = fl / (mt * 1e-3) / 1e12
         roof = {"kernel": "trace_kernel (sop_bake_trace)", "bound": "alu", "achieved": round(ach, 3),
                 "peak": round(peak_fp32, 1), "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
                 "traffic": traffic_for("trace_kernel", P),
-                "work": {"exact_evaluations": n_eval, "composited_hits": n_comp, "status_bits": status,
+                "work": {"box_tests": n_test, "exact_evaluations": n_eval, "composited_hits": n_comp,
+                         "status_bits": status, "flop_per_box_test": FLOP_PER_TEST,
                          "flop_per_evaluation": FLOP_PER_EVAL, "flop_per_composite": FLOP_PER_COMPOSITE},
                 "ms": round(mt, 4),
                 "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}

@@ -187,10 +187,11 @@ sop_status sop_bake_bin(const sop_gaussians* g, const sop_bake_params* params, v
 sop_status sop_bake_trace(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
                           size_t ws_bytes, void* stream);
 
-/* Work counters of the last sop_bake_trace on `ws` (synchronises stream):
- * out[0] = exact ray-Gaussian evaluations, out[1] = composited hits,
- * out[2] = status bits (bit 0: a grid cell held more hits with equal t* than
- * the hit buffer; that cell's later hits were dropped). */
+/* Work counters of the last sop_bake_trace on `ws` (synchronises stream);
+ * `out` holds 4 values: out[0] = exact ray-Gaussian evaluations, out[1] =
+ * composited hits, out[2] = status bits (bit 0: some ray met more hits at one
+ * t* than its hit buffer holds and stopped there), out[3] = grid-cell
+ * entries tested against rays (box tests). */
 sop_status sop_bake_stats(const void* ws, size_t ws_bytes, int64_t n_gauss, int64_t* out, void* stream);
 
 /* Workspace bytes for sop_query_shade / sop_query_shade_backward on M

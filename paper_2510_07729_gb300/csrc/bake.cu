@@ -46,7 +46,7 @@ BakeLayout bake_layout(int64_t N, int64_t entries_cap)
     size_t o = 0;
     L.hdr = o;        o = align256(o + sizeof(GaussGrid));
     L.bbox = o;       o = align256(o + 16 * sizeof(int32_t));
-    L.stats = o;      o = align256(o + 4 * sizeof(unsigned long long));
+    L.stats = o;      o = align256(o + 8 * sizeof(unsigned long long));
     L.rec = o;        o = align256(o + sizeof(GRec) * (size_t)(N > 0 ? N : 1));
     L.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)(L.cells_cap + 1));
     L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
@@ -342,7 +342,8 @@ struct TraceK {
     int32_t rgbo_dtype, depth_dtype;
     float inv_depth_scale;
     // stats[0]: next texel ray to trace; [1]: exact evaluations; [2]:
-    // composited hits; [3] bit 0: a cell window could not be split
+    // composited hits; [3] bit 0: a cell window could not be split; [4]: cell
+    // entries tested
     unsigned long long* stats;
 };
 
@@ -362,7 +363,7 @@ __device__ __forceinline__ uint64_t hit_key(float t, int32_t g)
 // composited terms (reduced once per ray).
 struct RayAcc {
     float T, L0, L1, L2, Dacc, Wacc;
-    int n_eval, n_comp;
+    int n_eval, n_comp, n_test;
     bool done;
 };
 
@@ -591,6 +592,7 @@ __device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const
                                           const float3 d)
 {
     int eb = e0;
+    if (eb < e1) acc.n_test += e1 - eb;
     if (eb < e1 && pe != eb) {
         pe = eb;
         if (eb + lane < e1) pv = __ldg(k.ent + eb + lane);
@@ -673,7 +675,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
     RayAcc acc;
     acc.T = 1.f;
     acc.L0 = acc.L1 = acc.L2 = acc.Dacc = acc.Wacc = 0.f;
-    acc.n_eval = acc.n_comp = 0;
+    acc.n_eval = acc.n_comp = acc.n_test = 0;
     acc.done = false;
     int n = 0, qn = 0;  // hits in key/alp[0, n) (unsorted); candidates in que[0, qn)
     uint4 pv = make_uint4(0u, 0u, 0u, 0u);  // entry pe + lane, loaded ahead
@@ -839,6 +841,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
         }
         atomicAdd(k.stats + 1, (unsigned long long)acc.n_eval);
         atomicAdd(k.stats + 2, (unsigned long long)acc.n_comp);
+        atomicAdd(k.stats + 4, (unsigned long long)acc.n_test);
     }
     }  // next ray
 }
@@ -889,7 +892,7 @@ __global__ void gutter_fill_kernel(int32_t P, int32_t R, void* __restrict__ rgbo
 
 __global__ void trace_reset_kernel(unsigned long long* stats)
 {
-    if (threadIdx.x < 4) stats[threadIdx.x] = 0ull;
+    if (threadIdx.x < 8) stats[threadIdx.x] = 0ull;
 }
 
 cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s)

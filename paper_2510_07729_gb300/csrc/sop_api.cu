@@ -202,7 +202,7 @@ sop_status sop_bake_stats(const void* ws, size_t ws_bytes, int64_t n_gauss, int6
     sop::BakeLayout L;
     sop_status st = bake_fit(n_gauss, const_cast<void*>(ws), ws_bytes, L);
     if (st != SOP_OK) return st;
-    unsigned long long v[4];
+    unsigned long long v[5];
     cudaStream_t s = (cudaStream_t)stream;
     st = cuda_status(cudaMemcpyAsync(v, (const char*)ws + L.stats, sizeof(v), cudaMemcpyDeviceToHost, s),
                      "sop_bake_stats");
@@ -212,6 +212,7 @@ sop_status sop_bake_stats(const void* ws, size_t ws_bytes, int64_t n_gauss, int6
     out[0] = (int64_t)v[1];
     out[1] = (int64_t)v[2];
     out[2] = (int64_t)v[3];
+    out[3] = (int64_t)v[4];
     return SOP_OK;
 }
 

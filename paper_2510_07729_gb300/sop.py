@@ -283,10 +283,11 @@ def bake_trace(gauss, atlas: Atlas, workspace: BakeWorkspace, t_near=0.0, alpha_
 
 
 def bake_stats(workspace: BakeWorkspace):
-    """(exact evaluations, composited hits, status bits) of the last trace."""
-    out = (C.c_int64 * 3)()
+    """(exact evaluations, composited hits, status bits, cell entries tested)
+    of the last trace."""
+    out = (C.c_int64 * 4)()
     _check(load().sop_bake_stats(_ptr(workspace.buf), workspace.buf.numel(), workspace.n, out, _stream()))
-    return int(out[0]), int(out[1]), int(out[2])
+    return int(out[0]), int(out[1]), int(out[2]), int(out[3])
 
 
 _bake_ws = {}

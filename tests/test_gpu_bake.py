@@ -90,3 +90,47 @@ def test_object_full_bake_sampled(sop, orc):
     o_rgb, o_occ, o_dep, fl = orc.bake(g, c["probe_pos"], c["R"], probes=probes)
     flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, "object")
     assert flagged <= 0.05 * fl.size
+
+
+def test_work_counters_tiny(sop, orc):
+    """With no early stop every hit is composited, so the composited count
+    equals the number of (texel ray, Gaussian) pairs with alpha >= 1/255 and
+    t* > 0, counted here by brute force in float64; each Gaussian is
+    evaluated at most once per ray, so evaluations do not exceed the box
+    tests and are at least the hits."""
+    c = I.make_tiny()
+    g, pp, R = c["gauss"], c["probe_pos"], c["R"]
+    at = sop.make_atlas(cuda(pp), R)
+    ws = sop.BakeWorkspace(len(g["mean"]), "cuda")
+    sop.bake({k: cuda(v) for k, v in g.items()}, at, t_stop=0.0, workspace=ws)
+    n_eval, n_comp, status, n_test = sop.bake_stats(ws)
+    assert status == 0
+    ii, jj = np.meshgrid(np.arange(R), np.arange(R), indexing="xy")
+    uv = np.stack([(ii.reshape(-1) + 0.5) / R, (jj.reshape(-1) + 0.5) / R], 1)
+    dirs = orc.oct_decode(uv)  # [R*R, 3]
+    mu = g["mean"].astype(np.float64)
+    s = g["scale"].astype(np.float64)
+    q = g["quat"].astype(np.float64)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w_, x_, y_, z_ = q.T
+    rot = np.stack([np.stack([1 - 2 * (y_ * y_ + z_ * z_), 2 * (x_ * y_ - w_ * z_), 2 * (x_ * z_ + w_ * y_)], -1),
+                    np.stack([2 * (x_ * y_ + w_ * z_), 1 - 2 * (x_ * x_ + z_ * z_), 2 * (y_ * z_ - w_ * x_)], -1),
+                    np.stack([2 * (x_ * z_ - w_ * y_), 2 * (y_ * z_ + w_ * x_), 1 - 2 * (x_ * x_ + y_ * y_)], -1)],
+                   1)
+    M = np.transpose(rot, (0, 2, 1)) / s[:, :, None]  # diag(1/s) R^T
+    op = g["opacity"].astype(np.float64)
+    hits = border = 0
+    for p in pp.astype(np.float64):
+        u = np.einsum("gab,gb->ga", M, p[None, :] - mu)  # [G, 3]
+        w = np.einsum("gab,tb->tga", M, dirs)  # [T, G, 3]
+        A = (w * w).sum(-1)
+        B = (w * u[None]).sum(-1)
+        ts = -B / A
+        m2 = (u * u).sum(-1)[None] - B * B / A
+        resp = op[None] * np.exp(-0.5 * m2)
+        hit = (ts > 0) & (resp >= 1.0 / 255.0)
+        hits += int(hit.sum())
+        border += int(((np.abs(resp * 255.0 - 1.0) < 1e-5) | (np.abs(ts) < 1e-6)).sum())
+    assert abs(n_comp - hits) <= border, (n_comp, hits, border)
+    assert n_comp <= n_eval <= n_test
+    assert n_eval <= len(mu) * len(pp) * R * R
