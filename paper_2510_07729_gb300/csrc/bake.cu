@@ -21,6 +21,8 @@
 // formed with an FMA, and m^2 is taken from the Mahalanobis norm of that
 // small vector, so alpha carries ~1e-7 relative error even for far, thin
 // Gaussians.
+#include <stdlib.h>
+
 #include "sop_device.cuh"
 #include "sop_internal.h"
 
@@ -345,6 +347,9 @@ struct TraceK {
     // composited hits; [3] bit 0: a cell window could not be split; [4]: cell
     // entries tested
     unsigned long long* stats;
+    // waiting hits plus candidates queued since the last composite that
+    // make the walk stop to composite
+    int32_t composite_at;
 };
 
 constexpr int kWarpsPerCta = 8;
@@ -588,8 +593,8 @@ __device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const
                                           const float3 sp, const float t0, const int e0, const int e1,
                                           const int nf, const int ne, const float tl, const float th_e,
                                           const int least, uint4& pv, int& pe, int32_t* que, int& qn,
-                                          uint64_t* key, float* alp, int& n, const int lane, RayAcc& acc,
-                                          const float3 d)
+                                          int& pend, uint64_t* key, float* alp, int& n, const int lane,
+                                          RayAcc& acc, const float3 d)
 {
     int eb = e0;
     if (eb < e1) acc.n_test += e1 - eb;
@@ -618,6 +623,7 @@ __device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const
             const unsigned pm = __ballot_sync(0xffffffffu, pass);
             if (pass) que[qn + __popc(pm & ((1u << lane) - 1u))] = (int32_t)en.w;
             qn += __popc(pm);
+            pend += __popc(pm);
             __syncwarp();
             if (qn < 32) continue;
         }
@@ -625,7 +631,7 @@ __device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const
     }
 }
 
-// hits (plus queued candidates) that make the walk stop to composite
+// default of TraceK::composite_at
 constexpr int kCompositeAt = 16;
 
 // One warp per texel ray. Lanes share the grid walk (uniform control flow)
@@ -637,6 +643,13 @@ constexpr int kCompositeAt = 16;
 // passed are composited, so that hits are taken in (t*, index) order even
 // when a box spans several cells. A cell whose entries alone could overflow
 // the buffer is taken in halves of its window until each part fits.
+// Binning fills each cell's entries in no fixed order, and which queued
+// candidates have been evaluated at a cell's end depends on that order. So
+// the decisions of when to composite and how to take a cell use only
+// order-free counts: nw, the hits left waiting by the last composite, plus
+// pend, the candidates queued since (an upper bound of hits + queue). At a
+// composite the queue is always empty, so the set of hits composited, and
+// with it every rounding, is the same on every run.
 __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
 {
     __shared__ uint64_t s_key[kWarpsPerCta][kHitCap];
@@ -678,6 +691,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
     acc.n_eval = acc.n_comp = acc.n_test = 0;
     acc.done = false;
     int n = 0, qn = 0;  // hits in key/alp[0, n) (unsorted); candidates in que[0, qn)
+    int nw = 0, pend = 0;  // hits waiting after the last composite; candidates queued since
     uint4 pv = make_uint4(0u, 0u, 0u, 0u);  // entry pe + lane, loaded ahead
     int pe = -1;
 
@@ -749,7 +763,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
             //   on in mode 0 if the cell now fits, else in
             // mode 2: take its window in parts [sl, sh), halving a part whose
             //   hits overflow the buffer.
-            int mode = n + qn + (e1 - e0) <= kHitCap ? 0 : 1;
+            int mode = nw + pend + (e1 - e0) <= kHitCap ? 0 : 1;
             int from = mode == 0 ? e0 : e1, least = mode == 0 ? 32 : 1;
             float sl = tl, sh = t_exit;
             int splits = 0;
@@ -757,18 +771,19 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
                 const bool sfin = last && !(sh < t_exit);
                 const float lo = mode == 2 ? sl : tl;
                 const float hi_e = (mode == 2 ? sfin : last) ? FLT_MAX : (mode == 2 ? sh : t_exit);
-                const int nb = n;
+                const int nb = n, pb = pend;
                 // in mode 0 the walk goes on to the next cell: load its first entries
                 scan_eval(k, o, iv, go, sp, t0, from, e1, mode == 0 ? ne0 : 0, mode == 0 ? ne1 : 0, lo, hi_e, least,
-                          pv, pe, que, qn, key, alp, n, lane, acc, d);
+                          pv, pe, que, qn, pend, key, alp, n, lane, acc, d);
                 if (mode == 0 && least == 32) {
-                    if (!(last || n + qn >= kCompositeAt)) break;
+                    if (!(last || nw + pend >= k.composite_at)) break;
                     from = e1;  // evaluate what is still queued, then composite
                     least = 1;
                     continue;
                 }
                 if (mode == 2 && n > kHitCap) {
                     n = nb;
+                    pend = pb;
                     if (++splits > 40 || !(sh > sl)) {
                         if (lane == 0) atomicOr(k.stats + 3, 1ull);
                         acc.done = true;
@@ -779,6 +794,8 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
                 }
                 composite_hits(k, key, alp, dkey, dalp, n, mode == 0 ? last : (mode == 2 && sfin),
                                mode == 0 ? t_exit : (mode == 1 ? tl : sh), lane, acc);
+                nw = n;
+                pend = 0;
                 if (acc.done || mode == 0) break;
                 if (mode == 2) {
                     if (!(sh < t_exit)) break;
@@ -936,6 +953,13 @@ cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp,
     k.depth_dtype = atlas.depth_dtype;
     k.inv_depth_scale = 1.f / atlas.depth_scale;
     k.stats = stats;
+    // SOP_BAKE_COMPOSITE_AT overrides the default for tuning
+    static const int composite_at = [] {
+        const char* e = getenv("SOP_BAKE_COMPOSITE_AT");
+        const int v = e ? atoi(e) : 0;
+        return (v >= 1 && v <= kHitCap / 2) ? v : kCompositeAt;
+    }();
+    k.composite_at = composite_at;
     const int64_t rays = (int64_t)atlas.P * R * R;
     // persistent grid: as many CTAs as fit on the device at once
     static int resident = 0;
