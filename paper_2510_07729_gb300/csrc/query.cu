@@ -8,6 +8,8 @@
 //                       integer stopping bound), then the Eq. 4-6 weights;
 //   env_pack_kernel     environment to float4 with a wrapped column and
 //                       clamped rows so the bilinear fetch needs no branches;
+//   atlas_quad_kernel   bilinear footprints of the atlas (RGBO, SHADE mode)
+//   / atlas_occ_quad_*  or occlusion alone (SHADOW mode reads only O);
 //   dirs_kernel         local light directions (Hammersley in fp64 -> fp32);
 //   shade_kernel        LANES threads per point split the S directions; per
 //                       direction one octahedral encode (world-frame maps),
@@ -310,6 +312,36 @@ __global__ void atlas_quad_kernel(const typename Texel<DT>::raw* __restrict__ at
     dst[3] = src[RS + 1];
 }
 
+// Occlusion footprints for SHADOW mode, which reads only O (Eq. 8): the
+// four O values of each footprint, as float4 (float32 atlas) or four
+// 16-bit values in 8 bytes, so one probe fetch is one 128/64-bit load.
+__global__ void atlas_occ_quad_f32_kernel(const float4* __restrict__ atlas, int32_t P, int32_t R,
+                                          float4* __restrict__ quads)
+{
+    const int RS = R + 2, RQ = R + 1;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)P * RQ * RQ) return;
+    const int64_t pr = i / (RQ * RQ);
+    const int r = (int)(i % (RQ * RQ));
+    const int b = r / RQ, a = r % RQ;
+    const float4* src = atlas + pr * RS * RS + (int64_t)b * RS + a;
+    quads[i] = make_float4(src[0].w, src[1].w, src[RS].w, src[RS + 1].w);
+}
+
+// 16-bit texels (R, G, B, O): O is the upper half of the second word.
+__global__ void atlas_occ_quad_16_kernel(const uint2* __restrict__ atlas, int32_t P, int32_t R,
+                                         uint2* __restrict__ quads)
+{
+    const int RS = R + 2, RQ = R + 1;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)P * RQ * RQ) return;
+    const int64_t pr = i / (RQ * RQ);
+    const int r = (int)(i % (RQ * RQ));
+    const int b = r / RQ, a = r % RQ;
+    const uint2* src = atlas + pr * RS * RS + (int64_t)b * RS + a;
+    quads[i] = make_uint2((src[0].y >> 16) | (src[1].y & 0xffff0000u), (src[RS].y >> 16) | (src[RS + 1].y & 0xffff0000u));
+}
+
 __device__ __forceinline__ double radical_inverse2(uint32_t i) { return (double)__brev(i) * 2.3283064365386963e-10; }
 
 // Local light directions: the caller's set, or the centred Hammersley set.
@@ -422,6 +454,29 @@ template <> struct Quad<SOP_BF16> {
     }
 };
 
+// One occlusion footprint: O at (a,b), (a+1,b), (a,b+1), (a+1,b+1).
+template <int DT> struct OQuad;
+template <> struct OQuad<SOP_F32> {
+    static __device__ __forceinline__ float4 load(const void* base, int64_t qi)
+    {
+        return __ldg(reinterpret_cast<const float4*>(base) + qi);
+    }
+};
+template <> struct OQuad<SOP_F16> {
+    static __device__ __forceinline__ float4 load(const void* base, int64_t qi)
+    {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(base) + qi);
+        return h4(v.x, v.y);
+    }
+};
+template <> struct OQuad<SOP_BF16> {
+    static __device__ __forceinline__ float4 load(const void* base, int64_t qi)
+    {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(base) + qi);
+        return b4(v.x, v.y);
+    }
+};
+
 struct ShadeK {
     const float *n, *wo, *albedo, *rough, *metal;
     int64_t M;
@@ -518,7 +573,13 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
         float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            if (k < a.K) {
+            if (MODE == SOP_MODE_SHADOW) {
+                if (k < a.K) {
+                    const float4 q = OQuad<DT>::load(a.quads, (int64_t)(base[k] + off));
+                    const float c00 = W[k] * w00, c10 = W[k] * w10, c01 = W[k] * w01, c11 = W[k] * w11;
+                    pr.w += c00 * q.x + c10 * q.y + c01 * q.z + c11 * q.w;
+                }
+            } else if (k < a.K) {
                 float4 t00, t10, t01, t11;
                 Quad<DT>::load(a.quads, (int64_t)(base[k] + off), t00, t10, t01, t11);
                 const float c00 = W[k] * w00, c10 = W[k] * w10, c01 = W[k] * w01, c11 = W[k] * w11;
@@ -619,7 +680,15 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
                                                                    a.We, reinterpret_cast<float4*>(ws + L.envq));
     const int64_t na = (int64_t)a.P * (a.R + 1) * (a.R + 1);
     const unsigned nba = (unsigned)((na + 255) / 256);
-    switch (a.rgbo_dtype) {
+    if (a.mode == SOP_MODE_SHADOW) {
+        // occlusion-only footprints (a quarter of the RGBO ones, same slot)
+        if (a.rgbo_dtype == SOP_F32)
+            atlas_occ_quad_f32_kernel<<<nba, 256, 0, s>>>(reinterpret_cast<const float4*>(a.rgbo), a.P, a.R,
+                                                          reinterpret_cast<float4*>(ws + L.quads));
+        else
+            atlas_occ_quad_16_kernel<<<nba, 256, 0, s>>>(reinterpret_cast<const uint2*>(a.rgbo), a.P, a.R,
+                                                         reinterpret_cast<uint2*>(ws + L.quads));
+    } else switch (a.rgbo_dtype) {
     case SOP_F32:
         atlas_quad_kernel<SOP_F32><<<nba, 256, 0, s>>>(reinterpret_cast<const float4*>(a.rgbo), a.P, a.R,
                                                       reinterpret_cast<float4*>(ws + L.quads));

@@ -113,6 +113,31 @@ def test_tiny_shadow_parity(sop, orc, tiny):
     assert_close(out, ro, what="shadow")
 
 
+def round_bf16(a):
+    """float32 -> nearest bfloat16 (ties to even), returned as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_16bit_atlas_exact_maps(sop, orc, tiny, dtype, mode):
+    """BF16 / FP16 atlases hold maps that are exact in that format: the GPU
+    output (FP32 arithmetic) then meets the FP64 oracle on the same maps
+    within the FP32 bound, in SHADE and SHADOW (occlusion-only footprints)
+    modes."""
+    c = tiny
+    maps = I.synthetic_maps(np.random.default_rng(30 + dtype), 64, 8)
+    rnd = round_bf16 if dtype == 1 else (lambda a: a.astype(np.float16).astype(np.float32))
+    maps = {k: rnd(v) for k, v in maps.items()}
+    at = atlas_from_maps(sop, c["probe_pos"], maps, dtype=dtype)
+    out, idx, _ = run_gpu(sop, c, at, c["K"], c["S"], mode=mode)
+    ro, ri, _ = run_orc(orc, c, maps, c["probe_pos"], c["K"], c["S"], mode=mode)
+    assert np.array_equal(idx, ri)
+    assert_close(out, ro, what=f"dtype {dtype} mode {mode}")
+
+
 @pytest.mark.parametrize("M", [1, 31, 4096 + 37])
 @pytest.mark.parametrize("K", [1, 3, 8, 32])
 def test_ragged_sizes_and_K(sop, orc, tiny, M, K):
