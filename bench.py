@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-rebake measurement")
+    ap.add_argument("--no-compose", action="store_true", help="skip the 1080p composition-frame query measurement")
     return ap.parse_args()
 
 
@@ -135,6 +136,16 @@ def load_workload(name):
 FLOP_PER_TEST = 29
 FLOP_PER_EVAL = 93
 FLOP_PER_COMPOSITE = 15
+
+
+def measured_peaks():
+    """(HBM GB/s, source) from the measured-peaks file at the repository
+    root, else the fallback copy bandwidth of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
 
 
 def traffic_for(kernel, P):
@@ -239,6 +250,13 @@ def surrogate_variant(sop, dev, flush, steps, n_scenes=6, train_steps=4000):
     pred = sop.make_atlas(pp, 16)
     surr.infer(surr.features(gt, pp), pred)
     true_err = sop.atlas_compare(exact, pred)[0].item() / (4096 * 256)
+    # the rebake's parts: features (32 nearest Gaussians of each probe),
+    # network inference, the 1% spot-check bake (binning + 41 probes)
+    feats = surr.features(gt, pp)
+    t_feat, _ = timed(lambda: surr.features(gt, pp))
+    t_inf, _ = timed(lambda: surr.infer(feats, pred))
+    spot = sop.make_atlas(pp[:41].contiguous(), 16)
+    t_spot, _ = timed(lambda: sop.bake(gt, spot, workspace=bws))
     texels = 4096 * 256
     return {"what": "learned rebake (MLP surrogate, 1% spot-check, fallback to the ray-traced bake above "
                     "mean |dO| 0.05) of 4,096 probes after the object's first ellipsoid moved",
@@ -246,11 +264,122 @@ def surrogate_variant(sop, dev, flush, steps, n_scenes=6, train_steps=4000):
             "rebake_ms": round(t_rebake, 4), "plain_bake_ms": round(t_plain, 4),
             "rebake_texels_per_s": round(texels / (t_rebake * 1e-3), 1),
             "speedup_vs_plain": round(t_plain / t_rebake, 3), "surrogate_mean_abs_dO": round(true_err, 5),
-            "spot_check_mean_abs_dO": round(err, 5), "fell_back": bool(fell)}
+            "spot_check_mean_abs_dO": round(err, 5), "fell_back": bool(fell),
+            "parts_ms": {"features": round(t_feat, 4), "inference": round(t_inf, 4),
+                         "spot_check_bake": round(t_spot, 4)},
+            "no_fallback_speedup": round(t_plain / (t_feat + t_inf + t_spot), 3)}
+
+
+def l2_read_peak_gbs(dev, reps=50):
+    """L2 read bandwidth measured in this run: a float32 sum over a 48 MB
+    buffer that stays resident in the 126 MB L2 (torch's reduction kernel;
+    bytes read / CUDA-event time, best of `reps`)."""
+    import torch
+    buf = torch.ones(12 << 20, dtype=torch.float32, device=dev)
+    out = torch.empty((), dtype=torch.float32, device=dev)
+    for _ in range(5):
+        torch.sum(buf, out=out)
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.sum(buf, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return buf.numel() * 4 / (best * 1e-3) / 1e9
+
+
+def query_demand(K, mode, texel_bytes):
+    """Algorithmic bytes of one shaded point-direction that the SMs must
+    receive from L2/L1: the 4 texels of each of K probe footprints (RGBO in
+    SHADE mode, O alone in SHADOW mode) and the 4 environment texels (RGB
+    fp32)."""
+    per_texel = texel_bytes if mode == 0 else texel_bytes // 4
+    return K * 4 * per_texel + 4 * 12
+
+
+def compose_frame_variant(sop, dev, flush, steps, l2_gbs, hbm_gbs, peak_fp32):
+    """The 1920x1080 composition frame (1.2M-Gaussian scene; 200k-Gaussian
+    object): object pixels SHADE against the 4,096 object probes, scene
+    pixels SHADOW against the 4,096 shadow-region probes (K=8, S=64), both
+    atlases baked from the object's Gaussians. Timed as the two
+    sop_query_shade calls of one frame, for a float32 and a float16 atlas,
+    with the HBM, L2 and FP32 roofs of that frame."""
+    import torch
+    from paper_2510_07729_gb300 import inputs as I
+    c = I.make_compose()
+    K, S, R = c["K"], c["S"], c["R"]
+
+    def cu(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    g = {k: cu(v) for k, v in c["gauss_object"].items()}
+    env = cu(c["env"])
+    parts = []
+    for name, mode in (("shade", 0), ("shadow", 1)):
+        d = c[name]
+        pts = [cu(d[k]) for k in ("x", "n", "wo", "albedo", "rough", "metal")]
+        parts.append(dict(name=name, mode=mode, pts=pts, pp=cu(d["probe_pos"]), M=len(d["x"])))
+    res = {"what": "1920x1080 composition frame: sop_query_shade of the object pixels (SHADE) and of the scene "
+                   "pixels (SHADOW), K=8, S=64, 2x4,096 probes at 16x16",
+           "points": {p["name"]: p["M"] for p in parts}}
+    outs = {}
+    for dt, label, tb in ((sop.SOP_F32, "fp32", 16), (sop.SOP_F16, "fp16", 8)):
+        for p in parts:
+            p["at"] = sop.make_atlas(p["pp"], R, rgbo_dtype=dt, depth_dtype=dt)
+            sop.bake(g, p["at"])
+            p["out"] = torch.empty((p["M"], 3), dtype=torch.float32, device=dev)
+            p["ws"] = torch.empty(sop.query_workspace_bytes(p["at"], p["M"], K, S, env.shape[0], env.shape[1],
+                                                            p["mode"]), dtype=torch.uint8, device=dev)
+
+        def call(p):
+            sop.query_shade(*p["pts"], p["at"], env, K, S, mode=p["mode"], out=p["out"], workspace=p["ws"])
+
+        for _ in range(3):
+            for p in parts:
+                call(p)
+        torch.cuda.synchronize()
+        ts, tp = [], {p["name"]: [] for p in parts}
+        for _ in range(steps):
+            flush.fill_(1)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
+            call(parts[0])
+            ev[1].record()
+            call(parts[1])
+            ev[2].record()
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[2]))
+            tp["shade"].append(ev[0].elapsed_time(ev[1]))
+            tp["shadow"].append(ev[1].elapsed_time(ev[2]))
+        ms = float(np.mean(ts))
+        pd = sum(p["M"] for p in parts) * S
+        fl = sum(flop_per_point_dir(K, p["mode"]) * p["M"] * S for p in parts)
+        dem = sum(query_demand(K, p["mode"], tb) * p["M"] * S for p in parts)
+        hbm = sum(68 * p["M"] for p in parts) + sum(p["at"].rgbo.numel() * p["at"].rgbo.element_size()
+                                                     for p in parts) + env.numel() * 4
+        t_hbm, t_l2, t_alu = hbm / (hbm_gbs * 1e9), dem / (l2_gbs * 1e9), fl / (peak_fp32 * 1e12)
+        bound = max((t_hbm, "hbm"), (t_l2, "l2"), (t_alu, "alu"))
+        outs[label] = [p["out"].clone() for p in parts]
+        res[label] = {"frame_ms": round(ms, 4), "shade_ms": round(float(np.mean(tp["shade"])), 4),
+                      "shadow_ms": round(float(np.mean(tp["shadow"])), 4),
+                      "point_dirs_per_s": round(pd / (ms * 1e-3), 1),
+                      "roofline": {"bound": bound[1], "t_hbm_ms": round(t_hbm * 1e3, 4),
+                                   "t_l2_ms": round(t_l2 * 1e3, 4), "t_alu_ms": round(t_alu * 1e3, 4),
+                                   "frac": round(bound[0] * 1e3 / ms, 4),
+                                   "l2_demand_bytes": int(dem), "hbm_bytes": int(hbm), "flop": int(fl)}}
+    num = sum((a - b).abs().sum().item() for a, b in zip(outs["fp16"], outs["fp32"]))
+    den = sum(b.abs().sum().item() for b in outs["fp32"])
+    res["fp16_rel_l1_vs_fp32_atlas"] = num / den
+    res["peaks"] = {"l2_read_gbs": round(l2_gbs, 1), "l2_note": "measured in this run (torch sum over a 48 MB "
+                    "L2-resident buffer)", "hbm_gbs": hbm_gbs, "fp32_tflops": round(peak_fp32, 1)}
+    return res
 
 
 def flop_per_point_dir(K, mode):
-    f = 15 + 12 + 10 + K * (32 + 4) + 40 + 24 + 8 + 9
+    # SHADOW mode blends the occlusion alone: 4 weight products + 4 FMA per probe
+    f = 15 + 12 + 10 + K * ((32 + 4) if mode == 0 else 12) + 40 + 24 + 8 + 9
     if mode == 0:
         f += 12 + 15 + 8 + 4 + 12 + 12
     return f
@@ -402,11 +531,14 @@ def main():
                   "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
         if roof is None:
             roof = roof_q
-    chosen = surr = None
+    chosen = surr = comp = None
     if do_query and args.part == "step":
         chosen = chosen_variant(sop, g, ppos, R, pargs, env, K, S, mode, out, flush, args.steps)
         if not args.no_surrogate and args.workload == "object":
             surr = surrogate_variant(sop, dev, flush, args.steps)
+        if not args.no_compose and args.workload == "object":
+            comp = compose_frame_variant(sop, dev, flush, args.steps, l2_read_peak_gbs(dev), measured_peaks()[0],
+                                         peak_fp32)
 
     clocks = clk.summary()
     line = {
@@ -436,6 +568,7 @@ def main():
         "roofline_query": roof_q,
         "chosen": chosen,
         "chosen_bake": surr,
+        "compose_frame_query": comp,
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.part == "step":
