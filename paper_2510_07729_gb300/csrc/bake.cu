@@ -40,10 +40,24 @@ struct GRec {
 constexpr float kMarginRel = 1e-4f;
 constexpr int kMaxR = 64;
 
+// Grid cells per Gaussian (the grid gets about half of cells_cap): SOP_BAKE_CELLS
+// overrides the default of one cell per 2 Gaussians (given as cells per 100
+// Gaussians, 5..400) for tuning.
+static int64_t cells_cap_for(int64_t N)
+{
+    static const int64_t per100 = [] {
+        const char* e = getenv("SOP_BAKE_CELLS");
+        const int v = e ? atoi(e) : 0;
+        return (int64_t)((v >= 5 && v <= 400) ? v : 50);
+    }();
+    const int64_t c = N * per100 / 100;
+    return c < 4096 ? 4096 : (c > (1 << 23) ? (1 << 23) : c);
+}
+
 BakeLayout bake_layout(int64_t N, int64_t entries_cap)
 {
     BakeLayout L{};
-    L.cells_cap = N / 2 < 4096 ? 4096 : (N / 2 > (1 << 23) ? (1 << 23) : N / 2);
+    L.cells_cap = cells_cap_for(N);
     L.entries_cap = entries_cap > 0 ? entries_cap : 24 * N + 65536;
     size_t o = 0;
     L.hdr = o;        o = align256(o + sizeof(GaussGrid));

@@ -571,15 +571,19 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
         const int off = j0 * RQ + i0;
         const float w00 = (1.f - fu) * (1.f - fv), w10 = fu * (1.f - fv), w01 = (1.f - fu) * fv, w11 = fu * fv;
         float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MODE == SOP_MODE_SHADOW) {
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
-            if (MODE == SOP_MODE_SHADOW) {
+            for (int k = 0; k < KMAX; ++k) {
                 if (k < a.K) {
                     const float4 q = OQuad<DT>::load(a.quads, (int64_t)(base[k] + off));
                     const float c00 = W[k] * w00, c10 = W[k] * w10, c01 = W[k] * w01, c11 = W[k] * w11;
                     pr.w += c00 * q.x + c10 * q.y + c01 * q.z + c11 * q.w;
                 }
-            } else if (k < a.K) {
+            }
+        } else
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (k < a.K) {
                 float4 t00, t10, t01, t11;
                 Quad<DT>::load(a.quads, (int64_t)(base[k] + off), t00, t10, t01, t11);
                 const float c00 = W[k] * w00, c10 = W[k] * w10, c01 = W[k] * w01, c11 = W[k] * w11;
@@ -919,6 +923,151 @@ size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K)
     return o;
 }
 
+// ---------------------------------------------------------------------------
+// Exact K <= 32 nearest sites, one warp per query point (the surrogate's 32
+// nearest Gaussians of each probe: few points, many sites, large K, where a
+// thread per point leaves most SMs idle and keeps its list in local memory).
+// The warp holds the best 32 (key, index) pairs, one per lane, ascending
+// over the lanes. Lanes scan a cell's entries 32 at a time; entries that
+// beat the current 32nd best are queued in shared memory, and every 32
+// queued ones are sorted across the lanes (bitonic) and merged into the
+// list (the elementwise minimum of the list and the reversed batch holds
+// the 32 smallest of both, as a bitonic sequence, which five more steps
+// sort). The ring search and its stopping bound are those of knn_kernel, so
+// the K nearest, and their order, are the same.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool kv_less(uint64_t ka, int32_t ia, uint64_t kb, int32_t ib)
+{
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// one compare-exchange step of a bitonic network over the lanes: the lower
+// lane of a pair keeps the smaller pair when `up`, the larger otherwise
+__device__ __forceinline__ void kv_step(uint64_t& k, int32_t& i, int lane, int j, bool up)
+{
+    const uint64_t ko = __shfl_xor_sync(0xffffffffu, k, j);
+    const int32_t io = __shfl_xor_sync(0xffffffffu, i, j);
+    const bool lower = (lane & j) == 0;
+    const bool take = (lower == up) ? kv_less(ko, io, k, i) : kv_less(k, i, ko, io);
+    if (take) {
+        k = ko;
+        i = io;
+    }
+}
+
+constexpr int kKnnWarps = 4;
+
+// merges que[0, min(qn, 32)) into the list (bk, bi); drops them from the queue
+__device__ __forceinline__ void knn_merge(uint64_t* qk, int32_t* qi, int& qn, uint64_t& bk, int32_t& bi, int lane)
+{
+    const int take = qn < 32 ? qn : 32;
+    uint64_t ck = lane < take ? qk[lane] : UINT64_MAX;
+    int32_t ci = lane < take ? qi[lane] : INT32_MAX;
+    __syncwarp();
+    if (lane < qn - take) {
+        qk[lane] = qk[lane + take];
+        qi[lane] = qi[lane + take];
+    }
+    qn -= take;
+    __syncwarp();
+#pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1)
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) kv_step(ck, ci, lane, j, (lane & kk) == 0);
+    // reversed batch against the list: the smaller of each pair
+    const uint64_t rk = __shfl_sync(0xffffffffu, ck, 31 - lane);
+    const int32_t ri = __shfl_sync(0xffffffffu, ci, 31 - lane);
+    if (kv_less(rk, ri, bk, bi)) {
+        bk = rk;
+        bi = ri;
+    }
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) kv_step(bk, bi, lane, j, true);
+}
+
+__global__ void __launch_bounds__(kKnnWarps * 32) knn_sites_warp_kernel(const float* __restrict__ x, int64_t M,
+                                                                         int32_t K,
+                                                                         const ProbeGrid* __restrict__ gridp,
+                                                                         const int32_t* __restrict__ cell_start,
+                                                                         const int4* __restrict__ entries,
+                                                                         int32_t* __restrict__ out_idx)
+{
+    __shared__ uint64_t s_qk[kKnnWarps][64];
+    __shared__ int32_t s_qi[kKnnWarps][64];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m = (int64_t)blockIdx.x * kKnnWarps + wib;
+    if (m >= M) return;  // warp-uniform
+    uint64_t* qk = s_qk[wib];
+    int32_t* qi = s_qi[wib];
+    const ProbeGrid G = *gridp;
+    const float3 xp = load3(x, m);
+    const int32_t q[3] = {quantise(xp.x), quantise(xp.y), quantise(xp.z)};
+    int64_t c[3], off_min = INT64_MAX;
+    for (int a = 0; a < 3; ++a) {
+        const int64_t rel = (int64_t)q[a] - G.qmin[a];
+        c[a] = floordiv(rel, G.cs);
+        const int64_t off = rel - c[a] * G.cs;
+        const int64_t m2 = off < G.cs - off ? off : G.cs - off;
+        off_min = m2 < off_min ? m2 : off_min;
+    }
+    uint64_t bk = UINT64_MAX;  // lane l: the (l+1)-th best so far
+    int32_t bi = INT32_MAX;
+    int qn = 0;
+    int64_t r0 = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int64_t d = c[a] < 0 ? -c[a] : (c[a] >= G.dims[a] ? c[a] - (G.dims[a] - 1) : 0);
+        r0 = d > r0 ? d : r0;
+    }
+    for (int64_t r = r0;; ++r) {
+        const int64_t zlo = max(c[2] - r, (int64_t)0), zhi = min(c[2] + r, (int64_t)G.dims[2] - 1);
+        const int64_t ylo = max(c[1] - r, (int64_t)0), yhi = min(c[1] + r, (int64_t)G.dims[1] - 1);
+        for (int64_t z = zlo; z <= zhi; ++z)
+            for (int64_t y = ylo; y <= yhi; ++y) {
+                const bool face = (z == c[2] - r) || (z == c[2] + r) || (y == c[1] - r) || (y == c[1] + r);
+                const int64_t xs = face ? 1 : 2 * r;
+                for (int64_t xx = c[0] - r; xx <= c[0] + r; xx += (xs > 0 ? xs : 1)) {
+                    if (xx < 0 || xx >= G.dims[0]) continue;
+                    const int cell = (int)((z * G.dims[1] + y) * G.dims[0] + xx);
+                    const int e0 = __ldg(cell_start + cell), e1 = __ldg(cell_start + cell + 1);
+                    const uint64_t wk = __shfl_sync(0xffffffffu, bk, 31);
+                    const int32_t wi = __shfl_sync(0xffffffffu, bi, 31);
+                    for (int eb = e0; eb < e1; eb += 32) {
+                        const int e = eb + lane;
+                        bool pass = false;
+                        uint64_t key = 0;
+                        int32_t id = 0;
+                        if (e < e1) {
+                            const int4 en = __ldg(entries + e);
+                            const int64_t dx = (int64_t)en.x - q[0], dy = (int64_t)en.y - q[1],
+                                          dz = (int64_t)en.z - q[2];
+                            key = (uint64_t)(dx * dx) + (uint64_t)(dy * dy) + (uint64_t)(dz * dz);
+                            id = en.w;
+                            pass = kv_less(key, id, wk, wi);
+                        }
+                        const unsigned pm = __ballot_sync(0xffffffffu, pass);
+                        if (pass) {
+                            const int j = qn + __popc(pm & ((1u << lane) - 1u));
+                            qk[j] = key;
+                            qi[j] = id;
+                        }
+                        qn += __popc(pm);
+                        __syncwarp();
+                        if (qn >= 32) knn_merge(qk, qi, qn, bk, bi, lane);
+                    }
+                }
+            }
+        while (qn > 0) knn_merge(qk, qi, qn, bk, bi, lane);
+        // stop once no site outside ring r can enter the best K
+        const uint64_t kth = __shfl_sync(0xffffffffu, bk, K - 1);
+        const int64_t bound = r * (int64_t)G.cs + off_min;
+        const bool full_grid = (c[0] - r <= 0) && (c[0] + r >= G.dims[0] - 1) && (c[1] - r <= 0) &&
+                               (c[1] + r >= G.dims[1] - 1) && (c[2] - r <= 0) && (c[2] + r >= G.dims[2] - 1);
+        if (full_grid) break;
+        if (kth != UINT64_MAX && kth < (uint64_t)bound * (uint64_t)bound) break;
+    }
+    if (lane < K) out_idx[m * K + lane] = bi;
+}
+
 cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,
                              char* ws, cudaStream_t s)
 {
@@ -949,13 +1098,10 @@ cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, in
         sites_fill_kernel<<<nb, 256, 0, s>>>(sites, N, grid, cstart, ccnt, ent);
     }
     if (M > 0) {
-        const unsigned nb = (unsigned)((M + 127) / 128);
-        // the blend weights are not needed here; the points stand in for normals
-        if (K <= 4) knn_kernel<4><<<nb, 128, 0, s>>>(pts, pts, M, K, 0, grid, cstart, ent, sites, idx, w, nullptr, nullptr);
-        else if (K <= 8) knn_kernel<8><<<nb, 128, 0, s>>>(pts, pts, M, K, 0, grid, cstart, ent, sites, idx, w, nullptr, nullptr);
-        else if (K <= 16) knn_kernel<16><<<nb, 128, 0, s>>>(pts, pts, M, K, 0, grid, cstart, ent, sites, idx, w, nullptr, nullptr);
-        else knn_kernel<32><<<nb, 128, 0, s>>>(pts, pts, M, K, 0, grid, cstart, ent, sites, idx, w, nullptr, nullptr);
+        const unsigned nb = (unsigned)((M + kKnnWarps - 1) / kKnnWarps);
+        knn_sites_warp_kernel<<<nb, kKnnWarps * 32, 0, s>>>(pts, M, K, grid, cstart, ent, idx);
     }
+    (void)w;
     return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ Every array is float32 (int32 for indices) and C-contiguous.
 """
 from __future__ import annotations
 
+import copy
 import functools
 
 import numpy as np
@@ -300,6 +301,9 @@ def make_tiny(seed=0):
 
 def make_object(seed=1):
     rng, ells, g, ppos, pnrm, _, diag = _object(seed)
+    # the cached scene's generator state is copied, so that every call draws
+    # the same view, materials and environment
+    rng = copy.deepcopy(rng)
     cam = _unit_vectors(rng, 1)[0] * 3.0
     x, n, wo, _ = _view(rng, ells, cam, 800, 800, OBJECT_FOV)
     mat = materials(rng, len(x))
