@@ -156,6 +156,16 @@ sop_status sop_atlas_pack(const float* maps_rgb, const float* maps_occ, const fl
  * Asynchronous. */
 sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream);
 
+/* Measurement utility (not part of the paper's method): reads the device
+ * buffer buf [bytes] `reps` times with 16-byte loads from every SM, so that
+ * the caller can time the read rate with events on `stream`: a buffer that
+ * fits in L2 gives the L2-to-SM rate that bounds the query's footprint
+ * gathers, a larger one the HBM rate. buf must be 16-byte aligned and bytes
+ * a positive multiple of 16; sink is one device float that is written only
+ * for one improbable checksum (it keeps the loads from being optimised
+ * away). Nothing else is written. Asynchronous. */
+sop_status sop_read_bandwidth_probe(const void* buf, size_t bytes, int32_t reps, float* sink, void* stream);
+
 /* Workspace bytes for sop_bake / sop_bake_bin / sop_bake_trace on n
  * Gaussians (the size does not depend on P or R; they are only checked). */
 size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R);

@@ -51,6 +51,26 @@ QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He,
 
 __device__ __forceinline__ int32_t quantise(float v) { return __float2int_rn(v * 1048576.0f); }
 
+// Cubic cell edge (quantised units) for a box of extents ext[3]: the smallest
+// edge whose grid, (ext/cs + 1) cells per axis, has at most `cap` cells. A
+// flat site set (probes on a ground plane) then gets fine cells in its
+// plane instead of the cbrt-per-axis split of a volume, which would put
+// cbrt(P) sites in every cell of its one layer.
+__device__ __forceinline__ int64_t grid_cell_edge(const int64_t ext[3], int64_t cap)
+{
+    int64_t emax = 0;
+    for (int a = 0; a < 3; ++a) emax = ext[a] > emax ? ext[a] : emax;
+    int64_t lo = 1, hi = emax + 1;  // hi: one cell per axis
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        int64_t n = 1;
+        for (int a = 0; a < 3 && n <= cap; ++a) n *= ext[a] / mid + 1;
+        if (n <= cap) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------
 // Probe grid (single CTA; P is small: thousands to ~1e5 probes).
 // ---------------------------------------------------------------------------
@@ -80,12 +100,9 @@ __global__ void __launch_bounds__(1024) probe_grid_kernel(const float* __restric
     __syncthreads();
     __shared__ ProbeGrid G;
     if (tid == 0) {
-        int64_t ext[3], emax = 0;
-        for (int a = 0; a < 3; ++a) {
-            ext[a] = (int64_t)s_max[a] - s_min[a];
-            emax = ext[a] > emax ? ext[a] : emax;
-        }
-        int64_t cs = emax / g_axis + 1;
+        int64_t ext[3];
+        for (int a = 0; a < 3; ++a) ext[a] = (int64_t)s_max[a] - s_min[a];
+        const int64_t cs = grid_cell_edge(ext, (int64_t)(g_axis + 1) * (g_axis + 1) * (g_axis + 1));
         G.cs = (int32_t)cs;
         int32_t nc = 1;
         for (int a = 0; a < 3; ++a) {
@@ -822,12 +839,9 @@ __global__ void sites_setup_kernel(int32_t* mm, int32_t g_axis, ProbeGrid* grid)
 {
     if (threadIdx.x == 0) {
         ProbeGrid G;
-        int64_t ext[3], emax = 0;
-        for (int a = 0; a < 3; ++a) {
-            ext[a] = (int64_t)mm[3 + a] - mm[a];
-            emax = ext[a] > emax ? ext[a] : emax;
-        }
-        const int64_t cs = emax / g_axis + 1;
+        int64_t ext[3];
+        for (int a = 0; a < 3; ++a) ext[a] = (int64_t)mm[3 + a] - mm[a];
+        const int64_t cs = grid_cell_edge(ext, (int64_t)(g_axis + 1) * (g_axis + 1) * (g_axis + 1));
         G.cs = (int32_t)cs;
         int32_t nc = 1;
         for (int a = 0; a < 3; ++a) {
@@ -1019,43 +1033,72 @@ __global__ void __launch_bounds__(kKnnWarps * 32) knn_sites_warp_kernel(const fl
         r0 = d > r0 ? d : r0;
     }
     for (int64_t r = r0;; ++r) {
-        const int64_t zlo = max(c[2] - r, (int64_t)0), zhi = min(c[2] + r, (int64_t)G.dims[2] - 1);
-        const int64_t ylo = max(c[1] - r, (int64_t)0), yhi = min(c[1] + r, (int64_t)G.dims[1] - 1);
-        for (int64_t z = zlo; z <= zhi; ++z)
-            for (int64_t y = ylo; y <= yhi; ++y) {
-                const bool face = (z == c[2] - r) || (z == c[2] + r) || (y == c[1] - r) || (y == c[1] + r);
-                const int64_t xs = face ? 1 : 2 * r;
-                for (int64_t xx = c[0] - r; xx <= c[0] + r; xx += (xs > 0 ? xs : 1)) {
-                    if (xx < 0 || xx >= G.dims[0]) continue;
-                    const int cell = (int)((z * G.dims[1] + y) * G.dims[0] + xx);
-                    const int e0 = __ldg(cell_start + cell), e1 = __ldg(cell_start + cell + 1);
-                    const uint64_t wk = __shfl_sync(0xffffffffu, bk, 31);
-                    const int32_t wi = __shfl_sync(0xffffffffu, bi, 31);
-                    for (int eb = e0; eb < e1; eb += 32) {
-                        const int e = eb + lane;
-                        bool pass = false;
-                        uint64_t key = 0;
-                        int32_t id = 0;
-                        if (e < e1) {
-                            const int4 en = __ldg(entries + e);
-                            const int64_t dx = (int64_t)en.x - q[0], dy = (int64_t)en.y - q[1],
-                                          dz = (int64_t)en.z - q[2];
-                            key = (uint64_t)(dx * dx) + (uint64_t)(dy * dy) + (uint64_t)(dz * dz);
-                            id = en.w;
-                            pass = kv_less(key, id, wk, wi);
-                        }
-                        const unsigned pm = __ballot_sync(0xffffffffu, pass);
-                        if (pass) {
-                            const int j = qn + __popc(pm & ((1u << lane) - 1u));
-                            qk[j] = key;
-                            qi[j] = id;
-                        }
-                        qn += __popc(pm);
-                        __syncwarp();
-                        if (qn >= 32) knn_merge(qk, qi, qn, bk, bi, lane);
-                    }
+        // the shell of ring r: grid cells at Chebyshev distance r from c,
+        // found in the cube of side 2r+1 clipped to the grid, one per lane;
+        // their entries are then taken 32 at a time across the lanes (prefix
+        // sum of the lanes' counts)
+        int64_t lo3[3], n3[3];
+        for (int a = 0; a < 3; ++a) {
+            lo3[a] = max(c[a] - r, (int64_t)0);
+            n3[a] = min(c[a] + r, (int64_t)G.dims[a] - 1) - lo3[a] + 1;
+            n3[a] = n3[a] > 0 ? n3[a] : 0;
+        }
+        const int64_t nbox = n3[0] * n3[1] * n3[2];
+        for (int64_t t0 = 0; t0 < nbox; t0 += 32) {
+            const int64_t t = t0 + lane;
+            int e0 = 0, cnt = 0;
+            if (t < nbox) {
+                const int64_t cx = lo3[0] + t % n3[0], cy = lo3[1] + (t / n3[0]) % n3[1], cz = lo3[2] + t / (n3[0] * n3[1]);
+                const int64_t dx = cx - c[0], dy = cy - c[1], dz = cz - c[2];
+                const int64_t adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy, adz = dz < 0 ? -dz : dz;
+                const bool shell = (adx > ady ? (adx > adz ? adx : adz) : (ady > adz ? ady : adz)) == r;
+                if (shell) {
+                    const int cell = (int)((cz * G.dims[1] + cy) * G.dims[0] + cx);
+                    e0 = __ldg(cell_start + cell);
+                    cnt = __ldg(cell_start + cell + 1) - e0;
                 }
             }
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int excl = incl - cnt;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const uint64_t wk = __shfl_sync(0xffffffffu, bk, 31);
+            const int32_t wi = __shfl_sync(0xffffffffu, bi, 31);
+            for (int f0 = 0; f0 < total; f0 += 32) {
+                const int f = f0 + lane;
+                // owner: the last lane whose first flattened entry is <= f
+                int own = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int ex = __shfl_sync(0xffffffffu, excl, own + st);
+                    if (ex <= f) own += st;
+                }
+                const int e = __shfl_sync(0xffffffffu, e0, own) + f - __shfl_sync(0xffffffffu, excl, own);
+                bool pass = false;
+                uint64_t key = 0;
+                int32_t id = 0;
+                if (f < total) {
+                    const int4 en = __ldg(entries + e);
+                    const int64_t ddx = (int64_t)en.x - q[0], ddy = (int64_t)en.y - q[1], ddz = (int64_t)en.z - q[2];
+                    key = (uint64_t)(ddx * ddx) + (uint64_t)(ddy * ddy) + (uint64_t)(ddz * ddz);
+                    id = en.w;
+                    pass = kv_less(key, id, wk, wi);
+                }
+                const unsigned pm = __ballot_sync(0xffffffffu, pass);
+                if (pass) {
+                    const int j = qn + __popc(pm & ((1u << lane) - 1u));
+                    qk[j] = key;
+                    qi[j] = id;
+                }
+                qn += __popc(pm);
+                __syncwarp();
+                if (qn >= 32) knn_merge(qk, qi, qn, bk, bi, lane);
+            }
+        }
         while (qn > 0) knn_merge(qk, qi, qn, bk, bi, lane);
         // stop once no site outside ring r can enter the best K
         const uint64_t kth = __shfl_sync(0xffffffffu, bk, K - 1);
@@ -1066,6 +1109,35 @@ __global__ void __launch_bounds__(kKnnWarps * 32) knn_sites_warp_kernel(const fl
         if (kth != UINT64_MAX && kth < (uint64_t)bound * (uint64_t)bound) break;
     }
     if (lane < K) out_idx[m * K + lane] = bi;
+}
+
+// ---------------------------------------------------------------------------
+// Read-bandwidth probe: every thread streams 16-byte loads over the buffer,
+// `reps` times, on all SMs. A buffer that fits in L2 gives the L2-to-SM read
+// rate that bounds the query's footprint gathers; a larger one the HBM rate.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) read_probe_kernel(const uint4* __restrict__ buf, int64_t n16, int32_t reps,
+                                                          float* __restrict__ sink)
+{
+    uint32_t acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+            const uint4 v = __ldcg(buf + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    // a store the compiler cannot drop, taken only for one improbable value
+    if (acc == 0x9e3779b9u) sink[0] = (float)acc;
+}
+
+cudaError_t launch_read_probe(const void* buf, size_t bytes, int32_t reps, float* sink, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    read_probe_kernel<<<(unsigned)(sms > 0 ? sms : 152) * 4, 512, 0, s>>>(reinterpret_cast<const uint4*>(buf),
+                                                                             (int64_t)(bytes / 16), reps, sink);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,

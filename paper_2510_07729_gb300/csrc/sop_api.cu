@@ -114,6 +114,16 @@ sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream)
     return cuda_status(sop::launch_hammersley(S, out_dirs, (cudaStream_t)stream), "sop_hammersley");
 }
 
+sop_status sop_read_bandwidth_probe(const void* buf, size_t bytes, int32_t reps, float* sink, void* stream)
+{
+    if (!buf || !sink) return fail(SOP_ERR_INVALID_ARG, "buf or sink is NULL");
+    if (bytes < 16 || bytes % 16 != 0 || ((uintptr_t)buf & 15u) != 0)
+        return fail(SOP_ERR_INVALID_ARG, "buf must be 16-byte aligned and bytes a positive multiple of 16");
+    if (reps < 1) return fail(SOP_ERR_INVALID_ARG, "reps = %d < 1", reps);
+    return cuda_status(sop::launch_read_probe(buf, bytes, reps, sink, (cudaStream_t)stream),
+                       "sop_read_bandwidth_probe");
+}
+
 size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R)
 {
     if (n_gauss < 0 || P < 1 || R < 2) return 0;

@@ -48,6 +48,7 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
 cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_adjoint(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_hammersley(int32_t S, float* out3, cudaStream_t s);
+cudaError_t launch_read_probe(const void* buf, size_t bytes, int32_t reps, float* sink, cudaStream_t s);
 
 // K nearest sites of M points (surrogate features)
 size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K);

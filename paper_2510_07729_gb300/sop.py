@@ -69,6 +69,7 @@ def load(build_if_missing: bool = True):
     lib.sop_atlas_bytes.argtypes = [i32, i32, i32, i32, C.POINTER(sz), C.POINTER(sz)]
     lib.sop_atlas_pack.argtypes = [vp, vp, vp, C.POINTER(AtlasDesc), vp]
     lib.sop_hammersley.argtypes = [i32, vp, vp]
+    lib.sop_read_bandwidth_probe.argtypes = [vp, sz, i32, vp, vp]
     lib.sop_bake_workspace_bytes.argtypes = [i64, i32, i32]
     lib.sop_bake_workspace_bytes.restype = sz
     lib.sop_bake.argtypes = [C.POINTER(Gaussians), C.POINTER(AtlasDesc), C.POINTER(BakeParams), vp, sz, vp]
@@ -101,7 +102,7 @@ def load(build_if_missing: bool = True):
         getattr(lib, name).restype = C.c_int
     for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_bake_bin", "sop_bake_trace",
                  "sop_bake_stats", "sop_query_shade",
-                 "sop_query_shade_backward", "sop_query_shade_noalloc"):
+                 "sop_query_shade_backward", "sop_query_shade_noalloc", "sop_read_bandwidth_probe"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -216,6 +217,25 @@ def hammersley(S, device="cuda"):
     out = torch.empty((S, 3), dtype=torch.float32, device=device)
     _check(load().sop_hammersley(S, _ptr(out), _stream()))
     return out
+
+
+def read_bandwidth_gbs(nbytes, reps, device="cuda", trials=5):
+    """Read rate (GB/s) of sop_read_bandwidth_probe over a buffer of nbytes
+    read `reps` times (best of `trials`, CUDA events on the current stream,
+    after one untimed pass that also makes a small buffer L2-resident)."""
+    buf = torch.ones(nbytes // 4, dtype=torch.float32, device=device)
+    sink = torch.zeros(1, dtype=torch.float32, device=device)
+    lib = load()
+    _check(lib.sop_read_bandwidth_probe(_ptr(buf), buf.numel() * 4, 1, _ptr(sink), _stream()))
+    best = float("inf")
+    for _ in range(trials):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _check(lib.sop_read_bandwidth_probe(_ptr(buf), buf.numel() * 4, reps, _ptr(sink), _stream()))
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return buf.numel() * 4 * reps / (best * 1e-3) / 1e9
 
 
 def _gauss(g):
