@@ -161,6 +161,44 @@ __global__ void __launch_bounds__(1024) probe_grid_kernel(const float* __restric
 // floor division for possibly negative numerators (positive divisor)
 __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// The search visits rings of cells (Chebyshev radius r in cell indices)
+// around cc, the point's cell clamped into the grid. This is a lower bound on
+// the squared quantised distance from the point q to every cell outside the
+// cube of radius r: an unsearched cell lies in a slab beyond the cube along
+// some axis b (below cc_b - r or above cc_b + r), at least d_b away along b,
+// and, being inside the grid, at least out_a away along every other axis a
+// (out_a: the point's distance outside the grid's extent on axis a; 0 for a
+// point within it). The bound is the smallest d_b^2 + sum_{a != b} out_a^2
+// over the slabs that hold cells; UINT64_MAX once the cube covers the grid.
+// A site whose key is below it has been seen; sums that overflow 64 bits
+// exceed every key and saturate.
+__device__ __forceinline__ uint64_t unsearched_bound2(const ProbeGrid& G, const int32_t q[3], const int64_t cc[3],
+                                                      int64_t r)
+{
+    uint64_t out2[3], osum = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int64_t lo = G.qmin[a], hi = lo + (int64_t)G.dims[a] * G.cs;
+        const int64_t o = q[a] < lo ? lo - q[a] : (q[a] >= hi ? q[a] - hi + 1 : 0);
+        out2[a] = (uint64_t)(o * o);
+        osum += out2[a];
+    }
+    uint64_t best = UINT64_MAX;
+    for (int b = 0; b < 3; ++b) {
+        const uint64_t rest = osum - out2[b];
+        // d^2 + rest, unless it exceeds 64 bits (then it bounds nothing)
+        auto take = [&](uint64_t d) {
+            if (__umul64hi(d, d) != 0) return;
+            const uint64_t v = d * d + rest;
+            if (v >= rest && v < best) best = v;
+        };
+        // cells of index <= cc_b - r - 1 end at qmin + (cc_b - r) cs
+        if (cc[b] - r > 0) take((uint64_t)((int64_t)q[b] - (G.qmin[b] + (cc[b] - r) * G.cs)));
+        // cells of index >= cc_b + r + 1 start at qmin + (cc_b + r + 1) cs
+        if (cc[b] + r < G.dims[b] - 1) take((uint64_t)((G.qmin[b] + (cc[b] + r + 1) * G.cs) - (int64_t)q[b]));
+    }
+    return best;
+}
+
 // ---------------------------------------------------------------------------
 // Exact K nearest probes + blend weights. One thread per point.
 // ---------------------------------------------------------------------------
@@ -178,13 +216,11 @@ __global__ void __launch_bounds__(128) knn_kernel(const float* __restrict__ x, c
     const ProbeGrid G = *gridp;
     const float3 xp = load3(x, m);
     const int32_t q[3] = {quantise(xp.x), quantise(xp.y), quantise(xp.z)};
-    int64_t c[3], off_min = INT64_MAX;
+    // rings are taken around the point's cell clamped into the grid
+    int64_t c[3];
     for (int a = 0; a < 3; ++a) {
-        int64_t rel = (int64_t)q[a] - G.qmin[a];
-        c[a] = floordiv(rel, G.cs);
-        int64_t off = rel - c[a] * G.cs;  // in [0, cs)
-        int64_t m2 = off < G.cs - off ? off : G.cs - off;
-        off_min = m2 < off_min ? m2 : off_min;
+        const int64_t ca = floordiv((int64_t)q[a] - G.qmin[a], G.cs);
+        c[a] = ca < 0 ? 0 : (ca > G.dims[a] - 1 ? G.dims[a] - 1 : ca);
     }
     uint64_t bk[KMAX];
     int32_t bi[KMAX];
@@ -193,12 +229,7 @@ __global__ void __launch_bounds__(128) knn_kernel(const float* __restrict__ x, c
         bk[k] = UINT64_MAX;
         bi[k] = INT32_MAX;
     }
-    int64_t r0 = 0;
-    for (int a = 0; a < 3; ++a) {
-        int64_t d = c[a] < 0 ? -c[a] : (c[a] >= G.dims[a] ? c[a] - (G.dims[a] - 1) : 0);
-        r0 = d > r0 ? d : r0;
-    }
-    for (int64_t r = r0;; ++r) {
+    for (int64_t r = 0;; ++r) {
         const int64_t zlo = max(c[2] - r, (int64_t)0), zhi = min(c[2] + r, (int64_t)G.dims[2] - 1);
         const int64_t ylo = max(c[1] - r, (int64_t)0), yhi = min(c[1] + r, (int64_t)G.dims[1] - 1);
         for (int64_t z = zlo; z <= zhi; ++z)
@@ -238,11 +269,8 @@ __global__ void __launch_bounds__(128) knn_kernel(const float* __restrict__ x, c
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
             if (k == K - 1) kth = bk[k];
-        const int64_t bound = r * (int64_t)G.cs + off_min;
-        const bool full_grid = (c[0] - r <= 0) && (c[0] + r >= G.dims[0] - 1) && (c[1] - r <= 0) &&
-                               (c[1] + r >= G.dims[1] - 1) && (c[2] - r <= 0) && (c[2] + r >= G.dims[2] - 1);
-        if (full_grid) break;
-        if (kth != UINT64_MAX && kth < (uint64_t)bound * (uint64_t)bound) break;
+        const uint64_t bnd = unsearched_bound2(G, q, c, r);
+        if (bnd == UINT64_MAX || kth < bnd) break;
     }
     // weights (Eq. 4-6)
     const float3 nr = load3(nrm, m);
@@ -835,13 +863,13 @@ __global__ void sites_bbox_kernel(const float* __restrict__ pos, int32_t N, int3
     }
 }
 
-__global__ void sites_setup_kernel(int32_t* mm, int32_t g_axis, ProbeGrid* grid)
+__global__ void sites_setup_kernel(int32_t* mm, int64_t cap, ProbeGrid* grid)
 {
     if (threadIdx.x == 0) {
         ProbeGrid G;
         int64_t ext[3];
         for (int a = 0; a < 3; ++a) ext[a] = (int64_t)mm[3 + a] - mm[a];
-        const int64_t cs = grid_cell_edge(ext, (int64_t)(g_axis + 1) * (g_axis + 1) * (g_axis + 1));
+        const int64_t cs = grid_cell_edge(ext, cap);
         G.cs = (int32_t)cs;
         int32_t nc = 1;
         for (int a = 0; a < 3; ++a) {
@@ -1016,43 +1044,47 @@ __global__ void __launch_bounds__(kKnnWarps * 32) knn_sites_warp_kernel(const fl
     const ProbeGrid G = *gridp;
     const float3 xp = load3(x, m);
     const int32_t q[3] = {quantise(xp.x), quantise(xp.y), quantise(xp.z)};
-    int64_t c[3], off_min = INT64_MAX;
+    int64_t c[3];
     for (int a = 0; a < 3; ++a) {
-        const int64_t rel = (int64_t)q[a] - G.qmin[a];
-        c[a] = floordiv(rel, G.cs);
-        const int64_t off = rel - c[a] * G.cs;
-        const int64_t m2 = off < G.cs - off ? off : G.cs - off;
-        off_min = m2 < off_min ? m2 : off_min;
+        const int64_t ca = floordiv((int64_t)q[a] - G.qmin[a], G.cs);
+        c[a] = ca < 0 ? 0 : (ca > G.dims[a] - 1 ? G.dims[a] - 1 : ca);
     }
     uint64_t bk = UINT64_MAX;  // lane l: the (l+1)-th best so far
     int32_t bi = INT32_MAX;
     int qn = 0;
-    int64_t r0 = 0;
-    for (int a = 0; a < 3; ++a) {
-        const int64_t d = c[a] < 0 ? -c[a] : (c[a] >= G.dims[a] ? c[a] - (G.dims[a] - 1) : 0);
-        r0 = d > r0 ? d : r0;
-    }
-    for (int64_t r = r0;; ++r) {
-        // the shell of ring r: grid cells at Chebyshev distance r from c,
-        // found in the cube of side 2r+1 clipped to the grid, one per lane;
-        // their entries are then taken 32 at a time across the lanes (prefix
-        // sum of the lanes' counts)
-        int64_t lo3[3], n3[3];
-        for (int a = 0; a < 3; ++a) {
-            lo3[a] = max(c[a] - r, (int64_t)0);
-            n3[a] = min(c[a] + r, (int64_t)G.dims[a] - 1) - lo3[a] + 1;
-            n3[a] = n3[a] > 0 ? n3[a] : 0;
-        }
-        const int64_t nbox = n3[0] * n3[1] * n3[2];
-        for (int64_t t0 = 0; t0 < nbox; t0 += 32) {
+    for (int64_t r = 0;; ++r) {
+        // the shell of ring r (the 24 r^2 + 2 cells at Chebyshev distance r
+        // from c: two z faces, two y faces without their z rows, two x faces
+        // without either), one cell per lane, clipped to the grid; the
+        // lanes' entries are then taken 32 at a time across the lanes
+        // (prefix sum of the lanes' counts)
+        const int64_t w = 2 * r + 1, wn = 2 * r - 1;
+        const int64_t nz = 2 * w * w, ny = 2 * w * wn, nshell = r == 0 ? 1 : nz + ny + 2 * wn * wn;
+        for (int64_t t0 = 0; t0 < nshell; t0 += 32) {
             const int64_t t = t0 + lane;
             int e0 = 0, cnt = 0;
-            if (t < nbox) {
-                const int64_t cx = lo3[0] + t % n3[0], cy = lo3[1] + (t / n3[0]) % n3[1], cz = lo3[2] + t / (n3[0] * n3[1]);
-                const int64_t dx = cx - c[0], dy = cy - c[1], dz = cz - c[2];
-                const int64_t adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy, adz = dz < 0 ? -dz : dz;
-                const bool shell = (adx > ady ? (adx > adz ? adx : adz) : (ady > adz ? ady : adz)) == r;
-                if (shell) {
+            if (t < nshell) {
+                int64_t dx = 0, dy = 0, dz = 0;
+                if (r > 0) {
+                    if (t < nz) {
+                        const int64_t u = t % (w * w);
+                        dx = u % w - r;
+                        dy = u / w - r;
+                        dz = t < w * w ? -r : r;
+                    } else if (t < nz + ny) {
+                        const int64_t t1 = t - nz, u = t1 % (w * wn);
+                        dx = u % w - r;
+                        dz = u / w - r + 1;
+                        dy = t1 < w * wn ? -r : r;
+                    } else {
+                        const int64_t t2 = t - nz - ny, u = t2 % (wn * wn);
+                        dy = u % wn - r + 1;
+                        dz = u / wn - r + 1;
+                        dx = t2 < wn * wn ? -r : r;
+                    }
+                }
+                const int64_t cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
+                if (cx >= 0 && cx < G.dims[0] && cy >= 0 && cy < G.dims[1] && cz >= 0 && cz < G.dims[2]) {
                     const int cell = (int)((cz * G.dims[1] + cy) * G.dims[0] + cx);
                     e0 = __ldg(cell_start + cell);
                     cnt = __ldg(cell_start + cell + 1) - e0;
@@ -1102,11 +1134,8 @@ __global__ void __launch_bounds__(kKnnWarps * 32) knn_sites_warp_kernel(const fl
         while (qn > 0) knn_merge(qk, qi, qn, bk, bi, lane);
         // stop once no site outside ring r can enter the best K
         const uint64_t kth = __shfl_sync(0xffffffffu, bk, K - 1);
-        const int64_t bound = r * (int64_t)G.cs + off_min;
-        const bool full_grid = (c[0] - r <= 0) && (c[0] + r >= G.dims[0] - 1) && (c[1] - r <= 0) &&
-                               (c[1] + r >= G.dims[1] - 1) && (c[2] - r <= 0) && (c[2] + r >= G.dims[2] - 1);
-        if (full_grid) break;
-        if (kth != UINT64_MAX && kth < (uint64_t)bound * (uint64_t)bound) break;
+        const uint64_t bnd = unsearched_bound2(G, q, c, r);
+        if (bnd == UINT64_MAX || kth < bnd) break;
     }
     if (lane < K) out_idx[m * K + lane] = bi;
 }
@@ -1164,7 +1193,10 @@ cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, in
         const unsigned nb = (unsigned)((N + 255) / 256);
         sites_zero_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(ccnt, cells, mm);
         sites_bbox_kernel<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(sites, N, mm);
-        sites_setup_kernel<<<1, 32, 0, s>>>(mm, g, grid);
+        // about 4 sites per grid cell: the warp search pays per ring (a
+        // round of dependent loads) far more than per candidate (32 lanes)
+        const int64_t cap = N / 4 > 4096 ? N / 4 : 4096;
+        sites_setup_kernel<<<1, 32, 0, s>>>(mm, cap < cells ? cap : cells, grid);
         sites_count_kernel<<<nb, 256, 0, s>>>(sites, N, grid, ccnt);
         sites_scan_kernel<<<1, 1024, 0, s>>>(grid, ccnt, cstart);
         sites_fill_kernel<<<nb, 256, 0, s>>>(sites, N, grid, cstart, ccnt, ent);
