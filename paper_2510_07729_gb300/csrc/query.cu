@@ -98,31 +98,46 @@ __global__ void __launch_bounds__(1024) probe_grid_kernel(const float* __restric
         atomicMax(&s_max[a], lmax[a]);
     }
     __syncthreads();
+    // cell edge: the finest grid within (g+1)^3 cells, coarsened (cap
+    // halved, at most 4 times) while there are fewer than 3 probes per
+    // occupied cell. A volume-like set keeps the fine grid; a flat one (the
+    // shadow probes on the ground), whose far query points need the K
+    // nearest from a wide strip, gets cells of a few probes each.
     __shared__ ProbeGrid G;
-    if (tid == 0) {
-        int64_t ext[3];
-        for (int a = 0; a < 3; ++a) ext[a] = (int64_t)s_max[a] - s_min[a];
-        const int64_t cs = grid_cell_edge(ext, (int64_t)(g_axis + 1) * (g_axis + 1) * (g_axis + 1));
-        G.cs = (int32_t)cs;
-        int32_t nc = 1;
-        for (int a = 0; a < 3; ++a) {
-            G.qmin[a] = s_min[a];
-            G.dims[a] = (int32_t)(ext[a] / cs) + 1;
-            nc *= G.dims[a];
+    __shared__ int64_t s_cap;
+    __shared__ int32_t s_occ;
+    if (tid == 0) s_cap = (int64_t)(g_axis + 1) * (g_axis + 1) * (g_axis + 1);
+    for (int it = 0;; ++it) {
+        if (tid == 0) {
+            int64_t ext[3];
+            for (int a = 0; a < 3; ++a) ext[a] = (int64_t)s_max[a] - s_min[a];
+            const int64_t cs = grid_cell_edge(ext, s_cap);
+            G.cs = (int32_t)cs;
+            int32_t nc = 1;
+            for (int a = 0; a < 3; ++a) {
+                G.qmin[a] = s_min[a];
+                G.dims[a] = (int32_t)(ext[a] / cs) + 1;
+                nc *= G.dims[a];
+            }
+            G.ncells = nc;
+            s_occ = 0;
         }
-        G.ncells = nc;
-        *grid = G;
+        __syncthreads();
+        for (int c = tid; c < G.ncells; c += nt) cell_cnt[c] = 0;
+        __syncthreads();
+        for (int p = tid; p < P; p += nt) {
+            int c[3];
+            for (int a = 0; a < 3; ++a) c[a] = (int)(((int64_t)quantise(probe_pos[3 * p + a]) - G.qmin[a]) / G.cs);
+            if (atomicAdd(&cell_cnt[(c[2] * G.dims[1] + c[1]) * G.dims[0] + c[0]], 1) == 0) atomicAdd(&s_occ, 1);
+        }
+        __syncthreads();
+        const bool again = it < 4 && (int64_t)P < 3 * (int64_t)s_occ && s_cap > 8;
+        __syncthreads();
+        if (!again) break;
+        if (tid == 0) s_cap >>= 1;
     }
-    __syncthreads();
+    if (tid == 0) *grid = G;
     const int nc = G.ncells;
-    for (int c = tid; c < nc; c += nt) cell_cnt[c] = 0;
-    __syncthreads();
-    for (int p = tid; p < P; p += nt) {
-        int c[3];
-        for (int a = 0; a < 3; ++a) c[a] = (int)(((int64_t)quantise(probe_pos[3 * p + a]) - G.qmin[a]) / G.cs);
-        atomicAdd(&cell_cnt[(c[2] * G.dims[1] + c[1]) * G.dims[0] + c[0]], 1);
-    }
-    __syncthreads();
     // exclusive scan of cell counts: contiguous chunk per thread + block scan
     const int chunk = (nc + nt - 1) / nt;
     const int c0 = tid * chunk, c1 = min(nc, c0 + chunk);
