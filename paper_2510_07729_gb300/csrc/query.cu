@@ -187,8 +187,7 @@ __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) { return a >= 
 // over the slabs that hold cells; UINT64_MAX once the cube covers the grid.
 // A site whose key is below it has been seen; sums that overflow 64 bits
 // exceed every key and saturate.
-__device__ __forceinline__ uint64_t unsearched_bound2(const ProbeGrid& G, const int32_t q[3], const int64_t cc[3],
-                                                      int64_t r)
+__device__ __forceinline__ uint64_t unsearched_bound2(const ProbeGrid& G, const int32_t q[3], const int cc[3], int r)
 {
     uint64_t out2[3], osum = 0;
     for (int a = 0; a < 3; ++a) {
@@ -207,9 +206,9 @@ __device__ __forceinline__ uint64_t unsearched_bound2(const ProbeGrid& G, const 
             if (v >= rest && v < best) best = v;
         };
         // cells of index <= cc_b - r - 1 end at qmin + (cc_b - r) cs
-        if (cc[b] - r > 0) take((uint64_t)((int64_t)q[b] - (G.qmin[b] + (cc[b] - r) * G.cs)));
+        if (cc[b] - r > 0) take((uint64_t)((int64_t)q[b] - (G.qmin[b] + (int64_t)(cc[b] - r) * G.cs)));
         // cells of index >= cc_b + r + 1 start at qmin + (cc_b + r + 1) cs
-        if (cc[b] + r < G.dims[b] - 1) take((uint64_t)((G.qmin[b] + (cc[b] + r + 1) * G.cs) - (int64_t)q[b]));
+        if (cc[b] + r < G.dims[b] - 1) take((uint64_t)((G.qmin[b] + (int64_t)(cc[b] + r + 1) * G.cs) - (int64_t)q[b]));
     }
     return best;
 }
@@ -218,7 +217,7 @@ __device__ __forceinline__ uint64_t unsearched_bound2(const ProbeGrid& G, const 
 // Exact K nearest probes + blend weights. One thread per point.
 // ---------------------------------------------------------------------------
 template <int KMAX>
-__global__ void __launch_bounds__(128) knn_kernel(const float* __restrict__ x, const float* __restrict__ nrm, int64_t M,
+__global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float* __restrict__ x, const float* __restrict__ nrm, int64_t M,
                                                    int32_t K, uint64_t snap_key, const ProbeGrid* __restrict__ gridp,
                                                    const int32_t* __restrict__ cell_start,
                                                    const int4* __restrict__ entries,
@@ -232,10 +231,10 @@ __global__ void __launch_bounds__(128) knn_kernel(const float* __restrict__ x, c
     const float3 xp = load3(x, m);
     const int32_t q[3] = {quantise(xp.x), quantise(xp.y), quantise(xp.z)};
     // rings are taken around the point's cell clamped into the grid
-    int64_t c[3];
+    int c[3];
     for (int a = 0; a < 3; ++a) {
         const int64_t ca = floordiv((int64_t)q[a] - G.qmin[a], G.cs);
-        c[a] = ca < 0 ? 0 : (ca > G.dims[a] - 1 ? G.dims[a] - 1 : ca);
+        c[a] = (int)(ca < 0 ? 0 : (ca > G.dims[a] - 1 ? G.dims[a] - 1 : ca));
     }
     uint64_t bk[KMAX];
     int32_t bi[KMAX];
@@ -244,16 +243,16 @@ __global__ void __launch_bounds__(128) knn_kernel(const float* __restrict__ x, c
         bk[k] = UINT64_MAX;
         bi[k] = INT32_MAX;
     }
-    for (int64_t r = 0;; ++r) {
-        const int64_t zlo = max(c[2] - r, (int64_t)0), zhi = min(c[2] + r, (int64_t)G.dims[2] - 1);
-        const int64_t ylo = max(c[1] - r, (int64_t)0), yhi = min(c[1] + r, (int64_t)G.dims[1] - 1);
-        for (int64_t z = zlo; z <= zhi; ++z)
-            for (int64_t y = ylo; y <= yhi; ++y) {
+    for (int r = 0;; ++r) {
+        const int zlo = max(c[2] - r, 0), zhi = min(c[2] + r, G.dims[2] - 1);
+        const int ylo = max(c[1] - r, 0), yhi = min(c[1] + r, G.dims[1] - 1);
+        for (int z = zlo; z <= zhi; ++z)
+            for (int y = ylo; y <= yhi; ++y) {
                 const bool face = (z == c[2] - r) || (z == c[2] + r) || (y == c[1] - r) || (y == c[1] + r);
-                const int64_t xs = face ? 1 : 2 * r;  // on a face row: every x; else only the two ends
-                for (int64_t xx = c[0] - r; xx <= c[0] + r; xx += (xs > 0 ? xs : 1)) {
+                const int xs = face ? 1 : 2 * r;  // on a face row: every x; else only the two ends
+                for (int xx = c[0] - r; xx <= c[0] + r; xx += (xs > 0 ? xs : 1)) {
                     if (xx < 0 || xx >= G.dims[0]) continue;
-                    const int cell = (int)((z * G.dims[1] + y) * G.dims[0] + xx);
+                    const int cell = (z * G.dims[1] + y) * G.dims[0] + xx;
                     const int e1 = __ldg(cell_start + cell + 1);
                     for (int e = __ldg(cell_start + cell); e < e1; ++e) {
                         const int4 en = __ldg(entries + e);
@@ -1059,15 +1058,15 @@ __global__ void __launch_bounds__(kKnnWarps * 32) knn_sites_warp_kernel(const fl
     const ProbeGrid G = *gridp;
     const float3 xp = load3(x, m);
     const int32_t q[3] = {quantise(xp.x), quantise(xp.y), quantise(xp.z)};
-    int64_t c[3];
+    int c[3];
     for (int a = 0; a < 3; ++a) {
         const int64_t ca = floordiv((int64_t)q[a] - G.qmin[a], G.cs);
-        c[a] = ca < 0 ? 0 : (ca > G.dims[a] - 1 ? G.dims[a] - 1 : ca);
+        c[a] = (int)(ca < 0 ? 0 : (ca > G.dims[a] - 1 ? G.dims[a] - 1 : ca));
     }
     uint64_t bk = UINT64_MAX;  // lane l: the (l+1)-th best so far
     int32_t bi = INT32_MAX;
     int qn = 0;
-    for (int64_t r = 0;; ++r) {
+    for (int r = 0;; ++r) {
         // the shell of ring r (the 24 r^2 + 2 cells at Chebyshev distance r
         // from c: two z faces, two y faces without their z rows, two x faces
         // without either), one cell per lane, clipped to the grid; the
