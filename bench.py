@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="object", choices=["object", "compose", "tiny"])
-    ap.add_argument("--part", default="step", choices=["step", "bake", "query"],
-                    help="profiling aid: run only one half (the JSON line then covers that half)")
+    ap.add_argument("--part", default="step", choices=["step", "bake", "query", "compose"],
+                    help="profiling aid: run only one half (the JSON line then covers that half), or only the "
+                         "1080p composition-frame query")
     ap.add_argument("--probes", type=int, default=0, help="profiling aid: bake only the first N probes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -198,7 +199,7 @@ def chosen_variant(sop, g, ppos, R, pargs, env, K, S, mode, out_ref, flush, step
             "query_point_dirs_per_s": round(M * S / (ms * 1e-3), 1), "rel_l1_vs_fp32_atlas": rel}
 
 
-def surrogate_variant(sop, dev, flush, steps, n_scenes=6, train_steps=4000):
+def surrogate_variant(sop, dev, flush, steps, n_scenes=25, train_steps=20000):
     """The learned rebake after the object's first ellipsoid moves: train on
     bakes of random scenes (untimed), then time the rebake of the moved
     scene's 4,096 probes (features, inference, 1% spot-check against the
@@ -409,6 +410,8 @@ def main():
 
     from paper_2510_07729_gb300 import sop
     sop.load()
+    if args.part == "compose":
+        return compose_only(args, dev, sop)
     W = load_workload(args.workload)
     P = len(W["probe_pos"]) if args.probes <= 0 else min(args.probes, len(W["probe_pos"]))
     R, K, S, mode = W["R"], W["K"], W["S"], W["mode"]
@@ -566,6 +569,16 @@ def main():
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def compose_only(args, dev, sop):
+    """--part compose: the composition-frame query alone (profiling aid)."""
+    import torch
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peak_fp32 = N_SMS * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    r = compose_frame_variant(sop, dev, flush, args.steps, l2_read_peak_gbs(dev), measured_peaks()[0], peak_fp32)
+    print(json.dumps({"metric": "composition-frame query point-dirs/s", "value": r["fp32"]["point_dirs_per_s"],
+                      "unit": "point-dirs/s", "steps": args.steps, "higher_is_better": True, "detail": r}))
 
 
 def launches_per_step(do_bake, do_query, P, R):
