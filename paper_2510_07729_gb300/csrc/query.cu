@@ -631,14 +631,20 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
         const float w00 = (1.f - fu) * (1.f - fv), w10 = fu * (1.f - fv), w01 = (1.f - fu) * fv, w11 = fu * fv;
         float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
         if (MODE == SOP_MODE_SHADOW) {
+            // blend each footprint corner over the probes, then weight the
+            // four corners once: O = sum_c w_c sum_k W_k O_k,c
+            float s00 = 0.f, s10 = 0.f, s01 = 0.f, s11 = 0.f;
 #pragma unroll
             for (int k = 0; k < KMAX; ++k) {
                 if (k < a.K) {
                     const float4 q = OQuad<DT>::load(a.quads, (int64_t)(base[k] + off));
-                    const float c00 = W[k] * w00, c10 = W[k] * w10, c01 = W[k] * w01, c11 = W[k] * w11;
-                    pr.w += c00 * q.x + c10 * q.y + c01 * q.z + c11 * q.w;
+                    s00 = fmaf(W[k], q.x, s00);
+                    s10 = fmaf(W[k], q.y, s10);
+                    s01 = fmaf(W[k], q.z, s01);
+                    s11 = fmaf(W[k], q.w, s11);
                 }
             }
+            pr.w = fmaf(w00, s00, fmaf(w10, s10, fmaf(w01, s01, w11 * s11)));
         } else
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
