@@ -51,6 +51,15 @@ QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He,
 
 __device__ __forceinline__ int32_t quantise(float v) { return __float2int_rn(v * 1048576.0f); }
 
+// Exact squared distance of two quantised points. Coordinates are below 2^30
+// in magnitude (positions below 1024), so each difference fits 32 bits and
+// each square is one 32x32 -> 64-bit multiply; the sum stays below 3 * 2^62.
+__device__ __forceinline__ uint64_t qdist2(int32_t ax, int32_t ay, int32_t az, const int32_t q[3])
+{
+    const uint32_t dx = (uint32_t)abs(ax - q[0]), dy = (uint32_t)abs(ay - q[1]), dz = (uint32_t)abs(az - q[2]);
+    return (uint64_t)dx * dx + (uint64_t)dy * dy + (uint64_t)dz * dz;
+}
+
 // Cubic cell edge (quantised units) for a box of extents ext[3]: the smallest
 // edge whose grid, (ext/cs + 1) cells per axis, has at most `cap` cells. A
 // flat site set (probes on a ground plane) then gets fine cells in its
@@ -256,25 +265,23 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
                     const int e1 = __ldg(cell_start + cell + 1);
                     for (int e = __ldg(cell_start + cell); e < e1; ++e) {
                         const int4 en = __ldg(entries + e);
-                        const int64_t dx = (int64_t)en.x - q[0], dy = (int64_t)en.y - q[1], dz = (int64_t)en.z - q[2];
-                        const uint64_t key = (uint64_t)(dx * dx) + (uint64_t)(dy * dy) + (uint64_t)(dz * dz);
+                        const uint64_t key = qdist2(en.x, en.y, en.z, q);
                         const int32_t id = en.w;
                         // keep the KMAX best (key, id) pairs sorted; the first K
                         // of them are the K nearest
                         const bool better = key < bk[KMAX - 1] || (key == bk[KMAX - 1] && id < bi[KMAX - 1]);
                         if (!better) continue;
-                        uint64_t ck = key;
-                        int32_t ci = id;
+                        // insert: every kept pair above the new one moves up a slot
+                        bool lt[KMAX];
 #pragma unroll
-                        for (int k = 0; k < KMAX; ++k) {
-                            const bool sw = (ck < bk[k]) || (ck == bk[k] && ci < bi[k]);
-                            const uint64_t tk = bk[k];
-                            const int32_t ti = bi[k];
-                            bk[k] = sw ? ck : bk[k];
-                            bi[k] = sw ? ci : bi[k];
-                            ck = sw ? tk : ck;
-                            ci = sw ? ti : ci;
+                        for (int k = 0; k < KMAX; ++k) lt[k] = key < bk[k] || (key == bk[k] && id < bi[k]);
+#pragma unroll
+                        for (int k = KMAX - 1; k > 0; --k) {
+                            bk[k] = lt[k - 1] ? bk[k - 1] : (lt[k] ? key : bk[k]);
+                            bi[k] = lt[k - 1] ? bi[k - 1] : (lt[k] ? id : bi[k]);
                         }
+                        bk[0] = lt[0] ? key : bk[0];
+                        bi[0] = lt[0] ? id : bi[0];
                     }
                 }
             }
@@ -1135,8 +1142,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32) knn_sites_warp_kernel(const fl
                 int32_t id = 0;
                 if (f < total) {
                     const int4 en = __ldg(entries + e);
-                    const int64_t ddx = (int64_t)en.x - q[0], ddy = (int64_t)en.y - q[1], ddz = (int64_t)en.z - q[2];
-                    key = (uint64_t)(ddx * ddx) + (uint64_t)(ddy * ddy) + (uint64_t)(ddz * ddz);
+                    key = qdist2(en.x, en.y, en.z, q);
                     id = en.w;
                     pass = kv_less(key, id, wk, wi);
                 }
