@@ -543,6 +543,59 @@ template <> struct OQuad<SOP_BF16> {
     }
 };
 
+// Geometry of one light direction at a point: the world direction (local
+// direction l rotated into the frame (t, b, n)), its octahedral footprint
+// (offset of the base texel in a probe's stored map) and bilinear weights.
+struct DirTerms {
+    float3 w;
+    int off;
+    float w00, w10, w01, w11;
+};
+__device__ __forceinline__ DirTerms dir_terms(const float4 l, const float3 tt, const float3 bb, const float3 n,
+                                              const float Rf, const int R, const int RQ)
+{
+    DirTerms d;
+    d.w = f3(fmaf(l.x, tt.x, fmaf(l.y, bb.x, l.z * n.x)), fmaf(l.x, tt.y, fmaf(l.y, bb.y, l.z * n.y)),
+             fmaf(l.x, tt.z, fmaf(l.y, bb.z, l.z * n.z)));
+    const float2 uv = oct_encode(d.w);
+    const float s = uv.x * Rf - 0.5f, t = uv.y * Rf - 0.5f;
+    const float fi = floorf(s), fj = floorf(t);
+    const float fu = s - fi, fv = t - fj;
+    const int i0 = min(max((int)fi + 1, 0), R), j0 = min(max((int)fj + 1, 0), R);
+    d.off = j0 * RQ + i0;
+    d.w00 = (1.f - fu) * (1.f - fv);
+    d.w10 = fu * (1.f - fv);
+    d.w01 = (1.f - fu) * fv;
+    d.w11 = fu * fv;
+    return d;
+}
+
+// Blended occlusion of one direction over a point's K probes (Eq. 5, applied
+// to O): each footprint corner is blended over the probes, then the four
+// corners are weighted once, O = sum_c w_c sum_k W_k O_k,c.
+template <int DT, int KMAX>
+__device__ __forceinline__ float shadow_blend(const void* quads, const int32_t* base, const float* W, const int K,
+                                              const int off, const float w00, const float w10, const float w01,
+                                              const float w11)
+{
+    float s00 = 0.f, s10 = 0.f, s01 = 0.f, s11 = 0.f;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < K) {
+            const float4 q = OQuad<DT>::load(quads, (int64_t)(base[k] + off));
+            s00 = fmaf(W[k], q.x, s00);
+            s10 = fmaf(W[k], q.y, s10);
+            s01 = fmaf(W[k], q.z, s01);
+            s11 = fmaf(W[k], q.w, s11);
+        }
+    }
+    return fmaf(w00, s00, fmaf(w10, s10, fmaf(w01, s01, w11 * s11)));
+}
+
+// SHADOW-mode warps whose points share a normal keep per-direction terms in
+// shared memory (32 bytes a direction per warp) for S up to this
+constexpr int kShadowTab = 128;
+
 struct ShadeK {
     const float *n, *wo, *albedo, *rough, *metal;
     int64_t M;
@@ -625,33 +678,52 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
     }
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, den0 = 0.f, den1 = 0.f, den2 = 0.f;
     const float Rf = (float)a.R;
+    // SHADOW mode, every point of the warp on the same normal (bit for bit; a
+    // planar receiver such as a ground plane): their light directions, and so
+    // the footprint offsets, bilinear weights and environment terms of every
+    // direction, coincide (Eq. 3 rotates one local set by the normal's frame).
+    // The lanes then compute those once for the warp into shared memory, and
+    // each point only gathers and blends its own probes.
+    bool warp_dirs = false;
+    if (MODE == SOP_MODE_SHADOW && a.S <= kShadowTab) {
+        const unsigned full = 0xffffffffu;
+        const unsigned bx = __float_as_uint(nr.x), by = __float_as_uint(nr.y), bz = __float_as_uint(nr.z);
+        const bool same = bx == __shfl_sync(full, bx, 0) && by == __shfl_sync(full, by, 0) &&
+                          bz == __shfl_sync(full, bz, 0);
+        warp_dirs = __all_sync(full, same);
+    }
+    if (MODE == SOP_MODE_SHADOW && warp_dirs) {
+        float4* tab = s_dirs + a.S + (threadIdx.x >> 5) * 2 * a.S;
+        for (int i = (int)(threadIdx.x & 31); i < a.S; i += 32) {
+            const float4 l = s_dirs[i];
+            const DirTerms d = dir_terms(l, tt, bb, n, Rf, a.R, RQ);
+            const float3 Ld = env_lookup(a.envq, a.He, a.We, d.w);
+            const float NdotL = l.z;
+            tab[i] = make_float4(__int_as_float(d.off), d.w00, d.w10, d.w01);
+            tab[a.S + i] = make_float4(d.w11, Ld.x * NdotL, Ld.y * NdotL, Ld.z * NdotL);
+        }
+        __syncwarp();
+        for (int i = sub; i < a.S; i += LANES) {
+            const float4 ta = tab[i], tb = tab[a.S + i];
+            const float vis =
+                1.f - shadow_blend<DT, KMAX>(a.quads, base, W, a.K, __float_as_int(ta.x), ta.y, ta.z, ta.w, tb.x);
+            acc0 = fmaf(tb.y, vis, acc0);
+            acc1 = fmaf(tb.z, vis, acc1);
+            acc2 = fmaf(tb.w, vis, acc2);
+            den0 += tb.y;
+            den1 += tb.z;
+            den2 += tb.w;
+        }
+    } else
     for (int i = sub; i < a.S; i += LANES) {
         const float4 l = s_dirs[i];
-        const float3 w = f3(fmaf(l.x, tt.x, fmaf(l.y, bb.x, l.z * n.x)), fmaf(l.x, tt.y, fmaf(l.y, bb.y, l.z * n.y)),
-                            fmaf(l.x, tt.z, fmaf(l.y, bb.z, l.z * n.z)));
-        const float2 uv = oct_encode(w);
-        const float s = uv.x * Rf - 0.5f, t = uv.y * Rf - 0.5f;
-        const float fi = floorf(s), fj = floorf(t);
-        const float fu = s - fi, fv = t - fj;
-        const int i0 = min(max((int)fi + 1, 0), a.R), j0 = min(max((int)fj + 1, 0), a.R);
-        const int off = j0 * RQ + i0;
-        const float w00 = (1.f - fu) * (1.f - fv), w10 = fu * (1.f - fv), w01 = (1.f - fu) * fv, w11 = fu * fv;
+        const DirTerms d = dir_terms(l, tt, bb, n, Rf, a.R, RQ);
+        const float3 w = d.w;
+        const int off = d.off;
+        const float w00 = d.w00, w10 = d.w10, w01 = d.w01, w11 = d.w11;
         float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
         if (MODE == SOP_MODE_SHADOW) {
-            // blend each footprint corner over the probes, then weight the
-            // four corners once: O = sum_c w_c sum_k W_k O_k,c
-            float s00 = 0.f, s10 = 0.f, s01 = 0.f, s11 = 0.f;
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k) {
-                if (k < a.K) {
-                    const float4 q = OQuad<DT>::load(a.quads, (int64_t)(base[k] + off));
-                    s00 = fmaf(W[k], q.x, s00);
-                    s10 = fmaf(W[k], q.y, s10);
-                    s01 = fmaf(W[k], q.z, s01);
-                    s11 = fmaf(W[k], q.w, s11);
-                }
-            }
-            pr.w = fmaf(w00, s00, fmaf(w10, s10, fmaf(w01, s01, w11 * s11)));
+            pr.w = shadow_blend<DT, KMAX>(a.quads, base, W, a.K, off, w00, w10, w01, w11);
         } else
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
@@ -686,12 +758,14 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
             acc1 += f1 * (vis * Ld.y + pr.y) * NdotL;
             acc2 += f2 * (vis * Ld.z + pr.z) * NdotL;
         } else {
-            acc0 += Ld.x * vis * NdotL;
-            acc1 += Ld.y * vis * NdotL;
-            acc2 += Ld.z * vis * NdotL;
-            den0 += Ld.x * NdotL;
-            den1 += Ld.y * NdotL;
-            den2 += Ld.z * NdotL;
+            // the same terms, in the same order, as the shared-direction path
+            const float L0 = Ld.x * NdotL, L1 = Ld.y * NdotL, L2 = Ld.z * NdotL;
+            acc0 = fmaf(L0, vis, acc0);
+            acc1 = fmaf(L1, vis, acc1);
+            acc2 = fmaf(L2, vis, acc2);
+            den0 += L0;
+            den1 += L1;
+            den2 += L2;
         }
     }
     for (int o = LANES / 2; o > 0; o >>= 1) {
@@ -788,7 +862,9 @@ static cudaError_t shade_launch(const ShadeK& k, int LANES, cudaStream_t s)
     const int bs = 256;
     const int64_t threads = k.M * LANES;
     const unsigned nb = (unsigned)((threads + bs - 1) / bs);
-    const size_t smem = sizeof(float4) * (size_t)k.S;
+    size_t smem = sizeof(float4) * (size_t)k.S;
+    // per-warp direction tables of the shared-normal SHADOW path (8 warps)
+    if (MODE == SOP_MODE_SHADOW && k.S <= kShadowTab) smem += (size_t)(bs / 32) * 2 * sizeof(float4) * k.S;
     auto fn = shade_kernel<DT, KMAX, MODE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

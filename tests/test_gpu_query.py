@@ -138,6 +138,30 @@ def test_16bit_atlas_exact_maps(sop, orc, tiny, dtype, mode):
     assert_close(out, ro, what=f"dtype {dtype} mode {mode}")
 
 
+@pytest.mark.parametrize("S", [64, 128, 130])
+def test_shadow_shared_normal(sop, orc, tiny, S):
+    """SHADOW mode on a planar receiver: warps whose points share a normal
+    take their per-direction terms from a per-warp table (S <= 128); warps
+    with one point off the plane, and S above the table's limit, take the
+    per-point path. All match the FP64 oracle."""
+    c = tiny
+    rng = np.random.default_rng(40 + S)
+    M = 32 * 40 + 7
+    x = rng.uniform(-1.0, 1.0, (M, 3)).astype(np.float32)
+    x[:, 2] = -1.05
+    n = np.zeros((M, 3), np.float32)
+    n[:, 2] = 1.0
+    n[32 * 3 + 5] = np.array([0.3, 0.1, 0.95], np.float32)  # one warp is mixed
+    pts = dict(x=x, n=n, wo=n.copy(), albedo=c["albedo"][:M], rough=c["rough"][:M], metal=c["metal"][:M])
+    maps = I.synthetic_maps(rng, 64, 8)
+    at = atlas_from_maps(sop, c["probe_pos"], maps)
+    out, idx, _ = run_gpu(sop, c, at, 4, S, mode=1, pts=pts)
+    ro, ri, _ = run_orc(orc, c, maps, c["probe_pos"], 4, S, mode=1, pts=pts)
+    assert np.array_equal(idx, ri)
+    kap = kappa(orc, c, maps, c["probe_pos"], 4, S, mode=1, pts=pts)
+    assert_close(out, ro, what=f"shadow S={S}", absolute=kap)
+
+
 @pytest.mark.parametrize("M", [1, 31, 4096 + 37])
 @pytest.mark.parametrize("K", [1, 3, 8, 32])
 def test_ragged_sizes_and_K(sop, orc, tiny, M, K):
