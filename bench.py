@@ -278,13 +278,14 @@ def l2_read_peak_gbs(dev):
     return sop.read_bandwidth_gbs(64 << 20, 40, device=dev)
 
 
-def query_demand(K, mode, texel_bytes):
-    """Algorithmic bytes of one shaded point-direction that the SMs must
-    receive from L2/L1: the 4 texels of each of K probe footprints (RGBO in
-    SHADE mode, O alone in SHADOW mode) and the 4 environment texels (RGB
-    fp32)."""
+def query_demand(K, mode, texel_bytes, M, S, n_normals):
+    """Algorithmic bytes that the SMs must receive from L2/L1 for M points
+    with n_normals distinct normals: per point-direction the 4 texels of each
+    of K probe footprints (RGBO in SHADE mode, O alone in SHADOW mode); per
+    distinct (normal, direction) the 4 environment texels (RGB fp32), since
+    points on one normal share their light directions."""
     per_texel = texel_bytes if mode == 0 else texel_bytes // 4
-    return K * 4 * per_texel + 4 * 12
+    return K * 4 * per_texel * M * S + 4 * 12 * n_normals * S
 
 
 def compose_frame_variant(sop, dev, flush, steps, l2_gbs, hbm_gbs, peak_fp32):
@@ -308,10 +309,12 @@ def compose_frame_variant(sop, dev, flush, steps, l2_gbs, hbm_gbs, peak_fp32):
     for name, mode in (("shade", 0), ("shadow", 1)):
         d = c[name]
         pts = [cu(d[k]) for k in ("x", "n", "wo", "albedo", "rough", "metal")]
-        parts.append(dict(name=name, mode=mode, pts=pts, pp=cu(d["probe_pos"]), M=len(d["x"])))
+        parts.append(dict(name=name, mode=mode, pts=pts, pp=cu(d["probe_pos"]), M=len(d["x"]),
+                          normals=len(np.unique(d["n"], axis=0))))
     res = {"what": "1920x1080 composition frame: sop_query_shade of the object pixels (SHADE) and of the scene "
                    "pixels (SHADOW), K=8, S=64, 2x4,096 probes at 16x16",
-           "points": {p["name"]: p["M"] for p in parts}}
+           "points": {p["name"]: p["M"] for p in parts},
+           "distinct_normals": {p["name"]: p["normals"] for p in parts}}
     outs = {}
     for dt, label, tb in ((sop.SOP_F32, "fp32", 16), (sop.SOP_F16, "fp16", 8)):
         for p in parts:
@@ -343,8 +346,9 @@ def compose_frame_variant(sop, dev, flush, steps, l2_gbs, hbm_gbs, peak_fp32):
             tp["shadow"].append(ev[1].elapsed_time(ev[2]))
         ms = float(np.mean(ts))
         pd = sum(p["M"] for p in parts) * S
-        fl = sum(flop_per_point_dir(K, p["mode"]) * p["M"] * S for p in parts)
-        dem = sum(query_demand(K, p["mode"], tb) * p["M"] * S for p in parts)
+        fl = sum((flop_per_point_dir(K, p["mode"]) - FLOP_DIR_GEOMETRY) * p["M"] * S +
+                 FLOP_DIR_GEOMETRY * p["normals"] * S for p in parts)
+        dem = sum(query_demand(K, p["mode"], tb, p["M"], S, p["normals"]) for p in parts)
         hbm = sum(68 * p["M"] for p in parts) + sum(p["at"].rgbo.numel() * p["at"].rgbo.element_size()
                                                      for p in parts) + env.numel() * 4
         t_hbm, t_l2, t_alu = hbm / (hbm_gbs * 1e9), dem / (l2_gbs * 1e9), fl / (peak_fp32 * 1e12)
@@ -367,9 +371,15 @@ def compose_frame_variant(sop, dev, flush, steps, l2_gbs, hbm_gbs, peak_fp32):
     return res
 
 
+# the part of flop_per_point_dir that depends only on the normal and the
+# direction: frame rotation, octahedral encode, texel coordinates, environment
+FLOP_DIR_GEOMETRY = 15 + 12 + 10 + 40 + 24 + 8
+
+
 def flop_per_point_dir(K, mode):
-    # SHADOW mode blends the occlusion alone: 4 weight products + 4 FMA per probe
-    f = 15 + 12 + 10 + K * ((32 + 4) if mode == 0 else 12) + 40 + 24 + 8 + 9
+    # SHADOW mode blends the occlusion alone: 4 FMA per probe (one per
+    # footprint corner), then the 4 bilinear weights once (7)
+    f = 15 + 12 + 10 + (K * (32 + 4) if mode == 0 else K * 8 + 7) + 40 + 24 + 8 + 9
     if mode == 0:
         f += 12 + 15 + 8 + 4 + 12 + 12
     return f

@@ -688,8 +688,10 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
     if (MODE == SOP_MODE_SHADOW && a.S <= kShadowTab) {
         const unsigned full = 0xffffffffu;
         const unsigned bx = __float_as_uint(nr.x), by = __float_as_uint(nr.y), bz = __float_as_uint(nr.z);
-        const bool same = bx == __shfl_sync(full, bx, 0) && by == __shfl_sync(full, by, 0) &&
-                          bz == __shfl_sync(full, bz, 0);
+        // every lane takes all three shuffles (no short-circuit: a lane that
+        // skipped one would leave the others waiting at it)
+        const unsigned x0 = __shfl_sync(full, bx, 0), y0 = __shfl_sync(full, by, 0), z0 = __shfl_sync(full, bz, 0);
+        const bool same = (bx == x0) & (by == y0) & (bz == z0);
         warp_dirs = __all_sync(full, same);
     }
     if (MODE == SOP_MODE_SHADOW && warp_dirs) {
@@ -1286,8 +1288,7 @@ cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, in
     o = align256(o + sizeof(int32_t) * (size_t)cells);
     int4* ent = reinterpret_cast<int4*>(ws + o);
     o = align256(o + sizeof(int4) * (size_t)N);
-    float* w = reinterpret_cast<float*>(ws + o);
-    o = align256(o + sizeof(float) * (size_t)M * K);
+    o = align256(o + sizeof(float) * (size_t)M * K);  // (room for weights; the sites search writes none)
     int32_t* mm = reinterpret_cast<int32_t*>(ws + o);
     if (N <= 16384) {
         probe_grid_kernel<<<1, 1024, 0, s>>>(sites, N, g, grid, cstart, ccnt, ent);
@@ -1307,7 +1308,6 @@ cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, in
         const unsigned nb = (unsigned)((M + kKnnWarps - 1) / kKnnWarps);
         knn_sites_warp_kernel<<<nb, kKnnWarps * 32, 0, s>>>(pts, M, K, grid, cstart, ent, idx);
     }
-    (void)w;
     return cudaGetLastError();
 }
 
