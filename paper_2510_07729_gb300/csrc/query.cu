@@ -186,20 +186,17 @@ __global__ void __launch_bounds__(1024) probe_grid_kernel(const float* __restric
 __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // The search visits rings of cells (Chebyshev radius r in cell indices)
-// around a box of cells [lo, hi] holding the point's cell clamped into the
-// grid (one cell for a single point, the cells of a warp's points for the
-// warp search). This is a lower bound on the squared quantised distance from
-// the point q to every cell outside the box grown by r: an unsearched cell
-// lies in a slab beyond it along some axis b (below lo_b - r or above
-// hi_b + r), at least d_b away along b,
+// around cc, the point's cell clamped into the grid. This is a lower bound on
+// the squared quantised distance from the point q to every cell outside the
+// cube of radius r: an unsearched cell lies in a slab beyond the cube along
+// some axis b (below cc_b - r or above cc_b + r), at least d_b away along b,
 // and, being inside the grid, at least out_a away along every other axis a
 // (out_a: the point's distance outside the grid's extent on axis a; 0 for a
 // point within it). The bound is the smallest d_b^2 + sum_{a != b} out_a^2
-// over the slabs that hold cells; UINT64_MAX once the box covers the grid.
+// over the slabs that hold cells; UINT64_MAX once the cube covers the grid.
 // A site whose key is below it has been seen; sums that overflow 64 bits
 // exceed every key and saturate.
-__device__ __forceinline__ uint64_t unsearched_bound2_box(const ProbeGrid& G, const int32_t q[3], const int lo[3],
-                                                          const int hi[3], int r)
+__device__ __forceinline__ uint64_t unsearched_bound2(const ProbeGrid& G, const int32_t q[3], const int cc[3], int r)
 {
     uint64_t out2[3], osum = 0;
     for (int a = 0; a < 3; ++a) {
@@ -217,18 +214,12 @@ __device__ __forceinline__ uint64_t unsearched_bound2_box(const ProbeGrid& G, co
             const uint64_t v = d * d + rest;
             if (v >= rest && v < best) best = v;
         };
-        // cells of index <= lo_b - r - 1 end at qmin + (lo_b - r) cs
-        if (lo[b] - r > 0) take((uint64_t)((int64_t)q[b] - (G.qmin[b] + (int64_t)(lo[b] - r) * G.cs)));
-        // cells of index >= hi_b + r + 1 start at qmin + (hi_b + r + 1) cs
-        if (hi[b] + r < G.dims[b] - 1) take((uint64_t)((G.qmin[b] + (int64_t)(hi[b] + r + 1) * G.cs) - (int64_t)q[b]));
+        // cells of index <= cc_b - r - 1 end at qmin + (cc_b - r) cs
+        if (cc[b] - r > 0) take((uint64_t)((int64_t)q[b] - (G.qmin[b] + (int64_t)(cc[b] - r) * G.cs)));
+        // cells of index >= cc_b + r + 1 start at qmin + (cc_b + r + 1) cs
+        if (cc[b] + r < G.dims[b] - 1) take((uint64_t)((G.qmin[b] + (int64_t)(cc[b] + r + 1) * G.cs) - (int64_t)q[b]));
     }
     return best;
-}
-
-// the same for the cube of radius r around one cell
-__device__ __forceinline__ uint64_t unsearched_bound2(const ProbeGrid& G, const int32_t q[3], const int cc[3], int r)
-{
-    return unsearched_bound2_box(G, q, cc, cc, r);
 }
 
 // ---------------------------------------------------------------------------
@@ -326,153 +317,6 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
     for (int k = 0; k < KMAX; ++k)
         if (k < K) {
             const float wk = snap ? w[k] : w[k] / wsum;
-            ws_idx[m * K + k] = bi[k];
-            ws_w[m * K + k] = wk;
-            if (user_idx) user_idx[m * K + k] = bi[k];
-            if (user_w) user_w[m * K + k] = wk;
-        }
-}
-
-// ---------------------------------------------------------------------------
-// Exact K nearest probes + weights, one warp per 32 consecutive points (pixels
-// of a view, which lie close together and mostly share their nearest probes).
-// The warp searches rings of cells around the box of its points' clamped
-// cells: each ring's cells are taken one per lane, their entries 32 at a time,
-// and every entry is broadcast to all lanes, each of which keeps the best K
-// (key, index) pairs of its own point. The warp stops once every lane's K-th
-// key is below its own bound on the unsearched cells, so each point gets the
-// same K nearest, in the same order, as the one-thread search.
-// ---------------------------------------------------------------------------
-template <int KMAX>
-__global__ void __launch_bounds__(128) knn_warp_kernel(const float* __restrict__ x, const float* __restrict__ nrm,
-                                                        int64_t M, int32_t K, uint64_t snap_key,
-                                                        const ProbeGrid* __restrict__ gridp,
-                                                        const int32_t* __restrict__ cell_start,
-                                                        const int4* __restrict__ entries,
-                                                        const float* __restrict__ probe_pos,
-                                                        int32_t* __restrict__ ws_idx, float* __restrict__ ws_w,
-                                                        int32_t* __restrict__ user_idx, float* __restrict__ user_w)
-{
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);  // first point of the warp
-    if (w0 >= M) return;  // warp-uniform
-    const int64_t m = w0 + lane;
-    const bool active = m < M;
-    const int64_t mm = active ? m : w0;  // idle lanes search for the warp's first point
-    const ProbeGrid G = *gridp;
-    const float3 xp = load3(x, mm);
-    const int32_t q[3] = {quantise(xp.x), quantise(xp.y), quantise(xp.z)};
-    int c[3], lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) {
-        const int64_t ca = floordiv((int64_t)q[a] - G.qmin[a], G.cs);
-        c[a] = (int)(ca < 0 ? 0 : (ca > G.dims[a] - 1 ? G.dims[a] - 1 : ca));
-        lo[a] = __reduce_min_sync(full, c[a]);
-        hi[a] = __reduce_max_sync(full, c[a]);
-    }
-    uint64_t bk[KMAX];
-    int32_t bi[KMAX];
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-        bk[k] = UINT64_MAX;
-        bi[k] = INT32_MAX;
-    }
-    for (int r = 0;; ++r) {
-        // ring r: the box grown by r, clipped to the grid, less the box grown
-        // by r - 1 (visited before)
-        int glo[3], n3[3];
-        for (int a = 0; a < 3; ++a) {
-            glo[a] = max(lo[a] - r, 0);
-            n3[a] = min(hi[a] + r, G.dims[a] - 1) - glo[a] + 1;
-        }
-        const int64_t nbox = (int64_t)n3[0] * n3[1] * n3[2];
-        for (int64_t t0 = 0; t0 < nbox; t0 += 32) {
-            const int64_t t = t0 + lane;
-            int e0 = 0, cnt = 0;
-            if (t < nbox) {
-                const int cx = glo[0] + (int)(t % n3[0]), cy = glo[1] + (int)((t / n3[0]) % n3[1]),
-                          cz = glo[2] + (int)(t / ((int64_t)n3[0] * n3[1]));
-                const bool inner = r > 0 && cx > lo[0] - r && cx < hi[0] + r && cy > lo[1] - r && cy < hi[1] + r &&
-                                   cz > lo[2] - r && cz < hi[2] + r;
-                if (!inner) {
-                    const int cell = (cz * G.dims[1] + cy) * G.dims[0] + cx;
-                    e0 = __ldg(cell_start + cell);
-                    cnt = __ldg(cell_start + cell + 1) - e0;
-                }
-            }
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(full, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int excl = incl - cnt;
-            const int total = __shfl_sync(full, incl, 31);
-            for (int f0 = 0; f0 < total; f0 += 32) {
-                const int f = f0 + lane;
-                int own = 0;
-#pragma unroll
-                for (int st = 16; st > 0; st >>= 1) {
-                    const int ex = __shfl_sync(full, excl, own + st);
-                    if (ex <= f) own += st;
-                }
-                const int e = __shfl_sync(full, e0, own) + f - __shfl_sync(full, excl, own);
-                int4 en = make_int4(0, 0, 0, INT32_MAX);
-                if (f < total) en = __ldg(entries + e);
-                const int nv = min(32, total - f0);
-                for (int j = 0; j < nv; ++j) {
-                    const int32_t ex = __shfl_sync(full, en.x, j), ey = __shfl_sync(full, en.y, j),
-                                  ez = __shfl_sync(full, en.z, j), id = __shfl_sync(full, en.w, j);
-                    const uint64_t key = qdist2(ex, ey, ez, q);
-                    const bool better = key < bk[KMAX - 1] || (key == bk[KMAX - 1] && id < bi[KMAX - 1]);
-                    if (better) {
-                        bool lt[KMAX];
-#pragma unroll
-                        for (int k = 0; k < KMAX; ++k) lt[k] = key < bk[k] || (key == bk[k] && id < bi[k]);
-#pragma unroll
-                        for (int k = KMAX - 1; k > 0; --k) {
-                            bk[k] = lt[k - 1] ? bk[k - 1] : (lt[k] ? key : bk[k]);
-                            bi[k] = lt[k - 1] ? bi[k - 1] : (lt[k] ? id : bi[k]);
-                        }
-                        bk[0] = lt[0] ? key : bk[0];
-                        bi[0] = lt[0] ? id : bi[0];
-                    }
-                }
-            }
-        }
-        // every lane: stop once no probe outside the grown box can enter its best K
-        uint64_t kth = bk[0];
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k == K - 1) kth = bk[k];
-        const uint64_t bnd = unsearched_bound2_box(G, q, lo, hi, r);
-        if (__all_sync(full, bnd == UINT64_MAX || kth < bnd)) break;
-    }
-    if (!active) return;
-    // weights (Eq. 4-6), as in knn_kernel
-    const float3 nr = load3(nrm, m);
-    const float nl = sqrtf(dot3(nr, nr));
-    const float3 nn = f3(nr.x / nl, nr.y / nl, nr.z / nl);
-    float wv[KMAX];
-    float wsum = 0.f;
-    const bool snap = bk[0] <= snap_key;
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-        wv[k] = 0.f;
-        if (k < K) {
-            const float3 pk = load3(probe_pos, bi[k]);
-            const float3 d = pk - xp;
-            const float dl = sqrtf(dot3(d, d));
-            const float ws = 1.f / dl;
-            const float wb = 0.5f * (1.f + dot3(d, nn) / dl) + 0.01f;
-            wv[k] = snap ? (k == 0 ? 1.f : 0.f) : ws * wb;
-            wsum += wv[k];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k)
-        if (k < K) {
-            const float wk = snap ? wv[k] : wv[k] / wsum;
             ws_idx[m * K + k] = bi[k];
             ws_w[m * K + k] = wk;
             if (user_idx) user_idx[m * K + k] = bi[k];
@@ -973,7 +817,7 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
         const int bs = 128;
         const unsigned nb = (unsigned)((a.M + bs - 1) / bs);
 #define SOP_KNN(KM) \
-    knn_warp_kernel<KM><<<nb, bs, 0, s>>>(a.x, a.n, a.M, a.K, a.snap_key, grid, cstart, ent, a.probe_pos, idx, w, a.out_idx, a.out_w)
+    knn_kernel<KM><<<nb, bs, 0, s>>>(a.x, a.n, a.M, a.K, a.snap_key, grid, cstart, ent, a.probe_pos, idx, w, a.out_idx, a.out_w)
         if (a.K <= 4) SOP_KNN(4);
         else if (a.K <= 8) SOP_KNN(8);
         else if (a.K <= 16) SOP_KNN(16);
