@@ -258,6 +258,46 @@ sop_status sop_query_shade_backward(const float* x, const float* n, const float*
                                     float* g_rough, float* g_metal, float* g_normal, float* g_env, float* g_maps,
                                     void* ws, size_t ws_bytes, void* stream);
 
+/* ---- SOP texture optimisation (Sec. 3.1.2, the second reconstruction step:
+ * L = L_pbr + lambda_lam L_lam + lambda_sops L_sops over the environment,
+ * the materials and the SOP textures, with Adam). One step is: pack the maps
+ * (sop_atlas_pack), shade (sop_query_shade), sop_l1_loss_grad, the adjoint
+ * (sop_query_shade_backward) and one sop_adam_l1_step per parameter block.
+ * L_pbr is read as the mean absolute error over the shaded RGB (the render
+ * loss's SSIM term needs an image grid, which the shading points are not). */
+
+/* dL/dC of L = mean |C - C_target| over n floats: grad[i] = sign(C_i -
+ * C_target,i) / n (sign(0) = 0), written to grad [n] (device). If loss_sum is
+ * not NULL, sum |C - C_target| is added to *loss_sum (one device float; the
+ * caller zeroes it; float atomics, so the last bits depend on the order).
+ * Asynchronous. */
+sop_status sop_l1_loss_grad(const float* C, const float* C_target, int64_t n, float* grad, float* loss_sum,
+                            void* stream);
+
+/* Settings of one Adam step on a parameter block. The L1 regulariser
+ * lam * |p - target| (target[i] if `target` is not NULL, else target_value)
+ * adds lam * sign(p - target) to the gradient. Elements i with
+ * i % period < split use lam[0], lo[0], hi[0], the others lam[1], lo[1],
+ * hi[1] (e.g. period 4, split 3 for RGB + O texels); after the Adam update
+ * (Kingma & Ba 2015, bias-corrected, step >= 1) each element is clamped to
+ * [lo, hi]. */
+typedef struct {
+    float lr, beta1, beta2, eps;
+    int32_t step;
+    const float* target;
+    float target_value;
+    int32_t period, split;
+    float lam[2], lo[2], hi[2];
+} sop_adam_params;
+
+/* One Adam step in place on p [n], with moments m [n], v [n] (caller-owned,
+ * zero before the first step) and the gradient g [n] (NULL = zero, e.g. a
+ * block that only the regulariser drives). All device pointers. Rejects
+ * period < 1, split outside [0, period], step < 1, lr <= 0 or beta outside
+ * [0, 1). Asynchronous. */
+sop_status sop_adam_l1_step(float* p, const float* g, float* m, float* v, int64_t n, const sop_adam_params* params,
+                            void* stream);
+
 /* ---- Learned bake surrogate ------------------------------------------------
  * A small MLP predicts a probe's maps (O, D/depth_scale, RGB) from its
  * neighbourhood, to rebake probes quickly after an object moves; the

@@ -114,6 +114,30 @@ sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream)
     return cuda_status(sop::launch_hammersley(S, out_dirs, (cudaStream_t)stream), "sop_hammersley");
 }
 
+sop_status sop_l1_loss_grad(const float* C, const float* C_target, int64_t n, float* grad, float* loss_sum,
+                            void* stream)
+{
+    if (n < 0) return fail(SOP_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    if (n > 0 && (!C || !C_target || !grad)) return fail(SOP_ERR_INVALID_ARG, "C, C_target or grad is NULL");
+    return cuda_status(sop::launch_l1_grad(C, C_target, n, grad, loss_sum, (cudaStream_t)stream), "sop_l1_loss_grad");
+}
+
+sop_status sop_adam_l1_step(float* p, const float* g, float* m, float* v, int64_t n, const sop_adam_params* a,
+                            void* stream)
+{
+    if (!a) return fail(SOP_ERR_INVALID_ARG, "params is NULL");
+    if (n < 0) return fail(SOP_ERR_INVALID_ARG, "n = %lld < 0", (long long)n);
+    if (n > 0 && (!p || !m || !v)) return fail(SOP_ERR_INVALID_ARG, "p, m or v is NULL");
+    if (a->period < 1 || a->split < 0 || a->split > a->period)
+        return fail(SOP_ERR_INVALID_ARG, "period = %d, split = %d: need period >= 1 and 0 <= split <= period",
+                    a->period, a->split);
+    if (a->step < 1) return fail(SOP_ERR_INVALID_ARG, "step = %d < 1", a->step);
+    if (!(a->lr > 0.f) || !(a->beta1 >= 0.f && a->beta1 < 1.f) || !(a->beta2 >= 0.f && a->beta2 < 1.f) ||
+        !(a->eps >= 0.f))
+        return fail(SOP_ERR_INVALID_ARG, "lr must be > 0, beta1/beta2 in [0, 1), eps >= 0");
+    return cuda_status(sop::launch_adam_l1(p, g, m, v, n, *a, (cudaStream_t)stream), "sop_adam_l1_step");
+}
+
 sop_status sop_read_bandwidth_probe(const void* buf, size_t bytes, int32_t reps, float* sink, void* stream)
 {
     if (!buf || !sink) return fail(SOP_ERR_INVALID_ARG, "buf or sink is NULL");

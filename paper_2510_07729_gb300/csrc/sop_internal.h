@@ -50,6 +50,11 @@ cudaError_t launch_adjoint(const QueryArgs& a, const QueryLayout& L, char* ws, c
 cudaError_t launch_hammersley(int32_t S, float* out3, cudaStream_t s);
 cudaError_t launch_read_probe(const void* buf, size_t bytes, int32_t reps, float* sink, cudaStream_t s);
 
+// SOP texture optimisation pieces (optimize.cu)
+cudaError_t launch_l1_grad(const float* C, const float* Ct, int64_t n, float* grad, float* loss_sum, cudaStream_t s);
+cudaError_t launch_adam_l1(float* p, const float* g, float* m, float* v, int64_t n, const sop_adam_params& a,
+                           cudaStream_t s);
+
 // K nearest sites of M points (surrogate features)
 size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K);
 cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,
