@@ -149,6 +149,12 @@ sop_status sop_atlas_bytes(int32_t P, int32_t R, int32_t rgbo_dtype, int32_t dep
 sop_status sop_atlas_pack(const float* maps_rgb, const float* maps_occ, const float* maps_depth,
                           const sop_atlas* atlas, void* stream);
 
+/* sop_atlas_pack for interleaved maps: maps_rgbo [P,R,R,4] = (L_in RGB, O)
+ * per texel (the layout of the adjoint's probe-map gradient and of the
+ * texture optimisation's parameters); the depth plane is left untouched.
+ * Asynchronous. */
+sop_status sop_atlas_pack_rgbo(const float* maps_rgbo, const sop_atlas* atlas, void* stream);
+
 /* The canonical S light directions in the local frame (z along the normal),
  * written to out_dirs [S,3] (device): a Hammersley set with centred first
  * coordinate, z_i = (i + 1/2)/S, phi_i = 2 pi radical_inverse_base2(i),

@@ -107,6 +107,15 @@ sop_status sop_atlas_pack(const float* maps_rgb, const float* maps_occ, const fl
                        "sop_atlas_pack");
 }
 
+sop_status sop_atlas_pack_rgbo(const float* maps_rgbo, const sop_atlas* atlas, void* stream)
+{
+    sop_status st = check_atlas(atlas, false);
+    if (st != SOP_OK) return st;
+    if (!maps_rgbo) return fail(SOP_ERR_INVALID_ARG, "maps_rgbo is NULL");
+    return cuda_status(sop::launch_atlas_pack(maps_rgbo, 4, maps_rgbo + 3, 4, nullptr, *atlas, (cudaStream_t)stream),
+                       "sop_atlas_pack_rgbo");
+}
+
 sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream)
 {
     if (S < 1 || S > 4096) return fail(SOP_ERR_INVALID_ARG, "S = %d outside [1, 4096]", S);

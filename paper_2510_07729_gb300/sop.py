@@ -41,6 +41,12 @@ class BakeParams(C.Structure):
     _fields_ = [("t_near", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float)]
 
 
+class AdamParams(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int32), ("target", C.c_void_p), ("target_value", C.c_float), ("period", C.c_int32),
+                ("split", C.c_int32), ("lam", C.c_float * 2), ("lo", C.c_float * 2), ("hi", C.c_float * 2)]
+
+
 class ShadeParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("S", C.c_int32), ("mode", C.c_int32), ("specular", C.c_float),
                 ("eps_snap", C.c_float)]
@@ -70,6 +76,9 @@ def load(build_if_missing: bool = True):
     lib.sop_atlas_pack.argtypes = [vp, vp, vp, C.POINTER(AtlasDesc), vp]
     lib.sop_hammersley.argtypes = [i32, vp, vp]
     lib.sop_read_bandwidth_probe.argtypes = [vp, sz, i32, vp, vp]
+    lib.sop_atlas_pack_rgbo.argtypes = [vp, C.POINTER(AtlasDesc), vp]
+    lib.sop_l1_loss_grad.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.sop_adam_l1_step.argtypes = [vp, vp, vp, vp, i64, C.POINTER(AdamParams), vp]
     lib.sop_bake_workspace_bytes.argtypes = [i64, i32, i32]
     lib.sop_bake_workspace_bytes.restype = sz
     lib.sop_bake.argtypes = [C.POINTER(Gaussians), C.POINTER(AtlasDesc), C.POINTER(BakeParams), vp, sz, vp]
@@ -102,7 +111,8 @@ def load(build_if_missing: bool = True):
         getattr(lib, name).restype = C.c_int
     for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_bake_bin", "sop_bake_trace",
                  "sop_bake_stats", "sop_query_shade",
-                 "sop_query_shade_backward", "sop_query_shade_noalloc", "sop_read_bandwidth_probe"):
+                 "sop_query_shade_backward", "sop_query_shade_noalloc", "sop_read_bandwidth_probe",
+                 "sop_atlas_pack_rgbo", "sop_l1_loss_grad", "sop_adam_l1_step"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -210,6 +220,14 @@ def atlas_pack(maps_rgb, maps_occ, maps_depth, atlas: Atlas):
     d = atlas.c()
     _check(load().sop_atlas_pack(_f32(maps_rgb, (P, R, R, 3)), _f32(maps_occ, (P, R, R)),
                                  None if maps_depth is None else _f32(maps_depth, (P, R, R)), C.byref(d), _stream()))
+    return atlas
+
+
+def atlas_pack_rgbo(maps, atlas: Atlas):
+    """Pack interleaved maps [P,R,R,4] (L_in RGB, O) into the atlas."""
+    P, R = atlas.P, atlas.R
+    d = atlas.c()
+    _check(load().sop_atlas_pack_rgbo(_f32(maps, (P, R, R, 4)), C.byref(d), _stream()))
     return atlas
 
 
@@ -405,8 +423,7 @@ class SopQueryShade(torch.autograd.Function):
     def forward(ctx, x, n, wo, albedo, rough, metal, maps, env, probe_pos, K, S):
         P, R = maps.shape[0], maps.shape[1]
         at = make_atlas(probe_pos, R, with_depth=False)
-        m = maps.contiguous()
-        atlas_pack(m[..., :3].contiguous(), m[..., 3].contiguous(), None, at)
+        atlas_pack_rgbo(maps.contiguous(), at)
         out = query_shade(x, n, wo, albedo, rough, metal, at, env, K, S)
         ctx.save_for_backward(x, n, wo, albedo, rough, metal, env)
         ctx.at, ctx.K, ctx.S = at, K, S
@@ -561,3 +578,83 @@ def surrogate_rebake(surr: Surrogate, gauss, out: Atlas, spot_frac=0.01, tau=0.0
         return err, True
     atlas_copy(spot, out, None, sel_t, n_spot)
     return err, False
+
+
+def l1_loss_grad(C_, C_target, grad=None, loss_sum=None):
+    """sop_l1_loss_grad: grad = sign(C - C_target) / n; adds sum |C - C_target|
+    to loss_sum (one float, zeroed by the caller) when given."""
+    n = C_.numel()
+    grad = grad if grad is not None else torch.empty_like(C_)
+    _check(load().sop_l1_loss_grad(_f32(C_), _f32(C_target, tuple(C_.shape)), n, _ptr(grad),
+                                   None if loss_sum is None else _ptr(loss_sum), _stream()))
+    return grad
+
+
+def adam_l1_step(p, g, m, v, step, lr, target=None, target_value=0.0, lam=(0.0, 0.0), lo=(-3.0e38, -3.0e38),
+                 hi=(3.0e38, 3.0e38), period=1, split=1, beta1=0.9, beta2=0.999, eps=1e-8):
+    """sop_adam_l1_step on one parameter block, in place."""
+    a = AdamParams(lr, beta1, beta2, eps, step, None if target is None else _ptr(target), target_value, period, split,
+                   (C.c_float * 2)(*lam), (C.c_float * 2)(*lo), (C.c_float * 2)(*hi))
+    _check(load().sop_adam_l1_step(_ptr(p), None if g is None else _ptr(g), _ptr(m), _ptr(v), p.numel(), C.byref(a),
+                                   _stream()))
+    return p
+
+
+class TextureOptimizer:
+    """The second reconstruction step of Sec. 3.1.2: Adam on the environment
+    map, the per-point albedo, roughness and metallic (lr 0.01) and the SOP
+    textures {L_in, O} (lr 0.001) against L = L_pbr + lam_lam L_lam +
+    lam_sops L_sops, with L_pbr the mean absolute error of the shaded RGB,
+    L_lam = L1(R, 1) + L1(M, 0) and L_sops = L1(L_in, L_tr) + L1(O, O_tr)
+    against the ray-traced maps. Parameters are clamped after each step
+    (albedo, metallic, O to [0, 1]; roughness to [0.1, 1]; environment and
+    L_in to [0, inf)). Every step runs in the library's kernels: pack, shade,
+    loss gradient, adjoint, one fused regularise + Adam + clamp per block."""
+
+    def __init__(self, albedo, rough, metal, env, maps, traced_maps, probe_pos, lr_mat=0.01, lr_sop=0.001,
+                 lam_lam=0.001, lam_sops=1.0):
+        self.p = {k: t.detach().float().contiguous().clone() for k, t in
+                  dict(albedo=albedo, rough=rough, metal=metal, env=env, maps=maps).items()}
+        self.m = {k: torch.zeros_like(t) for k, t in self.p.items()}
+        self.v = {k: torch.zeros_like(t) for k, t in self.p.items()}
+        self.traced = traced_maps.float().contiguous()
+        self.lr_mat, self.lr_sop, self.lam_lam, self.lam_sops = lr_mat, lr_sop, lam_lam, lam_sops
+        P, R = maps.shape[0], maps.shape[1]
+        self.atlas = make_atlas(probe_pos, R, with_depth=False)
+        self.g_env = torch.zeros_like(self.p["env"])
+        self.g_maps = torch.zeros_like(self.p["maps"])
+        self.loss_sum = torch.zeros(1, dtype=torch.float32, device=maps.device)
+        self.t = 0
+        self.ws = None
+
+    def step(self, x, n, wo, target, K, S):
+        """One step; returns the L_pbr of the shading before the update (a
+        device scalar)."""
+        p = self.p
+        M = x.shape[0]
+        atlas_pack_rgbo(p["maps"], self.atlas)
+        He, We = p["env"].shape[0], p["env"].shape[1]
+        if self.ws is None:
+            self.ws = _ws(query_workspace_bytes(self.atlas, M, K, S, He, We), x.device)
+        C_ = query_shade(x, n, wo, p["albedo"], p["rough"], p["metal"], self.atlas, p["env"], K, S, workspace=self.ws)
+        self.loss_sum.zero_()
+        gC = l1_loss_grad(C_, target, loss_sum=self.loss_sum)
+        self.g_env.zero_()
+        self.g_maps.zero_()
+        g = query_shade_backward(x, n, wo, p["albedo"], p["rough"], p["metal"], self.atlas, p["env"], K, S, gC,
+                                 g_env=self.g_env, g_maps=self.g_maps, workspace=self.ws)
+        self.t += 1
+        t, lm, ls = self.t, self.lr_mat, self.lr_sop
+        inf = 3.0e38
+        adam_l1_step(p["albedo"], g["albedo"], self.m["albedo"], self.v["albedo"], t, lm, lo=(0.0, 0.0), hi=(1.0, 1.0))
+        lam = self.lam_lam / M
+        adam_l1_step(p["rough"], g["rough"], self.m["rough"], self.v["rough"], t, lm, target_value=1.0, lam=(lam, lam),
+                     lo=(0.1, 0.1), hi=(1.0, 1.0))
+        adam_l1_step(p["metal"], g["metal"], self.m["metal"], self.v["metal"], t, lm, target_value=0.0, lam=(lam, lam),
+                     lo=(0.0, 0.0), hi=(1.0, 1.0))
+        adam_l1_step(p["env"], self.g_env, self.m["env"], self.v["env"], t, lm, lo=(0.0, 0.0), hi=(inf, inf))
+        texels = p["maps"].shape[0] * p["maps"].shape[1] * p["maps"].shape[2]
+        adam_l1_step(p["maps"], self.g_maps, self.m["maps"], self.v["maps"], t, ls, target=self.traced,
+                     lam=(self.lam_sops / (3 * texels), self.lam_sops / texels), lo=(0.0, 0.0), hi=(inf, 1.0),
+                     period=4, split=3)
+        return self.loss_sum / (3 * M)
