@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="object", choices=["object", "compose", "tiny"])
-    ap.add_argument("--part", default="step", choices=["step", "bake", "query", "compose"],
+    ap.add_argument("--part", default="step", choices=["step", "bake", "query", "compose", "optimize"],
                     help="profiling aid: run only one half (the JSON line then covers that half), or only the "
                          "1080p composition-frame query")
     ap.add_argument("--probes", type=int, default=0, help="profiling aid: bake only the first N probes")
@@ -423,6 +423,13 @@ def main():
     sop.load()
     if args.part == "compose":
         return compose_only(args, dev, sop)
+    if args.part == "optimize":
+        import torch
+        r = optimize_variant(sop, load_workload("object"), dev,
+                             torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev), args.steps)
+        print(json.dumps({"metric": "texture-optimisation step point-dirs/s", "value": r["point_dirs_per_s"],
+                          "unit": "point-dirs/s", "steps": args.steps, "higher_is_better": True, "detail": r}))
+        return
     W = load_workload(args.workload)
     P = len(W["probe_pos"]) if args.probes <= 0 else min(args.probes, len(W["probe_pos"]))
     R, K, S, mode = W["R"], W["K"], W["S"], W["mode"]
