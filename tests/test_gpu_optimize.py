@@ -58,14 +58,20 @@ def test_adam_kernel_matches_oracle(sop, opt, t):
     gt = g.astype(np.float64) + lam_e * np.sign(p.astype(np.float64) - tgt)
     lo_e, hi_e = np.where(rgb, lo[0], lo[1]), np.where(rgb, np.inf, 1.0)
     po, mo, vo = opt.adam(p.astype(np.float64), gt, m.astype(np.float64), v.astype(np.float64), t, 1e-3, lo_e, hi_e)
-    # float32 rounding of each product and sum (a few units of 2^-24 of the
-    # terms' magnitudes; the moments cancel when m and g differ in sign)
+    # the kernel's moments and bias corrections use the float32 betas it is
+    # given; with those constants, each product and sum rounds to within a
+    # few units of 2^-24 of the terms (the moments cancel when m and g
+    # differ in sign)
     u = 2.0 ** -24
+    b1, b2 = float(np.float32(0.9)), float(np.float32(0.999))
+    c1, c2 = float(np.float32(1.0 - b1)), float(np.float32(1.0 - b2))
+    me = b1 * m.astype(np.float64) + c1 * gt
+    ve = b2 * v.astype(np.float64) + c2 * gt * gt
     m_gpu, v_gpu = Mm.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)
-    assert np.all(np.abs(m_gpu - mo) <= 4 * u * (0.9 * np.abs(m) + 0.1 * (np.abs(g) + lam_e)))
-    assert np.all(np.abs(v_gpu - vo) <= 6 * u * (0.999 * v + 0.001 * gt * gt))
+    assert np.all(np.abs(m_gpu - me) <= 4 * u * (b1 * np.abs(m) + c1 * (np.abs(g) + lam_e)))
+    assert np.all(np.abs(v_gpu - ve) <= 6 * u * (b2 * v + c2 * gt * gt))
     # the update from the kernel's own moments: a few ulp of p and of the step
-    bc1, bc2 = 1 - 0.9 ** t, 1 - 0.999 ** t
+    bc1, bc2 = float(np.float32(1 - b1 ** t)), float(np.float32(1 - b2 ** t))
     step = 1e-3 * (m_gpu / bc1) / (np.sqrt(v_gpu / bc2) + 1e-8)
     pe = np.clip(p.astype(np.float64) - step, lo_e, hi_e)
     assert np.all(np.abs(P.cpu().numpy() - pe) <= 4 * u * (np.abs(p) + np.abs(step)))
