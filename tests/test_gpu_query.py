@@ -138,8 +138,8 @@ def test_16bit_atlas_exact_maps(sop, orc, tiny, dtype, mode):
     assert_close(out, ro, what=f"dtype {dtype} mode {mode}")
 
 
-@pytest.mark.parametrize("S", [64, 128, 130])
-def test_shadow_shared_normal(sop, orc, tiny, S):
+@pytest.mark.parametrize("S,dtype", [(64, 0), (128, 0), (130, 0), (64, 2), (128, 1)])
+def test_shadow_shared_normal(sop, orc, tiny, S, dtype):
     """SHADOW mode on a planar receiver: warps whose points share a normal
     take their per-direction terms from a per-warp table (S <= 128); warps
     with one point off the plane, and S above the table's limit, take the
@@ -154,12 +154,15 @@ def test_shadow_shared_normal(sop, orc, tiny, S):
     n[32 * 3 + 5] = np.array([0.3, 0.1, 0.95], np.float32)  # one warp is mixed
     pts = dict(x=x, n=n, wo=n.copy(), albedo=c["albedo"][:M], rough=c["rough"][:M], metal=c["metal"][:M])
     maps = I.synthetic_maps(rng, 64, 8)
-    at = atlas_from_maps(sop, c["probe_pos"], maps)
+    if dtype:  # maps exact in the atlas format (16-bit atlases: two lanes per point)
+        rnd = round_bf16 if dtype == 1 else (lambda a: a.astype(np.float16).astype(np.float32))
+        maps = {k: rnd(v) for k, v in maps.items()}
+    at = atlas_from_maps(sop, c["probe_pos"], maps, dtype=dtype)
     out, idx, _ = run_gpu(sop, c, at, 4, S, mode=1, pts=pts)
     ro, ri, _ = run_orc(orc, c, maps, c["probe_pos"], 4, S, mode=1, pts=pts)
     assert np.array_equal(idx, ri)
     kap = kappa(orc, c, maps, c["probe_pos"], 4, S, mode=1, pts=pts)
-    assert_close(out, ro, what=f"shadow S={S}", absolute=kap)
+    assert_close(out, ro, what=f"shadow S={S} dtype={dtype}", absolute=kap)
 
 
 @pytest.mark.parametrize("M", [1, 31, 4096 + 37])
