@@ -646,7 +646,7 @@ __device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const
 }
 
 // default of TraceK::composite_at
-constexpr int kCompositeAt = 16;
+constexpr int kCompositeAt = 48;
 
 // One warp per texel ray. Lanes share the grid walk (uniform control flow)
 // and split each cell's entries. Every Gaussian is evaluated once per ray:
@@ -770,60 +770,63 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
                 ne0 = __ldg(k.cell_start + cn);
                 ne1 = __ldg(k.cell_start + cn + 1);
             }
-            const float tl = t_enter;
-            // mode 0: the cell cannot overflow the hit buffer; scan it, and
-            //   composite once enough hits have gathered (or at the end).
-            // mode 1: it could; first composite what lies before it, then go
-            //   on in mode 0 if the cell now fits, else in
-            // mode 2: take its window in parts [sl, sh), halving a part whose
-            //   hits overflow the buffer.
-            int mode = nw + pend + (e1 - e0) <= kHitCap ? 0 : 1;
-            int from = mode == 0 ? e0 : e1, least = mode == 0 ? 32 : 1;
-            float sl = tl, sh = t_exit;
-            int splits = 0;
-            for (;;) {
-                const bool sfin = last && !(sh < t_exit);
-                const float lo = mode == 2 ? sl : tl;
-                const float hi_e = (mode == 2 ? sfin : last) ? FLT_MAX : (mode == 2 ? sh : t_exit);
-                const int nb = n, pb = pend;
-                // in mode 0 the walk goes on to the next cell: load its first entries
-                scan_eval(k, o, iv, go, sp, t0, from, e1, mode == 0 ? ne0 : 0, mode == 0 ? ne1 : 0, lo, hi_e, least,
-                          pv, pe, que, qn, pend, key, alp, n, lane, acc, d);
-                if (mode == 0 && least == 32) {
-                    if (!(last || nw + pend >= k.composite_at)) break;
-                    from = e1;  // evaluate what is still queued, then composite
-                    least = 1;
-                    continue;
-                }
-                if (mode == 2 && n > kHitCap) {
-                    n = nb;
-                    pend = pb;
-                    if (++splits > 40 || !(sh > sl)) {
-                        if (lane == 0) atomicOr(k.stats + 3, 1ull);
-                        acc.done = true;
-                        break;
+            // an empty cell with no composite due changes nothing: step on
+            if (!(e0 == e1 && !last && nw + pend < k.composite_at)) {
+                const float tl = t_enter;
+                // mode 0: the cell cannot overflow the hit buffer; scan it, and
+                //   composite once enough hits have gathered (or at the end).
+                // mode 1: it could; first composite what lies before it, then go
+                //   on in mode 0 if the cell now fits, else in
+                // mode 2: take its window in parts [sl, sh), halving a part whose
+                //   hits overflow the buffer.
+                int mode = nw + pend + (e1 - e0) <= kHitCap ? 0 : 1;
+                int from = mode == 0 ? e0 : e1, least = mode == 0 ? 32 : 1;
+                float sl = tl, sh = t_exit;
+                int splits = 0;
+                for (;;) {
+                    const bool sfin = last && !(sh < t_exit);
+                    const float lo = mode == 2 ? sl : tl;
+                    const float hi_e = (mode == 2 ? sfin : last) ? FLT_MAX : (mode == 2 ? sh : t_exit);
+                    const int nb = n, pb = pend;
+                    // in mode 0 the walk goes on to the next cell: load its first entries
+                    scan_eval(k, o, iv, go, sp, t0, from, e1, mode == 0 ? ne0 : 0, mode == 0 ? ne1 : 0, lo, hi_e, least,
+                              pv, pe, que, qn, pend, key, alp, n, lane, acc, d);
+                    if (mode == 0 && least == 32) {
+                        if (!(last || nw + pend >= k.composite_at)) break;
+                        from = e1;  // evaluate what is still queued, then composite
+                        least = 1;
+                        continue;
                     }
-                    sh = sl + 0.5f * (sh - sl);
-                    continue;
+                    if (mode == 2 && n > kHitCap) {
+                        n = nb;
+                        pend = pb;
+                        if (++splits > 40 || !(sh > sl)) {
+                            if (lane == 0) atomicOr(k.stats + 3, 1ull);
+                            acc.done = true;
+                            break;
+                        }
+                        sh = sl + 0.5f * (sh - sl);
+                        continue;
+                    }
+                    composite_hits(k, key, alp, dkey, dalp, n, mode == 0 ? last : (mode == 2 && sfin),
+                                   mode == 0 ? t_exit : (mode == 1 ? tl : sh), lane, acc);
+                    nw = n;
+                    pend = 0;
+                    if (acc.done || mode == 0) break;
+                    if (mode == 2) {
+                        if (!(sh < t_exit)) break;
+                        sl = sh;
+                        sh = t_exit;
+                        splits = 0;
+                    } else {
+                        // the waiting hits are now those beyond tl: the cell may fit
+                        mode = n + (e1 - e0) <= kHitCap ? 0 : 2;
+                        least = mode == 0 ? 32 : 1;
+                    }
+                    from = e0;
                 }
-                composite_hits(k, key, alp, dkey, dalp, n, mode == 0 ? last : (mode == 2 && sfin),
-                               mode == 0 ? t_exit : (mode == 1 ? tl : sh), lane, acc);
-                nw = n;
-                pend = 0;
-                if (acc.done || mode == 0) break;
-                if (mode == 2) {
-                    if (!(sh < t_exit)) break;
-                    sl = sh;
-                    sh = t_exit;
-                    splits = 0;
-                } else {
-                    // the waiting hits are now those beyond tl: the cell may fit
-                    mode = n + (e1 - e0) <= kHitCap ? 0 : 2;
-                    least = mode == 0 ? 32 : 1;
-                }
-                from = e0;
+                if (acc.done || last) break;
             }
-            if (acc.done || last) break;
             e0 = ne0;
             e1 = ne1;
             // step one cell; the boundary is recomputed from the cell index
