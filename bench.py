@@ -653,8 +653,8 @@ def launches_per_step(do_bake, do_query, P, R):
         # texel dirs, trace, atlas pack, depth pack
         n += 10
     if do_query:
-        # probe grid, knn, env pack, dirs, shade
-        n += 5
+        # probe grid, knn, env pack, env footprints, atlas footprints, dirs, shade
+        n += 7
     return n
 
 
