@@ -19,6 +19,7 @@ SRC = os.path.join(HERE, "sop_oracle.c")
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 MODE_SHADE, MODE_SHADOW = 0, 1
+ENV_EQUIRECT, ENV_OCTAHEDRAL = 0, 1
 FLAG_ALPHA_MIN, FLAG_ORDER, FLAG_TNEAR, FLAG_TSTOP = 1, 2, 4, 8
 
 _lib = None
@@ -194,7 +195,7 @@ def weights(x, n, probe_pos, idx, key, snap_key=None):
 
 
 def query_shade(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S,
-                mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None):
+                mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, env_layout=ENV_EQUIRECT):
     """FP64 query + shade. Returns out [M,3], idx [M,K], W [M,K]."""
     x, n, wo, albedo, rough, metal = (_f32(v) for v in (x, n, wo, albedo, rough, metal))
     pp, mr, mo, env = _f32(probe_pos), _f32(maps_rgb), _f32(maps_occ), _f32(env)
@@ -209,7 +210,8 @@ def query_shade(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, e
     lib().orc_query_shade(C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal),
                           C.c_int32(P), _p(pp), C.c_int32(R), _p(mr), _p(mo), C.c_int32(He), C.c_int32(We),
                           _p(env), C.c_int32(S), None if dp is None else _p(dp), C.c_int32(K),
-                          C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), _p(out), _p(idx), _p(W))
+                          C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_int32(env_layout), _p(out), _p(idx),
+                          _p(W))
     return out, idx, W
 
 
@@ -219,7 +221,8 @@ FP32_DIR_EPS = 2e-6
 
 
 def query_shade_sensitivity(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S,
-                            mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, eps=FP32_DIR_EPS):
+                            mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, eps=FP32_DIR_EPS,
+                            env_layout=ENV_EQUIRECT):
     """Per-output allowance [M,3] for an FP32 evaluation (see the C docs)."""
     x, n, wo, albedo, rough, metal = (_f32(v) for v in (x, n, wo, albedo, rough, metal))
     pp, mr, mo, env = _f32(probe_pos), _f32(maps_rgb), _f32(maps_occ), _f32(env)
@@ -232,8 +235,29 @@ def query_shade_sensitivity(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb,
     lib().orc_query_shade_sensitivity(
         C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal), C.c_int32(P), _p(pp), C.c_int32(R),
         _p(mr), _p(mo), C.c_int32(He), C.c_int32(We), _p(env), C.c_int32(S), None if dp is None else _p(dp),
-        C.c_int32(K), C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_double(eps), _p(kap))
+        C.c_int32(K), C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_int32(env_layout), C.c_double(eps),
+        _p(kap))
     return kap
+
+
+def env_to_octahedral(env, H):
+    """FP64 resampling of an equirectangular environment [He,We,3] into an
+    octahedral one [H,H,3] (texel centre directions, bilinear)."""
+    env = _f32(env)
+    He, We, _ = env.shape
+    out = np.empty((H, H, 3))
+    lib().orc_env_to_oct(_p(env), C.c_int32(He), C.c_int32(We), C.c_int32(H), _p(out))
+    return out
+
+
+def env_oct_lookup(env, w):
+    """FP64 bilinear lookup of an octahedral environment [H,H,3] at unit
+    directions w [n,3] (the probe maps' mapping and border rule)."""
+    env = _f32(env)
+    w = _f64(w).reshape(-1, 3)
+    out = np.empty((len(w), 3))
+    lib().orc_env_oct_lookup_n(C.c_int64(len(w)), _p(env), C.c_int32(env.shape[0]), _p(w), _p(out))
+    return out
 
 
 def query_shade_grad(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S, grad_out,

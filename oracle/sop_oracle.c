@@ -30,7 +30,8 @@
  *     specular D F G / (4 NdotL NdotV), alpha = r^2, Schlick-GGX k=(r+1)^2/8,
  *     F0 = 0.08 spec (1-m) + a m, Schlick Fresnel;
  *   - equirectangular environment, z-up, u = (phi + pi)/(2 pi),
- *     v = theta/pi, bilinear with u wrapping and v clamped.
+ *     v = theta/pi, bilinear with u wrapping and v clamped; or (Sec. 4.1)
+ *     an octahedral environment with the probe maps' mapping and border.
  */
 #include <math.h>
 #include <stdint.h>
@@ -389,6 +390,52 @@ void orc_env_lookup(const float* env, int32_t He, int32_t We, const double* w, d
         }
 }
 
+/* Octahedral environment lookup (Sec. 4.1: the estimated environment map is
+ * converted to an octahedral texture): env [H][H][3] with the mapping and the
+ * border rule of the probe maps (texel (i, j) = column i along u, row j
+ * along v), bilinear. */
+void orc_env_oct_lookup(const float* env, int32_t H, const double* w, double* out)
+{
+    double uv[2];
+    orc_oct_encode(w, uv);
+    double s = uv[0] * H - 0.5, t = uv[1] * H - 0.5;
+    double fi = floor(s), fj = floor(t);
+    double fu = s - fi, fv = t - fj;
+    int i0 = (int)fi, j0 = (int)fj;
+    out[0] = out[1] = out[2] = 0.0;
+    for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+            double wgt = (di ? fu : 1.0 - fu) * (dj ? fv : 1.0 - fv);
+            int si, sj;
+            orc_oct_wrap(H, i0 + di, j0 + dj, &si, &sj);
+            const float* e = env + ((size_t)sj * H + si) * 3;
+            out[0] += wgt * e[0];
+            out[1] += wgt * e[1];
+            out[2] += wgt * e[2];
+        }
+}
+
+/* L_dir(w) from the environment in its layout: 0 = equirectangular [He][We],
+ * 1 = octahedral [He][He]. */
+void orc_env_sample(const float* env, int32_t He, int32_t We, int32_t layout, const double* w, double* out)
+{
+    if (layout == 1) orc_env_oct_lookup(env, He, w, out);
+    else orc_env_lookup(env, He, We, w, out);
+}
+
+/* Resample an equirectangular environment [He][We][3] into an octahedral one
+ * [H][H][3]: each texel holds the bilinear equirectangular value at its
+ * centre direction. */
+void orc_env_to_oct(const float* env, int32_t He, int32_t We, int32_t H, double* out)
+{
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < H; ++i) {
+            double d[3];
+            orc_texel_dir(H, i, j, d);
+            orc_env_lookup(env, He, We, d, out + ((size_t)j * H + i) * 3);
+        }
+}
+
 /* GGX / Trowbridge-Reitz normal distribution D(h) for alpha = r^2, written
  * with sin^2 = |n x h|^2 so that it stays accurate near n . h = 1. */
 double orc_ggx_D(double NdotH, double sin2, double rough)
@@ -447,7 +494,8 @@ enum { ORC_MODE_SHADE = 0, ORC_MODE_SHADOW = 1 };
  *   shadow: g[0..2] = L_dir (1 - O) (n . w), g[3..5] = L_dir (n . w) (Eq. 7-8) */
 static void sample_terms(const double* nn, const double* vo, const double* a, double rough, double metal, double spec,
                          int mode, const double* w, int32_t K, const int32_t* idx, const double* W, int32_t R,
-                         const double* mrgb, const double* mocc, const float* env, int32_t He, int32_t We, double* g)
+                         const double* mrgb, const double* mocc, const float* env, int32_t He, int32_t We,
+                         int32_t env_layout, double* g)
 {
     size_t RR = (size_t)R * R;
     double uv[2];
@@ -461,7 +509,7 @@ static void sample_terms(const double* nn, const double* vo, const double* a, do
         for (int c = 0; c < 3; ++c) Lin[c] += W[k] * l3[c];
     }
     double Ld[3];
-    orc_env_lookup(env, He, We, w, Ld);
+    orc_env_sample(env, He, We, env_layout, w, Ld);
     double NdotL = nn[0] * w[0] + nn[1] * w[1] + nn[2] * w[2];
     if (mode == ORC_MODE_SHADE) {
         double f[3];
@@ -515,7 +563,7 @@ void orc_query_shade(int64_t M, const float* x, const float* n, const float* wo,
                      const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
                      const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We, const float* env,
                      int32_t S, const double* dirs, int32_t K, int32_t mode, double spec, uint64_t snap_key,
-                     double* out, int32_t* out_idx, double* out_w)
+                     int32_t env_layout, double* out, int32_t* out_idx, double* out_w)
 {
     double *dl, *mrgb, *mocc;
     query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, K, snap_key, out_idx, out_w, &dl, &mrgb,
@@ -530,7 +578,7 @@ void orc_query_shade(int64_t M, const float* x, const float* n, const float* wo,
             double w[3], g[6];
             for (int c = 0; c < 3; ++c) w[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
             sample_terms(nn, vo, a, rough[m], metal[m], spec, mode, w, K, out_idx + (size_t)m * K,
-                         out_w + (size_t)m * K, R, mrgb, mocc, env, He, We, g);
+                         out_w + (size_t)m * K, R, mrgb, mocc, env, He, We, env_layout, g);
             for (int c = 0; c < (mode == ORC_MODE_SHADE ? 3 : 6); ++c) acc[c] += g[c];
         }
         for (int c = 0; c < 3; ++c) {
@@ -556,7 +604,7 @@ void orc_query_shade_sensitivity(int64_t M, const float* x, const float* n, cons
                                  const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
                                  const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We,
                                  const float* env, int32_t S, const double* dirs, int32_t K, int32_t mode, double spec,
-                                 uint64_t snap_key, double eps, double* kappa)
+                                 uint64_t snap_key, int32_t env_layout, double eps, double* kappa)
 {
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1) * K);
     double* W = (double*)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1) * K);
@@ -572,7 +620,7 @@ void orc_query_shade_sensitivity(int64_t M, const float* x, const float* n, cons
             double w[3], g0[6];
             for (int c = 0; c < 3; ++c) w[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
             sample_terms(nn, vo, a, rough[m], metal[m], spec, mode, w, K, idx + (size_t)m * K, W + (size_t)m * K, R,
-                         mrgb, mocc, env, He, We, g0);
+                         mrgb, mocc, env, He, We, env_layout, g0);
             /* two unit axes normal to w */
             double u1[3] = {w[1] * nn[2] - w[2] * nn[1], w[2] * nn[0] - w[0] * nn[2], w[0] * nn[1] - w[1] * nn[0]};
             double ul = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
@@ -587,7 +635,7 @@ void orc_query_shade_sensitivity(int64_t M, const float* x, const float* n, cons
                 double wl = sqrt(wp[0] * wp[0] + wp[1] * wp[1] + wp[2] * wp[2]);
                 for (int c = 0; c < 3; ++c) wp[c] /= wl;
                 sample_terms(nn, vo, a, rough[m], metal[m], spec, mode, wp, K, idx + (size_t)m * K, W + (size_t)m * K,
-                             R, mrgb, mocc, env, He, We, g1);
+                             R, mrgb, mocc, env, He, We, env_layout, g1);
                 for (int c = 0; c < 6; ++c) {
                     double d = fabs(g1[c] - g0[c]);
                     if (d > mx[c]) mx[c] = d;
@@ -962,6 +1010,11 @@ void orc_oct_bilerp_n(int64_t n, const double* map, int R, int C, const double* 
 void orc_env_lookup_n(int64_t n, const float* env, int32_t He, int32_t We, const double* w, double* out)
 {
     for (int64_t i = 0; i < n; ++i) orc_env_lookup(env, He, We, w + 3 * i, out + 3 * i);
+}
+
+void orc_env_oct_lookup_n(int64_t n, const float* env, int32_t H, const double* w, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) orc_env_oct_lookup(env, H, w + 3 * i, out + 3 * i);
 }
 
 void orc_brdf_n(int64_t n, const double* nrm, const double* wo, const double* wi, const double* albedo,
