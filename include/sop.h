@@ -121,13 +121,20 @@ typedef struct {
  * (1..4096), mode (sop_mode), specular = the Disney "specular" level giving
  * F0 = 0.08 specular (1-m) + a m (0.5 gives F0 = 0.04), eps_snap = distance
  * below which a shading point counts as sitting on its nearest probe (the
- * blend is then one-hot on that probe; default 1e-6). */
+ * blend is then one-hot on that probe; default 1e-6), env_layout = the
+ * environment's layout (SOP_ENV_EQUIRECT: [He][We][3] equirectangular, z-up;
+ * SOP_ENV_OCTAHEDRAL: [He][He][3] octahedral with the probe maps' mapping and
+ * border rule, Sec. 4.1; zero-initialised callers get the equirectangular
+ * layout). */
+#define SOP_ENV_EQUIRECT 0
+#define SOP_ENV_OCTAHEDRAL 1
 typedef struct {
     int32_t K;
     int32_t S;
     int32_t mode;
     float specular;
     float eps_snap;
+    int32_t env_layout;
 } sop_shade_params;
 
 /* Message for the last non-OK status returned to the calling thread
@@ -161,6 +168,13 @@ sop_status sop_atlas_pack_rgbo(const float* maps_rgbo, const sop_atlas* atlas, v
  * uniform on the hemisphere (Sec. 3.1.2, Eq. 3 low-discrepancy rays).
  * Asynchronous. */
 sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream);
+
+/* Resample an equirectangular environment env [He][We][3] (z-up) into an
+ * octahedral one out [H][H][3] (Sec. 4.1: the estimated environment is
+ * converted to an octahedral texture): texel (i, j) takes the bilinear
+ * equirectangular value at its centre direction. 2 <= H <= 4096. Device
+ * pointers; asynchronous. */
+sop_status sop_env_to_octahedral(const float* env, int32_t He, int32_t We, float* out, int32_t H, void* stream);
 
 /* Measurement utility (not part of the paper's method): reads the device
  * buffer buf [bytes] `reps` times with 16-byte loads from every SM, so that

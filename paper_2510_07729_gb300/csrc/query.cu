@@ -40,7 +40,7 @@ QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He,
     L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
     L.entries = o;    o = align256(o + sizeof(int4) * (size_t)P);
     L.env4 = o;       o = align256(o + sizeof(float4) * (size_t)(He + 2) * (We + 1));
-    L.envq = o;       o = align256(o + 64 * (size_t)(He + 1) * We);
+    L.envq = o;       o = align256(o + 64 * (size_t)(He + 1) * (We + 1));  // both layouts
     L.quads = o;      o = align256(o + (rgbo_dtype == SOP_F32 ? 64 : 32) * (size_t)P * (R + 1) * (R + 1));
     L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)S);
     L.idx = o;        o = align256(o + sizeof(int32_t) * (size_t)M * K);
@@ -357,6 +357,30 @@ __global__ void env_quad_kernel(const float4* __restrict__ env4, int32_t He, int
     q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Octahedral environment footprints (Sec. 4.1 layout, [H][H][3]): for base
+// (a, b) in [0, H]^2, the texels (a-1+di, b-1+dj), di, dj in {0, 1}, through
+// the probe maps' border rule, in the 64-byte slot format of env_quad_kernel
+// (e00, e01 = next column, e10 = next row, e11).
+__global__ void env_oct_quad_kernel(const float* __restrict__ env, int32_t H, float4* __restrict__ envq)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int HQ = H + 1;
+    if (k >= (int64_t)HQ * HQ) return;
+    const int b = (int)(k / HQ), a = (int)(k % HQ);
+    float3 e[4];
+    for (int q = 0; q < 4; ++q) {
+        int si, sj;
+        oct_wrap(H, a - 1 + (q & 1), b - 1 + (q >> 1), si, sj);
+        const float* t = env + ((int64_t)sj * H + si) * 3;
+        e[q] = f3(t[0], t[1], t[2]);
+    }
+    float4* o = envq + 4 * k;
+    o[0] = make_float4(e[0].x, e[0].y, e[0].z, e[1].x);
+    o[1] = make_float4(e[1].y, e[1].z, e[2].x, e[2].y);
+    o[2] = make_float4(e[2].z, e[3].x, e[3].y, e[3].z);
+    o[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Atlas footprints: for probe p and base (a, b) in [0, R]^2 of the stored
 // (gutter) map, the texels (a,b), (a+1,b), (a,b+1), (a+1,b+1) stored
 // contiguously, so one bilinear fetch reads one aligned 32/64-byte block.
@@ -468,6 +492,26 @@ __device__ __forceinline__ float3 env_lookup(const float4* __restrict__ envq, in
               w00 * q0.z + w01 * q1.y + w10 * q2.x + w11 * q2.w);
 }
 
+// Bilinear lookup of an octahedral environment (Sec. 4.1) at the octahedral
+// coordinates uv of the direction (the probe maps' mapping: no atan2), from
+// the footprint table of env_oct_quad_kernel.
+__device__ __forceinline__ float3 env_oct_lookup(const float4* __restrict__ envq, int H, float2 uv)
+{
+    const float s = uv.x * H - 0.5f, t = uv.y * H - 0.5f;
+    const float fs = floorf(s), ft = floorf(t);
+    const float a = s - fs, b = t - ft;
+    const int c0 = min(max((int)fs + 1, 0), H), r0 = min(max((int)ft + 1, 0), H);
+    const float4* q = envq + 4 * ((int64_t)r0 * (H + 1) + c0);
+    uint64_t x0, x1, x2, x3;
+    ldg256(q, x0, x1, x2, x3);
+    const float4 q0 = make_float4(lo32f(x0), hi32f(x0), lo32f(x1), hi32f(x1));
+    const float4 q1 = make_float4(lo32f(x2), hi32f(x2), lo32f(x3), hi32f(x3));
+    const float4 q2 = __ldg(q + 2);
+    const float w00 = (1.f - a) * (1.f - b), w01 = a * (1.f - b), w10 = (1.f - a) * b, w11 = a * b;
+    return f3(w00 * q0.x + w01 * q0.w + w10 * q1.z + w11 * q2.y, w00 * q0.y + w01 * q1.x + w10 * q1.w + w11 * q2.z,
+              w00 * q0.z + w01 * q1.y + w10 * q2.x + w11 * q2.w);
+}
+
 // One bilinear footprint of the atlas: four texels as float4 (RGB, O).
 template <int DT> struct Quad;
 template <> struct Quad<SOP_F32> {
@@ -548,6 +592,7 @@ template <> struct OQuad<SOP_BF16> {
 // (offset of the base texel in a probe's stored map) and bilinear weights.
 struct DirTerms {
     float3 w;
+    float2 uv;
     int off;
     float w00, w10, w01, w11;
 };
@@ -558,6 +603,7 @@ __device__ __forceinline__ DirTerms dir_terms(const float4 l, const float3 tt, c
     d.w = f3(fmaf(l.x, tt.x, fmaf(l.y, bb.x, l.z * n.x)), fmaf(l.x, tt.y, fmaf(l.y, bb.y, l.z * n.y)),
              fmaf(l.x, tt.z, fmaf(l.y, bb.z, l.z * n.z)));
     const float2 uv = oct_encode(d.w);
+    d.uv = uv;
     const float s = uv.x * Rf - 0.5f, t = uv.y * Rf - 0.5f;
     const float fi = floorf(s), fj = floorf(t);
     const float fu = s - fi, fv = t - fj;
@@ -602,6 +648,7 @@ struct ShadeK {
     const void* rgbo;
     int32_t R, K, S, He, We;
     const float4* envq;
+    int32_t env_layout;
     const void* quads;
     const float4* dirs;
     const int32_t* idx;
@@ -699,7 +746,8 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
         for (int i = (int)(threadIdx.x & 31); i < a.S; i += 32) {
             const float4 l = s_dirs[i];
             const DirTerms d = dir_terms(l, tt, bb, n, Rf, a.R, RQ);
-            const float3 Ld = env_lookup(a.envq, a.He, a.We, d.w);
+            const float3 Ld = a.env_layout == SOP_ENV_OCTAHEDRAL ? env_oct_lookup(a.envq, a.He, d.uv)
+                                                                 : env_lookup(a.envq, a.He, a.We, d.w);
             const float NdotL = l.z;
             tab[i] = make_float4(__int_as_float(d.off), d.w00, d.w10, d.w01);
             tab[a.S + i] = make_float4(d.w11, Ld.x * NdotL, Ld.y * NdotL, Ld.z * NdotL);
@@ -739,7 +787,8 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
                 pr.w += c00 * t00.w + c10 * t10.w + c01 * t01.w + c11 * t11.w;
             }
         }
-        const float3 Ld = env_lookup(a.envq, a.He, a.We, w);
+        const float3 Ld = a.env_layout == SOP_ENV_OCTAHEDRAL ? env_oct_lookup(a.envq, a.He, d.uv)
+                                                             : env_lookup(a.envq, a.He, a.We, w);
         const float NdotL = l.z;
         const float vis = 1.f - pr.w;
         if (MODE == SOP_MODE_SHADE) {
@@ -824,12 +873,19 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
         else SOP_KNN(32);
 #undef SOP_KNN
     }
-    const int64_t ne = (int64_t)(a.He + 2) * (a.We + 1);
-    env_pack_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(a.env, a.He, a.We,
-                                                                   reinterpret_cast<float4*>(ws + L.env4));
-    const int64_t nq = (int64_t)(a.He + 1) * a.We;
-    env_quad_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(ws + L.env4), a.He,
-                                                                   a.We, reinterpret_cast<float4*>(ws + L.envq));
+    if (a.env_layout == SOP_ENV_OCTAHEDRAL) {
+        const int64_t nq = (int64_t)(a.He + 1) * (a.He + 1);
+        env_oct_quad_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(a.env, a.He,
+                                                                         reinterpret_cast<float4*>(ws + L.envq));
+    } else {
+        const int64_t ne = (int64_t)(a.He + 2) * (a.We + 1);
+        env_pack_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(a.env, a.He, a.We,
+                                                                       reinterpret_cast<float4*>(ws + L.env4));
+        const int64_t nq = (int64_t)(a.He + 1) * a.We;
+        env_quad_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(ws + L.env4),
+                                                                       a.He, a.We,
+                                                                       reinterpret_cast<float4*>(ws + L.envq));
+    }
     const int64_t na = (int64_t)a.P * (a.R + 1) * (a.R + 1);
     const unsigned nba = (unsigned)((na + 255) / 256);
     if (a.mode == SOP_MODE_SHADOW) {
@@ -928,6 +984,7 @@ cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cud
     k.He = a.He;
     k.We = a.We;
     k.envq = reinterpret_cast<const float4*>(ws + L.envq);
+    k.env_layout = a.env_layout;
     k.quads = ws + L.quads;
     k.dirs = reinterpret_cast<const float4*>(ws + L.dirs);
     k.idx = reinterpret_cast<const int32_t*>(ws + L.idx);
@@ -1355,6 +1412,29 @@ __device__ __forceinline__ float3 env_lookup_direct(const float* __restrict__ en
     return f3(w00 * __ldg(e00) + w01 * __ldg(e01) + w10 * __ldg(e10) + w11 * __ldg(e11),
               w00 * __ldg(e00 + 1) + w01 * __ldg(e01 + 1) + w10 * __ldg(e10 + 1) + w11 * __ldg(e11 + 1),
               w00 * __ldg(e00 + 2) + w01 * __ldg(e01 + 2) + w10 * __ldg(e10 + 2) + w11 * __ldg(e11 + 2));
+}
+
+// Equirectangular -> octahedral environment (Sec. 4.1): texel (i, j) of the
+// [H][H] map takes the bilinear equirectangular value at its centre
+// direction (computed in double, rounded once).
+__global__ void env_to_oct_kernel(const float* __restrict__ env, int32_t He, int32_t We, float* __restrict__ out,
+                                  int32_t H)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (int64_t)H * H) return;
+    double d[3];
+    oct_decode_centre_f64(H, (int)(k % H), (int)(k / H), d);
+    const float3 v = env_lookup_direct(env, He, We, f3((float)d[0], (float)d[1], (float)d[2]));
+    out[3 * k] = v.x;
+    out[3 * k + 1] = v.y;
+    out[3 * k + 2] = v.z;
+}
+
+cudaError_t launch_env_to_oct(const float* env, int32_t He, int32_t We, float* out, int32_t H, cudaStream_t s)
+{
+    const int64_t n = (int64_t)H * H;
+    env_to_oct_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(env, He, We, out, H);
+    return cudaGetLastError();
 }
 
 struct ShadeDirectK {

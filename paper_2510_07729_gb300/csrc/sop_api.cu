@@ -74,6 +74,8 @@ sop_status check_shade(const sop_shade_params* p, int32_t P)
         return fail(SOP_ERR_INVALID_ARG, "mode = %d is neither SHADE nor SHADOW", p->mode);
     if (!(p->eps_snap >= 0.f) || !isfinite(p->eps_snap)) return fail(SOP_ERR_INVALID_ARG, "eps_snap must be >= 0");
     if (!isfinite(p->specular)) return fail(SOP_ERR_INVALID_ARG, "specular must be finite");
+    if (p->env_layout != SOP_ENV_EQUIRECT && p->env_layout != SOP_ENV_OCTAHEDRAL)
+        return fail(SOP_ERR_INVALID_ARG, "env_layout = %d is neither EQUIRECT nor OCTAHEDRAL", p->env_layout);
     return SOP_OK;
 }
 
@@ -145,6 +147,15 @@ sop_status sop_adam_l1_step(float* p, const float* g, float* m, float* v, int64_
         !(a->eps >= 0.f))
         return fail(SOP_ERR_INVALID_ARG, "lr must be > 0, beta1/beta2 in [0, 1), eps >= 0");
     return cuda_status(sop::launch_adam_l1(p, g, m, v, n, *a, (cudaStream_t)stream), "sop_adam_l1_step");
+}
+
+sop_status sop_env_to_octahedral(const float* env, int32_t He, int32_t We, float* out, int32_t H, void* stream)
+{
+    if (!env || !out) return fail(SOP_ERR_INVALID_ARG, "env or out is NULL");
+    if (He < 1 || We < 1 || (int64_t)He * We > ((int64_t)1 << 28))
+        return fail(SOP_ERR_INVALID_ARG, "environment size %d x %d invalid", He, We);
+    if (H < 2 || H > 4096) return fail(SOP_ERR_INVALID_ARG, "H = %d outside [2, 4096]", H);
+    return cuda_status(sop::launch_env_to_oct(env, He, We, out, H, (cudaStream_t)stream), "sop_env_to_octahedral");
 }
 
 sop_status sop_read_bandwidth_probe(const void* buf, size_t bytes, int32_t reps, float* sink, void* stream)
@@ -280,6 +291,8 @@ static sop_status query_common(const float* x, const float* n, const float* wo, 
     if (M < 0 || M > ((int64_t)1 << 36)) return fail(SOP_ERR_INVALID_ARG, "M = %lld out of range", (long long)M);
     if (He < 1 || We < 1 || (int64_t)He * We > ((int64_t)1 << 28))
         return fail(SOP_ERR_INVALID_ARG, "environment size %d x %d invalid", He, We);
+    if (params->env_layout == SOP_ENV_OCTAHEDRAL && (He != We || He < 2))
+        return fail(SOP_ERR_INVALID_ARG, "an octahedral environment is square, H >= 2 (got %d x %d)", He, We);
     if (!env) return fail(SOP_ERR_INVALID_ARG, "env is NULL");
     if (M > 0 && (!x || !n || !wo || !albedo || !rough || !metal))
         return fail(SOP_ERR_INVALID_ARG, "a shading-point array is NULL");
@@ -306,6 +319,7 @@ static sop_status query_common(const float* x, const float* n, const float* wo, 
     a.K = params->K;
     a.S = params->S;
     a.mode = params->mode;
+    a.env_layout = params->env_layout;
     a.specular = params->specular;
     const double e = (double)params->eps_snap * 1048576.0;
     a.snap_key = (uint64_t)floor(e * e);
@@ -344,6 +358,8 @@ sop_status sop_query_shade_backward(const float* x, const float* n, const float*
     sop_status st = query_common(x, n, wo, albedo, rough, metal, M, atlas, env, He, We, dirs_local, params, ws,
                                  ws_bytes, a, L);
     if (st != SOP_OK) return st;
+    if (params && params->env_layout != SOP_ENV_EQUIRECT)
+        return fail(SOP_ERR_UNSUPPORTED, "the adjoint takes the equirectangular environment layout only");
     if (params->mode != SOP_MODE_SHADE)
         return fail(SOP_ERR_UNSUPPORTED, "sop_query_shade_backward: only SOP_MODE_SHADE has an adjoint");
     if (M > 0 && (!grad_out || !g_albedo || !g_rough || !g_metal || !g_normal))
@@ -373,6 +389,8 @@ sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* 
     if (st != SOP_OK) return st;
     st = check_shade(params, atlas->P);
     if (st != SOP_OK) return st;
+    if (params->env_layout != SOP_ENV_EQUIRECT)
+        return fail(SOP_ERR_UNSUPPORTED, "sop_query_shade_noalloc takes the equirectangular environment layout only");
     const size_t need = sop::noalloc_required_bytes(atlas->P, params->K, params->S);
     if (atlas->P > SOP_NOALLOC_MAX_PROBES || need > sop::noalloc_scratch_bytes())
         return fail(SOP_ERR_INVALID_ARG,
@@ -405,6 +423,7 @@ sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* 
     a.K = params->K;
     a.S = params->S;
     a.mode = params->mode;
+    a.env_layout = params->env_layout;
     a.specular = params->specular;
     const double e = (double)params->eps_snap * 1048576.0;
     a.snap_key = (uint64_t)floor(e * e);

@@ -17,6 +17,7 @@ from . import build as _build
 
 SOP_F32, SOP_BF16, SOP_F16, SOP_FP8E4M3 = 0, 1, 2, 3
 MODE_SHADE, MODE_SHADOW = 0, 1
+ENV_EQUIRECT, ENV_OCTAHEDRAL = 0, 1
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "WORKSPACE", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "DEVICE"}
 
 
@@ -49,7 +50,7 @@ class AdamParams(C.Structure):
 
 class ShadeParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("S", C.c_int32), ("mode", C.c_int32), ("specular", C.c_float),
-                ("eps_snap", C.c_float)]
+                ("eps_snap", C.c_float), ("env_layout", C.c_int32)]
 
 
 _lib = None
@@ -77,6 +78,7 @@ def load(build_if_missing: bool = True):
     lib.sop_hammersley.argtypes = [i32, vp, vp]
     lib.sop_read_bandwidth_probe.argtypes = [vp, sz, i32, vp, vp]
     lib.sop_atlas_pack_rgbo.argtypes = [vp, C.POINTER(AtlasDesc), vp]
+    lib.sop_env_to_octahedral.argtypes = [vp, i32, i32, vp, i32, vp]
     lib.sop_l1_loss_grad.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.sop_adam_l1_step.argtypes = [vp, vp, vp, vp, i64, C.POINTER(AdamParams), vp]
     lib.sop_bake_workspace_bytes.argtypes = [i64, i32, i32]
@@ -112,7 +114,7 @@ def load(build_if_missing: bool = True):
     for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_bake_bin", "sop_bake_trace",
                  "sop_bake_stats", "sop_query_shade",
                  "sop_query_shade_backward", "sop_query_shade_noalloc", "sop_read_bandwidth_probe",
-                 "sop_atlas_pack_rgbo", "sop_l1_loss_grad", "sop_adam_l1_step"):
+                 "sop_atlas_pack_rgbo", "sop_l1_loss_grad", "sop_adam_l1_step", "sop_env_to_octahedral"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -229,6 +231,15 @@ def atlas_pack_rgbo(maps, atlas: Atlas):
     d = atlas.c()
     _check(load().sop_atlas_pack_rgbo(_f32(maps, (P, R, R, 4)), C.byref(d), _stream()))
     return atlas
+
+
+def env_to_octahedral(env, H):
+    """sop_env_to_octahedral: an equirectangular environment [He,We,3] (device,
+    float32) resampled into an octahedral one [H,H,3]."""
+    He, We = env.shape[0], env.shape[1]
+    out = torch.empty((H, H, 3), dtype=torch.float32, device=env.device)
+    _check(load().sop_env_to_octahedral(_f32(env, (He, We, 3)), He, We, _ptr(out), H, _stream()))
+    return out
 
 
 def hammersley(S, device="cuda"):
@@ -355,14 +366,14 @@ def query_workspace_bytes(atlas: Atlas, M, K, S, He, We, mode=MODE_SHADE):
 
 
 def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MODE_SHADE, specular=0.5,
-                eps_snap=1e-6, dirs_local=None, out=None, return_idx=False, workspace=None):
+                eps_snap=1e-6, dirs_local=None, out=None, return_idx=False, workspace=None, env_layout=ENV_EQUIRECT):
     """SOP query + shade of M points; returns out [M,3] (and idx [M,K] int32,
     W [M,K] float32 when return_idx)."""
     lib = load()
     M = x.shape[0]
     He, We = env.shape[0], env.shape[1]
     dev = x.device
-    sp = ShadeParams(K, S, mode, specular, eps_snap)
+    sp = ShadeParams(K, S, mode, specular, eps_snap, env_layout)
     d = atlas.c()
     if out is None:
         out = torch.empty((M, 3), dtype=torch.float32, device=dev)
