@@ -934,22 +934,27 @@ static cudaError_t shade_launch(const ShadeK& k, int LANES, cudaStream_t s)
 
 // Threads per shading point (they split the S directions); SOP_SHADE_LANES
 // overrides the default for tuning.
-// Default (measured on GB300, 'object' workload): one thread per point for a
-// float32 atlas, two for 16-bit atlases.
-static int shade_lanes(int dtype)
+// Default (measured on GB300, object workload): one thread per point for a
+// float32 atlas, two for 16-bit atlases; small point sets (the composition
+// frame's 21,907 object pixels) take more lanes per point, up to 8, until the
+// launch has about two waves of threads on the 152 SMs.
+static int shade_lanes(int dtype, int64_t M)
 {
     static int lanes = [] {
         const char* e = getenv("SOP_SHADE_LANES");
         const int v = e ? atoi(e) : 0;
         return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 0;
     }();
-    return lanes ? lanes : (dtype == SOP_F32 ? 1 : 2);
+    if (lanes) return lanes;
+    int l = dtype == SOP_F32 ? 1 : 2;
+    while (l < 8 && M * l < (int64_t)2 * 152 * 1024) l *= 2;
+    return l;
 }
 
 template <int DT, int KMAX, int MODE>
 static cudaError_t shade_dispatch(const ShadeK& k, cudaStream_t s)
 {
-    return shade_launch<DT, KMAX, MODE>(k, shade_lanes(DT), s);
+    return shade_launch<DT, KMAX, MODE>(k, shade_lanes(DT, k.M), s);
 }
 
 template <int DT, int MODE>
