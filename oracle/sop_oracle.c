@@ -436,6 +436,51 @@ void orc_env_to_oct(const float* env, int32_t He, int32_t We, int32_t H, double*
         }
 }
 
+/* Importance-sampled light directions (Sec. 4.2, Eq. PDF: density
+ * H W I / (4 pi) over the octahedral environment's texels): S world
+ * directions with their density, out [S][4] = (x, y, z, pdf). Readings: the
+ * intensity of a texel is the float32 sum r + g + b; it is quantised to
+ * q_t = max(1, floor(I_t / I_max 2^20)) (in double) so that the choice of a
+ * texel is an exact integer decision; sample i takes the texel whose
+ * cumulative interval [C_{t-1}, C_t) holds floor((2i + 1) Q / (2S)),
+ * Q = sum q (stratified); its direction is the texel centre and its density
+ * H^2 q_t / (4 pi Q) (texels of equal solid angle, as the equation takes). */
+void orc_env_importance_dirs(const float* env, int32_t H, int32_t S, double* out)
+{
+    const int64_t T = (int64_t)H * H;
+    float imax = 0.f;
+    for (int64_t t = 0; t < T; ++t) {
+        float I = env[3 * t] + env[3 * t + 1] + env[3 * t + 2];
+        if (I > imax) imax = I;
+    }
+    int64_t* cum = (int64_t*)malloc(sizeof(int64_t) * (size_t)T);
+    int64_t Q = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        float I = env[3 * t] + env[3 * t + 1] + env[3 * t + 2];
+        int64_t q = imax > 0.f ? (int64_t)floor((double)I / (double)imax * 1048576.0) : 1;
+        if (q < 1) q = 1;
+        Q += q;
+        cum[t] = Q;
+    }
+    for (int32_t i = 0; i < S; ++i) {
+        const int64_t target = (2 * (int64_t)i + 1) * Q / (2 * (int64_t)S);
+        int64_t lo = 0, hi = T - 1;  /* smallest t with cum[t] > target */
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (cum[mid] > target) hi = mid;
+            else lo = mid + 1;
+        }
+        const int64_t q = cum[lo] - (lo > 0 ? cum[lo - 1] : 0);
+        double d[3];
+        orc_texel_dir(H, (int)(lo % H), (int)(lo / H), d);
+        out[4 * i] = d[0];
+        out[4 * i + 1] = d[1];
+        out[4 * i + 2] = d[2];
+        out[4 * i + 3] = (double)T * (double)q / (4.0 * M_PI * (double)Q);
+    }
+    free(cum);
+}
+
 /* GGX / Trowbridge-Reitz normal distribution D(h) for alpha = r^2, written
  * with sin^2 = |n x h|^2 so that it stays accurate near n . h = 1. */
 double orc_ggx_D(double NdotH, double sin2, double rough)
@@ -524,11 +569,13 @@ static void sample_terms(const double* nn, const double* vo, const double* a, do
 }
 
 static void query_setup(int64_t M, const float* x, const float* n, int32_t P, const float* probe_pos, int32_t R,
-                        const float* maps_rgb, const float* maps_occ, int32_t S, const double* dirs, int32_t K,
-                        uint64_t snap_key, int32_t* out_idx, double* out_w, double** dl, double** mrgb, double** mocc)
+                        const float* maps_rgb, const float* maps_occ, int32_t S, const double* dirs, int32_t dir_world,
+                        int32_t K, uint64_t snap_key, int32_t* out_idx, double* out_w, double** dl, double** mrgb,
+                        double** mocc)
 {
-    *dl = (double*)malloc(sizeof(double) * 3 * (size_t)S);
-    if (dirs) memcpy(*dl, dirs, sizeof(double) * 3 * (size_t)S);
+    const size_t st = dir_world ? 4 : 3;
+    *dl = (double*)malloc(sizeof(double) * st * (size_t)S);
+    if (dirs) memcpy(*dl, dirs, sizeof(double) * st * (size_t)S);
     else orc_hammersley(S, *dl);
     size_t RR = (size_t)R * R;
     *mrgb = (double*)malloc(sizeof(double) * 3 * RR * (size_t)P);
@@ -539,6 +586,23 @@ static void query_setup(int64_t M, const float* x, const float* n, int32_t P, co
     orc_knn(M, x, P, probe_pos, K, out_idx, key);
     orc_weights(M, x, n, probe_pos, K, out_idx, key, snap_key, out_w);
     free(key);
+}
+
+/* World direction w of sample i and its Monte Carlo weight: a local
+ * direction rotated into the frame (t, b, n) with weight 1 (the 2 pi / S
+ * factor is applied at the end), or (dir_world) an importance-sampled world
+ * direction with weight 1 / pdf, 0 below the point's horizon. */
+static double sample_dir(const double* dl, int32_t dir_world, int32_t i, const double* t, const double* b,
+                         const double* nn, double* w)
+{
+    if (dir_world) {
+        const double* l = dl + 4 * (size_t)i;
+        w[0] = l[0]; w[1] = l[1]; w[2] = l[2];
+        return (nn[0] * w[0] + nn[1] * w[1] + nn[2] * w[2]) > 0.0 ? 1.0 / l[3] : 0.0;
+    }
+    const double* l = dl + 3 * (size_t)i;
+    for (int c = 0; c < 3; ++c) w[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
+    return 1.0;
 }
 
 static void point_frame(const float* n, const float* wo, const float* albedo, int64_t m, double* nn, double* vo,
@@ -563,26 +627,26 @@ void orc_query_shade(int64_t M, const float* x, const float* n, const float* wo,
                      const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
                      const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We, const float* env,
                      int32_t S, const double* dirs, int32_t K, int32_t mode, double spec, uint64_t snap_key,
-                     int32_t env_layout, double* out, int32_t* out_idx, double* out_w)
+                     int32_t env_layout, int32_t dir_world, double* out, int32_t* out_idx, double* out_w)
 {
     double *dl, *mrgb, *mocc;
-    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, K, snap_key, out_idx, out_w, &dl, &mrgb,
-                &mocc);
+    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, dir_world, K, snap_key, out_idx, out_w, &dl,
+                &mrgb, &mocc);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t m = 0; m < M; ++m) {
         double nn[3], vo[3], a[3], t[3], b[3];
         point_frame(n, wo, albedo, m, nn, vo, a, t, b);
         double acc[6] = {0, 0, 0, 0, 0, 0};
         for (int32_t i = 0; i < S; ++i) {
-            const double* l = dl + 3 * i;
             double w[3], g[6];
-            for (int c = 0; c < 3; ++c) w[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
+            const double wt = sample_dir(dl, dir_world, i, t, b, nn, w);
+            if (wt == 0.0) continue;
             sample_terms(nn, vo, a, rough[m], metal[m], spec, mode, w, K, out_idx + (size_t)m * K,
                          out_w + (size_t)m * K, R, mrgb, mocc, env, He, We, env_layout, g);
-            for (int c = 0; c < (mode == ORC_MODE_SHADE ? 3 : 6); ++c) acc[c] += g[c];
+            for (int c = 0; c < (mode == ORC_MODE_SHADE ? 3 : 6); ++c) acc[c] += wt * g[c];
         }
         for (int c = 0; c < 3; ++c) {
-            if (mode == ORC_MODE_SHADE) out[3 * m + c] = 2.0 * M_PI / S * acc[c];
+            if (mode == ORC_MODE_SHADE) out[3 * m + c] = (dir_world ? 1.0 : 2.0 * M_PI) / S * acc[c];
             else out[3 * m + c] = (acc[3 + c] < 1e-20) ? 1.0 : acc[c] / acc[3 + c];
         }
     }
@@ -604,23 +668,25 @@ void orc_query_shade_sensitivity(int64_t M, const float* x, const float* n, cons
                                  const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
                                  const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We,
                                  const float* env, int32_t S, const double* dirs, int32_t K, int32_t mode, double spec,
-                                 uint64_t snap_key, int32_t env_layout, double eps, double* kappa)
+                                 uint64_t snap_key, int32_t env_layout, int32_t dir_world, double eps, double* kappa)
 {
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1) * K);
     double* W = (double*)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1) * K);
     double *dl, *mrgb, *mocc;
-    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, K, snap_key, idx, W, &dl, &mrgb, &mocc);
+    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, dir_world, K, snap_key, idx, W, &dl, &mrgb,
+                &mocc);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t m = 0; m < M; ++m) {
         double nn[3], vo[3], a[3], t[3], b[3];
         point_frame(n, wo, albedo, m, nn, vo, a, t, b);
         double acc[6] = {0, 0, 0, 0, 0, 0}, dev[6] = {0, 0, 0, 0, 0, 0};
         for (int32_t i = 0; i < S; ++i) {
-            const double* l = dl + 3 * i;
             double w[3], g0[6];
-            for (int c = 0; c < 3; ++c) w[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
+            const double wt = sample_dir(dl, dir_world, i, t, b, nn, w);
+            if (wt == 0.0) continue;
             sample_terms(nn, vo, a, rough[m], metal[m], spec, mode, w, K, idx + (size_t)m * K, W + (size_t)m * K, R,
                          mrgb, mocc, env, He, We, env_layout, g0);
+            for (int c = 0; c < 6; ++c) g0[c] *= wt;
             /* two unit axes normal to w */
             double u1[3] = {w[1] * nn[2] - w[2] * nn[1], w[2] * nn[0] - w[0] * nn[2], w[0] * nn[1] - w[1] * nn[0]};
             double ul = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
@@ -636,6 +702,7 @@ void orc_query_shade_sensitivity(int64_t M, const float* x, const float* n, cons
                 for (int c = 0; c < 3; ++c) wp[c] /= wl;
                 sample_terms(nn, vo, a, rough[m], metal[m], spec, mode, wp, K, idx + (size_t)m * K, W + (size_t)m * K,
                              R, mrgb, mocc, env, He, We, env_layout, g1);
+                for (int c = 0; c < 6; ++c) g1[c] *= wt;
                 for (int c = 0; c < 6; ++c) {
                     double d = fabs(g1[c] - g0[c]);
                     if (d > mx[c]) mx[c] = d;
@@ -647,7 +714,7 @@ void orc_query_shade_sensitivity(int64_t M, const float* x, const float* n, cons
             }
         }
         for (int c = 0; c < 3; ++c) {
-            if (mode == ORC_MODE_SHADE) kappa[3 * m + c] = 2.0 * M_PI / S * dev[c];
+            if (mode == ORC_MODE_SHADE) kappa[3 * m + c] = (dir_world ? 1.0 : 2.0 * M_PI) / S * dev[c];
             else if (acc[3 + c] < 1e-20) kappa[3 * m + c] = 0.0;
             else kappa[3 * m + c] = (dev[c] + fabs(acc[c] / acc[3 + c]) * dev[3 + c]) / acc[3 + c];
         }
@@ -774,7 +841,7 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
     double* W = (double*)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1) * K);
     uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(M > 0 ? M : 1) * K);
     double *dl, *mrgb, *mocc;
-    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, K, snap_key, idx, W, &dl, &mrgb, &mocc);
+    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, 0, K, snap_key, idx, W, &dl, &mrgb, &mocc);
     orc_knn(M, x, P, probe_pos, K, idx, key);
     size_t RR = (size_t)R * R;
 #pragma omp parallel for schedule(dynamic, 16)
