@@ -195,8 +195,10 @@ def weights(x, n, probe_pos, idx, key, snap_key=None):
 
 
 def query_shade(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S,
-                mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, env_layout=ENV_EQUIRECT):
-    """FP64 query + shade. Returns out [M,3], idx [M,K], W [M,K]."""
+                mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, env_layout=ENV_EQUIRECT, dir_world=False):
+    """FP64 query + shade. Returns out [M,3], idx [M,K], W [M,K]. dirs: the
+    local direction set [S,3] (None: the centred Hammersley set), or with
+    dir_world the importance-sampled world directions [S,4] (x, y, z, pdf)."""
     x, n, wo, albedo, rough, metal = (_f32(v) for v in (x, n, wo, albedo, rough, metal))
     pp, mr, mo, env = _f32(probe_pos), _f32(maps_rgb), _f32(maps_occ), _f32(env)
     P, R = mr.shape[0], mr.shape[1]
@@ -210,8 +212,8 @@ def query_shade(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, e
     lib().orc_query_shade(C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal),
                           C.c_int32(P), _p(pp), C.c_int32(R), _p(mr), _p(mo), C.c_int32(He), C.c_int32(We),
                           _p(env), C.c_int32(S), None if dp is None else _p(dp), C.c_int32(K),
-                          C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_int32(env_layout), _p(out), _p(idx),
-                          _p(W))
+                          C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_int32(env_layout),
+                          C.c_int32(1 if dir_world else 0), _p(out), _p(idx), _p(W))
     return out, idx, W
 
 
@@ -222,7 +224,7 @@ FP32_DIR_EPS = 2e-6
 
 def query_shade_sensitivity(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S,
                             mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, eps=FP32_DIR_EPS,
-                            env_layout=ENV_EQUIRECT):
+                            env_layout=ENV_EQUIRECT, dir_world=False):
     """Per-output allowance [M,3] for an FP32 evaluation (see the C docs)."""
     x, n, wo, albedo, rough, metal = (_f32(v) for v in (x, n, wo, albedo, rough, metal))
     pp, mr, mo, env = _f32(probe_pos), _f32(maps_rgb), _f32(maps_occ), _f32(env)
@@ -235,8 +237,8 @@ def query_shade_sensitivity(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb,
     lib().orc_query_shade_sensitivity(
         C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal), C.c_int32(P), _p(pp), C.c_int32(R),
         _p(mr), _p(mo), C.c_int32(He), C.c_int32(We), _p(env), C.c_int32(S), None if dp is None else _p(dp),
-        C.c_int32(K), C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_int32(env_layout), C.c_double(eps),
-        _p(kap))
+        C.c_int32(K), C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_int32(env_layout),
+        C.c_int32(1 if dir_world else 0), C.c_double(eps), _p(kap))
     return kap
 
 
@@ -247,6 +249,15 @@ def env_to_octahedral(env, H):
     He, We, _ = env.shape
     out = np.empty((H, H, 3))
     lib().orc_env_to_oct(_p(env), C.c_int32(He), C.c_int32(We), C.c_int32(H), _p(out))
+    return out
+
+
+def env_importance_dirs(env, S):
+    """Importance-sampled light directions [S,4] (x, y, z, pdf) from an
+    octahedral environment [H,H,3] (see orc_env_importance_dirs)."""
+    env = _f32(env)
+    out = np.empty((S, 4))
+    lib().orc_env_importance_dirs(_p(env), C.c_int32(env.shape[0]), C.c_int32(S), _p(out))
     return out
 
 
