@@ -125,7 +125,13 @@ typedef struct {
  * environment's layout (SOP_ENV_EQUIRECT: [He][We][3] equirectangular, z-up;
  * SOP_ENV_OCTAHEDRAL: [He][He][3] octahedral with the probe maps' mapping and
  * border rule, Sec. 4.1; zero-initialised callers get the equirectangular
- * layout). */
+ * layout), dir_world = 0: dirs_local is the local direction set (or NULL)
+ * and the estimator is 2 pi / S sum (Eq. 3); 1: dirs_local is required and
+ * holds S world directions with their density, [S][4] = (x, y, z, pdf), as
+ * sop_env_importance_dirs writes them, shared by every point, and the
+ * estimator is 1/S sum over the directions above the point's horizon of the
+ * terms divided by pdf (Sec. 4.2); the adjoint and the allocation-free entry
+ * point take dir_world = 0 only. */
 #define SOP_ENV_EQUIRECT 0
 #define SOP_ENV_OCTAHEDRAL 1
 typedef struct {
@@ -135,6 +141,7 @@ typedef struct {
     float specular;
     float eps_snap;
     int32_t env_layout;
+    int32_t dir_world;
 } sop_shade_params;
 
 /* Message for the last non-OK status returned to the calling thread
@@ -175,6 +182,22 @@ sop_status sop_hammersley(int32_t S, float* out_dirs, void* stream);
  * equirectangular value at its centre direction. 2 <= H <= 4096. Device
  * pointers; asynchronous. */
 sop_status sop_env_to_octahedral(const float* env, int32_t He, int32_t We, float* out, int32_t H, void* stream);
+
+/* Importance-sampled light directions for rendering (Sec. 4.2, Eq. PDF:
+ * density H W I / (4 pi) over the octahedral environment's texels): from an
+ * octahedral environment env [H][H][3], S world directions out [S][4] =
+ * (x, y, z, pdf) for sop_query_shade with dir_world = 1. The intensity of a
+ * texel is the float32 sum r + g + b; it is quantised to
+ * q = max(1, floor(I / I_max 2^20)) so that the texel chosen is an exact
+ * integer decision; sample i takes the texel whose cumulative interval holds
+ * floor((2i + 1) Q / (2S)) (Q = sum q; stratified), in its centre direction,
+ * with pdf = H^2 q / (4 pi Q) (texels taken as equal in solid angle, as the
+ * equation does). 2 <= H <= 2048, 1 <= S <= 4096. ws: workspace of
+ * sop_env_importance_workspace_bytes(H) bytes, 256-byte aligned. Device
+ * pointers; asynchronous. */
+size_t sop_env_importance_workspace_bytes(int32_t H);
+sop_status sop_env_importance_dirs(const float* env, int32_t H, int32_t S, float* out, void* ws, size_t ws_bytes,
+                                   void* stream);
 
 /* Measurement utility (not part of the paper's method): reads the device
  * buffer buf [bytes] `reps` times with 16-byte loads from every SM, so that

@@ -457,6 +457,15 @@ __global__ void dirs_kernel(int32_t S, const float* __restrict__ dirs_local, flo
     }
 }
 
+// Importance-sampled world directions (x, y, z, pdf) -> (x, y, z, 1/pdf).
+__global__ void world_dirs_kernel(int32_t S, const float4* __restrict__ dirs_world, float4* __restrict__ out4)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    const float4 d = dirs_world[i];
+    out4[i] = make_float4(d.x, d.y, d.z, 1.f / d.w);
+}
+
 // 256-bit read-only global load (sm_100+); p must be 32-byte aligned.
 __device__ __forceinline__ void ldg256(const void* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d)
 {
@@ -596,12 +605,11 @@ struct DirTerms {
     int off;
     float w00, w10, w01, w11;
 };
-__device__ __forceinline__ DirTerms dir_terms(const float4 l, const float3 tt, const float3 bb, const float3 n,
-                                              const float Rf, const int R, const int RQ)
+// footprint part for a world direction w
+__device__ __forceinline__ DirTerms footprint_terms(const float3 w, const float Rf, const int R, const int RQ)
 {
     DirTerms d;
-    d.w = f3(fmaf(l.x, tt.x, fmaf(l.y, bb.x, l.z * n.x)), fmaf(l.x, tt.y, fmaf(l.y, bb.y, l.z * n.y)),
-             fmaf(l.x, tt.z, fmaf(l.y, bb.z, l.z * n.z)));
+    d.w = w;
     const float2 uv = oct_encode(d.w);
     d.uv = uv;
     const float s = uv.x * Rf - 0.5f, t = uv.y * Rf - 0.5f;
@@ -614,6 +622,14 @@ __device__ __forceinline__ DirTerms dir_terms(const float4 l, const float3 tt, c
     d.w01 = (1.f - fu) * fv;
     d.w11 = fu * fv;
     return d;
+}
+
+__device__ __forceinline__ DirTerms dir_terms(const float4 l, const float3 tt, const float3 bb, const float3 n,
+                                              const float Rf, const int R, const int RQ)
+{
+    return footprint_terms(f3(fmaf(l.x, tt.x, fmaf(l.y, bb.x, l.z * n.x)), fmaf(l.x, tt.y, fmaf(l.y, bb.y, l.z * n.y)),
+                              fmaf(l.x, tt.z, fmaf(l.y, bb.z, l.z * n.z))),
+                           Rf, R, RQ);
 }
 
 // Blended occlusion of one direction over a point's K probes (Eq. 5, applied
@@ -845,6 +861,157 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
 }
 
 // ---------------------------------------------------------------------------
+// Query + shade over importance-sampled world directions (Sec. 4.2): the S
+// directions, their octahedral footprints, bilinear weights, environment
+// radiance and 1/pdf are the same for every point, so each CTA tabulates
+// them once in shared memory (48 bytes a direction). Per point and direction
+// there remain the horizon test, the gather of the K probe footprints and,
+// in SHADE mode, the BRDF; terms are weighted by 1/pdf and the estimate is
+// their sum over the directions above the horizon, divided by S.
+// ---------------------------------------------------------------------------
+template <int DT, int KMAX, int MODE>
+__global__ void __launch_bounds__(256, 4) shade_world_kernel(const ShadeK a, const int LANES)
+{
+    extern __shared__ float4 s_tab[];  // [S][3]: (w, 1/pdf), (L_dir, off), (w00, w10, w01, w11)
+    const float Rf = (float)a.R;
+    const int RQ = a.R + 1;
+    for (int i = threadIdx.x; i < a.S; i += blockDim.x) {
+        const float4 l = a.dirs[i];
+        const float3 w = f3(l.x, l.y, l.z);
+        const DirTerms d = footprint_terms(w, Rf, a.R, RQ);
+        const float3 Ld = a.env_layout == SOP_ENV_OCTAHEDRAL ? env_oct_lookup(a.envq, a.He, d.uv)
+                                                             : env_lookup(a.envq, a.He, a.We, w);
+        s_tab[3 * i] = l;
+        s_tab[3 * i + 1] = make_float4(Ld.x, Ld.y, Ld.z, __int_as_float(d.off));
+        s_tab[3 * i + 2] = make_float4(d.w00, d.w10, d.w01, d.w11);
+    }
+    __syncthreads();
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = gid / LANES;
+    const int sub = (int)(gid % LANES);
+    const bool active = m < a.M;
+    const int64_t mm = active ? m : 0;
+    const float3 nr = load3(a.n, mm);
+    const float nl = sqrtf(dot3(nr, nr));
+    const float3 n = f3(nr.x / nl, nr.y / nl, nr.z / nl);
+    const float3 wo = load3(a.wo, mm);
+    int32_t base[KMAX];
+    float W[KMAX];
+    int32_t ids[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const bool on = k < a.K;
+        ids[k] = on ? __ldg(a.idx + mm * a.K + k) : INT32_MAX;
+        W[k] = on ? __ldg(a.w + mm * a.K + k) : 0.f;
+    }
+    if (KMAX <= 8)
+#pragma unroll
+    for (int i = 1; i < KMAX; ++i)
+#pragma unroll
+        for (int j = KMAX - 1; j >= i; --j) {
+            const bool sw = ids[j - 1] > ids[j];
+            const int32_t ti = ids[j - 1];
+            const float tw = W[j - 1];
+            ids[j - 1] = sw ? ids[j] : ids[j - 1];
+            W[j - 1] = sw ? W[j] : W[j - 1];
+            ids[j] = sw ? ti : ids[j];
+            W[j] = sw ? tw : W[j];
+        }
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) base[k] = (k < a.K) ? ids[k] * RQ * RQ : 0;
+    float3 kd, F0;
+    float a2 = 0.f, kk = 0.f, specV = 0.f, NdotV = 1.f;
+    if (MODE == SOP_MODE_SHADE) {
+        const float3 alb = load3(a.albedo, mm);
+        const float r = __ldg(a.rough + mm), mt = __ldg(a.metal + mm);
+        const float dsc = (1.f - mt) * kInvPi;
+        kd = f3(dsc * alb.x, dsc * alb.y, dsc * alb.z);
+        const float f0d = 0.08f * a.specular * (1.f - mt);
+        F0 = f3(f0d + alb.x * mt, f0d + alb.y * mt, f0d + alb.z * mt);
+        const float al = r * r;
+        a2 = al * al;
+        kk = (r + 1.f) * (r + 1.f) * 0.125f;
+        NdotV = fmaxf(dot3(n, wo), 1e-4f);
+        const float G1V = NdotV / (NdotV * (1.f - kk) + kk);
+        specV = G1V / (4.f * NdotV);
+    }
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, den0 = 0.f, den1 = 0.f, den2 = 0.f;
+    for (int i = sub; i < a.S; i += LANES) {
+        const float4 ta = s_tab[3 * i], tb = s_tab[3 * i + 1], tc = s_tab[3 * i + 2];
+        const float3 w = f3(ta.x, ta.y, ta.z);
+        const float NdotL = dot3(n, w);
+        if (!(NdotL > 0.f)) continue;  // below the horizon: no contribution
+        const int off = __float_as_int(tb.w);
+        if (MODE == SOP_MODE_SHADOW) {
+            const float vis = 1.f - shadow_blend<DT, KMAX>(a.quads, base, W, a.K, off, tc.x, tc.y, tc.z, tc.w);
+            const float c = NdotL * ta.w;
+            const float L0 = tb.x * c, L1 = tb.y * c, L2 = tb.z * c;
+            acc0 = fmaf(L0, vis, acc0);
+            acc1 = fmaf(L1, vis, acc1);
+            acc2 = fmaf(L2, vis, acc2);
+            den0 += L0;
+            den1 += L1;
+            den2 += L2;
+        } else {
+            float4 pr = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                if (k < a.K) {
+                    float4 t00, t10, t01, t11;
+                    Quad<DT>::load(a.quads, (int64_t)(base[k] + off), t00, t10, t01, t11);
+                    const float c00 = W[k] * tc.x, c10 = W[k] * tc.y, c01 = W[k] * tc.z, c11 = W[k] * tc.w;
+                    pr.x += c00 * t00.x + c10 * t10.x + c01 * t01.x + c11 * t11.x;
+                    pr.y += c00 * t00.y + c10 * t10.y + c01 * t01.y + c11 * t11.y;
+                    pr.z += c00 * t00.z + c10 * t10.z + c01 * t01.z + c11 * t11.z;
+                    pr.w += c00 * t00.w + c10 * t10.w + c01 * t01.w + c11 * t11.w;
+                }
+            }
+            const float vis = 1.f - pr.w;
+            float3 h = w + wo;
+            const float hl2 = dot3(h, h);
+            h = hl2 > 1e-30f ? rsqrtf(hl2) * h : n;
+            const float NdotH = dot3(n, h), VdotH = dot3(wo, h);
+            const float3 cr = cross3(n, h);
+            const float sin2 = dot3(cr, cr);
+            const float den = NdotH * NdotH * a2 + sin2;
+            const float D = __fdividef(a2, kPi * den * den);
+            const float spec = __fdividef(D * specV, NdotL * (1.f - kk) + kk);
+            const float x1 = 1.f - VdotH, x2 = x1 * x1, fc = x2 * x2 * x1;
+            const float f0 = kd.x + spec * (F0.x + (1.f - F0.x) * fc);
+            const float f1 = kd.y + spec * (F0.y + (1.f - F0.y) * fc);
+            const float f2 = kd.z + spec * (F0.z + (1.f - F0.z) * fc);
+            const float c = NdotL * ta.w;
+            acc0 += f0 * (vis * tb.x + pr.x) * c;
+            acc1 += f1 * (vis * tb.y + pr.y) * c;
+            acc2 += f2 * (vis * tb.z + pr.z) * c;
+        }
+    }
+    for (int o = LANES / 2; o > 0; o >>= 1) {
+        acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+        acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+        acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+        if (MODE == SOP_MODE_SHADOW) {
+            den0 += __shfl_xor_sync(0xffffffffu, den0, o);
+            den1 += __shfl_xor_sync(0xffffffffu, den1, o);
+            den2 += __shfl_xor_sync(0xffffffffu, den2, o);
+        }
+    }
+    if (active && sub == 0) {
+        float* o = a.out + 3 * m;
+        if (MODE == SOP_MODE_SHADE) {
+            const float sc = 1.f / (float)a.S;
+            o[0] = sc * acc0;
+            o[1] = sc * acc1;
+            o[2] = sc * acc2;
+        } else {
+            o[0] = den0 < 1e-20f ? 1.f : acc0 / den0;
+            o[1] = den1 < 1e-20f ? 1.f : acc1 / den1;
+            o[2] = den2 < 1e-20f ? 1.f : acc2 / den2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_hammersley(int32_t S, float* out3, cudaStream_t s)
@@ -910,7 +1077,12 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
                                                       reinterpret_cast<uint2*>(ws + L.quads));
         break;
     }
-    dirs_kernel<<<(a.S + 127) / 128, 128, 0, s>>>(a.S, a.dirs_local, reinterpret_cast<float4*>(ws + L.dirs), nullptr);
+    if (a.dir_world)
+        world_dirs_kernel<<<(a.S + 127) / 128, 128, 0, s>>>(a.S, reinterpret_cast<const float4*>(a.dirs_local),
+                                                            reinterpret_cast<float4*>(ws + L.dirs));
+    else
+        dirs_kernel<<<(a.S + 127) / 128, 128, 0, s>>>(a.S, a.dirs_local, reinterpret_cast<float4*>(ws + L.dirs),
+                                                      nullptr);
     return cudaGetLastError();
 }
 
@@ -966,11 +1138,39 @@ static cudaError_t shade_k(const ShadeK& k, cudaStream_t s)
     return shade_dispatch<DT, 32, MODE>(k, s);
 }
 
-template <int DT>
-static cudaError_t shade_mode(const ShadeK& k, int mode, cudaStream_t s)
+template <int DT, int KMAX, int MODE>
+static cudaError_t shade_world_launch(const ShadeK& k, cudaStream_t s)
 {
+    const int bs = 256, LANES = shade_lanes(DT, k.M);
+    const int64_t threads = k.M * LANES;
+    const unsigned nb = (unsigned)((threads + bs - 1) / bs);
+    const size_t smem = 3 * sizeof(float4) * (size_t)k.S;
+    auto fn = shade_world_kernel<DT, KMAX, MODE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    fn<<<nb, bs, smem, s>>>(k, LANES);
+    return cudaGetLastError();
+}
+
+template <int DT, int MODE>
+static cudaError_t shade_world_k(const ShadeK& k, cudaStream_t s)
+{
+    if (k.K <= 4) return shade_world_launch<DT, 4, MODE>(k, s);
+    if (k.K <= 8) return shade_world_launch<DT, 8, MODE>(k, s);
+    if (k.K <= 16) return shade_world_launch<DT, 16, MODE>(k, s);
+    return shade_world_launch<DT, 32, MODE>(k, s);
+}
+
+template <int DT>
+static cudaError_t shade_mode(const ShadeK& k, int mode, bool world, cudaStream_t s)
+{
+    if (world)
+        return mode == SOP_MODE_SHADE ? shade_world_k<DT, SOP_MODE_SHADE>(k, s) : shade_world_k<DT, SOP_MODE_SHADOW>(k, s);
     return mode == SOP_MODE_SHADE ? shade_k<DT, SOP_MODE_SHADE>(k, s) : shade_k<DT, SOP_MODE_SHADOW>(k, s);
 }
+
 
 cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cudaStream_t s)
 {
@@ -997,9 +1197,9 @@ cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cud
     k.specular = a.specular;
     k.out = a.out;
     switch (a.rgbo_dtype) {
-    case SOP_F32: return shade_mode<SOP_F32>(k, a.mode, s);
-    case SOP_BF16: return shade_mode<SOP_BF16>(k, a.mode, s);
-    case SOP_F16: return shade_mode<SOP_F16>(k, a.mode, s);
+    case SOP_F32: return shade_mode<SOP_F32>(k, a.mode, a.dir_world != 0, s);
+    case SOP_BF16: return shade_mode<SOP_BF16>(k, a.mode, a.dir_world != 0, s);
+    case SOP_F16: return shade_mode<SOP_F16>(k, a.mode, a.dir_world != 0, s);
     default: return cudaErrorInvalidValue;
     }
 }

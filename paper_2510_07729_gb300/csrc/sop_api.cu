@@ -76,6 +76,7 @@ sop_status check_shade(const sop_shade_params* p, int32_t P)
     if (!isfinite(p->specular)) return fail(SOP_ERR_INVALID_ARG, "specular must be finite");
     if (p->env_layout != SOP_ENV_EQUIRECT && p->env_layout != SOP_ENV_OCTAHEDRAL)
         return fail(SOP_ERR_INVALID_ARG, "env_layout = %d is neither EQUIRECT nor OCTAHEDRAL", p->env_layout);
+    if (p->dir_world != 0 && p->dir_world != 1) return fail(SOP_ERR_INVALID_ARG, "dir_world must be 0 or 1");
     return SOP_OK;
 }
 
@@ -156,6 +157,24 @@ sop_status sop_env_to_octahedral(const float* env, int32_t He, int32_t We, float
         return fail(SOP_ERR_INVALID_ARG, "environment size %d x %d invalid", He, We);
     if (H < 2 || H > 4096) return fail(SOP_ERR_INVALID_ARG, "H = %d outside [2, 4096]", H);
     return cuda_status(sop::launch_env_to_oct(env, He, We, out, H, (cudaStream_t)stream), "sop_env_to_octahedral");
+}
+
+size_t sop_env_importance_workspace_bytes(int32_t H)
+{
+    if (H < 2 || H > 2048) return 0;
+    return sop::importance_ws_bytes(H);
+}
+
+sop_status sop_env_importance_dirs(const float* env, int32_t H, int32_t S, float* out, void* ws, size_t ws_bytes,
+                                   void* stream)
+{
+    if (!env || !out) return fail(SOP_ERR_INVALID_ARG, "env or out is NULL");
+    if (H < 2 || H > 2048) return fail(SOP_ERR_INVALID_ARG, "H = %d outside [2, 2048]", H);
+    if (S < 1 || S > 4096) return fail(SOP_ERR_INVALID_ARG, "S = %d outside [1, 4096]", S);
+    sop_status st = check_ws(ws, ws_bytes, sop::importance_ws_bytes(H));
+    if (st != SOP_OK) return st;
+    return cuda_status(sop::launch_importance_dirs(env, H, S, out, (char*)ws, (cudaStream_t)stream),
+                       "sop_env_importance_dirs");
 }
 
 sop_status sop_read_bandwidth_probe(const void* buf, size_t bytes, int32_t reps, float* sink, void* stream)
@@ -294,6 +313,8 @@ static sop_status query_common(const float* x, const float* n, const float* wo, 
     if (params->env_layout == SOP_ENV_OCTAHEDRAL && (He != We || He < 2))
         return fail(SOP_ERR_INVALID_ARG, "an octahedral environment is square, H >= 2 (got %d x %d)", He, We);
     if (!env) return fail(SOP_ERR_INVALID_ARG, "env is NULL");
+    if (params->dir_world && !dirs_local)
+        return fail(SOP_ERR_INVALID_ARG, "dir_world = 1 needs the world directions [S][4] in dirs_local");
     if (M > 0 && (!x || !n || !wo || !albedo || !rough || !metal))
         return fail(SOP_ERR_INVALID_ARG, "a shading-point array is NULL");
     L = sop::query_layout(atlas->P, M, params->K, params->S, He, We, atlas->R, atlas->rgbo_dtype);
@@ -320,6 +341,7 @@ static sop_status query_common(const float* x, const float* n, const float* wo, 
     a.S = params->S;
     a.mode = params->mode;
     a.env_layout = params->env_layout;
+    a.dir_world = params->dir_world;
     a.specular = params->specular;
     const double e = (double)params->eps_snap * 1048576.0;
     a.snap_key = (uint64_t)floor(e * e);
@@ -358,8 +380,9 @@ sop_status sop_query_shade_backward(const float* x, const float* n, const float*
     sop_status st = query_common(x, n, wo, albedo, rough, metal, M, atlas, env, He, We, dirs_local, params, ws,
                                  ws_bytes, a, L);
     if (st != SOP_OK) return st;
-    if (params && params->env_layout != SOP_ENV_EQUIRECT)
-        return fail(SOP_ERR_UNSUPPORTED, "the adjoint takes the equirectangular environment layout only");
+    if (params && (params->env_layout != SOP_ENV_EQUIRECT || params->dir_world))
+        return fail(SOP_ERR_UNSUPPORTED,
+                    "the adjoint takes the equirectangular environment layout and local directions only");
     if (params->mode != SOP_MODE_SHADE)
         return fail(SOP_ERR_UNSUPPORTED, "sop_query_shade_backward: only SOP_MODE_SHADE has an adjoint");
     if (M > 0 && (!grad_out || !g_albedo || !g_rough || !g_metal || !g_normal))
@@ -389,8 +412,9 @@ sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* 
     if (st != SOP_OK) return st;
     st = check_shade(params, atlas->P);
     if (st != SOP_OK) return st;
-    if (params->env_layout != SOP_ENV_EQUIRECT)
-        return fail(SOP_ERR_UNSUPPORTED, "sop_query_shade_noalloc takes the equirectangular environment layout only");
+    if (params->env_layout != SOP_ENV_EQUIRECT || params->dir_world)
+        return fail(SOP_ERR_UNSUPPORTED,
+                    "sop_query_shade_noalloc takes the equirectangular environment layout and local directions only");
     const size_t need = sop::noalloc_required_bytes(atlas->P, params->K, params->S);
     if (atlas->P > SOP_NOALLOC_MAX_PROBES || need > sop::noalloc_scratch_bytes())
         return fail(SOP_ERR_INVALID_ARG,
@@ -424,6 +448,7 @@ sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* 
     a.S = params->S;
     a.mode = params->mode;
     a.env_layout = params->env_layout;
+    a.dir_world = params->dir_world;
     a.specular = params->specular;
     const double e = (double)params->eps_snap * 1048576.0;
     a.snap_key = (uint64_t)floor(e * e);

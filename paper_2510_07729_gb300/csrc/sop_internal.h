@@ -31,7 +31,7 @@ struct QueryArgs {
     const float* env;
     int32_t He, We;
     const float* dirs_local;
-    int32_t K, S, mode, env_layout;
+    int32_t K, S, mode, env_layout, dir_world;
     float specular;
     uint64_t snap_key;
     float* out;
@@ -50,6 +50,8 @@ cudaError_t launch_adjoint(const QueryArgs& a, const QueryLayout& L, char* ws, c
 cudaError_t launch_hammersley(int32_t S, float* out3, cudaStream_t s);
 cudaError_t launch_read_probe(const void* buf, size_t bytes, int32_t reps, float* sink, cudaStream_t s);
 cudaError_t launch_env_to_oct(const float* env, int32_t He, int32_t We, float* out, int32_t H, cudaStream_t s);
+size_t importance_ws_bytes(int32_t H);
+cudaError_t launch_importance_dirs(const float* env, int32_t H, int32_t S, float* out, char* ws, cudaStream_t s);
 
 // SOP texture optimisation pieces (optimize.cu)
 cudaError_t launch_l1_grad(const float* C, const float* Ct, int64_t n, float* grad, float* loss_sum, cudaStream_t s);

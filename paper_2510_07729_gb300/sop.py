@@ -50,7 +50,7 @@ class AdamParams(C.Structure):
 
 class ShadeParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("S", C.c_int32), ("mode", C.c_int32), ("specular", C.c_float),
-                ("eps_snap", C.c_float), ("env_layout", C.c_int32)]
+                ("eps_snap", C.c_float), ("env_layout", C.c_int32), ("dir_world", C.c_int32)]
 
 
 _lib = None
@@ -79,6 +79,9 @@ def load(build_if_missing: bool = True):
     lib.sop_read_bandwidth_probe.argtypes = [vp, sz, i32, vp, vp]
     lib.sop_atlas_pack_rgbo.argtypes = [vp, C.POINTER(AtlasDesc), vp]
     lib.sop_env_to_octahedral.argtypes = [vp, i32, i32, vp, i32, vp]
+    lib.sop_env_importance_workspace_bytes.argtypes = [i32]
+    lib.sop_env_importance_workspace_bytes.restype = sz
+    lib.sop_env_importance_dirs.argtypes = [vp, i32, i32, vp, vp, sz, vp]
     lib.sop_l1_loss_grad.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.sop_adam_l1_step.argtypes = [vp, vp, vp, vp, i64, C.POINTER(AdamParams), vp]
     lib.sop_bake_workspace_bytes.argtypes = [i64, i32, i32]
@@ -114,7 +117,8 @@ def load(build_if_missing: bool = True):
     for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_bake_bin", "sop_bake_trace",
                  "sop_bake_stats", "sop_query_shade",
                  "sop_query_shade_backward", "sop_query_shade_noalloc", "sop_read_bandwidth_probe",
-                 "sop_atlas_pack_rgbo", "sop_l1_loss_grad", "sop_adam_l1_step", "sop_env_to_octahedral"):
+                 "sop_atlas_pack_rgbo", "sop_l1_loss_grad", "sop_adam_l1_step", "sop_env_to_octahedral",
+                 "sop_env_importance_dirs"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -242,6 +246,18 @@ def env_to_octahedral(env, H):
     return out
 
 
+def env_importance_dirs(env_oct, S):
+    """sop_env_importance_dirs: S importance-sampled world directions [S,4]
+    (x, y, z, pdf) from an octahedral environment [H,H,3] (device, float32),
+    for query_shade(..., dirs_world=...)."""
+    H = env_oct.shape[0]
+    lib = load()
+    ws = _ws(int(lib.sop_env_importance_workspace_bytes(H)), env_oct.device)
+    out = torch.empty((S, 4), dtype=torch.float32, device=env_oct.device)
+    _check(lib.sop_env_importance_dirs(_f32(env_oct, (H, H, 3)), H, S, _ptr(out), _ptr(ws), ws.numel(), _stream()))
+    return out
+
+
 def hammersley(S, device="cuda"):
     out = torch.empty((S, 3), dtype=torch.float32, device=device)
     _check(load().sop_hammersley(S, _ptr(out), _stream()))
@@ -366,14 +382,19 @@ def query_workspace_bytes(atlas: Atlas, M, K, S, He, We, mode=MODE_SHADE):
 
 
 def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MODE_SHADE, specular=0.5,
-                eps_snap=1e-6, dirs_local=None, out=None, return_idx=False, workspace=None, env_layout=ENV_EQUIRECT):
+                eps_snap=1e-6, dirs_local=None, out=None, return_idx=False, workspace=None, env_layout=ENV_EQUIRECT,
+                dirs_world=None):
     """SOP query + shade of M points; returns out [M,3] (and idx [M,K] int32,
     W [M,K] float32 when return_idx)."""
     lib = load()
     M = x.shape[0]
     He, We = env.shape[0], env.shape[1]
     dev = x.device
-    sp = ShadeParams(K, S, mode, specular, eps_snap, env_layout)
+    sp = ShadeParams(K, S, mode, specular, eps_snap, env_layout, 0 if dirs_world is None else 1)
+    if dirs_world is not None:
+        dl = _f32(dirs_world, (S, 4))
+    else:
+        dl = None if dirs_local is None else _f32(dirs_local, (S, 3))
     d = atlas.c()
     if out is None:
         out = torch.empty((M, 3), dtype=torch.float32, device=dev)
@@ -385,7 +406,7 @@ def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MO
                    (env, (He, We, 3))):
         _f32(t, shp)
     _check(lib.sop_query_shade(_ptr(x), _ptr(n), _ptr(wo), _ptr(albedo), _ptr(rough), _ptr(metal), M, C.byref(d),
-                               _ptr(env), He, We, None if dirs_local is None else _f32(dirs_local, (S, 3)),
+                               _ptr(env), He, We, dl,
                                C.byref(sp), _ptr(out), _ptr(idx), _ptr(w), _ptr(ws), ws.numel(), _stream()))
     if return_idx:
         return out, idx, w
