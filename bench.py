@@ -395,6 +395,40 @@ def compose_frame_variant(sop, dev, flush, steps, l2_gbs, hbm_gbs, peak_fp32):
                                    "t_l2_ms": round(t_l2 * 1e3, 4), "t_alu_ms": round(t_alu * 1e3, 4),
                                    "frac": round(bound[0] * 1e3 / ms, 4),
                                    "l2_demand_bytes": int(dem), "hbm_bytes": int(hbm), "flop": int(fl)}}
+    # the paper's rendering configuration: the environment as a 512x512
+    # octahedral texture (Sec. 4.1) and S importance-sampled world directions
+    # (Sec. 4.2, Eq. PDF) shared by all points, float32 atlas
+    env_oct = sop.env_to_octahedral(env, 512)
+    dirs = sop.env_importance_dirs(env_oct, S)
+    for p in parts:
+        p["at"] = sop.make_atlas(p["pp"], R)
+        sop.bake(g, p["at"])
+
+    def call_is(p):
+        sop.query_shade(*p["pts"], p["at"], env_oct, K, S, mode=p["mode"], out=p["out"], workspace=p["ws"],
+                        env_layout=sop.ENV_OCTAHEDRAL, dirs_world=dirs)
+
+    for _ in range(3):
+        for p in parts:
+            call_is(p)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for p in parts:
+            call_is(p)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    pd = sum(p["M"] for p in parts) * S
+    res["fp32_octahedral_importance"] = {
+        "env": "octahedral 512x512 resampled from the equirectangular map; S importance-sampled world directions",
+        "frame_ms": round(ms, 4), "point_dirs_per_s": round(pd / (ms * 1e-3), 1),
+        "shadow_mean_vs_hammersley": round(float(parts[1]["out"].mean().item()) /
+                                           float(outs["fp32"][1].mean().item()), 4)}
     num = sum((a - b).abs().sum().item() for a, b in zip(outs["fp16"], outs["fp32"]))
     den = sum(b.abs().sum().item() for b in outs["fp32"])
     res["fp16_rel_l1_vs_fp32_atlas"] = num / den
