@@ -403,6 +403,8 @@ def compose_frame_variant(sop, dev, flush, steps, l2_gbs, hbm_gbs, peak_fp32):
     for p in parts:
         p["at"] = sop.make_atlas(p["pp"], R)
         sop.bake(g, p["at"])
+        p["ws"] = torch.empty(sop.query_workspace_bytes(p["at"], p["M"], K, S, 512, 512, p["mode"]),
+                              dtype=torch.uint8, device=dev)
 
     def call_is(p):
         sop.query_shade(*p["pts"], p["at"], env_oct, K, S, mode=p["mode"], out=p["out"], workspace=p["ws"],
