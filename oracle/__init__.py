@@ -173,12 +173,31 @@ def snap_key_for(eps_snap=1e-6):
     return int(np.floor((eps_snap * 1048576.0) ** 2))
 
 
-def knn(x, probe_pos, K):
+UNBOUNDED = (1 << 64) - 1
+
+
+def radius_key(radius=0.0):
+    """Search radius (Sec. 3.2, fixed-radius neighbours) as a bound on the
+    quantised squared distance: a probe takes part when its key is at most
+    (r 2^20)^2, i.e. when its quantised distance is at most r; radius 0 is
+    no bound. r is taken as float32; (r 2^20)^2 has at most 48 significant
+    bits, so the double product is exact and its floor is the bound."""
+    r = float(np.float32(radius))
+    if r == 0.0:
+        return UNBOUNDED
+    rq = r * 1048576.0
+    return int(np.floor(rq * rq))
+
+
+def knn(x, probe_pos, K, radius=0.0):
+    """K nearest probes (within the radius, if one is given): idx [M,K] with
+    -1 in empty slots, key [M,K] (UINT64_MAX there)."""
     x, pp = _f32(x), _f32(probe_pos)
     M = len(x)
     idx = np.empty((M, K), np.int32)
     key = np.empty((M, K), np.uint64)
-    lib().orc_knn(C.c_int64(M), _p(x), C.c_int32(len(pp)), _p(pp), C.c_int32(K), _p(idx), _p(key))
+    lib().orc_knn(C.c_int64(M), _p(x), C.c_int32(len(pp)), _p(pp), C.c_int32(K), C.c_uint64(radius_key(radius)),
+                  _p(idx), _p(key))
     return idx, key
 
 
@@ -195,10 +214,13 @@ def weights(x, n, probe_pos, idx, key, snap_key=None):
 
 
 def query_shade(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S,
-                mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, env_layout=ENV_EQUIRECT, dir_world=False):
+                mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, env_layout=ENV_EQUIRECT, dir_world=False,
+                radius=0.0):
     """FP64 query + shade. Returns out [M,3], idx [M,K], W [M,K]. dirs: the
     local direction set [S,3] (None: the centred Hammersley set), or with
-    dir_world the importance-sampled world directions [S,4] (x, y, z, pdf)."""
+    dir_world the importance-sampled world directions [S,4] (x, y, z, pdf).
+    radius > 0 limits the neighbours to probes within it (idx -1, W 0 in
+    the slots it leaves empty)."""
     x, n, wo, albedo, rough, metal = (_f32(v) for v in (x, n, wo, albedo, rough, metal))
     pp, mr, mo, env = _f32(probe_pos), _f32(maps_rgb), _f32(maps_occ), _f32(env)
     P, R = mr.shape[0], mr.shape[1]
@@ -212,8 +234,8 @@ def query_shade(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, e
     lib().orc_query_shade(C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal),
                           C.c_int32(P), _p(pp), C.c_int32(R), _p(mr), _p(mo), C.c_int32(He), C.c_int32(We),
                           _p(env), C.c_int32(S), None if dp is None else _p(dp), C.c_int32(K),
-                          C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_int32(env_layout),
-                          C.c_int32(1 if dir_world else 0), _p(out), _p(idx), _p(W))
+                          C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_uint64(radius_key(radius)),
+                          C.c_int32(env_layout), C.c_int32(1 if dir_world else 0), _p(out), _p(idx), _p(W))
     return out, idx, W
 
 
@@ -224,7 +246,7 @@ FP32_DIR_EPS = 2e-6
 
 def query_shade_sensitivity(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S,
                             mode=MODE_SHADE, spec=0.5, dirs=None, snap_key=None, eps=FP32_DIR_EPS,
-                            env_layout=ENV_EQUIRECT, dir_world=False):
+                            env_layout=ENV_EQUIRECT, dir_world=False, radius=0.0):
     """Per-output allowance [M,3] for an FP32 evaluation (see the C docs)."""
     x, n, wo, albedo, rough, metal = (_f32(v) for v in (x, n, wo, albedo, rough, metal))
     pp, mr, mo, env = _f32(probe_pos), _f32(maps_rgb), _f32(maps_occ), _f32(env)
@@ -237,8 +259,8 @@ def query_shade_sensitivity(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb,
     lib().orc_query_shade_sensitivity(
         C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal), C.c_int32(P), _p(pp), C.c_int32(R),
         _p(mr), _p(mo), C.c_int32(He), C.c_int32(We), _p(env), C.c_int32(S), None if dp is None else _p(dp),
-        C.c_int32(K), C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_int32(env_layout),
-        C.c_int32(1 if dir_world else 0), C.c_double(eps), _p(kap))
+        C.c_int32(K), C.c_int32(mode), C.c_double(spec), C.c_uint64(sk), C.c_uint64(radius_key(radius)),
+        C.c_int32(env_layout), C.c_int32(1 if dir_world else 0), C.c_double(eps), _p(kap))
     return kap
 
 
@@ -272,7 +294,7 @@ def env_oct_lookup(env, w):
 
 
 def query_shade_grad(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_occ, env, K, S, grad_out,
-                     spec=0.5, dirs=None, snap_key=None):
+                     spec=0.5, dirs=None, snap_key=None, radius=0.0):
     """Analytic FP64 gradients of sum(grad_out * C) (SHADE mode). Returns a
     dict: albedo [M,3], rough [M], metal [M], normal [M,3] (w.r.t. the raw
     normal), env [He,We,3], maps_rgb [P,R,R,3], maps_occ [P,R,R], and the
@@ -292,7 +314,7 @@ def query_shade_grad(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_o
     lib().orc_query_shade_grad(
         C.c_int64(M), _p(x), _p(n), _p(wo), _p(albedo), _p(rough), _p(metal), C.c_int32(P), _p(pp), C.c_int32(R),
         _p(mr), _p(mo), C.c_int32(He), C.c_int32(We), _p(env), C.c_int32(S), None if dp is None else _p(dp),
-        C.c_int32(K), C.c_double(spec), C.c_uint64(sk), _p(go), _p(out["albedo"]), _p(out["rough"]),
+        C.c_int32(K), C.c_double(spec), C.c_uint64(sk), C.c_uint64(radius_key(radius)), _p(go), _p(out["albedo"]), _p(out["rough"]),
         _p(out["metal"]), _p(out["normal"]), _p(out["env"]), _p(out["maps_rgb"]), _p(out["maps_occ"]),
         _p(out["abs_albedo"]), _p(out["abs_rough"]), _p(out["abs_metal"]), _p(out["abs_normal"]))
     return out

@@ -267,8 +267,11 @@ void orc_bake_rays(int64_t N, const float* mean, const float* scale, const float
 static int64_t quantise(float v) { return (int64_t)nearbyint((double)v * 1048576.0); }
 
 /* Exact K nearest probes of each point, by the integer squared distance of
- * positions quantised to 2^-20, ties to the lower probe index. */
-void orc_knn(int64_t M, const float* x, int32_t P, const float* probe_pos, int32_t K,
+ * positions quantised to 2^-20, ties to the lower probe index. With a
+ * search radius (Sec. 3.2, fixed-radius neighbours) only probes whose key is
+ * <= r2_key take part; slots left empty hold index -1 and key UINT64_MAX.
+ * r2_key = UINT64_MAX is the plain K nearest. */
+void orc_knn(int64_t M, const float* x, int32_t P, const float* probe_pos, int32_t K, uint64_t r2_key,
              int32_t* out_idx, uint64_t* out_key)
 {
 #pragma omp parallel for schedule(static)
@@ -282,6 +285,7 @@ void orc_knn(int64_t M, const float* x, int32_t P, const float* probe_pos, int32
             int64_t dy = quantise(probe_pos[3 * p + 1]) - qy;
             int64_t dz = quantise(probe_pos[3 * p + 2]) - qz;
             uint64_t key = (uint64_t)(dx * dx) + (uint64_t)(dy * dy) + (uint64_t)(dz * dz);
+            if (key > r2_key) continue;
             /* insertion into the sorted list of the best K (key, index) */
             if (n == K && key >= bk[K - 1]) continue; /* equal key: larger index loses */
             int pos = (n < K) ? n++ : K - 1;
@@ -293,18 +297,28 @@ void orc_knn(int64_t M, const float* x, int32_t P, const float* probe_pos, int32
             bk[pos] = key;
             bi[pos] = p;
         }
+        for (int k = n; k < K; ++k) {
+            bi[k] = -1;
+            bk[k] = UINT64_MAX;
+        }
     }
 }
 
 /* Normalised blend weights W_k = w_s w_b / sum_j w_s w_b (Eq. 4-6) for the
  * neighbours found by orc_knn. When the nearest probe's quantised squared
- * distance is <= snap_key the point sits on that probe: W is one-hot. */
+ * distance is <= snap_key the point sits on that probe: W is one-hot. Empty
+ * slots (index -1) weigh 0; with no neighbour at all every W is 0. */
 void orc_weights(int64_t M, const float* x, const float* n, const float* probe_pos, int32_t K,
                  const int32_t* idx, const uint64_t* key, uint64_t snap_key, double* out_w)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t m = 0; m < M; ++m) {
         double* W = out_w + (size_t)m * K;
+        const int32_t* id = idx + (size_t)m * K;
+        if (id[0] < 0) {
+            for (int k = 0; k < K; ++k) W[k] = 0.0;
+            continue;
+        }
         if (key[(size_t)m * K] <= snap_key) {
             for (int k = 0; k < K; ++k) W[k] = (k == 0) ? 1.0 : 0.0;
             continue;
@@ -313,7 +327,9 @@ void orc_weights(int64_t M, const float* x, const float* n, const float* probe_p
         double nl = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
         double sum = 0.0;
         for (int k = 0; k < K; ++k) {
-            const float* p = probe_pos + 3 * (size_t)idx[(size_t)m * K + k];
+            W[k] = 0.0;
+            if (id[k] < 0) continue;
+            const float* p = probe_pos + 3 * (size_t)id[k];
             double d[3] = {(double)p[0] - x[3 * m], (double)p[1] - x[3 * m + 1], (double)p[2] - x[3 * m + 2]};
             double dl = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             double ws = 1.0 / dl;
@@ -547,6 +563,7 @@ static void sample_terms(const double* nn, const double* vo, const double* a, do
     orc_oct_encode(w, uv);
     double O = 0.0, Lin[3] = {0, 0, 0};
     for (int k = 0; k < K; ++k) {
+        if (idx[k] < 0) continue;
         double o1, l3[3];
         orc_oct_bilerp(mocc + RR * idx[k], R, 1, uv, &o1);
         orc_oct_bilerp(mrgb + 3 * RR * idx[k], R, 3, uv, l3);
@@ -570,8 +587,8 @@ static void sample_terms(const double* nn, const double* vo, const double* a, do
 
 static void query_setup(int64_t M, const float* x, const float* n, int32_t P, const float* probe_pos, int32_t R,
                         const float* maps_rgb, const float* maps_occ, int32_t S, const double* dirs, int32_t dir_world,
-                        int32_t K, uint64_t snap_key, int32_t* out_idx, double* out_w, double** dl, double** mrgb,
-                        double** mocc)
+                        int32_t K, uint64_t snap_key, uint64_t r2_key, int32_t* out_idx, double* out_w, double** dl,
+                        double** mrgb, double** mocc)
 {
     const size_t st = dir_world ? 4 : 3;
     *dl = (double*)malloc(sizeof(double) * st * (size_t)S);
@@ -583,7 +600,7 @@ static void query_setup(int64_t M, const float* x, const float* n, int32_t P, co
     for (size_t i = 0; i < 3 * RR * (size_t)P; ++i) (*mrgb)[i] = maps_rgb[i];
     for (size_t i = 0; i < RR * (size_t)P; ++i) (*mocc)[i] = maps_occ[i];
     uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(M > 0 ? M : 1) * K);
-    orc_knn(M, x, P, probe_pos, K, out_idx, key);
+    orc_knn(M, x, P, probe_pos, K, r2_key, out_idx, key);
     orc_weights(M, x, n, probe_pos, K, out_idx, key, snap_key, out_w);
     free(key);
 }
@@ -627,11 +644,12 @@ void orc_query_shade(int64_t M, const float* x, const float* n, const float* wo,
                      const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
                      const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We, const float* env,
                      int32_t S, const double* dirs, int32_t K, int32_t mode, double spec, uint64_t snap_key,
-                     int32_t env_layout, int32_t dir_world, double* out, int32_t* out_idx, double* out_w)
+                     uint64_t r2_key, int32_t env_layout, int32_t dir_world, double* out, int32_t* out_idx,
+                     double* out_w)
 {
     double *dl, *mrgb, *mocc;
-    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, dir_world, K, snap_key, out_idx, out_w, &dl,
-                &mrgb, &mocc);
+    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, dir_world, K, snap_key, r2_key, out_idx, out_w,
+                &dl, &mrgb, &mocc);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t m = 0; m < M; ++m) {
         double nn[3], vo[3], a[3], t[3], b[3];
@@ -668,13 +686,14 @@ void orc_query_shade_sensitivity(int64_t M, const float* x, const float* n, cons
                                  const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
                                  const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We,
                                  const float* env, int32_t S, const double* dirs, int32_t K, int32_t mode, double spec,
-                                 uint64_t snap_key, int32_t env_layout, int32_t dir_world, double eps, double* kappa)
+                                 uint64_t snap_key, uint64_t r2_key, int32_t env_layout, int32_t dir_world, double eps,
+                                 double* kappa)
 {
     int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1) * K);
     double* W = (double*)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1) * K);
     double *dl, *mrgb, *mocc;
-    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, dir_world, K, snap_key, idx, W, &dl, &mrgb,
-                &mocc);
+    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, dir_world, K, snap_key, r2_key, idx, W, &dl,
+                &mrgb, &mocc);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t m = 0; m < M; ++m) {
         double nn[3], vo[3], a[3], t[3], b[3];
@@ -832,7 +851,7 @@ static void env_grad(const float* env, int32_t He, int32_t We, const double* w, 
 void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float* wo, const float* albedo,
                           const float* rough, const float* metal, int32_t P, const float* probe_pos, int32_t R,
                           const float* maps_rgb, const float* maps_occ, int32_t He, int32_t We, const float* env,
-                          int32_t S, const double* dirs, int32_t K, double spec, uint64_t snap_key,
+                          int32_t S, const double* dirs, int32_t K, double spec, uint64_t snap_key, uint64_t r2_key,
                           const double* grad_out, double* g_albedo, double* g_rough, double* g_metal,
                           double* g_normal, double* g_env, double* g_maps_rgb, double* g_maps_occ,
                           double* abs_albedo, double* abs_rough, double* abs_metal, double* abs_normal)
@@ -841,8 +860,9 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
     double* W = (double*)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1) * K);
     uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(M > 0 ? M : 1) * K);
     double *dl, *mrgb, *mocc;
-    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, 0, K, snap_key, idx, W, &dl, &mrgb, &mocc);
-    orc_knn(M, x, P, probe_pos, K, idx, key);
+    query_setup(M, x, n, P, probe_pos, R, maps_rgb, maps_occ, S, dirs, 0, K, snap_key, r2_key, idx, W, &dl, &mrgb,
+                &mocc);
+    orc_knn(M, x, P, probe_pos, K, r2_key, idx, key);
     size_t RR = (size_t)R * R;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t m = 0; m < M; ++m) {
@@ -876,6 +896,7 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
             double ok[32], lk[32][3], dok[32][2], dlk[32][6], wto[32][4];
             int txo[32][4];
             for (int k = 0; k < K; ++k) {
+                if (id[k] < 0) continue; /* empty slot of a radius search */
                 double wt[4];
                 int tx[4];
                 bilerp_grad(mocc + RR * id[k], R, 1, uv, &ok[k], dok[k], tx, wt);
@@ -945,6 +966,7 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
             }
             /* texel scatter and weight gradients */
             for (int k = 0; k < K; ++k) {
+                if (id[k] < 0) continue;
                 gW[k] += gOt * ok[k] + gLin[0] * lk[k][0] + gLin[1] * lk[k][1] + gLin[2] * lk[k][2];
                 for (int q = 0; q < 4; ++q) {
                     size_t tix = RR * id[k] + txo[k][q];
@@ -999,9 +1021,12 @@ void orc_query_shade_grad(int64_t M, const float* x, const float* n, const float
             sn += sqrt(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
         }
         /* blend weights W_k = w_s w_b / sum (Eq. 4-6): w_b moves with n */
-        if (key[(size_t)m * K] > snap_key) {
+        if (id[0] >= 0 && key[(size_t)m * K] > snap_key) {
             double u[32], U = 0, ws[32], dh[32][3];
             for (int k = 0; k < K; ++k) {
+                u[k] = ws[k] = 0.0;
+                for (int j = 0; j < 3; ++j) dh[k][j] = 0.0;
+                if (id[k] < 0) continue;
                 const float* p = probe_pos + 3 * (size_t)id[k];
                 double d[3] = {(double)p[0] - x[3 * m], (double)p[1] - x[3 * m + 1], (double)p[2] - x[3 * m + 2]};
                 double dlen = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
