@@ -233,6 +233,44 @@ def env_oct_variant(sop, atlas, pargs, env, K, S, mode, out_ref, flush, steps, H
             "query_point_dirs_per_s": round(M * S / (ms * 1e-3), 1), "rel_l1_vs_equirect": rel}
 
 
+def frnn_variant(sop, atlas, pargs, env, K, S, mode, out_ref, flush, steps, ppos):
+    """The query with the fixed-radius neighbour search (Sec. 3.2; the paper
+    does not give its radius): the radius is the median distance of the 4th
+    nearest probe over 512 evenly spaced points, so a point keeps from one
+    to K probes. Time, mean number of neighbours and relative L1 difference
+    from the plain K nearest (a different blend, not an error)."""
+    import torch
+    x = pargs[0]
+    M = x.shape[0]
+    sub = x[torch.linspace(0, M - 1, 512, device=x.device).long()]
+    d = torch.cdist(sub.double(), ppos.double()).sort(dim=1).values[:, 3]
+    radius = float(np.float32(d.median().item()))
+    out = torch.empty((M, 3), dtype=torch.float32, device=x.device)
+    ws = torch.empty(sop.query_workspace_bytes(atlas, M, K, S, env.shape[0], env.shape[1], mode), dtype=torch.uint8,
+                     device=x.device)
+    _, idx, _ = sop.query_shade(*pargs, atlas, env, K, S, mode=mode, return_idx=True, radius=radius)
+    n_mean = (idx >= 0).float().sum(1).mean().item()
+
+    def call():
+        sop.query_shade(*pargs, atlas, env, K, S, mode=mode, out=out, workspace=ws, radius=radius)
+
+    for _ in range(3):
+        call()
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts))
+    rel = ((out - out_ref).abs().sum() / out_ref.abs().sum()).item()
+    return {"radius": radius, "neighbours_mean": round(n_mean, 3), "query_ms": round(ms, 4),
+            "query_point_dirs_per_s": round(M * S / (ms * 1e-3), 1), "rel_l1_vs_knn": rel}
+
+
 def surrogate_variant(sop, dev, flush, steps, n_scenes=25, train_steps=20000):
     """The learned rebake after the object's first ellipsoid moves: train on
     bakes of random scenes (untimed), then time the rebake of the moved
@@ -610,10 +648,11 @@ def main():
                   "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
         if roof is None:
             roof = roof_q
-    chosen = surr = comp = optim = envoct = None
+    chosen = surr = comp = optim = envoct = frnn = None
     if do_query and args.part == "step":
         chosen = chosen_variant(sop, g, ppos, R, pargs, env, K, S, mode, out, flush, args.steps)
         envoct = env_oct_variant(sop, atlas, pargs, env, K, S, mode, out, flush, args.steps)
+        frnn = frnn_variant(sop, atlas, pargs, env, K, S, mode, out, flush, args.steps, ppos)
         if not args.no_surrogate and args.workload == "object":
             surr = surrogate_variant(sop, dev, flush, args.steps)
         if not args.no_optimize and args.workload == "object":
@@ -651,6 +690,7 @@ def main():
         "chosen": chosen,
         "chosen_bake": surr,
         "env_octahedral": envoct,
+        "frnn_query": frnn,
         "compose_frame_query": comp,
         "optimize_step": optim,
         "e2e": e2e,

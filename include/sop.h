@@ -131,7 +131,15 @@ typedef struct {
  * sop_env_importance_dirs writes them, shared by every point, and the
  * estimator is 1/S sum over the directions above the point's horizon of the
  * terms divided by pdf (Sec. 4.2); the adjoint and the allocation-free entry
- * point take dir_world = 0 only. */
+ * point take dir_world = 0 only. radius = the fixed-radius neighbour search
+ * of Sec. 3.2 (0, what zero-initialised callers get: no radius, the plain K
+ * nearest): a point's neighbours are then the at most K nearest probes whose
+ * quantised distance (positions rounded to multiples of 2^-20) is <= radius,
+ * i.e. whose integer squared distance is <= floor((radius 2^20)^2); slots
+ * left empty get index -1 and weight 0 in out_idx/out_w, the weights are
+ * normalised over the probes found, and a point with none gets O = 0 and
+ * L_in = 0 (the environment term alone). 0 <= radius <= 2048 (positions lie
+ * within +-1024); every entry point, the adjoint included, takes it. */
 #define SOP_ENV_EQUIRECT 0
 #define SOP_ENV_OCTAHEDRAL 1
 typedef struct {
@@ -142,6 +150,7 @@ typedef struct {
     float eps_snap;
     int32_t env_layout;
     int32_t dir_world;
+    float radius;
 } sop_shade_params;
 
 /* Message for the last non-OK status returned to the calling thread

@@ -204,7 +204,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
         // ---- scatter: probe texels (folded through the border rule) and env ----
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            if (k < a.K) {
+            // a zero weight (an empty slot of a radius search, or a probe
+            // other than the one a snapped point sits on) scatters nothing
+            if (k < a.K && W[k] != 0.f) {
                 gW[k] += gO * tk[k].w + gLin[0] * tk[k].x + gLin[1] * tk[k].y + gLin[2] * tk[k].z;
                 const float Wk = W[k];
                 const float q[4] = {w00, w10, w01, w11};
@@ -273,8 +275,11 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
             gn[j] += v;
         }
     }
-    // blend weights W_k = w_s w_b / sum (Eq. 5-6): w_b moves with the normal;
-    // a point sitting on its nearest probe has a one-hot W (no dependence)
+    // blend weights W_k = w_s w_b / sum (Eq. 5-6) over the probes found (the
+    // nonzero W: a found probe's weight is at least 0.01 w_s / sum): w_b moves
+    // with the normal. A one-hot W (a point sitting on its nearest probe, or
+    // a radius search that found one probe) and an all-zero one (none found)
+    // do not depend on it; then W[1] == 0.
     const bool snapped = a.K > 1 && W[1] == 0.f;
     if (a.K > 1 && !snapped) {
         const float3 xp = load3(a.x, m);
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
         for (int k = 0; k < KMAX; ++k) {
             ws[k] = 0.f;
             dh[k] = f3(0.f, 0.f, 0.f);
-            if (k < a.K) {
+            if (k < a.K && W[k] != 0.f) {
                 const float3 d = load3(a.probe_pos, pid[k]) - xp;
                 const float dl = sqrtf(dot3(d, d));
                 ws[k] = 1.f / dl;
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
         }
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            if (k < a.K) {
+            if (k < a.K && W[k] != 0.f) {
                 const float gu = (gW[k] - gdot) / U;
                 gn[0] += gu * ws[k] * 0.5f * dh[k].x;
                 gn[1] += gu * ws[k] * 0.5f * dh[k].y;

@@ -227,7 +227,8 @@ __device__ __forceinline__ uint64_t unsearched_bound2(const ProbeGrid& G, const 
 // ---------------------------------------------------------------------------
 template <int KMAX>
 __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float* __restrict__ x, const float* __restrict__ nrm, int64_t M,
-                                                   int32_t K, uint64_t snap_key, const ProbeGrid* __restrict__ gridp,
+                                                   int32_t K, uint64_t snap_key, uint64_t r2_key,
+                                                   const ProbeGrid* __restrict__ gridp,
                                                    const int32_t* __restrict__ cell_start,
                                                    const int4* __restrict__ entries,
                                                    const float* __restrict__ probe_pos, int32_t* __restrict__ ws_idx,
@@ -267,9 +268,10 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
                         const int4 en = __ldg(entries + e);
                         const uint64_t key = qdist2(en.x, en.y, en.z, q);
                         const int32_t id = en.w;
-                        // keep the KMAX best (key, id) pairs sorted; the first K
-                        // of them are the K nearest
-                        const bool better = key < bk[KMAX - 1] || (key == bk[KMAX - 1] && id < bi[KMAX - 1]);
+                        // keep the KMAX best (key, id) pairs within the radius
+                        // sorted; the first K of them are the K nearest
+                        const bool better = key <= r2_key &&
+                                            (key < bk[KMAX - 1] || (key == bk[KMAX - 1] && id < bi[KMAX - 1]));
                         if (!better) continue;
                         // insert: every kept pair above the new one moves up a slot
                         bool lt[KMAX];
@@ -285,13 +287,14 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
                     }
                 }
             }
-        // stop once no probe outside ring r can enter the best K
+        // stop once no probe outside ring r can enter the best K, nor lie
+        // within the radius
         uint64_t kth = bk[0];
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
             if (k == K - 1) kth = bk[k];
         const uint64_t bnd = unsearched_bound2(G, q, c, r);
-        if (bnd == UINT64_MAX || kth < bnd) break;
+        if (bnd == UINT64_MAX || kth < bnd || r2_key < bnd) break;
     }
     // weights (Eq. 4-6)
     const float3 nr = load3(nrm, m);
@@ -299,11 +302,14 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
     const float3 nn = f3(nr.x / nl, nr.y / nl, nr.z / nl);
     float w[KMAX];
     float wsum = 0.f;
-    const bool snap = bk[0] <= snap_key;
+    // slots a radius search left empty keep bi = INT32_MAX: weight 0, and the
+    // shading reads (with weight 0) the nearest probe found, or probe 0
+    const bool snap = bi[0] != INT32_MAX && bk[0] <= snap_key;
+    const int32_t fill = bi[0] != INT32_MAX ? bi[0] : 0;
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
         w[k] = 0.f;
-        if (k < K) {
+        if (k < K && bi[k] != INT32_MAX) {
             const float3 pk = load3(probe_pos, bi[k]);
             const float3 d = pk - xp;
             const float dl = sqrtf(dot3(d, d));
@@ -316,10 +322,11 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
         if (k < K) {
-            const float wk = snap ? w[k] : w[k] / wsum;
-            ws_idx[m * K + k] = bi[k];
+            const bool found = bi[k] != INT32_MAX;
+            const float wk = (snap || !found) ? w[k] : w[k] / wsum;
+            ws_idx[m * K + k] = found ? bi[k] : fill;
             ws_w[m * K + k] = wk;
-            if (user_idx) user_idx[m * K + k] = bi[k];
+            if (user_idx) user_idx[m * K + k] = found ? bi[k] : -1;
             if (user_w) user_w[m * K + k] = wk;
         }
 }
@@ -1033,7 +1040,8 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
         const int bs = 128;
         const unsigned nb = (unsigned)((a.M + bs - 1) / bs);
 #define SOP_KNN(KM) \
-    knn_kernel<KM><<<nb, bs, 0, s>>>(a.x, a.n, a.M, a.K, a.snap_key, grid, cstart, ent, a.probe_pos, idx, w, a.out_idx, a.out_w)
+    knn_kernel<KM><<<nb, bs, 0, s>>>(a.x, a.n, a.M, a.K, a.snap_key, a.r2_key, grid, cstart, ent, a.probe_pos, idx, w, \
+                                     a.out_idx, a.out_w)
         if (a.K <= 4) SOP_KNN(4);
         else if (a.K <= 8) SOP_KNN(8);
         else if (a.K <= 16) SOP_KNN(16);
@@ -1856,8 +1864,8 @@ cudaError_t launch_query_noalloc(const QueryArgs& a, cudaStream_t s)
         int32_t* uidx = a.out_idx ? a.out_idx + m0 * a.K : nullptr;
         float* uw = a.out_w ? a.out_w + m0 * a.K : nullptr;
 #define SOP_KNN_NA(KM)                                                                                             \
-    knn_kernel<KM><<<nb, 128, 0, s>>>(a.x + 3 * m0, a.n + 3 * m0, mc, a.K, a.snap_key, grid, cstart, ent, a.probe_pos, \
-                                      idx, w, uidx, uw)
+    knn_kernel<KM><<<nb, 128, 0, s>>>(a.x + 3 * m0, a.n + 3 * m0, mc, a.K, a.snap_key, a.r2_key, grid, cstart, ent, \
+                                      a.probe_pos, idx, w, uidx, uw)
         if (a.K <= 4) SOP_KNN_NA(4);
         else if (a.K <= 8) SOP_KNN_NA(8);
         else if (a.K <= 16) SOP_KNN_NA(16);

@@ -77,7 +77,19 @@ sop_status check_shade(const sop_shade_params* p, int32_t P)
     if (p->env_layout != SOP_ENV_EQUIRECT && p->env_layout != SOP_ENV_OCTAHEDRAL)
         return fail(SOP_ERR_INVALID_ARG, "env_layout = %d is neither EQUIRECT nor OCTAHEDRAL", p->env_layout);
     if (p->dir_world != 0 && p->dir_world != 1) return fail(SOP_ERR_INVALID_ARG, "dir_world must be 0 or 1");
+    if (!(p->radius >= 0.f && p->radius <= 2048.f))
+        return fail(SOP_ERR_INVALID_ARG, "radius = %g outside [0, 2048]", (double)p->radius);
     return SOP_OK;
+}
+
+// Largest integer squared distance (units of 2^-40) within a search radius:
+// (radius 2^20)^2 has at most 48 significant bits, so the double square is
+// exact and its floor is the bound. Radius 0 means no bound.
+uint64_t radius_key(float radius)
+{
+    if (radius == 0.f) return UINT64_MAX;
+    const double r = (double)radius * 1048576.0;
+    return (uint64_t)floor(r * r);
 }
 
 }  // namespace
@@ -345,6 +357,7 @@ static sop_status query_common(const float* x, const float* n, const float* wo, 
     a.specular = params->specular;
     const double e = (double)params->eps_snap * 1048576.0;
     a.snap_key = (uint64_t)floor(e * e);
+    a.r2_key = radius_key(params->radius);
     return SOP_OK;
 }
 
@@ -452,6 +465,7 @@ sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* 
     a.specular = params->specular;
     const double e = (double)params->eps_snap * 1048576.0;
     a.snap_key = (uint64_t)floor(e * e);
+    a.r2_key = radius_key(params->radius);
     a.out = out;
     a.out_idx = out_idx;
     a.out_w = out_w;

@@ -34,6 +34,7 @@ struct QueryArgs {
     int32_t K, S, mode, env_layout, dir_world;
     float specular;
     uint64_t snap_key;
+    uint64_t r2_key;  // fixed-radius search: keys above it are not neighbours (UINT64_MAX: no radius)
     float* out;
     int32_t* out_idx;
     float* out_w;

@@ -50,7 +50,7 @@ class AdamParams(C.Structure):
 
 class ShadeParams(C.Structure):
     _fields_ = [("K", C.c_int32), ("S", C.c_int32), ("mode", C.c_int32), ("specular", C.c_float),
-                ("eps_snap", C.c_float), ("env_layout", C.c_int32), ("dir_world", C.c_int32)]
+                ("eps_snap", C.c_float), ("env_layout", C.c_int32), ("dir_world", C.c_int32), ("radius", C.c_float)]
 
 
 _lib = None
@@ -383,14 +383,15 @@ def query_workspace_bytes(atlas: Atlas, M, K, S, He, We, mode=MODE_SHADE):
 
 def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MODE_SHADE, specular=0.5,
                 eps_snap=1e-6, dirs_local=None, out=None, return_idx=False, workspace=None, env_layout=ENV_EQUIRECT,
-                dirs_world=None):
+                dirs_world=None, radius=0.0):
     """SOP query + shade of M points; returns out [M,3] (and idx [M,K] int32,
-    W [M,K] float32 when return_idx)."""
+    W [M,K] float32 when return_idx). radius > 0: fixed-radius neighbours
+    (at most K probes within it; idx -1 and W 0 in the empty slots)."""
     lib = load()
     M = x.shape[0]
     He, We = env.shape[0], env.shape[1]
     dev = x.device
-    sp = ShadeParams(K, S, mode, specular, eps_snap, env_layout, 0 if dirs_world is None else 1)
+    sp = ShadeParams(K, S, mode, specular, eps_snap, env_layout, 0 if dirs_world is None else 1, radius)
     if dirs_world is not None:
         dl = _f32(dirs_world, (S, 4))
     else:
@@ -414,7 +415,7 @@ def query_shade(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MO
 
 
 def query_shade_backward(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, grad_out, g_env=None, g_maps=None,
-                         specular=0.5, eps_snap=1e-6, dirs_local=None, workspace=None):
+                         specular=0.5, eps_snap=1e-6, dirs_local=None, workspace=None, radius=0.0):
     """sop_query_shade_backward (SHADE mode). Returns a dict of gradients:
     albedo, rough, metal, normal (fresh tensors) and env [He,We,3], maps
     [P,R,R,4] (accumulated into g_env / g_maps when given, else zeros)."""
@@ -423,7 +424,7 @@ def query_shade_backward(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S
     He, We = env.shape[0], env.shape[1]
     dev = x.device
     P, R = atlas.P, atlas.R
-    sp = ShadeParams(K, S, MODE_SHADE, specular, eps_snap)
+    sp = ShadeParams(K, S, MODE_SHADE, specular, eps_snap, ENV_EQUIRECT, 0, radius)
     d = atlas.c()
     g = dict(albedo=torch.empty((M, 3), dtype=torch.float32, device=dev),
              rough=torch.empty((M,), dtype=torch.float32, device=dev),
@@ -470,7 +471,7 @@ class SopQueryShade(torch.autograd.Function):
 
 
 def query_shade_noalloc(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S, mode=MODE_SHADE, specular=0.5,
-                        eps_snap=1e-6, dirs_local=None, out=None, return_idx=False):
+                        eps_snap=1e-6, dirs_local=None, out=None, return_idx=False, radius=0.0):
     """sop_query_shade_noalloc: the same query + shade without a workspace,
     for callers that cannot allocate device memory (the library's fixed
     scratch array is used instead; see include/sop.h)."""
@@ -478,7 +479,7 @@ def query_shade_noalloc(x, n, wo, albedo, rough, metal, atlas: Atlas, env, K, S,
     M = x.shape[0]
     He, We = env.shape[0], env.shape[1]
     dev = x.device
-    sp = ShadeParams(K, S, mode, specular, eps_snap)
+    sp = ShadeParams(K, S, mode, specular, eps_snap, ENV_EQUIRECT, 0, radius)
     d = atlas.c()
     if out is None:
         out = torch.empty((M, 3), dtype=torch.float32, device=dev)

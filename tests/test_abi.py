@@ -43,3 +43,20 @@ def test_host_side_queries_without_a_gpu():
     lib.sop_read_bandwidth_probe.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_void_p,
                                              ctypes.c_void_p]
     assert lib.sop_read_bandwidth_probe(None, 64, 1, None, None) == 1
+
+
+def test_radius_checked_on_the_host():
+    """A search radius outside [0, 2048] (or NaN) is refused before any
+    device work, by every query entry point."""
+    from paper_2510_07729_gb300 import sop as S
+    lib = S.load()
+    fake = 1 << 20  # never dereferenced: the argument checks come first
+    at = S.AtlasDesc(fake, None, 0, 0, 64, 8, 1.0, fake, None)
+    for r in (-1.0, float("nan"), 4096.0):
+        sp = S.ShadeParams(4, 64, 0, 0.5, 1e-6, 0, 0, r)
+        assert lib.sop_query_shade(fake, fake, fake, fake, fake, fake, 16, ctypes.byref(at), fake, 16, 32, None,
+                                   ctypes.byref(sp), fake, None, None, fake, 1 << 30, None) == 1
+        assert b"radius" in lib.sop_last_error()
+        assert lib.sop_query_shade_noalloc(fake, fake, fake, fake, fake, fake, 16, ctypes.byref(at), fake, 16, 32,
+                                           None, ctypes.byref(sp), fake, None, None, None) == 1
+        assert b"radius" in lib.sop_last_error()
