@@ -16,11 +16,12 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "sop_oracle.c")
+SRCS = (SRC, os.path.join(HERE, "gbuffer_oracle.c"))
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 MODE_SHADE, MODE_SHADOW = 0, 1
 ENV_EQUIRECT, ENV_OCTAHEDRAL = 0, 1
-FLAG_ALPHA_MIN, FLAG_ORDER, FLAG_TNEAR, FLAG_TSTOP = 1, 2, 4, 8
+FLAG_ALPHA_MIN, FLAG_ORDER, FLAG_TNEAR, FLAG_TSTOP, FLAG_GRAZING = 1, 2, 4, 8, 16
 
 _lib = None
 
@@ -28,14 +29,14 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (IEEE double, no FMA contraction)."""
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in SRCS):
         return LIB
     base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
     tmp = LIB + f".tmp{os.getpid()}"
     try:
-        subprocess.run(base + ["-fopenmp", SRC, "-o", tmp, "-lm"], check=True, capture_output=True)
+        subprocess.run(base + ["-fopenmp", *SRCS, "-o", tmp, "-lm"], check=True, capture_output=True)
     except subprocess.CalledProcessError:
-        subprocess.run(base + [SRC, "-o", tmp, "-lm"], check=True)
+        subprocess.run(base + [*SRCS, "-o", tmp, "-lm"], check=True)
     os.replace(tmp, LIB)
     return LIB
 
@@ -46,6 +47,7 @@ def lib():
         build()
         _lib = C.CDLL(LIB)
         _lib.orc_num_threads.restype = C.c_int
+        _lib.orc_gbuffer_points.restype = C.c_int64
     return _lib
 
 
@@ -317,4 +319,76 @@ def query_shade_grad(x, n, wo, albedo, rough, metal, probe_pos, maps_rgb, maps_o
         C.c_int32(K), C.c_double(spec), C.c_uint64(sk), C.c_uint64(radius_key(radius)), _p(go), _p(out["albedo"]), _p(out["rough"]),
         _p(out["metal"]), _p(out["normal"]), _p(out["env"]), _p(out["maps_rgb"]), _p(out["maps_occ"]),
         _p(out["abs_albedo"]), _p(out["abs_rough"]), _p(out["abs_metal"]), _p(out["abs_normal"]))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# deferred front end: G-buffers, shading points, depth compositing
+# ----------------------------------------------------------------------------
+GBUF_C, GBUF_W, GBUF_N, GBUF_D, GBUF_A, GBUF_R, GBUF_M = slice(0, 3), 3, slice(4, 7), 7, slice(8, 11), 11, 12
+
+
+def trace_gbuffer(gauss, mats, origins, dirs, rays=None, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99,
+                  t_stop=1e-4):
+    """FP64 multi-target rendering (see gbuffer_oracle.c). gauss: dict of
+    mean/scale/quat/opacity/rgb; mats: albedo [N,3], rough [N], metal [N];
+    origins [n_o,3]; dirs [n_d,4] (or [n_d,3]) float32 unit directions;
+    rays: ray ids (origin id // n_d, direction id % n_d), default all.
+    Returns (gbuf [n_rays,16], flags [n_rays])."""
+    g = {k: _f32(gauss[k]) for k in ("mean", "scale", "quat", "opacity", "rgb")}
+    al, ro, me = _f32(mats["albedo"]), _f32(mats["rough"]), _f32(mats["metal"])
+    org = _f32(origins).reshape(-1, 3)
+    d = np.asarray(dirs, np.float32)
+    if d.shape[-1] == 3:
+        d = np.concatenate([d, np.zeros((len(d), 1), np.float32)], axis=1)
+    d = np.ascontiguousarray(d)
+    nd = len(d)
+    rays = np.arange(len(org) * nd, dtype=np.int64) if rays is None else np.ascontiguousarray(rays, np.int64)
+    out = np.empty((len(rays), 16))
+    fl = np.empty(len(rays), np.int32)
+    lib().orc_trace_gbuffer(C.c_int64(len(g["mean"])), _p(g["mean"]), _p(g["scale"]), _p(g["quat"]),
+                            _p(g["opacity"]), _p(g["rgb"]), _p(al), _p(ro), _p(me), _p(org), C.c_int64(nd), _p(d),
+                            C.c_int64(len(rays)), _p(rays), C.c_double(t_near), C.c_double(alpha_min),
+                            C.c_double(alpha_max), C.c_double(t_stop), _p(out), _p(fl))
+    return out, fl
+
+
+def pinhole_dirs(W, H, eye, target, fov_y_deg, up=(0.0, 0.0, 1.0)):
+    out = np.empty((H * W, 3))
+    lib().orc_pinhole_dirs(C.c_int32(W), C.c_int32(H), _p(_f64(eye)), _p(_f64(target)), _p(_f64(up)),
+                           C.c_double(fov_y_deg), _p(out))
+    return out
+
+
+def panorama_dirs(W, H):
+    out = np.empty((H * W, 3))
+    lib().orc_panorama_dirs(C.c_int32(W), C.c_int32(H), _p(out))
+    return out
+
+
+def gbuffer_points(gbuf, origin, dirs, w_min=0.5, front=None):
+    """Shading points of a float32 G-buffer [n,16] (see gbuffer_oracle.c):
+    returns (pix [k] int64, points dict x, n, wo, albedo, rough, metal)."""
+    gb = _f32(gbuf)
+    d = np.asarray(dirs, np.float32)
+    if d.shape[-1] == 3:
+        d = np.concatenate([d, np.zeros((len(d), 1), np.float32)], axis=1)
+    d = np.ascontiguousarray(d)
+    fr = None if front is None else _f32(front)
+    n = len(gb)
+    pix = np.empty(n, np.int64)
+    out = np.empty((n, 14))
+    k = lib().orc_gbuffer_points(C.c_int64(n), _p(gb), _p(_f32(origin)), _p(d), C.c_float(w_min),
+                                 None if fr is None else _p(fr), _p(pix), _p(out))
+    o = out[:k]
+    return pix[:k], dict(x=o[:, 0:3], n=o[:, 3:6], wo=o[:, 6:9], albedo=o[:, 9:12], rough=o[:, 12], metal=o[:, 13])
+
+
+def depth_composite(scene_gbuf, obj_gbuf, sc_pix, shadow, obj_pix, obj_rgb):
+    sg, og = _f32(scene_gbuf), _f32(obj_gbuf)
+    n = len(sg)
+    out = np.empty((n, 3))
+    lib().orc_depth_composite(C.c_int64(n), _p(sg), _p(og), C.c_int64(len(sc_pix)),
+                              _p(np.ascontiguousarray(sc_pix, np.int64)), _p(_f32(shadow)), C.c_int64(len(obj_pix)),
+                              _p(np.ascontiguousarray(obj_pix, np.int64)), _p(_f32(obj_rgb)), _p(out))
     return out

@@ -20,6 +20,11 @@ workloads:
             Gaussians total), 4096 object probes + 4096 shadow-region probes
             within 6x the object size (Sec. 4.1), 1920x1080 view, K=8, S=64
   diff      the 'object' scene seen from 4 cameras (adjoint workload)
+  deferred  the composition rebuilt from flattened (surfel-like) Gaussians
+            with per-Gaussian materials, for the G-buffer front end: the
+            object (200k) and the scene (ground 700k + clutter 300k) traced
+            separately from a 1920x1080 camera, the two probe sets of
+            'compose'
 
 Every array is float32 (int32 for indices) and C-contiguous.
 """
@@ -215,6 +220,45 @@ def gaussians_on_surface(rng, ells, n, scale_range=(0.002, 0.02), opacity_range=
     )
 
 
+def _quats_with_axis(rng, nrm):
+    """Unit quaternions (w, x, y, z) whose rotation takes the local z axis
+    to the unit vectors nrm [n,3], with a uniform random spin about it."""
+    n = len(nrm)
+    a = np.where(np.abs(nrm[:, :1]) < 0.9, np.array([[1.0, 0.0, 0.0]]), np.array([[0.0, 1.0, 0.0]]))
+    t = np.cross(a, nrm)
+    t /= np.linalg.norm(t, axis=1, keepdims=True)
+    b = np.cross(nrm, t)
+    ang = rng.uniform(0, 2 * np.pi, n)[:, None]
+    t, b = np.cos(ang) * t + np.sin(ang) * b, -np.sin(ang) * t + np.cos(ang) * b
+    Rm = np.stack([t, b, nrm], axis=2)  # columns: local axes in world space
+    # rotation matrix to quaternion, through the largest of the four
+    # candidate denominators (w, x, y, z) for accuracy
+    m = Rm
+    cand = np.stack([1.0 + m[:, 0, 0] + m[:, 1, 1] + m[:, 2, 2], 1.0 + m[:, 0, 0] - m[:, 1, 1] - m[:, 2, 2],
+                     1.0 - m[:, 0, 0] + m[:, 1, 1] - m[:, 2, 2], 1.0 - m[:, 0, 0] - m[:, 1, 1] + m[:, 2, 2]], axis=1)
+    k = np.argmax(cand, axis=1)
+    r = np.sqrt(np.maximum(cand[np.arange(n), k], 1e-300))
+    s21, s02, s10 = m[:, 2, 1] - m[:, 1, 2], m[:, 0, 2] - m[:, 2, 0], m[:, 1, 0] - m[:, 0, 1]
+    a01, a02, a12 = m[:, 0, 1] + m[:, 1, 0], m[:, 0, 2] + m[:, 2, 0], m[:, 1, 2] + m[:, 2, 1]
+    q = np.select([k[:, None] == 0, k[:, None] == 1, k[:, None] == 2, k[:, None] == 3],
+                  [np.stack([r * r, s21, s02, s10], 1), np.stack([s21, r * r, a01, a02], 1),
+                   np.stack([s02, a01, r * r, a12], 1), np.stack([s10, a02, a12, r * r], 1)])
+    q = q / (2.0 * r[:, None])
+    return q
+
+
+def surfels(rng, mean, nrm, scale_range=(0.002, 0.02), flat=0.1, opacity_range=(0.2, 1.0)):
+    """Flattened Gaussians at mean [n,3]: two tangent scales log-uniform in
+    scale_range, the third (along nrm) `flat` times the smaller, opacity
+    uniform, rgb uniform."""
+    n = len(mean)
+    lo, hi = np.log(scale_range[0]), np.log(scale_range[1])
+    st = np.exp(rng.uniform(lo, hi, (n, 2)))
+    scale = np.concatenate([st, flat * st.min(1, keepdims=True)], axis=1)
+    return dict(mean=mean.astype(F32), scale=scale.astype(F32), quat=_quats_with_axis(rng, nrm).astype(F32),
+                opacity=rng.uniform(*opacity_range, n).astype(F32), rgb=rng.uniform(0.0, 1.0, (n, 3)).astype(F32))
+
+
 def concat_gaussians(*gs):
     return {k: np.ascontiguousarray(np.concatenate([g[k] for g in gs])) for k in gs[0]}
 
@@ -401,6 +445,66 @@ def make_compose(seed=2):
                   n=n_sc[is_sc].astype(F32), wo=(-d[is_sc]).astype(F32), **mat_s)
     return dict(name="compose", gauss_object=gobj, gauss_scene=scene, shade=shade, shadow=shadow,
                 R=16, K=8, S=64, env=env, pixels=1920 * 1080, object_size=diag)
+
+
+@functools.lru_cache(maxsize=1)
+def make_deferred(seed=5):
+    """The composition workload for the deferred front end (G-buffers traced
+    from the camera): the 'object' ellipsoids, probes and size, covered by
+    200k surfels with per-Gaussian materials; a scene of 700k ground surfels
+    (normal +z) in the square of side 6x the object size and 300k surfels on
+    30 clutter ellipsoids; 4096 shadow-region probes by FPS over ground
+    samples; a 1920x1080 camera looking down at the object from 35 degrees;
+    a 256x512 log-normal environment. The scene does not contain the object:
+    the two are traced separately and composed by depth."""
+    _, obj_ells, _, opos, onrm, osamp, diag = _object(1)
+    rng = np.random.default_rng(seed)
+    m, nr = obj_ells.sample_surface(rng, 200_000)
+    gobj = surfels(rng, m, nr)
+    mobj = materials(rng, 200_000)
+    lo, hi = osamp.min(0), osamp.max(0)
+    size = float(np.max(hi - lo))
+    zg = float(lo[2])
+    cxy = 0.5 * (lo[:2] + hi[:2])
+    half = 3.0 * size
+    ng = 700_000
+    gm = np.empty((ng, 3))
+    gm[:, :2] = cxy + rng.uniform(-half, half, (ng, 2))
+    gm[:, 2] = zg
+    ground = surfels(rng, gm, np.tile(np.array([0.0, 0.0, 1.0]), (ng, 1)))
+    nc = 30
+    ax = rng.uniform(0.05, 0.15, (nc, 3))
+    cc = np.empty((nc, 3))
+    k = 0
+    while k < nc:
+        p = cxy + rng.uniform(-half, half, 2)
+        if np.linalg.norm(p - cxy) > 0.75 * size:
+            cc[k, :2] = p
+            k += 1
+    cc[:, 2] = zg + ax[:, 2]
+    clutter_ells = Ellipsoids(cc, ax, np.repeat(np.eye(3)[None], nc, axis=0))
+    m, nr = clutter_ells.sample_surface(rng, 300_000)
+    scene = concat_gaussians(ground, surfels(rng, m, nr))
+    mscene = materials(rng, len(scene["mean"]))
+    gs = np.empty((65_536, 3))
+    gs[:, :2] = cxy + rng.uniform(-half, half, (65_536, 2))
+    gs[:, 2] = zg
+    gs = gs[~clutter_ells.inside(gs)]
+    sel = farthest_point_sampling(gs, 4096)
+    spos = gs[sel] + np.array([0.0, 0.0, 0.01 * diag])
+    az = rng.uniform(0, 2 * np.pi)
+    el = np.deg2rad(35.0)
+    dist = 2.2 * size / np.tan(np.deg2rad(25.0))
+    target = np.array([cxy[0], cxy[1], zg + 0.3 * size])
+    eye = target + dist * np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+    W, H, fov = 1920, 1080, 50.0
+    d = pinhole_rays(eye, target, W, H, fov)
+    dirs = np.concatenate([d, np.zeros((len(d), 1))], axis=1).astype(F32)
+    env = env_lognormal(rng, 256, 512)
+    return dict(name="deferred", gauss_object=gobj, mats_object=mobj, gauss_scene=scene, mats_scene=mscene,
+                eye=eye.astype(F32), target=target, fov=fov, W=W, H=H, dirs=dirs,
+                obj_probe_pos=opos.astype(F32), scene_probe_pos=spos.astype(F32), env=env, R=16, K=8, S=64,
+                object_size=diag)
 
 
 def subsample(rng, arrays, keys, m):
