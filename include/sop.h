@@ -429,6 +429,82 @@ sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* 
                                    const sop_shade_params* params, float* out, int32_t* out_idx, float* out_w,
                                    void* stream);
 
+/* ---- deferred front end (Sec. 3.1 multi-target rendering, Sec. 4.3) -------- */
+
+/* Per-Gaussian materials, device: albedo [N][3], roughness [N], metallic [N]. */
+typedef struct {
+    const float* albedo;
+    const float* rough;
+    const float* metal;
+} sop_materials;
+
+/* Workspace bytes for sop_trace_gbuffer on n Gaussians: the bake's grid
+ * (sop_bake_bin builds it; a larger workspace holds more cell entries). */
+size_t sop_trace_workspace_bytes(int64_t n_gauss);
+
+/* Multi-target rendering (Sec. 3.1, the alpha blending of G-buffers
+ * B = sum_i T_i alpha_i b_i with b_i = {c, 1, d, n, a, r, m}) of the
+ * Gaussians g along n_origins x n_dirs rays: ray p n_dirs + t starts at
+ * origins[p] ([n_origins][3], device) and runs along dirs[t] ([n_dirs][4],
+ * device, 16-byte aligned; x, y, z used as given, unit length expected).
+ * Each Gaussian is evaluated as in the bake (point of maximum density t*,
+ * alpha = min(alpha_max, o exp(-m^2/2)), kept when alpha >= alpha_min and
+ * t* > t_near), hits are composited in increasing (t*, index) order until
+ * T < t_stop; d = t*; the normal n is the Gaussian's local axis of smallest
+ * scale (the first of equal ones), turned against the ray (n . d <= 0).
+ * out [rays][16] float32, device, 16-byte aligned: C.rgb, W, N.xyz, D,
+ * A.rgb, R, M, 0, 0, 0 (W = sum T alpha; D / W is the unbiased depth along
+ * the ray). ws must hold the grid that sop_bake_bin built for the same g and
+ * params (with the same ws_bytes). Asynchronous. */
+sop_status sop_trace_gbuffer(const sop_gaussians* g, const sop_materials* m, const float* origins,
+                             int32_t n_origins, const float* dirs, int64_t n_dirs, const sop_bake_params* params,
+                             float* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Ray directions of a pinhole camera, W x H pixels, row 0 at the top: pixel
+ * (i, j) looks along f + sx r + sy u, sx = ((i + 1/2)/W 2 - 1) tan(fov/2)
+ * W/H, sy = (1 - (j + 1/2)/H 2) tan(fov/2), with f the unit direction from
+ * eye to target, r = f x up normalised, u = r x f (up replaced by +y when
+ * within 0.99 of f). eye, target, up: host float[3]; fov_y in degrees,
+ * (0, 180). out [H W][4] device (unit x, y, z, 0), computed in double and
+ * rounded once. Asynchronous. */
+sop_status sop_pinhole_dirs(int32_t W, int32_t H, const float* eye, const float* target, const float* up,
+                            float fov_y_deg, float* out, void* stream);
+
+/* Directions of an equirectangular panorama (the 360 degree sweep of
+ * Sec. 4.2), z-up, the environment map's parameterisation: pixel (i, j) of
+ * W x H has azimuth (i + 1/2)/W 2 pi - pi and polar angle (j + 1/2)/H pi.
+ * out [H W][4] device. Asynchronous. */
+sop_status sop_panorama_dirs(int32_t W, int32_t H, float* out, void* stream);
+
+/* Workspace bytes for sop_gbuffer_points on n_pix pixels. */
+size_t sop_gbuffer_points_workspace_bytes(int64_t n_pix);
+
+/* Shading points of a G-buffer (Sec. 4.3; the unbiased depth of Sec. 3.1):
+ * pixel p of gbuf [n_pix][16] (device) is kept when W >= w_min, N != 0 and,
+ * with `front` (another G-buffer of the same pixels, or NULL) kept at p,
+ * when D/W < D'/W' (float32 quotients). Kept pixels are written in pixel
+ * order: out_pix [k] (int64), out_x = origin + (D/W) d, out_n = N/|N|,
+ * out_wo = -d, out_albedo = A/W ([k][3] each), out_rough = R/W,
+ * out_metal = M/W ([k]); origin is a host float[3], dirs [n_pix][4] the
+ * pixels' directions. out_count: one device int64, the number kept. Output
+ * arrays hold n_pix entries at most. Asynchronous. */
+sop_status sop_gbuffer_points(const float* gbuf, const float* front, int64_t n_pix, const float* origin,
+                              const float* dirs, float w_min, int64_t* out_pix, float* out_x, float* out_n,
+                              float* out_wo, float* out_albedo, float* out_rough, float* out_metal,
+                              int64_t* out_count, void* ws, size_t ws_bytes, void* stream);
+
+/* Depth compositing of the composed frame (Sec. 4.3): out [n_pix][3] =
+ * the scene's traced colour C_s (scene_gbuf), multiplied at the scene's
+ * shading points sc_pix [n_sc] by their shadow ratio shadow [n_sc][3]
+ * (Eq. 9); then at the object's shading points obj_pix [n_obj] (the pixels
+ * where it lies in front, from sop_gbuffer_points with front = scene_gbuf)
+ * W_o obj_rgb + (1 - W_o) out, W_o the object's G-buffer weight. Pixel
+ * lists hold distinct pixels; entries outside [0, n_pix) are skipped.
+ * All device. Asynchronous. */
+sop_status sop_depth_composite(const float* scene_gbuf, const float* obj_gbuf, int64_t n_pix, const int64_t* sc_pix,
+                               const float* shadow, int64_t n_sc, const int64_t* obj_pix, const float* obj_rgb,
+                               int64_t n_obj, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -364,7 +364,17 @@ struct TraceK {
     // waiting hits plus candidates queued since the last composite that
     // make the walk stop to composite
     int32_t composite_at;
+    // rays are origin p (of P) along direction t (of n_dirs): ray = p n_dirs + t
+    int64_t n_dirs;
+    // G-buffer mode (multi-target rendering): the Gaussians' orientation,
+    // scales and materials, and the output [rays][4] float4
+    const float *quat, *scale, *albedo, *rough, *metal;
+    float4* gbuf;
 };
+
+// what a traced ray writes: the probe atlas texel (O, L_in, depth) or the
+// G-buffer entry (C, W, N, D, A, R, M)
+enum { kTraceAtlas = 0, kTraceGbuf = 1 };
 
 constexpr int kWarpsPerCta = 8;
 constexpr int kHitCap = 256;  // per-warp hit buffer (shared memory)
@@ -382,9 +392,31 @@ __device__ __forceinline__ uint64_t hit_key(float t, int32_t g)
 // composited terms (reduced once per ray).
 struct RayAcc {
     float T, L0, L1, L2, Dacc, Wacc;
+    float N0, N1, N2, A0, A1, A2, Rg, Mg;  // G-buffer mode only
     int n_eval, n_comp, n_test;
     bool done;
 };
+
+// Unit normal of a Gaussian read as a surfel: its local axis of smallest
+// scale (the first of equal ones), a column of R(q).
+__device__ __forceinline__ float3 surfel_normal(const TraceK& k, const int32_t g)
+{
+    const float sx = __ldg(k.scale + 3 * g), sy = __ldg(k.scale + 3 * g + 1), sz = __ldg(k.scale + 3 * g + 2);
+    int am = 0;
+    float sm = sx;
+    if (sy < sm) {
+        am = 1;
+        sm = sy;
+    }
+    if (sz < sm) am = 2;
+    const float qw = __ldg(k.quat + 4 * g), qx = __ldg(k.quat + 4 * g + 1), qy = __ldg(k.quat + 4 * g + 2),
+                qz = __ldg(k.quat + 4 * g + 3);
+    const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    const float w = qw / qn, x = qx / qn, y = qy / qn, z = qz / qn;
+    if (am == 0) return f3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+    if (am == 1) return f3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+    return f3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+}
 
 // Exact responses of up to 32 queued candidates (one per lane). Hits are
 // appended to the warp's buffer key/alp[0, n); n keeps counting past
@@ -521,10 +553,13 @@ __device__ __forceinline__ void sort_hits(uint64_t* key, float* alp, const int n
 // scratch buffer dkey/dalp (the others close up, in order, at the front of
 // key/alp, and n becomes their count), are sorted by (t*, index) and taken
 // front to back, 32 at a time, with a prefix product of (1 - alpha). The
-// ray stops once the transmittance falls below t_stop.
+// ray stops once the transmittance falls below t_stop. In G-buffer mode each
+// hit also adds its normal (turned against the ray direction d) and its
+// materials.
+template <int OUT>
 __device__ __forceinline__ void composite_hits(const TraceK& k, uint64_t* key, float* alp, uint64_t* dkey,
                                                float* dalp, int& n, const bool all, const float thr, const int lane,
-                                               RayAcc& acc)
+                                               RayAcc& acc, const float3 d)
 {
     const unsigned below = (1u << lane) - 1u;
     int nd = 0, nr = 0;
@@ -584,6 +619,18 @@ __device__ __forceinline__ void composite_hits(const TraceK& k, uint64_t* key, f
             acc.L2 = fmaf(w, r4.x, acc.L2);
             acc.Dacc = fmaf(w, th_hit, acc.Dacc);
             acc.Wacc += w;
+            if (OUT == kTraceGbuf) {
+                const float3 nv = surfel_normal(k, gh);
+                const float ws = dot3(nv, d) > 0.f ? -w : w;
+                acc.N0 = fmaf(ws, nv.x, acc.N0);
+                acc.N1 = fmaf(ws, nv.y, acc.N1);
+                acc.N2 = fmaf(ws, nv.z, acc.N2);
+                acc.A0 = fmaf(w, __ldg(k.albedo + 3 * gh), acc.A0);
+                acc.A1 = fmaf(w, __ldg(k.albedo + 3 * gh + 1), acc.A1);
+                acc.A2 = fmaf(w, __ldg(k.albedo + 3 * gh + 2), acc.A2);
+                acc.Rg = fmaf(w, __ldg(k.rough + gh), acc.Rg);
+                acc.Mg = fmaf(w, __ldg(k.metal + gh), acc.Mg);
+            }
         }
         const int cnt = stop_lane < 32 ? stop_lane + 1 : min(32, nd - cb);
         used += cnt;
@@ -664,7 +711,8 @@ constexpr int kCompositeAt = 48;
 // pend, the candidates queued since (an upper bound of hits + queue). At a
 // composite the queue is always empty, so the set of hits composited, and
 // with it every rounding, is the same on every run.
-__global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
+template <int OUT>
+__global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(const TraceK k)
 {
     __shared__ uint64_t s_key[kWarpsPerCta][kHitCap];
     __shared__ float s_alpha[kWarpsPerCta][kHitCap];
@@ -677,7 +725,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
     uint64_t* dkey = s_dkey[wib];
     float* dalp = s_dalpha[wib];
     int32_t* que = s_que[wib];
-    const int RR = k.R * k.R;
+    const int64_t RR = k.n_dirs;
     const int64_t total = (int64_t)k.P * RR;
     const GaussGrid G = *k.grid;
     const float3 go = f3(G.origin[0], G.origin[1], G.origin[2]);
@@ -702,6 +750,7 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
     RayAcc acc;
     acc.T = 1.f;
     acc.L0 = acc.L1 = acc.L2 = acc.Dacc = acc.Wacc = 0.f;
+    acc.N0 = acc.N1 = acc.N2 = acc.A0 = acc.A1 = acc.A2 = acc.Rg = acc.Mg = 0.f;
     acc.n_eval = acc.n_comp = acc.n_test = 0;
     acc.done = false;
     int n = 0, qn = 0;  // hits in key/alp[0, n) (unsorted); candidates in que[0, qn)
@@ -808,8 +857,8 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
                         sh = sl + 0.5f * (sh - sl);
                         continue;
                     }
-                    composite_hits(k, key, alp, dkey, dalp, n, mode == 0 ? last : (mode == 2 && sfin),
-                                   mode == 0 ? t_exit : (mode == 1 ? tl : sh), lane, acc);
+                    composite_hits<OUT>(k, key, alp, dkey, dalp, n, mode == 0 ? last : (mode == 2 && sfin),
+                                        mode == 0 ? t_exit : (mode == 1 ? tl : sh), lane, acc, d);
                     nw = n;
                     pend = 0;
                     if (acc.done || mode == 0) break;
@@ -853,6 +902,24 @@ __global__ void __launch_bounds__(256, 4) trace_kernel(const TraceK k)
         L2 += __shfl_xor_sync(0xffffffffu, L2, off);
         Dacc += __shfl_xor_sync(0xffffffffu, Dacc, off);
         Wacc += __shfl_xor_sync(0xffffffffu, Wacc, off);
+    }
+    if (OUT == kTraceGbuf) {
+        float v[8] = {acc.N0, acc.N1, acc.N2, acc.A0, acc.A1, acc.A2, acc.Rg, acc.Mg};
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
+        if (lane == 0) {
+            float4* o4 = k.gbuf + 4 * ray;
+            o4[0] = make_float4(L0, L1, L2, Wacc);
+            o4[1] = make_float4(v[0], v[1], v[2], Dacc);
+            o4[2] = make_float4(v[3], v[4], v[5], v[6]);
+            o4[3] = make_float4(v[7], 0.f, 0.f, 0.f);
+            atomicAdd(k.stats + 1, (unsigned long long)acc.n_eval);
+            atomicAdd(k.stats + 2, (unsigned long long)acc.n_comp);
+            atomicAdd(k.stats + 4, (unsigned long long)acc.n_test);
+        }
+        continue;
     }
     if (lane == 0) {
         // interior texel (t % R, t / R) of probe p, stored at (+1, +1)
@@ -942,6 +1009,23 @@ cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* 
     return cudaGetLastError();
 }
 
+// persistent grid: as many CTAs as fit on the device at once (fewer for a
+// small launch)
+template <int OUT>
+static unsigned trace_blocks(int64_t rays)
+{
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<OUT>, kWarpsPerCta * 32, 0);
+        resident = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+    }
+    const int64_t need = (rays + kWarpsPerCta - 1) / kWarpsPerCta;
+    return (unsigned)(need < resident ? need : resident);
+}
+
 cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp, const BakeLayout& L, char* ws,
                               cudaStream_t s)
 {
@@ -977,20 +1061,49 @@ cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp,
         return (v >= 1 && v <= kHitCap / 2) ? v : kCompositeAt;
     }();
     k.composite_at = composite_at;
+    k.n_dirs = (int64_t)R * R;
+    k.quat = k.scale = k.albedo = k.rough = k.metal = nullptr;
+    k.gbuf = nullptr;
     const int64_t rays = (int64_t)atlas.P * R * R;
-    // persistent grid: as many CTAs as fit on the device at once
-    static int resident = 0;
-    if (!resident) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel, kWarpsPerCta * 32, 0);
-        resident = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
-    }
-    const int64_t need = (rays + kWarpsPerCta - 1) / kWarpsPerCta;
-    const unsigned nb = (unsigned)(need < resident ? need : resident);
-    trace_kernel<<<nb, kWarpsPerCta * 32, 0, s>>>(k);
+    trace_kernel<kTraceAtlas><<<trace_blocks<kTraceAtlas>(rays), kWarpsPerCta * 32, 0, s>>>(k);
     return launch_gutter_fill(atlas, s);
+}
+
+cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, const float* rough, const float* metal,
+                                 const float* origins, int32_t n_origins, const float* dirs, int64_t n_dirs,
+                                 const sop_bake_params& bp, const BakeLayout& L, char* ws, float* out, cudaStream_t s)
+{
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(ws + L.stats);
+    trace_reset_kernel<<<1, 32, 0, s>>>(stats);
+    TraceK k;
+    k.rec = reinterpret_cast<GRec*>(ws + L.rec);
+    k.grid = reinterpret_cast<GaussGrid*>(ws + L.hdr);
+    k.cell_start = reinterpret_cast<int32_t*>(ws + L.cell_start);
+    k.ent = reinterpret_cast<uint4*>(ws + L.ent);
+    k.dirs = reinterpret_cast<const float4*>(dirs);
+    k.probe_pos = origins;
+    k.P = n_origins;
+    k.R = 0;
+    k.t_near = bp.t_near;
+    k.alpha_min = bp.alpha_min;
+    k.alpha_max = bp.alpha_max;
+    k.t_stop = bp.t_stop;
+    k.rgbo = k.depth = nullptr;
+    k.rgbo_dtype = k.depth_dtype = 0;
+    k.inv_depth_scale = 1.f;
+    k.stats = stats;
+    k.composite_at = kCompositeAt;
+    k.n_dirs = n_dirs;
+    k.quat = g.quat;
+    k.scale = g.scale;
+    k.albedo = albedo;
+    k.rough = rough;
+    k.metal = metal;
+    k.gbuf = reinterpret_cast<float4*>(out);
+    const int64_t rays = (int64_t)n_origins * n_dirs;
+    if (rays == 0) return cudaGetLastError();
+    trace_kernel<kTraceGbuf><<<trace_blocks<kTraceGbuf>(rays), kWarpsPerCta * 32, 0, s>>>(k);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s)

@@ -582,4 +582,106 @@ sop_status sop_atlas_copy(const sop_atlas* src, const int32_t* src_probes, const
                        "sop_atlas_copy");
 }
 
+// ---- deferred front end ------------------------------------------------------
+
+size_t sop_trace_workspace_bytes(int64_t n_gauss)
+{
+    if (n_gauss < 0) return 0;
+    return sop::bake_layout(n_gauss, 0).total;
+}
+
+sop_status sop_trace_gbuffer(const sop_gaussians* g, const sop_materials* m, const float* origins,
+                             int32_t n_origins, const float* dirs, int64_t n_dirs, const sop_bake_params* params,
+                             float* out, void* ws, size_t ws_bytes, void* stream)
+{
+    sop_status st = check_bake_args(g, params);
+    if (st != SOP_OK) return st;
+    if (!m || (g->n > 0 && (!m->albedo || !m->rough || !m->metal)))
+        return fail(SOP_ERR_INVALID_ARG, "materials NULL");
+    if (n_origins < 1 || !origins) return fail(SOP_ERR_INVALID_ARG, "need at least one origin");
+    if (n_dirs < 1 || n_dirs > (int64_t)INT32_MAX || !dirs || !aligned(dirs, 16))
+        return fail(SOP_ERR_INVALID_ARG, "dirs: NULL, not 16-byte aligned, or n_dirs outside [1, 2^31)");
+    if ((int64_t)n_origins * n_dirs > ((int64_t)1 << 36))
+        return fail(SOP_ERR_INVALID_ARG, "n_origins * n_dirs exceeds 2^36 rays");
+    if (!out || !aligned(out, 16)) return fail(SOP_ERR_INVALID_ARG, "out NULL or not 16-byte aligned");
+    sop::BakeLayout L;
+    if ((st = bake_fit(g->n, ws, ws_bytes, L)) != SOP_OK) return st;
+    return cuda_status(sop::launch_trace_gbuffer(*g, m->albedo, m->rough, m->metal, origins, n_origins, dirs, n_dirs,
+                                                 *params, L, (char*)ws, out, (cudaStream_t)stream),
+                       "sop_trace_gbuffer");
+}
+
+sop_status sop_pinhole_dirs(int32_t W, int32_t H, const float* eye, const float* target, const float* up,
+                            float fov_y_deg, float* out, void* stream)
+{
+    if (W < 1 || H < 1 || (int64_t)W * H > (int64_t)INT32_MAX)
+        return fail(SOP_ERR_INVALID_ARG, "image %d x %d invalid", W, H);
+    if (!eye || !target || !up) return fail(SOP_ERR_INVALID_ARG, "eye, target or up is NULL");
+    if (!(fov_y_deg > 0.f && fov_y_deg < 180.f)) return fail(SOP_ERR_INVALID_ARG, "fov_y outside (0, 180)");
+    double f2 = 0.0, u2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(eye[a]) || !isfinite(target[a]) || !isfinite(up[a]))
+            return fail(SOP_ERR_INVALID_ARG, "camera not finite");
+        f2 += ((double)target[a] - eye[a]) * ((double)target[a] - eye[a]);
+        u2 += (double)up[a] * up[a];
+    }
+    if (!(f2 > 0.0) || !(u2 > 0.0)) return fail(SOP_ERR_INVALID_ARG, "eye == target or up == 0");
+    if (!out || !aligned(out, 16)) return fail(SOP_ERR_INVALID_ARG, "out NULL or not 16-byte aligned");
+    return cuda_status(sop::launch_pinhole_dirs(W, H, eye, target, up, fov_y_deg, out, (cudaStream_t)stream),
+                       "sop_pinhole_dirs");
+}
+
+sop_status sop_panorama_dirs(int32_t W, int32_t H, float* out, void* stream)
+{
+    if (W < 1 || H < 1 || (int64_t)W * H > (int64_t)INT32_MAX)
+        return fail(SOP_ERR_INVALID_ARG, "panorama %d x %d invalid", W, H);
+    if (!out || !aligned(out, 16)) return fail(SOP_ERR_INVALID_ARG, "out NULL or not 16-byte aligned");
+    return cuda_status(sop::launch_panorama_dirs(W, H, out, (cudaStream_t)stream), "sop_panorama_dirs");
+}
+
+size_t sop_gbuffer_points_workspace_bytes(int64_t n_pix)
+{
+    if (n_pix < 0 || n_pix > (int64_t)INT32_MAX) return 0;
+    return sop::points_ws_bytes(n_pix);
+}
+
+sop_status sop_gbuffer_points(const float* gbuf, const float* front, int64_t n_pix, const float* origin,
+                              const float* dirs, float w_min, int64_t* out_pix, float* out_x, float* out_n,
+                              float* out_wo, float* out_albedo, float* out_rough, float* out_metal,
+                              int64_t* out_count, void* ws, size_t ws_bytes, void* stream)
+{
+    if (n_pix < 0 || n_pix > (int64_t)INT32_MAX) return fail(SOP_ERR_INVALID_ARG, "n_pix out of range");
+    if (!out_count) return fail(SOP_ERR_INVALID_ARG, "out_count is NULL");
+    if (!origin) return fail(SOP_ERR_INVALID_ARG, "origin is NULL");
+    if (!(w_min > 0.f) || !isfinite(w_min)) return fail(SOP_ERR_INVALID_ARG, "w_min must be finite and > 0");
+    if (n_pix > 0) {
+        if (!gbuf || !aligned(gbuf, 16) || !dirs || !aligned(dirs, 16) || (front && !aligned(front, 16)))
+            return fail(SOP_ERR_INVALID_ARG, "gbuf, front or dirs NULL or not 16-byte aligned");
+        if (!out_pix || !out_x || !out_n || !out_wo || !out_albedo || !out_rough || !out_metal)
+            return fail(SOP_ERR_INVALID_ARG, "an output array is NULL");
+    }
+    sop_status st = check_ws(ws, ws_bytes, sop::points_ws_bytes(n_pix));
+    if (st != SOP_OK) return st;
+    return cuda_status(sop::launch_gbuffer_points(gbuf, front, n_pix, origin, dirs, w_min, out_pix, out_x, out_n,
+                                                  out_wo, out_albedo, out_rough, out_metal, out_count, (char*)ws,
+                                                  (cudaStream_t)stream),
+                       "sop_gbuffer_points");
+}
+
+sop_status sop_depth_composite(const float* scene_gbuf, const float* obj_gbuf, int64_t n_pix, const int64_t* sc_pix,
+                               const float* shadow, int64_t n_sc, const int64_t* obj_pix, const float* obj_rgb,
+                               int64_t n_obj, float* out, void* stream)
+{
+    if (n_pix < 0 || n_sc < 0 || n_obj < 0 || n_sc > n_pix || n_obj > n_pix)
+        return fail(SOP_ERR_INVALID_ARG, "sizes out of range");
+    if (n_pix > 0 && (!scene_gbuf || !aligned(scene_gbuf, 16) || !out))
+        return fail(SOP_ERR_INVALID_ARG, "scene_gbuf or out NULL (or scene_gbuf not 16-byte aligned)");
+    if (n_sc > 0 && (!sc_pix || !shadow)) return fail(SOP_ERR_INVALID_ARG, "sc_pix or shadow NULL");
+    if (n_obj > 0 && (!obj_pix || !obj_rgb || !obj_gbuf || !aligned(obj_gbuf, 16)))
+        return fail(SOP_ERR_INVALID_ARG, "obj_pix, obj_rgb or obj_gbuf NULL (or obj_gbuf not 16-byte aligned)");
+    return cuda_status(sop::launch_depth_composite(scene_gbuf, obj_gbuf, n_pix, sc_pix, shadow, n_sc, obj_pix,
+                                                   obj_rgb, n_obj, out, (cudaStream_t)stream),
+                       "sop_depth_composite");
+}
+
 }  // extern "C"

@@ -89,6 +89,21 @@ cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s);
 cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp, const BakeLayout& L, char* ws,
                               cudaStream_t s);
 
+// ---- deferred front end (G-buffers, shading points, compositing) --------------
+cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, const float* rough, const float* metal,
+                                 const float* origins, int32_t n_origins, const float* dirs, int64_t n_dirs,
+                                 const sop_bake_params& bp, const BakeLayout& L, char* ws, float* out, cudaStream_t s);
+cudaError_t launch_pinhole_dirs(int32_t W, int32_t H, const float* eye, const float* target, const float* up,
+                                float fov_y_deg, float* out, cudaStream_t s);
+cudaError_t launch_panorama_dirs(int32_t W, int32_t H, float* out, cudaStream_t s);
+size_t points_ws_bytes(int64_t n_pix);
+cudaError_t launch_gbuffer_points(const float* gbuf, const float* front, int64_t n, const float* origin,
+                                  const float* dirs, float w_min, int64_t* pix, float* x, float* nrm, float* wo,
+                                  float* albedo, float* rough, float* metal, int64_t* count, char* ws, cudaStream_t s);
+cudaError_t launch_depth_composite(const float* scene_gbuf, const float* obj_gbuf, int64_t n, const int64_t* sc_pix,
+                                   const float* shadow, int64_t n_sc, const int64_t* obj_pix, const float* obj_rgb,
+                                   int64_t n_obj, float* out, cudaStream_t s);
+
 // ---- learned bake surrogate ---------------------------------------------------
 struct SurrState;
 int surr_n_params();

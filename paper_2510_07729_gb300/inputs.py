@@ -22,7 +22,8 @@ workloads:
   diff      the 'object' scene seen from 4 cameras (adjoint workload)
   deferred  the composition rebuilt from flattened (surfel-like) Gaussians
             with per-Gaussian materials, for the G-buffer front end: the
-            object (200k) and the scene (ground 700k + clutter 300k) traced
+            object (200k) and the scene (ground 700k, heights jittered, + clutter
+            300k) traced
             separately from a 1920x1080 camera, the two probe sets of
             'compose'
 
@@ -470,7 +471,9 @@ def make_deferred(seed=5):
     ng = 700_000
     gm = np.empty((ng, 3))
     gm[:, :2] = cxy + rng.uniform(-half, half, (ng, 2))
-    gm[:, 2] = zg
+    # a reconstructed ground is not exactly planar: heights jitter by 0.5%
+    # of the object size (exactly coplanar surfels would tie in depth)
+    gm[:, 2] = zg + rng.normal(0.0, 5e-3 * size, ng)
     ground = surfels(rng, gm, np.tile(np.array([0.0, 0.0, 1.0]), (ng, 1)))
     nc = 30
     ax = rng.uniform(0.05, 0.15, (nc, 3))

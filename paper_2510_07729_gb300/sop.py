@@ -38,6 +38,10 @@ class AtlasDesc(C.Structure):
                 ("probe_nrm", C.c_void_p)]
 
 
+class Materials(C.Structure):
+    _fields_ = [("albedo", C.c_void_p), ("rough", C.c_void_p), ("metal", C.c_void_p)]
+
+
 class BakeParams(C.Structure):
     _fields_ = [("t_near", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float)]
 
@@ -84,6 +88,17 @@ def load(build_if_missing: bool = True):
     lib.sop_env_importance_dirs.argtypes = [vp, i32, i32, vp, vp, sz, vp]
     lib.sop_l1_loss_grad.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.sop_adam_l1_step.argtypes = [vp, vp, vp, vp, i64, C.POINTER(AdamParams), vp]
+    lib.sop_trace_workspace_bytes.argtypes = [i64]
+    lib.sop_trace_workspace_bytes.restype = sz
+    lib.sop_trace_gbuffer.argtypes = [C.POINTER(Gaussians), C.POINTER(Materials), vp, i32, vp, i64,
+                                      C.POINTER(BakeParams), vp, vp, sz, vp]
+    f3 = C.POINTER(C.c_float)
+    lib.sop_pinhole_dirs.argtypes = [i32, i32, f3, f3, f3, C.c_float, vp, vp]
+    lib.sop_panorama_dirs.argtypes = [i32, i32, vp, vp]
+    lib.sop_gbuffer_points_workspace_bytes.argtypes = [i64]
+    lib.sop_gbuffer_points_workspace_bytes.restype = sz
+    lib.sop_gbuffer_points.argtypes = [vp, vp, i64, f3, vp, C.c_float, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.sop_depth_composite.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, i64, vp, vp]
     lib.sop_bake_workspace_bytes.argtypes = [i64, i32, i32]
     lib.sop_bake_workspace_bytes.restype = sz
     lib.sop_bake.argtypes = [C.POINTER(Gaussians), C.POINTER(AtlasDesc), C.POINTER(BakeParams), vp, sz, vp]
@@ -297,6 +312,103 @@ def _gauss(g):
         if n:
             _f32(t, shp)
     return s
+
+
+# ----------------------------------------------------------------------------
+# deferred front end: G-buffer trace, camera / panorama rays, shading points,
+# depth compositing
+# ----------------------------------------------------------------------------
+def _f3(v):
+    return (C.c_float * 3)(*[float(a) for a in v])
+
+
+class GbufferTracer:
+    """Multi-target rendering of one Gaussian set with per-Gaussian
+    materials: bins the Gaussians once (sop_bake_bin), then traces any
+    origins x directions (sop_trace_gbuffer) into [rays, 16] G-buffers
+    (C.rgb, W, N.xyz, D, A.rgb, R, M, 0, 0, 0)."""
+
+    def __init__(self, gauss, mats, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4):
+        self.gauss, self.mats = gauss, mats
+        n = gauss["mean"].shape[0]
+        self.params = (t_near, alpha_min, alpha_max, t_stop)
+        self.ws = BakeWorkspace(n, gauss["mean"].device)
+        bake_bin(gauss, self.ws, *self.params)
+        for k, shp in (("albedo", (n, 3)), ("rough", (n,)), ("metal", (n,))):
+            _f32(mats[k], shp)
+        self.m = Materials(mats["albedo"].data_ptr() if n else None, mats["rough"].data_ptr() if n else None,
+                           mats["metal"].data_ptr() if n else None)
+
+    def trace(self, origins, dirs, out=None):
+        """origins [n_o, 3], dirs [n_d, 4] float32 CUDA tensors; returns out
+        [n_o * n_d, 16]."""
+        lib = load()
+        no, nd = origins.shape[0], dirs.shape[0]
+        _f32(origins, (no, 3))
+        _f32(dirs, (nd, 4))
+        if out is None:
+            out = torch.empty((no * nd, 16), dtype=torch.float32, device=dirs.device)
+        _f32(out, (no * nd, 16))
+        g = _gauss(self.gauss)
+        bp = _bake_params(*self.params)
+        _check(lib.sop_trace_gbuffer(C.byref(g), C.byref(self.m), _ptr(origins), no, _ptr(dirs), nd, C.byref(bp),
+                                     _ptr(out), _ptr(self.ws.buf), self.ws.buf.numel(), _stream()))
+        return out
+
+
+def pinhole_dirs(W, H, eye, target, fov_y_deg, up=(0.0, 0.0, 1.0), device="cuda"):
+    out = torch.empty((H * W, 4), dtype=torch.float32, device=device)
+    _check(load().sop_pinhole_dirs(W, H, _f3(eye), _f3(target), _f3(up), float(fov_y_deg), _ptr(out), _stream()))
+    return out
+
+
+def panorama_dirs(W, H, device="cuda"):
+    out = torch.empty((H * W, 4), dtype=torch.float32, device=device)
+    _check(load().sop_panorama_dirs(W, H, _ptr(out), _stream()))
+    return out
+
+
+def gbuffer_points(gbuf, origin, dirs, w_min=0.5, front=None, count_only=False):
+    """Shading points of a G-buffer [n, 16] (see sop_gbuffer_points):
+    returns (pix [k] int64, dict x, n, wo, albedo [k,3], rough, metal [k]).
+    Reads the count back (one synchronisation)."""
+    lib = load()
+    n = gbuf.shape[0]
+    dev = gbuf.device
+    _f32(gbuf, (n, 16))
+    _f32(dirs, (n, 4))
+    if front is not None:
+        _f32(front, (n, 16))
+    pix = torch.empty(n, dtype=torch.int64, device=dev)
+    v3 = [torch.empty((n, 3), dtype=torch.float32, device=dev) for _ in range(4)]
+    v1 = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(2)]
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = _ws(lib.sop_gbuffer_points_workspace_bytes(n), dev)
+    _check(lib.sop_gbuffer_points(_ptr(gbuf), _ptr(front), n, _f3(origin), _ptr(dirs), float(w_min), _ptr(pix),
+                                  *[_ptr(t) for t in v3], *[_ptr(t) for t in v1], _ptr(cnt), _ptr(ws), ws.numel(),
+                                  _stream()))
+    k = int(cnt.item())
+    pts = dict(x=v3[0][:k], n=v3[1][:k], wo=v3[2][:k], albedo=v3[3][:k], rough=v1[0][:k], metal=v1[1][:k])
+    return pix[:k], pts
+
+
+def depth_composite(scene_gbuf, obj_gbuf, sc_pix, shadow, obj_pix, obj_rgb, out=None):
+    lib = load()
+    n = scene_gbuf.shape[0]
+    _f32(scene_gbuf, (n, 16))
+    _f32(obj_gbuf, (n, 16))
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=scene_gbuf.device)
+    ns, no = sc_pix.shape[0], obj_pix.shape[0]
+    for t in (sc_pix, obj_pix):
+        if t.dtype != torch.int64:
+            raise TypeError("pixel lists are int64")
+    _f32(shadow, (ns, 3))
+    _f32(obj_rgb, (no, 3))
+    _check(lib.sop_depth_composite(_ptr(scene_gbuf), _ptr(obj_gbuf), n, _ptr(sc_pix) if ns else None,
+                                   _ptr(shadow) if ns else None, ns, _ptr(obj_pix) if no else None,
+                                   _ptr(obj_rgb) if no else None, no, _ptr(out), _stream()))
+    return out
 
 
 def bake_workspace_bytes(n_gauss, P, R):
