@@ -88,7 +88,7 @@ def test_trace_gbuffer_small(sop, orc, t_stop):
         gb = tr.trace(cuda(eye[None]), dirs).cpu().numpy()
         o, fl = orc.trace_gbuffer(g, m, eye[None], dn, t_stop=t_stop)
         flagged = compare_gbuf(orc, gb, o, fl, what, extent=8.0)
-        assert flagged <= 0.02 * len(fl)
+        assert flagged <= 0.05 * len(fl)
         assert (o[:, 3] > 0.5).mean() > 0.1
 
 
