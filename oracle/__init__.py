@@ -329,12 +329,14 @@ GBUF_C, GBUF_W, GBUF_N, GBUF_D, GBUF_A, GBUF_R, GBUF_M = slice(0, 3), 3, slice(4
 
 
 def trace_gbuffer(gauss, mats, origins, dirs, rays=None, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99,
-                  t_stop=1e-4):
+                  t_stop=1e-4, order_allowance=False):
     """FP64 multi-target rendering (see gbuffer_oracle.c). gauss: dict of
     mean/scale/quat/opacity/rgb; mats: albedo [N,3], rough [N], metal [N];
     origins [n_o,3]; dirs [n_d,4] (or [n_d,3]) float32 unit directions;
     rays: ray ids (origin id // n_d, direction id % n_d), default all.
-    Returns (gbuf [n_rays,16], flags [n_rays])."""
+    Returns (gbuf [n_rays,16], flags [n_rays]) and, with order_allowance,
+    the per-value bound [n_rays,16] on what reordering tied hits can
+    change."""
     g = {k: _f32(gauss[k]) for k in ("mean", "scale", "quat", "opacity", "rgb")}
     al, ro, me = _f32(mats["albedo"]), _f32(mats["rough"]), _f32(mats["metal"])
     org = _f32(origins).reshape(-1, 3)
@@ -346,11 +348,13 @@ def trace_gbuffer(gauss, mats, origins, dirs, rays=None, t_near=0.0, alpha_min=1
     rays = np.arange(len(org) * nd, dtype=np.int64) if rays is None else np.ascontiguousarray(rays, np.int64)
     out = np.empty((len(rays), 16))
     fl = np.empty(len(rays), np.int32)
+    tie = np.empty((len(rays), 16))
     lib().orc_trace_gbuffer(C.c_int64(len(g["mean"])), _p(g["mean"]), _p(g["scale"]), _p(g["quat"]),
                             _p(g["opacity"]), _p(g["rgb"]), _p(al), _p(ro), _p(me), _p(org), C.c_int64(nd), _p(d),
                             C.c_int64(len(rays)), _p(rays), C.c_double(t_near), C.c_double(alpha_min),
-                            C.c_double(alpha_max), C.c_double(t_stop), _p(out), _p(fl))
-    return out, fl
+                            C.c_double(alpha_max), C.c_double(t_stop), _p(out), _p(fl),
+                            _p(tie) if order_allowance else None)
+    return (out, fl, tie) if order_allowance else (out, fl)
 
 
 def pinhole_dirs(W, H, eye, target, fov_y_deg, up=(0.0, 0.0, 1.0)):

@@ -75,12 +75,17 @@ enum {
 
 /* n_rays rays given by id: origin id / n_dirs, direction id % n_dirs (the
  * float32 table dirs [n_dirs][4], used as given). Output per ray, 16 values:
- * C.rgb, W, N.xyz, D, A.rgb, R, M, 0, 0, 0. */
+ * C.rgb, W, N.xyz, D, A.rgb, R, M, 0, 0, 0. out_tie (or NULL), per ray and
+ * value: how far any order of hits whose t* tie within 1e-6 relative (runs
+ * of consecutive hits closer than that) can move the value: swapping two
+ * adjacent hits i, j behind transmittance T changes B by
+ * T alpha_i alpha_j (b_i - b_j), so a run starting behind T_run gets
+ * 2 T_run sum over its pairs of alpha_i alpha_j |b_i - b_j|. */
 void orc_trace_gbuffer(int64_t N, const float* mean, const float* scale, const float* quat, const float* opacity,
                        const float* rgb, const float* albedo, const float* rough, const float* metal,
                        const float* origins, int64_t n_dirs, const float* dirs, int64_t n_rays, const int64_t* rays,
                        double t_near, double alpha_min, double alpha_max, double t_stop, double* out,
-                       int32_t* out_flags)
+                       int32_t* out_flags, double* out_tie)
 {
     double* Mg = (double*)malloc(sizeof(double) * 9 * (size_t)(N > 0 ? N : 1));
     double* Ng = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
@@ -99,6 +104,8 @@ void orc_trace_gbuffer(int64_t N, const float* mean, const float* scale, const f
     {
         size_t cap = 1024;
         gb_hit* hits = (gb_hit*)malloc(sizeof(gb_hit) * cap);
+        double* pay = (double*)malloc(sizeof(double) * 16 * cap); /* b_i of the composited hits */
+        double* tb = (double*)malloc(sizeof(double) * cap);       /* transmittance before hit i */
 #pragma omp for schedule(dynamic, 4)
         for (int64_t r = 0; r < n_rays; ++r) {
             const int64_t id = rays[r];
@@ -132,6 +139,8 @@ void orc_trace_gbuffer(int64_t N, const float* mean, const float* scale, const f
                 if (nh == cap) {
                     cap *= 2;
                     hits = (gb_hit*)realloc(hits, sizeof(gb_hit) * cap);
+                    pay = (double*)realloc(pay, sizeof(double) * 16 * cap);
+                    tb = (double*)realloc(tb, sizeof(double) * cap);
                 }
                 hits[nh].t = ts;
                 hits[nh].alpha = resp < alpha_max ? resp : alpha_max;
@@ -141,6 +150,7 @@ void orc_trace_gbuffer(int64_t N, const float* mean, const float* scale, const f
             qsort(hits, nh, sizeof(gb_hit), gb_hit_cmp);
             double T = 1.0, B[16];
             memset(B, 0, sizeof(B));
+            size_t used = 0;
             for (size_t k = 0; k < nh; ++k) {
                 if (k + 1 < nh && hits[k + 1].t - hits[k].t <= 1e-6 * fabs(hits[k + 1].t)) flags |= GB_FLAG_ORDER;
                 const int64_t g = hits[k].idx;
@@ -149,22 +159,45 @@ void orc_trace_gbuffer(int64_t N, const float* mean, const float* scale, const f
                 const double nd = ng[0] * d[0] + ng[1] * d[1] + ng[2] * d[2];
                 if (fabs(nd) < 1e-4) flags |= GB_FLAG_GRAZING;
                 const double sg = nd > 0.0 ? -1.0 : 1.0;
+                double* b = pay + 16 * k;
+                memset(b, 0, 16 * sizeof(double));
                 for (int c = 0; c < 3; ++c) {
-                    B[c] += wk * rgb[3 * g + c];
-                    B[4 + c] += wk * sg * ng[c];
-                    B[8 + c] += wk * albedo[3 * g + c];
+                    b[c] = rgb[3 * g + c];
+                    b[4 + c] = sg * ng[c];
+                    b[8 + c] = albedo[3 * g + c];
                 }
-                B[3] += wk;
-                B[7] += wk * hits[k].t;
-                B[11] += wk * rough[g];
-                B[12] += wk * metal[g];
+                b[3] = 1.0;
+                b[7] = hits[k].t;
+                b[11] = rough[g];
+                b[12] = metal[g];
+                for (int c = 0; c < 16; ++c) B[c] += wk * b[c];
+                tb[k] = T;
+                used = k + 1;
                 T *= (1.0 - hits[k].alpha);
                 if (t_stop > 0.0 && fabs(T - t_stop) <= 1e-3 * t_stop) flags |= GB_FLAG_TSTOP;
                 if (T < t_stop) break;
             }
             memcpy(out + 16 * (size_t)r, B, sizeof(B));
             out_flags[r] = flags;
+            if (out_tie) {
+                double* a = out_tie + 16 * (size_t)r;
+                memset(a, 0, 16 * sizeof(double));
+                size_t s0 = 0;
+                while (s0 < used) {
+                    size_t s1 = s0 + 1; /* the run is [s0, s1) */
+                    while (s1 < nh && hits[s1].t - hits[s1 - 1].t <= 1e-6 * fabs(hits[s1].t)) ++s1;
+                    if (s1 > used) s1 = used;
+                    for (size_t i = s0; i < s1; ++i)
+                        for (size_t j = i + 1; j < s1; ++j) {
+                            const double aa = 2.0 * tb[s0] * hits[i].alpha * hits[j].alpha;
+                            for (int c = 0; c < 16; ++c) a[c] += aa * fabs(pay[16 * i + c] - pay[16 * j + c]);
+                        }
+                    s0 = s1 > s0 + 1 ? s1 : s0 + 1;
+                }
+            }
         }
+        free(tb);
+        free(pay);
         free(hits);
     }
     free(Ng);

@@ -227,3 +227,30 @@ def test_depth_composite_rules(orc):
     a = float(og[5, 3])
     want = a * obj_rgb[0].astype(np.float64) + (1 - a) * (sg[5, 0:3].astype(np.float64) * shadow[5])
     np.testing.assert_allclose(out[5], want, rtol=1e-14)
+
+
+def test_order_allowance_bounds_a_swap_of_tied_hits(orc):
+    """Two isotropic Gaussians with the same t* (mirror images across the
+    ray; other orientations, so other normals): the
+    oracle orders them by index, so swapping their indices swaps their
+    order. The reported allowance is twice the change, T a1 a2 |b1 - b2|."""
+    s, r = 0.05, 0.02
+    g = gauss([[2.0, r, 0], [2.0, -r, 0]], [[s] * 3, [s] * 3], [[1, 0, 0, 0], [0.9, 0.3, 0.1, 0.2]],
+              [0.8, 0.6], [[0.9, 0.1, 0.2], [0.1, 0.7, 0.5]])
+    m = mats(2, 9)
+    sw = {k: v[::-1].copy() for k, v in g.items()}
+    msw = {k: v[::-1].copy() for k, v in m.items()}
+    ray = np.array([[1, 0, 0, 0]], F)
+    a, fa, ta = orc.trace_gbuffer(g, m, [[0, 0, 0]], ray, t_stop=0.0, order_allowance=True)
+    b, fb, tb = orc.trace_gbuffer(sw, msw, [[0, 0, 0]], ray, t_stop=0.0, order_allowance=True)
+    assert fa[0] & orc.FLAG_ORDER and fb[0] & orc.FLAG_ORDER
+    diff = np.abs(a[0] - b[0])
+    assert diff[0:3].max() > 1e-3  # the order matters for the colour
+    assert a[0, 3] == pytest.approx(b[0, 3], rel=1e-15)  # not for W
+    np.testing.assert_allclose(ta[0], 2 * diff, rtol=1e-9, atol=1e-15)
+    np.testing.assert_allclose(tb[0], ta[0], rtol=1e-9, atol=1e-15)
+    # hits that do not tie get no allowance
+    far = gauss([[2.0, r, 0], [3.0, -r, 0]], [[s] * 3, [s] * 3], [[1, 0, 0, 0]] * 2, [0.8, 0.6],
+                [[0.9, 0.1, 0.2], [0.1, 0.7, 0.5]])
+    _, ff, tf = orc.trace_gbuffer(far, m, [[0, 0, 0]], ray, t_stop=0.0, order_allowance=True)
+    assert ff[0] == 0 and not tf.any()
