@@ -730,15 +730,26 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
     const GaussGrid G = *k.grid;
     const float3 go = f3(G.origin[0], G.origin[1], G.origin[2]);
     const float3 sp = f3(G.bmax[0] - G.origin[0], G.bmax[1] - G.origin[1], G.bmax[2] - G.origin[2]);
-    // persistent warps: each takes the next texel ray from a global counter,
-    // so long rays (escaping the object) do not hold up short ones; the next
-    // ray's number is fetched while the current ray is traced
+    // persistent warps: each takes its next rays from a global counter, so
+    // long rays (escaping the object) do not hold up short ones. Rays are
+    // taken kBatch at a time (camera rays are mostly short: one counter
+    // update per ray would serialise on it); the next batch's number is
+    // fetched while the current batch is traced
+    constexpr int kBatch = OUT == kTraceGbuf ? 8 : 1;
     unsigned long long rr = 0;
-    if (lane == 0) rr = atomicAdd(k.stats, 1ull);
+    if (lane == 0) rr = atomicAdd(k.stats, (unsigned long long)kBatch);
+    int64_t base = 0;
+    int sub = kBatch;
+    // work counters, summed over the warp's rays and added once at the end
+    unsigned long long t_eval = 0, t_comp = 0, t_test = 0;
     for (;;) {
-    const int64_t ray = (int64_t)__shfl_sync(0xffffffffu, rr, 0);
+    if (sub == kBatch) {
+        base = (int64_t)__shfl_sync(0xffffffffu, rr, 0);
+        sub = 0;
+        if (lane == 0 && base < total) rr = atomicAdd(k.stats, (unsigned long long)kBatch);
+    }
+    const int64_t ray = base + sub++;
     if (ray >= total) break;
-    if (lane == 0) rr = atomicAdd(k.stats, 1ull);
     const int p = (int)(ray / RR), t = (int)(ray % RR);
     const float4 d4 = __ldg(k.dirs + t);
     const float3 d = f3(d4.x, d4.y, d4.z);
@@ -915,10 +926,10 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
             o4[1] = make_float4(v[0], v[1], v[2], Dacc);
             o4[2] = make_float4(v[3], v[4], v[5], v[6]);
             o4[3] = make_float4(v[7], 0.f, 0.f, 0.f);
-            atomicAdd(k.stats + 1, (unsigned long long)acc.n_eval);
-            atomicAdd(k.stats + 2, (unsigned long long)acc.n_comp);
-            atomicAdd(k.stats + 4, (unsigned long long)acc.n_test);
         }
+        t_eval += (unsigned long long)acc.n_eval;
+        t_comp += (unsigned long long)acc.n_comp;
+        t_test += (unsigned long long)acc.n_test;
         continue;
     }
     if (lane == 0) {
@@ -940,11 +951,16 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
             default: reinterpret_cast<__nv_fp8_e4m3*>(k.depth)[ti] = __nv_fp8_e4m3(dv); break;
             }
         }
-        atomicAdd(k.stats + 1, (unsigned long long)acc.n_eval);
-        atomicAdd(k.stats + 2, (unsigned long long)acc.n_comp);
-        atomicAdd(k.stats + 4, (unsigned long long)acc.n_test);
     }
+    t_eval += (unsigned long long)acc.n_eval;
+    t_comp += (unsigned long long)acc.n_comp;
+    t_test += (unsigned long long)acc.n_test;
     }  // next ray
+    if (lane == 0) {
+        atomicAdd(k.stats + 1, t_eval);
+        atomicAdd(k.stats + 2, t_comp);
+        atomicAdd(k.stats + 4, t_test);
+    }
 }
 
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s)
