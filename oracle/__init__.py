@@ -396,3 +396,15 @@ def depth_composite(scene_gbuf, obj_gbuf, sc_pix, shadow, obj_pix, obj_rgb):
                               _p(np.ascontiguousarray(sc_pix, np.int64)), _p(_f32(shadow)), C.c_int64(len(obj_pix)),
                               _p(np.ascontiguousarray(obj_pix, np.int64)), _p(_f32(obj_rgb)), _p(out))
     return out
+
+
+def fps(pts, k, start=0, nrm=None, offset=0.0):
+    """Farthest point sampling with exact integer keys (see orc_fps):
+    returns (idx [k] int64, positions [k,3] offset along nrm)."""
+    p = _f32(pts).reshape(-1, 3)
+    nr = None if nrm is None else _f32(nrm).reshape(-1, 3)
+    idx = np.empty(k, np.int64)
+    pos = np.empty((k, 3))
+    lib().orc_fps(C.c_int64(len(p)), _p(p), None if nr is None else _p(nr), C.c_int32(k), C.c_int64(start),
+                  C.c_double(offset), _p(idx), _p(pos))
+    return idx, pos

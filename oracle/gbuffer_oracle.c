@@ -13,6 +13,9 @@
  *   orc_gbuffer_points   shading points of a G-buffer: position from the
  *                        unbiased depth D / W (Sec. 3.1), normal N / |N|,
  *                        materials per unit weight (Sec. 4.3)
+ *   orc_fps              automatic placement of SOPs (Sec. 3.2): farthest
+ *                        point sampling with exact integer keys, offset
+ *                        along the normals
  *   orc_depth_composite  the composed frame: the scene colour times its
  *                        shadow ratio (Eq. 9), the relit object over it where
  *                        it is in front (Sec. 4.3, depth compositing)
@@ -311,4 +314,48 @@ void orc_depth_composite(int64_t n_pix, const float* scene_gbuf, const float* ob
         const double a = obj_gbuf[16 * (size_t)p + 3];
         for (int c = 0; c < 3; ++c) out[3 * p + c] = a * obj_rgb[3 * k + c] + (1.0 - a) * out[3 * p + c];
     }
+}
+
+/* Automatic placement of SOPs (Sec. 3.2): farthest point sampling of a
+ * surface point cloud, then an offset along the normals. Distances are the
+ * exact integer squared distances of positions quantised to 2^-20 (the
+ * query's keys), so every choice is exact: the first point is `start`;
+ * each next one maximises the smallest key to the points already chosen,
+ * ties to the lower index. out_pos[i] = pts[idx] + offset * nrm[idx] (when
+ * out_pos and nrm are given). */
+static int64_t gb_quant(float v) { return (int64_t)nearbyint((double)v * 1048576.0); }
+
+void orc_fps(int64_t n, const float* pts, const float* nrm, int32_t k, int64_t start, double offset,
+             int64_t* out_idx, double* out_pos)
+{
+    int64_t* q = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)(n > 0 ? n : 1));
+    uint64_t* dmin = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) q[3 * i + a] = gb_quant(pts[3 * i + a]);
+        dmin[i] = UINT64_MAX;
+    }
+    int64_t cur = start;
+    for (int32_t it = 0; it < k; ++it) {
+        out_idx[it] = cur;
+        uint64_t best = 0;
+        int64_t bi = -1;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t dx = q[3 * i] - q[3 * cur], dy = q[3 * i + 1] - q[3 * cur + 1], dz = q[3 * i + 2] - q[3 * cur + 2];
+            const uint64_t key = (uint64_t)(dx * dx) + (uint64_t)(dy * dy) + (uint64_t)(dz * dz);
+            if (key < dmin[i]) dmin[i] = key;
+            if (bi < 0 || dmin[i] > best) {
+                best = dmin[i];
+                bi = i;
+            }
+        }
+        cur = bi;
+    }
+    if (out_pos)
+        for (int32_t it = 0; it < k; ++it) {
+            const int64_t i = out_idx[it];
+            for (int a = 0; a < 3; ++a)
+                out_pos[3 * it + a] = (double)pts[3 * i + a] + (nrm ? offset * (double)nrm[3 * i + a] : 0.0);
+        }
+    free(dmin);
+    free(q);
 }
