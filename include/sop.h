@@ -505,6 +505,25 @@ sop_status sop_depth_composite(const float* scene_gbuf, const float* obj_gbuf, i
                                const float* shadow, int64_t n_sc, const int64_t* obj_pix, const float* obj_rgb,
                                int64_t n_obj, float* out, void* stream);
 
+/* ---- automatic placement of SOPs (Sec. 3.2) ---------------------------------- */
+
+/* Workspace bytes for sop_place_probes on n points. */
+size_t sop_place_probes_workspace_bytes(int64_t n_points);
+
+/* Farthest point sampling of the surface points pts [n][3] (device; within
+ * +-1024), then the offset of each chosen point along its normal (Sec. 3.2:
+ * probes slightly off the surface). Distances are the exact integer squared
+ * distances of positions quantised to 2^-20: the first point is `start`,
+ * each next one maximises the smallest distance to the points already
+ * chosen, ties to the lower index; the result is that of a sequential FPS
+ * and the same on every run. out_idx [k] (int64, device): the chosen
+ * points in order; out_pos [k][3] (device, or NULL): pts + offset nrm,
+ * computed in double and rounded once (nrm [n][3] device, or NULL: no
+ * offset). 1 <= k <= n, 0 <= start < n. Runs as one thread-block cluster
+ * (8 CTAs) for all k iterations. Asynchronous. */
+sop_status sop_place_probes(const float* pts, const float* nrm, int64_t n_points, int32_t k, int64_t start,
+                            float offset, int64_t* out_idx, float* out_pos, void* ws, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -684,4 +684,25 @@ sop_status sop_depth_composite(const float* scene_gbuf, const float* obj_gbuf, i
                        "sop_depth_composite");
 }
 
+size_t sop_place_probes_workspace_bytes(int64_t n_points)
+{
+    if (n_points < 1 || n_points > (int64_t)INT32_MAX) return 0;
+    return sop::fps_ws_bytes(n_points);
+}
+
+sop_status sop_place_probes(const float* pts, const float* nrm, int64_t n_points, int32_t k, int64_t start,
+                            float offset, int64_t* out_idx, float* out_pos, void* ws, size_t ws_bytes, void* stream)
+{
+    if (n_points < 1 || n_points > (int64_t)INT32_MAX) return fail(SOP_ERR_INVALID_ARG, "n_points out of range");
+    if (k < 1 || (int64_t)k > n_points) return fail(SOP_ERR_INVALID_ARG, "k = %d outside [1, n_points]", k);
+    if (start < 0 || start >= n_points) return fail(SOP_ERR_INVALID_ARG, "start outside [0, n_points)");
+    if (!pts || !out_idx) return fail(SOP_ERR_INVALID_ARG, "pts or out_idx is NULL");
+    if (!isfinite(offset)) return fail(SOP_ERR_INVALID_ARG, "offset must be finite");
+    sop_status st = check_ws(ws, ws_bytes, sop::fps_ws_bytes(n_points));
+    if (st != SOP_OK) return st;
+    return cuda_status(sop::launch_fps(pts, nrm, n_points, k, start, offset, out_idx, out_pos, (char*)ws,
+                                       (cudaStream_t)stream),
+                       "sop_place_probes");
+}
+
 }  // extern "C"

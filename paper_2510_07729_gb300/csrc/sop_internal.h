@@ -104,6 +104,11 @@ cudaError_t launch_depth_composite(const float* scene_gbuf, const float* obj_gbu
                                    const float* shadow, int64_t n_sc, const int64_t* obj_pix, const float* obj_rgb,
                                    int64_t n_obj, float* out, cudaStream_t s);
 
+// ---- automatic probe placement (FPS) ----------------------------------------------
+size_t fps_ws_bytes(int64_t n);
+cudaError_t launch_fps(const float* pts, const float* nrm, int64_t n, int32_t k, int64_t start, float offset,
+                       int64_t* out_idx, float* out_pos, char* ws, cudaStream_t s);
+
 // ---- learned bake surrogate ---------------------------------------------------
 struct SurrState;
 int surr_n_params();

@@ -99,6 +99,9 @@ def load(build_if_missing: bool = True):
     lib.sop_gbuffer_points_workspace_bytes.restype = sz
     lib.sop_gbuffer_points.argtypes = [vp, vp, i64, f3, vp, C.c_float, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.sop_depth_composite.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, i64, vp, vp]
+    lib.sop_place_probes_workspace_bytes.argtypes = [i64]
+    lib.sop_place_probes_workspace_bytes.restype = sz
+    lib.sop_place_probes.argtypes = [vp, vp, i64, i32, i64, C.c_float, vp, vp, vp, sz, vp]
     lib.sop_bake_workspace_bytes.argtypes = [i64, i32, i32]
     lib.sop_bake_workspace_bytes.restype = sz
     lib.sop_bake.argtypes = [C.POINTER(Gaussians), C.POINTER(AtlasDesc), C.POINTER(BakeParams), vp, sz, vp]
@@ -409,6 +412,23 @@ def depth_composite(scene_gbuf, obj_gbuf, sc_pix, shadow, obj_pix, obj_rgb, out=
                                    _ptr(shadow) if ns else None, ns, _ptr(obj_pix) if no else None,
                                    _ptr(obj_rgb) if no else None, no, _ptr(out), _stream()))
     return out
+
+
+def place_probes(pts, k, nrm=None, offset=0.0, start=0):
+    """Automatic placement (sop_place_probes): farthest point sampling of
+    pts [n,3] with exact integer keys, offset along nrm [n,3]. Returns
+    (idx [k] int64, positions [k,3])."""
+    lib = load()
+    n = pts.shape[0]
+    _f32(pts, (n, 3))
+    if nrm is not None:
+        _f32(nrm, (n, 3))
+    idx = torch.empty(k, dtype=torch.int64, device=pts.device)
+    pos = torch.empty((k, 3), dtype=torch.float32, device=pts.device)
+    ws = _ws(lib.sop_place_probes_workspace_bytes(n), pts.device)
+    _check(lib.sop_place_probes(_ptr(pts), _ptr(nrm), n, k, start, float(offset), _ptr(idx), _ptr(pos), _ptr(ws),
+                                ws.numel(), _stream()))
+    return idx, pos
 
 
 def bake_workspace_bytes(n_gauss, P, R):
