@@ -45,6 +45,11 @@ QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He,
     L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)S);
     L.idx = o;        o = align256(o + sizeof(int32_t) * (size_t)M * K);
     L.w = o;          o = align256(o + sizeof(float) * (size_t)M * K);
+    // adjoint only: points grouped by nearest probe, and the environment
+    // gradient as float4 texels
+    L.perm = o;       o = align256(o + sizeof(int32_t) * (size_t)M);
+    L.bucket = o;     o = align256(o + sizeof(int32_t) * (size_t)(P + 1));
+    L.genv4 = o;      o = align256(o + sizeof(float4) * (size_t)He * We);
     L.total = o;
     return L;
 }

@@ -15,7 +15,7 @@ struct GaussGrid;
 
 // ---- query ----------------------------------------------------------------
 struct QueryLayout {
-    size_t grid_hdr, cell_start, cell_cnt, entries, env4, envq, quads, dirs, idx, w, total;
+    size_t grid_hdr, cell_start, cell_cnt, entries, env4, envq, quads, dirs, idx, w, perm, bucket, genv4, total;
     int32_t cells_cap, g_axis;
 };
 QueryLayout query_layout(int32_t P, int64_t M, int32_t K, int32_t S, int32_t He, int32_t We, int32_t R,

@@ -180,3 +180,24 @@ def test_autograd_function(sop):
                                  (out - target).detach().contiguous())
     for t, k in ((a, "albedo"), (r, "rough"), (mt, "metal"), (n, "normal"), (env, "env"), (mp, "maps")):
         assert torch.allclose(t.grad, g[k], rtol=1e-5, atol=1e-7 * g[k].abs().max().item()), k
+
+
+@pytest.mark.parametrize("R", [32, 64])
+def test_adjoint_scatter_paths(sop, orc, R):
+    """Probe maps of 32x32 (6 shared-memory probe slots a CTA, so the 8
+    probes of the points overflow them into global atomics) and 64x64 (no
+    slots: global atomics only): the same gradients as the oracle."""
+    c = I.make_tiny()
+    rng = np.random.default_rng(60 + R)
+    pts = tilted({k: c[k] for k in KEYS}, rng)
+    maps = I.smooth_maps(rng, 64, R)
+    go = rng.standard_normal((len(pts["x"]), 3))
+    at = atlas(sop, c["probe_pos"], maps)
+    g = gpu_grads(sop, pts, at, c["env"], 8, 64, go)
+    o = orc_grads(orc, pts, c["probe_pos"], maps, c["env"], 8, 64, go)
+    for k in ("albedo", "rough", "metal"):
+        assert_close(g[k], o[k], rtol=1e-4, absolute=TERM_FRAC * o["abs_" + k], what=k)
+    assert_close(g["normal"], o["normal"], rtol=1e-4, absolute=TERM_FRAC * o["abs_normal"][:, None], what="normal")
+    assert_close(g["env"], o["env"], rtol=1e-4, floor=0, absolute=1e-6 * np.abs(o["env"]).max(), what="env")
+    om = maps_of(o)
+    assert_close(g["maps"], om, rtol=1e-4, floor=0, absolute=1e-6 * np.abs(om).max(), what="maps")
