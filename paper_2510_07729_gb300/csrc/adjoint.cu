@@ -129,7 +129,13 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
     float ga[3] = {0.f, 0.f, 0.f}, gr = 0.f, gm = 0.f, gn[3] = {0.f, 0.f, 0.f};
     const float Rf = (float)a.R;
 
-    for (int i = 0; i < a.S; ++i) {
+    // the lanes of a warp (neighbouring points, nearly the same frame) start
+    // S/32 directions apart, so that at each step they scatter into other
+    // texels instead of all into the same ones (the order of the sum over
+    // directions only changes rounding)
+    const int i_first = (int)(((threadIdx.x & 31) * (int64_t)a.S) >> 5);
+    for (int ii = 0; ii < a.S; ++ii) {
+        const int i = ii + i_first < a.S ? ii + i_first : ii + i_first - a.S;
         const float4 l = s_dirs[i];
         const float3 w = f3(fmaf(l.x, tt.x, fmaf(l.y, bb.x, l.z * n.x)), fmaf(l.x, tt.y, fmaf(l.y, bb.y, l.z * n.y)),
                             fmaf(l.x, tt.z, fmaf(l.y, bb.z, l.z * n.z)));
