@@ -20,6 +20,8 @@
 // float4 atomic (probes beyond the slots go straight to global atomics).
 // The environment gradient is accumulated as float4 texels (4 vector
 // atomics a direction instead of 12 scalar ones) and folded into g_env.
+#include <stdlib.h>
+
 #include "sop_device.cuh"
 #include "sop_internal.h"
 
@@ -494,6 +496,12 @@ cudaError_t launch_adjoint(const QueryArgs& a, const QueryLayout& L, char* ws, c
     const int64_t slot_bytes = (int64_t)a.R * a.R * (int64_t)sizeof(float4);
     const int64_t cap = (kAdjSmemBudget - (int64_t)sizeof(float4) * a.S) / slot_bytes;
     k.cap = cap < 4 ? 0 : (int32_t)(cap < kAdjCapMax ? cap : kAdjCapMax);
+    // SOP_ADJOINT_SLOTS caps the shared-memory probe slots (0: global atomics only), for tuning
+    static const int slots_env = [] {
+        const char* v = getenv("SOP_ADJOINT_SLOTS");
+        return v ? atoi(v) : -1;
+    }();
+    if (slots_env >= 0 && slots_env < k.cap) k.cap = slots_env < 4 ? 0 : slots_env;
     cudaError_t e = cudaMemsetAsync(bucket, 0, sizeof(int32_t) * (size_t)(a.P + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(k.genv4, 0, sizeof(float4) * (size_t)a.He * a.We, s);
     if (e != cudaSuccess) return e;
