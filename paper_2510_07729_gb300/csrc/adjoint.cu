@@ -12,14 +12,11 @@
 // compact [P][R][R] maps. Environment and probe gradients are scattered with
 // float atomics (order-nondeterministic sums).
 //
-// Scatter traffic: points are taken grouped by their nearest probe (a
-// counting sort), so the 128 points of a CTA share most of their probes.
-// Each CTA gives its distinct probes shared-memory slots (a bounded
-// linear-probing table) and accumulates their map gradients there; at the
-// end each nonzero slot texel is added to the global gradient with one
-// float4 atomic (probes beyond the slots go straight to global atomics).
-// The environment gradient is accumulated as float4 texels (4 vector
-// atomics a direction instead of 12 scalar ones) and folded into g_env.
+// Scatter traffic (bound by L2 atomics): neighbouring points in a warp
+// start their direction loops S/32 apart, so that they do not update the
+// same probe texels at the same step; the environment gradient is
+// accumulated as float4 texels (4 vector atomics a direction instead of 12
+// scalar ones) and folded into g_env at the end.
 #include <stdlib.h>
 
 #include "sop_device.cuh"
@@ -41,34 +38,20 @@ struct AdjK {
     const float* grad_out;
     float *g_albedo, *g_rough, *g_metal, *g_normal, *g_env;
     float4* g_maps;  // [P][R][R] (d rgb, d O)
-    const int32_t* perm;  // points grouped by nearest probe
-    int32_t cap;          // shared-memory probe slots of a CTA (0: none)
+    const int32_t* perm;  // order in which the points are taken
     float4* genv4;        // [He][We] environment gradient (rgb, -)
 };
-
-constexpr int kAdjCapMax = 64;
-// dynamic shared memory of a CTA (directions + slots): two CTAs fit an SM
-constexpr int64_t kAdjSmemBudget = 104 * 1024;
 
 template <int DT, int KMAX>
 __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
 {
     using TX = Texel<DT>;
-    extern __shared__ float4 s_dyn[];  // [S] directions, then [cap][R*R] probe-map gradient slots
-    __shared__ int32_t s_slot_pid[kAdjCapMax];
-    float4* s_dirs = s_dyn;
-    float4* s_acc = s_dyn + a.S;
-    const int RR = a.R * a.R;
+    extern __shared__ float4 s_dirs[];
     for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_dirs[i] = a.dirs[i];
-    for (int i = threadIdx.x; i < a.cap * RR; i += blockDim.x) s_acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = threadIdx.x; i < kAdjCapMax; i += blockDim.x) s_slot_pid[i] = -1;
     __syncthreads();
-    // threads past the last point redo the last point with a zero upstream
-    // gradient (every scattered term is then zero) and write nothing: all
-    // threads reach the CTA barriers
     const int64_t slot_m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = slot_m < a.M;
-    const int64_t m = __ldg(a.perm + (active ? slot_m : a.M - 1));
+    if (slot_m >= a.M) return;
+    const int64_t m = a.perm ? (int64_t)__ldg(a.perm + slot_m) : slot_m;
 
     const float3 nr = load3(a.n, m);
     const float nl = sqrtf(dot3(nr, nr));
@@ -78,7 +61,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
     const float3 wo = load3(a.wo, m);
     const float3 alb = load3(a.albedo, m);
     const float r = __ldg(a.rough + m), mt = __ldg(a.metal + m);
-    const float3 go = active ? load3(a.grad_out, m) : f3(0.f, 0.f, 0.f);
+    const float3 go = load3(a.grad_out, m);
     const int RS = a.R + 2;
     const typename TX::raw* atlas = reinterpret_cast<const typename TX::raw*>(a.rgbo);
     int32_t pid[KMAX];
@@ -90,24 +73,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
         W[k] = on ? __ldg(a.w + m * a.K + k) : 0.f;
         gW[k] = 0.f;
     }
-    // shared-memory slots of this point's probes (-1: global atomics)
-    int sl[KMAX];
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-        sl[k] = -1;
-        if (active && k < a.K && W[k] != 0.f && a.cap > 0) {
-            int h = pid[k] % a.cap;
-            for (int t = 0; t < a.cap; ++t) {
-                const int old = atomicCAS(&s_slot_pid[h], -1, pid[k]);
-                if (old == -1 || old == pid[k]) {
-                    sl[k] = h;
-                    break;
-                }
-                h = h + 1 == a.cap ? 0 : h + 1;
-            }
-        }
-    }
-    __syncthreads();
+
     // per-point BRDF constants
     const float al = r * r, a2 = al * al, kk = (r + 1.f) * (r + 1.f) * 0.125f;
     const float NdotVraw = dot3(n, wo);
@@ -267,24 +233,14 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
                     int si, sj;
                     oct_wrap(a.R, i0 - 1 + (qq & 1), j0 - 1 + (qq >> 1), si, sj);
                     const float c = Wk * q[qq];
-                    const float4 v = make_float4(gLin[0] * c, gLin[1] * c, gLin[2] * c, gO * c);
-                    if (sl[k] >= 0) {
-                        float* p = reinterpret_cast<float*>(s_acc + (sl[k] * RR + sj * a.R + si));
-                        atomicAdd(p, v.x);
-                        atomicAdd(p + 1, v.y);
-                        atomicAdd(p + 2, v.z);
-                        atomicAdd(p + 3, v.w);
-                    } else if (active) {
-                        atomicAdd(a.g_maps + ((int64_t)pid[k] * a.R + sj) * a.R + si, v);
-                    }
+                    atomicAdd(a.g_maps + ((int64_t)pid[k] * a.R + sj) * a.R + si,
+                              make_float4(gLin[0] * c, gLin[1] * c, gLin[2] * c, gO * c));
                 }
             }
         }
-        if (active) {
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq)
-                atomicAdd(a.genv4 + ei[qq] / 3, make_float4(gLd[0] * ew[qq], gLd[1] * ew[qq], gLd[2] * ew[qq], 0.f));
-        }
+        for (int qq = 0; qq < 4; ++qq)
+            atomicAdd(a.genv4 + ei[qq] / 3, make_float4(gLd[0] * ew[qq], gLd[1] * ew[qq], gLd[2] * ew[qq], 0.f));
         // ---- d/dw ---------------------------------------------------------------
         // octahedral coordinates: uv = (p + 1)/2, p = w.xy/|w|_1 (folded below)
         float gw[3];
@@ -368,26 +324,15 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
         }
     }
     // through n = n_raw / |n_raw|
-    if (active) {
-        const float ng = gn[0] * n.x + gn[1] * n.y + gn[2] * n.z;
-        a.g_normal[3 * m] = (gn[0] - ng * n.x) / nl;
-        a.g_normal[3 * m + 1] = (gn[1] - ng * n.y) / nl;
-        a.g_normal[3 * m + 2] = (gn[2] - ng * n.z) / nl;
-        a.g_albedo[3 * m] = ga[0];
-        a.g_albedo[3 * m + 1] = ga[1];
-        a.g_albedo[3 * m + 2] = ga[2];
-        a.g_rough[m] = gr;
-        a.g_metal[m] = gm;
-    }
-    // the CTA's probe-map gradients: one float4 atomic per nonzero texel
-    __syncthreads();
-    for (int e = threadIdx.x; e < a.cap * RR; e += blockDim.x) {
-        const int ps = s_slot_pid[e / RR];
-        if (ps < 0) continue;
-        const float4 v = s_acc[e];
-        if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
-            atomicAdd(a.g_maps + (int64_t)ps * RR + e % RR, v);
-    }
+    const float ng = gn[0] * n.x + gn[1] * n.y + gn[2] * n.z;
+    a.g_normal[3 * m] = (gn[0] - ng * n.x) / nl;
+    a.g_normal[3 * m + 1] = (gn[1] - ng * n.y) / nl;
+    a.g_normal[3 * m + 2] = (gn[2] - ng * n.z) / nl;
+    a.g_albedo[3 * m] = ga[0];
+    a.g_albedo[3 * m + 1] = ga[1];
+    a.g_albedo[3 * m + 2] = ga[2];
+    a.g_rough[m] = gr;
+    a.g_metal[m] = gm;
 }
 
 // ---- grouping of the points by nearest probe (counting sort) -----------------
@@ -440,7 +385,7 @@ __global__ void env_fold_kernel(const float4* __restrict__ genv4, int64_t n, flo
 template <int DT, int KMAX>
 static cudaError_t adjoint_launch(const AdjK& k, cudaStream_t s)
 {
-    const size_t smem = sizeof(float4) * ((size_t)k.S + (size_t)k.cap * k.R * k.R);
+    const size_t smem = sizeof(float4) * (size_t)k.S;
     auto fn = adjoint_kernel<DT, KMAX>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -493,22 +438,22 @@ cudaError_t launch_adjoint(const QueryArgs& a, const QueryLayout& L, char* ws, c
     int32_t* bucket = reinterpret_cast<int32_t*>(ws + L.bucket);
     k.perm = perm;
     k.genv4 = reinterpret_cast<float4*>(ws + L.genv4);
-    const int64_t slot_bytes = (int64_t)a.R * a.R * (int64_t)sizeof(float4);
-    const int64_t cap = (kAdjSmemBudget - (int64_t)sizeof(float4) * a.S) / slot_bytes;
-    k.cap = cap < 4 ? 0 : (int32_t)(cap < kAdjCapMax ? cap : kAdjCapMax);
-    // SOP_ADJOINT_SLOTS caps the shared-memory probe slots (0: global atomics only), for tuning
-    static const int slots_env = [] {
-        const char* v = getenv("SOP_ADJOINT_SLOTS");
-        return v ? atoi(v) : -1;
+    // SOP_ADJOINT_GROUP=0 takes the points in their given order, for tuning
+    static const int group = [] {
+        const char* v = getenv("SOP_ADJOINT_GROUP");
+        return v ? atoi(v) : 1;
     }();
-    if (slots_env >= 0 && slots_env < k.cap) k.cap = slots_env < 4 ? 0 : slots_env;
     cudaError_t e = cudaMemsetAsync(bucket, 0, sizeof(int32_t) * (size_t)(a.P + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(k.genv4, 0, sizeof(float4) * (size_t)a.He * a.We, s);
     if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)((a.M + 255) / 256);
-    perm_count_kernel<<<nb, 256, 0, s>>>(k.idx, a.K, a.M, bucket);
-    perm_scan_kernel<<<1, 1024, 0, s>>>(bucket, a.P);
-    perm_fill_kernel<<<nb, 256, 0, s>>>(k.idx, a.K, a.M, bucket, perm);
+    if (group) {
+        perm_count_kernel<<<nb, 256, 0, s>>>(k.idx, a.K, a.M, bucket);
+        perm_scan_kernel<<<1, 1024, 0, s>>>(bucket, a.P);
+        perm_fill_kernel<<<nb, 256, 0, s>>>(k.idx, a.K, a.M, bucket, perm);
+    } else {
+        k.perm = nullptr;
+    }
     switch (a.rgbo_dtype) {
     case SOP_F32: e = adjoint_k<SOP_F32>(k, s); break;
     case SOP_BF16: e = adjoint_k<SOP_BF16>(k, s); break;

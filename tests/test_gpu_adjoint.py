@@ -183,10 +183,9 @@ def test_autograd_function(sop):
 
 
 @pytest.mark.parametrize("R", [32, 64])
-def test_adjoint_scatter_paths(sop, orc, R):
-    """Probe maps of 32x32 (6 shared-memory probe slots a CTA, so the 8
-    probes of the points overflow them into global atomics) and 64x64 (no
-    slots: global atomics only): the same gradients as the oracle."""
+def test_adjoint_large_maps(sop, orc, R):
+    """Probe maps of 32x32 and 64x64 (16 KB and 64 KB of gradient per
+    probe): the same gradients as the oracle."""
     c = I.make_tiny()
     rng = np.random.default_rng(60 + R)
     pts = tilted({k: c[k] for k in KEYS}, rng)
