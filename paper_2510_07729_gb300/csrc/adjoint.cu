@@ -12,13 +12,12 @@
 // compact [P][R][R] maps. Environment and probe gradients are scattered with
 // float atomics (order-nondeterministic sums).
 //
-// Scatter traffic (bound by L2 atomics): neighbouring points in a warp
-// start their direction loops S/32 apart, so that they do not update the
-// same probe texels at the same step; the environment gradient is
-// accumulated as float4 texels (4 vector atomics a direction instead of 12
-// scalar ones) and folded into g_env at the end.
-#include <stdlib.h>
-
+// Scatter traffic (bound by L2 atomics): the points are taken grouped by
+// their nearest probe (a counting sort), so that a CTA's atomics go to few
+// probes' texels; neighbouring points in a warp start their direction
+// loops S/32 apart, so that they do not update the same texels at the same
+// step; the environment gradient is accumulated as float4 texels (4 vector
+// atomics a direction instead of 12 scalar ones) and folded into g_env.
 #include "sop_device.cuh"
 #include "sop_internal.h"
 
@@ -51,7 +50,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
     __syncthreads();
     const int64_t slot_m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot_m >= a.M) return;
-    const int64_t m = a.perm ? (int64_t)__ldg(a.perm + slot_m) : slot_m;
+    const int64_t m = __ldg(a.perm + slot_m);
 
     const float3 nr = load3(a.n, m);
     const float nl = sqrtf(dot3(nr, nr));
@@ -438,22 +437,14 @@ cudaError_t launch_adjoint(const QueryArgs& a, const QueryLayout& L, char* ws, c
     int32_t* bucket = reinterpret_cast<int32_t*>(ws + L.bucket);
     k.perm = perm;
     k.genv4 = reinterpret_cast<float4*>(ws + L.genv4);
-    // SOP_ADJOINT_GROUP=0 takes the points in their given order, for tuning
-    static const int group = [] {
-        const char* v = getenv("SOP_ADJOINT_GROUP");
-        return v ? atoi(v) : 1;
-    }();
+
     cudaError_t e = cudaMemsetAsync(bucket, 0, sizeof(int32_t) * (size_t)(a.P + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(k.genv4, 0, sizeof(float4) * (size_t)a.He * a.We, s);
     if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)((a.M + 255) / 256);
-    if (group) {
-        perm_count_kernel<<<nb, 256, 0, s>>>(k.idx, a.K, a.M, bucket);
-        perm_scan_kernel<<<1, 1024, 0, s>>>(bucket, a.P);
-        perm_fill_kernel<<<nb, 256, 0, s>>>(k.idx, a.K, a.M, bucket, perm);
-    } else {
-        k.perm = nullptr;
-    }
+    perm_count_kernel<<<nb, 256, 0, s>>>(k.idx, a.K, a.M, bucket);
+    perm_scan_kernel<<<1, 1024, 0, s>>>(bucket, a.P);
+    perm_fill_kernel<<<nb, 256, 0, s>>>(k.idx, a.K, a.M, bucket, perm);
     switch (a.rgbo_dtype) {
     case SOP_F32: e = adjoint_k<SOP_F32>(k, s); break;
     case SOP_BF16: e = adjoint_k<SOP_BF16>(k, s); break;
