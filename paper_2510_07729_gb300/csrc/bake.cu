@@ -366,6 +366,8 @@ struct TraceK {
     int32_t composite_at;
     // rays are origin p (of P) along direction t (of n_dirs): ray = p n_dirs + t
     int64_t n_dirs;
+    // rays a warp takes from the counter at a time
+    int32_t batch;
     // G-buffer mode (multi-target rendering): the Gaussians' orientation,
     // scales and materials, and the output [rays][4] float4
     const float *quat, *scale, *albedo, *rough, *metal;
@@ -735,7 +737,7 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
     // taken kBatch at a time (camera rays are mostly short: one counter
     // update per ray would serialise on it); the next batch's number is
     // fetched while the current batch is traced
-    constexpr int kBatch = OUT == kTraceGbuf ? 8 : 1;
+    const int kBatch = k.batch;
     unsigned long long rr = 0;
     if (lane == 0) rr = atomicAdd(k.stats, (unsigned long long)kBatch);
     int64_t base = 0;
@@ -1078,6 +1080,13 @@ cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp,
     }();
     k.composite_at = composite_at;
     k.n_dirs = (int64_t)R * R;
+    // SOP_BAKE_BATCH overrides the rays a warp takes at a time (1..16), for tuning
+    static const int batch = [] {
+        const char* e = getenv("SOP_BAKE_BATCH");
+        const int v = e ? atoi(e) : 0;
+        return (v >= 1 && v <= 16) ? v : 1;
+    }();
+    k.batch = batch;
     k.quat = k.scale = k.albedo = k.rough = k.metal = nullptr;
     k.gbuf = nullptr;
     const int64_t rays = (int64_t)atlas.P * R * R;
@@ -1110,6 +1119,7 @@ cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, co
     k.stats = stats;
     k.composite_at = kCompositeAt;
     k.n_dirs = n_dirs;
+    k.batch = 8;
     k.quat = g.quat;
     k.scale = g.scale;
     k.albedo = albedo;
