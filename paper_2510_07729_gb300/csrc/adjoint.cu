@@ -48,9 +48,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
     extern __shared__ float4 s_dirs[];
     for (int i = threadIdx.x; i < a.S; i += blockDim.x) s_dirs[i] = a.dirs[i];
     __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // position in the grouped order
-    if (j >= a.M) return;
-    const int64_t m = __ldg(a.perm + j);
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // position in the grouped order
+    if (pos >= a.M) return;
+    const int64_t m = __ldg(a.perm + pos);
 
     const float3 nr = load3(a.n, m);
     const float nl = sqrtf(dot3(nr, nr));
