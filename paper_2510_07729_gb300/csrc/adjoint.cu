@@ -14,9 +14,9 @@
 //
 // Scatter traffic (bound by L2 atomics): the points are taken grouped by
 // their nearest probe (a counting sort), so that a CTA's atomics go to few
-// probes' texels; neighbouring points in a warp start their direction
-// loops S/32 apart, so that they do not update the same texels at the same
-// step; the environment gradient is accumulated as float4 texels (4 vector
+// probes' texels; neighbouring points start their direction loops S/32
+// apart (by point index), so that a warp's lanes do not update the same
+// texels at the same step; the environment gradient is accumulated as float4 texels (4 vector
 // atomics a direction instead of 12 scalar ones) and folded into g_env.
 #include "sop_device.cuh"
 #include "sop_internal.h"
@@ -96,11 +96,12 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
     float ga[3] = {0.f, 0.f, 0.f}, gr = 0.f, gm = 0.f, gn[3] = {0.f, 0.f, 0.f};
     const float Rf = (float)a.R;
 
-    // the lanes of a warp (neighbouring points, nearly the same frame) start
-    // S/32 directions apart, so that at each step they scatter into other
-    // texels instead of all into the same ones (the order of the sum over
-    // directions only changes rounding)
-    const int i_first = (int)(((threadIdx.x & 31) * (int64_t)a.S) >> 5);
+    // neighbouring points (nearly the same frame) start their direction loops
+    // S/32 apart, by their index, so that the lanes of a warp scatter into
+    // other texels at each step instead of all into the same ones; the start
+    // depends on the point alone, so each point's sums keep one order from
+    // call to call whatever lane it lands in
+    const int i_first = (int)(((m & 31) * (int64_t)a.S) >> 5);
     for (int ii = 0; ii < a.S; ++ii) {
         const int i = ii + i_first < a.S ? ii + i_first : ii + i_first - a.S;
         const float4 l = s_dirs[i];
