@@ -778,9 +778,9 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
     if (lane == 0) rr = atomicAdd(k.stats, (unsigned long long)kBatch);
     int64_t base = 0;
     int sub = kBatch;
-    // G-buffer mode: the first kBatch (<= 32) lanes test one ray of the batch
-    // each against the grid's box and write the (zero) entry of a ray that
-    // misses it; the warp then traces the rays that enter, one after another
+    // G-buffer mode takes 32 rays at a time: each lane tests its own ray
+    // against the grid's box and writes the (zero) entry of one that misses
+    // it; the warp then traces the rays that enter, one after another
     unsigned live = 0;
     // work counters, summed over the warp's rays and added once at the end
     unsigned long long t_eval = 0, t_comp = 0, t_test = 0;
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
             if (lane == 0) rr = atomicAdd(k.stats, (unsigned long long)kBatch);
             const int64_t r = base + lane;
             bool enter = false;
-            if (lane < kBatch && r < total) {
+            if (r < total) {
                 const float4 dl = __ldg(k.dirs + (int)(r % RR));
                 const float3 dd = f3(dl.x, dl.y, dl.z);
                 float a0, a1;
@@ -1171,7 +1171,7 @@ cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, co
     k.stats = stats;
     k.composite_at = kCompositeAt;
     k.n_dirs = n_dirs;
-    k.batch = 8;
+    k.batch = 32;
     k.quat = g.quat;
     k.scale = g.scale;
     k.albedo = albedo;
