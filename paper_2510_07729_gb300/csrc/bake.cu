@@ -713,42 +713,6 @@ constexpr int kCompositeAt = 48;
 // pend, the candidates queued since (an upper bound of hits + queue). At a
 // composite the queue is always empty, so the set of hits composited, and
 // with it every rounding, is the same on every run.
-// Span [t0, t1] of the ray o + t d (t >= 0) inside the box [lo, hi] (slab
-// test, per axis in scalars so that nothing is indexed by a run-time axis);
-// t1 < t0 when it misses. iv: the reciprocal direction.
-__device__ __forceinline__ void box_span(const float3 o, const float3 d, const float3 iv, const float lx,
-                                         const float ly, const float lz, const float hx, const float hy,
-                                         const float hz, float& t0, float& t1)
-{
-    t0 = 0.f;
-    t1 = FLT_MAX;
-#define SOP_SLAB(OA, DA, IA, LO, HI)                                 \
-    if (DA != 0.f) {                                                 \
-        float ta = (LO - OA) * IA, tb = (HI - OA) * IA;              \
-        if (ta > tb) {                                               \
-            const float tmp = ta;                                    \
-            ta = tb;                                                 \
-            tb = tmp;                                                \
-        }                                                            \
-        t0 = fmaxf(t0, ta);                                          \
-        t1 = fminf(t1, tb);                                          \
-    } else if (OA < LO || OA > HI) {                                 \
-        t1 = -1.f;                                                   \
-    }
-    SOP_SLAB(o.x, d.x, iv.x, lx, hx)
-    SOP_SLAB(o.y, d.y, iv.y, ly, hy)
-    SOP_SLAB(o.z, d.z, iv.z, lz, hz)
-#undef SOP_SLAB
-}
-
-// reciprocal direction for the box entries (a zero component becomes a tiny
-// one: the slab along that axis is then all or nothing)
-__device__ __forceinline__ float3 recip_dir(const float3 d)
-{
-    return f3(1.f / (fabsf(d.x) > 1e-30f ? d.x : 1e-30f), 1.f / (fabsf(d.y) > 1e-30f ? d.y : 1e-30f),
-              1.f / (fabsf(d.z) > 1e-30f ? d.z : 1e-30f));
-}
-
 template <int OUT>
 __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(const TraceK k)
 {
@@ -778,56 +742,24 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
     if (lane == 0) rr = atomicAdd(k.stats, (unsigned long long)kBatch);
     int64_t base = 0;
     int sub = kBatch;
-    // G-buffer mode takes 32 rays at a time: each lane tests its own ray
-    // against the grid's box and writes the (zero) entry of one that misses
-    // it; the warp then traces the rays that enter, one after another
-    unsigned live = 0;
     // work counters, summed over the warp's rays and added once at the end
     unsigned long long t_eval = 0, t_comp = 0, t_test = 0;
     for (;;) {
-    int64_t ray;
-    if (OUT == kTraceGbuf) {
-        if (live == 0) {
-            base = (int64_t)__shfl_sync(0xffffffffu, rr, 0);
-            if (base >= total) break;
-            if (lane == 0) rr = atomicAdd(k.stats, (unsigned long long)kBatch);
-            const int64_t r = base + lane;
-            bool enter = false;
-            if (r < total) {
-                const float4 dl = __ldg(k.dirs + (int)(r % RR));
-                const float3 dd = f3(dl.x, dl.y, dl.z);
-                float a0, a1;
-                box_span(load3(k.probe_pos, (int)(r / RR)), dd, recip_dir(dd), G.origin[0], G.origin[1],
-                         G.origin[2], G.bmax[0], G.bmax[1], G.bmax[2], a0, a1);
-                enter = G.n_entries > 0 && a0 <= a1;
-                if (!enter) {
-                    float4* o4 = k.gbuf + 4 * r;
-                    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                    o4[0] = z;
-                    o4[1] = z;
-                    o4[2] = z;
-                    o4[3] = z;
-                }
-            }
-            live = __ballot_sync(0xffffffffu, enter);
-            if (live == 0) continue;
-        }
-        ray = base + (__ffs(live) - 1);
-        live &= live - 1;
-    } else {
-        if (sub == kBatch) {
-            base = (int64_t)__shfl_sync(0xffffffffu, rr, 0);
-            sub = 0;
-            if (lane == 0 && base < total) rr = atomicAdd(k.stats, (unsigned long long)kBatch);
-        }
-        ray = base + sub++;
-        if (ray >= total) break;
+    if (sub == kBatch) {
+        base = (int64_t)__shfl_sync(0xffffffffu, rr, 0);
+        sub = 0;
+        if (lane == 0 && base < total) rr = atomicAdd(k.stats, (unsigned long long)kBatch);
     }
+    const int64_t ray = base + sub++;
+    if (ray >= total) break;
     const int p = (int)(ray / RR), t = (int)(ray % RR);
     const float4 d4 = __ldg(k.dirs + t);
     const float3 d = f3(d4.x, d4.y, d4.z);
     const float3 o = load3(k.probe_pos, p);
-    const float3 iv = recip_dir(d);
+    // reciprocal direction for the box entries (a zero component becomes a
+    // tiny one: the slab along that axis is then all or nothing)
+    const float3 iv = f3(1.f / (fabsf(d.x) > 1e-30f ? d.x : 1e-30f), 1.f / (fabsf(d.y) > 1e-30f ? d.y : 1e-30f),
+                         1.f / (fabsf(d.z) > 1e-30f ? d.z : 1e-30f));
     RayAcc acc;
     acc.T = 1.f;
     acc.L0 = acc.L1 = acc.L2 = acc.Dacc = acc.Wacc = 0.f;
@@ -845,8 +777,24 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
     const float gmx = G.bmax[0], gmy = G.bmax[1], gmz = G.bmax[2];
     const int gdx = G.dims[0], gdy = G.dims[1], gdz = G.dims[2];
     const float gh = G.h, gih = G.inv_h;
-    float t0, t1;
-    box_span(o, d, iv, gox, goy, goz, gmx, gmy, gmz, t0, t1);
+    float t0 = 0.f, t1 = FLT_MAX;
+#define SOP_SLAB(OA, DA, IA, LO, HI)                                 \
+    if (DA != 0.f) {                                                 \
+        float ta = (LO - OA) * IA, tb = (HI - OA) * IA;              \
+        if (ta > tb) {                                               \
+            const float tmp = ta;                                    \
+            ta = tb;                                                 \
+            tb = tmp;                                                \
+        }                                                            \
+        t0 = fmaxf(t0, ta);                                          \
+        t1 = fminf(t1, tb);                                          \
+    } else if (OA < LO || OA > HI) {                                 \
+        t1 = -1.f;                                                   \
+    }
+    SOP_SLAB(o.x, d.x, iv.x, gox, gmx)
+    SOP_SLAB(o.y, d.y, iv.y, goy, gmy)
+    SOP_SLAB(o.z, d.z, iv.z, goz, gmz)
+#undef SOP_SLAB
     if (G.n_entries > 0 && t0 <= t1) {
         int cx = min(max((int)floorf((o.x + t0 * d.x - gox) * gih), 0), gdx - 1);
         int cy = min(max((int)floorf((o.y + t0 * d.y - goy) * gih), 0), gdy - 1);
@@ -1171,7 +1119,7 @@ cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, co
     k.stats = stats;
     k.composite_at = kCompositeAt;
     k.n_dirs = n_dirs;
-    k.batch = 32;
+    k.batch = 8;
     k.quat = g.quat;
     k.scale = g.scale;
     k.albedo = albedo;
