@@ -520,7 +520,8 @@ size_t sop_place_probes_workspace_bytes(int64_t n_points);
  * points in order; out_pos [k][3] (device, or NULL): pts + offset nrm,
  * computed in double and rounded once (nrm [n][3] device, or NULL: no
  * offset). 1 <= k <= n, 0 <= start < n. Runs as one thread-block cluster
- * (8 CTAs) for all k iterations. Asynchronous. */
+ * (16 CTAs where the device holds such a cluster, else 8) for all k
+ * iterations. Asynchronous. */
 sop_status sop_place_probes(const float* pts, const float* nrm, int64_t n_points, int32_t k, int64_t start,
                             float offset, int64_t* out_idx, float* out_pos, void* ws, size_t ws_bytes, void* stream);
 

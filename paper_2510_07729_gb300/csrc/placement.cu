@@ -7,14 +7,15 @@
 // sequential FPS: the first point is `start`, each next one has the largest
 // smallest key to the chosen ones, ties to the lower index.
 //
-// fps_cluster_kernel: one thread-block cluster of kFpsCtas CTAs runs all k
-// iterations. CTA r owns a contiguous slice of the points; their quantised
-// positions and current smallest keys live in its shared memory when the
-// slice fits (else in the workspace). Per iteration every thread updates
+// fps_cluster_kernel: one thread-block cluster of 16 CTAs (the non-portable
+// size, where the device schedules it; else 8) runs all k iterations. CTA r
+// owns a contiguous slice of the points; their quantised positions and
+// current smallest keys live in its shared memory when the slice fits (else
+// in the workspace). Per iteration every thread updates
 // its points with the point just chosen and keeps its best (key, index); a
 // warp then a CTA reduction gives the CTA's best, published in its shared
 // memory (double-buffered by iteration parity); one cluster barrier; every
-// thread reads the kFpsCtas bests through distributed shared memory and
+// thread reads the cluster's bests through distributed shared memory and
 // takes the same winner. The barrier is the hardware cluster barrier, which
 // every thread of the cluster reaches once per iteration.
 #include <climits>
@@ -27,7 +28,7 @@ namespace cg = cooperative_groups;
 
 namespace sop {
 
-constexpr int kFpsCtas = 8;
+constexpr int kFpsCtasMax = 16;
 constexpr int kFpsThreads = 1024;
 constexpr size_t kFpsPointBytes = sizeof(int4) + sizeof(unsigned long long);
 constexpr size_t kFpsSmemMax = 220 * 1024;
@@ -57,7 +58,7 @@ __device__ __forceinline__ bool fps_better(unsigned long long ka, long long ia, 
     return ka > kb || (ka == kb && ia < ib);
 }
 
-__global__ void __cluster_dims__(kFpsCtas, 1, 1) __launch_bounds__(kFpsThreads) fps_cluster_kernel(const FpsK k)
+__global__ void __launch_bounds__(kFpsThreads) fps_cluster_kernel(const FpsK k)
 {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ unsigned long long s_wkey[32];
@@ -66,6 +67,7 @@ __global__ void __cluster_dims__(kFpsCtas, 1, 1) __launch_bounds__(kFpsThreads) 
     __shared__ long long s_cidx[2];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
+    const int n_ctas = (int)cl.num_blocks();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t lo = (int64_t)rank * k.chunk;
     const int64_t hi = min(k.n, lo + k.chunk);
@@ -142,7 +144,7 @@ __global__ void __cluster_dims__(kFpsCtas, 1, 1) __launch_bounds__(kFpsThreads) 
         cl.sync();
         unsigned long long gk = 0ull;
         long long gi = LLONG_MAX;
-        for (int r = 0; r < kFpsCtas; ++r) {
+        for (int r = 0; r < n_ctas; ++r) {
             const unsigned long long rk = *cl.map_shared_rank(&s_ckey[buf], r);
             const long long ri = *cl.map_shared_rank(&s_cidx[buf], r);
             if (fps_better(rk, ri, gk, gi)) {
@@ -165,7 +167,31 @@ cudaError_t launch_fps(const float* pts, const float* nrm, int64_t n, int32_t k,
     a.pts = pts;
     a.nrm = nrm;
     a.n = n;
-    a.chunk = (n + kFpsCtas - 1) / kFpsCtas;
+    // the cluster: 16 CTAs where the device can hold such a cluster, else 8
+    static int ctas = 0;
+    if (!ctas) {
+        ctas = 8;
+        if (cudaFuncSetAttribute(fps_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(kFpsCtasMax);
+            cfg.blockDim = dim3(kFpsThreads);
+            cfg.dynamicSmemBytes = kFpsSmemMax;
+            cudaLaunchAttribute at;
+            at.id = cudaLaunchAttributeClusterDimension;
+            at.val.clusterDim.x = kFpsCtasMax;
+            at.val.clusterDim.y = 1;
+            at.val.clusterDim.z = 1;
+            cfg.attrs = &at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            cudaFuncSetAttribute(fps_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFpsSmemMax);
+            if (cudaOccupancyMaxActiveClusters(&nclusters, fps_cluster_kernel, &cfg) == cudaSuccess && nclusters > 0)
+                ctas = kFpsCtasMax;
+        }
+        cudaGetLastError();  // a refused query leaves the 8-CTA cluster
+    }
+    a.chunk = (n + ctas - 1) / ctas;
     a.start = start;
     a.k = k;
     a.offset = offset;
@@ -178,7 +204,20 @@ cudaError_t launch_fps(const float* pts, const float* nrm, int64_t n, int32_t k,
     const size_t dyn = a.use_smem ? smem : 0;
     cudaError_t e = cudaFuncSetAttribute(fps_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    fps_cluster_kernel<<<kFpsCtas, kFpsThreads, dyn, s>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(kFpsThreads);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = ctas;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, fps_cluster_kernel, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
