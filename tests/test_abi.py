@@ -60,3 +60,44 @@ def test_radius_checked_on_the_host():
         assert lib.sop_query_shade_noalloc(fake, fake, fake, fake, fake, fake, 16, ctypes.byref(at), fake, 16, 32,
                                            None, ctypes.byref(sp), fake, None, None, None) == 1
         assert b"radius" in lib.sop_last_error()
+
+
+def test_front_end_and_placement_checks_on_the_host():
+    """The deferred front end and the placement entry points refuse bad
+    arguments before any device work (SOP_ERR_INVALID_ARG = 1, with a
+    message), so these run without a GPU."""
+    from paper_2510_07729_gb300 import sop as S
+    lib = S.load()
+    fake = 1 << 20  # 16-byte aligned, never dereferenced
+    f3 = lambda *v: (ctypes.c_float * 3)(*v)  # noqa: E731
+    # pinhole: empty image, degenerate camera, field of view out of range
+    assert lib.sop_pinhole_dirs(0, 10, f3(0, 0, 1), f3(0, 0, 0), f3(0, 0, 1), 40.0, fake, None) == 1
+    assert lib.sop_pinhole_dirs(8, 8, f3(0, 0, 1), f3(0, 0, 1), f3(0, 0, 1), 40.0, fake, None) == 1
+    assert b"eye == target" in lib.sop_last_error()
+    assert lib.sop_pinhole_dirs(8, 8, f3(0, 0, 1), f3(0, 0, 0), f3(0, 0, 1), 180.0, fake, None) == 1
+    assert lib.sop_pinhole_dirs(8, 8, f3(0, 0, 1), f3(0, 0, 0), f3(0, 0, 1), 40.0, fake + 4, None) == 1
+    assert lib.sop_panorama_dirs(16, 0, fake, None) == 1
+    # G-buffer trace: no origin, unaligned directions, no materials
+    g = S.Gaussians(fake, fake, fake, fake, fake, 10)
+    m = S.Materials(fake, fake, fake)
+    bp = S.BakeParams(0.0, 1.0 / 255.0, 0.99, 1e-4)
+    assert lib.sop_trace_gbuffer(ctypes.byref(g), ctypes.byref(m), fake, 0, fake, 4, ctypes.byref(bp), fake, fake,
+                                 1 << 30, None) == 1
+    assert lib.sop_trace_gbuffer(ctypes.byref(g), ctypes.byref(m), fake, 1, fake + 8, 4, ctypes.byref(bp), fake,
+                                 fake, 1 << 30, None) == 1
+    assert lib.sop_trace_gbuffer(ctypes.byref(g), None, fake, 1, fake, 4, ctypes.byref(bp), fake, fake, 1 << 30,
+                                 None) == 1
+    assert b"materials" in lib.sop_last_error()
+    # shading points: non-positive threshold, missing outputs
+    cnt = ctypes.c_void_p(fake)
+    assert lib.sop_gbuffer_points(fake, None, 16, f3(0, 0, 0), fake, 0.0, fake, fake, fake, fake, fake, fake, fake,
+                                  cnt, fake, 1 << 20, None) == 1
+    assert lib.sop_gbuffer_points(fake, None, 16, f3(0, 0, 0), fake, 0.5, None, fake, fake, fake, fake, fake, fake,
+                                  cnt, fake, 1 << 20, None) == 1
+    # compositing: more points than pixels
+    assert lib.sop_depth_composite(fake, fake, 4, fake, fake, 5, None, None, 0, fake, None) == 1
+    # placement: k above n, start outside, non-finite offset
+    assert lib.sop_place_probes(fake, None, 10, 11, 0, 0.0, fake, None, fake, 1 << 20, None) == 1
+    assert lib.sop_place_probes(fake, None, 10, 4, 10, 0.0, fake, None, fake, 1 << 20, None) == 1
+    assert lib.sop_place_probes(fake, None, 10, 4, 0, float("inf"), fake, None, fake, 1 << 20, None) == 1
+    assert lib.sop_place_probes_workspace_bytes(0) == 0 and lib.sop_place_probes_workspace_bytes(100) > 0
