@@ -109,12 +109,19 @@ typedef struct {
  * o exp(-m^2/2)) with m the Mahalanobis distance at the maximising t*;
  * responses with t* <= t_near or alpha < alpha_min are skipped; compositing
  * stops once the transmittance falls below t_stop (0 = never).
- * Defaults: t_near 0, alpha_min 1/255, alpha_max 0.99, t_stop 1e-4. */
+ * Defaults: t_near 0, alpha_min 1/255, alpha_max 0.99, t_stop 1e-4.
+ * grid_density: cells of the binning grid per Gaussian (an implementation
+ * choice, not the method's: results do not depend on it), 0 (what
+ * zero-initialised callers get) for the default of one cell per 4
+ * Gaussians, else in [0.01, 2]; probe bakes run fastest near the default,
+ * camera G-buffers near 0.06. sop_bake_bin and the traces that use its grid
+ * take the same value. */
 typedef struct {
     float t_near;
     float alpha_min;
     float alpha_max;
     float t_stop;
+    float grid_density;
 } sop_bake_params;
 
 /* Query/shade parameters. K nearest probes (1..32), S light directions

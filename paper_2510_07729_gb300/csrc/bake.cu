@@ -40,24 +40,25 @@ struct GRec {
 constexpr float kMarginRel = 1e-4f;
 constexpr int kMaxR = 64;
 
-// Grid cells per Gaussian (the grid gets about half of cells_cap): SOP_BAKE_CELLS
+// Grid cells per Gaussian (the grid gets about half of cells_cap): `density`
+// cells a Gaussian when given (> 0), else one per 4; SOP_BAKE_CELLS
 // overrides the default of one cell per 2 Gaussians (given as cells per 100
 // Gaussians, 5..400) for tuning.
-static int64_t cells_cap_for(int64_t N)
+static int64_t cells_cap_for(int64_t N, float density)
 {
     static const int64_t per100 = [] {
         const char* e = getenv("SOP_BAKE_CELLS");
         const int v = e ? atoi(e) : 0;
         return (int64_t)((v >= 5 && v <= 400) ? v : 50);
     }();
-    const int64_t c = N * per100 / 100;
+    const int64_t c = density > 0.f ? (int64_t)(2.0 * (double)density * (double)N) : N * per100 / 100;
     return c < 4096 ? 4096 : (c > (1 << 23) ? (1 << 23) : c);
 }
 
-BakeLayout bake_layout(int64_t N, int64_t entries_cap)
+BakeLayout bake_layout(int64_t N, int64_t entries_cap, float density)
 {
     BakeLayout L{};
-    L.cells_cap = cells_cap_for(N);
+    L.cells_cap = cells_cap_for(N, density);
     L.entries_cap = entries_cap > 0 ? entries_cap : 24 * N + 65536;
     size_t o = 0;
     L.hdr = o;        o = align256(o + sizeof(GaussGrid));

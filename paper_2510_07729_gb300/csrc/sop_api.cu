@@ -212,20 +212,21 @@ static sop_status check_bake_args(const sop_gaussians* g, const sop_bake_params*
     if (g->n > 0 && (!g->mean || !g->scale || !g->quat || !g->opacity || !g->rgb))
         return fail(SOP_ERR_INVALID_ARG, "a Gaussian array is NULL");
     if (!(params->alpha_min > 0.f) || !(params->alpha_max >= params->alpha_min) || !(params->alpha_max < 1.f) ||
-        !(params->t_stop >= 0.f) || !(params->t_stop < 1.f) || !isfinite(params->t_near))
+        !(params->t_stop >= 0.f) || !(params->t_stop < 1.f) || !isfinite(params->t_near) ||
+        !(params->grid_density == 0.f || (params->grid_density >= 0.01f && params->grid_density <= 2.f)))
         return fail(SOP_ERR_INVALID_ARG, "bake params out of range (need 0 < alpha_min <= alpha_max < 1, "
-                                         "0 <= t_stop < 1, finite t_near)");
+                                         "0 <= t_stop < 1, finite t_near, grid_density 0 or in [0.01, 2])");
     return SOP_OK;
 }
 
 // The layout with the largest cell-entry capacity that fits ws_bytes.
-static sop_status bake_fit(int64_t n, void* ws, size_t ws_bytes, sop::BakeLayout& L)
+static sop_status bake_fit(int64_t n, float density, void* ws, size_t ws_bytes, sop::BakeLayout& L)
 {
-    const sop::BakeLayout L0 = sop::bake_layout(n, 1);
-    if (!ws || ws_bytes < L0.total) return check_ws(ws, ws_bytes, sop::bake_layout(n, 0).total);
+    const sop::BakeLayout L0 = sop::bake_layout(n, 1, density);
+    if (!ws || ws_bytes < L0.total) return check_ws(ws, ws_bytes, sop::bake_layout(n, 0, density).total);
     int64_t cap = 64 + (int64_t)((ws_bytes - L0.total) / sop::kBakeEntryBytes);
-    L = sop::bake_layout(n, cap);
-    while (L.total > ws_bytes && L.entries_cap > 1) L = sop::bake_layout(n, L.entries_cap - 1);
+    L = sop::bake_layout(n, cap, density);
+    while (L.total > ws_bytes && L.entries_cap > 1) L = sop::bake_layout(n, L.entries_cap - 1, density);
     return check_ws(ws, ws_bytes, L.total);
 }
 
@@ -235,7 +236,7 @@ sop_status sop_bake_bin(const sop_gaussians* g, const sop_bake_params* params, v
     sop_status st = check_bake_args(g, params);
     if (st != SOP_OK) return st;
     sop::BakeLayout L;
-    if ((st = bake_fit(g->n, ws, ws_bytes, L)) != SOP_OK) return st;
+    if ((st = bake_fit(g->n, params->grid_density, ws, ws_bytes, L)) != SOP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     char* w = (char*)ws;
     st = cuda_status(sop::launch_bake_bin(*g, params->alpha_min, L, w, s), "sop_bake_bin (binning)");
@@ -249,7 +250,7 @@ sop_status sop_bake_bin(const sop_gaussians* g, const sop_bake_params* params, v
     st = cuda_status(cudaStreamSynchronize(s), "sop_bake_bin (sync)");
     if (st != SOP_OK) return st;
     if (n_entries == INT32_MAX || (int64_t)n_entries > L.entries_cap) {
-        const sop::BakeLayout need = sop::bake_layout(g->n, (int64_t)n_entries + 1);
+        const sop::BakeLayout need = sop::bake_layout(g->n, (int64_t)n_entries + 1, params->grid_density);
         return fail(SOP_ERR_WORKSPACE, "sop_bake: %d grid entries exceed the workspace; need %zu bytes", n_entries,
                     need.total);
     }
@@ -265,7 +266,7 @@ sop_status sop_bake_trace(const sop_gaussians* g, const sop_atlas* atlas, const 
     if ((int64_t)atlas->P * atlas->R * atlas->R > (int64_t)INT32_MAX)
         return fail(SOP_ERR_INVALID_ARG, "P * R^2 exceeds 2^31 texels");
     sop::BakeLayout L;
-    if ((st = bake_fit(g->n, ws, ws_bytes, L)) != SOP_OK) return st;
+    if ((st = bake_fit(g->n, params->grid_density, ws, ws_bytes, L)) != SOP_OK) return st;
     return cuda_status(sop::launch_bake_trace(*atlas, *params, L, (char*)ws, (cudaStream_t)stream), "sop_bake_trace");
 }
 
@@ -285,7 +286,7 @@ sop_status sop_bake_stats(const void* ws, size_t ws_bytes, int64_t n_gauss, int6
 {
     if (!out) return fail(SOP_ERR_INVALID_ARG, "out is NULL");
     sop::BakeLayout L;
-    sop_status st = bake_fit(n_gauss, const_cast<void*>(ws), ws_bytes, L);
+    sop_status st = bake_fit(n_gauss, 0.f, const_cast<void*>(ws), ws_bytes, L);
     if (st != SOP_OK) return st;
     unsigned long long v[5];
     cudaStream_t s = (cudaStream_t)stream;
@@ -605,7 +606,7 @@ sop_status sop_trace_gbuffer(const sop_gaussians* g, const sop_materials* m, con
         return fail(SOP_ERR_INVALID_ARG, "n_origins * n_dirs exceeds 2^36 rays");
     if (!out || !aligned(out, 16)) return fail(SOP_ERR_INVALID_ARG, "out NULL or not 16-byte aligned");
     sop::BakeLayout L;
-    if ((st = bake_fit(g->n, ws, ws_bytes, L)) != SOP_OK) return st;
+    if ((st = bake_fit(g->n, params->grid_density, ws, ws_bytes, L)) != SOP_OK) return st;
     return cuda_status(sop::launch_trace_gbuffer(*g, m->albedo, m->rough, m->metal, origins, n_origins, dirs, n_dirs,
                                                  *params, L, (char*)ws, out, (cudaStream_t)stream),
                        "sop_trace_gbuffer");

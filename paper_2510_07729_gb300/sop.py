@@ -43,7 +43,8 @@ class Materials(C.Structure):
 
 
 class BakeParams(C.Structure):
-    _fields_ = [("t_near", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float)]
+    _fields_ = [("t_near", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float),
+                ("grid_density", C.c_float)]
 
 
 class AdamParams(C.Structure):
@@ -331,10 +332,13 @@ class GbufferTracer:
     origins x directions (sop_trace_gbuffer) into [rays, 16] G-buffers
     (C.rgb, W, N.xyz, D, A.rgb, R, M, 0, 0, 0)."""
 
-    def __init__(self, gauss, mats, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4):
+    def __init__(self, gauss, mats, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4,
+                 grid_density=0.06):
         self.gauss, self.mats = gauss, mats
         n = gauss["mean"].shape[0]
-        self.params = (t_near, alpha_min, alpha_max, t_stop)
+        # camera rays cross many cells they do not stop in: a coarser grid
+        # than the probe bake's (one cell per 4 Gaussians) walks faster
+        self.params = (t_near, alpha_min, alpha_max, t_stop, grid_density)
         self.ws = BakeWorkspace(n, gauss["mean"].device)
         bake_bin(gauss, self.ws, *self.params)
         for k, shp in (("albedo", (n, 3)), ("rough", (n,)), ("metal", (n,))):
@@ -446,16 +450,18 @@ class BakeWorkspace:
         self.buf = _ws(nbytes, self.buf.device)
 
 
-def _bake_params(t_near, alpha_min, alpha_max, t_stop):
-    return BakeParams(t_near, alpha_min, alpha_max, t_stop)
+def _bake_params(t_near, alpha_min, alpha_max, t_stop, grid_density=0.0):
+    return BakeParams(t_near, alpha_min, alpha_max, t_stop, grid_density)
 
 
-def bake_bin(gauss, workspace: BakeWorkspace, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4):
+def bake_bin(gauss, workspace: BakeWorkspace, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4,
+             grid_density=0.0):
     """Bin the Gaussians into the grid kept in the workspace (syncs once);
-    grows the workspace once if the scene needs more cell entries."""
+    grows the workspace once if the scene needs more cell entries.
+    grid_density: grid cells per Gaussian (0: one per 4)."""
     lib = load()
     g = _gauss(gauss)
-    bp = _bake_params(t_near, alpha_min, alpha_max, t_stop)
+    bp = _bake_params(t_near, alpha_min, alpha_max, t_stop, grid_density)
     ws = workspace
     st = lib.sop_bake_bin(C.byref(g), C.byref(bp), _ptr(ws.buf), ws.buf.numel(), _stream())
     if st == 3:

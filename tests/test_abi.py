@@ -80,7 +80,7 @@ def test_front_end_and_placement_checks_on_the_host():
     # G-buffer trace: no origin, unaligned directions, no materials
     g = S.Gaussians(fake, fake, fake, fake, fake, 10)
     m = S.Materials(fake, fake, fake)
-    bp = S.BakeParams(0.0, 1.0 / 255.0, 0.99, 1e-4)
+    bp = S.BakeParams(0.0, 1.0 / 255.0, 0.99, 1e-4, 0.0)
     assert lib.sop_trace_gbuffer(ctypes.byref(g), ctypes.byref(m), fake, 0, fake, 4, ctypes.byref(bp), fake, fake,
                                  1 << 30, None) == 1
     assert lib.sop_trace_gbuffer(ctypes.byref(g), ctypes.byref(m), fake, 1, fake + 8, 4, ctypes.byref(bp), fake,
