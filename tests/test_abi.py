@@ -101,3 +101,14 @@ def test_front_end_and_placement_checks_on_the_host():
     assert lib.sop_place_probes(fake, None, 10, 4, 10, 0.0, fake, None, fake, 1 << 20, None) == 1
     assert lib.sop_place_probes(fake, None, 10, 4, 0, float("inf"), fake, None, fake, 1 << 20, None) == 1
     assert lib.sop_place_probes_workspace_bytes(0) == 0 and lib.sop_place_probes_workspace_bytes(100) > 0
+
+
+def test_grid_density_checked_on_the_host():
+    from paper_2510_07729_gb300 import sop as S
+    lib = S.load()
+    fake = 1 << 20
+    g = S.Gaussians(fake, fake, fake, fake, fake, 10)
+    for dens in (5.0, 0.001, -1.0, float("nan")):
+        bp = S.BakeParams(0.0, 1.0 / 255.0, 0.99, 1e-4, dens)
+        assert lib.sop_bake_bin(ctypes.byref(g), ctypes.byref(bp), fake, 1 << 30, None) == 1
+        assert b"grid_density" in lib.sop_last_error()
