@@ -112,8 +112,8 @@ typedef struct {
  * Defaults: t_near 0, alpha_min 1/255, alpha_max 0.99, t_stop 1e-4.
  * grid_density: cells of the binning grid per Gaussian (an implementation
  * choice, not the method's: results do not depend on it), 0 (what
- * zero-initialised callers get) for the default of one cell per 4
- * Gaussians, else in [0.01, 2]; probe bakes run fastest near the default,
+ * zero-initialised callers get) for the default of 0.35 cells per
+ * Gaussian, else in [0.01, 2]; probe bakes run fastest near the default,
  * camera G-buffers near 0.06. sop_bake_bin and the traces that use its grid
  * take the same value. */
 typedef struct {

@@ -40,16 +40,16 @@ struct GRec {
 constexpr float kMarginRel = 1e-4f;
 constexpr int kMaxR = 64;
 
-// Grid cells per Gaussian (the grid gets about half of cells_cap): `density`
-// cells a Gaussian when given (> 0), else one per 4; SOP_BAKE_CELLS
-// overrides the default of one cell per 2 Gaussians (given as cells per 100
-// Gaussians, 5..400) for tuning.
+// Capacity of the binning grid: the grid gets about half of it, i.e.
+// `density` cells per Gaussian when given (> 0), else 0.35 (a capacity of 70
+// cells per 100 Gaussians; SOP_BAKE_CELLS overrides that capacity, 5..400,
+// for tuning).
 static int64_t cells_cap_for(int64_t N, float density)
 {
     static const int64_t per100 = [] {
         const char* e = getenv("SOP_BAKE_CELLS");
         const int v = e ? atoi(e) : 0;
-        return (int64_t)((v >= 5 && v <= 400) ? v : 50);
+        return (int64_t)((v >= 5 && v <= 400) ? v : 70);
     }();
     const int64_t c = density > 0.f ? (int64_t)(2.0 * (double)density * (double)N) : N * per100 / 100;
     return c < 4096 ? 4096 : (c > (1 << 23) ? (1 << 23) : c);

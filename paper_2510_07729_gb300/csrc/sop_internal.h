@@ -82,7 +82,7 @@ struct BakeLayout {
 // bytes per cell entry: quantised box and Gaussian index
 constexpr size_t kBakeEntryBytes = 16;
 // bake workspace layout for N Gaussians (independent of the atlas)
-// density: grid cells per Gaussian (0: the default, one per 4 Gaussians)
+// density: grid cells per Gaussian (0: the default, 0.35)
 BakeLayout bake_layout(int64_t N, int64_t entries_cap, float density = 0.f);
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s);

@@ -337,7 +337,7 @@ class GbufferTracer:
         self.gauss, self.mats = gauss, mats
         n = gauss["mean"].shape[0]
         # camera rays cross many cells they do not stop in: a coarser grid
-        # than the probe bake's (one cell per 4 Gaussians) walks faster
+        # than the probe bake's (0.35 cells per Gaussian) walks faster
         self.params = (t_near, alpha_min, alpha_max, t_stop, grid_density)
         self.ws = BakeWorkspace(n, gauss["mean"].device)
         bake_bin(gauss, self.ws, *self.params)
@@ -458,7 +458,7 @@ def bake_bin(gauss, workspace: BakeWorkspace, t_near=0.0, alpha_min=1.0 / 255.0,
              grid_density=0.0):
     """Bin the Gaussians into the grid kept in the workspace (syncs once);
     grows the workspace once if the scene needs more cell entries.
-    grid_density: grid cells per Gaussian (0: one per 4)."""
+    grid_density: grid cells per Gaussian (0: the default, 0.35)."""
     lib = load()
     g = _gauss(gauss)
     bp = _bake_params(t_near, alpha_min, alpha_max, t_stop, grid_density)
