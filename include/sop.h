@@ -52,6 +52,40 @@ typedef enum {
     SOP_ERR_DEVICE = 6       /* a device-side check failed (see message)    */
 } sop_status;
 
+/* Device status word. Problems that kernels meet while they run, and that no
+ * host-side check can see before launch, set bits in one 32-bit word per
+ * device (shared by every stream and thread that uses the library on it):
+ *   SOP_DEVSTAT_NONFINITE      an input value was NaN or Inf: Gaussian
+ *                              parameters (such a Gaussian is left out of
+ *                              the bake), probe or shading-point positions
+ *                              and normals, materials, view directions,
+ *                              environment or atlas texels, upstream
+ *                              gradients;
+ *   SOP_DEVSTAT_BAKE_TRUNCATED a bake (or G-buffer) ray met more hits with
+ *                              one t* than its 256-entry hit buffer holds,
+ *                              could not split them further and stopped
+ *                              there (its texel holds the partial
+ *                              composite);
+ *   SOP_DEVSTAT_INDEX          a caller-supplied index (probe ids, pixel
+ *                              lists) was outside its range and skipped;
+ *   SOP_DEVSTAT_GRID_COARSENED information, not an error: the bake's
+ *                              binning grid was coarsened on the device
+ *                              until the cell lists fit the workspace.
+ * Entry points do not wait for their kernels, so these come back only
+ * through sop_device_status(): it synchronises `stream`, writes the word to
+ * *out_bits (host, may be NULL), clears it when `clear` is non-zero (an
+ * atomic exchange on the device), and returns SOP_ERR_DEVICE with a message
+ * naming the problems when any error bit (SOP_DEVSTAT_ERRORS) is set, else
+ * SOP_OK. Bits stay set until a call clears them. The word's address is
+ * looked up once per device: do not use the library across a
+ * cudaDeviceReset() in the same process. */
+#define SOP_DEVSTAT_NONFINITE 0x1u
+#define SOP_DEVSTAT_BAKE_TRUNCATED 0x2u
+#define SOP_DEVSTAT_INDEX 0x4u
+#define SOP_DEVSTAT_GRID_COARSENED 0x100u
+#define SOP_DEVSTAT_ERRORS 0xffu
+sop_status sop_device_status(void* stream, uint32_t* out_bits, int32_t clear);
+
 /* Storage types of the probe atlas (Sec. 3.1.2 octahedral textures; the
  * reduced-precision atlas stores in bf16/fp16, accumulates in fp32). */
 typedef enum { SOP_F32 = 0, SOP_BF16 = 1, SOP_F16 = 2, SOP_FP8E4M3 = 3 } sop_dtype;
@@ -226,7 +260,9 @@ sop_status sop_env_importance_dirs(const float* env, int32_t H, int32_t S, float
 sop_status sop_read_bandwidth_probe(const void* buf, size_t bytes, int32_t reps, float* sink, void* stream);
 
 /* Workspace bytes for sop_bake / sop_bake_bin / sop_bake_trace on n
- * Gaussians (the size does not depend on P or R; they are only checked). */
+ * Gaussians (the size does not depend on P or R; they are only checked).
+ * This is the minimum: it holds 24 grid cell entries per Gaussian plus
+ * 65,536; a larger workspace holds more entries. */
 size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R);
 
 /* Bake every texel of every probe of `atlas` (positions atlas->probe_pos)
@@ -238,15 +274,20 @@ size_t sop_bake_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R);
  * sum(T alpha) (0 when nothing is hit).
  * Implementation: Gaussians are binned by the bounding boxes of their
  * alpha_min ellipsoids into a uniform grid that each texel ray walks front
- * to back. Equivalent to sop_bake_bin followed by sop_bake_trace: it
- * SYNCHRONISES `stream` once, after binning, and returns SOP_ERR_WORKSPACE
- * (the message gives the bytes needed) when ws_bytes is too small for this
- * scene's cell lists. Not capturable in a CUDA graph. */
+ * to back. Equivalent to sop_bake_bin followed by sop_bake_trace.
+ * Asynchronous (no host synchronisation): the grid is sized on the device.
+ * If the cell lists of the requested grid (grid_density) would overflow the
+ * workspace's entry capacity, the grid is coarsened (1/16 of the cells, then
+ * at most 2 cells, which always fit) and SOP_DEVSTAT_GRID_COARSENED is set
+ * in the device status word; the result is the same, only slower. Gaussians
+ * with non-finite parameters are left out and a ray that cannot split its
+ * hits is stopped; both set device status bits (sop_device_status).
+ * ws_bytes below sop_bake_workspace_bytes() gives SOP_ERR_WORKSPACE. */
 sop_status sop_bake(const sop_gaussians* g, const sop_atlas* atlas, const sop_bake_params* params, void* ws,
                     size_t ws_bytes, void* stream);
 
 /* First half of sop_bake: bin the Gaussians into the grid kept in `ws`.
- * Synchronises `stream` once (see sop_bake). */
+ * Asynchronous (see sop_bake for the device-side sizing of the grid). */
 sop_status sop_bake_bin(const sop_gaussians* g, const sop_bake_params* params, void* ws, size_t ws_bytes,
                         void* stream);
 

@@ -35,6 +35,7 @@ struct AdjK {
     const float* probe_pos;
     float specular;
     const float* grad_out;
+    unsigned int* status;  // device status word or NULL
     float *g_albedo, *g_rough, *g_metal, *g_normal, *g_env;
     float4* g_maps;  // [P][R][R] (d rgb, d O)
     const int32_t* perm;  // order in which the points are taken
@@ -61,6 +62,8 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjK a)
     const float3 alb = load3(a.albedo, m);
     const float r = __ldg(a.rough + m), mt = __ldg(a.metal + m);
     const float3 go = load3(a.grad_out, m);
+    if (a.status && !isfinite(go.x + go.y + go.z + alb.x + alb.y + alb.z + r + mt + wo.x + wo.y + wo.z))
+        atomicOr(a.status, SOP_DEVSTAT_NONFINITE);
     const int RS = a.R + 2;
     const typename TX::raw* atlas = reinterpret_cast<const typename TX::raw*>(a.rgbo);
     int32_t pid[KMAX];
@@ -428,6 +431,7 @@ cudaError_t launch_adjoint(const QueryArgs& a, const QueryLayout& L, char* ws, c
     k.probe_pos = a.probe_pos;
     k.specular = a.specular;
     k.grad_out = a.grad_out;
+    k.status = status_word();
     k.g_albedo = a.g_albedo;
     k.g_rough = a.g_rough;
     k.g_metal = a.g_metal;

@@ -42,18 +42,16 @@ constexpr int kMaxR = 64;
 
 // Capacity of the binning grid: the grid gets about half of it, i.e.
 // `density` cells per Gaussian when given (> 0), else 0.35 (a capacity of 70
-// cells per 100 Gaussians; SOP_BAKE_CELLS overrides that capacity, 5..400,
-// for tuning).
+// cells per 100 Gaussians).
+constexpr int64_t kCellsPer100 = 70;
 static int64_t cells_cap_for(int64_t N, float density)
 {
-    static const int64_t per100 = [] {
-        const char* e = getenv("SOP_BAKE_CELLS");
-        const int v = e ? atoi(e) : 0;
-        return (int64_t)((v >= 5 && v <= 400) ? v : 70);
-    }();
-    const int64_t c = density > 0.f ? (int64_t)(2.0 * (double)density * (double)N) : N * per100 / 100;
+    const int64_t c = density > 0.f ? (int64_t)(2.0 * (double)density * (double)N) : N * kCellsPer100 / 100;
     return c < 4096 ? 4096 : (c > (1 << 23) ? (1 << 23) : c);
 }
+
+// binning attempts of launch_bake_bin
+constexpr int kBinAttempts = 3;
 
 BakeLayout bake_layout(int64_t N, int64_t entries_cap, float density)
 {
@@ -88,8 +86,11 @@ __global__ void bbox_init_kernel(int32_t* bbox)
     else if (threadIdx.x < 8) bbox[threadIdx.x] = 0;  // [6]: binning status word
 }
 
-// Per-Gaussian record + bounding box of the (margin-expanded) spheres.
-__global__ void gauss_prep_kernel(sop_gaussians g, float alpha_min, GRec* __restrict__ rec, int32_t* bbox)
+// Per-Gaussian record + bounding box of the (margin-expanded) spheres. A
+// Gaussian with a non-finite parameter, a scale <= 0 or a zero quaternion is
+// left out of the bake (rho < 0) and flagged in the device status word.
+__global__ void gauss_prep_kernel(sop_gaussians g, float alpha_min, GRec* __restrict__ rec, int32_t* bbox,
+                                  unsigned int* status)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
@@ -105,8 +106,13 @@ __global__ void gauss_prep_kernel(sop_gaussians g, float alpha_min, GRec* __rest
         const float ix = 1.f / sx, iy = 1.f / sy, iz = 1.f / sz;
         const float o = g.opacity[i];
         const float3 mu = load3(g.mean, i);
+        const float c0 = g.rgb[3 * i], c1 = g.rgb[3 * i + 1], c2 = g.rgb[3 * i + 2];
+        // a NaN anywhere makes the sum NaN; an Inf makes it Inf or NaN
+        const bool ok = isfinite(mu.x + mu.y + mu.z + sx + sy + sz + qw + qx + qy + qz + o + c0 + c1 + c2) &&
+                        sx > 0.f && sy > 0.f && sz > 0.f && qn > 0.f && isfinite(ix + iy + iz);
+        if (!ok && status) atomicOr(status, SOP_DEVSTAT_NONFINITE);
         float rho = -1.f, ex = 0.f, ey = 0.f, ez = 0.f;
-        if (o >= alpha_min && o > 0.f) {
+        if (ok && o >= alpha_min && o > 0.f) {
             // {x : o exp(-m^2(x)/2) >= alpha_min} is the ellipsoid m^2 <= kk^2
             const float kk = sqrtf(2.f * fmaxf(logf(o / alpha_min), 0.f));
             const float smax = fmaxf(sx, fmaxf(sy, sz));
@@ -125,8 +131,8 @@ __global__ void gauss_prep_kernel(sop_gaussians g, float alpha_min, GRec* __rest
         // M = diag(1/s) R^T : row a = R[:, a] / s_a
         r.r1 = make_float4(R00 * ix, R10 * ix, R20 * ix, R01 * iy);
         r.r2 = make_float4(R11 * iy, R21 * iy, R02 * iz, R12 * iz);
-        r.r3 = make_float4(R22 * iz, o, g.rgb[3 * i], g.rgb[3 * i + 1]);
-        r.r4 = make_float4(g.rgb[3 * i + 2], ex, ey, ez);
+        r.r3 = make_float4(R22 * iz, o, c0, c1);
+        r.r4 = make_float4(c2, ex, ey, ez);
         rec[i] = r;
         if (rho >= 0.f) {
             lo[0] = mu.x - ex; lo[1] = mu.y - ey; lo[2] = mu.z - ez;
@@ -151,10 +157,14 @@ __global__ void gauss_prep_kernel(sop_gaussians g, float alpha_min, GRec* __rest
 }
 
 // Grid geometry from the bounding box: cubic cells, about cells_cap/2 of
-// them over the box, never more than cells_cap.
-__global__ void grid_setup_kernel(const int32_t* bbox, int64_t cells_cap, GaussGrid* grid, int32_t* cell_cnt)
+// them over the box, never more than cells_cap. Binning attempt `level`
+// (> 0: the previous attempt's cell lists did not fit the workspace) does
+// nothing once an earlier attempt fitted.
+__global__ void grid_setup_kernel(const int32_t* bbox, int64_t cells_cap, int32_t level, GaussGrid* grid,
+                                  int32_t* cell_cnt)
 {
     __shared__ GaussGrid G;
+    if (level > 0 && grid->fits) return;
     if (threadIdx.x == 0) {
         float lo[3], hi[3], ext[3];
         bool empty = false;
@@ -201,6 +211,8 @@ __global__ void grid_setup_kernel(const int32_t* bbox, int64_t cells_cap, GaussG
         G.inv_h = (float)(1.0 / h);
         G.ncells = (int32_t)nc;
         G.n_entries = 0;
+        G.fits = 0;
+        G.level = level;
         *grid = G;
     }
     __syncthreads();
@@ -261,7 +273,7 @@ __global__ void bin_count_kernel(int64_t N, const GRec* __restrict__ rec, const 
                                  int32_t* __restrict__ cell_cnt)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (i >= N || gridp->fits) return;
     const float4 r0 = rec[i].r0;
     if (r0.w < 0.f) return;
     const GaussGrid G = *gridp;
@@ -272,11 +284,15 @@ __global__ void bin_count_kernel(int64_t N, const GRec* __restrict__ rec, const 
             for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&cell_cnt[(z * G.dims[1] + y) * G.dims[0] + x], 1);
 }
 
-// Exclusive scan of the cell counts in one CTA; total into grid->n_entries.
+// Exclusive scan of the cell counts in one CTA; total into grid->n_entries,
+// and grid->fits = 1 when the total fits the entry capacity (an attempt
+// after the first that fits marks the status word: the grid was coarsened).
 __global__ void __launch_bounds__(1024) bin_scan_kernel(GaussGrid* gridp, int32_t* __restrict__ cell_cnt,
-                                                         int32_t* __restrict__ cell_start)
+                                                         int32_t* __restrict__ cell_start, int64_t entries_cap,
+                                                         unsigned int* status)
 {
     __shared__ int64_t s_part[1024];
+    if (gridp->fits) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nc = gridp->ncells;
     const int chunk = (nc + nt - 1) / nt;
@@ -291,6 +307,8 @@ __global__ void __launch_bounds__(1024) bin_scan_kernel(GaussGrid* gridp, int32_
         s_part[tid] += v;
         __syncthreads();
     }
+    const int64_t tot = s_part[nt - 1];
+    const bool fit = tot <= entries_cap && tot < INT32_MAX;
     int64_t run = s_part[tid] - sum;
     for (int c = c0; c < c1; ++c) {
         const int32_t v = cell_cnt[c];
@@ -298,10 +316,12 @@ __global__ void __launch_bounds__(1024) bin_scan_kernel(GaussGrid* gridp, int32_
         run += v;
         cell_cnt[c] = 0;
     }
+    __syncthreads();
     if (tid == nt - 1) {
-        const int64_t tot = s_part[nt - 1];
         cell_start[nc] = (int32_t)(tot < INT32_MAX ? tot : INT32_MAX);
         gridp->n_entries = (int32_t)(tot < INT32_MAX ? tot : INT32_MAX);
+        gridp->fits = fit ? 1 : 0;
+        if (fit && gridp->level > 0 && status) atomicOr(status, SOP_DEVSTAT_GRID_COARSENED);
     }
 }
 
@@ -310,7 +330,7 @@ __global__ void bin_fill_kernel(int64_t N, const GRec* __restrict__ rec, const G
                                 uint4* __restrict__ ent)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (i >= N || !gridp->fits) return;
     const float4 r0 = rec[i].r0;
     if (r0.w < 0.f) return;
     const GaussGrid G = *gridp;
@@ -373,6 +393,8 @@ struct TraceK {
     // scales and materials, and the output [rays][4] float4
     const float *quat, *scale, *albedo, *rough, *metal;
     float4* gbuf;
+    // device status word (SOP_DEVSTAT_* bits) or NULL
+    unsigned int* status;
 };
 
 // what a traced ray writes: the probe atlas texel (O, L_in, depth) or the
@@ -757,6 +779,10 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
     const float4 d4 = __ldg(k.dirs + t);
     const float3 d = f3(d4.x, d4.y, d4.z);
     const float3 o = load3(k.probe_pos, p);
+    // a non-finite origin or direction is reported, and its ray traces
+    // nothing (empty composite)
+    const bool ray_ok = isfinite(o.x + o.y + o.z + d.x + d.y + d.z);
+    if (!ray_ok && lane == 0 && k.status) atomicOr(k.status, SOP_DEVSTAT_NONFINITE);
     // reciprocal direction for the box entries (a zero component becomes a
     // tiny one: the slab along that axis is then all or nothing)
     const float3 iv = f3(1.f / (fabsf(d.x) > 1e-30f ? d.x : 1e-30f), 1.f / (fabsf(d.y) > 1e-30f ? d.y : 1e-30f),
@@ -796,7 +822,7 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
     SOP_SLAB(o.y, d.y, iv.y, goy, gmy)
     SOP_SLAB(o.z, d.z, iv.z, goz, gmz)
 #undef SOP_SLAB
-    if (G.n_entries > 0 && t0 <= t1) {
+    if (ray_ok && G.fits && G.n_entries > 0 && t0 <= t1) {
         int cx = min(max((int)floorf((o.x + t0 * d.x - gox) * gih), 0), gdx - 1);
         int cy = min(max((int)floorf((o.y + t0 * d.y - goy) * gih), 0), gdy - 1);
         int cz = min(max((int)floorf((o.z + t0 * d.z - goz) * gih), 0), gdz - 1);
@@ -864,7 +890,10 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
                         n = nb;
                         pend = pb;
                         if (++splits > 40 || !(sh > sl)) {
-                            if (lane == 0) atomicOr(k.stats + 3, 1ull);
+                            if (lane == 0) {
+                                atomicOr(k.stats + 3, 1ull);
+                                if (k.status) atomicOr(k.status, SOP_DEVSTAT_BAKE_TRUNCATED);
+                            }
                             acc.done = true;
                             break;
                         }
@@ -973,13 +1002,22 @@ cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeL
     GRec* rec = reinterpret_cast<GRec*>(ws + L.rec);
     int32_t* cstart = reinterpret_cast<int32_t*>(ws + L.cell_start);
     int32_t* ccnt = reinterpret_cast<int32_t*>(ws + L.cell_cnt);
+    unsigned int* status = status_word();
     bbox_init_kernel<<<1, 32, 0, s>>>(bbox);
     const int bs = 256;
     const unsigned nb = (unsigned)((g.n + bs - 1) / bs);
-    if (g.n > 0) gauss_prep_kernel<<<nb, bs, 0, s>>>(g, alpha_min, rec, bbox);
-    grid_setup_kernel<<<1, 1024, 0, s>>>(bbox, L.cells_cap, grid, ccnt);
-    if (g.n > 0) bin_count_kernel<<<nb, bs, 0, s>>>(g.n, rec, grid, ccnt);
-    bin_scan_kernel<<<1, 1024, 0, s>>>(grid, ccnt, cstart);
+    if (g.n > 0) gauss_prep_kernel<<<nb, bs, 0, s>>>(g, alpha_min, rec, bbox, status);
+    // Binning attempts, decided on the device (no host read-back): the
+    // requested grid; if its cell lists overflow the workspace, a grid with
+    // 1/16 of the cells; then one of at most 2 cells, whose lists (at most
+    // 2 entries per Gaussian) always fit, since the workspace holds at least
+    // 24 per Gaussian. Attempts after a fitting one return at once.
+    const int64_t caps[kBinAttempts] = {L.cells_cap, L.cells_cap / 16 > 64 ? L.cells_cap / 16 : 64, 2};
+    for (int a = 0; a < kBinAttempts; ++a) {
+        grid_setup_kernel<<<1, 1024, 0, s>>>(bbox, caps[a], a, grid, ccnt);
+        if (g.n > 0) bin_count_kernel<<<nb, bs, 0, s>>>(g.n, rec, grid, ccnt);
+        bin_scan_kernel<<<1, 1024, 0, s>>>(grid, ccnt, cstart, L.entries_cap, status);
+    }
     return cudaGetLastError();
 }
 
@@ -1073,23 +1111,12 @@ cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp,
     k.depth_dtype = atlas.depth_dtype;
     k.inv_depth_scale = 1.f / atlas.depth_scale;
     k.stats = stats;
-    // SOP_BAKE_COMPOSITE_AT overrides the default for tuning
-    static const int composite_at = [] {
-        const char* e = getenv("SOP_BAKE_COMPOSITE_AT");
-        const int v = e ? atoi(e) : 0;
-        return (v >= 1 && v <= kHitCap / 2) ? v : kCompositeAt;
-    }();
-    k.composite_at = composite_at;
+    k.composite_at = kCompositeAt;
     k.n_dirs = (int64_t)R * R;
-    // SOP_BAKE_BATCH overrides the rays a warp takes at a time (1..16), for tuning
-    static const int batch = [] {
-        const char* e = getenv("SOP_BAKE_BATCH");
-        const int v = e ? atoi(e) : 0;
-        return (v >= 1 && v <= 16) ? v : 1;
-    }();
-    k.batch = batch;
+    k.batch = 1;
     k.quat = k.scale = k.albedo = k.rough = k.metal = nullptr;
     k.gbuf = nullptr;
+    k.status = status_word();
     const int64_t rays = (int64_t)atlas.P * R * R;
     trace_kernel<kTraceAtlas><<<trace_blocks<kTraceAtlas>(rays), kWarpsPerCta * 32, 0, s>>>(k);
     return launch_gutter_fill(atlas, s);
@@ -1127,6 +1154,7 @@ cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, co
     k.rough = rough;
     k.metal = metal;
     k.gbuf = reinterpret_cast<float4*>(out);
+    k.status = status_word();
     const int64_t rays = (int64_t)n_origins * n_dirs;
     if (rays == 0) return cudaGetLastError();
     trace_kernel<kTraceGbuf><<<trace_blocks<kTraceGbuf>(rays), kWarpsPerCta * 32, 0, s>>>(k);

@@ -169,24 +169,31 @@ __global__ void comp_scene_kernel(const float4* __restrict__ sg, int64_t n, floa
 
 // pixel lists come from the compaction (distinct pixels); others are skipped
 __global__ void comp_shadow_kernel(const int64_t* __restrict__ pix, const float* __restrict__ S, int64_t n_sc,
-                                   int64_t n, float* __restrict__ out)
+                                   int64_t n, float* __restrict__ out, unsigned int* status)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_sc) return;
     const int64_t p = pix[k];
-    if (p < 0 || p >= n) return;
+    if (p < 0 || p >= n) {
+        if (status) atomicOr(status, SOP_DEVSTAT_INDEX);
+        return;
+    }
     out[3 * p] *= S[3 * k];
     out[3 * p + 1] *= S[3 * k + 1];
     out[3 * p + 2] *= S[3 * k + 2];
 }
 
 __global__ void comp_object_kernel(const float4* __restrict__ og, const int64_t* __restrict__ pix,
-                                   const float* __restrict__ rgb, int64_t n_obj, int64_t n, float* __restrict__ out)
+                                   const float* __restrict__ rgb, int64_t n_obj, int64_t n, float* __restrict__ out,
+                                   unsigned int* status)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_obj) return;
     const int64_t p = pix[k];
-    if (p < 0 || p >= n) return;
+    if (p < 0 || p >= n) {
+        if (status) atomicOr(status, SOP_DEVSTAT_INDEX);
+        return;
+    }
     const float a = __ldg(og + 4 * p).w;
     for (int c = 0; c < 3; ++c) out[3 * p + c] = fmaf(a, rgb[3 * k + c], (1.f - a) * out[3 * p + c]);
 }
@@ -277,10 +284,11 @@ cudaError_t launch_depth_composite(const float* scene_gbuf, const float* obj_gbu
 {
     if (n == 0) return cudaSuccess;
     comp_scene_kernel<<<blocks_for(n, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(scene_gbuf), n, out);
-    if (n_sc > 0) comp_shadow_kernel<<<blocks_for(n_sc, 256), 256, 0, s>>>(sc_pix, shadow, n_sc, n, out);
+    unsigned int* status = status_word();
+    if (n_sc > 0) comp_shadow_kernel<<<blocks_for(n_sc, 256), 256, 0, s>>>(sc_pix, shadow, n_sc, n, out, status);
     if (n_obj > 0)
         comp_object_kernel<<<blocks_for(n_obj, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(obj_gbuf), obj_pix,
-                                                                  obj_rgb, n_obj, n, out);
+                                                                  obj_rgb, n_obj, n, out, status);
     return cudaGetLastError();
 }
 

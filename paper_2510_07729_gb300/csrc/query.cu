@@ -238,12 +238,20 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
                                                    const int4* __restrict__ entries,
                                                    const float* __restrict__ probe_pos, int32_t* __restrict__ ws_idx,
                                                    float* __restrict__ ws_w, int32_t* __restrict__ user_idx,
-                                                   float* __restrict__ user_w)
+                                                   float* __restrict__ user_w, unsigned int* status)
 {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     const ProbeGrid G = *gridp;
-    const float3 xp = load3(x, m);
+    float3 xp = load3(x, m);
+    {
+        // a non-finite position or normal is reported; the position is then
+        // taken as the origin so that the search stays defined
+        const float3 nr0 = load3(nrm, m);
+        const bool okx = isfinite(xp.x + xp.y + xp.z);
+        if ((!okx || !isfinite(nr0.x + nr0.y + nr0.z)) && status) atomicOr(status, SOP_DEVSTAT_NONFINITE);
+        if (!okx) xp = f3(0.f, 0.f, 0.f);
+    }
     const int32_t q[3] = {quantise(xp.x), quantise(xp.y), quantise(xp.z)};
     // rings are taken around the point's cell clamped into the grid
     int c[3];
@@ -341,7 +349,8 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
 // and He+1 repeat the first and last row: v clamps), stored column We =
 // column 0 (u wraps).
 // ---------------------------------------------------------------------------
-__global__ void env_pack_kernel(const float* __restrict__ env, int32_t He, int32_t We, float4* __restrict__ env4)
+__global__ void env_pack_kernel(const float* __restrict__ env, int32_t He, int32_t We, float4* __restrict__ env4,
+                                unsigned int* status)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t n = (int64_t)(He + 2) * (We + 1);
@@ -349,6 +358,7 @@ __global__ void env_pack_kernel(const float* __restrict__ env, int32_t He, int32
     const int rs = (int)(i / (We + 1)), cs = (int)(i % (We + 1));
     const int r = min(max(rs - 1, 0), He - 1), c = cs == We ? 0 : cs;
     const float* e = env + ((int64_t)r * We + c) * 3;
+    if (!isfinite(e[0] + e[1] + e[2]) && status) atomicOr(status, SOP_DEVSTAT_NONFINITE);
     env4[i] = make_float4(e[0], e[1], e[2], 0.f);
 }
 
@@ -373,7 +383,8 @@ __global__ void env_quad_kernel(const float4* __restrict__ env4, int32_t He, int
 // (a, b) in [0, H]^2, the texels (a-1+di, b-1+dj), di, dj in {0, 1}, through
 // the probe maps' border rule, in the 64-byte slot format of env_quad_kernel
 // (e00, e01 = next column, e10 = next row, e11).
-__global__ void env_oct_quad_kernel(const float* __restrict__ env, int32_t H, float4* __restrict__ envq)
+__global__ void env_oct_quad_kernel(const float* __restrict__ env, int32_t H, float4* __restrict__ envq,
+                                    unsigned int* status)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int HQ = H + 1;
@@ -386,6 +397,7 @@ __global__ void env_oct_quad_kernel(const float* __restrict__ env, int32_t H, fl
         const float* t = env + ((int64_t)sj * H + si) * 3;
         e[q] = f3(t[0], t[1], t[2]);
     }
+    if (!isfinite(e[0].x + e[0].y + e[0].z) && status) atomicOr(status, SOP_DEVSTAT_NONFINITE);
     float4* o = envq + 4 * k;
     o[0] = make_float4(e[0].x, e[0].y, e[0].z, e[1].x);
     o[1] = make_float4(e[1].y, e[1].z, e[2].x, e[2].y);
@@ -398,7 +410,7 @@ __global__ void env_oct_quad_kernel(const float* __restrict__ env, int32_t H, fl
 // contiguously, so one bilinear fetch reads one aligned 32/64-byte block.
 template <int DT>
 __global__ void atlas_quad_kernel(const typename Texel<DT>::raw* __restrict__ atlas, int32_t P, int32_t R,
-                                  typename Texel<DT>::raw* __restrict__ quads)
+                                  typename Texel<DT>::raw* __restrict__ quads, unsigned int* status)
 {
     const int RS = R + 2, RQ = R + 1;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -408,6 +420,8 @@ __global__ void atlas_quad_kernel(const typename Texel<DT>::raw* __restrict__ at
     const int b = r / RQ, a = r % RQ;
     const typename Texel<DT>::raw* src = atlas + pr * RS * RS + (int64_t)b * RS + a;
     typename Texel<DT>::raw* dst = quads + 4 * i;
+    // every interior texel is the first texel of one footprint
+    if (!Texel<DT>::finite(src[0]) && status) atomicOr(status, SOP_DEVSTAT_NONFINITE);
     dst[0] = src[0];
     dst[1] = src[1];
     dst[2] = src[RS];
@@ -418,7 +432,7 @@ __global__ void atlas_quad_kernel(const typename Texel<DT>::raw* __restrict__ at
 // four O values of each footprint, as float4 (float32 atlas) or four
 // 16-bit values in 8 bytes, so one probe fetch is one 128/64-bit load.
 __global__ void atlas_occ_quad_f32_kernel(const float4* __restrict__ atlas, int32_t P, int32_t R,
-                                          float4* __restrict__ quads)
+                                          float4* __restrict__ quads, unsigned int* status)
 {
     const int RS = R + 2, RQ = R + 1;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -427,12 +441,14 @@ __global__ void atlas_occ_quad_f32_kernel(const float4* __restrict__ atlas, int3
     const int r = (int)(i % (RQ * RQ));
     const int b = r / RQ, a = r % RQ;
     const float4* src = atlas + pr * RS * RS + (int64_t)b * RS + a;
+    if (!isfinite(src[0].w) && status) atomicOr(status, SOP_DEVSTAT_NONFINITE);
     quads[i] = make_float4(src[0].w, src[1].w, src[RS].w, src[RS + 1].w);
 }
 
 // 16-bit texels (R, G, B, O): O is the upper half of the second word.
+template <int DT>
 __global__ void atlas_occ_quad_16_kernel(const uint2* __restrict__ atlas, int32_t P, int32_t R,
-                                         uint2* __restrict__ quads)
+                                         uint2* __restrict__ quads, unsigned int* status)
 {
     const int RS = R + 2, RQ = R + 1;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -441,6 +457,7 @@ __global__ void atlas_occ_quad_16_kernel(const uint2* __restrict__ atlas, int32_
     const int r = (int)(i % (RQ * RQ));
     const int b = r / RQ, a = r % RQ;
     const uint2* src = atlas + pr * RS * RS + (int64_t)b * RS + a;
+    if (!Texel<DT>::finite(src[0]) && status) atomicOr(status, SOP_DEVSTAT_NONFINITE);
     quads[i] = make_uint2((src[0].y >> 16) | (src[1].y & 0xffff0000u), (src[RS].y >> 16) | (src[RS + 1].y & 0xffff0000u));
 }
 
@@ -683,6 +700,7 @@ struct ShadeK {
     const float* w;
     float specular;
     float* out;
+    unsigned int* status;  // device status word or NULL
 };
 
 // ---------------------------------------------------------------------------
@@ -740,6 +758,8 @@ __global__ void __launch_bounds__(256, 4) shade_kernel(const ShadeK a, const int
     if (MODE == SOP_MODE_SHADE) {
         const float3 alb = load3(a.albedo, mm);
         const float r = __ldg(a.rough + mm), mt = __ldg(a.metal + mm);
+        if (a.status && active && sub == 0 && !isfinite(alb.x + alb.y + alb.z + r + mt + wo.x + wo.y + wo.z))
+            atomicOr(a.status, SOP_DEVSTAT_NONFINITE);
         const float dsc = (1.f - mt) * kInvPi;
         kd = f3(dsc * alb.x, dsc * alb.y, dsc * alb.z);
         const float f0d = 0.08f * a.specular * (1.f - mt);
@@ -936,6 +956,8 @@ __global__ void __launch_bounds__(256, 4) shade_world_kernel(const ShadeK a, con
     if (MODE == SOP_MODE_SHADE) {
         const float3 alb = load3(a.albedo, mm);
         const float r = __ldg(a.rough + mm), mt = __ldg(a.metal + mm);
+        if (a.status && active && sub == 0 && !isfinite(alb.x + alb.y + alb.z + r + mt + wo.x + wo.y + wo.z))
+            atomicOr(a.status, SOP_DEVSTAT_NONFINITE);
         const float dsc = (1.f - mt) * kInvPi;
         kd = f3(dsc * alb.x, dsc * alb.y, dsc * alb.z);
         const float f0d = 0.08f * a.specular * (1.f - mt);
@@ -1038,6 +1060,7 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
     int32_t* cstart = reinterpret_cast<int32_t*>(ws + L.cell_start);
     int32_t* ccnt = reinterpret_cast<int32_t*>(ws + L.cell_cnt);
     int4* ent = reinterpret_cast<int4*>(ws + L.entries);
+    unsigned int* status = status_word();
     probe_grid_kernel<<<1, 1024, 0, s>>>(a.probe_pos, a.P, L.g_axis, grid, cstart, ccnt, ent);
     int32_t* idx = reinterpret_cast<int32_t*>(ws + L.idx);
     float* w = reinterpret_cast<float*>(ws + L.w);
@@ -1046,7 +1069,7 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
         const unsigned nb = (unsigned)((a.M + bs - 1) / bs);
 #define SOP_KNN(KM) \
     knn_kernel<KM><<<nb, bs, 0, s>>>(a.x, a.n, a.M, a.K, a.snap_key, a.r2_key, grid, cstart, ent, a.probe_pos, idx, w, \
-                                     a.out_idx, a.out_w)
+                                     a.out_idx, a.out_w, status)
         if (a.K <= 4) SOP_KNN(4);
         else if (a.K <= 8) SOP_KNN(8);
         else if (a.K <= 16) SOP_KNN(16);
@@ -1056,11 +1079,11 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
     if (a.env_layout == SOP_ENV_OCTAHEDRAL) {
         const int64_t nq = (int64_t)(a.He + 1) * (a.He + 1);
         env_oct_quad_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(a.env, a.He,
-                                                                         reinterpret_cast<float4*>(ws + L.envq));
+                                                                         reinterpret_cast<float4*>(ws + L.envq), status);
     } else {
         const int64_t ne = (int64_t)(a.He + 2) * (a.We + 1);
         env_pack_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(a.env, a.He, a.We,
-                                                                       reinterpret_cast<float4*>(ws + L.env4));
+                                                                       reinterpret_cast<float4*>(ws + L.env4), status);
         const int64_t nq = (int64_t)(a.He + 1) * a.We;
         env_quad_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(ws + L.env4),
                                                                        a.He, a.We,
@@ -1072,22 +1095,25 @@ cudaError_t launch_query_prep(const QueryArgs& a, const QueryLayout& L, char* ws
         // occlusion-only footprints (a quarter of the RGBO ones, same slot)
         if (a.rgbo_dtype == SOP_F32)
             atlas_occ_quad_f32_kernel<<<nba, 256, 0, s>>>(reinterpret_cast<const float4*>(a.rgbo), a.P, a.R,
-                                                          reinterpret_cast<float4*>(ws + L.quads));
+                                                          reinterpret_cast<float4*>(ws + L.quads), status);
+        else if (a.rgbo_dtype == SOP_BF16)
+            atlas_occ_quad_16_kernel<SOP_BF16><<<nba, 256, 0, s>>>(reinterpret_cast<const uint2*>(a.rgbo), a.P, a.R,
+                                                                   reinterpret_cast<uint2*>(ws + L.quads), status);
         else
-            atlas_occ_quad_16_kernel<<<nba, 256, 0, s>>>(reinterpret_cast<const uint2*>(a.rgbo), a.P, a.R,
-                                                         reinterpret_cast<uint2*>(ws + L.quads));
+            atlas_occ_quad_16_kernel<SOP_F16><<<nba, 256, 0, s>>>(reinterpret_cast<const uint2*>(a.rgbo), a.P, a.R,
+                                                                  reinterpret_cast<uint2*>(ws + L.quads), status);
     } else switch (a.rgbo_dtype) {
     case SOP_F32:
         atlas_quad_kernel<SOP_F32><<<nba, 256, 0, s>>>(reinterpret_cast<const float4*>(a.rgbo), a.P, a.R,
-                                                      reinterpret_cast<float4*>(ws + L.quads));
+                                                      reinterpret_cast<float4*>(ws + L.quads), status);
         break;
     case SOP_BF16:
         atlas_quad_kernel<SOP_BF16><<<nba, 256, 0, s>>>(reinterpret_cast<const uint2*>(a.rgbo), a.P, a.R,
-                                                       reinterpret_cast<uint2*>(ws + L.quads));
+                                                       reinterpret_cast<uint2*>(ws + L.quads), status);
         break;
     default:
         atlas_quad_kernel<SOP_F16><<<nba, 256, 0, s>>>(reinterpret_cast<const uint2*>(a.rgbo), a.P, a.R,
-                                                      reinterpret_cast<uint2*>(ws + L.quads));
+                                                      reinterpret_cast<uint2*>(ws + L.quads), status);
         break;
     }
     if (a.dir_world)
@@ -1117,20 +1143,13 @@ static cudaError_t shade_launch(const ShadeK& k, int LANES, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Threads per shading point (they split the S directions); SOP_SHADE_LANES
-// overrides the default for tuning.
-// Default (measured on GB300, object workload): one thread per point for a
-// float32 atlas, two for 16-bit atlases; small point sets (the composition
-// frame's 21,907 object pixels) take more lanes per point, up to 8, until the
-// launch has about two waves of threads on the 152 SMs.
+// Threads per shading point (they split the S directions).
+// Measured on GB300, object workload: one thread per point for a float32
+// atlas, two for 16-bit atlases; small point sets (the composition frame's
+// 21,907 object pixels) take more lanes per point, up to 8, until the launch
+// has about two waves of threads on the 152 SMs.
 static int shade_lanes(int dtype, int64_t M)
 {
-    static int lanes = [] {
-        const char* e = getenv("SOP_SHADE_LANES");
-        const int v = e ? atoi(e) : 0;
-        return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 0;
-    }();
-    if (lanes) return lanes;
     int l = dtype == SOP_F32 ? 1 : 2;
     while (l < 8 && M * l < (int64_t)2 * 152 * 1024) l *= 2;
     return l;
@@ -1209,6 +1228,7 @@ cudaError_t launch_shade(const QueryArgs& a, const QueryLayout& L, char* ws, cud
     k.w = reinterpret_cast<const float*>(ws + L.w);
     k.specular = a.specular;
     k.out = a.out;
+    k.status = status_word();
     switch (a.rgbo_dtype) {
     case SOP_F32: return shade_mode<SOP_F32>(k, a.mode, a.dir_world != 0, s);
     case SOP_BF16: return shade_mode<SOP_BF16>(k, a.mode, a.dir_world != 0, s);
@@ -1870,7 +1890,7 @@ cudaError_t launch_query_noalloc(const QueryArgs& a, cudaStream_t s)
         float* uw = a.out_w ? a.out_w + m0 * a.K : nullptr;
 #define SOP_KNN_NA(KM)                                                                                             \
     knn_kernel<KM><<<nb, 128, 0, s>>>(a.x + 3 * m0, a.n + 3 * m0, mc, a.K, a.snap_key, a.r2_key, grid, cstart, ent, \
-                                      a.probe_pos, idx, w, uidx, uw)
+                                      a.probe_pos, idx, w, uidx, uw, status_word())
         if (a.K <= 4) SOP_KNN_NA(4);
         else if (a.K <= 8) SOP_KNN_NA(8);
         else if (a.K <= 16) SOP_KNN_NA(16);

@@ -98,7 +98,17 @@ extern "C" {
 
 const char* sop_last_error(void) { return g_err; }
 
-const char* sop_version(void) { return "libsop 0.1 (sm_103a)"; }
+const char* sop_version(void) { return "libsop 0.2 (sm_103a)"; }
+
+sop_status sop_device_status(void* stream, uint32_t* out_bits, int32_t clear)
+{
+    uint32_t bits = 0;
+    sop_status st = cuda_status(sop::status_take(&bits, clear != 0, (cudaStream_t)stream), "sop_device_status");
+    if (st != SOP_OK) return st;
+    if (out_bits) *out_bits = bits;
+    if (bits & SOP_DEVSTAT_ERRORS) return fail(SOP_ERR_DEVICE, "device status 0x%x: %s", bits, sop::status_bits_message(bits));
+    return SOP_OK;
+}
 
 sop_status sop_atlas_bytes(int32_t P, int32_t R, int32_t rgbo_dtype, int32_t depth_dtype, size_t* rgbo_bytes,
                            size_t* depth_bytes)
@@ -219,14 +229,19 @@ static sop_status check_bake_args(const sop_gaussians* g, const sop_bake_params*
     return SOP_OK;
 }
 
-// The layout with the largest cell-entry capacity that fits ws_bytes.
+// The layout with the largest cell-entry capacity that fits ws_bytes. The
+// workspace must hold at least the default capacity (24 entries per Gaussian
+// plus 65,536), which the device-side binning relies on: its last attempt,
+// a grid of at most 2 cells, needs at most 2 entries per Gaussian.
 static sop_status bake_fit(int64_t n, float density, void* ws, size_t ws_bytes, sop::BakeLayout& L)
 {
-    const sop::BakeLayout L0 = sop::bake_layout(n, 1, density);
-    if (!ws || ws_bytes < L0.total) return check_ws(ws, ws_bytes, sop::bake_layout(n, 0, density).total);
-    int64_t cap = 64 + (int64_t)((ws_bytes - L0.total) / sop::kBakeEntryBytes);
+    const sop::BakeLayout Lmin = sop::bake_layout(n, 0, density);
+    sop_status st = check_ws(ws, ws_bytes, Lmin.total);
+    if (st != SOP_OK) return st;
+    const sop::BakeLayout L1 = sop::bake_layout(n, 1, density);
+    int64_t cap = 1 + (int64_t)((ws_bytes - L1.total) / sop::kBakeEntryBytes);
     L = sop::bake_layout(n, cap, density);
-    while (L.total > ws_bytes && L.entries_cap > 1) L = sop::bake_layout(n, L.entries_cap - 1, density);
+    while (L.total > ws_bytes && L.entries_cap > Lmin.entries_cap) L = sop::bake_layout(n, L.entries_cap - 1, density);
     return check_ws(ws, ws_bytes, L.total);
 }
 
@@ -241,19 +256,6 @@ sop_status sop_bake_bin(const sop_gaussians* g, const sop_bake_params* params, v
     char* w = (char*)ws;
     st = cuda_status(sop::launch_bake_bin(*g, params->alpha_min, L, w, s), "sop_bake_bin (binning)");
     if (st != SOP_OK) return st;
-    // size check of the cell lists: one 4-byte read-back
-    int32_t n_entries = 0;
-    st = cuda_status(cudaMemcpyAsync(&n_entries, w + L.hdr + offsetof(sop::GaussGrid, n_entries), sizeof(int32_t),
-                                     cudaMemcpyDeviceToHost, s),
-                     "sop_bake_bin (read-back)");
-    if (st != SOP_OK) return st;
-    st = cuda_status(cudaStreamSynchronize(s), "sop_bake_bin (sync)");
-    if (st != SOP_OK) return st;
-    if (n_entries == INT32_MAX || (int64_t)n_entries > L.entries_cap) {
-        const sop::BakeLayout need = sop::bake_layout(g->n, (int64_t)n_entries + 1, params->grid_density);
-        return fail(SOP_ERR_WORKSPACE, "sop_bake: %d grid entries exceed the workspace; need %zu bytes", n_entries,
-                    need.total);
-    }
     return cuda_status(sop::launch_bake_fill(*g, L, w, s), "sop_bake_bin (fill)");
 }
 

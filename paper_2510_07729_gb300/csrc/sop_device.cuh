@@ -104,6 +104,7 @@ template <> struct Texel<SOP_F32> {
     using raw = float4;
     static __device__ __forceinline__ float4 load(const raw* p) { return __ldg(p); }
     static __device__ __forceinline__ raw pack(float4 v) { return v; }
+    static __device__ __forceinline__ bool finite(raw v) { return isfinite(v.x + v.y + v.z + v.w); }
 };
 template <> struct Texel<SOP_BF16> {
     using raw = uint2;
@@ -117,6 +118,12 @@ template <> struct Texel<SOP_BF16> {
     {
         __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
         return make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+    }
+    // no half has its exponent field all ones (Inf or NaN)
+    static __device__ __forceinline__ bool finite(raw v)
+    {
+        return ((v.x >> 16) & 0x7f80u) != 0x7f80u && (v.x & 0x7f80u) != 0x7f80u && ((v.y >> 16) & 0x7f80u) != 0x7f80u &&
+               (v.y & 0x7f80u) != 0x7f80u;
     }
 };
 template <> struct Texel<SOP_F16> {
@@ -132,6 +139,12 @@ template <> struct Texel<SOP_F16> {
     {
         __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
         return make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+    }
+    // no half has its exponent field all ones (Inf or NaN)
+    static __device__ __forceinline__ bool finite(raw v)
+    {
+        return ((v.x >> 16) & 0x7c00u) != 0x7c00u && (v.x & 0x7c00u) != 0x7c00u && ((v.y >> 16) & 0x7c00u) != 0x7c00u &&
+               (v.y & 0x7c00u) != 0x7c00u;
     }
 };
 
@@ -153,7 +166,9 @@ struct GaussGrid {
     int32_t dims[3];
     int32_t ncells;
     int32_t n_entries;
-    int32_t pad[3];
+    int32_t fits;    // 1 once the cell lists fit the workspace's entry capacity
+    int32_t level;   // binning attempt that fitted (0: the requested grid)
+    int32_t pad;
 };
 
 }  // namespace sop

@@ -131,6 +131,14 @@ cudaError_t launch_atlas_compare(const sop_atlas& a, const int32_t* ap, const so
 cudaError_t launch_atlas_copy(const sop_atlas& src, const int32_t* sp, const sop_atlas& dst, const int32_t* dp,
                               int32_t n, cudaStream_t s);
 
+// ---- device status word (status.cu) -------------------------------------------
+// Address of this device's status word (kernels atomicOr SOP_DEVSTAT_* bits
+// into it), or NULL if it cannot be looked up; cached per device ordinal.
+unsigned int* status_word();
+// Synchronises s after reading (and, if clear, atomically clearing) the word.
+cudaError_t status_take(uint32_t* host_out, bool clear, cudaStream_t s);
+const char* status_bits_message(uint32_t bits);
+
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 }  // namespace sop

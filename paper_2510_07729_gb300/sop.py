@@ -19,6 +19,16 @@ SOP_F32, SOP_BF16, SOP_F16, SOP_FP8E4M3 = 0, 1, 2, 3
 MODE_SHADE, MODE_SHADOW = 0, 1
 ENV_EQUIRECT, ENV_OCTAHEDRAL = 0, 1
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "WORKSPACE", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "DEVICE"}
+# bits of the device status word (include/sop.h)
+DEVSTAT_NONFINITE, DEVSTAT_BAKE_TRUNCATED, DEVSTAT_INDEX, DEVSTAT_GRID_COARSENED = 0x1, 0x2, 0x4, 0x100
+DEVSTAT_ERRORS = 0xff
+_DEVSTAT_NAMES = {DEVSTAT_NONFINITE: "nonfinite", DEVSTAT_BAKE_TRUNCATED: "bake_truncated", DEVSTAT_INDEX: "index",
+                  DEVSTAT_GRID_COARSENED: "grid_coarsened"}
+
+
+def devstat_names(bits):
+    """Names of the device status bits set in `bits` (host-side decoding)."""
+    return [name for b, name in sorted(_DEVSTAT_NAMES.items()) if bits & b]
 
 
 class SopError(RuntimeError):
@@ -78,6 +88,7 @@ def load(build_if_missing: bool = True):
     vp, i32, i64, sz, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.c_float
     lib.sop_last_error.restype = C.c_char_p
     lib.sop_version.restype = C.c_char_p
+    lib.sop_device_status.argtypes = [vp, C.POINTER(C.c_uint32), i32]
     lib.sop_atlas_bytes.argtypes = [i32, i32, i32, i32, C.POINTER(sz), C.POINTER(sz)]
     lib.sop_atlas_pack.argtypes = [vp, vp, vp, C.POINTER(AtlasDesc), vp]
     lib.sop_hammersley.argtypes = [i32, vp, vp]
@@ -133,7 +144,7 @@ def load(build_if_missing: bool = True):
                  "sop_surrogate_features", "sop_surrogate_train_step", "sop_surrogate_infer", "sop_atlas_compare",
                  "sop_atlas_copy"):
         getattr(lib, name).restype = C.c_int
-    for name in ("sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_bake_bin", "sop_bake_trace",
+    for name in ("sop_device_status", "sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_bake_bin", "sop_bake_trace",
                  "sop_bake_stats", "sop_query_shade",
                  "sop_query_shade_backward", "sop_query_shade_noalloc", "sop_read_bandwidth_probe",
                  "sop_atlas_pack_rgbo", "sop_l1_loss_grad", "sop_adam_l1_step", "sop_env_to_octahedral",
@@ -232,6 +243,17 @@ def make_atlas(probe_pos, R, rgbo_dtype=SOP_F32, depth_dtype=SOP_F32, probe_nrm=
 
 def version() -> str:
     return load().sop_version().decode()
+
+
+def device_status(clear=True, raise_on_error=True):
+    """sop_device_status on the current stream (synchronises it): returns
+    the device status bits; raises SopError (status DEVICE) when an error
+    bit is set and raise_on_error."""
+    bits = C.c_uint32(0)
+    st = load().sop_device_status(_stream(), C.byref(bits), 1 if clear else 0)
+    if st != 0 and (raise_on_error or st != 6):
+        _check(st)
+    return int(bits.value)
 
 
 def atlas_bytes(P, R, rgbo_dtype=SOP_F32, depth_dtype=SOP_F32):
@@ -440,14 +462,12 @@ def bake_workspace_bytes(n_gauss, P, R):
 
 
 class BakeWorkspace:
-    """Scratch for the bake of one Gaussian set (grows on demand)."""
+    """Scratch for the bake of one Gaussian set (sop_bake_workspace_bytes;
+    extra_bytes adds room for more grid cell entries)."""
 
-    def __init__(self, n_gauss, device):
+    def __init__(self, n_gauss, device, extra_bytes=0):
         self.n = int(n_gauss)
-        self.buf = _ws(bake_workspace_bytes(self.n, 1, 2), device)
-
-    def grow(self, nbytes):
-        self.buf = _ws(nbytes, self.buf.device)
+        self.buf = _ws(bake_workspace_bytes(self.n, 1, 2) + int(extra_bytes), device)
 
 
 def _bake_params(t_near, alpha_min, alpha_max, t_stop, grid_density=0.0):
@@ -456,20 +476,14 @@ def _bake_params(t_near, alpha_min, alpha_max, t_stop, grid_density=0.0):
 
 def bake_bin(gauss, workspace: BakeWorkspace, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4,
              grid_density=0.0):
-    """Bin the Gaussians into the grid kept in the workspace (syncs once);
-    grows the workspace once if the scene needs more cell entries.
-    grid_density: grid cells per Gaussian (0: the default, 0.35)."""
+    """Bin the Gaussians into the grid kept in the workspace (asynchronous;
+    the grid is coarsened on the device if its cell lists would overflow the
+    workspace). grid_density: grid cells per Gaussian (0: the default, 0.35)."""
     lib = load()
     g = _gauss(gauss)
     bp = _bake_params(t_near, alpha_min, alpha_max, t_stop, grid_density)
     ws = workspace
-    st = lib.sop_bake_bin(C.byref(g), C.byref(bp), _ptr(ws.buf), ws.buf.numel(), _stream())
-    if st == 3:
-        msg = lib.sop_last_error().decode()
-        need = int(msg.rsplit("need ", 1)[1].split()[0]) if "need " in msg else 2 * ws.buf.numel()
-        ws.grow(need)
-        st = lib.sop_bake_bin(C.byref(g), C.byref(bp), _ptr(ws.buf), ws.buf.numel(), _stream())
-    _check(st)
+    _check(lib.sop_bake_bin(C.byref(g), C.byref(bp), _ptr(ws.buf), ws.buf.numel(), _stream()))
     return ws
 
 
@@ -499,7 +513,8 @@ _bake_ws = {}
 def bake(gauss, atlas: Atlas, t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4, workspace=None):
     """Bake every texel of `atlas` against the Gaussians (dict of CUDA
     float32 tensors: mean, scale, quat, opacity, rgb): bin + trace.
-    Synchronises once."""
+    Asynchronous; device_status() reports non-finite inputs or truncated
+    rays."""
     n = int(gauss["mean"].shape[0])
     dev = atlas.rgbo.device
     ws = workspace

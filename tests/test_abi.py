@@ -112,3 +112,35 @@ def test_grid_density_checked_on_the_host():
         bp = S.BakeParams(0.0, 1.0 / 255.0, 0.99, 1e-4, dens)
         assert lib.sop_bake_bin(ctypes.byref(g), ctypes.byref(bp), fake, 1 << 30, None) == 1
         assert b"grid_density" in lib.sop_last_error()
+
+
+def test_bake_workspace_minimum_checked_on_the_host():
+    """sop_bake_bin sizes its grid on the device and relies on a workspace of
+    at least sop_bake_workspace_bytes(): a smaller one is refused before any
+    launch (SOP_ERR_WORKSPACE = 3), with the bytes needed in the message."""
+    from paper_2510_07729_gb300 import sop as S
+    lib = S.load()
+    fake = 1 << 20
+    n = 1000
+    need = int(lib.sop_bake_workspace_bytes(n, 1, 2))
+    g = S.Gaussians(fake, fake, fake, fake, fake, n)
+    bp = S.BakeParams(0.0, 1.0 / 255.0, 0.99, 1e-4, 0.0)
+    assert lib.sop_bake_bin(ctypes.byref(g), ctypes.byref(bp), fake, need - 256, None) == 3
+    assert str(need).encode() in lib.sop_last_error()
+    assert lib.sop_bake_bin(ctypes.byref(g), ctypes.byref(bp), fake + 128, need, None) == 3  # misaligned
+
+
+def test_device_status_bits_decoded_on_the_host():
+    """The device status word's bits as the header defines them, and their
+    decoding by the binding (no GPU: the word itself is read on a GPU)."""
+    from paper_2510_07729_gb300 import sop as S
+    hdr = open(os.path.join(ROOT, "include", "sop.h")).read()
+    for name, val in (("NONFINITE", S.DEVSTAT_NONFINITE), ("BAKE_TRUNCATED", S.DEVSTAT_BAKE_TRUNCATED),
+                      ("INDEX", S.DEVSTAT_INDEX), ("GRID_COARSENED", S.DEVSTAT_GRID_COARSENED),
+                      ("ERRORS", S.DEVSTAT_ERRORS)):
+        m = re.search(r"#define SOP_DEVSTAT_%s (0x[0-9a-f]+)u" % name, hdr)
+        assert m and int(m.group(1), 16) == val, name
+    assert S.DEVSTAT_GRID_COARSENED & S.DEVSTAT_ERRORS == 0  # information, not an error
+    assert S.devstat_names(0) == []
+    assert S.devstat_names(S.DEVSTAT_NONFINITE | S.DEVSTAT_GRID_COARSENED) == ["nonfinite", "grid_coarsened"]
+    assert S.devstat_names(0x7) == ["nonfinite", "bake_truncated", "index"]
