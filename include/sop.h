@@ -464,8 +464,11 @@ sop_status sop_atlas_copy(const sop_atlas* src, const int32_t* src_probes, const
  * chunk of 16,384 points' neighbour lists must fit it, which holds for up to
  * SOP_NOALLOC_MAX_PROBES probes at any K <= 32 and S <= 4096 (larger P is
  * rejected with SOP_ERR_INVALID_ARG and a message; use sop_query_shade).
- * The first call on a device looks up the array's address on that device,
- * so make that first call before any CUDA stream capture on the device.
+ * The first call on a device looks up the array's address on that device
+ * and keeps it for the life of the process, so make that first call before
+ * any CUDA stream capture on the device, and do not call this entry point
+ * after a cudaDeviceReset() in the same process (the library's device
+ * memory is reloaded then, and the kept address would be stale).
  * Every call uses the same array and leaves its contents behind; calls that
  * overlap on the GPU (other streams or host threads) race on it and must be
  * serialised by the caller. Asynchronous on `stream`. */

@@ -16,7 +16,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "sop_oracle.c")
-SRCS = (SRC, os.path.join(HERE, "gbuffer_oracle.c"))
+SRCS = (SRC, os.path.join(HERE, "gbuffer_oracle.c"), os.path.join(HERE, "surrogate_oracle.c"))
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 MODE_SHADE, MODE_SHADOW = 0, 1
@@ -48,6 +48,7 @@ def lib():
         _lib = C.CDLL(LIB)
         _lib.orc_num_threads.restype = C.c_int
         _lib.orc_gbuffer_points.restype = C.c_int64
+        _lib.orc_surr_grid_dims.restype = C.c_int64
     return _lib
 
 
@@ -408,3 +409,126 @@ def fps(pts, k, start=0, nrm=None, offset=0.0):
     lib().orc_fps(C.c_int64(len(p)), _p(p), None if nr is None else _p(nr), C.c_int32(k), C.c_int64(start),
                   C.c_double(offset), _p(idx), _p(pos))
     return idx, pos
+
+
+# ----------------------------------------------------------------------------
+# storage formats of the atlas depth plane
+# ----------------------------------------------------------------------------
+def fp8_e4m3_bits(x):
+    """Bits of the FP8 E4M3 value nearest to each float32 x (1 sign bit, 4
+    exponent bits with bias 7, 3 mantissa bits, subnormals below 2^-6, no
+    infinities): ties to the even code, magnitudes beyond the largest
+    finite value 448 saturate to it (NaN -> 0x7f). Written from the format's
+    definition: the representable magnitudes are k 2^(e-3) for k = 8..15 and
+    e = -6..8, and k 2^-9 for k = 0..7."""
+    shape = np.shape(x)
+    x = np.atleast_1d(np.asarray(x, np.float32)).astype(np.float64)
+    s = np.signbit(x).astype(np.uint8) << 7
+    a = np.abs(x)
+    out = np.empty(a.shape, np.uint8)
+    nan = np.isnan(a)
+    # every magnitude at or above the largest finite value saturates to it
+    a = np.minimum(np.where(nan, 0.0, a), 448.0)
+    # the spacing of the representable values around a: 2^(e-3) for a in
+    # [2^e, 2^(e+1)), e >= -6; 2^-9 below 2^-6
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** -6)))
+    step = 2.0 ** (e - 3)
+    q = a / step                      # exact: a power-of-two scaling
+    k = np.floor(q)
+    frac = q - k
+    k = k + ((frac > 0.5) | ((frac == 0.5) & (np.mod(k, 2) == 1)))
+    v = k * step                      # the rounded magnitude
+    v = np.minimum(v, 448.0)
+    # encode v: subnormal codes k for v < 2^-6, else exponent and mantissa
+    sub = v < 2.0 ** -6
+    ev = np.floor(np.log2(np.maximum(v, 2.0 ** -6)))
+    mant = np.where(sub, v / 2.0 ** -9, v / 2.0 ** (ev - 3) - 8)
+    code = np.where(sub, mant, (ev + 7) * 8 + mant)
+    out[:] = code.astype(np.int64).astype(np.uint8)
+    out = out | s
+    out[nan] = 0x7F
+    return out.reshape(shape)
+
+
+# ----------------------------------------------------------------------------
+# learned bake surrogate: texel features (surrogate_oracle.c)
+# ----------------------------------------------------------------------------
+SURR_KN = 256          # near field: at most this many nearest Gaussians
+SURR_G = 128           # far field: cells along the longest axis
+SURR_N_FEAT = 18       # direction (3), near (O, L rgb, D, W), far (6 x O, L rgb)
+
+
+def surr_near_list(probe_pos, mean, r_n, KN=SURR_KN):
+    """The near list of every probe: its at most KN nearest Gaussian centres
+    within r_n (integer keys, ties to the lower index; -1 ends a short
+    list), and t0, where the far field starts: the last listed Gaussian's
+    distance when the list is full, else r_n."""
+    idx, key = knn(probe_pos, mean, KN, radius=r_n)
+    full = idx[:, KN - 1] >= 0
+    t0 = np.where(full, np.sqrt(key[:, KN - 1].astype(np.float64)) / 1048576.0, float(r_n))
+    return idx.astype(np.int32), t0
+
+
+def surr_grid(gauss, alpha_min=1.0 / 255.0, alpha_max=0.99, G=SURR_G):
+    """The far-field grid: (qlo [3], hq, dims [3], mass_q [cells], col_q
+    [cells, 3]) with fixed-point sums in units of 2^-40."""
+    mean, scale, op, rgb = (_f32(gauss[k]) for k in ("mean", "scale", "opacity", "rgb"))
+    N = len(op)
+    qlo = np.zeros(3, np.int64)
+    hq = C.c_int64(0)
+    dims = np.zeros(3, np.int32)
+    cells = lib().orc_surr_grid_dims(C.c_int64(N), _p(mean), _p(op), C.c_double(alpha_min), C.c_int32(G), _p(qlo),
+                                     C.byref(hq), _p(dims))
+    n = max(int(cells), 1)
+    mass = np.zeros(n, np.int64)
+    col = np.zeros((n, 3), np.int64)
+    if cells > 0:
+        lib().orc_surr_grid_fill(C.c_int64(N), _p(mean), _p(scale), _p(op), _p(rgb), C.c_double(alpha_min),
+                                 C.c_double(alpha_max), _p(qlo), C.c_int64(hq.value), _p(dims), _p(mass), _p(col))
+    return qlo, int(hq.value), dims, mass, col
+
+
+def surr_features(gauss, probe_pos, R, r_n, alpha_min=1.0 / 255.0, alpha_max=0.99, KN=SURR_KN, G=SURR_G,
+                  near_list=None):
+    """FP64 texel features [P, R*R, 18] of every probe: the texel direction,
+    the near field (O_n, L_n rgb, D_n, W_n) and the far field (1 - exp(-tau)
+    at the 5 checkpoints and at the end, L_f rgb). Returns (feats, flags
+    [P, R*R], near list [P, KN], t0 [P])."""
+    pp = _f32(probe_pos)
+    P = len(pp)
+    if near_list is None:
+        lst, t0 = surr_near_list(pp, gauss["mean"], r_n, KN)
+    else:
+        lst, t0 = near_list
+    mean, scale, quat, op, rgb = (_f32(gauss[k]) for k in ("mean", "scale", "quat", "opacity", "rgb"))
+    near = np.empty((P, R * R, 6))
+    flags = np.zeros((P, R * R), np.int32)
+    lst = np.ascontiguousarray(lst, np.int32)
+    lib().orc_surr_near(C.c_int32(P), _p(pp), C.c_int32(R), _p(mean), _p(scale), _p(quat), _p(op), _p(rgb),
+                        _p(lst), C.c_int32(lst.shape[1]), C.c_double(alpha_min), C.c_double(alpha_max), _p(near),
+                        _p(flags))
+    far = surr_far(pp, t0, R, *surr_grid(gauss, alpha_min, alpha_max, G))
+    dirs = np.array([_texel_dir(R, t % R, t // R) for t in range(R * R)])
+    feats = np.concatenate([np.broadcast_to(dirs, (P, R * R, 3)), near, far], axis=-1)
+    return feats, flags, lst, t0
+
+
+def surr_far(probe_pos, t0, R, qlo, hq, dims, mass, col):
+    """The far-field features [P, R*R, 9] of every texel of the probes, from
+    t0 [P] on, through a grid (qlo, hq, dims, fixed-point mass, col)."""
+    pp = _f32(probe_pos)
+    far = np.empty((len(pp), R * R, 9))
+    t0 = np.ascontiguousarray(t0, np.float64)
+    qlo = np.ascontiguousarray(qlo, np.int64)
+    dims = np.ascontiguousarray(dims, np.int32)
+    mass = np.ascontiguousarray(mass, np.int64)
+    col = np.ascontiguousarray(col, np.int64)
+    lib().orc_surr_far(C.c_int32(len(pp)), _p(pp), _p(t0), C.c_int32(R), _p(qlo), C.c_int64(int(hq)), _p(dims),
+                       _p(mass), _p(col), _p(far))
+    return far
+
+
+def _texel_dir(R, i, j):
+    d = np.empty(3)
+    lib().orc_texel_dir(C.c_int(R), C.c_int(i), C.c_int(j), _p(d))
+    return d

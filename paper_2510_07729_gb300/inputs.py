@@ -533,8 +533,8 @@ def smooth_maps(rng, P, R):
 # --------------------------------------------------------------------------
 # learned bake surrogate: initial parameters and training / evaluation scenes
 # --------------------------------------------------------------------------
-SURR_BLOCKS = [("W1p", (64, 416)), ("W1d", (64, 3)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
-               ("W3", (64, 64)), ("b3", (64,)), ("W4", (5, 64)), ("b4", (5,))]
+SURR_BLOCKS = [("W1", (64, 18)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (64, 64)), ("b3", (64,)),
+               ("W4", (5, 64)), ("b4", (5,))]
 
 
 def surrogate_init(seed):
@@ -546,8 +546,7 @@ def surrogate_init(seed):
         if name.startswith("b"):
             out.append(np.zeros(shp))
         else:
-            fan_in = 419 if name in ("W1p", "W1d") else shp[1]
-            b = np.sqrt(6.0 / fan_in)
+            b = np.sqrt(6.0 / shp[1])
             out.append(rng.uniform(-b, b, shp))
     return np.concatenate([o.reshape(-1) for o in out]).astype(F32)
 

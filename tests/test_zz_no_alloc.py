@@ -6,8 +6,9 @@ allocator). For them the library offers a variant of sop_query_shade that
 takes no workspace and uses a fixed scratch array compiled into the library.
 These checks call it through the C ABI and compare it with the regular
 entry point, twice in a row (the scratch array keeps the previous call's
-contents, which must not leak into the next result). The file is named so
-that pytest collects it last.
+contents, which must not leak into the next result), and with the FP64
+oracle directly, including a caller-given direction set and a search
+radius. The file is named so that pytest collects it last.
 """
 import ctypes as C
 
@@ -25,12 +26,13 @@ def cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def call_noalloc(lib, sop, pts, at, env, K, S, mode, out, idx, w):
-    sp = sop.ShadeParams(K, S, mode, 0.5, 1e-6)
+def call_noalloc(lib, sop, pts, at, env, K, S, mode, out, idx, w, dirs=None, radius=0.0):
+    sp = sop.ShadeParams(K, S, mode, 0.5, 1e-6, 0, 0, radius)
     d = at.c()
     M = pts[0].shape[0]
     st = lib.sop_query_shade_noalloc(*[C.c_void_p(t.data_ptr()) for t in pts], M, C.byref(d),
-                                     C.c_void_p(env.data_ptr()), env.shape[0], env.shape[1], None, C.byref(sp),
+                                     C.c_void_p(env.data_ptr()), env.shape[0], env.shape[1],
+                                     None if dirs is None else C.c_void_p(dirs.data_ptr()), C.byref(sp),
                                      C.c_void_p(out.data_ptr()), C.c_void_p(idx.data_ptr()),
                                      C.c_void_p(w.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 0, lib.sop_last_error().decode()
@@ -86,3 +88,47 @@ def test_noalloc_rejects_too_many_probes():
                                      None, C.byref(sp), C.c_void_p(z.data_ptr()), None, None, None)
     assert st == 1
     assert "scratch" in lib.sop_last_error().decode()
+
+
+def _hemisphere_dirs(rng, S):
+    v = rng.standard_normal((S, 3))
+    v[:, 2] = np.abs(v[:, 2]) + 0.05
+    return (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("case", ["plain", "dirs_radius"])
+def test_noalloc_matches_oracle(orc, mode, case):
+    """Against the FP64 oracle on the tiny workload (4,096 points, 64 probes,
+    K=4, S=64): probe indices bit-exact, weights and shading within the FP32
+    parity bound; once with the canonical directions and no radius, once
+    with a caller-given local direction set and a fixed search radius (0.3:
+    some points find fewer than K probes, a few none)."""
+    from paper_2510_07729_gb300 import sop
+    lib = sop.load()
+    c = I.make_tiny()
+    K, S = c["K"], c["S"]
+    maps = I.synthetic_maps(np.random.default_rng(50 + mode), 64, 8)
+    at = sop.make_atlas(cuda(c["probe_pos"]), 8)
+    sop.atlas_pack(cuda(maps["rgb"]), cuda(maps["occ"]), cuda(maps["depth"]), at)
+    keys = ("x", "n", "wo", "albedo", "rough", "metal")
+    pts = [cuda(c[k]) for k in keys]
+    dirs, radius = None, 0.0
+    if case == "dirs_radius":
+        dirs, radius = _hemisphere_dirs(np.random.default_rng(60), S), 0.3
+    M = len(c["x"])
+    ro, ri, rw = orc.query_shade(*[c[k] for k in keys], c["probe_pos"], maps["rgb"], maps["occ"], c["env"], K, S,
+                                 mode=mode, dirs=None if dirs is None else dirs.astype(np.float64), radius=radius)
+    if case == "dirs_radius":
+        found = (ri >= 0).sum(1)
+        assert (found < K).mean() > 0.2 and (found == 0).any()
+    for _ in range(2):
+        out = torch.full((M, 3), float("nan"), device="cuda")
+        idx = torch.full((M, K), -7, dtype=torch.int32, device="cuda")
+        w = torch.full((M, K), float("nan"), device="cuda")
+        call_noalloc(lib, sop, pts, at, cuda(c["env"]), K, S, mode, out, idx, w,
+                     dirs=None if dirs is None else cuda(dirs), radius=radius)
+        torch.cuda.synchronize()
+        assert np.array_equal(idx.cpu().numpy(), ri)
+        assert_close(w.cpu().numpy(), rw, what="noalloc weights vs oracle")
+        assert_close(out.cpu().numpy(), ro, what="noalloc vs oracle")
