@@ -1,13 +1,17 @@
 """Benchmark of the SOP hot path on GB300: probe bake + probe query/shade.
 
-One step = one pass of the whole path over the 'object' workload
-(200,000 anisotropic Gaussians on 5 ellipsoids, 4,096 probes at 16x16,
-418,111 shading points from an 800x800 view, K=8, S=128, 256x512 HDR
-environment): sop_bake of all 4,096 probes (1,048,576 texel rays,
-Gaussian binning, grid walk, compositing, atlas packing) followed by
-sop_query_shade of all points against the freshly baked atlas (nearest
-probes, weights, S directions, BRDF). `value` is shaded point-directions
-per second of that step; the bake's texels/s is reported beside it.
+One step = one pass of the whole path over the 1920x1080 composition
+workload (an object of 200,000 anisotropic Gaussians on a 1M-Gaussian
+ground-and-clutter scene): sop_bake of all 8,192 probes (4,096 on the
+object and 4,096 shadow-region probes on the ground, 16x16 each, 2,097,152
+texel rays traced through the object's Gaussians: binning, grid walk,
+compositing, atlas border) followed by the frame's two sop_query_shade
+calls: the 21,907 object pixels in SHADE mode against the object probes and
+the 2,051,693 scene pixels in SHADOW mode against the shadow-region probes
+(K=8, S=64, 256x512 HDR environment). `value` is shaded point-directions per
+second of that step; the bake's texels/s is reported beside it. The
+object-reconstruction workload (4,096 probes, 418,111 points, K=8, S=128) is
+timed the same way as a secondary line (`object_step`).
 
 Usage (driver contract):
   python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
@@ -41,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="object", choices=["object", "compose", "tiny"])
+    ap.add_argument("--workload", default="compose", choices=["compose", "object", "tiny"])
     ap.add_argument("--part", default="step", choices=["step", "bake", "query", "compose", "optimize", "deferred"],
                     help="profiling aid: run only one half (the JSON line then covers that half), or only the "
                          "1080p composition-frame query")
@@ -105,22 +109,40 @@ class ClockSampler:
 # workload
 # ----------------------------------------------------------------------------
 def load_workload(name):
+    """A workload: Gaussians, all probes (one atlas, baked in one call) and
+    its query parts, each a point set with its mode and its slice of the
+    atlas's probes."""
     from paper_2510_07729_gb300 import inputs as I
-    if name == "object":
-        c = I.make_object()
-        return dict(name="object", gauss=c["gauss"], probe_pos=c["probe_pos"], probe_nrm=c["probe_nrm"], R=c["R"],
-                    pts={k: c[k] for k in ("x", "n", "wo", "albedo", "rough", "metal")}, env=c["env"], K=c["K"],
-                    S=c["S"], mode=0)
-    if name == "tiny":
-        c = I.make_tiny()
-        return dict(name="tiny", gauss=c["gauss"], probe_pos=c["probe_pos"], probe_nrm=c["probe_nrm"], R=c["R"],
-                    pts={k: c[k] for k in ("x", "n", "wo", "albedo", "rough", "metal")}, env=c["env"], K=c["K"],
-                    S=c["S"], mode=0)
+    keys = ("x", "n", "wo", "albedo", "rough", "metal")
+    if name in ("object", "tiny"):
+        c = I.make_object() if name == "object" else I.make_tiny()
+        P = len(c["probe_pos"])
+        return dict(name=name, gauss=c["gauss"], probe_pos=c["probe_pos"], R=c["R"], env=c["env"], K=c["K"],
+                    S=c["S"], depth_scale=float(c.get("object_size", 2.0)),
+                    parts=[dict(name="shade", mode=0, probes=(0, P), pts={k: c[k] for k in keys})],
+                    label=f"{name}: {len(c['gauss']['mean'])} Gaussians, {P} probes {c['R']}x{c['R']}, "
+                          f"{len(c['x'])} points SHADE, K={c['K']}, S={c['S']}, env {c['env'].shape[0]}x"
+                          f"{c['env'].shape[1]}")
     c = I.make_compose()
-    d = c["shadow"]
-    return dict(name="compose-shadow", gauss=c["gauss_object"], probe_pos=d["probe_pos"], probe_nrm=d["probe_nrm"],
-                R=c["R"], pts={k: d[k] for k in ("x", "n", "wo", "albedo", "rough", "metal")}, env=c["env"],
-                K=c["K"], S=c["S"], mode=1)
+    po, ps = c["shade"]["probe_pos"], c["shadow"]["probe_pos"]
+    Po, Ps = len(po), len(ps)
+    n_scene = len(c["gauss_scene"]["mean"])
+    n_obj = len(c["gauss_object"]["mean"])
+    return dict(name="compose", gauss=c["gauss_object"], probe_pos=np.concatenate([po, ps]), R=c["R"], env=c["env"],
+                K=c["K"], S=c["S"], depth_scale=float(c["object_size"]),
+                parts=[dict(name="shade", mode=0, probes=(0, Po), pts={k: c["shade"][k] for k in keys}),
+                       dict(name="shadow", mode=1, probes=(Po, Po + Ps), pts={k: c["shadow"][k] for k in keys})],
+                label=f"compose 1920x1080: object {n_obj} Gaussians in a {n_scene}-Gaussian scene; {Po} object + "
+                      f"{Ps} shadow-region probes {c['R']}x{c['R']} baked against the object; "
+                      f"{len(c['shade']['x'])} object pixels SHADE + {len(c['shadow']['x'])} scene pixels SHADOW, "
+                      f"K={c['K']}, S={c['S']}, env {c['env'].shape[0]}x{c['env'].shape[1]}")
+
+
+def atlas_view(sop, atlas, lo, hi):
+    """The probes [lo, hi) of an atlas as an atlas of their own (views of the
+    same memory: probe-major storage makes each slice contiguous)."""
+    return sop.Atlas(atlas.rgbo[lo:hi], None if atlas.depth is None else atlas.depth[lo:hi],
+                     atlas.probe_pos[lo:hi], None, atlas.rgbo_dtype, atlas.depth_dtype, atlas.depth_scale)
 
 
 # algorithmic FP32 work of one shaded point-direction (K probes, SHADE mode):
@@ -483,123 +505,174 @@ def deferred_frame_variant(sop, dev, flush, steps):
                           "views_and_fps_ms": round(float(np.mean(tpl)), 3)}}
 
 
-def compose_frame_variant(sop, dev, flush, steps, l2_gbs, hbm_gbs, peak_fp32):
-    """The 1920x1080 composition frame (1.2M-Gaussian scene; 200k-Gaussian
-    object): object pixels SHADE against the 4,096 object probes, scene
-    pixels SHADOW against the 4,096 shadow-region probes (K=8, S=64), both
-    atlases baked from the object's Gaussians. Timed as the two
-    sop_query_shade calls of one frame, for a float32 and a float16 atlas,
-    with the HBM, L2 and FP32 roofs of that frame."""
+def _rel_errors(gpu, ref):
+    gpu, ref = np.asarray(gpu, np.float64), np.asarray(ref, np.float64)
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).mean())
+    return {"rel_l1": float(np.abs(gpu - ref).sum() / np.abs(ref).sum()),
+            "max_rel": float((np.abs(gpu - ref) / scale).max())}
+
+
+def compose_frame_variant(sop, dev, flush, steps, l2_gbs, hbm_gbs, peak_fp32, baked=None, n_shadow=4096,
+                          n_shade=1024):
+    """The 1920x1080 composition frame: the two sop_query_shade calls (object
+    pixels SHADE against the 4,096 object probes, scene pixels SHADOW
+    against the 4,096 shadow-region probes, K=8, S=64), timed for float32,
+    bfloat16 and float16 atlases (each baked once, untimed), with the HBM,
+    L2 and FP32 roofs of the frame. Every precision's output is compared
+    with the FP64 oracle on a seeded sample of points (4,096 scene pixels,
+    1,024 object pixels), the oracle shading with the float32 bake's maps;
+    the depth plane's storage types (float32, float16, bfloat16, FP8 E4M3)
+    are compared with the oracle's own bake of 16 sampled probes."""
     import torch
-    from paper_2510_07729_gb300 import inputs as I
-    c = I.make_compose()
-    K, S, R = c["K"], c["S"], c["R"]
 
-    def cu(a):
-        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-
-    g = {k: cu(v) for k, v in c["gauss_object"].items()}
-    env = cu(c["env"])
-    parts = []
-    for name, mode in (("shade", 0), ("shadow", 1)):
-        d = c[name]
-        pts = [cu(d[k]) for k in ("x", "n", "wo", "albedo", "rough", "metal")]
-        parts.append(dict(name=name, mode=mode, pts=pts, pp=cu(d["probe_pos"]), M=len(d["x"]),
-                          normals=len(np.unique(d["n"], axis=0))))
+    import oracle
+    W = load_workload("compose")
+    K, S, R = W["K"], W["S"], W["R"]
+    if baked is None:
+        baked = StepState(sop, W, dev)
+        baked.bake()
+    states = {"fp32": baked}
+    for dt, label in ((sop.SOP_BF16, "bf16"), (sop.SOP_F16, "fp16")):
+        s = StepState(sop, W, dev, rgbo_dtype=dt, depth_dtype=dt)
+        s.bake()
+        states[label] = s
+    parts = baked.parts
+    normals = {q["name"]: len(np.unique(p["pts"]["n"], axis=0)) for q, p in zip(parts, W["parts"])}
     res = {"what": "1920x1080 composition frame: sop_query_shade of the object pixels (SHADE) and of the scene "
                    "pixels (SHADOW), K=8, S=64, 2x4,096 probes at 16x16",
-           "points": {p["name"]: p["M"] for p in parts},
-           "distinct_normals": {p["name"]: p["normals"] for p in parts}}
-    outs = {}
-    for dt, label, tb in ((sop.SOP_F32, "fp32", 16), (sop.SOP_F16, "fp16", 8)):
-        for p in parts:
-            p["at"] = sop.make_atlas(p["pp"], R, rgbo_dtype=dt, depth_dtype=dt)
-            sop.bake(g, p["at"])
-            p["out"] = torch.empty((p["M"], 3), dtype=torch.float32, device=dev)
-            p["ws"] = torch.empty(sop.query_workspace_bytes(p["at"], p["M"], K, S, env.shape[0], env.shape[1],
-                                                            p["mode"]), dtype=torch.uint8, device=dev)
-
-        def call(p):
-            sop.query_shade(*p["pts"], p["at"], env, K, S, mode=p["mode"], out=p["out"], workspace=p["ws"])
-
+           "points": {q["name"]: q["M"] for q in parts}, "distinct_normals": normals}
+    tex_bytes = {"fp32": 16, "bf16": 8, "fp16": 8}
+    for label, st in states.items():
         for _ in range(3):
-            for p in parts:
-                call(p)
+            for q in st.parts:
+                st.query(q)
         torch.cuda.synchronize()
-        ts, tp = [], {p["name"]: [] for p in parts}
+        ts, tp = [], {q["name"]: [] for q in st.parts}
         for _ in range(steps):
             flush.fill_(1)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(st.parts) + 1)]
             ev[0].record()
-            call(parts[0])
-            ev[1].record()
-            call(parts[1])
-            ev[2].record()
+            for i, q in enumerate(st.parts):
+                st.query(q)
+                ev[i + 1].record()
             torch.cuda.synchronize()
-            ts.append(ev[0].elapsed_time(ev[2]))
-            tp["shade"].append(ev[0].elapsed_time(ev[1]))
-            tp["shadow"].append(ev[1].elapsed_time(ev[2]))
+            ts.append(ev[0].elapsed_time(ev[-1]))
+            for i, q in enumerate(st.parts):
+                tp[q["name"]].append(ev[i].elapsed_time(ev[i + 1]))
         ms = float(np.mean(ts))
-        pd = sum(p["M"] for p in parts) * S
-        fl = sum((flop_per_point_dir(K, p["mode"]) - FLOP_DIR_GEOMETRY) * p["M"] * S +
-                 FLOP_DIR_GEOMETRY * p["normals"] * S for p in parts)
-        dem = sum(query_demand(K, p["mode"], tb, p["M"], S, p["normals"]) for p in parts)
-        hbm = sum(68 * p["M"] for p in parts) + sum(p["at"].rgbo.numel() * p["at"].rgbo.element_size()
-                                                     for p in parts) + env.numel() * 4
+        pd = st.M * S
+        fl = sum((flop_per_point_dir(K, q["mode"]) - FLOP_DIR_GEOMETRY) * q["M"] * S +
+                 FLOP_DIR_GEOMETRY * normals[q["name"]] * S for q in st.parts)
+        dem = sum(query_demand(K, q["mode"], tex_bytes[label], q["M"], S, normals[q["name"]]) for q in st.parts)
+        hbm = 68 * st.M + st.atlas.rgbo.numel() * st.atlas.rgbo.element_size() + st.env.numel() * 4
         t_hbm, t_l2, t_alu = hbm / (hbm_gbs * 1e9), dem / (l2_gbs * 1e9), fl / (peak_fp32 * 1e12)
         bound = max((t_hbm, "hbm"), (t_l2, "l2"), (t_alu, "alu"))
-        outs[label] = [p["out"].clone() for p in parts]
-        res[label] = {"frame_ms": round(ms, 4), "shade_ms": round(float(np.mean(tp["shade"])), 4),
-                      "shadow_ms": round(float(np.mean(tp["shadow"])), 4),
+        res[label] = {"frame_ms": round(ms, 4),
+                      **{f"{q['name']}_ms": round(float(np.mean(tp[q["name"]])), 4) for q in st.parts},
                       "point_dirs_per_s": round(pd / (ms * 1e-3), 1),
-                      "roofline": {"bound": bound[1], "t_hbm_ms": round(t_hbm * 1e3, 4),
+                      "roofline": {"kernel": "shade_kernel (the frame's two sop_query_shade calls)",
+                                   "bound": bound[1], "t_hbm_ms": round(t_hbm * 1e3, 4),
                                    "t_l2_ms": round(t_l2 * 1e3, 4), "t_alu_ms": round(t_alu * 1e3, 4),
-                                   "frac": round(bound[0] * 1e3 / ms, 4),
-                                   "l2_demand_bytes": int(dem), "hbm_bytes": int(hbm), "flop": int(fl)}}
+                                   "frac": round(bound[0] * 1e3 / ms, 4), "l2_demand_bytes": int(dem),
+                                   "hbm_bytes": int(hbm), "flop": int(fl)}}
+    # errors against the FP64 oracle on sampled points (the oracle shades
+    # with the float32 bake's maps; the 16-bit atlases round those maps)
+    rng = np.random.default_rng(2024)
+    prec = {}
+    for iq, (q, part) in enumerate(zip(parts, W["parts"])):
+        n = min(n_shadow if q["mode"] == 1 else n_shade, q["M"])
+        sel = np.sort(rng.choice(q["M"], n, replace=False))
+        lo, hi = part["probes"]
+        rgb, occ, _ = q["at"].interior()
+        ref, _, _ = oracle.query_shade(*[part["pts"][k][sel] for k in ("x", "n", "wo", "albedo", "rough", "metal")],
+                                       W["probe_pos"][lo:hi], rgb.cpu().numpy(), occ.cpu().numpy(), W["env"], K, S,
+                                       mode=q["mode"])
+        selt = torch.from_numpy(sel).to(dev)
+        for label, st in states.items():
+            out = st.parts[iq]["out"][selt].cpu().numpy()
+            prec.setdefault(label, {})[q["name"]] = _rel_errors(out, ref)
+    for label in states:
+        prec[label]["atlas"] = {"fp32": "float32 RGBO (16 B/texel)", "bf16": "bfloat16 RGBO (8 B/texel)",
+                                "fp16": "float16 RGBO (8 B/texel)"}[label]
+        prec[label]["frame_ms"] = res[label]["frame_ms"]
+    prec["sample"] = (f"{n_shadow} scene pixels (SHADOW) and {n_shade} object pixels (SHADE), seeded; the oracle "
+                      f"shades with the float32 bake's maps, so the 16-bit rows include the storage rounding")
+    prec["depth"] = depth_precision(sop, W, dev)
+    res["precision"] = prec
+    res["chosen"] = {"atlas": "fp16 RGBO, fp32 accumulation", "frame_ms": res["fp16"]["frame_ms"],
+                     "point_dirs_per_s": res["fp16"]["point_dirs_per_s"],
+                     "speedup_vs_fp32_frame": round(res["fp32"]["frame_ms"] / res["fp16"]["frame_ms"], 4),
+                     "error_vs_oracle": {k: v for k, v in prec["fp16"].items() if k in ("shade", "shadow")}}
     # the paper's rendering configuration: the environment as a 512x512
     # octahedral texture (Sec. 4.1) and S importance-sampled world directions
     # (Sec. 4.2, Eq. PDF) shared by all points, float32 atlas
-    env_oct = sop.env_to_octahedral(env, 512)
+    env_oct = sop.env_to_octahedral(baked.env, 512)
     dirs = sop.env_importance_dirs(env_oct, S)
-    for p in parts:
-        p["at"] = sop.make_atlas(p["pp"], R)
-        sop.bake(g, p["at"])
-        p["ws"] = torch.empty(sop.query_workspace_bytes(p["at"], p["M"], K, S, 512, 512, p["mode"]),
-                              dtype=torch.uint8, device=dev)
+    ref_mean = parts[1]["out"].mean().item()
+    wsi = [torch.empty(sop.query_workspace_bytes(q["at"], q["M"], K, S, 512, 512, q["mode"]), dtype=torch.uint8,
+                       device=dev) for q in parts]
+    outs = [torch.empty_like(q["out"]) for q in parts]
 
-    def call_is(p):
-        sop.query_shade(*p["pts"], p["at"], env_oct, K, S, mode=p["mode"], out=p["out"], workspace=p["ws"],
-                        env_layout=sop.ENV_OCTAHEDRAL, dirs_world=dirs)
+    def call_is():
+        for q, w, o in zip(parts, wsi, outs):
+            sop.query_shade(*q["pts"], q["at"], env_oct, K, S, mode=q["mode"], out=o, workspace=w,
+                            env_layout=sop.ENV_OCTAHEDRAL, dirs_world=dirs)
 
     for _ in range(3):
-        for p in parts:
-            call_is(p)
+        call_is()
     torch.cuda.synchronize()
     ts = []
     for _ in range(steps):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for p in parts:
-            call_is(p)
+        call_is()
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = float(np.mean(ts))
-    pd = sum(p["M"] for p in parts) * S
     res["fp32_octahedral_importance"] = {
         "env": "octahedral 512x512 resampled from the equirectangular map; S importance-sampled world directions",
-        "frame_ms": round(ms, 4), "point_dirs_per_s": round(pd / (ms * 1e-3), 1),
-        "shadow_mean_vs_hammersley": round(float(parts[1]["out"].mean().item()) /
-                                           float(outs["fp32"][1].mean().item()), 4)}
-    num = sum((a - b).abs().sum().item() for a, b in zip(outs["fp16"], outs["fp32"]))
-    den = sum(b.abs().sum().item() for b in outs["fp32"])
-    res["fp16_rel_l1_vs_fp32_atlas"] = num / den
+        "frame_ms": round(ms, 4), "point_dirs_per_s": round(baked.M * S / (ms * 1e-3), 1),
+        "shadow_mean_vs_hammersley": round(float(outs[1].mean().item()) / ref_mean, 4)}
     res["peaks"] = {"l2_read_gbs": round(l2_gbs, 1), "l2_note": "measured in this run (sop_read_bandwidth_probe: "
                     "a 64 MB L2-resident buffer read 40 times, 16-byte loads on every SM)", "hbm_gbs": hbm_gbs,
                     "hbm_note": "MEASURED_PEAKS.json copy bandwidth", "fp32_tflops": round(peak_fp32, 1),
                     "fp32_note": "derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"}
     return res
+
+
+def depth_precision(sop, W, dev, n_probes=16):
+    """The depth plane in each storage type (D / depth_scale, depth_scale =
+    the object's bounding-box diagonal) against the FP64 oracle's bake of
+    the same sampled probes (half object, half shadow-region), over the
+    texels that hit something; texels the oracle flags as order- or
+    threshold-ambiguous are left out."""
+    import torch
+
+    import oracle
+    rng = np.random.default_rng(77)
+    P = len(W["probe_pos"])
+    sel = np.sort(np.concatenate([rng.choice(P // 2, n_probes // 2, replace=False),
+                                  P // 2 + rng.choice(P - P // 2, n_probes - n_probes // 2, replace=False)]))
+    pp = W["probe_pos"][sel]
+    _, o_occ, o_dep, fl = oracle.bake(W["gauss"], pp, W["R"])
+    ok = (fl == 0) & (o_occ > 0)
+    g = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in W["gauss"].items()}
+    ds = W["depth_scale"]
+    out = {"probes": int(n_probes), "texels_compared": int(ok.sum()), "depth_scale": round(ds, 4),
+           "note": "the query reads O and L_in only; the depth plane is the unbiased depth D/W of the bake"}
+    for dt, label in ((sop.SOP_F32, "fp32"), (sop.SOP_F16, "fp16"), (sop.SOP_BF16, "bf16"),
+                      (sop.SOP_FP8E4M3, "fp8_e4m3")):
+        at = sop.make_atlas(torch.from_numpy(np.ascontiguousarray(pp)).to(dev), W["R"], depth_dtype=dt,
+                            depth_scale=ds)
+        sop.bake(g, at)
+        _, _, dep = at.interior()
+        d = dep.cpu().numpy().astype(np.float64)
+        err = np.abs(d[ok] - o_dep[ok])
+        out[label] = {"mean_abs_over_scale": float(err.mean() / ds), "max_abs_over_scale": float(err.max() / ds),
+                      "mean_rel": float((err / np.maximum(o_dep[ok], 1e-6)).mean())}
+    return out
 
 
 # the part of flop_per_point_dir that depends only on the normal and the
@@ -633,6 +706,147 @@ def whole_job_value(units_per_rank, ms_step, world):
     return world * units_per_rank / (ms_step * 1e-3)
 
 
+class StepState:
+    """Device state of one workload's step: Gaussians, the atlas of all its
+    probes, and each query part's points, atlas view, output and workspace."""
+
+    def __init__(self, sop, W, dev, n_probes=0, rgbo_dtype=0, depth_dtype=0):
+        import torch
+
+        def cu(a):
+            return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+        self.sop, self.W, self.dev = sop, W, dev
+        self.g = {k: cu(v) for k, v in W["gauss"].items()}
+        P_all = len(W["probe_pos"])
+        self.P = P_all if n_probes <= 0 else min(n_probes, P_all)
+        self.full = self.P == P_all
+        self.ppos = cu(W["probe_pos"][:self.P])
+        self.R, self.K, self.S = W["R"], W["K"], W["S"]
+        self.env = cu(W["env"])
+        self.atlas = sop.make_atlas(self.ppos, self.R, rgbo_dtype=rgbo_dtype, depth_dtype=depth_dtype,
+                                    depth_scale=W["depth_scale"])
+        self.bws = sop.BakeWorkspace(len(W["gauss"]["mean"]), dev)
+        self.parts = []
+        for part in W["parts"]:
+            q = dict(name=part["name"], mode=part["mode"], M=len(part["pts"]["x"]))
+            q["pts"] = [cu(part["pts"][k]) for k in ("x", "n", "wo", "albedo", "rough", "metal")]
+            if self.full:
+                q["at"] = atlas_view(sop, self.atlas, *part["probes"])
+                q["out"] = torch.empty((q["M"], 3), dtype=torch.float32, device=dev)
+                q["ws"] = torch.empty(sop.query_workspace_bytes(q["at"], q["M"], self.K, self.S, self.env.shape[0],
+                                                                self.env.shape[1], q["mode"]),
+                                      dtype=torch.uint8, device=dev)
+            self.parts.append(q)
+        self.M = sum(q["M"] for q in self.parts)
+
+    def bake(self):
+        self.sop.bake_bin(self.g, self.bws)
+        self.sop.bake_trace(self.g, self.atlas, self.bws)
+
+    def query(self, q, **kw):
+        self.sop.query_shade(*q["pts"], q["at"], self.env, self.K, self.S, mode=q["mode"], out=q["out"],
+                             workspace=q["ws"], **kw)
+
+    def step(self, evs, do_bake=True, do_query=True):
+        import torch
+        st = torch.cuda.current_stream()
+        if do_bake:
+            evs[0].record(st)
+            self.sop.bake_bin(self.g, self.bws)
+            evs[4].record(st)
+            self.sop.bake_trace(self.g, self.atlas, self.bws)
+            evs[1].record(st)
+        if do_query:
+            evs[2].record(st)
+            for q in self.parts:
+                self.query(q)
+            evs[3].record(st)
+
+
+def time_steps(state, flush, steps, warmup, do_bake, do_query, world=1, clock_index=None):
+    """Times `steps` whole steps with CUDA events on the current stream (L2
+    flushed before each, outside the events), after `warmup` untimed ones,
+    with a barrier and a synchronisation on both sides; nvidia-smi clocks
+    are sampled during the timed region when clock_index is given."""
+    import contextlib
+
+    import torch
+    import torch.distributed as dist
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for _ in range(warmup):
+        flush.fill_(1)
+        state.step([ev() for _ in range(5)], do_bake, do_query)
+    torch.cuda.synchronize()
+    records = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(clock_index) if clock_index is not None else contextlib.nullcontext()
+    t_wall0 = time.perf_counter()
+    with clk:
+        for _ in range(steps):
+            flush.fill_(1)
+            evs = [ev() for _ in range(5)]
+            state.step(evs, do_bake, do_query)
+            records.append(evs)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    r = {"bake": [e[0].elapsed_time(e[1]) for e in records] if do_bake else [0.0],
+         "trace": [e[4].elapsed_time(e[1]) for e in records] if do_bake else [0.0],
+         "query": [e[2].elapsed_time(e[3]) for e in records] if do_query else [0.0], "wall_s": t_wall}
+    r["ms_step"] = float(np.sum(r["bake"]) + np.sum(r["query"])) / steps
+    r["clocks"] = clk.summary() if clock_index is not None else None
+    return r
+
+
+def trace_roofline(sop, state, ms_trace, peak_fp32):
+    """The bake's trace kernel against the FP32 ALU roof: its own work
+    counters (box tests, exact evaluations, composited hits of the last
+    trace on the workspace) x their FP32 operations / the CUDA-event time."""
+    n_eval, n_comp, status, n_test = sop.bake_stats(state.bws)
+    fl = n_test * FLOP_PER_TEST + n_eval * FLOP_PER_EVAL + n_comp * FLOP_PER_COMPOSITE
+    ach = fl / (ms_trace * 1e-3) / 1e12
+    rays = state.P * state.R * state.R
+    return {"kernel": "trace_kernel (sop_bake_trace)", "bound": "alu", "achieved": round(ach, 3),
+            "peak": round(peak_fp32, 1), "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
+            "traffic": traffic_for("trace_kernel", state.P),
+            "work": {"rays": rays, "box_tests": n_test, "exact_evaluations": n_eval, "composited_hits": n_comp,
+                     "per_ray": {"box_tests": round(n_test / rays, 2), "exact_evaluations": round(n_eval / rays, 2),
+                                 "composited_hits": round(n_comp / rays, 2)},
+                     "status_bits": status, "flop_per_box_test": FLOP_PER_TEST,
+                     "flop_per_evaluation": FLOP_PER_EVAL, "flop_per_composite": FLOP_PER_COMPOSITE},
+            "ms": round(ms_trace, 4),
+            "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived from unit counts and the "
+                         "maximum clock; the measured-peaks file holds no FP32 figure)"}
+
+
+def object_step_variant(sop, dev, flush, steps, peak_fp32):
+    """The object-reconstruction workload's step (bake of 4,096 probes +
+    SHADE query of 418,111 points, K=8, S=128), timed like the headline
+    step, with its trace roofline, the FP16-atlas query and the query
+    variants of the paper (octahedral environment, fixed-radius search)."""
+    W = load_workload("object")
+    st = StepState(sop, W, dev)
+    r = time_steps(st, flush, steps, 3, True, True)
+    q = st.parts[0]
+    mb, mq, mt = (float(np.mean(r[k])) for k in ("bake", "query", "trace"))
+    pd = st.M * st.S
+    res = {"workload": W["label"], "ms_per_step": round(r["ms_step"], 4),
+           "point_dirs_per_s": round(pd / (r["ms_step"] * 1e-3), 1),
+           "bake": {"ms": round(mb, 4), "texels_per_s": round(st.P * st.R * st.R / (mb * 1e-3), 1)},
+           "query": {"ms": round(mq, 4), "point_dirs_per_s": round(pd / (mq * 1e-3), 1)},
+           "roofline": trace_roofline(sop, st, mt, peak_fp32)}
+    pargs = q["pts"]
+    res["chosen"] = chosen_variant(sop, st.g, st.ppos, st.R, pargs, st.env, st.K, st.S, 0, q["out"], flush, steps)
+    res["env_octahedral"] = env_oct_variant(sop, q["at"], pargs, st.env, st.K, st.S, 0, q["out"], flush, steps)
+    res["frnn_query"] = frnn_variant(sop, q["at"], pargs, st.env, st.K, st.S, 0, q["out"], flush, steps, st.ppos)
+    return res, st
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -651,148 +865,60 @@ def main():
 
     from paper_2510_07729_gb300 import sop
     sop.load()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peak_fp32 = N_SMS * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
     if args.part == "compose":
         return compose_only(args, dev, sop)
     if args.part == "deferred":
-        import torch
-        r = deferred_frame_variant(sop, dev, torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev), args.steps)
+        r = deferred_frame_variant(sop, dev, flush, args.steps)
         print(json.dumps({"metric": "composed deferred frames/s", "value": r["fps"], "unit": "frames/s",
                           "steps": args.steps, "higher_is_better": True, "detail": r}))
         return
     if args.part == "optimize":
-        import torch
-        r = optimize_variant(sop, load_workload("object"), dev,
-                             torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev), args.steps)
+        r = optimize_variant(sop, load_workload("object"), dev, flush, args.steps)
         print(json.dumps({"metric": "texture-optimisation step point-dirs/s", "value": r["point_dirs_per_s"],
                           "unit": "point-dirs/s", "steps": args.steps, "higher_is_better": True, "detail": r}))
         return
     W = load_workload(args.workload)
-    P = len(W["probe_pos"]) if args.probes <= 0 else min(args.probes, len(W["probe_pos"]))
-    R, K, S, mode = W["R"], W["K"], W["S"], W["mode"]
-    M = len(W["pts"]["x"])
-
-    def cu(a):
-        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-
-    g = {k: cu(v) for k, v in W["gauss"].items()}
-    ppos = cu(W["probe_pos"][:P])
-    pts = {k: cu(v) for k, v in W["pts"].items()}
-    env = cu(W["env"])
-    atlas = sop.make_atlas(ppos, R)
-    out = torch.empty((M, 3), dtype=torch.float32, device=dev)
-    qws = torch.empty(sop.query_workspace_bytes(atlas, M, K, S, env.shape[0], env.shape[1], mode), dtype=torch.uint8,
-                      device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    pargs = [pts[k] for k in ("x", "n", "wo", "albedo", "rough", "metal")]
+    st = StepState(sop, W, dev, n_probes=args.probes)
     do_bake = args.part in ("step", "bake")
-    do_query = args.part in ("step", "query")
+    do_query = args.part in ("step", "query") and st.full
     if not do_bake:
-        sop.bake(g, atlas)  # query-only runs shade against a baked atlas
-
-    stream = torch.cuda.current_stream()
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-
-    bws = sop.BakeWorkspace(len(W["gauss"]["mean"]), dev)
-
-    def step(evs):
-        if do_bake:
-            evs[0].record(stream)
-            sop.bake_bin(g, bws)
-            evs[4].record(stream)
-            sop.bake_trace(g, atlas, bws)
-            evs[1].record(stream)
-        if do_query:
-            evs[2].record(stream)
-            sop.query_shade(*pargs, atlas, env, K, S, mode=mode, out=out, workspace=qws)
-            evs[3].record(stream)
-
-    for _ in range(args.warmup):
-        flush.fill_(1)
-        step([ev() for _ in range(5)])
-    torch.cuda.synchronize()
-
-    gpu_index = torch.cuda.get_device_properties(dev).index if hasattr(
-        torch.cuda.get_device_properties(dev), "index") else local_rank
+        st.bake()  # query-only runs shade against a baked atlas
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     smi_index = vis.split(",")[local_rank] if vis else str(local_rank)
-    records = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.perf_counter()
-    with ClockSampler(smi_index) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1)  # L2 flush between timed steps (outside the step events)
-            evs = [ev() for _ in range(5)]
-            step(evs)
-            records.append(evs)
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall0
-
-    t_bake = [r[0].elapsed_time(r[1]) for r in records] if do_bake else [0.0]
-    t_trace = [r[4].elapsed_time(r[1]) for r in records] if do_bake else [0.0]
-    t_query = [r[2].elapsed_time(r[3]) for r in records] if do_query else [0.0]
-    ms_step = float(np.sum(t_bake) + np.sum(t_query)) / args.steps
-    ms_step, mb, mq = reduce_max([ms_step, float(np.mean(t_bake)), float(np.mean(t_query))], world, dev)
-
-    texels = P * R * R
-    pd = M * S
+    r = time_steps(st, flush, args.steps, args.warmup, do_bake, do_query, world, smi_index)
+    ms_step, mb, mq = reduce_max([r["ms_step"], float(np.mean(r["bake"])), float(np.mean(r["query"]))], world, dev)
+    texels = st.P * st.R * st.R
+    pd = st.M * st.S
     if args.part == "bake":
         units, unit_name = texels, "texels/s"
     else:
         units, unit_name = pd, "point-dirs/s"
     value = whole_job_value(units, ms_step, world)
 
-    # e2e: public API from pinned host buffers, H2D + bake + query + D2H each step
+    # e2e: public API from pinned host buffers, H2D + bake + queries + D2H each step
     e2e = None
     if not args.no_e2e and args.part == "step":
-        e2e = measure_e2e(args, W, P, dev, sop, flush)
+        e2e = measure_e2e(args, W, dev, sop, flush)
 
-    # rooflines, from the timed region: the bake's trace kernel (the step's
-    # dominant kernel) and the query/shade kernel
-    roof = roof_q = None
-    peak_fp32 = N_SMS * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
-    if do_bake:
-        n_eval, n_comp, status, n_test = sop.bake_stats(bws)
-        fl = n_test * FLOP_PER_TEST + n_eval * FLOP_PER_EVAL + n_comp * FLOP_PER_COMPOSITE
-        mt = float(np.mean(t_trace))
-        ach = fl / (mt * 1e-3) / 1e12
-        roof = {"kernel": "trace_kernel (sop_bake_trace)", "bound": "alu", "achieved": round(ach, 3),
-                "peak": round(peak_fp32, 1), "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
-                "traffic": traffic_for("trace_kernel", P),
-                "work": {"box_tests": n_test, "exact_evaluations": n_eval, "composited_hits": n_comp,
-                         "status_bits": status, "flop_per_box_test": FLOP_PER_TEST,
-                         "flop_per_evaluation": FLOP_PER_EVAL, "flop_per_composite": FLOP_PER_COMPOSITE},
-                "ms": round(mt, 4),
-                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
-    if do_query:
-        fl = flop_per_point_dir(K, mode) * pd
-        ach = fl / (mq * 1e-3) / 1e12
-        roof_q = {"kernel": "shade_kernel (sop_query_shade call)", "bound": "alu", "achieved": round(ach, 3),
-                  "peak": round(peak_fp32, 1), "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
-                  "traffic": traffic_for("shade_kernel", P),
-                  "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, not measured)"}
-        if roof is None:
-            roof = roof_q
-    chosen = surr = comp = optim = envoct = frnn = defer = None
+    roof = trace_roofline(sop, st, float(np.mean(r["trace"])), peak_fp32) if do_bake else None
+    frame = objstep = surr = optim = defer = None
     if do_query and args.part == "step":
-        chosen = chosen_variant(sop, g, ppos, R, pargs, env, K, S, mode, out, flush, args.steps)
-        envoct = env_oct_variant(sop, atlas, pargs, env, K, S, mode, out, flush, args.steps)
-        frnn = frnn_variant(sop, atlas, pargs, env, K, S, mode, out, flush, args.steps, ppos)
-        if not args.no_surrogate and args.workload == "object":
+        if W["name"] == "compose" and not args.no_compose:
+            frame = compose_frame_variant(sop, dev, flush, args.steps, l2_read_peak_gbs(dev), measured_peaks()[0],
+                                          peak_fp32, baked=st)
+        if W["name"] == "compose":
+            objstep, _ = object_step_variant(sop, dev, flush, max(5, args.steps // 2), peak_fp32)
+        if not args.no_surrogate:
             surr = surrogate_variant(sop, dev, flush, args.steps)
-        if not args.no_optimize and args.workload == "object":
-            optim = optimize_variant(sop, W, dev, flush, args.steps)
-        if not args.no_deferred and args.workload == "object":
+        if not args.no_optimize:
+            optim = optimize_variant(sop, load_workload("object"), dev, flush, args.steps)
+        if not args.no_deferred:
             defer = deferred_frame_variant(sop, dev, flush, args.steps)
-        if not args.no_compose and args.workload == "object":
-            comp = compose_frame_variant(sop, dev, flush, args.steps, l2_read_peak_gbs(dev), measured_peaks()[0],
-                                         peak_fp32)
+    if roof is None and frame is not None:
+        roof = frame["fp32"]["roofline"]
 
-    clocks = clk.summary()
     line = {
         "metric": "SOP-shaded point-dirs/s (bake + query/shade step)" if args.part != "bake" else
         "probe-bake texels/s",
@@ -807,28 +933,27 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded generators; the paper's SynCom/TensoIR scenes are not available)",
-        "config": {"workload": f"{W['name']}: {len(W['gauss']['mean'])} Gaussians, {P} probes {R}x{R}, "
-                               f"{M} points, K={K}, S={S}, env {W['env'].shape[0]}x{W['env'].shape[1]}",
-                   "part": args.part, "l2": "512 MB buffer written between timed steps",
-                   "parallelism": f"replicas x{world}"},
+        "config": {"workload": W["label"], "part": args.part, "probes_baked": st.P,
+                   "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{world}"},
         "bake": {"ms": round(mb, 4), "texels_per_s": round(texels / (mb * 1e-3), 1) if do_bake else None},
-        "query": {"ms": round(mq, 4), "point_dirs_per_s": round(pd / (mq * 1e-3), 1) if do_query else None},
-        "wall_s_timed_region": round(t_wall, 4),
-        "gpu_launches": launches_per_step(do_bake, do_query, P, R) * args.steps,
-        "clocks": clocks,
+        "query": {"ms": round(mq, 4), "point_dirs_per_s": round(pd / (mq * 1e-3), 1) if do_query else None,
+                  "parts": {q["name"]: q["M"] for q in st.parts}},
+        "wall_s_timed_region": round(r["wall_s"], 4),
+        "gpu_launches": launches_per_step(do_bake, len(st.parts) if do_query else 0) * args.steps,
+        "clocks": r["clocks"],
         "roofline": roof,
-        "roofline_query": roof_q,
-        "chosen": chosen,
+        "roofline_query": frame["fp32"]["roofline"] if frame else None,
+        "precision": frame["precision"] if frame else None,
+        "chosen": frame["chosen"] if frame else None,
         "chosen_bake": surr,
-        "env_octahedral": envoct,
-        "frnn_query": frnn,
+        "compose_frame_query": frame,
+        "object_step": objstep,
         "deferred_frame": defer,
-        "compose_frame_query": comp,
         "optimize_step": optim,
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.part == "step":
-        line["cpu_baseline"] = cpu_baseline(W, P, R, K, S, mode)
+        line["cpu_baseline"] = cpu_baseline(W)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -853,7 +978,7 @@ def optimize_variant(sop, W, dev, flush, steps):
     sop.bake(g, at)
     rgb, occ, _ = at.interior()
     traced = torch.cat([rgb, occ[..., None]], dim=-1).contiguous()
-    pts = {k: cu(v) for k, v in W["pts"].items()}
+    pts = {k: cu(v) for k, v in W["parts"][0]["pts"].items()}
     M = pts["x"].shape[0]
     target = cu(np.random.default_rng(11).uniform(0, 1, (M, 3)).astype(np.float32))
     opt = sop.TextureOptimizer(pts["albedo"], pts["rough"], pts["metal"], cu(W["env"]), traced.clone(), traced, pp)
@@ -889,40 +1014,43 @@ def compose_only(args, dev, sop):
                       "unit": "point-dirs/s", "steps": args.steps, "higher_is_better": True, "detail": r}))
 
 
-def launches_per_step(do_bake, do_query, P, R):
+def launches_per_step(do_bake, n_queries):
+    """This library's kernel launches in one step."""
     n = 0
     if do_bake:
-        # bbox init, gauss prep, grid setup, bin count, bin scan, bin fill,
-        # texel dirs, trace, atlas pack, depth pack
-        n += 10
-    if do_query:
-        # probe grid, knn, env pack, env footprints, atlas footprints, dirs, shade
-        n += 7
+        # binning: bbox init, Gaussian records, 3 attempts x (grid setup,
+        # count, scan) decided on the device, fill; trace: counter reset,
+        # texel directions, trace, atlas border
+        n += 2 + 3 * 3 + 1 + 4
+    # per query: probe grid, nearest probes, environment table and
+    # footprints, atlas footprints, directions, shade
+    n += 7 * n_queries
     return n
 
 
-def measure_e2e(args, W, P, dev, sop, flush):
+def measure_e2e(args, W, dev, sop, flush):
+    """The step through the public API from pinned host buffers: every step
+    copies the Gaussians and probe positions (before the bake) and the
+    points and environment (on a side stream while the bake runs) to the
+    device, and reads every shaded output back."""
     import torch
     host = {}
     for k, v in W["gauss"].items():
         host["g_" + k] = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
-    for k, v in W["pts"].items():
-        host["p_" + k] = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
-    host["probe_pos"] = torch.from_numpy(np.ascontiguousarray(W["probe_pos"][:P])).pin_memory()
+    for i, part in enumerate(W["parts"]):
+        for k, v in part["pts"].items():
+            host[f"p{i}_{k}"] = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+    host["probe_pos"] = torch.from_numpy(np.ascontiguousarray(W["probe_pos"])).pin_memory()
     host["env"] = torch.from_numpy(np.ascontiguousarray(W["env"])).pin_memory()
     dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-    M = len(W["pts"]["x"])
-    R, K, S, mode = W["R"], W["K"], W["S"], W["mode"]
-    out_h = torch.empty((M, 3), dtype=torch.float32).pin_memory()
+    R, K, S = W["R"], W["K"], W["S"]
+    outs_h = [torch.empty((len(part["pts"]["x"]), 3), dtype=torch.float32).pin_memory() for part in W["parts"]]
     bi = sum(v.numel() * v.element_size() for v in host.values())
-    bo = out_h.numel() * out_h.element_size()
-
+    bo = sum(o.numel() * o.element_size() for o in outs_h)
+    M = sum(len(part["pts"]["x"]) for part in W["parts"])
     side = torch.cuda.Stream(device=dev)
 
     def one():
-        # the bake's inputs first; the query's inputs on a side stream while
-        # the bake runs (the side stream starts after everything issued so
-        # far on the main stream, so the timed region holds every copy)
         main = torch.cuda.current_stream()
         for k in host:
             if k.startswith("g_") or k == "probe_pos":
@@ -930,15 +1058,16 @@ def measure_e2e(args, W, P, dev, sop, flush):
         side.wait_stream(main)
         with torch.cuda.stream(side):
             for k in host:
-                if k.startswith("p_") or k == "env":
+                if k.startswith("p") and k != "probe_pos" or k == "env":
                     dbuf[k].copy_(host[k], non_blocking=True)
         g = {k[2:]: dbuf[k] for k in dbuf if k.startswith("g_")}
-        at = sop.make_atlas(dbuf["probe_pos"], R)
+        at = sop.make_atlas(dbuf["probe_pos"], R, depth_scale=W["depth_scale"])
         sop.bake(g, at)
         main.wait_stream(side)
-        o = sop.query_shade(*[dbuf["p_" + k] for k in ("x", "n", "wo", "albedo", "rough", "metal")], at, dbuf["env"],
-                            K, S, mode=mode)
-        out_h.copy_(o, non_blocking=True)
+        for i, part in enumerate(W["parts"]):
+            o = sop.query_shade(*[dbuf[f"p{i}_{k}"] for k in ("x", "n", "wo", "albedo", "rough", "metal")],
+                                atlas_view(sop, at, *part["probes"]), dbuf["env"], K, S, mode=part["mode"])
+            outs_h[i].copy_(o, non_blocking=True)
 
     for _ in range(2):
         one()
@@ -957,68 +1086,67 @@ def measure_e2e(args, W, P, dev, sop, flush):
             "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)}
 
 
-def cpu_baseline(W, P, R, K, S, mode, seconds_hint=True):
-    """The FP64 oracle, as it stands, on a bounded sample of the same
-    workload: 16 probes (4,096 texel rays) of the bake and 4,096 points of
-    the query; scaled to the whole step."""
+def _oracle_step_seconds(W, rng, n_probes, n_points):
+    """The FP64 oracle on a bounded sample of one step: n_probes probes of the
+    bake and n_points points of each query part (at most), scaled to the
+    whole step. Returns (seconds of the step, description)."""
     import oracle
     from paper_2510_07729_gb300 import inputs as I
-    rng = np.random.default_rng(123)
-    probes = np.sort(rng.choice(P, min(16, P), replace=False))
+    P, R, K, S = len(W["probe_pos"]), W["R"], W["K"], W["S"]
+    probes = np.sort(rng.choice(P, min(n_probes, P), replace=False))
     t0 = time.perf_counter()
-    rgb, occ, dep, _ = oracle.bake(W["gauss"], W["probe_pos"][:P], R, probes=probes)
+    oracle.bake(W["gauss"], W["probe_pos"], R, probes=probes)
     tb = time.perf_counter() - t0
-    sel, pts = I.subsample(rng, W["pts"], ["x", "n", "wo", "albedo", "rough", "metal"], 4096)
-    maps = I.synthetic_maps(rng, P, R)
-    t0 = time.perf_counter()
-    oracle.query_shade(pts["x"], pts["n"], pts["wo"], pts["albedo"], pts["rough"], pts["metal"], W["probe_pos"][:P],
-                       maps["rgb"], maps["occ"], W["env"], K, S, mode=mode)
-    tq = time.perf_counter() - t0
-    M = len(W["pts"]["x"])
-    t_step = tb * (P / len(probes)) + tq * (M / len(sel))
-    return {"value": round(M * S / t_step, 1), "unit": "point-dirs/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"bake of {len(probes)} probes ({len(probes) * R * R} rays, {tb:.2f} s) + query of "
-                      f"{len(sel)} points x {S} dirs ({tq:.2f} s), scaled to the full step"}
+    t_step = tb * (P / len(probes))
+    desc = [f"bake of {len(probes)} probes ({len(probes) * R * R} rays, {tb:.2f} s)"]
+    for part in W["parts"]:
+        lo, hi = part["probes"]
+        M = len(part["pts"]["x"])
+        sel, pts = I.subsample(rng, part["pts"], ["x", "n", "wo", "albedo", "rough", "metal"], min(n_points, M))
+        maps = I.synthetic_maps(rng, hi - lo, R)
+        t0 = time.perf_counter()
+        oracle.query_shade(pts["x"], pts["n"], pts["wo"], pts["albedo"], pts["rough"], pts["metal"],
+                           W["probe_pos"][lo:hi], maps["rgb"], maps["occ"], W["env"], K, S, mode=part["mode"])
+        tq = time.perf_counter() - t0
+        t_step += tq * (M / len(sel))
+        desc.append(f"{part['name']} query of {len(sel)} points x {S} dirs ({tq:.2f} s)")
+    return t_step, " + ".join(desc) + ", scaled to the full step"
+
+
+def cpu_baseline(W):
+    """The FP64 oracle, as it stands, on a bounded sample of the same
+    workload (16 probes of the bake, 4,096 points of each query part),
+    scaled to the whole step."""
+    import oracle
+    t_step, desc = _oracle_step_seconds(W, np.random.default_rng(123), 16, 4096)
+    M = sum(len(p["pts"]["x"]) for p in W["parts"])
+    return {"value": round(M * W["S"] / t_step, 1), "unit": "point-dirs/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": desc}
 
 
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle timed on the host cores, each step a
-    bounded sample of the same workload, in the same metric."""
+    bounded sample of the same workload (2 probes of the bake, 512 points of
+    each query part, scaled to the step), in the same metric."""
     if rank != 0:
         return
     import oracle
-    from paper_2510_07729_gb300 import inputs as I
     W = load_workload(args.workload)
-    P, R, K, S, mode = len(W["probe_pos"]), W["R"], W["K"], W["S"], W["mode"]
-    M = len(W["pts"]["x"])
+    M = sum(len(p["pts"]["x"]) for p in W["parts"])
     rng = np.random.default_rng(7)
-    maps = I.synthetic_maps(rng, P, R)
-
-    def one():
-        probes = np.sort(rng.choice(P, 2, replace=False))
-        t0 = time.perf_counter()
-        oracle.bake(W["gauss"], W["probe_pos"], R, probes=probes)
-        tb = time.perf_counter() - t0
-        sel, pts = I.subsample(rng, W["pts"], ["x", "n", "wo", "albedo", "rough", "metal"], 512)
-        t0 = time.perf_counter()
-        oracle.query_shade(pts["x"], pts["n"], pts["wo"], pts["albedo"], pts["rough"], pts["metal"], W["probe_pos"],
-                           maps["rgb"], maps["occ"], W["env"], K, S, mode=mode)
-        tq = time.perf_counter() - t0
-        return tb * (P / 2) + tq * (M / 512)
-
     for _ in range(args.warmup):
-        one()
-    ts = [one() for _ in range(args.steps)]
+        _oracle_step_seconds(W, rng, 2, 512)
+    ts = [_oracle_step_seconds(W, rng, 2, 512)[0] for _ in range(args.steps)]
     t = float(np.mean(ts))
-    v = M * S / t
+    v = M * W["S"] / t
     line = {"impl": "reference", "metric": "SOP-shaded point-dirs/s (bake + query/shade step)", "value": round(v, 3),
             "unit": "point-dirs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": {"workload": W["name"], "parallelism": "host cores"},
+            "dtype": "f64", "data": "synthetic", "config": {"workload": W["label"], "parallelism": "host cores"},
             "cpu_baseline": {"value": round(v, 3), "unit": "point-dirs/s", "cores": oracle.num_threads(),
                              "kind": "oracle",
-                             "sample": "per step: bake of 2 probes + query of 512 points, scaled to the full step"},
+                             "sample": "per step: bake of 2 probes + 512 points of each query part, scaled to the "
+                                       "full step"},
             "e2e": {"value": round(v, 3), "unit": "point-dirs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
