@@ -68,6 +68,10 @@ typedef enum {
  *                              composite);
  *   SOP_DEVSTAT_INDEX          a caller-supplied index (probe ids, pixel
  *                              lists) was outside its range and skipped;
+ *   SOP_DEVSTAT_CAPACITY       a fixed-capacity buffer overflowed and the
+ *                              result was computed from part of its input
+ *                              (the surrogate's near-field search found
+ *                              more than 4,096 centres within r_near);
  *   SOP_DEVSTAT_GRID_COARSENED information, not an error: the bake's
  *                              binning grid was coarsened on the device
  *                              until the cell lists fit the workspace.
@@ -82,6 +86,7 @@ typedef enum {
 #define SOP_DEVSTAT_NONFINITE 0x1u
 #define SOP_DEVSTAT_BAKE_TRUNCATED 0x2u
 #define SOP_DEVSTAT_INDEX 0x4u
+#define SOP_DEVSTAT_CAPACITY 0x8u
 #define SOP_DEVSTAT_GRID_COARSENED 0x100u
 #define SOP_DEVSTAT_ERRORS 0xffu
 sop_status sop_device_status(void* stream, uint32_t* out_bits, int32_t clear);
@@ -399,51 +404,132 @@ sop_status sop_adam_l1_step(float* p, const float* g, float* m, float* v, int64_
                             void* stream);
 
 /* ---- Learned bake surrogate ------------------------------------------------
- * A small MLP predicts a probe's maps (O, D/depth_scale, RGB) from its
- * neighbourhood, to rebake probes quickly after an object moves; the
- * ray-traced sop_bake is its fallback and its judge (the paper has no
- * surrogate: it initialises SOPs by ray tracing, Sec. 3.1.2 / 3.2.2).
- *   probe features f_p (416 floats): the 32 Gaussians nearest to the probe
- *     (exact integer-key search, ties to the lower index), nearest first,
- *     each as (centre - probe) * 10, log(scale) + 5, opacity, rgb; then
- *     sin and cos of pi 2^(f/3) p for f = 0..15 and each axis;
- *   per texel: h1 = relu(W1p f_p + W1d d_t + b1), h2 = relu(W2 h1 + b2),
- *     h3 = relu(W3 h2 + b3), y = W4 h3 + b4 with d_t the texel direction and
- *     y = (O, D / depth_scale, R, G, B); written to an atlas as O clamped to
- *     [0,1] and D, RGB clamped at 0.
- * Parameters: one float32 vector of sop_surrogate_param_count() values, in
- * the order W1p [64][416], W1d [64][3], b1 [64], W2 [64][64], b2, W3 [64][64],
- * b3, W4 [5][64], b4 [5] (row-major, out x in). Weights are used as bfloat16
- * with float32 accumulation; the 64x64 layers run on the tensor cores.
- * Training: mean absolute error over the 5 outputs, Adam (0.9, 0.999, 1e-8,
- * bias-corrected), float32 master weights. The caller owns the state buffer
- * (sop_surrogate_state_bytes(), 256-byte aligned). */
+ * A small MLP predicts a probe texel's maps (O, D/depth_scale, RGB) from
+ * features of the probe's neighbourhood along the texel's ray, to rebake
+ * probes quickly after an object moves; the ray-traced sop_bake is its
+ * fallback and its judge (the paper has no surrogate: it initialises SOPs
+ * by ray tracing, Sec. 3.1.2 / 3.2.2).
+ * Texel features (SOP_SURROGATE_FEATURES = 18 per texel, float32,
+ * [P][R*R][18]), for the texel direction d (the octahedral decode of its
+ * centre):
+ *   [0..2]   d;
+ *   [3..8]   near field: the probe's nearest Gaussians (at most
+ *            SOP_SURROGATE_NEAR_CAP = 256 of the centres within r_near,
+ *            nearest first by the integer squared distance of positions
+ *            quantised to 2^-20, ties to the lower index), composited along
+ *            the texel ray in that order with the bake's ray-Gaussian
+ *            response: O_n = 1 - prod(1 - alpha), L_n (rgb) = sum T alpha
+ *            rgb, D_n = sum T alpha t* / W_n (0 when W_n <= 1e-8),
+ *            W_n = sum T alpha;
+ *   [9..17]  far field: each Gaussian with opacity >= alpha_min carries
+ *            the optical mass -ln(1 - min(o, alpha_max)) 2 pi s_2 s_3 (its
+ *            two largest scales) into the cubic cell of its quantised
+ *            centre (fixed-point sums; 128 cells along the longest axis of
+ *            the centres' bounding box, edge h); along the ray from t0 (the
+ *            last listed Gaussian's distance when the list is full, else
+ *            r_near) the cells' extinction sigma = mass / h^3 gives the
+ *            optical depth tau; the features are 1 - exp(-tau) at t0 + h
+ *            {2, 4, 8, 16, 32} and at the end of the grid, then the
+ *            emission-absorption colour sum exp(-tau) (1 - exp(-sigma dt))
+ *            rgb_cell (the march stops once tau > 20).
+ * Network: 18 -> 64 -> 64 -> 64 -> 5, ReLU, no output activation:
+ * y = (O, D / depth_scale, R, G, B); written to an atlas as O clamped to
+ * [0, 1], D and RGB clamped at 0. Parameters: one float32 vector of
+ * sop_surrogate_param_count() values in the order W1 [64][18], b1 [64],
+ * W2 [64][64], b2, W3 [64][64], b3, W4 [5][64], b4 [5] (row-major, out x
+ * in). Every matrix operand (weights, features, activations, back-
+ * propagated deltas) is used as bfloat16 (nearest-even) with float32
+ * accumulation; all four layers run on the tensor cores. Training: mean
+ * absolute error over the 5 outputs (an L1 loss, like the L1 texture
+ * supervision of Sec. 3.1.2), Adam (0.9, 0.999, 1e-8, bias-corrected) on
+ * float32 master weights. */
+#define SOP_SURROGATE_FEATURES 18
+#define SOP_SURROGATE_NEAR_CAP 256
+typedef struct sop_surrogate sop_surrogate; /* opaque handle */
 int32_t sop_surrogate_param_count(void);
+/* Bytes of the device state a handle works on (master weights, Adam
+ * moments, gradient, bf16 copy, step), caller-owned, 256-byte aligned. */
 size_t sop_surrogate_state_bytes(void);
-/* Load parameters (device [count] float32) into the state; resets Adam. */
-sop_status sop_surrogate_set_params(void* state, const float* params, void* stream);
-sop_status sop_surrogate_get_params(const void* state, float* params, void* stream);
-/* The gradient summed by the last sop_surrogate_train_step (device [count]). */
-sop_status sop_surrogate_get_grad(const void* state, float* grad, void* stream);
-/* Workspace for features / train / infer on n Gaussians, P probes of side R. */
+/* Make a handle over the caller's device state [state_bytes]: parameters
+ * from `params` (device [count] float32) or, when NULL, He-uniform initial
+ * weights (bound sqrt(6 / fan_in); weight i draws splitmix64(seed + i))
+ * with zero biases; Adam moments and step zero. r_near (> 0, world units)
+ * is the near-field radius of the features. The handle itself is one
+ * small host allocation that sop_surrogate_destroy frees; the library
+ * allocates no device memory. Asynchronous. */
+sop_status sop_surrogate_create(void* state, size_t state_bytes, const float* params, uint64_t seed, float r_near,
+                                sop_surrogate** out, void* stream);
+sop_status sop_surrogate_destroy(sop_surrogate* net);
+/* Parameters in and out (device [count] float32); set_params resets Adam.
+ * get_grad: the gradient summed by the last training step. Asynchronous. */
+sop_status sop_surrogate_set_params(sop_surrogate* net, const float* params, void* stream);
+sop_status sop_surrogate_get_params(const sop_surrogate* net, float* params, void* stream);
+sop_status sop_surrogate_get_grad(const sop_surrogate* net, float* grad, void* stream);
+/* Checkpoint: save writes the master weights, Adam moments and step to
+ * the file `path`; load reads such a file into the handle (bf16 copy
+ * refreshed, gradient zeroed), so that training resumes exactly where the
+ * save left it. Both synchronise `stream`. File format (little-endian):
+ * "SOPSURR2" (8 bytes), int32 count, int32 step, then count float32
+ * parameters, count float32 first moments, count float32 second moments.
+ * SOP_ERR_INVALID_ARG for a missing, short or mismatched file. */
+sop_status sop_surrogate_save(const sop_surrogate* net, const char* path, void* stream);
+sop_status sop_surrogate_load(sop_surrogate* net, const char* path, void* stream);
+/* The checkpoint format from and to host arrays (no GPU involved). */
+sop_status sop_surrogate_file_write(const char* path, int32_t count, int32_t step, const float* params,
+                                    const float* m, const float* v);
+sop_status sop_surrogate_file_read(const char* path, int32_t count, int32_t* step, float* params, float* m,
+                                   float* v);
+/* Workspace of sop_surrogate_features / _train / _infer on n Gaussians, P
+ * probes of side R (256-byte aligned). */
 size_t sop_surrogate_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R);
-/* Probe features: feats [P][416] float32 (device). Needs n >= 32. */
-sop_status sop_surrogate_features(const sop_gaussians* g, const float* probe_pos, int32_t P, float* feats, void* ws,
-                                  size_t ws_bytes, void* stream);
-/* One Adam step on B probes: probe_ids [B] (device; NULL = 0..B-1) index both
- * feats and the target atlas (baked maps, R x R texels each). loss_out
- * (device float, may be NULL) receives the mean absolute error of the batch
- * before the step. */
-sop_status sop_surrogate_train_step(void* state, const float* feats, const int32_t* probe_ids, int32_t B,
-                                    const sop_atlas* targets, float lr, float* loss_out, void* ws, size_t ws_bytes,
-                                    void* stream);
-/* Predict the maps of B probes (probe_ids as above) into `out` (interior
- * and border texels). */
-sop_status sop_surrogate_infer(const void* state, const float* feats, const int32_t* probe_ids, int32_t B,
-                               const sop_atlas* out, void* ws, size_t ws_bytes, void* stream);
+/* Texel features of P probes (probe_pos [P,3] device) against the
+ * Gaussians: feats [P][R*R][18] float32 (device); near_list [P][256] int32
+ * (device, -1 after the last) or NULL. bake params give alpha_min and
+ * alpha_max. Asynchronous. */
+sop_status sop_surrogate_features(const sop_surrogate* net, const sop_gaussians* g, const float* probe_pos,
+                                  int32_t P, int32_t R, const sop_bake_params* params, float* feats,
+                                  int32_t* near_list, void* ws, size_t ws_bytes, void* stream);
+/* Workspace of sop_surrogate_train alone (drawn batches, per-CTA partial
+ * gradients that are summed in a fixed order, so that training is
+ * bit-reproducible); sop_surrogate_workspace_bytes() covers it too. */
+size_t sop_surrogate_train_workspace_bytes(void);
+/* `steps` Adam steps at learning rate lr, each on `batch` probes of
+ * targets (P probes, baked maps of side R) with their features feats
+ * [P][R*R][18]: the probes probe_ids [batch] (device) when given, else
+ * drawn for each step as splitmix64(seed ^ (step 2^32 + i)) mod P (with
+ * replacement; step = the handle's step count). out_loss (device [steps]
+ * float32, or NULL) receives each step's mean absolute error before its
+ * update. 1 <= batch <= 65536. ws: sop_surrogate_train_workspace_bytes().
+ * The result is the same on every run. Asynchronous. */
+sop_status sop_surrogate_train(sop_surrogate* net, const float* feats, const int32_t* probe_ids, int32_t batch,
+                               const sop_atlas* targets, int32_t steps, float lr, uint64_t seed, float* out_loss,
+                               void* ws, size_t ws_bytes, void* stream);
+/* The network on given features: the maps of B probes (probe_ids [B]
+ * device, or NULL for 0..B-1, indexing feats and `out`) written into the
+ * atlas `out` (interior; border by the border rule when all of out's
+ * probes are predicted, i.e. probe_ids NULL and B = out->P). Asynchronous. */
+sop_status sop_surrogate_predict(const sop_surrogate* net, const float* feats, const int32_t* probe_ids, int32_t B,
+                                 const sop_atlas* out, void* stream);
+/* The learned rebake of every probe of `out` (positions out->probe_pos)
+ * against the Gaussians g, with its spot check and fallback, all on the
+ * device: bin the Gaussians (as sop_bake_bin), compute the features,
+ * predict every probe into `out`; ray-trace n = max(1, ceil(spot_frac P))
+ * probes (probe i of the sample is floor((i + u_i) P / n), u_i =
+ * splitmix64(seed + i) / 2^64: distinct and spread over the probes) and
+ * compare their O with the prediction: err = mean |dO| over their interior
+ * texels. If err > tau (or is not finite) every probe of `out` is
+ * ray-traced instead (fallback); the checked probes always keep their
+ * traced maps. out_spot_err (device float) receives err, out_fell_back
+ * (device int32) 1 after a fallback, else 0. 0 < spot_frac <= 1.
+ * Asynchronous: no host synchronisation, the decision is taken on the
+ * device. */
+sop_status sop_surrogate_infer(const sop_surrogate* net, const sop_gaussians* g, const sop_atlas* out,
+                               const sop_bake_params* params, float spot_frac, float tau, uint64_t seed,
+                               float* out_spot_err, int32_t* out_fell_back, void* ws, size_t ws_bytes, void* stream);
 /* Spot-check helpers: out[0] = sum |O_a - O_b| and out[1] = sum of |RGB_a -
  * RGB_b| over the interior texels of n probe pairs (a_probes[i],
- * b_probes[i]; NULL = 0..n-1), written to device out[2]. */
+ * b_probes[i]; NULL = 0..n-1), written to device out[2]; indices outside
+ * an atlas are skipped (SOP_DEVSTAT_INDEX). */
 sop_status sop_atlas_compare(const sop_atlas* a, const int32_t* a_probes, const sop_atlas* b, const int32_t* b_probes,
                              int32_t n, float* out, void* stream);
 /* Copy whole probes (all (R+2)^2 texels) src_probes[i] -> dst_probes[i]. */

@@ -395,6 +395,9 @@ struct TraceK {
     float4* gbuf;
     // device status word (SOP_DEVSTAT_* bits) or NULL
     unsigned int* status;
+    // when not NULL, the launch does nothing unless *run_if != 0 (a decision
+    // taken on the device, e.g. the surrogate's fallback)
+    const int32_t* run_if;
 };
 
 // what a traced ray writes: the probe atlas texel (O, L_in, depth) or the
@@ -744,6 +747,7 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
     __shared__ uint64_t s_dkey[kWarpsPerCta][kHitCap];
     __shared__ float s_dalpha[kWarpsPerCta][kHitCap];
     __shared__ int32_t s_que[kWarpsPerCta][64];
+    if (k.run_if && __ldg(k.run_if) == 0) return;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t* key = s_key[wib];
     float* alp = s_alpha[wib];
@@ -1023,8 +1027,9 @@ cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeL
 
 // Border texels of an atlas copied from the texels the border rule names.
 __global__ void gutter_fill_kernel(int32_t P, int32_t R, void* __restrict__ rgbo, int rgbo_bytes,
-                                   void* __restrict__ depth, int depth_bytes)
+                                   void* __restrict__ depth, int depth_bytes, const int32_t* run_if)
 {
+    if (run_if && __ldg(run_if) == 0) return;
     const int RS = R + 2, NB = 4 * (R + 1);  // border texels per probe
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)P * NB) return;
@@ -1084,7 +1089,7 @@ static unsigned trace_blocks(int64_t rays)
 }
 
 cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp, const BakeLayout& L, char* ws,
-                              cudaStream_t s)
+                              cudaStream_t s, const int32_t* run_if)
 {
     GaussGrid* grid = reinterpret_cast<GaussGrid*>(ws + L.hdr);
     const int R = atlas.R;
@@ -1117,9 +1122,10 @@ cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp,
     k.quat = k.scale = k.albedo = k.rough = k.metal = nullptr;
     k.gbuf = nullptr;
     k.status = status_word();
+    k.run_if = run_if;
     const int64_t rays = (int64_t)atlas.P * R * R;
     trace_kernel<kTraceAtlas><<<trace_blocks<kTraceAtlas>(rays), kWarpsPerCta * 32, 0, s>>>(k);
-    return launch_gutter_fill(atlas, s);
+    return launch_gutter_fill(atlas, s, run_if);
 }
 
 cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, const float* rough, const float* metal,
@@ -1155,18 +1161,19 @@ cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, co
     k.metal = metal;
     k.gbuf = reinterpret_cast<float4*>(out);
     k.status = status_word();
+    k.run_if = nullptr;
     const int64_t rays = (int64_t)n_origins * n_dirs;
     if (rays == 0) return cudaGetLastError();
     trace_kernel<kTraceGbuf><<<trace_blocks<kTraceGbuf>(rays), kWarpsPerCta * 32, 0, s>>>(k);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s)
+cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s, const int32_t* run_if)
 {
     const int64_t nbord = (int64_t)atlas.P * 4 * (atlas.R + 1);
     const int db = atlas.depth_dtype == SOP_F32 ? 4 : (atlas.depth_dtype == SOP_FP8E4M3 ? 1 : 2);
     gutter_fill_kernel<<<(unsigned)((nbord + 255) / 256), 256, 0, s>>>(
-        atlas.P, atlas.R, atlas.rgbo, atlas.rgbo_dtype == SOP_F32 ? 16 : 8, atlas.depth, db);
+        atlas.P, atlas.R, atlas.rgbo, atlas.rgbo_dtype == SOP_F32 ? 16 : 8, atlas.depth, db, run_if);
     return cudaGetLastError();
 }
 

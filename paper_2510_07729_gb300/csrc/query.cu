@@ -1568,13 +1568,13 @@ cudaError_t launch_read_probe(const void* buf, size_t bytes, int32_t reps, float
     return cudaGetLastError();
 }
 
-cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,
-                             char* ws, cudaStream_t s)
+SitesGrid launch_sites_grid(const float* sites, int32_t N, char* ws, cudaStream_t s)
 {
     int g = 1;
     while ((int64_t)g * g * g < N) ++g;
     const int64_t cells = (int64_t)(g + 1) * (g + 1) * (g + 1);
     size_t o = 0;
+    SitesGrid r;
     ProbeGrid* grid = reinterpret_cast<ProbeGrid*>(ws + o);
     o = align256(sizeof(ProbeGrid));
     int32_t* cstart = reinterpret_cast<int32_t*>(ws + o);
@@ -1583,7 +1583,6 @@ cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, in
     o = align256(o + sizeof(int32_t) * (size_t)cells);
     int4* ent = reinterpret_cast<int4*>(ws + o);
     o = align256(o + sizeof(int4) * (size_t)N);
-    o = align256(o + sizeof(float) * (size_t)M * K);  // (room for weights; the sites search writes none)
     int32_t* mm = reinterpret_cast<int32_t*>(ws + o);
     if (N <= 16384) {
         probe_grid_kernel<<<1, 1024, 0, s>>>(sites, N, g, grid, cstart, ccnt, ent);
@@ -1599,9 +1598,21 @@ cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, in
         sites_scan_kernel<<<1, 1024, 0, s>>>(grid, ccnt, cstart);
         sites_fill_kernel<<<nb, 256, 0, s>>>(sites, N, grid, cstart, ccnt, ent);
     }
+    r.grid = grid;
+    r.cell_start = cstart;
+    r.entries = ent;
+    return r;
+}
+
+size_t sites_grid_bytes(int32_t N) { return knn_sites_bytes(N, 0, 0); }
+
+cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,
+                             char* ws, cudaStream_t s)
+{
+    const SitesGrid sg = launch_sites_grid(sites, N, ws, s);
     if (M > 0) {
         const unsigned nb = (unsigned)((M + kKnnWarps - 1) / kKnnWarps);
-        knn_sites_warp_kernel<<<nb, kKnnWarps * 32, 0, s>>>(pts, M, K, grid, cstart, ent, idx);
+        knn_sites_warp_kernel<<<nb, kKnnWarps * 32, 0, s>>>(pts, M, K, sg.grid, sg.cell_start, sg.entries, idx);
     }
     return cudaGetLastError();
 }

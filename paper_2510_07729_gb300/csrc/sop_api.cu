@@ -1,6 +1,10 @@
 // C ABI of libsop: argument validation, workspace layout, launch sequencing.
 #include <math.h>
 #include <stdarg.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <new>
 #include <stdio.h>
 #include <string.h>
 
@@ -476,87 +480,316 @@ sop_status sop_query_shade_noalloc(const float* x, const float* n, const float* 
 }
 
 // ---- learned bake surrogate ----------------------------------------------------
+}  // extern "C"
+
+struct sop_surrogate {
+    uint32_t magic;
+    char* state;
+    float r_near;
+};
+
+namespace {
+
+constexpr uint32_t kSurrMagic = 0x53555232u;  // "SUR2"
+constexpr int32_t kMaxBatch = 65536;
+
+sop_status check_net(const sop_surrogate* net)
+{
+    if (!net || net->magic != kSurrMagic) return fail(SOP_ERR_INVALID_ARG, "not a surrogate handle");
+    return SOP_OK;
+}
+
+// the surrogate's workspace: a bake workspace (grid, records), the feature
+// scratch, the features, a spot-check atlas for up to P probes, the sample
+struct SurrRunLayout {
+    size_t bake, feat, feats, spot_rgbo, spot_depth, spot_ids, spot_pos, sums, ids, total;
+    sop::BakeLayout B;
+};
+
+SurrRunLayout surr_run_layout(int64_t n, int32_t P, int32_t R)
+{
+    SurrRunLayout L{};
+    L.B = sop::bake_layout(n, 0, 0.f);
+    const size_t tex = (size_t)P * (R + 2) * (R + 2);
+    size_t o = 0;
+    L.bake = o;       o = sop::align256(o + L.B.total);
+    L.feat = o;       o = sop::align256(o + sop::surr_feat_layout(n, P, R).total);
+    L.feats = o;      o = sop::align256(o + sizeof(float) * (size_t)P * R * R * sop::surr_n_features());
+    L.spot_rgbo = o;  o = sop::align256(o + 16 * tex);
+    L.spot_depth = o; o = sop::align256(o + 4 * tex);
+    L.spot_ids = o;   o = sop::align256(o + sizeof(int32_t) * (size_t)P);
+    L.spot_pos = o;   o = sop::align256(o + 3 * sizeof(float) * (size_t)P);
+    L.sums = o;       o = sop::align256(o + 4 * sizeof(float));
+    L.ids = o;        o = sop::align256(o + sizeof(int32_t) * (size_t)kMaxBatch);
+    L.total = o;
+    return L;
+}
+
+sop_status check_gauss(const sop_gaussians* g)
+{
+    if (!g) return fail(SOP_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 1 || g->n > (int64_t)INT32_MAX) return fail(SOP_ERR_INVALID_ARG, "n = %lld out of range", (long long)g->n);
+    if (!g->mean || !g->scale || !g->quat || !g->opacity || !g->rgb)
+        return fail(SOP_ERR_INVALID_ARG, "a Gaussian array is NULL");
+    return SOP_OK;
+}
+
+// features of every probe of `atlas`-sized sets into the run workspace
+sop_status surr_feats_into(const sop_surrogate* net, const sop_gaussians* g, const float* probe_pos, int32_t P,
+                           int32_t R, const sop_bake_params* bp, float* feats, int32_t* list, char* w,
+                           const SurrRunLayout& L, cudaStream_t s, const char* what)
+{
+    sop_status st = cuda_status(sop::launch_bake_bin(*g, bp->alpha_min, L.B, w + L.bake, s), what);
+    if (st != SOP_OK) return st;
+    st = cuda_status(sop::launch_bake_fill(*g, L.B, w + L.bake, s), what);
+    if (st != SOP_OK) return st;
+    return cuda_status(sop::surr_features(*g, probe_pos, P, R, net->r_near, bp->alpha_min, bp->alpha_max,
+                                          w + L.bake + L.B.rec, feats, list, w + L.feat, s),
+                       what);
+}
+
+}  // namespace
+
+extern "C" {
+
 int32_t sop_surrogate_param_count(void) { return sop::surr_n_params(); }
 
 size_t sop_surrogate_state_bytes(void) { return sop::surr_state_bytes(); }
 
-sop_status sop_surrogate_set_params(void* state, const float* params, void* stream)
+sop_status sop_surrogate_create(void* state, size_t state_bytes, const float* params, uint64_t seed, float r_near,
+                                sop_surrogate** out, void* stream)
 {
-    if (!state || !params) return fail(SOP_ERR_INVALID_ARG, "state / params is NULL");
-    if (!aligned(state, 256)) return fail(SOP_ERR_INVALID_ARG, "state must be 256-byte aligned");
-    return cuda_status(sop::surr_set_params((char*)state, params, (cudaStream_t)stream), "sop_surrogate_set_params");
+    if (!out) return fail(SOP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!state || !aligned(state, 256)) return fail(SOP_ERR_INVALID_ARG, "state is NULL or not 256-byte aligned");
+    if (state_bytes < sop::surr_state_bytes())
+        return fail(SOP_ERR_WORKSPACE, "state too small: %zu < %zu bytes", state_bytes, sop::surr_state_bytes());
+    if (!(r_near > 0.f) || !isfinite(r_near) || r_near > 2048.f)
+        return fail(SOP_ERR_INVALID_ARG, "r_near = %g must be in (0, 2048]", (double)r_near);
+    sop_status st = cuda_status(sop::surr_set_params((char*)state, params, seed, (cudaStream_t)stream),
+                                "sop_surrogate_create");
+    if (st != SOP_OK) return st;
+    sop_surrogate* net = new (std::nothrow) sop_surrogate;
+    if (!net) return fail(SOP_ERR_INVALID_ARG, "out of host memory for the handle");
+    net->magic = kSurrMagic;
+    net->state = (char*)state;
+    net->r_near = r_near;
+    *out = net;
+    return SOP_OK;
 }
 
-sop_status sop_surrogate_get_params(const void* state, float* params, void* stream)
+sop_status sop_surrogate_destroy(sop_surrogate* net)
 {
-    if (!state || !params) return fail(SOP_ERR_INVALID_ARG, "state / params is NULL");
-    return cuda_status(sop::surr_get_params((const char*)state, params, (cudaStream_t)stream),
-                       "sop_surrogate_get_params");
+    if (!net) return SOP_OK;
+    sop_status st = check_net(net);
+    if (st != SOP_OK) return st;
+    net->magic = 0;
+    delete net;
+    return SOP_OK;
 }
 
-sop_status sop_surrogate_get_grad(const void* state, float* grad, void* stream)
+sop_status sop_surrogate_set_params(sop_surrogate* net, const float* params, void* stream)
 {
-    if (!state || !grad) return fail(SOP_ERR_INVALID_ARG, "state / grad is NULL");
-    return cuda_status(sop::surr_get_grad((const char*)state, grad, (cudaStream_t)stream), "sop_surrogate_get_grad");
+    sop_status st = check_net(net);
+    if (st != SOP_OK) return st;
+    if (!params) return fail(SOP_ERR_INVALID_ARG, "params is NULL");
+    return cuda_status(sop::surr_set_params(net->state, params, 0, (cudaStream_t)stream), "sop_surrogate_set_params");
+}
+
+sop_status sop_surrogate_get_params(const sop_surrogate* net, float* params, void* stream)
+{
+    sop_status st = check_net(net);
+    if (st != SOP_OK) return st;
+    if (!params) return fail(SOP_ERR_INVALID_ARG, "params is NULL");
+    return cuda_status(sop::surr_get_params(net->state, params, (cudaStream_t)stream), "sop_surrogate_get_params");
+}
+
+sop_status sop_surrogate_get_grad(const sop_surrogate* net, float* grad, void* stream)
+{
+    sop_status st = check_net(net);
+    if (st != SOP_OK) return st;
+    if (!grad) return fail(SOP_ERR_INVALID_ARG, "grad is NULL");
+    return cuda_status(sop::surr_get_grad(net->state, grad, (cudaStream_t)stream), "sop_surrogate_get_grad");
+}
+
+sop_status sop_surrogate_file_write(const char* path, int32_t count, int32_t step, const float* params,
+                                    const float* m, const float* v)
+{
+    if (!path || !params || !m || !v || count < 1) return fail(SOP_ERR_INVALID_ARG, "bad checkpoint arguments");
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(SOP_ERR_INVALID_ARG, "cannot open %s for writing", path);
+    bool ok = fwrite("SOPSURR2", 1, 8, f) == 8 && fwrite(&count, 4, 1, f) == 1 && fwrite(&step, 4, 1, f) == 1 &&
+              fwrite(params, 4, (size_t)count, f) == (size_t)count && fwrite(m, 4, (size_t)count, f) == (size_t)count &&
+              fwrite(v, 4, (size_t)count, f) == (size_t)count;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(SOP_ERR_INVALID_ARG, "writing %s failed", path);
+    return SOP_OK;
+}
+
+sop_status sop_surrogate_file_read(const char* path, int32_t count, int32_t* step, float* params, float* m, float* v)
+{
+    if (!path || !step || !params || !m || !v || count < 1) return fail(SOP_ERR_INVALID_ARG, "bad checkpoint arguments");
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(SOP_ERR_INVALID_ARG, "cannot open %s", path);
+    char magic[8];
+    int32_t n = 0, st = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "SOPSURR2", 8) == 0 && fread(&n, 4, 1, f) == 1 &&
+              fread(&st, 4, 1, f) == 1;
+    if (ok && n != count) {
+        fclose(f);
+        return fail(SOP_ERR_INVALID_ARG, "%s holds %d parameters, expected %d", path, n, count);
+    }
+    ok = ok && fread(params, 4, (size_t)count, f) == (size_t)count && fread(m, 4, (size_t)count, f) == (size_t)count &&
+         fread(v, 4, (size_t)count, f) == (size_t)count;
+    char extra;
+    ok = ok && fread(&extra, 1, 1, f) == 0;
+    fclose(f);
+    if (!ok) return fail(SOP_ERR_INVALID_ARG, "%s is not a surrogate checkpoint of this size (bad header or length)",
+                         path);
+    *step = st;
+    return SOP_OK;
+}
+
+sop_status sop_surrogate_save(const sop_surrogate* net, const char* path, void* stream)
+{
+    sop_status st = check_net(net);
+    if (st != SOP_OK) return st;
+    if (!path) return fail(SOP_ERR_INVALID_ARG, "path is NULL");
+    const int n = sop::surr_n_params();
+    float* buf = (float*)malloc(sizeof(float) * 3 * (size_t)n);
+    if (!buf) return fail(SOP_ERR_INVALID_ARG, "out of host memory");
+    int32_t step = 0;
+    st = cuda_status(sop::surr_state_io(net->state, buf, buf + n, buf + 2 * n, &step, false, (cudaStream_t)stream),
+                     "sop_surrogate_save");
+    if (st == SOP_OK) st = sop_surrogate_file_write(path, n, step, buf, buf + n, buf + 2 * n);
+    free(buf);
+    return st;
+}
+
+sop_status sop_surrogate_load(sop_surrogate* net, const char* path, void* stream)
+{
+    sop_status st = check_net(net);
+    if (st != SOP_OK) return st;
+    const int n = sop::surr_n_params();
+    float* buf = (float*)malloc(sizeof(float) * 3 * (size_t)n);
+    if (!buf) return fail(SOP_ERR_INVALID_ARG, "out of host memory");
+    int32_t step = 0;
+    st = sop_surrogate_file_read(path, n, &step, buf, buf + n, buf + 2 * n);
+    if (st == SOP_OK)
+        st = cuda_status(sop::surr_state_io(net->state, buf, buf + n, buf + 2 * n, &step, true, (cudaStream_t)stream),
+                         "sop_surrogate_load");
+    free(buf);
+    return st;
 }
 
 size_t sop_surrogate_workspace_bytes(int64_t n_gauss, int32_t P, int32_t R)
 {
-    if (n_gauss < 32 || P < 1 || R < 2) return 0;
-    const size_t a = sop::surr_features_ws_bytes(n_gauss, P), b = sop::surr_run_ws_bytes(P, R);
+    if (n_gauss < 1 || P < 1 || R < 2 || R > 64) return 0;
+    const size_t a = surr_run_layout(n_gauss, P, R).total, b = sop::surr_train_ws_bytes();
     return a > b ? a : b;
 }
 
-sop_status sop_surrogate_features(const sop_gaussians* g, const float* probe_pos, int32_t P, float* feats, void* ws,
-                                  size_t ws_bytes, void* stream)
+size_t sop_surrogate_train_workspace_bytes(void) { return sop::surr_train_ws_bytes(); }
+
+sop_status sop_surrogate_features(const sop_surrogate* net, const sop_gaussians* g, const float* probe_pos,
+                                  int32_t P, int32_t R, const sop_bake_params* params, float* feats,
+                                  int32_t* near_list, void* ws, size_t ws_bytes, void* stream)
 {
-    if (!g || !probe_pos || !feats) return fail(SOP_ERR_INVALID_ARG, "a pointer is NULL");
-    if (P < 1) return fail(SOP_ERR_INVALID_ARG, "P = %d < 1", P);
-    if (g->n < 32 || g->n > (int64_t)INT32_MAX)
-        return fail(SOP_ERR_INVALID_ARG, "the surrogate needs at least 32 Gaussians (n = %lld)", (long long)g->n);
-    if (!g->mean || !g->scale || !g->opacity || !g->rgb) return fail(SOP_ERR_INVALID_ARG, "a Gaussian array is NULL");
-    sop_status st = check_ws(ws, ws_bytes, sop::surr_features_ws_bytes(g->n, P));
+    sop_status st = check_net(net);
     if (st != SOP_OK) return st;
-    return cuda_status(sop::surr_features(*g, probe_pos, P, feats, (char*)ws, (cudaStream_t)stream),
-                       "sop_surrogate_features");
+    if ((st = check_gauss(g)) != SOP_OK || (st = check_bake_args(g, params)) != SOP_OK) return st;
+    if (!probe_pos || !feats) return fail(SOP_ERR_INVALID_ARG, "probe_pos / feats is NULL");
+    if (P < 1 || R < 2 || R > 64) return fail(SOP_ERR_INVALID_ARG, "P = %d, R = %d invalid", P, R);
+    const SurrRunLayout L = surr_run_layout(g->n, P, R);
+    if ((st = check_ws(ws, ws_bytes, L.total)) != SOP_OK) return st;
+    return surr_feats_into(net, g, probe_pos, P, R, params, feats, near_list, (char*)ws, L, (cudaStream_t)stream,
+                           "sop_surrogate_features");
 }
 
-sop_status sop_surrogate_train_step(void* state, const float* feats, const int32_t* probe_ids, int32_t B,
-                                    const sop_atlas* targets, float lr, float* loss_out, void* ws, size_t ws_bytes,
-                                    void* stream)
+sop_status sop_surrogate_train(sop_surrogate* net, const float* feats, const int32_t* probe_ids, int32_t batch,
+                               const sop_atlas* targets, int32_t steps, float lr, uint64_t seed, float* out_loss,
+                               void* ws, size_t ws_bytes, void* stream)
 {
-    if (!state || !feats) return fail(SOP_ERR_INVALID_ARG, "state / feats is NULL");
-    sop_status st = check_atlas(targets, true);
+    sop_status st = check_net(net);
     if (st != SOP_OK) return st;
-    if (B < 1) return fail(SOP_ERR_INVALID_ARG, "B = %d < 1", B);
-    if (!probe_ids && B > targets->P) return fail(SOP_ERR_INVALID_ARG, "B exceeds the target atlas' probes");
+    if ((st = check_atlas(targets, true)) != SOP_OK) return st;
+    if (!feats) return fail(SOP_ERR_INVALID_ARG, "feats is NULL");
+    if (batch < 1 || batch > kMaxBatch) return fail(SOP_ERR_INVALID_ARG, "batch = %d outside [1, %d]", batch, kMaxBatch);
+    if (steps < 0) return fail(SOP_ERR_INVALID_ARG, "steps = %d < 0", steps);
     if (!(lr > 0.f) || !isfinite(lr)) return fail(SOP_ERR_INVALID_ARG, "lr must be finite and > 0");
-    st = check_ws(ws, ws_bytes, sop::surr_run_ws_bytes(B, targets->R));
-    if (st != SOP_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
-    st = cuda_status(sop::surr_train_step((char*)state, feats, probe_ids, B, *targets, lr, (char*)ws, s),
-                     "sop_surrogate_train_step");
-    if (st != SOP_OK || !loss_out) return st;
-    const float scale = 1.f / ((float)B * targets->R * targets->R * 5.f);
-    return cuda_status(sop::surr_loss_out((const char*)state, scale, loss_out, s), "sop_surrogate_train_step (loss)");
+    if ((st = check_ws(ws, ws_bytes, sop::surr_train_ws_bytes())) != SOP_OK) return st;
+    return cuda_status(sop::surr_train_steps(net->state, feats, probe_ids, batch, targets->P, *targets, steps, lr, seed,
+                                             out_loss, (char*)ws, (cudaStream_t)stream),
+                       "sop_surrogate_train");
 }
 
-sop_status sop_surrogate_infer(const void* state, const float* feats, const int32_t* probe_ids, int32_t B,
-                               const sop_atlas* out, void* ws, size_t ws_bytes, void* stream)
+sop_status sop_surrogate_predict(const sop_surrogate* net, const float* feats, const int32_t* probe_ids, int32_t B,
+                                 const sop_atlas* out, void* stream)
 {
-    if (!state || !feats) return fail(SOP_ERR_INVALID_ARG, "state / feats is NULL");
-    sop_status st = check_atlas(out, true);
+    sop_status st = check_net(net);
     if (st != SOP_OK) return st;
-    if (B < 1) return fail(SOP_ERR_INVALID_ARG, "B = %d < 1", B);
-    if (!probe_ids && B > out->P) return fail(SOP_ERR_INVALID_ARG, "B exceeds the atlas' probes");
-    st = check_ws(ws, ws_bytes, sop::surr_run_ws_bytes(B, out->R));
-    if (st != SOP_OK) return st;
+    if ((st = check_atlas(out, true)) != SOP_OK) return st;
+    if (!feats) return fail(SOP_ERR_INVALID_ARG, "feats is NULL");
+    if (B < 0 || (!probe_ids && B > out->P)) return fail(SOP_ERR_INVALID_ARG, "B = %d invalid", B);
     cudaStream_t s = (cudaStream_t)stream;
-    st = cuda_status(sop::surr_infer((const char*)state, feats, probe_ids, B, *out, (char*)ws, s),
-                     "sop_surrogate_infer");
+    st = cuda_status(sop::surr_infer(net->state, feats, probe_ids, B, out->P, *out, s), "sop_surrogate_predict");
+    if (st != SOP_OK || probe_ids || B != out->P) return st;
+    return cuda_status(sop::launch_gutter_fill(*out, s), "sop_surrogate_predict (border)");
+}
+
+sop_status sop_surrogate_infer(const sop_surrogate* net, const sop_gaussians* g, const sop_atlas* out,
+                               const sop_bake_params* params, float spot_frac, float tau, uint64_t seed,
+                               float* out_spot_err, int32_t* out_fell_back, void* ws, size_t ws_bytes, void* stream)
+{
+    sop_status st = check_net(net);
     if (st != SOP_OK) return st;
-    // border texels from the predicted interior
-    return cuda_status(sop::launch_gutter_fill(*out, s), "sop_surrogate_infer (border)");
+    if ((st = check_gauss(g)) != SOP_OK || (st = check_bake_args(g, params)) != SOP_OK) return st;
+    if ((st = check_atlas(out, true)) != SOP_OK) return st;
+    if (!(spot_frac > 0.f && spot_frac <= 1.f)) return fail(SOP_ERR_INVALID_ARG, "spot_frac must be in (0, 1]");
+    if (!(tau >= 0.f) || !isfinite(tau)) return fail(SOP_ERR_INVALID_ARG, "tau must be finite and >= 0");
+    if (!out_fell_back) return fail(SOP_ERR_INVALID_ARG, "out_fell_back is NULL");
+    const int32_t P = out->P, R = out->R;
+    const SurrRunLayout L = surr_run_layout(g->n, P, R);
+    if ((st = check_ws(ws, ws_bytes, L.total)) != SOP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = (char*)ws;
+    float* feats = (float*)(w + L.feats);
+    // features (binning included) and the prediction of every probe
+    if ((st = surr_feats_into(net, g, out->probe_pos, P, R, params, feats, nullptr, w, L, s,
+                              "sop_surrogate_infer (features)")) != SOP_OK)
+        return st;
+    st = cuda_status(sop::surr_infer(net->state, feats, nullptr, P, P, *out, s), "sop_surrogate_infer (network)");
+    if (st != SOP_OK) return st;
+    if ((st = cuda_status(sop::launch_gutter_fill(*out, s), "sop_surrogate_infer (border)")) != SOP_OK) return st;
+    // spot check: trace the sample into the workspace's atlas and compare
+    const int32_t n_spot = std::max(1, std::min(P, (int32_t)ceil((double)spot_frac * P)));
+    int32_t* ids = (int32_t*)(w + L.spot_ids);
+    float* pos = (float*)(w + L.spot_pos);
+    if ((st = cuda_status(sop::launch_spot_pick(seed, P, n_spot, out->probe_pos, ids, pos, s),
+                          "sop_surrogate_infer (sample)")) != SOP_OK)
+        return st;
+    sop_atlas spot = *out;
+    spot.rgbo = w + L.spot_rgbo;
+    spot.depth = out->depth ? w + L.spot_depth : nullptr;
+    spot.P = n_spot;
+    spot.probe_pos = pos;
+    spot.probe_nrm = nullptr;
+    if ((st = cuda_status(sop::launch_bake_trace(spot, *params, L.B, w + L.bake, s), "sop_surrogate_infer (spot bake)")) !=
+        SOP_OK)
+        return st;
+    float* sums = (float*)(w + L.sums);
+    if ((st = cuda_status(sop::launch_atlas_compare(spot, nullptr, *out, ids, n_spot, sums, s),
+                          "sop_surrogate_infer (compare)")) != SOP_OK)
+        return st;
+    if ((st = cuda_status(sop::launch_spot_decide(sums, 1.f / ((float)n_spot * R * R), tau, out_spot_err,
+                                                  out_fell_back, s),
+                          "sop_surrogate_infer (decision)")) != SOP_OK)
+        return st;
+    // fallback: every probe traced, only when the device decided so
+    if ((st = cuda_status(sop::launch_bake_trace(*out, *params, L.B, w + L.bake, s, out_fell_back),
+                          "sop_surrogate_infer (fallback bake)")) != SOP_OK)
+        return st;
+    return cuda_status(sop::launch_atlas_copy(spot, nullptr, *out, ids, n_spot, s), "sop_surrogate_infer (spot copy)");
 }
 
 sop_status sop_atlas_compare(const sop_atlas* a, const int32_t* a_probes, const sop_atlas* b, const int32_t* b_probes,

@@ -59,8 +59,17 @@ cudaError_t launch_l1_grad(const float* C, const float* Ct, int64_t n, float* gr
 cudaError_t launch_adam_l1(float* p, const float* g, float* m, float* v, int64_t n, const sop_adam_params& a,
                            cudaStream_t s);
 
-// K nearest sites of M points (surrogate features)
+// K nearest sites of M points
 size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K);
+// the uniform grid of N sites (quantised positions and indices) that the
+// site searches use, built in ws (sites_grid_bytes(N) bytes)
+struct SitesGrid {
+    const ProbeGrid* grid;
+    const int32_t* cell_start;
+    const int4* entries;
+};
+size_t sites_grid_bytes(int32_t N);
+SitesGrid launch_sites_grid(const float* sites, int32_t N, char* ws, cudaStream_t s);
 cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,
                              char* ws, cudaStream_t s);
 
@@ -86,9 +95,10 @@ constexpr size_t kBakeEntryBytes = 16;
 BakeLayout bake_layout(int64_t N, int64_t entries_cap, float density = 0.f);
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s);
-cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s);
+// run_if: when not NULL, the launches do nothing unless *run_if != 0 (device)
+cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s, const int32_t* run_if = nullptr);
 cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp, const BakeLayout& L, char* ws,
-                              cudaStream_t s);
+                              cudaStream_t s, const int32_t* run_if = nullptr);
 
 // ---- deferred front end (G-buffers, shading points, compositing) --------------
 cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, const float* rough, const float* metal,
@@ -113,23 +123,42 @@ cudaError_t launch_fps(const float* pts, const float* nrm, int64_t n, int32_t k,
 // ---- learned bake surrogate ---------------------------------------------------
 struct SurrState;
 int surr_n_params();
+int surr_n_features();
+int surr_near_cap();
 size_t surr_state_bytes();
-cudaError_t surr_set_params(char* state, const float* params, cudaStream_t s);
+// params NULL: He-uniform initial weights from `seed`; resets Adam
+cudaError_t surr_set_params(char* state, const float* params, uint64_t seed, cudaStream_t s);
 cudaError_t surr_get_params(const char* state, float* params, cudaStream_t s);
 cudaError_t surr_get_grad(const char* state, float* grad, cudaStream_t s);
-size_t surr_features_ws_bytes(int64_t N, int32_t P);
-size_t surr_run_ws_bytes(int32_t B, int32_t R);
-cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_t P, float* feats, char* ws,
+// host arrays <-> the state (master weights, Adam moments, step); synchronises
+cudaError_t surr_state_io(char* state, float* master, float* m, float* v, int32_t* step, bool to_device,
                           cudaStream_t s);
-cudaError_t surr_train_step(char* state, const float* feats, const int32_t* pid, int32_t B, const sop_atlas& tgt,
-                            float lr, char* ws, cudaStream_t s);
-cudaError_t surr_infer(const char* state, const float* feats, const int32_t* pid, int32_t B, const sop_atlas& out,
-                       char* ws, cudaStream_t s);
+struct SurrFeatLayout {
+    size_t sites, tdirs, t0, fhdr, fmm, facc, fcells, total;
+};
+SurrFeatLayout surr_feat_layout(int64_t N, int32_t P, int32_t R);
+// features [P][R*R][18] of every texel; bake_rec: the Gaussian records of a
+// binned bake workspace; list [P][near cap] or NULL
+cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_t P, int32_t R, float r_n,
+                          float alpha_min, float alpha_max, const char* bake_rec, float* feats, int32_t* list,
+                          char* ws, cudaStream_t s);
+// `steps` Adam steps on B probes each (pid, or drawn from seed); ws holds
+// surr_train_ws_bytes() (drawn ids, per-CTA gradient and loss sums)
+size_t surr_train_ws_bytes();
+cudaError_t surr_train_steps(char* state, const float* feats, const int32_t* pid, int32_t B, int32_t P,
+                             const sop_atlas& tgt, int32_t steps, float lr, uint64_t seed, float* loss_out,
+                             char* ws, cudaStream_t s);
+cudaError_t surr_infer(const char* state, const float* feats, const int32_t* pid, int32_t B, int32_t P,
+                       const sop_atlas& out, cudaStream_t s);
 cudaError_t surr_loss_out(const char* state, float scale, float* out, cudaStream_t s);
 cudaError_t launch_atlas_compare(const sop_atlas& a, const int32_t* ap, const sop_atlas& b, const int32_t* bp,
                                  int32_t n, float* out, cudaStream_t s);
 cudaError_t launch_atlas_copy(const sop_atlas& src, const int32_t* sp, const sop_atlas& dst, const int32_t* dp,
                               int32_t n, cudaStream_t s);
+cudaError_t launch_spot_pick(uint64_t seed, int32_t P, int32_t n, const float* probe_pos, int32_t* ids, float* pos,
+                             cudaStream_t s);
+cudaError_t launch_spot_decide(const float* sums, float inv_texels, float tau, float* err_out, int32_t* fell_back,
+                               cudaStream_t s);
 
 // ---- device status word (status.cu) -------------------------------------------
 // Address of this device's status word (kernels atomicOr SOP_DEVSTAT_* bits

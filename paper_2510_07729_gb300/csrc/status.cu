@@ -53,6 +53,7 @@ const char* status_bits_message(uint32_t bits)
     if (bits & SOP_DEVSTAT_BAKE_TRUNCATED)
         add("a bake ray met more hits at one depth than its hit buffer holds and stopped there");
     if (bits & SOP_DEVSTAT_INDEX) add("an index outside its range was skipped");
+    if (bits & SOP_DEVSTAT_CAPACITY) add("a fixed-capacity buffer overflowed (part of the input was used)");
     if (bits & SOP_DEVSTAT_GRID_COARSENED) add("(info) the binning grid was coarsened to fit the workspace");
     return g_msg;
 }

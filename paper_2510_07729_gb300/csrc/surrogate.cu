@@ -1,34 +1,47 @@
-// Learned bake surrogate for sm_103a: a small MLP that predicts a probe's
-// octahedral maps (O, D/depth_scale, RGB) from the probe's 32 nearest
-// Gaussians and the texel direction, so probes can be rebaked fast after an
-// object moves. The ray-traced bake stays its fallback and its judge.
+// Learned bake surrogate for sm_103a: a small MLP predicts each probe texel's
+// maps (O, D/depth_scale, RGB) from 18 features of the probe's neighbourhood
+// along that texel's ray, so that probes can be rebaked quickly after an
+// object moves. The ray-traced bake stays its fallback and its judge. The
+// paper has none of this: it initialises SOPs by ray tracing (Sec. 3.1.2)
+// and caches occlusion (Sec. 3.2.2).
 //
-//   f_p (416)  = 32 nearest Gaussians (nearest first) x [(mu - p) * 10,
-//                log(scale) + 5, opacity, rgb], then sin/cos of
-//                pi 2^(f/3) p_axis for f = 0..15
-//   h1 = relu(W1p f_p + W1d d_t + b1)   (the f_p part once per probe)
-//   h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3), y = W4 h3 + b4 (5 outputs)
-//
-// Weights are used as bfloat16 with float32 accumulation; float32 master
-// weights and Adam moments live in the caller's state buffer. The two
-// 64x64 layers run on the tensor cores (mma.sync m16n8k16 bf16 -> f32) in
-// the forward pass, in the back-propagation of deltas and in the weight
-// gradients (sums over samples); the small layers (416 -> 64 per probe,
-// 3 -> 64, 64 -> 5) are plain FP32 FMA.
+// Features of texel t of probe p (direction d_t, the octahedral decode of
+// its centre):
+//   d_t (3);
+//   near field (6): the probe's nearest Gaussians (at most kNearCap, centres
+//     within r_n, nearest first by the integer squared distance of positions
+//     quantised to 2^-20, ties to the lower index), composited along the
+//     texel ray in that order with the bake's ray-Gaussian response:
+//     O_n = 1 - prod(1 - alpha), L_n rgb = sum T alpha rgb, D_n =
+//     sum T alpha t* / W_n, W_n = sum T alpha;
+//   far field (9): a coarse extinction grid (optical mass -ln(1 -
+//     min(o, alpha_max)) 2 pi s_2 s_3 of each Gaussian in the cubic cell of
+//     its quantised centre, fixed-point sums, kFarCells along the longest
+//     axis) marched along the ray from t0 (the last listed Gaussian's
+//     distance when the list is full, else r_n): 1 - exp(-tau) at t0 + h
+//     {2, 4, 8, 16, 32} and at the end, and the emission-absorption colour.
+// Network: 18 -> 64 -> 64 -> 64 -> 5, ReLU; every matrix operand (weights,
+// features, activations, back-propagated deltas) rounded to bfloat16, sums
+// in float32, all four layers on the tensor cores (mma.sync m16n8k16 bf16 ->
+// f32) in the forward pass, the delta back-propagation and the weight
+// gradients. Float32 master weights and Adam moments live in the caller's
+// state buffer.
 #include "sop_device.cuh"
 #include "sop_internal.h"
 
 namespace sop {
 
-constexpr int kNeigh = 32;
-constexpr int kNFreq = 16;
-constexpr int kFP = kNeigh * 10 + 6 * kNFreq;  // 416
+constexpr int kIn = 18;       // features per texel
+constexpr int kInPad = 32;    // padded to two mma k-steps
 constexpr int kHid = 64;
 constexpr int kOut = 5;
+constexpr int kNearCap = 256;     // near field: Gaussians per probe at most
+constexpr int kCandCap = 4096;    // candidates sorted per probe
+constexpr int kFarCells = 128;    // far field: cells along the longest axis
+constexpr float kTauMax = 20.f;   // the far march stops beyond this depth
 // flat parameter blocks (row-major, out x in)
-constexpr int oW1p = 0, oW1d = oW1p + kHid * kFP, ob1 = oW1d + kHid * 3, oW2 = ob1 + kHid, ob2 = oW2 + kHid * kHid,
-              oW3 = ob2 + kHid, ob3 = oW3 + kHid * kHid, oW4 = ob3 + kHid, ob4 = oW4 + kOut * kHid,
-              kNParam = ob4 + kOut;
+constexpr int oW1 = 0, ob1 = oW1 + kHid * kIn, oW2 = ob1 + kHid, ob2 = oW2 + kHid * kHid, oW3 = ob2 + kHid,
+              ob3 = oW3 + kHid * kHid, oW4 = ob3 + kHid, ob4 = oW4 + kOut * kHid, kNParam = ob4 + kOut;
 
 // Caller-owned state: master weights, Adam moments, gradient accumulator,
 // bf16 copy of the parameters (biases included, unused as bf16), step.
@@ -51,6 +64,8 @@ SurrState surr_state_layout()
 }
 int surr_n_params() { return kNParam; }
 size_t surr_state_bytes() { return surr_state_layout().total; }
+int surr_n_features() { return kIn; }
+int surr_near_cap() { return kNearCap; }
 
 __device__ __forceinline__ uint16_t f2bf(float x)
 {
@@ -58,21 +73,23 @@ __device__ __forceinline__ uint16_t f2bf(float x)
     return *reinterpret_cast<uint16_t*>(&b);
 }
 __device__ __forceinline__ float bf2f(uint16_t u) { return __uint_as_float((uint32_t)u << 16); }
-__device__ __forceinline__ float rbf(float x) { return bf2f(f2bf(x)); }
 
-// bf16 copy of the master weights
+// ---------------------------------------------------------------------------
+// state: bf16 copy, Adam, step
+// ---------------------------------------------------------------------------
 __global__ void surr_to_bf16_kernel(const float* __restrict__ master, uint16_t* __restrict__ wbf)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < kNParam) wbf[i] = f2bf(master[i]);
 }
 
-__global__ void surr_reset_kernel(float* m, float* v, int32_t* step)
+__global__ void surr_reset_kernel(float* m, float* v, float* grad, int32_t* step)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < kNParam) {
         m[i] = 0.f;
         v[i] = 0.f;
+        grad[i] = 0.f;
     }
     if (i == 0) step[0] = 0;
 }
@@ -98,63 +115,435 @@ __global__ void surr_adam_kernel(float* __restrict__ master, float* __restrict__
 
 __global__ void surr_step_kernel(int32_t* step) { step[0] += 1; }
 
-// Probe features from the 32 nearest Gaussians (idx [P,32], nearest first).
-__global__ void surr_features_kernel(sop_gaussians g, const float* __restrict__ probe_pos, int32_t P,
-                                     const int32_t* __restrict__ idx, float* __restrict__ feats)
+__global__ void zero_f32_kernel(float* p, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)P * kFP) return;
-    const int64_t p = i / kFP;
-    const int f = (int)(i % kFP);
-    // computed in double and rounded once, so that the bf16 rounding the
-    // network applies to each feature sees the correctly rounded value
-    const double pp[3] = {probe_pos[3 * p], probe_pos[3 * p + 1], probe_pos[3 * p + 2]};
-    double v;
-    if (f < kNeigh * 10) {
-        const int j = f / 10, c = f % 10;
-        const int64_t gi = idx[p * kNeigh + j];
-        if (c < 3) v = ((double)g.mean[3 * gi + c] - pp[c]) * 10.0;
-        else if (c < 6) v = log((double)g.scale[3 * gi + c - 3]) + 5.0;
-        else if (c == 6) v = g.opacity[gi];
-        else v = g.rgb[3 * gi + c - 7];
-    } else {
-        const int e = f - kNeigh * 10, ax = e / 32, r = e % 32, fr = r % 16;
-        const double arg = pp[ax] * (3.14159265358979323846 * exp2((double)fr / 3.0));
-        v = r < 16 ? sin(arg) : cos(arg);
-    }
-    feats[i] = (float)v;
+    if (i < n) p[i] = 0.f;
 }
 
-// h1p[b] = W1p bf16(f_{pid[b]}) + b1, one thread per (probe, output).
-__global__ void surr_l1_fwd_kernel(const float* __restrict__ feats, const int32_t* __restrict__ pid, int32_t B,
-                                   const uint16_t* __restrict__ wbf, const float* __restrict__ master,
-                                   float* __restrict__ h1p)
+// splitmix64 (Steele, Lea & Flood 2014): the counter-based generator of the
+// training batches and of the spot-check sample
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)B * kHid) return;
-    const int64_t b = i / kHid;
-    const int o = (int)(i % kHid);
-    const int64_t p = pid ? pid[b] : b;
-    const float* f = feats + p * kFP;
-    const uint16_t* w = wbf + oW1p + o * kFP;
-    float acc = 0.f;
-    for (int k = 0; k < kFP; ++k) acc = fmaf(bf2f(w[k]), rbf(f[k]), acc);
-    h1p[i] = acc + master[ob1 + o];
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
 }
 
-// dW1p[o][k] += sum_b dh1p[b][o] bf16(f_{pid[b]})[k], db1 via the texel kernel.
-__global__ void surr_l1_bwd_kernel(const float* __restrict__ feats, const int32_t* __restrict__ pid, int32_t B,
-                                   const float* __restrict__ dh1p, float* __restrict__ grad)
+// He-uniform initial weights (bound sqrt(6 / fan_in)), zero biases, from the
+// counter-based generator (weight i draws splitmix64(seed + i))
+__global__ void surr_init_kernel(float* __restrict__ master, uint64_t seed)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kHid * kFP) return;
-    const int o = i / kFP, k = i % kFP;
-    float acc = 0.f;
-    for (int b = 0; b < B; ++b) {
-        const int64_t p = pid ? pid[b] : b;
-        acc = fmaf(dh1p[(int64_t)b * kHid + o], rbf(feats[p * kFP + k]), acc);
+    if (i >= kNParam) return;
+    int fan = 0;
+    if (i < ob1) fan = kIn;
+    else if ((i >= oW2 && i < ob2) || (i >= oW3 && i < ob3) || (i >= oW4 && i < ob4)) fan = kHid;
+    if (fan == 0) {
+        master[i] = 0.f;
+        return;
     }
-    grad[oW1p + i] += acc;
+    const double u = (double)(splitmix64(seed + (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+    master[i] = (float)((2.0 * u - 1.0) * sqrt(6.0 / fan));
+}
+
+// ---------------------------------------------------------------------------
+// Near field. One CTA per probe: the centres within r_n (integer keys) are
+// gathered from the site grid into shared memory, sorted by (key, index)
+// (bitonic), the first kNearCap kept; their bake records are staged in
+// shared memory and each thread composites them along its texels' rays.
+// ---------------------------------------------------------------------------
+struct NearK {
+    const float* probe_pos;
+    int32_t P, R;
+    const ProbeGrid* grid;
+    const int32_t* cell_start;
+    const int4* ent;
+    uint64_t r2key;       // floor((r_n 2^20)^2)
+    int32_t r_q;          // ceil(r_n 2^20)
+    float r_n;
+    const float4* rec;    // the bake's Gaussian records, 5 float4 each
+    const float4* tdirs;  // [R*R] texel directions
+    float alpha_min, alpha_max;
+    float* feats;         // [P][R*R][kIn]
+    int32_t* list;        // [P][kNearCap] or NULL
+    float* t0;            // [P]
+    unsigned int* status;
+};
+
+__device__ __forceinline__ int32_t quantise_s(float v) { return __float2int_rn(v * 1048576.0f); }
+__device__ __forceinline__ int64_t floordiv_s(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+__device__ __forceinline__ void two_diff_s(float a, float b, float& hi, float& lo)
+{
+    hi = a - b;
+    const float bv = a - hi;
+    const float av = hi + bv;
+    lo = (a - av) + (bv - b);
+}
+
+constexpr int kNearThreads = 256;
+
+__global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* ckey = reinterpret_cast<uint64_t*>(smem);                 // [kCandCap]
+    int32_t* cidx = reinterpret_cast<int32_t*>(ckey + kCandCap);          // [kCandCap]
+    float4* srec = reinterpret_cast<float4*>(smem);                       // [kNearCap][5], after the sort
+    __shared__ int32_t s_count, s_box[6];
+    __shared__ int32_t s_list[kNearCap];
+    const int tid = threadIdx.x, p = blockIdx.x;
+    const float3 pp = load3(k.probe_pos, p);
+    const int32_t q[3] = {quantise_s(pp.x), quantise_s(pp.y), quantise_s(pp.z)};
+    const ProbeGrid G = *k.grid;
+    if (tid == 0) {
+        s_count = 0;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t lo = floordiv_s((int64_t)q[a] - k.r_q - G.qmin[a], G.cs);
+            const int64_t hi = floordiv_s((int64_t)q[a] + k.r_q - G.qmin[a], G.cs);
+            s_box[a] = (int)(lo < 0 ? 0 : (lo > G.dims[a] - 1 ? G.dims[a] - 1 : lo));
+            s_box[3 + a] = (int)(hi < 0 ? -1 : (hi > G.dims[a] - 1 ? G.dims[a] - 1 : hi));
+        }
+    }
+    __syncthreads();
+    // gather: each warp takes cells of the box in turn, its lanes the entries
+    const int nx = s_box[3] - s_box[0] + 1, ny = s_box[4] - s_box[1] + 1, nz = s_box[5] - s_box[2] + 1;
+    const int ncell = (nx > 0 && ny > 0 && nz > 0) ? nx * ny * nz : 0;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int c = warp; c < ncell; c += kNearThreads / 32) {
+        const int cx = s_box[0] + c % nx, cy = s_box[1] + (c / nx) % ny, cz = s_box[2] + c / (nx * ny);
+        const int cell = (cz * G.dims[1] + cy) * G.dims[0] + cx;
+        const int e1 = __ldg(k.cell_start + cell + 1);
+        for (int e = __ldg(k.cell_start + cell) + lane; e < e1; e += 32) {
+            const int4 en = __ldg(k.ent + e);
+            const uint32_t dx = (uint32_t)abs(en.x - q[0]), dy = (uint32_t)abs(en.y - q[1]),
+                           dz = (uint32_t)abs(en.z - q[2]);
+            const uint64_t key = (uint64_t)dx * dx + (uint64_t)dy * dy + (uint64_t)dz * dz;
+            if (key <= k.r2key) {
+                const int pos = atomicAdd(&s_count, 1);
+                if (pos < kCandCap) {
+                    ckey[pos] = key;
+                    cidx[pos] = en.w;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int total = s_count;
+    const int n = total < kCandCap ? total : kCandCap;
+    if (total > kCandCap && tid == 0 && k.status) atomicOr(k.status, SOP_DEVSTAT_CAPACITY);
+    // bitonic sort of the candidates by (key, index), padded to a power of two
+    int n2 = 32;
+    while (n2 < n) n2 <<= 1;
+    for (int i = n + tid; i < n2; i += kNearThreads) {
+        ckey[i] = UINT64_MAX;
+        cidx[i] = INT32_MAX;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= n2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < n2; i += kNearThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = ckey[i], b = ckey[ixj];
+                    const int32_t ia = cidx[i], ib = cidx[ixj];
+                    const bool gt = a > b || (a == b && ia > ib);
+                    if (gt == ((i & kk) == 0)) {
+                        ckey[i] = b;
+                        ckey[ixj] = a;
+                        cidx[i] = ib;
+                        cidx[ixj] = ia;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int nl = n < kNearCap ? n : kNearCap;
+    for (int i = tid; i < kNearCap; i += kNearThreads) {
+        const int32_t g = i < nl ? cidx[i] : -1;
+        s_list[i] = g;
+        if (k.list) k.list[(int64_t)p * kNearCap + i] = g;
+    }
+    if (tid == 0) {
+        // one square root per probe, in double, so that the far field's
+        // start is the correctly rounded distance
+        k.t0[p] = nl == kNearCap ? (float)(sqrt((double)ckey[kNearCap - 1]) * (1.0 / 1048576.0)) : k.r_n;
+    }
+    __syncthreads();
+    // stage the listed Gaussians' records (over the candidate buffer)
+    for (int i = tid; i < nl * 5; i += kNearThreads) srec[i] = __ldg(k.rec + (int64_t)s_list[i / 5] * 5 + i % 5);
+    __syncthreads();
+    const int RR = k.R * k.R;
+    for (int t = tid; t < RR; t += kNearThreads) {
+        const float4 d4 = __ldg(k.tdirs + t);
+        const float3 d = f3(d4.x, d4.y, d4.z);
+        float T = 1.f, L0 = 0.f, L1 = 0.f, L2 = 0.f, W = 0.f, Dacc = 0.f;
+        for (int j = 0; j < nl; ++j) {
+            const float4 r0 = srec[5 * j], r1 = srec[5 * j + 1], r2 = srec[5 * j + 2], r3 = srec[5 * j + 3];
+            float hx, lx, hy, ly, hz, lz;
+            two_diff_s(pp.x, r0.x, hx, lx);
+            two_diff_s(pp.y, r0.y, hy, ly);
+            two_diff_s(pp.z, r0.z, hz, lz);
+            const float u0 = fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz));
+            const float u1 = fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz));
+            const float u2 = fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz));
+            const float w0 = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
+            const float w1 = fmaf(r1.w, d.x, fmaf(r2.x, d.y, r2.y * d.z));
+            const float w2 = fmaf(r2.z, d.x, fmaf(r2.w, d.y, r3.x * d.z));
+            const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
+            const float B = fmaf(w0, u0, fmaf(w1, u1, w2 * u2));
+            const float ts = -B / A;
+            if (!(ts > 0.f)) continue;
+            const float ex = fmaf(ts, d.x, hx) + lx, ey = fmaf(ts, d.y, hy) + ly, ez = fmaf(ts, d.z, hz) + lz;
+            const float v0 = fmaf(r1.x, ex, fmaf(r1.y, ey, r1.z * ez));
+            const float v1 = fmaf(r1.w, ex, fmaf(r2.x, ey, r2.y * ez));
+            const float v2 = fmaf(r2.z, ex, fmaf(r2.w, ey, r3.x * ez));
+            const float resp = r3.y * expf(-0.5f * fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+            if (resp < k.alpha_min) continue;
+            const float al = fminf(resp, k.alpha_max);
+            const float w = T * al;
+            const float4 r4 = srec[5 * j + 4];
+            L0 = fmaf(w, r3.z, L0);
+            L1 = fmaf(w, r3.w, L1);
+            L2 = fmaf(w, r4.x, L2);
+            W += w;
+            Dacc = fmaf(w, ts, Dacc);
+            T *= 1.f - al;
+        }
+        float* f = k.feats + ((int64_t)p * RR + t) * kIn;
+        f[0] = d.x;
+        f[1] = d.y;
+        f[2] = d.z;
+        f[3] = 1.f - T;
+        f[4] = L0;
+        f[5] = L1;
+        f[6] = L2;
+        f[7] = W > 1e-8f ? Dacc / W : 0.f;
+        f[8] = W;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Far field: grid geometry, fixed-point splat, per-cell (sigma, colour),
+// and the DDA march of every texel ray.
+// ---------------------------------------------------------------------------
+struct FarGrid {
+    int32_t qlo[3];
+    int32_t hq;
+    int32_t dims[3];
+    int32_t ncells;
+    float lo[3];
+    float h;
+};
+
+__global__ void far_bbox_init_kernel(int32_t* mm)
+{
+    if (threadIdx.x < 3) mm[threadIdx.x] = INT32_MAX;
+    else if (threadIdx.x < 6) mm[threadIdx.x] = INT32_MIN;
+}
+
+__device__ __forceinline__ bool far_massive(const sop_gaussians& g, int64_t i, float alpha_min)
+{
+    const float o = g.opacity[i];
+    return o >= alpha_min && isfinite(g.mean[3 * i] + g.mean[3 * i + 1] + g.mean[3 * i + 2]);
+}
+
+__global__ void far_bbox_kernel(sop_gaussians g, float alpha_min, int32_t* mm)
+{
+    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!far_massive(g, i, alpha_min)) continue;
+        for (int a = 0; a < 3; ++a) {
+            const int32_t qv = quantise_s(g.mean[3 * i + a]);
+            lo[a] = min(lo[a], qv);
+            hi[a] = max(hi[a], qv);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&mm[a], lo[a]);
+            atomicMax(&mm[3 + a], hi[a]);
+        }
+    }
+}
+
+__global__ void far_setup_kernel(const int32_t* mm, FarGrid* fg)
+{
+    if (threadIdx.x != 0) return;
+    FarGrid F;
+    if (mm[0] > mm[3]) {  // nothing carries mass
+        for (int a = 0; a < 3; ++a) {
+            F.qlo[a] = 0;
+            F.dims[a] = 1;
+            F.lo[a] = 0.f;
+        }
+        F.hq = 1;
+        F.ncells = 1;
+        F.h = 1.f / 1048576.f;
+        *fg = F;
+        return;
+    }
+    int64_t ext = 0;
+    for (int a = 0; a < 3; ++a) ext = max(ext, (int64_t)mm[3 + a] - mm[a] + 1);
+    const int64_t hq = (ext + kFarCells - 1) / kFarCells;
+    int32_t nc = 1;
+    for (int a = 0; a < 3; ++a) {
+        F.qlo[a] = mm[a];
+        F.dims[a] = (int32_t)(((int64_t)mm[3 + a] - mm[a]) / hq + 1);
+        nc *= F.dims[a];
+        F.lo[a] = (float)((double)mm[a] * (1.0 / 1048576.0));
+    }
+    F.hq = (int32_t)hq;
+    F.ncells = nc;
+    F.h = (float)((double)hq * (1.0 / 1048576.0));
+    *fg = F;
+}
+
+__global__ void far_zero_kernel(const FarGrid* fg, unsigned long long* __restrict__ acc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 4 * (int64_t)fg->ncells) acc[i] = 0ull;
+}
+
+// acc [cells][4]: mass and mass x rgb in units of 2^-40 (two's complement)
+__global__ void far_splat_kernel(sop_gaussians g, float alpha_min, float alpha_max, const FarGrid* fg,
+                                 unsigned long long* __restrict__ acc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n || !far_massive(g, i, alpha_min)) return;
+    const FarGrid F = *fg;
+    const float s0 = g.scale[3 * i], s1 = g.scale[3 * i + 1], s2 = g.scale[3 * i + 2];
+    const float prod2 = s0 * s1 * s2 / fminf(s0, fminf(s1, s2));
+    const float mass = -log1pf(-fminf(g.opacity[i], alpha_max)) * 6.283185307179586f * prod2;
+    if (!isfinite(mass)) return;
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = (quantise_s(g.mean[3 * i + a]) - F.qlo[a]) / F.hq;
+    const int64_t cell = ((int64_t)c[2] * F.dims[1] + c[1]) * F.dims[0] + c[0];
+    const float fix = 1099511627776.f;  // 2^40
+    atomicAdd(acc + 4 * cell, (unsigned long long)__float2ll_rn(mass * fix));
+    for (int k = 0; k < 3; ++k)
+        atomicAdd(acc + 4 * cell + 1 + k, (unsigned long long)__float2ll_rn(mass * g.rgb[3 * i + k] * fix));
+}
+
+// per cell: (sigma = mass / h^3, mass-weighted colour)
+__global__ void far_cells_kernel(const FarGrid* fg, const unsigned long long* __restrict__ acc,
+                                 float4* __restrict__ cells)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const FarGrid F = *fg;
+    if (i >= F.ncells) return;
+    const double m = (double)(long long)acc[4 * i];
+    const double inv_fix = 1.0 / 1099511627776.0;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m > 0.0) {
+        const double h = (double)F.hq * (1.0 / 1048576.0);
+        v.x = (float)(m * inv_fix / (h * h * h));
+        v.y = (float)((double)(long long)acc[4 * i + 1] / m);
+        v.z = (float)((double)(long long)acc[4 * i + 2] / m);
+        v.w = (float)((double)(long long)acc[4 * i + 3] / m);
+    }
+    cells[i] = v;
+}
+
+// one thread per texel ray
+__global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict__ probe_pos, int32_t P, int32_t R,
+                                                        const float* __restrict__ t0p, const float4* __restrict__ tdirs,
+                                                        const FarGrid* __restrict__ fg,
+                                                        const float4* __restrict__ cells, float* __restrict__ feats)
+{
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int RR = R * R;
+    if (id >= (int64_t)P * RR) return;
+    const int p = (int)(id / RR), t = (int)(id % RR);
+    const FarGrid F = *fg;
+    const float3 o = load3(probe_pos, p);
+    const float4 d4 = __ldg(tdirs + t);
+    const float d[3] = {d4.x, d4.y, d4.z}, oo[3] = {o.x, o.y, o.z};
+    const float t0 = __ldg(t0p + p);
+    const float h = F.h;
+    float ck[5];
+    ck[0] = fmaf(2.f, h, t0);
+    ck[1] = fmaf(4.f, h, t0);
+    ck[2] = fmaf(8.f, h, t0);
+    ck[3] = fmaf(16.f, h, t0);
+    ck[4] = fmaf(32.f, h, t0);
+    float tau_ck[5];
+    int next = 0;
+    float tau = 0.f, L0 = 0.f, L1 = 0.f, L2 = 0.f;
+    float ta = t0, tb = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        const float lo = F.lo[a], hi = F.lo[a] + F.dims[a] * h;
+        if (d[a] != 0.f) {
+            float t1 = (lo - oo[a]) / d[a], t2 = (hi - oo[a]) / d[a];
+            if (t1 > t2) {
+                const float tmp = t1;
+                t1 = t2;
+                t2 = tmp;
+            }
+            ta = fmaxf(ta, t1);
+            tb = fminf(tb, t2);
+        } else if (oo[a] < lo || oo[a] >= hi) {
+            tb = -INFINITY;
+        }
+    }
+    if (ta < tb) {
+        int c[3], st[3];
+        float tn[3];
+        for (int a = 0; a < 3; ++a) {
+            const int ci = (int)floorf((fmaf(ta, d[a], oo[a]) - F.lo[a]) / h);
+            c[a] = ci < 0 ? 0 : (ci >= F.dims[a] ? F.dims[a] - 1 : ci);
+            st[a] = d[a] > 0.f ? 1 : (d[a] < 0.f ? -1 : 0);
+            tn[a] = st[a] == 0 ? INFINITY : (F.lo[a] + (c[a] + (st[a] > 0 ? 1 : 0)) * h - oo[a]) / d[a];
+        }
+        float tc = ta;
+        // at most one step per cell along each axis: bounded by the dims
+        const int max_steps = F.dims[0] + F.dims[1] + F.dims[2] + 3;
+        for (int it = 0; it < max_steps && tc < tb && tau <= kTauMax; ++it) {
+            const int ax = (tn[0] <= tn[1] && tn[0] <= tn[2]) ? 0 : (tn[1] <= tn[2] ? 1 : 2);
+            float te = fminf(tn[ax], tb);
+            te = fmaxf(te, tc);
+            const float4 cv = __ldg(cells + ((int64_t)c[2] * F.dims[1] + c[1]) * F.dims[0] + c[0]);
+            while (next < 5 && ck[next] < te) {
+                tau_ck[next] = ck[next] <= tc ? tau : fmaf(cv.x, ck[next] - tc, tau);
+                ++next;
+            }
+            if (cv.x > 0.f) {
+                const float dtau = cv.x * (te - tc);
+                const float a = __expf(-tau) * -expm1f(-dtau);
+                L0 = fmaf(a, cv.y, L0);
+                L1 = fmaf(a, cv.z, L1);
+                L2 = fmaf(a, cv.w, L2);
+                tau += dtau;
+            }
+            tc = te;
+            if (!(te < tb)) break;
+            c[ax] += st[ax];
+            if (c[ax] < 0 || c[ax] >= F.dims[ax]) break;
+            tn[ax] = (F.lo[ax] + (c[ax] + (st[ax] > 0 ? 1 : 0)) * h - oo[ax]) / d[ax];
+        }
+    }
+    while (next < 5) tau_ck[next++] = tau;
+    float* f = feats + id * kIn + 9;
+    for (int k = 0; k < 5; ++k) f[k] = -expm1f(-tau_ck[k]);
+    f[5] = -expm1f(-tau);
+    f[6] = L0;
+    f[7] = L1;
+    f[8] = L2;
+}
+
+__global__ void surr_tdirs_kernel(int R, float4* __restrict__ dirs)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= R * R) return;
+    double d[3];
+    oct_decode_centre_f64(R, t % R, t / R, d);
+    dirs[t] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -174,11 +563,13 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
 __device__ __forceinline__ uint32_t pk(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
 __device__ __forceinline__ uint32_t ld2(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
-constexpr int kLD = 72;    // row stride of bf16 tiles in shared memory
+constexpr int kLD = 72;    // row stride of 64-wide bf16 tiles in shared memory
+constexpr int kLDX = 40;   // row stride of the 32-wide (padded) feature tile
 constexpr int kCH = 128;   // samples per chunk (8 warps x 16 rows)
 
-// out[16 rows of this warp] = act(in[rows] W^T + b): W is [64 out][kLD] bf16.
-template <bool RELU_BF16>
+// out[16 rows of this warp] = relu(in[rows] W^T + b) in bf16: in is
+// [kCH][LDI] with KD columns, W is [64 out][LDW] with KD columns.
+template <int KD, int LDI, int LDW>
 __device__ __forceinline__ void layer_fwd(const uint16_t* in, const uint16_t* W, const float* bias, uint16_t* out,
                                           int row0, int lane)
 {
@@ -187,11 +578,11 @@ __device__ __forceinline__ void layer_fwd(const uint16_t* in, const uint16_t* W,
     for (int nt = 0; nt < 8; ++nt) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k0 = 0; k0 < kHid; k0 += 16) {
-            const uint32_t a[4] = {ld2(in + (row0 + g) * kLD + k0 + 2 * t), ld2(in + (row0 + g + 8) * kLD + k0 + 2 * t),
-                                   ld2(in + (row0 + g) * kLD + k0 + 8 + 2 * t),
-                                   ld2(in + (row0 + g + 8) * kLD + k0 + 8 + 2 * t)};
-            const uint32_t b[2] = {ld2(W + (nt * 8 + g) * kLD + k0 + 2 * t), ld2(W + (nt * 8 + g) * kLD + k0 + 8 + 2 * t)};
+        for (int k0 = 0; k0 < KD; k0 += 16) {
+            const uint32_t a[4] = {ld2(in + (row0 + g) * LDI + k0 + 2 * t), ld2(in + (row0 + g + 8) * LDI + k0 + 2 * t),
+                                   ld2(in + (row0 + g) * LDI + k0 + 8 + 2 * t),
+                                   ld2(in + (row0 + g + 8) * LDI + k0 + 8 + 2 * t)};
+            const uint32_t b[2] = {ld2(W + (nt * 8 + g) * LDW + k0 + 2 * t), ld2(W + (nt * 8 + g) * LDW + k0 + 8 + 2 * t)};
             mma_bf16(c, a, b);
         }
         const int col = nt * 8 + 2 * t;
@@ -203,9 +594,12 @@ __device__ __forceinline__ void layer_fwd(const uint16_t* in, const uint16_t* W,
     }
 }
 
-// acc[4 n-tiles][4] += D^T H over the chunk's rows: dW[m][n] = sum_s D[s][m] H[s][n]
-// for the m-tile mt and n-tiles nt0..nt0+3 (D and H are [kCH][kLD] bf16).
-__device__ __forceinline__ void wgrad(const uint16_t* D, const uint16_t* H, int mt, int nt0, float acc[4][4], int lane)
+// acc[NT n-tiles][4] += D^T H over the chunk's rows: dW[m][n] = sum_s D[s][m]
+// H[s][n], for the m-tile mt and n-tiles nt0..nt0+NT-1 (D is [kCH][kLD], H
+// is [kCH][LDH]).
+template <int NT, int LDH>
+__device__ __forceinline__ void wgrad(const uint16_t* D, const uint16_t* H, int mt, int nt0, float acc[][4],
+                                      int lane)
 {
     const int g = lane >> 2, t = lane & 3, m0 = mt * 16;
 #pragma unroll
@@ -216,16 +610,16 @@ __device__ __forceinline__ void wgrad(const uint16_t* D, const uint16_t* H, int 
                                pk(D[kb * kLD + m0 + g], D[(kb + 1) * kLD + m0 + g]),
                                pk(D[kb * kLD + m0 + g + 8], D[(kb + 1) * kLD + m0 + g + 8])};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < NT; ++j) {
             const int n = (nt0 + j) * 8 + g;
-            const uint32_t b[2] = {pk(H[ka * kLD + n], H[(ka + 1) * kLD + n]), pk(H[kb * kLD + n], H[(kb + 1) * kLD + n])};
+            const uint32_t b[2] = {pk(H[ka * LDH + n], H[(ka + 1) * LDH + n]), pk(H[kb * LDH + n], H[(kb + 1) * LDH + n])};
             mma_bf16(acc[j], a, b);
         }
     }
 }
 
-// c[nt][4] = D[rows] W (back-propagation of deltas through a layer whose
-// weights are W [out][in]: result[s][i] = sum_j D[s][j] W[j][i]).
+// c[nt][4] = D[rows] W (back-propagation of deltas through a 64x64 layer
+// whose weights are W [out][in]: result[s][i] = sum_j D[s][j] W[j][i]).
 __device__ __forceinline__ void delta_bwd(const uint16_t* D, const uint16_t* W, int row0, float c[8][4], int lane)
 {
     const int g = lane >> 2, t = lane & 3;
@@ -246,108 +640,158 @@ __device__ __forceinline__ void delta_bwd(const uint16_t* D, const uint16_t* W, 
     }
 }
 
+// the next layer's delta, bf16((c) * (activation > 0)), written over `out`
+__device__ __forceinline__ void store_delta(float c[8][4], const uint16_t* act, uint16_t* out, int row0, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int col = nt * 8 + 2 * t;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = row0 + g + (q >= 2 ? 8 : 0), cc = col + (q & 1);
+            out[r * kLD + cc] = f2bf(bf2f(act[r * kLD + cc]) > 0.f ? c[nt][q] : 0.f);
+        }
+    }
+}
+
 struct MlpK {
-    const float* h1p;         // [B][64]
-    const int32_t* pid;       // [B] atlas probe of each batch entry (NULL: identity)
-    int32_t B, R;
-    const float4* tdirs;      // [R*R] texel directions
+    const float* feats;       // [probes][R*R][kIn]
+    const int32_t* pid;       // [B] probe of each batch entry (NULL: identity)
+    int32_t B, R, P;
     const uint16_t* wbf;      // bf16 parameters
     const float* master;      // f32 parameters (biases)
     // targets (train) or outputs (infer): an atlas
     void* rgbo;
     void* depth;
     int32_t rgbo_dtype, depth_dtype;
+    float inv_depth_scale;    // infer: D/depth_scale is what the net predicts (written as is)
     float inv_count;          // 1 / (samples * 5) for the mean absolute error
-    float* grad;              // train: gradient accumulator
-    float* dh1p;              // train: [B][64]
-    float* loss;              // train: sum of |y - target|
+    float* grad_part;         // train: [gridDim][kNParam] this CTA's gradient sums
+    float* loss_part;         // train: [gridDim] this CTA's sum of |y - target|
+    unsigned int* status;
 };
+
+__device__ __forceinline__ float depth_at(const void* depth, int dt, int64_t ti)
+{
+    switch (dt) {
+    case SOP_F32: return reinterpret_cast<const float*>(depth)[ti];
+    case SOP_F16: return __half2float(reinterpret_cast<const __half*>(depth)[ti]);
+    case SOP_BF16: return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(depth)[ti]);
+    default: return float(reinterpret_cast<const __nv_fp8_e4m3*>(depth)[ti]);
+    }
+}
+
+__device__ __forceinline__ void depth_put(void* depth, int dt, int64_t ti, float v)
+{
+    switch (dt) {
+    case SOP_F32: reinterpret_cast<float*>(depth)[ti] = v; break;
+    case SOP_F16: reinterpret_cast<__half*>(depth)[ti] = __float2half_rn(v); break;
+    case SOP_BF16: reinterpret_cast<__nv_bfloat16*>(depth)[ti] = __float2bfloat16_rn(v); break;
+    default: reinterpret_cast<__nv_fp8_e4m3*>(depth)[ti] = __nv_fp8_e4m3(v); break;
+    }
+}
+
+__device__ __forceinline__ float4 texel_load(const void* rgbo, int dt, int64_t ti)
+{
+    if (dt == SOP_F32) return reinterpret_cast<const float4*>(rgbo)[ti];
+    if (dt == SOP_BF16) return Texel<SOP_BF16>::load(reinterpret_cast<const uint2*>(rgbo) + ti);
+    return Texel<SOP_F16>::load(reinterpret_cast<const uint2*>(rgbo) + ti);
+}
+
+__device__ __forceinline__ void texel_store(void* rgbo, int dt, int64_t ti, float4 v)
+{
+    if (dt == SOP_F32) reinterpret_cast<float4*>(rgbo)[ti] = v;
+    else if (dt == SOP_BF16) reinterpret_cast<uint2*>(rgbo)[ti] = Texel<SOP_BF16>::pack(v);
+    else reinterpret_cast<uint2*>(rgbo)[ti] = Texel<SOP_F16>::pack(v);
+}
 
 template <bool TRAIN>
 __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint16_t* sW2 = reinterpret_cast<uint16_t*>(smem);
+    uint16_t* sW1 = reinterpret_cast<uint16_t*>(smem);  // [64][kLDX]
+    uint16_t* sW2 = sW1 + kHid * kLDX;                  // [64][kLD]
     uint16_t* sW3 = sW2 + kHid * kLD;
-    uint16_t* sH1 = sW3 + kHid * kLD;
+    uint16_t* sX = sW3 + kHid * kLD;                    // [kCH][kLDX]
+    uint16_t* sH1 = sX + kCH * kLDX;                    // [kCH][kLD]
     uint16_t* sH2 = sH1 + kCH * kLD;
-    uint16_t* sH3 = sH2 + kCH * kLD;  // later holds D2
-    uint16_t* sD3 = sH3 + kCH * kLD;
+    uint16_t* sH3 = sH2 + kCH * kLD;                    // later D2
+    uint16_t* sD3 = sH3 + kCH * kLD;                    // later D1
     float* fs = reinterpret_cast<float*>(sD3 + kCH * kLD);
     float* sW4 = fs;                  // [5][64]
-    float* sb2 = sW4 + kOut * kHid;   // [64]
-    float* sb3 = sb2 + kHid;          // [64]
+    float* sb1 = sW4 + kOut * kHid;   // [64]
+    float* sb2 = sb1 + kHid;
+    float* sb3 = sb2 + kHid;
     float* sb4 = sb3 + kHid;          // [8]
-    float* sW1d = sb4 + 8;            // [64][3]
-    float* sh1p = sW1d + kHid * 3;    // [64]
-    float* sG4 = sh1p + kHid;         // [kCH][5]
-    float* sDir = sG4 + kCH * kOut;   // [kCH][3] (bf16-rounded)
-    float* gW4 = sDir + kCH * 3;      // [5][64]
+    float* sG4 = sb4 + 8;             // [kCH][5]
+    float* gW4 = sG4 + kCH * kOut;    // [5][64]
     float* gb4 = gW4 + kOut * kHid;   // [8]
     float* gb3 = gb4 + 8;             // [64]
-    float* gb2 = gb3 + kHid;          // [64]
-    float* gW1d = gb2 + kHid;         // [64][3]
-    float* gb1 = gW1d + kHid * 3;     // [64]
-    float* sdh = gb1 + kHid;          // [64] per probe
+    float* gb2 = gb3 + kHid;
+    float* gb1 = gb2 + kHid;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+    for (int i = tid; i < kHid * kLDX; i += blockDim.x) {
+        const int r = i / kLDX, c = i % kLDX;
+        sW1[i] = c < kIn ? k.wbf[oW1 + r * kIn + c] : (uint16_t)0;
+    }
     for (int i = tid; i < kHid * kHid; i += blockDim.x) {
         const int r = i / kHid, c = i % kHid;
         sW2[r * kLD + c] = k.wbf[oW2 + i];
         sW3[r * kLD + c] = k.wbf[oW3 + i];
     }
-    for (int i = tid; i < kOut * kHid; i += blockDim.x) sW4[i] = bf2f(k.wbf[oW4 + i]);
+    for (int i = tid; i < kOut * kHid; i += blockDim.x) {
+        sW4[i] = bf2f(k.wbf[oW4 + i]);
+        if (TRAIN) gW4[i] = 0.f;
+    }
     for (int i = tid; i < kHid; i += blockDim.x) {
+        sb1[i] = k.master[ob1 + i];
         sb2[i] = k.master[ob2 + i];
         sb3[i] = k.master[ob3 + i];
-        for (int c = 0; c < 3; ++c) sW1d[3 * i + c] = bf2f(k.wbf[oW1d + 3 * i + c]);
-        if (TRAIN) gb3[i] = gb2[i] = gb1[i] = sdh[i] = 0.f, gW1d[3 * i] = gW1d[3 * i + 1] = gW1d[3 * i + 2] = 0.f;
+        if (TRAIN) gb1[i] = gb2[i] = gb3[i] = 0.f;
     }
     for (int i = tid; i < 8; i += blockDim.x) {
         sb4[i] = i < kOut ? k.master[ob4 + i] : 0.f;
         if (TRAIN) gb4[i] = 0.f;
     }
-    if (TRAIN)
-        for (int i = tid; i < kOut * kHid; i += blockDim.x) gW4[i] = 0.f;
-    float acc3[4][4], acc2[4][4];
+    // weight-gradient accumulators of layers 1-3 (tensor cores): m-tile
+    // warp & 3; n-tiles (warp >> 2) * 4 .. +3 of the 64-wide inputs, and
+    // (warp >> 2) * 2 .. +1 of the 32-wide (padded) features
+    float acc3[4][4], acc2[4][4], acc1[2][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc3[j][q] = acc2[j][q] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc1[j][q] = 0.f;
     float lsum = 0.f;
     const int RR = k.R * k.R, RS = k.R + 2;
-    const int row0 = warp * 16, mt = warp & 3, nt0 = (warp >> 2) * 4;
+    const int row0 = warp * 16, mt = warp & 3, nt0 = (warp >> 2) * 4, nx0 = (warp >> 2) * 2;
     __syncthreads();
 
     for (int b = blockIdx.x; b < k.B; b += gridDim.x) {
-        const int64_t p = k.pid ? k.pid[b] : b;
-        for (int i = tid; i < kHid; i += blockDim.x) sh1p[i] = k.h1p[(int64_t)b * kHid + i];
+        int64_t p = k.pid ? k.pid[b] : b;
+        if (p < 0 || p >= k.P) {
+            if (tid == 0 && k.status) atomicOr(k.status, SOP_DEVSTAT_INDEX);
+            continue;
+        }
         for (int s0 = 0; s0 < RR; s0 += kCH) {
             const int ns = min(kCH, RR - s0);
             __syncthreads();
-            for (int i = tid; i < kCH * 3; i += blockDim.x) {
-                const int s = i / 3, c = i % 3;
-                float v = 0.f;
-                if (s < ns) {
-                    const float4 d = k.tdirs[s0 + s];
-                    v = rbf(c == 0 ? d.x : (c == 1 ? d.y : d.z));
-                }
-                sDir[i] = v;
+            const float* fp = k.feats + ((int64_t)p * RR + s0) * kIn;
+            for (int i = tid; i < kCH * kLDX; i += blockDim.x) {
+                const int s = i / kLDX, c = i % kLDX;
+                sX[i] = (s < ns && c < kIn) ? f2bf(fp[s * kIn + c]) : (uint16_t)0;
             }
             __syncthreads();
-            // layer 1: h1 = relu(h1p + W1d d)
-            for (int i = tid; i < kCH * kHid; i += blockDim.x) {
-                const int s = i / kHid, o = i % kHid;
-                float z = 0.f;
-                if (s < ns)
-                    z = sh1p[o] + sW1d[3 * o] * sDir[3 * s] + sW1d[3 * o + 1] * sDir[3 * s + 1] +
-                        sW1d[3 * o + 2] * sDir[3 * s + 2];
-                sH1[s * kLD + o] = f2bf(fmaxf(z, 0.f));
-            }
-            __syncthreads();
-            layer_fwd<true>(sH1, sW2, sb2, sH2, row0, lane);
+            layer_fwd<kInPad, kLDX, kLDX>(sX, sW1, sb1, sH1, row0, lane);
             __syncwarp();
-            layer_fwd<true>(sH2, sW3, sb3, sH3, row0, lane);
+            layer_fwd<kHid, kLD, kLD>(sH1, sW2, sb2, sH2, row0, lane);
+            __syncwarp();
+            layer_fwd<kHid, kLD, kLD>(sH2, sW3, sb3, sH3, row0, lane);
             __syncthreads();
             // output layer (f32) and its loss gradient / the atlas write
             for (int i = tid; i < kCH * kOut; i += blockDim.x) {
@@ -361,22 +805,9 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
                     if (s < ns) {
                         float tg;
                         if (o == 1) {
-                            tg = 0.f;
-                            if (k.depth) {
-                                switch (k.depth_dtype) {
-                                case SOP_F32: tg = reinterpret_cast<const float*>(k.depth)[ti]; break;
-                                case SOP_F16: tg = __half2float(reinterpret_cast<const __half*>(k.depth)[ti]); break;
-                                case SOP_BF16:
-                                    tg = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(k.depth)[ti]);
-                                    break;
-                                default: tg = float(reinterpret_cast<const __nv_fp8_e4m3*>(k.depth)[ti]); break;
-                                }
-                            }
+                            tg = k.depth ? depth_at(k.depth, k.depth_dtype, ti) : 0.f;
                         } else {
-                            float4 v;
-                            if (k.rgbo_dtype == SOP_F32) v = reinterpret_cast<const float4*>(k.rgbo)[ti];
-                            else if (k.rgbo_dtype == SOP_BF16) v = Texel<SOP_BF16>::load(reinterpret_cast<const uint2*>(k.rgbo) + ti);
-                            else v = Texel<SOP_F16>::load(reinterpret_cast<const uint2*>(k.rgbo) + ti);
+                            const float4 v = texel_load(k.rgbo, k.rgbo_dtype, ti);
                             tg = o == 0 ? v.w : (o == 2 ? v.x : (o == 3 ? v.y : v.z));
                         }
                         const float df = y - tg;
@@ -385,17 +816,8 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
                     }
                     sG4[i] = g;
                 } else if (s < ns) {
-                    // write the prediction into the atlas interior
                     if (o == 1) {
-                        if (k.depth) {
-                            const float dv = fmaxf(y, 0.f);
-                            switch (k.depth_dtype) {
-                            case SOP_F32: reinterpret_cast<float*>(k.depth)[ti] = dv; break;
-                            case SOP_F16: reinterpret_cast<__half*>(k.depth)[ti] = __float2half_rn(dv); break;
-                            case SOP_BF16: reinterpret_cast<__nv_bfloat16*>(k.depth)[ti] = __float2bfloat16_rn(dv); break;
-                            default: reinterpret_cast<__nv_fp8_e4m3*>(k.depth)[ti] = __nv_fp8_e4m3(dv); break;
-                            }
-                        }
+                        if (k.depth) depth_put(k.depth, k.depth_dtype, ti, fmaxf(y, 0.f));
                     } else {
                         sG4[i] = o == 0 ? fminf(fmaxf(y, 0.f), 1.f) : fmaxf(y, 0.f);
                     }
@@ -406,14 +828,12 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
                 for (int s = tid; s < ns; s += blockDim.x) {
                     const int t = s0 + s;
                     const int64_t ti = p * RS * RS + (int64_t)(t / k.R + 1) * RS + (t % k.R + 1);
-                    const float4 v = make_float4(sG4[s * kOut + 2], sG4[s * kOut + 3], sG4[s * kOut + 4], sG4[s * kOut]);
-                    if (k.rgbo_dtype == SOP_F32) reinterpret_cast<float4*>(k.rgbo)[ti] = v;
-                    else if (k.rgbo_dtype == SOP_BF16) reinterpret_cast<uint2*>(k.rgbo)[ti] = Texel<SOP_BF16>::pack(v);
-                    else reinterpret_cast<uint2*>(k.rgbo)[ti] = Texel<SOP_F16>::pack(v);
+                    texel_store(k.rgbo, k.rgbo_dtype, ti,
+                                make_float4(sG4[s * kOut + 2], sG4[s * kOut + 3], sG4[s * kOut + 4], sG4[s * kOut]));
                 }
                 continue;
             }
-            // ---- backward (train) --------------------------------------------------
+            // ---- backward ----------------------------------------------------------
             // output layer: dW4 += G4^T H3, db4 += sum G4; D3 = bf16((G4 W4) * (h3 > 0))
             for (int i = tid; i < kOut * kHid; i += blockDim.x) {
                 const int o = i / kHid, j = i % kHid;
@@ -434,8 +854,8 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
                 sD3[s * kLD + j] = f2bf(bf2f(sH3[s * kLD + j]) > 0.f ? a : 0.f);
             }
             __syncthreads();
-            // layer 3: dW3 += D3^T H2 (tensor cores), db3; D2 = bf16((D3 W3) * (h2 > 0)) into sH3
-            wgrad(sD3, sH2, mt, nt0, acc3, lane);
+            // layer 3: dW3 += D3^T H2, db3; D2 = bf16((D3 W3) * (h2 > 0)) into sH3
+            wgrad<4, kLD>(sD3, sH2, mt, nt0, acc3, lane);
             if (tid < kHid) {
                 float a = 0.f;
                 for (int s = 0; s < ns; ++s) a += bf2f(sD3[s * kLD + tid]);
@@ -444,20 +864,11 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
             {
                 float c[8][4];
                 delta_bwd(sD3, sW3, row0, c, lane);
-                const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const int col = nt * 8 + 2 * t;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int r = row0 + g + (q >= 2 ? 8 : 0), cc = col + (q & 1);
-                        sH3[r * kLD + cc] = f2bf(bf2f(sH2[r * kLD + cc]) > 0.f ? c[nt][q] : 0.f);
-                    }
-                }
+                store_delta(c, sH2, sH3, row0, lane);
             }
             __syncthreads();
-            // layer 2: dW2 += D2^T H1, db2; D1 = (D2 W2) * (h1 > 0) in f32
-            wgrad(sH3, sH1, mt, nt0, acc2, lane);
+            // layer 2: dW2 += D2^T H1, db2; D1 = bf16((D2 W2) * (h1 > 0)) into sD3
+            wgrad<4, kLD>(sH3, sH1, mt, nt0, acc2, lane);
             if (tid < kHid) {
                 float a = 0.f;
                 for (int s = 0; s < ns; ++s) a += bf2f(sH3[s * kLD + tid]);
@@ -466,59 +877,25 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
             {
                 float c[8][4];
                 delta_bwd(sH3, sW2, row0, c, lane);
-                const int g = lane >> 2, t = lane & 3;
-                const int ra = row0 + g, rb = row0 + g + 8;
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const int col = nt * 8 + 2 * t;
-                    float v[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int r = q >= 2 ? rb : ra, cc = col + (q & 1);
-                        v[q] = bf2f(sH1[r * kLD + cc]) > 0.f ? c[nt][q] : 0.f;
-                    }
-                    // sums over this warp's 16 rows: d(h1p) and dW1d
-                    float s0 = v[0] + v[2], s1 = v[1] + v[3];
-                    float w0[3], w1[3];
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        w0[e] = v[0] * sDir[3 * ra + e] + v[2] * sDir[3 * rb + e];
-                        w1[e] = v[1] * sDir[3 * ra + e] + v[3] * sDir[3 * rb + e];
-                    }
-#pragma unroll
-                    for (int off = 4; off < 32; off <<= 1) {
-                        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-                        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-#pragma unroll
-                        for (int e = 0; e < 3; ++e) {
-                            w0[e] += __shfl_xor_sync(0xffffffffu, w0[e], off);
-                            w1[e] += __shfl_xor_sync(0xffffffffu, w1[e], off);
-                        }
-                    }
-                    if (g == 0) {
-                        atomicAdd(&sdh[col], s0);
-                        atomicAdd(&sdh[col + 1], s1);
-#pragma unroll
-                        for (int e = 0; e < 3; ++e) {
-                            atomicAdd(&gW1d[3 * col + e], w0[e]);
-                            atomicAdd(&gW1d[3 * (col + 1) + e], w1[e]);
-                        }
-                    }
-                }
+                // sD3 (D3) was last read before the barrier above
+                store_delta(c, sH1, sD3, row0, lane);
             }
-        }
-        if (TRAIN) {
             __syncthreads();
-            for (int i = tid; i < kHid; i += blockDim.x) {
-                k.dh1p[(int64_t)b * kHid + i] = sdh[i];
-                gb1[i] += sdh[i];
-                sdh[i] = 0.f;
+            // layer 1: dW1 += D1^T X (padded columns give zero), db1
+            wgrad<2, kLDX>(sD3, sX, mt, nx0, acc1, lane);
+            if (tid < kHid) {
+                float a = 0.f;
+                for (int s = 0; s < ns; ++s) a += bf2f(sD3[s * kLD + tid]);
+                gb1[tid] += a;
             }
         }
     }
     if (TRAIN) {
         __syncthreads();
-        // flush this CTA's gradient sums
+        // this CTA's gradient sums into its own slot (summed over the CTAs in
+        // a fixed order by surr_grad_reduce_kernel: training is bit-
+        // reproducible)
+        float* gp = k.grad_part + (int64_t)blockIdx.x * kNParam;
         const int g = lane >> 2, t = lane & 3, m0 = mt * 16;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -526,58 +903,185 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int m = m0 + g + (q >= 2 ? 8 : 0), nn = n + (q & 1);
-                atomicAdd(k.grad + oW3 + m * kHid + nn, acc3[j][q]);
-                atomicAdd(k.grad + oW2 + m * kHid + nn, acc2[j][q]);
+                gp[oW3 + m * kHid + nn] = acc3[j][q];
+                gp[oW2 + m * kHid + nn] = acc2[j][q];
             }
         }
-        for (int i = tid; i < kOut * kHid; i += blockDim.x) atomicAdd(k.grad + oW4 + i, gW4[i]);
-        for (int i = tid; i < kHid; i += blockDim.x) {
-            atomicAdd(k.grad + ob3 + i, gb3[i]);
-            atomicAdd(k.grad + ob2 + i, gb2[i]);
-            atomicAdd(k.grad + ob1 + i, gb1[i]);
-            for (int e = 0; e < 3; ++e) atomicAdd(k.grad + oW1d + 3 * i + e, gW1d[3 * i + e]);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int n = (nx0 + j) * 8 + 2 * t;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m = m0 + g + (q >= 2 ? 8 : 0), nn = n + (q & 1);
+                if (nn < kIn) gp[oW1 + m * kIn + nn] = acc1[j][q];
+            }
         }
-        if (tid < kOut) atomicAdd(k.grad + ob4 + tid, gb4[tid]);
+        for (int i = tid; i < kOut * kHid; i += blockDim.x) gp[oW4 + i] = gW4[i];
+        for (int i = tid; i < kHid; i += blockDim.x) {
+            gp[ob3 + i] = gb3[i];
+            gp[ob2 + i] = gb2[i];
+            gp[ob1 + i] = gb1[i];
+        }
+        if (tid < kOut) gp[ob4 + tid] = gb4[tid];
         for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
-        if (lane == 0) atomicAdd(k.loss, lsum);
+        __shared__ float s_loss[8];
+        if (lane == 0) s_loss[warp] = lsum;
+        __syncthreads();
+        if (tid == 0) {
+            float l = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) l += s_loss[w];
+            k.loss_part[blockIdx.x] = l;
+        }
+    }
+}
+
+// grad[i] = sum over the CTAs, in CTA order, of their partial sums; loss
+// likewise (thread 0)
+__global__ void surr_grad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ loss_part, int nb,
+                                        float* __restrict__ grad, float* __restrict__ loss)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kNParam) {
+        float a = 0.f;
+        for (int b = 0; b < nb; ++b) a += part[(int64_t)b * kNParam + i];
+        grad[i] = a;
+    }
+    if (i == 0) {
+        float l = 0.f;
+        for (int b = 0; b < nb; ++b) l += loss_part[b];
+        loss[0] = l;
     }
 }
 
 size_t surr_mlp_smem()
 {
-    return sizeof(uint16_t) * (2 * kHid * kLD + 4 * kCH * kLD) +
-           sizeof(float) * (kOut * kHid + kHid + kHid + 8 + kHid * 3 + kHid + kCH * kOut + kCH * 3 + kOut * kHid + 8 +
-                            kHid + kHid + kHid * 3 + kHid + kHid);
+    return sizeof(uint16_t) * (kHid * kLDX + 2 * kHid * kLD + kCH * kLDX + 4 * kCH * kLD) +
+           sizeof(float) * (kOut * kHid + 3 * kHid + 8 + kCH * kOut + kOut * kHid + 8 + 3 * kHid);
 }
 
-__global__ void surr_tdirs_kernel(int R, float4* __restrict__ dirs)
+// batch probe ids of a training step: id i = splitmix64(seed ^ (step 2^32
+// + i)) mod P (with replacement), step read from the state
+__global__ void surr_pick_kernel(uint64_t seed, const int32_t* step, int32_t P, int32_t B, int32_t* ids)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= R * R) return;
-    double d[3];
-    oct_decode_centre_f64(R, t % R, t / R, d);
-    dirs[t] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const uint64_t r = splitmix64(seed ^ (((uint64_t)(uint32_t)step[0] << 32) | (uint32_t)i));
+    ids[i] = (int32_t)(r % (uint64_t)P);
 }
 
-__global__ void zero_f32_kernel(float* p, int64_t n)
+__global__ void surr_loss_kernel(const float* sum, float scale, float* out) { out[0] = sum[0] * scale; }
+
+// ---------------------------------------------------------------------------
+// Atlas helpers for the spot-check: compare and copy whole probes.
+// ---------------------------------------------------------------------------
+// out[0] += sum |O_a - O_b|, out[1] += sum |RGB_a - RGB_b| over the interior
+// texels of n probe pairs (a_probes[i], b_probes[i]).
+__global__ void atlas_compare_kernel(sop_atlas a, const int32_t* ap, sop_atlas b, const int32_t* bp, int32_t n,
+                                     float* out, unsigned int* status)
 {
+    const int R = a.R, RS = R + 2, RR = R * R;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = 0.f;
+    float dO = 0.f, dC = 0.f;
+    if (i < (int64_t)n * RR) {
+        const int64_t q = i / RR;
+        const int t = (int)(i % RR);
+        const int64_t off = (int64_t)(t / R + 1) * RS + (t % R + 1);
+        const int64_t ia = ap ? ap[q] : q, ib = bp ? bp[q] : q;
+        if (ia < 0 || ia >= a.P || ib < 0 || ib >= b.P) {
+            if (status) atomicOr(status, SOP_DEVSTAT_INDEX);
+        } else {
+            const float4 va = texel_load(a.rgbo, a.rgbo_dtype, ia * RS * RS + off);
+            const float4 vb = texel_load(b.rgbo, b.rgbo_dtype, ib * RS * RS + off);
+            dO = fabsf(va.w - vb.w);
+            dC = fabsf(va.x - vb.x) + fabsf(va.y - vb.y) + fabsf(va.z - vb.z);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dO += __shfl_xor_sync(0xffffffffu, dO, o);
+        dC += __shfl_xor_sync(0xffffffffu, dC, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, dO);
+        atomicAdd(out + 1, dC);
+    }
+}
+
+// dst probe dp[i] <- src probe sp[i] (all (R+2)^2 texels; same dtypes)
+__global__ void atlas_copy_kernel(sop_atlas src, const int32_t* sp, sop_atlas dst, const int32_t* dp, int32_t n,
+                                  unsigned int* status)
+{
+    const int RS = src.R + 2, T = RS * RS;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * T) return;
+    const int64_t q = i / T;
+    const int t = (int)(i % T);
+    const int64_t ps = sp ? sp[q] : q, pd = dp ? dp[q] : q;
+    if (ps < 0 || ps >= src.P || pd < 0 || pd >= dst.P) {
+        if (status && t == 0) atomicOr(status, SOP_DEVSTAT_INDEX);
+        return;
+    }
+    const int64_t si = ps * T + t, di = pd * T + t;
+    if (src.rgbo_dtype == SOP_F32) reinterpret_cast<float4*>(dst.rgbo)[di] = reinterpret_cast<const float4*>(src.rgbo)[si];
+    else reinterpret_cast<uint2*>(dst.rgbo)[di] = reinterpret_cast<const uint2*>(src.rgbo)[si];
+    if (src.depth && dst.depth) {
+        if (src.depth_dtype == SOP_F32) reinterpret_cast<float*>(dst.depth)[di] = reinterpret_cast<const float*>(src.depth)[si];
+        else if (src.depth_dtype == SOP_FP8E4M3) reinterpret_cast<uint8_t*>(dst.depth)[di] = reinterpret_cast<const uint8_t*>(src.depth)[si];
+        else reinterpret_cast<uint16_t*>(dst.depth)[di] = reinterpret_cast<const uint16_t*>(src.depth)[si];
+    }
+}
+
+// The spot-check sample: n_spot of P probes, one per stratum: probe i is
+// floor((i + u_i) P / n) with u_i = splitmix64(seed + i) / 2^64, so the
+// sample is distinct, spread over the probe order and seeded; positions
+// gathered for the trace.
+__global__ void spot_pick_kernel(uint64_t seed, int32_t P, int32_t n, const float* __restrict__ probe_pos,
+                                 int32_t* __restrict__ ids, float* __restrict__ pos)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double u = (double)(splitmix64(seed + (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+    int64_t id = (int64_t)floor(((double)i + u) * (double)P / (double)n);
+    id = id < 0 ? 0 : (id >= P ? P - 1 : id);
+    ids[i] = (int32_t)id;
+    for (int a = 0; a < 3; ++a) pos[3 * i + a] = probe_pos[3 * id + a];
+}
+
+// mean |dO| of the spot check and the fallback decision, on the device:
+// err = sums[0] / texels; fell_back = err > tau (or not finite)
+__global__ void spot_decide_kernel(const float* sums, float inv_texels, float tau, float* err_out,
+                                   int32_t* fell_back)
+{
+    const float e = sums[0] * inv_texels;
+    if (err_out) err_out[0] = e;
+    fell_back[0] = (e > tau || !isfinite(e)) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-cudaError_t surr_set_params(char* state, const float* params, cudaStream_t s)
+cudaError_t surr_set_params(char* state, const float* params, uint64_t seed, cudaStream_t s)
 {
     const SurrState S = surr_state_layout();
-    cudaError_t e = cudaMemcpyAsync(state + S.master, params, sizeof(float) * kNParam, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
+    float* master = reinterpret_cast<float*>(state + S.master);
     const unsigned nb = (kNParam + 255) / 256;
+    if (params) {
+        cudaError_t e = cudaMemcpyAsync(master, params, sizeof(float) * kNParam, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        surr_init_kernel<<<nb, 256, 0, s>>>(master, seed);
+    }
     surr_reset_kernel<<<nb, 256, 0, s>>>(reinterpret_cast<float*>(state + S.m), reinterpret_cast<float*>(state + S.v),
+                                         reinterpret_cast<float*>(state + S.grad),
                                          reinterpret_cast<int32_t*>(state + S.step));
-    surr_to_bf16_kernel<<<nb, 256, 0, s>>>(reinterpret_cast<const float*>(state + S.master),
-                                           reinterpret_cast<uint16_t*>(state + S.wbf));
+    surr_to_bf16_kernel<<<nb, 256, 0, s>>>(master, reinterpret_cast<uint16_t*>(state + S.wbf));
+    return cudaGetLastError();
+}
+
+cudaError_t surr_refresh_bf16(char* state, cudaStream_t s)
+{
+    const SurrState S = surr_state_layout();
+    surr_to_bf16_kernel<<<(kNParam + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float*>(state + S.master),
+                                                               reinterpret_cast<uint16_t*>(state + S.wbf));
     return cudaGetLastError();
 }
 
@@ -593,36 +1097,98 @@ cudaError_t surr_get_grad(const char* state, float* grad, cudaStream_t s)
     return cudaMemcpyAsync(grad, state + S.grad, sizeof(float) * kNParam, cudaMemcpyDeviceToDevice, s);
 }
 
-cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_t P, float* feats, char* ws,
-                          cudaStream_t s)
+// ---- features ---------------------------------------------------------------
+SurrFeatLayout surr_feat_layout(int64_t N, int32_t P, int32_t R)
 {
-    int32_t* idx = reinterpret_cast<int32_t*>(ws);
-    char* kws = ws + align256(sizeof(int32_t) * (size_t)P * kNeigh);
-    cudaError_t e = launch_knn_sites(probe_pos, P, g.mean, (int32_t)g.n, kNeigh, idx, kws, s);
+    SurrFeatLayout L{};
+    size_t o = 0;
+    L.sites = o;  o = align256(o + sites_grid_bytes((int32_t)(N > 0 ? N : 1)));
+    L.tdirs = o;  o = align256(o + sizeof(float4) * (size_t)R * R);
+    L.t0 = o;     o = align256(o + sizeof(float) * (size_t)P);
+    L.fhdr = o;   o = align256(o + sizeof(FarGrid));
+    L.fmm = o;    o = align256(o + 8 * sizeof(int32_t));
+    const size_t cells = (size_t)kFarCells * kFarCells * kFarCells;
+    L.facc = o;   o = align256(o + 4 * sizeof(unsigned long long) * cells);
+    L.fcells = o; o = align256(o + sizeof(float4) * cells);
+    L.total = o;
+    return L;
+}
+
+size_t surr_near_smem() { return (sizeof(uint64_t) + sizeof(int32_t)) * kCandCap; }
+
+cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_t P, int32_t R, float r_n,
+                          float alpha_min, float alpha_max, const char* bake_rec, float* feats, int32_t* list,
+                          char* ws, cudaStream_t s)
+{
+    const SurrFeatLayout L = surr_feat_layout(g.n, P, R);
+    unsigned int* status = status_word();
+    const SitesGrid sg = launch_sites_grid(g.mean, (int32_t)g.n, ws + L.sites, s);
+    float4* tdirs = reinterpret_cast<float4*>(ws + L.tdirs);
+    surr_tdirs_kernel<<<(R * R + 127) / 128, 128, 0, s>>>(R, tdirs);
+    float* t0 = reinterpret_cast<float*>(ws + L.t0);
+    NearK nk;
+    nk.probe_pos = probe_pos;
+    nk.P = P;
+    nk.R = R;
+    nk.grid = sg.grid;
+    nk.cell_start = sg.cell_start;
+    nk.ent = sg.entries;
+    const double rq = (double)r_n * 1048576.0;
+    nk.r2key = (uint64_t)floor(rq * rq);
+    nk.r_q = (int32_t)ceil(rq);
+    nk.r_n = r_n;
+    nk.rec = reinterpret_cast<const float4*>(bake_rec);
+    nk.tdirs = tdirs;
+    nk.alpha_min = alpha_min;
+    nk.alpha_max = alpha_max;
+    nk.feats = feats;
+    nk.list = list;
+    nk.t0 = t0;
+    nk.status = status;
+    const size_t smem = surr_near_smem();
+    cudaError_t e = cudaFuncSetAttribute(surr_near_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t n = (int64_t)P * kFP;
-    surr_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, probe_pos, P, idx, feats);
+    if (P > 0) surr_near_kernel<<<P, kNearThreads, smem, s>>>(nk);
+    // far field
+    FarGrid* fg = reinterpret_cast<FarGrid*>(ws + L.fhdr);
+    int32_t* mm = reinterpret_cast<int32_t*>(ws + L.fmm);
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(ws + L.facc);
+    float4* cells = reinterpret_cast<float4*>(ws + L.fcells);
+    far_bbox_init_kernel<<<1, 32, 0, s>>>(mm);
+    const unsigned nb = (unsigned)((g.n + 255) / 256);
+    if (g.n > 0) far_bbox_kernel<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(g, alpha_min, mm);
+    far_setup_kernel<<<1, 32, 0, s>>>(mm, fg);
+    const int64_t maxc = (int64_t)kFarCells * kFarCells * kFarCells;
+    far_zero_kernel<<<(unsigned)((4 * maxc + 255) / 256), 256, 0, s>>>(fg, acc);
+    if (g.n > 0) far_splat_kernel<<<nb, 256, 0, s>>>(g, alpha_min, alpha_max, fg, acc);
+    far_cells_kernel<<<(unsigned)((maxc + 255) / 256), 256, 0, s>>>(fg, acc, cells);
+    const int64_t rays = (int64_t)P * R * R;
+    if (rays > 0)
+        far_march_kernel<<<(unsigned)((rays + 255) / 256), 256, 0, s>>>(probe_pos, P, R, t0, tdirs, fg, cells, feats);
     return cudaGetLastError();
 }
 
-size_t surr_features_ws_bytes(int64_t N, int32_t P)
+// ---- network -----------------------------------------------------------------
+// CTAs of a network launch: two per SM at most (kMaxMlpCtas)
+constexpr int kMaxMlpCtas = 2 * 160;
+
+static unsigned mlp_blocks(int32_t B)
 {
-    return align256(sizeof(int32_t) * (size_t)P * kNeigh) + knn_sites_bytes((int32_t)N, P, kNeigh);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    int nb = 2 * sms < kMaxMlpCtas ? 2 * sms : kMaxMlpCtas;
+    return (unsigned)(B < nb ? B : nb);
 }
 
-// per-call scratch of train / infer: h1p, dh1p, texel directions
-size_t surr_run_ws_bytes(int32_t B, int32_t R)
-{
-    return 2 * align256(sizeof(float) * (size_t)B * kHid) + align256(sizeof(float4) * (size_t)R * R);
-}
-
-static cudaError_t mlp_launch(bool train, const MlpK& k, cudaStream_t s)
+static cudaError_t mlp_launch(bool train, const MlpK& k, unsigned nb, cudaStream_t s)
 {
     const size_t smem = surr_mlp_smem();
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned nb = (unsigned)(k.B < 2 * sms ? k.B : 2 * sms);
+    if (nb == 0) return cudaSuccess;
     if (train) {
         cudaError_t e = cudaFuncSetAttribute(surr_mlp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -635,132 +1201,81 @@ static cudaError_t mlp_launch(bool train, const MlpK& k, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t surr_train_step(char* state, const float* feats, const int32_t* pid, int32_t B, const sop_atlas& tgt,
-                            float lr, char* ws, cudaStream_t s)
+size_t surr_train_ws_bytes()
+{
+    return align256(sizeof(int32_t) * 65536) + align256(sizeof(float) * (size_t)kMaxMlpCtas * kNParam) +
+           align256(sizeof(float) * kMaxMlpCtas);
+}
+
+cudaError_t surr_train_steps(char* state, const float* feats, const int32_t* pid, int32_t B, int32_t P,
+                             const sop_atlas& tgt, int32_t steps, float lr, uint64_t seed, float* loss_out,
+                             char* ws, cudaStream_t s)
 {
     const SurrState S = surr_state_layout();
-    float* h1p = reinterpret_cast<float*>(ws);
-    float* dh1p = reinterpret_cast<float*>(ws + align256(sizeof(float) * (size_t)B * kHid));
-    float4* tdirs = reinterpret_cast<float4*>(ws + 2 * align256(sizeof(float) * (size_t)B * kHid));
     float* grad = reinterpret_cast<float*>(state + S.grad);
     float* loss = reinterpret_cast<float*>(state + S.loss);
-    const int R = tgt.R;
-    zero_f32_kernel<<<(kNParam + 255) / 256, 256, 0, s>>>(grad, kNParam);
-    zero_f32_kernel<<<1, 32, 0, s>>>(loss, 1);
-    surr_tdirs_kernel<<<(R * R + 127) / 128, 128, 0, s>>>(R, tdirs);
+    int32_t* step = reinterpret_cast<int32_t*>(state + S.step);
     const uint16_t* wbf = reinterpret_cast<const uint16_t*>(state + S.wbf);
     const float* master = reinterpret_cast<const float*>(state + S.master);
-    surr_l1_fwd_kernel<<<(unsigned)(((int64_t)B * kHid + 255) / 256), 256, 0, s>>>(feats, pid, B, wbf, master, h1p);
-    MlpK k;
-    k.h1p = h1p;
-    k.pid = pid;
-    k.B = B;
-    k.R = R;
-    k.tdirs = tdirs;
-    k.wbf = wbf;
-    k.master = master;
-    k.rgbo = tgt.rgbo;
-    k.depth = tgt.depth;
-    k.rgbo_dtype = tgt.rgbo_dtype;
-    k.depth_dtype = tgt.depth_dtype;
-    k.inv_count = 1.f / ((float)B * R * R * kOut);
-    k.grad = grad;
-    k.dh1p = dh1p;
-    k.loss = loss;
-    cudaError_t e = mlp_launch(true, k, s);
-    if (e != cudaSuccess) return e;
-    surr_l1_bwd_kernel<<<(kHid * kFP + 255) / 256, 256, 0, s>>>(feats, pid, B, dh1p, grad);
-    surr_adam_kernel<<<(kNParam + 255) / 256, 256, 0, s>>>(reinterpret_cast<float*>(state + S.master),
-                                                           reinterpret_cast<float*>(state + S.m),
-                                                           reinterpret_cast<float*>(state + S.v), grad,
-                                                           reinterpret_cast<uint16_t*>(state + S.wbf),
-                                                           reinterpret_cast<const int32_t*>(state + S.step), lr);
-    surr_step_kernel<<<1, 1, 0, s>>>(reinterpret_cast<int32_t*>(state + S.step));
+    int32_t* ids_ws = reinterpret_cast<int32_t*>(ws);
+    float* part = reinterpret_cast<float*>(ws + align256(sizeof(int32_t) * 65536));
+    float* lpart = reinterpret_cast<float*>(ws + align256(sizeof(int32_t) * 65536) +
+                                            align256(sizeof(float) * (size_t)kMaxMlpCtas * kNParam));
+    const int R = tgt.R;
+    const unsigned nb = mlp_blocks(B);
+    for (int it = 0; it < steps; ++it) {
+        const int32_t* ids = pid;
+        if (!ids) {
+            surr_pick_kernel<<<(B + 255) / 256, 256, 0, s>>>(seed, step, P, B, ids_ws);
+            ids = ids_ws;
+        }
+        MlpK k{};
+        k.feats = feats;
+        k.pid = ids;
+        k.B = B;
+        k.R = R;
+        k.P = P;
+        k.wbf = wbf;
+        k.master = master;
+        k.rgbo = tgt.rgbo;
+        k.depth = tgt.depth;
+        k.rgbo_dtype = tgt.rgbo_dtype;
+        k.depth_dtype = tgt.depth_dtype;
+        k.inv_count = 1.f / ((float)B * R * R * kOut);
+        k.grad_part = part;
+        k.loss_part = lpart;
+        k.status = status_word();
+        cudaError_t e = mlp_launch(true, k, nb, s);
+        if (e != cudaSuccess) return e;
+        surr_grad_reduce_kernel<<<(kNParam + 255) / 256, 256, 0, s>>>(part, lpart, (int)nb, grad, loss);
+        if (loss_out) surr_loss_kernel<<<1, 1, 0, s>>>(loss, 1.f / ((float)B * R * R * kOut), loss_out + it);
+        surr_adam_kernel<<<(kNParam + 255) / 256, 256, 0, s>>>(reinterpret_cast<float*>(state + S.master),
+                                                               reinterpret_cast<float*>(state + S.m),
+                                                               reinterpret_cast<float*>(state + S.v), grad,
+                                                               reinterpret_cast<uint16_t*>(state + S.wbf), step, lr);
+        surr_step_kernel<<<1, 1, 0, s>>>(step);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t surr_infer(const char* state, const float* feats, const int32_t* pid, int32_t B, const sop_atlas& out,
-                       char* ws, cudaStream_t s)
+cudaError_t surr_infer(const char* state, const float* feats, const int32_t* pid, int32_t B, int32_t P,
+                       const sop_atlas& out, cudaStream_t s)
 {
     const SurrState S = surr_state_layout();
-    float* h1p = reinterpret_cast<float*>(ws);
-    float4* tdirs = reinterpret_cast<float4*>(ws + 2 * align256(sizeof(float) * (size_t)B * kHid));
-    const int R = out.R;
-    surr_tdirs_kernel<<<(R * R + 127) / 128, 128, 0, s>>>(R, tdirs);
-    const uint16_t* wbf = reinterpret_cast<const uint16_t*>(state + S.wbf);
-    const float* master = reinterpret_cast<const float*>(state + S.master);
-    surr_l1_fwd_kernel<<<(unsigned)(((int64_t)B * kHid + 255) / 256), 256, 0, s>>>(feats, pid, B, wbf, master, h1p);
     MlpK k{};
-    k.h1p = h1p;
+    k.feats = feats;
     k.pid = pid;
     k.B = B;
-    k.R = R;
-    k.tdirs = tdirs;
-    k.wbf = wbf;
-    k.master = master;
+    k.R = out.R;
+    k.P = P;
+    k.wbf = reinterpret_cast<const uint16_t*>(state + S.wbf);
+    k.master = reinterpret_cast<const float*>(state + S.master);
     k.rgbo = out.rgbo;
     k.depth = out.depth;
     k.rgbo_dtype = out.rgbo_dtype;
     k.depth_dtype = out.depth_dtype;
-    return mlp_launch(false, k, s);
-}
-
-
-__global__ void surr_loss_kernel(const float* sum, float scale, float* out) { out[0] = sum[0] * scale; }
-
-// ---------------------------------------------------------------------------
-// Atlas helpers for the spot-check: compare and copy whole probes.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float4 texel_at(const sop_atlas& a, int64_t i)
-{
-    if (a.rgbo_dtype == SOP_F32) return reinterpret_cast<const float4*>(a.rgbo)[i];
-    if (a.rgbo_dtype == SOP_BF16) return Texel<SOP_BF16>::load(reinterpret_cast<const uint2*>(a.rgbo) + i);
-    return Texel<SOP_F16>::load(reinterpret_cast<const uint2*>(a.rgbo) + i);
-}
-
-// out[0] += sum |O_a - O_b|, out[1] += sum |RGB_a - RGB_b| over the interior
-// texels of n probe pairs (a_probes[i], b_probes[i]).
-__global__ void atlas_compare_kernel(sop_atlas a, const int32_t* ap, sop_atlas b, const int32_t* bp, int32_t n,
-                                     float* out)
-{
-    const int R = a.R, RS = R + 2, RR = R * R;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float dO = 0.f, dC = 0.f;
-    if (i < (int64_t)n * RR) {
-        const int64_t q = i / RR;
-        const int t = (int)(i % RR);
-        const int64_t off = (int64_t)(t / R + 1) * RS + (t % R + 1);
-        const float4 va = texel_at(a, (int64_t)(ap ? ap[q] : q) * RS * RS + off);
-        const float4 vb = texel_at(b, (int64_t)(bp ? bp[q] : q) * RS * RS + off);
-        dO = fabsf(va.w - vb.w);
-        dC = fabsf(va.x - vb.x) + fabsf(va.y - vb.y) + fabsf(va.z - vb.z);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        dO += __shfl_xor_sync(0xffffffffu, dO, o);
-        dC += __shfl_xor_sync(0xffffffffu, dC, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(out, dO);
-        atomicAdd(out + 1, dC);
-    }
-}
-
-// dst probe dp[i] <- src probe sp[i] (all (R+2)^2 texels; same dtypes)
-__global__ void atlas_copy_kernel(sop_atlas src, const int32_t* sp, sop_atlas dst, const int32_t* dp, int32_t n)
-{
-    const int RS = src.R + 2, T = RS * RS;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n * T) return;
-    const int64_t q = i / T;
-    const int t = (int)(i % T);
-    const int64_t si = (int64_t)(sp ? sp[q] : q) * T + t, di = (int64_t)(dp ? dp[q] : q) * T + t;
-    if (src.rgbo_dtype == SOP_F32) reinterpret_cast<float4*>(dst.rgbo)[di] = reinterpret_cast<const float4*>(src.rgbo)[si];
-    else reinterpret_cast<uint2*>(dst.rgbo)[di] = reinterpret_cast<const uint2*>(src.rgbo)[si];
-    if (src.depth && dst.depth) {
-        if (src.depth_dtype == SOP_F32) reinterpret_cast<float*>(dst.depth)[di] = reinterpret_cast<const float*>(src.depth)[si];
-        else if (src.depth_dtype == SOP_FP8E4M3) reinterpret_cast<uint8_t*>(dst.depth)[di] = reinterpret_cast<const uint8_t*>(src.depth)[si];
-        else reinterpret_cast<uint16_t*>(dst.depth)[di] = reinterpret_cast<const uint16_t*>(src.depth)[si];
-    }
+    k.status = status_word();
+    return mlp_launch(false, k, mlp_blocks(B), s);
 }
 
 cudaError_t launch_atlas_compare(const sop_atlas& a, const int32_t* ap, const sop_atlas& b, const int32_t* bp,
@@ -768,7 +1283,8 @@ cudaError_t launch_atlas_compare(const sop_atlas& a, const int32_t* ap, const so
 {
     zero_f32_kernel<<<1, 32, 0, s>>>(out, 2);
     const int64_t m = (int64_t)n * a.R * a.R;
-    if (m > 0) atlas_compare_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(a, ap, b, bp, n, out);
+    if (m > 0)
+        atlas_compare_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(a, ap, b, bp, n, out, status_word());
     return cudaGetLastError();
 }
 
@@ -776,7 +1292,22 @@ cudaError_t launch_atlas_copy(const sop_atlas& src, const int32_t* sp, const sop
                               int32_t n, cudaStream_t s)
 {
     const int64_t m = (int64_t)n * (src.R + 2) * (src.R + 2);
-    if (m > 0) atlas_copy_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(src, sp, dst, dp, n);
+    if (m > 0)
+        atlas_copy_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(src, sp, dst, dp, n, status_word());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spot_pick(uint64_t seed, int32_t P, int32_t n, const float* probe_pos, int32_t* ids, float* pos,
+                             cudaStream_t s)
+{
+    spot_pick_kernel<<<(n + 127) / 128, 128, 0, s>>>(seed, P, n, probe_pos, ids, pos);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spot_decide(const float* sums, float inv_texels, float tau, float* err_out, int32_t* fell_back,
+                               cudaStream_t s)
+{
+    spot_decide_kernel<<<1, 1, 0, s>>>(sums, inv_texels, tau, err_out, fell_back);
     return cudaGetLastError();
 }
 
@@ -785,6 +1316,32 @@ cudaError_t surr_loss_out(const char* state, float scale, float* out, cudaStream
     const SurrState S = surr_state_layout();
     surr_loss_kernel<<<1, 1, 0, s>>>(reinterpret_cast<const float*>(state + S.loss), scale, out);
     return cudaGetLastError();
+}
+
+cudaError_t surr_state_io(char* state, float* master, float* m, float* v, int32_t* step, bool to_device,
+                          cudaStream_t s)
+{
+    const SurrState S = surr_state_layout();
+    const cudaMemcpyKind kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    struct {
+        size_t off;
+        void* host;
+        size_t bytes;
+    } parts[4] = {{S.master, master, sizeof(float) * kNParam},
+                  {S.m, m, sizeof(float) * kNParam},
+                  {S.v, v, sizeof(float) * kNParam},
+                  {S.step, step, sizeof(int32_t)}};
+    for (auto& q : parts) {
+        cudaError_t e = to_device ? cudaMemcpyAsync(state + q.off, q.host, q.bytes, kind, s)
+                                  : cudaMemcpyAsync(q.host, state + q.off, q.bytes, kind, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (to_device) {
+        zero_f32_kernel<<<(kNParam + 255) / 256, 256, 0, s>>>(reinterpret_cast<float*>(state + S.grad), kNParam);
+        cudaError_t e = surr_refresh_bf16(state, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaStreamSynchronize(s);
 }
 
 }  // namespace sop

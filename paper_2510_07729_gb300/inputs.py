@@ -579,5 +579,12 @@ def moved_object(seed=4):
     moved = Ellipsoids(ells.c + np.where(np.arange(5)[:, None] == 0, shift, 0.0), ells.a, ells.R)
     samp, snrm = moved.sample_surface(rng, 4096)
     ppos = samp + 0.01 * diag * snrm
-    return dict(gauss=g2, probe_pos=ppos.astype(F32), probe_nrm=snrm.astype(F32), R=16, moved=int(on0.sum()),
-                shift=shift)
+    out = dict(gauss=g2, probe_pos=ppos.astype(F32), probe_nrm=snrm.astype(F32), R=16, moved=int(on0.sum()),
+               shift=shift)
+    # a view of the moved object (drawn after the scene, which it leaves
+    # unchanged): shading points, materials, a log-normal environment
+    cam = _unit_vectors(rng, 1)[0] * 3.0
+    x, n, wo, _ = _view(rng, moved, cam, 400, 400, OBJECT_FOV)
+    out.update(x=x.astype(F32), n=n.astype(F32), wo=wo.astype(F32), **materials(rng, len(x)),
+               env=env_lognormal(rng, 256, 512), K=8, S=128)
+    return out

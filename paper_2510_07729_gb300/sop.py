@@ -130,18 +130,31 @@ def load(build_if_missing: bool = True):
                                             C.POINTER(ShadeParams), vp, vp, vp, vp]
     lib.sop_surrogate_param_count.restype = i32
     lib.sop_surrogate_state_bytes.restype = sz
+    pp_ = C.POINTER(C.c_void_p)
+    lib.sop_surrogate_create.argtypes = [vp, sz, vp, C.c_uint64, f32, pp_, vp]
+    lib.sop_surrogate_destroy.argtypes = [vp]
     lib.sop_surrogate_set_params.argtypes = [vp, vp, vp]
     lib.sop_surrogate_get_params.argtypes = [vp, vp, vp]
     lib.sop_surrogate_get_grad.argtypes = [vp, vp, vp]
+    lib.sop_surrogate_save.argtypes = [vp, C.c_char_p, vp]
+    lib.sop_surrogate_load.argtypes = [vp, C.c_char_p, vp]
+    lib.sop_surrogate_file_write.argtypes = [C.c_char_p, i32, i32, vp, vp, vp]
+    lib.sop_surrogate_file_read.argtypes = [C.c_char_p, i32, C.POINTER(i32), vp, vp, vp]
     lib.sop_surrogate_workspace_bytes.argtypes = [i64, i32, i32]
     lib.sop_surrogate_workspace_bytes.restype = sz
-    lib.sop_surrogate_features.argtypes = [C.POINTER(Gaussians), vp, i32, vp, vp, sz, vp]
-    lib.sop_surrogate_train_step.argtypes = [vp, vp, vp, i32, C.POINTER(AtlasDesc), f32, vp, vp, sz, vp]
-    lib.sop_surrogate_infer.argtypes = [vp, vp, vp, i32, C.POINTER(AtlasDesc), vp, sz, vp]
+    lib.sop_surrogate_train_workspace_bytes.restype = sz
+    lib.sop_surrogate_features.argtypes = [vp, C.POINTER(Gaussians), vp, i32, i32, C.POINTER(BakeParams), vp, vp, vp,
+                                           sz, vp]
+    lib.sop_surrogate_train.argtypes = [vp, vp, vp, i32, C.POINTER(AtlasDesc), i32, f32, C.c_uint64, vp, vp, sz, vp]
+    lib.sop_surrogate_predict.argtypes = [vp, vp, vp, i32, C.POINTER(AtlasDesc), vp]
+    lib.sop_surrogate_infer.argtypes = [vp, C.POINTER(Gaussians), C.POINTER(AtlasDesc), C.POINTER(BakeParams), f32,
+                                        f32, C.c_uint64, vp, vp, vp, sz, vp]
     lib.sop_atlas_compare.argtypes = [C.POINTER(AtlasDesc), vp, C.POINTER(AtlasDesc), vp, i32, vp, vp]
     lib.sop_atlas_copy.argtypes = [C.POINTER(AtlasDesc), vp, C.POINTER(AtlasDesc), vp, i32, vp]
-    for name in ("sop_surrogate_set_params", "sop_surrogate_get_params", "sop_surrogate_get_grad",
-                 "sop_surrogate_features", "sop_surrogate_train_step", "sop_surrogate_infer", "sop_atlas_compare",
+    for name in ("sop_surrogate_create", "sop_surrogate_destroy", "sop_surrogate_set_params",
+                 "sop_surrogate_get_params", "sop_surrogate_get_grad", "sop_surrogate_save", "sop_surrogate_load",
+                 "sop_surrogate_file_write", "sop_surrogate_file_read", "sop_surrogate_features",
+                 "sop_surrogate_train", "sop_surrogate_predict", "sop_surrogate_infer", "sop_atlas_compare",
                  "sop_atlas_copy"):
         getattr(lib, name).restype = C.c_int
     for name in ("sop_device_status", "sop_atlas_bytes", "sop_atlas_pack", "sop_hammersley", "sop_bake", "sop_bake_bin", "sop_bake_trace",
@@ -662,61 +675,135 @@ def _i32(t):
 
 
 class Surrogate:
-    """Caller-owned surrogate state (parameters, Adam moments, gradient)."""
+    """The learned bake surrogate (sop_surrogate handle over a caller-owned
+    device state). params: initial parameters (sop_surrogate_param_count()
+    floats) or None for the library's seeded He-uniform initialisation;
+    r_near: the near-field radius of the texel features."""
 
-    def __init__(self, params, device="cuda"):
+    N_FEATURES = 18
+    NEAR_CAP = 256
+
+    def __init__(self, params=None, device="cuda", r_near=0.08, seed=0):
         lib = load()
         self.n_params = int(lib.sop_surrogate_param_count())
-        self.state = _ws(int(lib.sop_surrogate_state_bytes()), device)
         self.device = torch.device(device)
-        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
-        self.set_params(params)
+        self.state = _ws(int(lib.sop_surrogate_state_bytes()), self.device)
+        self.r_near = float(r_near)
+        p = None
+        if params is not None:
+            p = torch.as_tensor(params, dtype=torch.float32).to(self.device).contiguous()
+            if p.numel() != self.n_params:
+                raise ValueError(f"expected {self.n_params} parameters")
+        h = C.c_void_p()
+        _check(lib.sop_surrogate_create(_ptr(self.state), self.state.numel(), _ptr(p), C.c_uint64(seed),
+                                        C.c_float(self.r_near), C.byref(h), _stream()))
+        self._keep = p
+        self.h = h
+        self._ws = {}
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) and self.h.value:
+                load().sop_surrogate_destroy(self.h)
+                self.h = C.c_void_p()
+        except Exception:
+            pass
 
     def set_params(self, params):
         p = torch.as_tensor(params, dtype=torch.float32).to(self.device).contiguous()
         if p.numel() != self.n_params:
             raise ValueError(f"expected {self.n_params} parameters")
-        _check(load().sop_surrogate_set_params(_ptr(self.state), _ptr(p), _stream()))
+        _check(load().sop_surrogate_set_params(self.h, _ptr(p), _stream()))
         self._keep = p
 
     def params(self):
         out = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
-        _check(load().sop_surrogate_get_params(_ptr(self.state), _ptr(out), _stream()))
+        _check(load().sop_surrogate_get_params(self.h, _ptr(out), _stream()))
         return out
 
     def grad(self):
         out = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
-        _check(load().sop_surrogate_get_grad(_ptr(self.state), _ptr(out), _stream()))
+        _check(load().sop_surrogate_get_grad(self.h, _ptr(out), _stream()))
         return out
 
-    def _ws(self, n_gauss, P, R):
-        return _ws(int(load().sop_surrogate_workspace_bytes(max(int(n_gauss), 32), int(P), int(R))), self.device)
+    def save(self, path):
+        _check(load().sop_surrogate_save(self.h, str(path).encode(), _stream()))
 
-    def features(self, gauss, probe_pos, workspace=None):
+    def load_file(self, path):
+        _check(load().sop_surrogate_load(self.h, str(path).encode(), _stream()))
+
+    def workspace(self, n_gauss, P, R):
+        key = (int(n_gauss), int(P), int(R))
+        if key not in self._ws:
+            self._ws.clear()
+            self._ws[key] = _ws(int(load().sop_surrogate_workspace_bytes(*key)), self.device)
+        return self._ws[key]
+
+    def features(self, gauss, probe_pos, R, alpha_min=1.0 / 255.0, alpha_max=0.99, with_list=False):
+        """Texel features [P, R*R, 18] (and the near lists [P, 256] int32)."""
         P = probe_pos.shape[0]
         g = _gauss(gauss)
-        feats = torch.empty((P, 416), dtype=torch.float32, device=self.device)
-        ws = workspace if workspace is not None else self._ws(g.n, P, 2)
-        _check(load().sop_surrogate_features(C.byref(g), _f32(probe_pos, (P, 3)), P, _ptr(feats), _ptr(ws),
-                                             ws.numel(), _stream()))
-        return feats
+        feats = torch.empty((P, R * R, self.N_FEATURES), dtype=torch.float32, device=self.device)
+        lst = torch.empty((P, self.NEAR_CAP), dtype=torch.int32, device=self.device) if with_list else None
+        ws = self.workspace(g.n, P, R)
+        bp = _bake_params(0.0, alpha_min, alpha_max, 1e-4)
+        _check(load().sop_surrogate_features(self.h, C.byref(g), _f32(probe_pos, (P, 3)), P, R, C.byref(bp),
+                                             _ptr(feats), _ptr(lst), _ptr(ws), ws.numel(), _stream()))
+        return (feats, lst) if with_list else feats
 
-    def train_step(self, feats, targets: Atlas, lr=1e-3, probe_ids=None, workspace=None):
-        """One Adam step; returns the batch's mean absolute error (device)."""
-        B = probe_ids.shape[0] if probe_ids is not None else targets.P
+    def train(self, feats, targets: Atlas, steps=1, batch=64, lr=1e-3, seed=0, probe_ids=None, losses=None):
+        """`steps` Adam steps on `batch` probes each (probe_ids [batch] int32,
+        or drawn on the device from seed and the step count). losses: a
+        device float32 tensor [steps] for each step's loss, or None."""
         d = targets.c()
-        ws = workspace if workspace is not None else self._ws(32, B, targets.R)
-        _check(load().sop_surrogate_train_step(_ptr(self.state), _ptr(feats), _i32(probe_ids), B, C.byref(d),
-                                               C.c_float(lr), _ptr(self.loss), _ptr(ws), ws.numel(), _stream()))
-        return self.loss
+        B = probe_ids.shape[0] if probe_ids is not None else batch
+        if getattr(self, "_train_ws", None) is None:
+            self._train_ws = _ws(int(load().sop_surrogate_train_workspace_bytes()), self.device)
+        ws = self._train_ws
+        _check(load().sop_surrogate_train(self.h, _ptr(feats), _i32(probe_ids), B, C.byref(d), steps, C.c_float(lr),
+                                          C.c_uint64(seed), _ptr(losses), _ptr(ws), ws.numel(), _stream()))
+        return losses
 
-    def infer(self, feats, out: Atlas, probe_ids=None, workspace=None):
+    def predict(self, feats, out: Atlas, probe_ids=None):
         B = probe_ids.shape[0] if probe_ids is not None else out.P
         d = out.c()
-        ws = workspace if workspace is not None else self._ws(32, B, out.R)
-        _check(load().sop_surrogate_infer(_ptr(self.state), _ptr(feats), _i32(probe_ids), B, C.byref(d), _ptr(ws),
-                                          ws.numel(), _stream()))
+        _check(load().sop_surrogate_predict(self.h, _ptr(feats), _i32(probe_ids), B, C.byref(d), _stream()))
         return out
+
+    def rebake(self, gauss, out: Atlas, spot_frac=0.01, tau=0.05, seed=0, alpha_min=1.0 / 255.0, alpha_max=0.99,
+               t_stop=1e-4):
+        """sop_surrogate_infer: the learned rebake of every probe of `out`
+        with its spot check and fallback, decided on the device. Returns
+        (spot-check mean |dO|, fell back) as device tensors."""
+        g = _gauss(gauss)
+        d = out.c()
+        bp = _bake_params(0.0, alpha_min, alpha_max, t_stop)
+        err = torch.empty(1, dtype=torch.float32, device=self.device)
+        fell = torch.empty(1, dtype=torch.int32, device=self.device)
+        ws = self.workspace(g.n, out.P, out.R)
+        _check(load().sop_surrogate_infer(self.h, C.byref(g), C.byref(d), C.byref(bp), C.c_float(spot_frac),
+                                          C.c_float(tau), C.c_uint64(seed), _ptr(err), _ptr(fell), _ptr(ws),
+                                          ws.numel(), _stream()))
+        return err, fell
+
+
+def surrogate_file_write(path, step, params, m, v):
+    """The checkpoint format from host arrays (no GPU)."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (params, m, v)]
+    n = arrs[0].size
+    _check(load(build_if_missing=False).sop_surrogate_file_write(
+        str(path).encode(), n, int(step), *[a.ctypes.data_as(C.c_void_p) for a in arrs]))
+
+
+def surrogate_file_read(path, n):
+    """(step, params, m, v) of a checkpoint file of n parameters (no GPU)."""
+    import numpy as np
+    arrs = [np.empty(n, np.float32) for _ in range(3)]
+    step = C.c_int32(0)
+    _check(load(build_if_missing=False).sop_surrogate_file_read(
+        str(path).encode(), n, C.byref(step), *[a.ctypes.data_as(C.c_void_p) for a in arrs]))
+    return int(step.value), arrs[0], arrs[1], arrs[2]
 
 
 def atlas_compare(a: Atlas, b: Atlas, a_probes=None, b_probes=None, n=None):
@@ -733,37 +820,6 @@ def atlas_copy(src: Atlas, dst: Atlas, src_probes=None, dst_probes=None, n=None)
     n = n if n is not None else (src_probes.shape[0] if src_probes is not None else src.P)
     ds, dd = src.c(), dst.c()
     _check(load().sop_atlas_copy(C.byref(ds), _i32(src_probes), C.byref(dd), _i32(dst_probes), n, _stream()))
-
-
-def surrogate_rebake(surr: Surrogate, gauss, out: Atlas, spot_frac=0.01, tau=0.05, seed=0, bake_workspace=None):
-    """Rebake all probes of `out` with the surrogate, then spot-check
-    ceil(spot_frac * P) random probes against the ray-traced bake: if their
-    mean |dO| exceeds tau, bake every probe with the ray-traced bake instead
-    (fallback); otherwise the checked probes keep their exact bake. Returns
-    (mean |dO| of the spot-check, fell_back). Synchronises once for the
-    decision."""
-    import math
-
-    import numpy as np
-    P, R = out.P, out.R
-    feats = surr.features(gauss, out.probe_pos)
-    surr.infer(feats, out)
-    n_spot = max(1, math.ceil(spot_frac * P))
-    sel = np.sort(np.random.default_rng(seed).choice(P, n_spot, replace=False)).astype(np.int32)
-    sel_t = torch.from_numpy(sel).to(out.rgbo.device)
-    spot = make_atlas(out.probe_pos[sel_t.long()].contiguous(), R, out.rgbo_dtype, out.depth_dtype,
-                      depth_scale=out.depth_scale, with_depth=out.depth is not None)
-    n = int(gauss["mean"].shape[0])
-    ws = bake_workspace if bake_workspace is not None else BakeWorkspace(n, out.rgbo.device)
-    bake_bin(gauss, ws)
-    bake_trace(gauss, spot, ws)
-    diff = atlas_compare(spot, out, None, sel_t, n_spot)
-    err = float(diff[0].item()) / (n_spot * R * R)
-    if err > tau:
-        bake_trace(gauss, out, ws)
-        return err, True
-    atlas_copy(spot, out, None, sel_t, n_spot)
-    return err, False
 
 
 def l1_loss_grad(C_, C_target, grad=None, loss_sum=None):

@@ -23,8 +23,9 @@ def test_library_exports_every_declared_function():
     assert len(names) >= 20, names
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
-    for must in ("sop_bake", "sop_query_shade", "sop_query_shade_backward", "sop_surrogate_train_step",
-                 "sop_surrogate_infer", "sop_query_shade_noalloc", "sop_last_error"):
+    for must in ("sop_bake", "sop_query_shade", "sop_query_shade_backward", "sop_surrogate_create",
+                 "sop_surrogate_destroy", "sop_surrogate_save", "sop_surrogate_load", "sop_surrogate_train",
+                 "sop_surrogate_infer", "sop_query_shade_noalloc", "sop_device_status", "sop_last_error"):
         assert must in names
 
 
@@ -144,3 +145,26 @@ def test_device_status_bits_decoded_on_the_host():
     assert S.devstat_names(0) == []
     assert S.devstat_names(S.DEVSTAT_NONFINITE | S.DEVSTAT_GRID_COARSENED) == ["nonfinite", "grid_coarsened"]
     assert S.devstat_names(0x7) == ["nonfinite", "bake_truncated", "index"]
+
+
+def test_surrogate_arguments_checked_on_the_host():
+    """The surrogate's entry points refuse bad arguments before any device
+    work: no state, a bad near-field radius, a foreign handle, an empty
+    batch, a spot fraction outside (0, 1]."""
+    from paper_2510_07729_gb300 import sop as S
+    lib = S.load()
+    fake = 1 << 20
+    h = ctypes.c_void_p()
+    assert lib.sop_surrogate_create(None, 1 << 20, None, 0, ctypes.c_float(0.08), ctypes.byref(h), None) == 1
+    assert lib.sop_surrogate_create(fake, 1 << 30, None, 0, ctypes.c_float(0.0), ctypes.byref(h), None) == 1
+    assert b"r_near" in lib.sop_last_error()
+    assert lib.sop_surrogate_create(fake, 16, None, 0, ctypes.c_float(0.08), ctypes.byref(h), None) == 3
+    junk = (ctypes.c_uint32 * 16)()
+    at = S.AtlasDesc(fake, None, 0, 0, 64, 8, 1.0, fake, None)
+    assert lib.sop_surrogate_train(ctypes.byref(junk), fake, None, 64, ctypes.byref(at), 1, ctypes.c_float(1e-3), 0,
+                                   None, fake, 1 << 30, None) == 1
+    assert b"handle" in lib.sop_last_error()
+    assert lib.sop_surrogate_destroy(ctypes.byref(junk)) == 1
+    assert lib.sop_surrogate_destroy(None) == 0
+    assert lib.sop_surrogate_workspace_bytes(0, 64, 8) == 0
+    assert lib.sop_surrogate_workspace_bytes(1000, 64, 8) >= lib.sop_surrogate_train_workspace_bytes()
