@@ -893,7 +893,15 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
                     if (mode == 2 && n > kHitCap) {
                         n = nb;
                         pend = pb;
-                        if (++splits > 40 || !(sh > sl)) {
+                        // halve the part; once it cannot shrink (the midpoint
+                        // rounds onto sl: more hits than the buffer holds
+                        // share one entry point) or after 40 halvings, stop
+                        // the ray. The test comes before the part is taken:
+                        // an empty part [sl, sl) would count as taken and
+                        // restart the halving from t_exit without progress.
+                        // Every part taken therefore advances sl strictly.
+                        const float mid = sl + 0.5f * (sh - sl);
+                        if (++splits > 40 || !(mid > sl)) {
                             if (lane == 0) {
                                 atomicOr(k.stats + 3, 1ull);
                                 if (k.status) atomicOr(k.status, SOP_DEVSTAT_BAKE_TRUNCATED);
@@ -901,7 +909,7 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
                             acc.done = true;
                             break;
                         }
-                        sh = sl + 0.5f * (sh - sl);
+                        sh = mid;
                         continue;
                     }
                     composite_hits<OUT>(k, key, alp, dkey, dalp, n, mode == 0 ? last : (mode == 2 && sfin),

@@ -113,7 +113,11 @@ def test_grid_coarsened_on_the_device_gives_the_same_bake(sop, orc):
              quat=rng.standard_normal((n, 4)).astype(np.float32),
              opacity=rng.uniform(0.05, 0.3, n).astype(np.float32),
              rgb=rng.uniform(0, 1, (n, 3)).astype(np.float32))
-    pp = rng.uniform(-0.6, 0.6, (6, 3)).astype(np.float32)
+    # probes outside every box (a probe inside hundreds of boxes would give
+    # them one shared entry point, the walk's start, and more hits there than
+    # the hit buffer holds)
+    v = rng.standard_normal((6, 3))
+    pp = (3.0 * v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
     R = 8
     ws = sop.BakeWorkspace(n, "cuda")
     rgb, occ, dep = bake(sop, g, pp, R, workspace=ws, t_stop=0.0)
