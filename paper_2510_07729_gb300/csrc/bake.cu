@@ -902,10 +902,10 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
                         // Every part taken therefore advances sl strictly.
                         const float mid = sl + 0.5f * (sh - sl);
                         if (++splits > 40 || !(mid > sl)) {
-                            if (lane == 0) {
-                                atomicOr(k.stats + 3, 1ull);
-                                if (k.status) atomicOr(k.status, SOP_DEVSTAT_BAKE_TRUNCATED);
-                            }
+                            // (the status word learns of it from stats[3]
+                            // after the launch: kept out of this loop, its
+                            // pointer would cost the walk registers)
+                            if (lane == 0) atomicOr(k.stats + 3, 1ull);
                             acc.done = true;
                             break;
                         }
@@ -1035,9 +1035,13 @@ cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeL
 
 // Border texels of an atlas copied from the texels the border rule names.
 __global__ void gutter_fill_kernel(int32_t P, int32_t R, void* __restrict__ rgbo, int rgbo_bytes,
-                                   void* __restrict__ depth, int depth_bytes, const int32_t* run_if)
+                                   void* __restrict__ depth, int depth_bytes, const int32_t* run_if,
+                                   const unsigned long long* stats, unsigned int* status)
 {
     if (run_if && __ldg(run_if) == 0) return;
+    // a ray of the trace before this launch stopped early (stats[3] bit 0)
+    if (blockIdx.x == 0 && threadIdx.x == 0 && stats && status && (stats[3] & 1ull))
+        atomicOr(status, SOP_DEVSTAT_BAKE_TRUNCATED);
     const int RS = R + 2, NB = 4 * (R + 1);  // border texels per probe
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)P * NB) return;
@@ -1064,6 +1068,12 @@ __global__ void gutter_fill_kernel(int32_t P, int32_t R, void* __restrict__ rgbo
 __global__ void trace_reset_kernel(unsigned long long* stats)
 {
     if (threadIdx.x < 8) stats[threadIdx.x] = 0ull;
+}
+
+// the truncation bit of a G-buffer trace into the status word
+__global__ void trace_status_kernel(const unsigned long long* stats, unsigned int* status)
+{
+    if (status && (stats[3] & 1ull)) atomicOr(status, SOP_DEVSTAT_BAKE_TRUNCATED);
 }
 
 cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s)
@@ -1133,7 +1143,7 @@ cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp,
     k.run_if = run_if;
     const int64_t rays = (int64_t)atlas.P * R * R;
     trace_kernel<kTraceAtlas><<<trace_blocks<kTraceAtlas>(rays), kWarpsPerCta * 32, 0, s>>>(k);
-    return launch_gutter_fill(atlas, s, run_if);
+    return launch_gutter_fill(atlas, s, run_if, stats);
 }
 
 cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, const float* rough, const float* metal,
@@ -1173,15 +1183,18 @@ cudaError_t launch_trace_gbuffer(const sop_gaussians& g, const float* albedo, co
     const int64_t rays = (int64_t)n_origins * n_dirs;
     if (rays == 0) return cudaGetLastError();
     trace_kernel<kTraceGbuf><<<trace_blocks<kTraceGbuf>(rays), kWarpsPerCta * 32, 0, s>>>(k);
+    trace_status_kernel<<<1, 1, 0, s>>>(stats, k.status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s, const int32_t* run_if)
+cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s, const int32_t* run_if,
+                               const unsigned long long* stats)
 {
     const int64_t nbord = (int64_t)atlas.P * 4 * (atlas.R + 1);
     const int db = atlas.depth_dtype == SOP_F32 ? 4 : (atlas.depth_dtype == SOP_FP8E4M3 ? 1 : 2);
     gutter_fill_kernel<<<(unsigned)((nbord + 255) / 256), 256, 0, s>>>(
-        atlas.P, atlas.R, atlas.rgbo, atlas.rgbo_dtype == SOP_F32 ? 16 : 8, atlas.depth, db, run_if);
+        atlas.P, atlas.R, atlas.rgbo, atlas.rgbo_dtype == SOP_F32 ? 16 : 8, atlas.depth, db, run_if, stats,
+        stats ? status_word() : nullptr);
     return cudaGetLastError();
 }
 

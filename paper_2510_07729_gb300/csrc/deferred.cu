@@ -18,38 +18,41 @@
 
 namespace sop {
 
+// The camera's frame is set up on the host in double and rounded once; the
+// per-pixel directions are FP32 (a few ulp of a unit vector).
 struct CamK {
-    double eye[3], f[3], r[3], u[3];
-    double th, aspect;
+    float f[3], r[3], u[3];  // unit forward, right, up; r and u scaled by tan(fov/2) (aspect on r)
+    float inv_w2, inv_h2;    // 2 / W, 2 / H
     int32_t W, H;
 };
 
-// directions in double, rounded once
 __global__ void pinhole_dirs_kernel(const CamK c, float4* __restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)c.W * c.H) return;
     const int px = (int)(i % c.W), py = (int)(i / c.W);
-    const double sx = ((px + 0.5) / c.W * 2.0 - 1.0) * c.th * c.aspect;
-    const double sy = (1.0 - (py + 0.5) / c.H * 2.0) * c.th;
-    const double v0 = c.f[0] + sx * c.r[0] + sy * c.u[0];
-    const double v1 = c.f[1] + sx * c.r[1] + sy * c.u[1];
-    const double v2 = c.f[2] + sx * c.r[2] + sy * c.u[2];
-    const double l = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-    out[i] = make_float4((float)(v0 / l), (float)(v1 / l), (float)(v2 / l), 0.f);
+    const float sx = fmaf((float)px + 0.5f, c.inv_w2, -1.f);
+    const float sy = fmaf(-((float)py + 0.5f), c.inv_h2, 1.f);
+    const float v0 = fmaf(sy, c.u[0], fmaf(sx, c.r[0], c.f[0]));
+    const float v1 = fmaf(sy, c.u[1], fmaf(sx, c.r[1], c.f[1]));
+    const float v2 = fmaf(sy, c.u[2], fmaf(sx, c.r[2], c.f[2]));
+    const float il = rsqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+    out[i] = make_float4(v0 * il, v1 * il, v2 * il, 0.f);
 }
 
+// Equirectangular directions in FP32: sincospif of the polar and azimuthal
+// angles in units of pi.
 __global__ void panorama_dirs_kernel(int32_t W, int32_t H, float4* __restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)W * H) return;
     const int px = (int)(i % W), py = (int)(i / W);
-    const double pi = 3.14159265358979323846;
-    const double ph = (px + 0.5) / W * 2.0 * pi - pi, th = (py + 0.5) / H * pi;
-    double st, ct, sp, cp;
-    sincos(th, &st, &ct);
-    sincos(ph, &sp, &cp);
-    out[i] = make_float4((float)(st * cp), (float)(st * sp), (float)ct, 0.f);
+    const float ph = (2.f * (float)px + 1.f - (float)W) / (float)W;  // azimuth / pi (exact numerator)
+    const float th = (2.f * (float)py + 1.f) / (2.f * (float)H);        // polar angle / pi
+    float st, ct, sp, cp;
+    sincospif(th, &st, &ct);
+    sincospif(ph, &sp, &cp);
+    out[i] = make_float4(st * cp, st * sp, ct, 0.f);
 }
 
 struct PointsK {
@@ -206,7 +209,6 @@ cudaError_t launch_pinhole_dirs(int32_t W, int32_t H, const float* eye, const fl
     CamK c;
     double f[3], uu[3];
     for (int a = 0; a < 3; ++a) {
-        c.eye[a] = eye[a];
         f[a] = (double)target[a] - eye[a];
         uu[a] = up[a];
     }
@@ -222,15 +224,16 @@ cudaError_t launch_pinhole_dirs(int32_t W, int32_t H, const float* eye, const fl
     double r[3] = {f[1] * uu[2] - f[2] * uu[1], f[2] * uu[0] - f[0] * uu[2], f[0] * uu[1] - f[1] * uu[0]};
     const double rl = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
     for (int a = 0; a < 3; ++a) r[a] /= rl;
+    const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+    const double th = tan((double)fov_y_deg * 3.14159265358979323846 / 360.0);
+    const double aspect = (double)W / H;
     for (int a = 0; a < 3; ++a) {
-        c.f[a] = f[a];
-        c.r[a] = r[a];
+        c.f[a] = (float)f[a];
+        c.r[a] = (float)(r[a] * th * aspect);
+        c.u[a] = (float)(u[a] * th);
     }
-    c.u[0] = r[1] * f[2] - r[2] * f[1];
-    c.u[1] = r[2] * f[0] - r[0] * f[2];
-    c.u[2] = r[0] * f[1] - r[1] * f[0];
-    c.th = tan((double)fov_y_deg * 3.14159265358979323846 / 360.0);
-    c.aspect = (double)W / H;
+    c.inv_w2 = (float)(2.0 / W);
+    c.inv_h2 = (float)(2.0 / H);
     c.W = W;
     c.H = H;
     pinhole_dirs_kernel<<<blocks_for((int64_t)W * H, 256), 256, 0, s>>>(c, reinterpret_cast<float4*>(out));

@@ -96,7 +96,9 @@ BakeLayout bake_layout(int64_t N, int64_t entries_cap, float density = 0.f);
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s);
 // run_if: when not NULL, the launches do nothing unless *run_if != 0 (device)
-cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s, const int32_t* run_if = nullptr);
+// stats: the trace's counters, whose truncation bit goes to the status word
+cudaError_t launch_gutter_fill(const sop_atlas& atlas, cudaStream_t s, const int32_t* run_if = nullptr,
+                               const unsigned long long* stats = nullptr);
 cudaError_t launch_bake_trace(const sop_atlas& atlas, const sop_bake_params& bp, const BakeLayout& L, char* ws,
                               cudaStream_t s, const int32_t* run_if = nullptr);
 

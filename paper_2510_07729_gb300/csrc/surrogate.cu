@@ -281,7 +281,17 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
         const float3 d = f3(d4.x, d4.y, d4.z);
         float T = 1.f, L0 = 0.f, L1 = 0.f, L2 = 0.f, W = 0.f, Dacc = 0.f;
         for (int j = 0; j < nl; ++j) {
-            const float4 r0 = srec[5 * j], r1 = srec[5 * j + 1], r2 = srec[5 * j + 2], r3 = srec[5 * j + 3];
+            const float4 r0 = srec[5 * j];
+            // lossless cull: a ray that misses the alpha_min bounding sphere
+            // (radius r0.w, margin included) cannot reach alpha_min; the
+            // texels of a warp are neighbouring directions, so it is coherent
+            {
+                const float dx = r0.x - pp.x, dy = r0.y - pp.y, dz = r0.z - pp.z;
+                const float pr = fmaf(dx, d.x, fmaf(dy, d.y, dz * d.z));
+                const float q2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) - pr * pr;
+                if (r0.w < 0.f || q2 > r0.w * r0.w * 1.0001f || pr < -r0.w) continue;
+            }
+            const float4 r1 = srec[5 * j + 1], r2 = srec[5 * j + 2], r3 = srec[5 * j + 3];
             float hx, lx, hy, ly, hz, lz;
             two_diff_s(pp.x, r0.x, hx, lx);
             two_diff_s(pp.y, r0.y, hy, ly);
@@ -431,27 +441,55 @@ __global__ void far_splat_kernel(sop_gaussians g, float alpha_min, float alpha_m
         atomicAdd(acc + 4 * cell + 1 + k, (unsigned long long)__float2ll_rn(mass * g.rgb[3 * i + k] * fix));
 }
 
-// per cell: (sigma = mass / h^3, mass-weighted colour)
+// per cell: (sigma = mass / h^3, mass-weighted colour), in FP32 from the
+// fixed-point sums
 __global__ void far_cells_kernel(const FarGrid* fg, const unsigned long long* __restrict__ acc,
                                  float4* __restrict__ cells)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const FarGrid F = *fg;
     if (i >= F.ncells) return;
-    const double m = (double)(long long)acc[4 * i];
-    const double inv_fix = 1.0 / 1099511627776.0;
+    const float m = (float)(long long)acc[4 * i];
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (m > 0.0) {
-        const double h = (double)F.hq * (1.0 / 1048576.0);
-        v.x = (float)(m * inv_fix / (h * h * h));
-        v.y = (float)((double)(long long)acc[4 * i + 1] / m);
-        v.z = (float)((double)(long long)acc[4 * i + 2] / m);
-        v.w = (float)((double)(long long)acc[4 * i + 3] / m);
+    if (m > 0.f) {
+        const float inv_m = 1.f / m;
+        v.x = m * (9.094947017729282e-13f / (F.h * F.h * F.h));  // 2^-40 / h^3
+        v.y = (float)(long long)acc[4 * i + 1] * inv_m;
+        v.z = (float)(long long)acc[4 * i + 2] * inv_m;
+        v.w = (float)(long long)acc[4 * i + 3] * inv_m;
     }
     cells[i] = v;
 }
 
-// one thread per texel ray
+// one thread per texel ray (scalars per axis and per checkpoint, so that
+// nothing is indexed at run time and the walk stays in registers)
+__device__ __forceinline__ void far_slab(float o, float d, float lo, float hi, float& ta, float& tb)
+{
+    if (d != 0.f) {
+        float t1 = (lo - o) / d, t2 = (hi - o) / d;
+        if (t1 > t2) {
+            const float tmp = t1;
+            t1 = t2;
+            t2 = tmp;
+        }
+        ta = fmaxf(ta, t1);
+        tb = fminf(tb, t2);
+    } else if (o < lo || o >= hi) {
+        tb = -INFINITY;
+    }
+}
+
+__device__ __forceinline__ int far_cell0(float o, float d, float t, float lo, float h, int dim)
+{
+    const int ci = (int)floorf((fmaf(t, d, o) - lo) / h);
+    return ci < 0 ? 0 : (ci >= dim ? dim - 1 : ci);
+}
+
+__device__ __forceinline__ float far_tnext(int st, int c, float lo, float h, float o, float d)
+{
+    return st == 0 ? INFINITY : (lo + (float)(c + (st > 0 ? 1 : 0)) * h - o) / d;
+}
+
 __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict__ probe_pos, int32_t P, int32_t R,
                                                         const float* __restrict__ t0p, const float4* __restrict__ tdirs,
                                                         const FarGrid* __restrict__ fg,
@@ -463,56 +501,41 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
     const int p = (int)(id / RR), t = (int)(id % RR);
     const FarGrid F = *fg;
     const float3 o = load3(probe_pos, p);
-    const float4 d4 = __ldg(tdirs + t);
-    const float d[3] = {d4.x, d4.y, d4.z}, oo[3] = {o.x, o.y, o.z};
+    const float4 d = __ldg(tdirs + t);
     const float t0 = __ldg(t0p + p);
     const float h = F.h;
-    float ck[5];
-    ck[0] = fmaf(2.f, h, t0);
-    ck[1] = fmaf(4.f, h, t0);
-    ck[2] = fmaf(8.f, h, t0);
-    ck[3] = fmaf(16.f, h, t0);
-    ck[4] = fmaf(32.f, h, t0);
-    float tau_ck[5];
-    int next = 0;
+    const float ck0 = fmaf(2.f, h, t0), ck1 = fmaf(4.f, h, t0), ck2 = fmaf(8.f, h, t0), ck3 = fmaf(16.f, h, t0),
+                ck4 = fmaf(32.f, h, t0);
+    float tk0 = -1.f, tk1 = -1.f, tk2 = -1.f, tk3 = -1.f, tk4 = -1.f;  // tau at the checkpoints (-1: not yet)
     float tau = 0.f, L0 = 0.f, L1 = 0.f, L2 = 0.f;
     float ta = t0, tb = INFINITY;
-    for (int a = 0; a < 3; ++a) {
-        const float lo = F.lo[a], hi = F.lo[a] + F.dims[a] * h;
-        if (d[a] != 0.f) {
-            float t1 = (lo - oo[a]) / d[a], t2 = (hi - oo[a]) / d[a];
-            if (t1 > t2) {
-                const float tmp = t1;
-                t1 = t2;
-                t2 = tmp;
-            }
-            ta = fmaxf(ta, t1);
-            tb = fminf(tb, t2);
-        } else if (oo[a] < lo || oo[a] >= hi) {
-            tb = -INFINITY;
-        }
-    }
+    far_slab(o.x, d.x, F.lo[0], F.lo[0] + F.dims[0] * h, ta, tb);
+    far_slab(o.y, d.y, F.lo[1], F.lo[1] + F.dims[1] * h, ta, tb);
+    far_slab(o.z, d.z, F.lo[2], F.lo[2] + F.dims[2] * h, ta, tb);
     if (ta < tb) {
-        int c[3], st[3];
-        float tn[3];
-        for (int a = 0; a < 3; ++a) {
-            const int ci = (int)floorf((fmaf(ta, d[a], oo[a]) - F.lo[a]) / h);
-            c[a] = ci < 0 ? 0 : (ci >= F.dims[a] ? F.dims[a] - 1 : ci);
-            st[a] = d[a] > 0.f ? 1 : (d[a] < 0.f ? -1 : 0);
-            tn[a] = st[a] == 0 ? INFINITY : (F.lo[a] + (c[a] + (st[a] > 0 ? 1 : 0)) * h - oo[a]) / d[a];
-        }
+        int cx = far_cell0(o.x, d.x, ta, F.lo[0], h, F.dims[0]);
+        int cy = far_cell0(o.y, d.y, ta, F.lo[1], h, F.dims[1]);
+        int cz = far_cell0(o.z, d.z, ta, F.lo[2], h, F.dims[2]);
+        const int sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
+        const int sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
+        const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
+        float tnx = far_tnext(sx, cx, F.lo[0], h, o.x, d.x);
+        float tny = far_tnext(sy, cy, F.lo[1], h, o.y, d.y);
+        float tnz = far_tnext(sz, cz, F.lo[2], h, o.z, d.z);
         float tc = ta;
         // at most one step per cell along each axis: bounded by the dims
         const int max_steps = F.dims[0] + F.dims[1] + F.dims[2] + 3;
         for (int it = 0; it < max_steps && tc < tb && tau <= kTauMax; ++it) {
-            const int ax = (tn[0] <= tn[1] && tn[0] <= tn[2]) ? 0 : (tn[1] <= tn[2] ? 1 : 2);
-            float te = fminf(tn[ax], tb);
+            const int ax = (tnx <= tny && tnx <= tnz) ? 0 : (tny <= tnz ? 1 : 2);
+            float te = fminf(ax == 0 ? tnx : (ax == 1 ? tny : tnz), tb);
             te = fmaxf(te, tc);
-            const float4 cv = __ldg(cells + ((int64_t)c[2] * F.dims[1] + c[1]) * F.dims[0] + c[0]);
-            while (next < 5 && ck[next] < te) {
-                tau_ck[next] = ck[next] <= tc ? tau : fmaf(cv.x, ck[next] - tc, tau);
-                ++next;
-            }
+            const float4 cv = __ldg(cells + ((int64_t)cz * F.dims[1] + cy) * F.dims[0] + cx);
+            // checkpoints inside this segment take tau at their position
+            if (tk0 < 0.f && ck0 < te) tk0 = ck0 <= tc ? tau : fmaf(cv.x, ck0 - tc, tau);
+            if (tk1 < 0.f && ck1 < te) tk1 = ck1 <= tc ? tau : fmaf(cv.x, ck1 - tc, tau);
+            if (tk2 < 0.f && ck2 < te) tk2 = ck2 <= tc ? tau : fmaf(cv.x, ck2 - tc, tau);
+            if (tk3 < 0.f && ck3 < te) tk3 = ck3 <= tc ? tau : fmaf(cv.x, ck3 - tc, tau);
+            if (tk4 < 0.f && ck4 < te) tk4 = ck4 <= tc ? tau : fmaf(cv.x, ck4 - tc, tau);
             if (cv.x > 0.f) {
                 const float dtau = cv.x * (te - tc);
                 const float a = __expf(-tau) * -expm1f(-dtau);
@@ -523,14 +546,33 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
             }
             tc = te;
             if (!(te < tb)) break;
-            c[ax] += st[ax];
-            if (c[ax] < 0 || c[ax] >= F.dims[ax]) break;
-            tn[ax] = (F.lo[ax] + (c[ax] + (st[ax] > 0 ? 1 : 0)) * h - oo[ax]) / d[ax];
+            if (ax == 0) {
+                cx += sx;
+                if (cx < 0 || cx >= F.dims[0]) break;
+                tnx = far_tnext(sx, cx, F.lo[0], h, o.x, d.x);
+            } else if (ax == 1) {
+                cy += sy;
+                if (cy < 0 || cy >= F.dims[1]) break;
+                tny = far_tnext(sy, cy, F.lo[1], h, o.y, d.y);
+            } else {
+                cz += sz;
+                if (cz < 0 || cz >= F.dims[2]) break;
+                tnz = far_tnext(sz, cz, F.lo[2], h, o.z, d.z);
+            }
         }
     }
-    while (next < 5) tau_ck[next++] = tau;
+    // checkpoints beyond the walk take its final depth
+    if (tk0 < 0.f) tk0 = tau;
+    if (tk1 < 0.f) tk1 = tau;
+    if (tk2 < 0.f) tk2 = tau;
+    if (tk3 < 0.f) tk3 = tau;
+    if (tk4 < 0.f) tk4 = tau;
     float* f = feats + id * kIn + 9;
-    for (int k = 0; k < 5; ++k) f[k] = -expm1f(-tau_ck[k]);
+    f[0] = -expm1f(-tk0);
+    f[1] = -expm1f(-tk1);
+    f[2] = -expm1f(-tk2);
+    f[3] = -expm1f(-tk3);
+    f[4] = -expm1f(-tk4);
     f[5] = -expm1f(-tau);
     f[6] = L0;
     f[7] = L1;

@@ -43,6 +43,15 @@ def params(seed=0):
     return mlp.flatten(w).astype(np.float32)
 
 
+def check_near(gf, of, ok, what):
+    """O_n, L_n, W_n at the FP32 bound; D_n with the bake's depth allowance:
+    a t* next to the probe (B ~ 0) cannot be resolved better than a few ulp
+    of the coordinates it comes from."""
+    cols = [3, 4, 5, 6, 8]
+    assert_close(gf[..., cols][ok], of[..., cols][ok], what=what)
+    assert_close(gf[..., 7][ok], of[..., 7][ok], what=what + " D_n", absolute=4 * 2.0 ** -24 * 4.0)
+
+
 def test_features_match_oracle(sop, orc, scene):
     g = scene["gauss"]
     pp = scene["probe_pos"]
@@ -52,12 +61,11 @@ def test_features_match_oracle(sop, orc, scene):
     gf, lst = gf.cpu().numpy(), lst.cpu().numpy()
     of, flags, olst, t0 = orc.surr_features(g, pp, R, R_NEAR)
     assert np.array_equal(lst, olst)  # the near lists: exact integer decisions
-    assert (olst[:, -1] >= 0).mean() > 0.5  # most lists are full (256 within r_near)
+    assert (olst >= 0).sum(1).mean() > 30  # (this cut-down scene's lists are short)
     assert np.array_equal(gf[..., :3], of[..., :3].astype(np.float32))
     ok = flags == 0
     assert ok.mean() > 0.98
-    near_g, near_o = gf[..., 3:9][ok], of[..., 3:9][ok]
-    assert_close(near_g, near_o, what="near field")
+    check_near(gf, of, ok, "near field")
     # far field: FP32 march against FP64; the start t0 (a float32 distance)
     # and the cell walk's rounding move tau by a few ulp of its magnitude
     assert_close(gf[..., 9:], of[..., 9:], rtol=2e-5, what="far field")
@@ -75,8 +83,9 @@ def test_features_full_scene_sampled(sop, orc):
     of, flags, olst, _ = orc.surr_features(g, pp[sel], R, R_NEAR)
     gf, lst = gf.cpu().numpy()[sel], lst.cpu().numpy()[sel]
     assert np.array_equal(lst, olst)
+    assert (olst[:, -1] >= 0).mean() > 0.5  # most lists are full (256 within r_near)
     ok = flags == 0
-    assert_close(gf[..., 3:9][ok], of[..., 3:9][ok], what="near field (object scene)")
+    check_near(gf, of, ok, "near field (object scene)")
     assert_close(gf[..., 9:], of[..., 9:], rtol=2e-5, what="far field (object scene)")
 
 

@@ -119,6 +119,13 @@ def test_noalloc_matches_oracle(orc, mode, case):
     M = len(c["x"])
     ro, ri, rw = orc.query_shade(*[c[k] for k in keys], c["probe_pos"], maps["rgb"], maps["occ"], c["env"], K, S,
                                  mode=mode, dirs=None if dirs is None else dirs.astype(np.float64), radius=radius)
+    # each direction carries an FP32 angular error of a few ulp; the
+    # oracle's sensitivity of each output to it is the allowance, as in the
+    # other query parity tests (it matters for the sharp lobes of this
+    # environment along a caller's arbitrary directions)
+    kap = orc.query_shade_sensitivity(*[c[k] for k in keys], c["probe_pos"], maps["rgb"], maps["occ"], c["env"], K,
+                                      S, mode=mode, dirs=None if dirs is None else dirs.astype(np.float64),
+                                      radius=radius)
     if case == "dirs_radius":
         found = (ri >= 0).sum(1)
         assert (found < K).mean() > 0.2 and (found == 0).any()
@@ -131,4 +138,4 @@ def test_noalloc_matches_oracle(orc, mode, case):
         torch.cuda.synchronize()
         assert np.array_equal(idx.cpu().numpy(), ri)
         assert_close(w.cpu().numpy(), rw, what="noalloc weights vs oracle")
-        assert_close(out.cpu().numpy(), ro, what="noalloc vs oracle")
+        assert_close(out.cpu().numpy(), ro, what="noalloc vs oracle", absolute=kap)
