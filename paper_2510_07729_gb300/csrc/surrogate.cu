@@ -610,30 +610,58 @@ constexpr int kLDX = 40;   // row stride of the 32-wide (padded) feature tile
 constexpr int kCH = 128;   // samples per chunk (8 warps x 16 rows)
 
 // out[16 rows of this warp] = relu(in[rows] W^T + b) in bf16: in is
-// [kCH][LDI] with KD columns, W is [64 out][LDW] with KD columns.
+// [kCH][LDI] with KD columns, W is [64 out][LDW] with KD columns. The A
+// fragments of a k-step are loaded once and used for all 8 n-tiles.
 template <int KD, int LDI, int LDW>
 __device__ __forceinline__ void layer_fwd(const uint16_t* in, const uint16_t* W, const float* bias, uint16_t* out,
                                           int row0, int lane)
 {
     const int g = lane >> 2, t = lane & 3;
+    float c[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+#pragma unroll
+    for (int k0 = 0; k0 < KD; k0 += 16) {
+        const uint32_t a[4] = {ld2(in + (row0 + g) * LDI + k0 + 2 * t), ld2(in + (row0 + g + 8) * LDI + k0 + 2 * t),
+                               ld2(in + (row0 + g) * LDI + k0 + 8 + 2 * t),
+                               ld2(in + (row0 + g + 8) * LDI + k0 + 8 + 2 * t)};
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const uint32_t b[2] = {ld2(W + (nt * 8 + g) * LDW + k0 + 2 * t), ld2(W + (nt * 8 + g) * LDW + k0 + 8 + 2 * t)};
+            mma_bf16(c[nt], a, b);
+        }
+    }
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k0 = 0; k0 < KD; k0 += 16) {
-            const uint32_t a[4] = {ld2(in + (row0 + g) * LDI + k0 + 2 * t), ld2(in + (row0 + g + 8) * LDI + k0 + 2 * t),
-                                   ld2(in + (row0 + g) * LDI + k0 + 8 + 2 * t),
-                                   ld2(in + (row0 + g + 8) * LDI + k0 + 8 + 2 * t)};
-            const uint32_t b[2] = {ld2(W + (nt * 8 + g) * LDW + k0 + 2 * t), ld2(W + (nt * 8 + g) * LDW + k0 + 8 + 2 * t)};
-            mma_bf16(c, a, b);
-        }
         const int col = nt * 8 + 2 * t;
         const float b0 = bias[col], b1 = bias[col + 1];
-        out[(row0 + g) * kLD + col] = f2bf(fmaxf(c[0] + b0, 0.f));
-        out[(row0 + g) * kLD + col + 1] = f2bf(fmaxf(c[1] + b1, 0.f));
-        out[(row0 + g + 8) * kLD + col] = f2bf(fmaxf(c[2] + b0, 0.f));
-        out[(row0 + g + 8) * kLD + col + 1] = f2bf(fmaxf(c[3] + b1, 0.f));
+        *reinterpret_cast<uint32_t*>(out + (row0 + g) * kLD + col) =
+            pk(f2bf(fmaxf(c[nt][0] + b0, 0.f)), f2bf(fmaxf(c[nt][1] + b1, 0.f)));
+        *reinterpret_cast<uint32_t*>(out + (row0 + g + 8) * kLD + col) =
+            pk(f2bf(fmaxf(c[nt][2] + b0, 0.f)), f2bf(fmaxf(c[nt][3] + b1, 0.f)));
     }
+}
+
+// y[16 rows of this warp][8] = H3[rows] W4^T + b4 in f32 (W4 padded to 8
+// rows of zeros beyond the 5 outputs): one n-tile, four k-steps
+__device__ __forceinline__ void out_fwd(const uint16_t* H3, const uint16_t* W4b, const float* b4, float* y, int row0,
+                                        int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k0 = 0; k0 < kHid; k0 += 16) {
+        const uint32_t a[4] = {ld2(H3 + (row0 + g) * kLD + k0 + 2 * t), ld2(H3 + (row0 + g + 8) * kLD + k0 + 2 * t),
+                               ld2(H3 + (row0 + g) * kLD + k0 + 8 + 2 * t),
+                               ld2(H3 + (row0 + g + 8) * kLD + k0 + 8 + 2 * t)};
+        const uint32_t b[2] = {ld2(W4b + g * kLD + k0 + 2 * t), ld2(W4b + g * kLD + k0 + 8 + 2 * t)};
+        mma_bf16(c, a, b);
+    }
+    const int col = 2 * t;
+    y[(row0 + g) * 8 + col] = c[0] + b4[col];
+    y[(row0 + g) * 8 + col + 1] = c[1] + b4[col + 1];
+    y[(row0 + g + 8) * 8 + col] = c[2] + b4[col];
+    y[(row0 + g + 8) * 8 + col + 1] = c[3] + b4[col + 1];
 }
 
 // acc[NT n-tiles][4] += D^T H over the chunk's rows: dW[m][n] = sum_s D[s][m]
@@ -758,9 +786,12 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
     uint16_t* sX = sW3 + kHid * kLD;                    // [kCH][kLDX]
     uint16_t* sH1 = sX + kCH * kLDX;                    // [kCH][kLD]
     uint16_t* sH2 = sH1 + kCH * kLD;
-    uint16_t* sH3 = sH2 + kCH * kLD;                    // later D2
-    uint16_t* sD3 = sH3 + kCH * kLD;                    // later D1
-    float* fs = reinterpret_cast<float*>(sD3 + kCH * kLD);
+    // inference keeps two activation buffers (h3 over h1: each warp works on
+    // its own 16 rows); training keeps h1..h3 and the deltas for backward
+    uint16_t* sH3 = TRAIN ? sH2 + kCH * kLD : sH1;     // (train: later D2)
+    uint16_t* sD3 = TRAIN ? sH3 + kCH * kLD : sH2;     // (train: later D1; unused in inference)
+    uint16_t* sW4b = (TRAIN ? sD3 : sH2) + kCH * kLD;   // [8][kLD] (rows 5..7 zero)
+    float* fs = reinterpret_cast<float*>(sW4b + 8 * kLD);
     float* sW4 = fs;                  // [5][64]
     float* sb1 = sW4 + kOut * kHid;   // [64]
     float* sb2 = sb1 + kHid;
@@ -772,6 +803,7 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
     float* gb3 = gb4 + 8;             // [64]
     float* gb2 = gb3 + kHid;
     float* gb1 = gb2 + kHid;
+    float* sY = gb1 + kHid;           // [kCH][8] outputs of the chunk
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int i = tid; i < kHid * kLDX; i += blockDim.x) {
@@ -786,6 +818,10 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
     for (int i = tid; i < kOut * kHid; i += blockDim.x) {
         sW4[i] = bf2f(k.wbf[oW4 + i]);
         if (TRAIN) gW4[i] = 0.f;
+    }
+    for (int i = tid; i < 8 * kLD; i += blockDim.x) {
+        const int r = i / kLD, c = i % kLD;
+        sW4b[i] = (r < kOut && c < kHid) ? k.wbf[oW4 + r * kHid + c] : (uint16_t)0;
     }
     for (int i = tid; i < kHid; i += blockDim.x) {
         sb1[i] = k.master[ob1 + i];
@@ -834,12 +870,13 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
             layer_fwd<kHid, kLD, kLD>(sH1, sW2, sb2, sH2, row0, lane);
             __syncwarp();
             layer_fwd<kHid, kLD, kLD>(sH2, sW3, sb3, sH3, row0, lane);
+            __syncwarp();
+            out_fwd(sH3, sW4b, sb4, sY, row0, lane);
             __syncthreads();
-            // output layer (f32) and its loss gradient / the atlas write
+            // the loss gradient / the atlas write of the outputs
             for (int i = tid; i < kCH * kOut; i += blockDim.x) {
                 const int s = i / kOut, o = i % kOut;
-                float y = sb4[o];
-                for (int j = 0; j < kHid; ++j) y = fmaf(bf2f(sH3[s * kLD + j]), sW4[o * kHid + j], y);
+                const float y = sY[s * 8 + o];
                 const int t = s0 + s;
                 const int64_t ti = p * RS * RS + (int64_t)(t / k.R + 1) * RS + (t % k.R + 1);
                 if (TRAIN) {
@@ -995,10 +1032,10 @@ __global__ void surr_grad_reduce_kernel(const float* __restrict__ part, const fl
     }
 }
 
-size_t surr_mlp_smem()
+size_t surr_mlp_smem(bool train)
 {
-    return sizeof(uint16_t) * (kHid * kLDX + 2 * kHid * kLD + kCH * kLDX + 4 * kCH * kLD) +
-           sizeof(float) * (kOut * kHid + 3 * kHid + 8 + kCH * kOut + kOut * kHid + 8 + 3 * kHid);
+    return sizeof(uint16_t) * (kHid * kLDX + 2 * kHid * kLD + kCH * kLDX + (train ? 4 : 2) * kCH * kLD + 8 * kLD) +
+           sizeof(float) * (kOut * kHid + 3 * kHid + 8 + kCH * kOut + kOut * kHid + 8 + 3 * kHid + kCH * 8);
 }
 
 // batch probe ids of a training step: id i = splitmix64(seed ^ (step 2^32
@@ -1229,7 +1266,7 @@ static unsigned mlp_blocks(int32_t B)
 
 static cudaError_t mlp_launch(bool train, const MlpK& k, unsigned nb, cudaStream_t s)
 {
-    const size_t smem = surr_mlp_smem();
+    const size_t smem = surr_mlp_smem(train);
     if (nb == 0) return cudaSuccess;
     if (train) {
         cudaError_t e = cudaFuncSetAttribute(surr_mlp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
