@@ -46,9 +46,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="compose", choices=["compose", "object", "tiny"])
-    ap.add_argument("--part", default="step", choices=["step", "bake", "query", "compose", "optimize", "deferred"],
-                    help="profiling aid: run only one half (the JSON line then covers that half), or only the "
-                         "1080p composition-frame query")
+    ap.add_argument("--part", default="step",
+                    choices=["step", "bake", "query", "compose", "optimize", "deferred", "surrogate"],
+                    help="profiling aid: run only one half (the JSON line then covers that half), only the "
+                         "1080p composition-frame query, or only the learned rebake (untrained network)")
     ap.add_argument("--probes", type=int, default=0, help="profiling aid: bake only the first N probes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -292,6 +293,35 @@ def frnn_variant(sop, atlas, pargs, env, K, S, mode, out_ref, flush, steps, ppos
     rel = ((out - out_ref).abs().sum() / out_ref.abs().sum()).item()
     return {"radius": radius, "neighbours_mean": round(n_mean, 3), "query_ms": round(ms, 4),
             "query_point_dirs_per_s": round(M * S / (ms * 1e-3), 1), "rel_l1_vs_knn": rel}
+
+
+def rebake_only(sop, dev, flush, steps, warmup, n_probes=0, r_near=0.08):
+    """Profiling aid: the learned rebake of the moved-object scene (its first
+    n_probes probes, all when 0) with an untrained network and the fallback
+    off (tau huge), so that every launch runs features, network and the
+    spot check. The kernels' work does not depend on the weights."""
+    import torch
+    from paper_2510_07729_gb300 import inputs as I
+    mv = I.moved_object()
+    gt = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in mv["gauss"].items()}
+    pp = mv["probe_pos"][:n_probes] if n_probes > 0 else mv["probe_pos"]
+    pp = torch.from_numpy(np.ascontiguousarray(pp)).to(dev)
+    net = sop.Surrogate(I.surrogate_init(0), device=dev, r_near=r_near)
+    out = sop.make_atlas(pp, 16)
+    for _ in range(warmup):
+        net.rebake(gt, out, spot_frac=0.01, tau=1e30, seed=3)
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.rebake(gt, out, spot_frac=0.01, tau=1e30, seed=3)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ts)) if ts else 0.0
+    texels = out.P * out.R * out.R
+    return {"probes": out.P, "ms": round(ms, 4), "texels_per_s": round(texels / (ms * 1e-3), 1) if ms else 0.0}
 
 
 def surrogate_variant(sop, dev, flush, steps, n_scenes=25, train_steps=30000, r_near=0.08):
@@ -890,6 +920,11 @@ def main():
     if args.part == "deferred":
         r = deferred_frame_variant(sop, dev, flush, args.steps)
         print(json.dumps({"metric": "composed deferred frames/s", "value": r["fps"], "unit": "frames/s",
+                          "steps": args.steps, "higher_is_better": True, "detail": r}))
+        return
+    if args.part == "surrogate":
+        r = rebake_only(sop, dev, flush, args.steps, args.warmup, args.probes)
+        print(json.dumps({"metric": "learned rebake texels/s", "value": r["texels_per_s"], "unit": "texels/s",
                           "steps": args.steps, "higher_is_better": True, "detail": r}))
         return
     if args.part == "optimize":

@@ -489,11 +489,12 @@ def surr_grid(gauss, alpha_min=1.0 / 255.0, alpha_max=0.99, G=SURR_G):
 
 
 def surr_features(gauss, probe_pos, R, r_n, alpha_min=1.0 / 255.0, alpha_max=0.99, KN=SURR_KN, G=SURR_G,
-                  near_list=None):
+                  near_list=None, far_sens=False):
     """FP64 texel features [P, R*R, 18] of every probe: the texel direction,
     the near field (O_n, L_n rgb, D_n, W_n) and the far field (1 - exp(-tau)
     at the 5 checkpoints and at the end, L_f rgb). Returns (feats, flags
-    [P, R*R], near list [P, KN], t0 [P])."""
+    [P, R*R], near list [P, KN], t0 [P]), and with far_sens the far march's
+    conditioning [P, R*R] (see surr_far)."""
     pp = _f32(probe_pos)
     P = len(pp)
     if near_list is None:
@@ -507,25 +508,29 @@ def surr_features(gauss, probe_pos, R, r_n, alpha_min=1.0 / 255.0, alpha_max=0.9
     lib().orc_surr_near(C.c_int32(P), _p(pp), C.c_int32(R), _p(mean), _p(scale), _p(quat), _p(op), _p(rgb),
                         _p(lst), C.c_int32(lst.shape[1]), C.c_double(alpha_min), C.c_double(alpha_max), _p(near),
                         _p(flags))
-    far = surr_far(pp, t0, R, *surr_grid(gauss, alpha_min, alpha_max, G))
+    far, sens = surr_far(pp, t0, R, *surr_grid(gauss, alpha_min, alpha_max, G), with_sens=True)
     dirs = np.array([_texel_dir(R, t % R, t // R) for t in range(R * R)])
     feats = np.concatenate([np.broadcast_to(dirs, (P, R * R, 3)), near, far], axis=-1)
-    return feats, flags, lst, t0
+    return (feats, flags, lst, t0, sens) if far_sens else (feats, flags, lst, t0)
 
 
-def surr_far(probe_pos, t0, R, qlo, hq, dims, mass, col):
+def surr_far(probe_pos, t0, R, qlo, hq, dims, mass, col, with_sens=False):
     """The far-field features [P, R*R, 9] of every texel of the probes, from
-    t0 [P] on, through a grid (qlo, hq, dims, fixed-point mass, col)."""
+    t0 [P] on, through a grid (qlo, hq, dims, fixed-point mass, col). With
+    with_sens, also the march's conditioning [P, R*R]: how far tau can move
+    when its cell boundary times are taken in FP32 (sum over the segments of
+    sigma times the rounding scale of their two ends)."""
     pp = _f32(probe_pos)
     far = np.empty((len(pp), R * R, 9))
+    sens = np.empty((len(pp), R * R)) if with_sens else None
     t0 = np.ascontiguousarray(t0, np.float64)
     qlo = np.ascontiguousarray(qlo, np.int64)
     dims = np.ascontiguousarray(dims, np.int32)
     mass = np.ascontiguousarray(mass, np.int64)
     col = np.ascontiguousarray(col, np.int64)
     lib().orc_surr_far(C.c_int32(len(pp)), _p(pp), _p(t0), C.c_int32(R), _p(qlo), C.c_int64(int(hq)), _p(dims),
-                       _p(mass), _p(col), _p(far))
-    return far
+                       _p(mass), _p(col), _p(far), _p(sens) if with_sens else None)
+    return (far, sens) if with_sens else far
 
 
 def _texel_dir(R, i, j):

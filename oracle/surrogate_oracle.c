@@ -42,6 +42,7 @@ void orc_texel_dir(int R, int i, int j, double* d);
 #endif
 static const double kQ = 1048576.0; /* 2^20 */
 static const double kFix = 1099511627776.0; /* 2^40 */
+static const double kEps32 = 5.9604644775390625e-08; /* 2^-24, the FP32 unit roundoff */
 
 static int64_t quant(float v) { return (int64_t)nearbyint((double)v * kQ); }
 
@@ -183,9 +184,17 @@ void orc_surr_grid_fill(int64_t N, const float* mean, const float* scale, const 
 }
 
 /* Far field of every texel of P probes, from t0[p] on. out [P][R*R][9] =
- * (1 - exp(-tau) at t0 + h {2, 4, 8, 16, 32} and at the end, L_f rgb). */
+ * (1 - exp(-tau) at t0 + h {2, 4, 8, 16, 32} and at the end, L_f rgb).
+ * sens [P][R*R] (may be NULL): the march's conditioning, for tests of an
+ * FP32 march. A boundary time (B - o_a) / d_a taken in FP32 (B the cell
+ * plane's coordinate) is off by about 2^-24 (|B| + |o_a|) / |d_a| + 2^-24 |t|,
+ * and a segment [t, te] of a cell of extinction sigma moves tau by sigma
+ * times the errors of its two ends: sens = sum of sigma (e(t) + e(te)) over
+ * the segments, with e = 2^-24 ((|B| + |o_a|) / |d_a| + 2 |t|). A short
+ * segment clipped off a dense cell's corner is the case it covers: tau is
+ * sigma times a small difference of two large times. */
 void orc_surr_far(int32_t P, const float* probe_pos, const double* t0, int32_t R, const int64_t* qlo, int64_t hq,
-                  const int32_t* dims, const int64_t* mass_q, const int64_t* col_q, double* out)
+                  const int32_t* dims, const int64_t* mass_q, const int64_t* col_q, double* out, double* sens)
 {
     static const double mult[5] = {2, 4, 8, 16, 32};
     const int RR = R * R;
@@ -208,29 +217,44 @@ void orc_surr_far(int32_t P, const float* probe_pos, const double* t0, int32_t R
             double tau = 0.0, L[3] = {0, 0, 0};
             /* the part of the ray inside the grid box, from t0 on */
             double ta = t0[p], tb = INFINITY;
+            double pm_in = 0.0, pm_out = 0.0, s_out = 0.0; /* conditioning (entry, exit planes; total) */
             for (int a = 0; a < 3; ++a) {
                 if (d[a] != 0.0) {
                     double t1 = (lo[a] - o[a]) / d[a], t2 = (hi[a] - o[a]) / d[a];
+                    double B1 = lo[a], B2 = hi[a];
                     if (t1 > t2) {
                         const double tmp = t1;
                         t1 = t2;
                         t2 = tmp;
+                        B1 = hi[a];
+                        B2 = lo[a];
                     }
-                    if (t1 > ta) ta = t1;
-                    if (t2 < tb) tb = t2;
+                    if (t1 > ta) {
+                        ta = t1;
+                        pm_in = (fabs(B1) + fabs(o[a])) / fabs(d[a]);
+                    }
+                    if (t2 < tb) {
+                        tb = t2;
+                        pm_out = (fabs(B2) + fabs(o[a])) / fabs(d[a]);
+                    }
                 } else if (o[a] < lo[a] || o[a] >= hi[a]) {
                     tb = -INFINITY;
                 }
             }
             if (ta < tb) {
                 int c[3], st[3];
-                double tnext[3];
+                double tnext[3], pm[3];
                 for (int a = 0; a < 3; ++a) {
                     int ci = (int)floor((o[a] + ta * d[a] - lo[a]) / h);
                     c[a] = ci < 0 ? 0 : (ci >= dims[a] ? dims[a] - 1 : ci);
                     st[a] = d[a] > 0.0 ? 1 : (d[a] < 0.0 ? -1 : 0);
-                    tnext[a] = st[a] == 0 ? INFINITY : (lo[a] + (c[a] + (st[a] > 0)) * h - o[a]) / d[a];
+                    const double B = lo[a] + (c[a] + (st[a] > 0)) * h;
+                    tnext[a] = st[a] == 0 ? INFINITY : (B - o[a]) / d[a];
+                    pm[a] = st[a] == 0 ? 0.0 : (fabs(B) + fabs(o[a])) / fabs(d[a]);
                 }
+                /* conditioning: the rounding scale of the segment's start
+                 * (the walk's start: the box's entry plane, or t0) */
+                double e_start = kEps32 * (pm_in + 2.0 * fabs(ta)), s_acc = 0.0;
                 double t = ta;
                 while (t < tb && tau <= 20.0) {
                     int ax = 0;
@@ -238,6 +262,7 @@ void orc_surr_far(int32_t P, const float* probe_pos, const double* t0, int32_t R
                     if (tnext[2] < tnext[ax]) ax = 2;
                     double te = tnext[ax] < tb ? tnext[ax] : tb;
                     if (te < t) te = t;
+                    const double e_end = kEps32 * ((tnext[ax] < tb ? pm[ax] : pm_out) + 2.0 * fabs(te));
                     const int64_t cell = ((int64_t)c[2] * dims[1] + c[1]) * dims[0] + c[0];
                     const double m = (double)mass_q[cell] / kFix;
                     const double sig = m / h3;
@@ -245,6 +270,8 @@ void orc_surr_far(int32_t P, const float* probe_pos, const double* t0, int32_t R
                         tau_ck[next] = ck[next] <= t ? tau : tau + sig * (ck[next] - t);
                         ++next;
                     }
+                    s_acc += sig * (e_start + e_end);
+                    e_start = e_end;
                     if (m > 0.0) {
                         const double dtau = sig * (te - t);
                         const double a = exp(-tau) * (1.0 - exp(-dtau));
@@ -255,9 +282,13 @@ void orc_surr_far(int32_t P, const float* probe_pos, const double* t0, int32_t R
                     if (!(te < tb)) break;
                     c[ax] += st[ax];
                     if (c[ax] < 0 || c[ax] >= dims[ax]) break;
-                    tnext[ax] = (lo[ax] + (c[ax] + (st[ax] > 0)) * h - o[ax]) / d[ax];
+                    const double B = lo[ax] + (c[ax] + (st[ax] > 0)) * h;
+                    tnext[ax] = (B - o[ax]) / d[ax];
+                    pm[ax] = (fabs(B) + fabs(o[ax])) / fabs(d[ax]);
                 }
+                s_out = s_acc;
             }
+            if (sens) sens[(size_t)p * RR + t] = s_out;
             while (next < 5) tau_ck[next++] = tau;
             tau_ck[5] = tau;
             double* out_t = out + ((size_t)p * RR + t) * 9;

@@ -170,3 +170,53 @@ def test_march_single_cell_is_sigma_times_chord(orc):
         assert far[t, 5] == pytest.approx(1 - np.exp(-m_exact * chord), rel=1e-9, abs=1e-14)
         hit += chord > 0
     assert hit > 0
+
+
+def test_march_conditioning_single_cell(orc):
+    """The far march's conditioning (with_sens) for rays through one dense
+    cell: sigma times the FP32 rounding scales of the entry and exit times,
+    e(t) = 2^-24 ((|B| + |o_a|) / |d_a| + 2 |t|) with B the crossed face's
+    coordinate; zero for rays that miss the cell. And it covers what it is
+    for: the chord taken with FP32 boundary times (B - o_a) / d_a moves tau
+    by less than it."""
+    hq = 1 << 16  # h = 1/16
+    dims = (8, 8, 8)
+    h = hq / Q
+    mass = np.zeros(512, np.int64)
+    col = np.zeros((512, 3), np.int64)
+    c = (3, 4, 5)
+    cell = (c[2] * 8 + c[1]) * 8 + c[0]
+    mass[cell] = int(round(40.0 * h ** 3 * FIX))
+    p = np.array([[0.21, 0.28, 0.2]], np.float32)
+    R = 16
+    far, sens = orc.surr_far(p, np.array([0.0]), R, np.zeros(3, np.int64), hq, np.array(dims), mass, col,
+                             with_sens=True)
+    sig = mass[cell] / FIX / h ** 3
+    eps = 2.0 ** -24
+    o = p[0].astype(np.float64)
+    lo = np.array(c) * h
+    hi = lo + h
+    hit = 0
+    for t in range(R * R):
+        d = orc._texel_dir(R, t % R, t // R)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1 = (lo - o) / d
+            t2 = (hi - o) / d
+        tin, tout = np.minimum(t1, t2), np.maximum(t1, t2)
+        a_in, a_out = int(np.argmax(tin)), int(np.argmin(tout))
+        ta, tb = tin[a_in], tout[a_out]
+        if not tb > max(ta, 0.0):
+            assert sens[0, t] == 0.0
+            continue
+        hit += 1
+        B_in = lo[a_in] if d[a_in] > 0 else hi[a_in]
+        B_out = hi[a_out] if d[a_out] > 0 else lo[a_out]
+        e_in = eps * ((abs(B_in) + abs(o[a_in])) / abs(d[a_in]) + 2 * abs(ta))
+        e_out = eps * ((abs(B_out) + abs(o[a_out])) / abs(d[a_out]) + 2 * abs(tb))
+        assert sens[0, t] == pytest.approx(sig * (e_in + e_out), rel=1e-12)
+        # the chord from FP32 boundary times
+        d32 = d.astype(np.float32)
+        ta32 = (np.float32(B_in) - p[0][a_in]) / d32[a_in]
+        tb32 = (np.float32(B_out) - p[0][a_out]) / d32[a_out]
+        assert abs(sig * (float(tb32) - float(ta32)) - sig * (tb - ta)) <= sens[0, t]
+    assert hit >= 8

@@ -13,7 +13,10 @@ Two derived allowances are added where the arithmetic requires them:
     1e-5 only for a rough HDR environment (neighbouring texels differ ~10x);
   - bake depth: 4 ulp of the scene extent, because t* of a Gaussian next to
     the probe cannot be resolved better than the FP32 coordinates it comes
-    from.
+    from;
+  - surrogate far field: the march's conditioning (oracle.surr_far with
+    with_sens), sigma times the FP32 rounding of each cell boundary time,
+    summed over the segments.
 """
 import numpy as np
 
