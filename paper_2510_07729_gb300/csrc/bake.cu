@@ -23,6 +23,7 @@
 // Gaussians.
 #include <stdlib.h>
 
+#include "scan.cuh"
 #include "sop_device.cuh"
 #include "sop_internal.h"
 
@@ -65,6 +66,7 @@ BakeLayout bake_layout(int64_t N, int64_t entries_cap, float density)
     L.rec = o;        o = align256(o + sizeof(GRec) * (size_t)(N > 0 ? N : 1));
     L.cell_start = o; o = align256(o + sizeof(int32_t) * (size_t)(L.cells_cap + 1));
     L.cell_cnt = o;   o = align256(o + sizeof(int32_t) * (size_t)L.cells_cap);
+    L.scan = o;       o = align256(o + sizeof(long long) * scan_scratch_count(L.cells_cap));
     L.dirs = o;       o = align256(o + sizeof(float4) * (size_t)kMaxR * kMaxR);
     L.ent = o;        o = align256(o + sizeof(uint4) * (size_t)L.entries_cap);
     L.total = o;
@@ -287,43 +289,20 @@ __global__ void bin_count_kernel(int64_t N, const GRec* __restrict__ rec, const 
 // Exclusive scan of the cell counts in one CTA; total into grid->n_entries,
 // and grid->fits = 1 when the total fits the entry capacity (an attempt
 // after the first that fits marks the status word: the grid was coarsened).
-__global__ void __launch_bounds__(1024) bin_scan_kernel(GaussGrid* gridp, int32_t* __restrict__ cell_cnt,
-                                                         int32_t* __restrict__ cell_start, int64_t entries_cap,
-                                                         unsigned int* status)
-{
-    __shared__ int64_t s_part[1024];
-    if (gridp->fits) return;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int nc = gridp->ncells;
-    const int chunk = (nc + nt - 1) / nt;
-    const int c0 = tid * chunk, c1 = min(nc, c0 + chunk);
-    int64_t sum = 0;
-    for (int c = c0; c < c1; ++c) sum += cell_cnt[c];
-    s_part[tid] = sum;
-    __syncthreads();
-    for (int off = 1; off < nt; off <<= 1) {
-        int64_t v = (tid >= off) ? s_part[tid - off] : 0;
-        __syncthreads();
-        s_part[tid] += v;
-        __syncthreads();
+// After the count pass of a binning attempt: whether the cell lists fit the
+// entry capacity (the fill pass and later attempts read it).
+struct BinScanFinal {
+    GaussGrid* grid;
+    int64_t entries_cap;
+    unsigned int* status;
+    __device__ void operator()(long long tot) const
+    {
+        const bool fit = tot <= entries_cap && tot < INT32_MAX;
+        grid->n_entries = (int32_t)(tot < INT32_MAX ? tot : INT32_MAX);
+        grid->fits = fit ? 1 : 0;
+        if (fit && grid->level > 0 && status) atomicOr(status, SOP_DEVSTAT_GRID_COARSENED);
     }
-    const int64_t tot = s_part[nt - 1];
-    const bool fit = tot <= entries_cap && tot < INT32_MAX;
-    int64_t run = s_part[tid] - sum;
-    for (int c = c0; c < c1; ++c) {
-        const int32_t v = cell_cnt[c];
-        cell_start[c] = (int32_t)(run < INT32_MAX ? run : INT32_MAX);
-        run += v;
-        cell_cnt[c] = 0;
-    }
-    __syncthreads();
-    if (tid == nt - 1) {
-        cell_start[nc] = (int32_t)(tot < INT32_MAX ? tot : INT32_MAX);
-        gridp->n_entries = (int32_t)(tot < INT32_MAX ? tot : INT32_MAX);
-        gridp->fits = fit ? 1 : 0;
-        if (fit && gridp->level > 0 && status) atomicOr(status, SOP_DEVSTAT_GRID_COARSENED);
-    }
-}
+};
 
 __global__ void bin_fill_kernel(int64_t N, const GRec* __restrict__ rec, const GaussGrid* __restrict__ gridp,
                                 const int32_t* __restrict__ cell_start, int32_t* __restrict__ cell_cnt,
@@ -1028,7 +1007,13 @@ cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeL
     for (int a = 0; a < kBinAttempts; ++a) {
         grid_setup_kernel<<<1, 1024, 0, s>>>(bbox, caps[a], a, grid, ccnt);
         if (g.n > 0) bin_count_kernel<<<nb, bs, 0, s>>>(g.n, rec, grid, ccnt);
-        bin_scan_kernel<<<1, 1024, 0, s>>>(grid, ccnt, cstart, L.entries_cap, status);
+        ScanArgs sa;
+        sa.n = &grid->ncells;
+        sa.skip = &grid->fits;
+        sa.cnt = ccnt;
+        sa.start = cstart;
+        sa.scratch = reinterpret_cast<long long*>(ws + L.scan);
+        launch_scan(sa, caps[a], BinScanFinal{grid, L.entries_cap, status}, s);
     }
     return cudaGetLastError();
 }

@@ -21,6 +21,7 @@
 
 #include <mutex>
 
+#include "scan.cuh"
 #include "sop_device.cuh"
 #include "sop_internal.h"
 
@@ -1310,32 +1311,6 @@ __global__ void sites_count_kernel(const float* __restrict__ pos, int32_t N, con
     atomicAdd(&cnt[site_cell(G, pos, i, q)], 1);
 }
 
-__global__ void __launch_bounds__(1024) sites_scan_kernel(const ProbeGrid* __restrict__ gp, int32_t* __restrict__ cnt,
-                                                           int32_t* __restrict__ start)
-{
-    __shared__ int32_t s_part[1024];
-    const int tid = threadIdx.x, nt = blockDim.x, nc = gp->ncells;
-    const int chunk = (nc + nt - 1) / nt, c0 = tid * chunk, c1 = min(nc, c0 + chunk);
-    int32_t sum = 0;
-    for (int c = c0; c < c1; ++c) sum += cnt[c];
-    s_part[tid] = sum;
-    __syncthreads();
-    for (int off = 1; off < nt; off <<= 1) {
-        const int32_t v = tid >= off ? s_part[tid - off] : 0;
-        __syncthreads();
-        s_part[tid] += v;
-        __syncthreads();
-    }
-    int32_t run = s_part[tid] - sum;
-    for (int c = c0; c < c1; ++c) {
-        const int32_t v = cnt[c];
-        start[c] = run;
-        run += v;
-        cnt[c] = 0;
-    }
-    if (tid == nt - 1) start[nc] = s_part[nt - 1];
-}
-
 __global__ void sites_fill_kernel(const float* __restrict__ pos, int32_t N, const ProbeGrid* __restrict__ gp,
                                   const int32_t* __restrict__ start, int32_t* __restrict__ cnt, int4* __restrict__ ent)
 {
@@ -1362,6 +1337,7 @@ size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K)
     o = align256(o + sizeof(int4) * (size_t)N);
     o = align256(o + sizeof(float) * (size_t)M * K);
     o = align256(o + 8 * sizeof(int32_t));
+    o = align256(o + sizeof(long long) * scan_scratch_count(cells));
     return o;
 }
 
@@ -1584,6 +1560,8 @@ SitesGrid launch_sites_grid(const float* sites, int32_t N, char* ws, cudaStream_
     int4* ent = reinterpret_cast<int4*>(ws + o);
     o = align256(o + sizeof(int4) * (size_t)N);
     int32_t* mm = reinterpret_cast<int32_t*>(ws + o);
+    o = align256(o + 8 * sizeof(int32_t));
+    long long* scan = reinterpret_cast<long long*>(ws + o);
     if (N <= 16384) {
         probe_grid_kernel<<<1, 1024, 0, s>>>(sites, N, g, grid, cstart, ccnt, ent);
     } else {
@@ -1595,7 +1573,13 @@ SitesGrid launch_sites_grid(const float* sites, int32_t N, char* ws, cudaStream_
         const int64_t cap = N / 4 > 4096 ? N / 4 : 4096;
         sites_setup_kernel<<<1, 32, 0, s>>>(mm, cap < cells ? cap : cells, grid);
         sites_count_kernel<<<nb, 256, 0, s>>>(sites, N, grid, ccnt);
-        sites_scan_kernel<<<1, 1024, 0, s>>>(grid, ccnt, cstart);
+        ScanArgs sa;
+        sa.n = &grid->ncells;
+        sa.skip = nullptr;
+        sa.cnt = ccnt;
+        sa.start = cstart;
+        sa.scratch = scan;
+        launch_scan(sa, cap < cells ? cap : cells, ScanNoFinal{}, s);
         sites_fill_kernel<<<nb, 256, 0, s>>>(sites, N, grid, cstart, ccnt, ent);
     }
     r.grid = grid;

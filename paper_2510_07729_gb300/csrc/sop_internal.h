@@ -85,7 +85,7 @@ cudaError_t launch_atlas_pack(const float* rgb, int rgb_stride, const float* occ
 
 // ---- bake -------------------------------------------------------------------
 struct BakeLayout {
-    size_t hdr, bbox, stats, rec, cell_start, cell_cnt, dirs, ent, total;
+    size_t hdr, bbox, stats, rec, cell_start, cell_cnt, scan, dirs, ent, total;
     int64_t cells_cap, entries_cap;
 };
 // bytes per cell entry: quantised box and Gaussian index
@@ -136,7 +136,7 @@ cudaError_t surr_get_grad(const char* state, float* grad, cudaStream_t s);
 cudaError_t surr_state_io(char* state, float* master, float* m, float* v, int32_t* step, bool to_device,
                           cudaStream_t s);
 struct SurrFeatLayout {
-    size_t sites, tdirs, t0, fhdr, fmm, facc, fcells, total;
+    size_t sites, tdirs, t0, fhdr, fmm, fctr, facc, fcells, total;
 };
 SurrFeatLayout surr_feat_layout(int64_t N, int32_t P, int32_t R);
 // features [P][R*R][18] of every texel; bake_rec: the Gaussian records of a

@@ -184,13 +184,15 @@ __device__ __forceinline__ void two_diff_s(float a, float b, float& hi, float& l
 }
 
 constexpr int kNearThreads = 256;
+constexpr int kNearRec = 7;  // staged float4 per listed Gaussian
+static_assert(kNearCap * kNearRec * 16 <= kCandCap * 12, "the staged records must fit the candidate buffer");
 
 __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* ckey = reinterpret_cast<uint64_t*>(smem);                 // [kCandCap]
     int32_t* cidx = reinterpret_cast<int32_t*>(ckey + kCandCap);          // [kCandCap]
-    float4* srec = reinterpret_cast<float4*>(smem);                       // [kNearCap][5], after the sort
+    float4* srec = reinterpret_cast<float4*>(smem);                       // [kNearCap][kNearRec], after the sort
     __shared__ int32_t s_count, s_box[6];
     __shared__ int32_t s_list[kNearCap];
     const int tid = threadIdx.x, p = blockIdx.x;
@@ -215,16 +217,32 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
         const int cx = s_box[0] + c % nx, cy = s_box[1] + (c / nx) % ny, cz = s_box[2] + c / (nx * ny);
         const int cell = (cz * G.dims[1] + cy) * G.dims[0] + cx;
         const int e1 = __ldg(k.cell_start + cell + 1);
-        for (int e = __ldg(k.cell_start + cell) + lane; e < e1; e += 32) {
-            const int4 en = __ldg(k.ent + e);
-            const uint32_t dx = (uint32_t)abs(en.x - q[0]), dy = (uint32_t)abs(en.y - q[1]),
-                           dz = (uint32_t)abs(en.z - q[2]);
-            const uint64_t key = (uint64_t)dx * dx + (uint64_t)dy * dy + (uint64_t)dz * dz;
-            if (key <= k.r2key) {
-                const int pos = atomicAdd(&s_count, 1);
+        for (int eb = __ldg(k.cell_start + cell); eb < e1; eb += 32) {
+            const int e = eb + lane;
+            bool in = false;
+            uint64_t key = 0;
+            int32_t gi = 0;
+            if (e < e1) {
+                const int4 en = __ldg(k.ent + e);
+                const uint32_t dx = (uint32_t)abs(en.x - q[0]), dy = (uint32_t)abs(en.y - q[1]),
+                               dz = (uint32_t)abs(en.z - q[2]);
+                key = (uint64_t)dx * dx + (uint64_t)dy * dy + (uint64_t)dz * dz;
+                gi = en.w;
+                in = key <= k.r2key;
+            }
+            // one shared-memory atomic per warp and batch
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            int base = 0;
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                if (lane == leader) base = atomicAdd(&s_count, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+            }
+            if (in) {
+                const int pos = base + __popc(m & ((1u << lane) - 1u));
                 if (pos < kCandCap) {
                     ckey[pos] = key;
-                    cidx[pos] = en.w;
+                    cidx[pos] = gi;
                 }
             }
         }
@@ -272,8 +290,31 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
         k.t0[p] = nl == kNearCap ? (float)(sqrt((double)ckey[kNearCap - 1]) * (1.0 / 1048576.0)) : k.r_n;
     }
     __syncthreads();
-    // stage the listed Gaussians' records (over the candidate buffer)
-    for (int i = tid; i < nl * 5; i += kNearThreads) srec[i] = __ldg(k.rec + (int64_t)s_list[i / 5] * 5 + i % 5);
+    // stage what each listed Gaussian contributes to every texel of this
+    // probe (over the candidate buffer), kNearRec float4 each:
+    //   0: mu - p, rho (the alpha_min bounding sphere; < 0: never a hit)
+    //   1: |mu - p|^2, rho^2 (1 + 1e-4) (-1 when rho < 0), h = p - mu (x, y)
+    //   2: h (z), the low parts l of p - mu = h + l (error-free)
+    //   3, 4, 5 (x): M = diag(1/s) R^T, row by row; 5 (yzw): u = M h
+    //   6: opacity, rgb
+    for (int j = tid; j < nl; j += kNearThreads) {
+        const float4* r = k.rec + (int64_t)s_list[j] * 5;
+        const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3), r4 = __ldg(r + 4);
+        const float dx = r0.x - pp.x, dy = r0.y - pp.y, dz = r0.z - pp.z;
+        float hx, lx, hy, ly, hz, lz;
+        two_diff_s(pp.x, r0.x, hx, lx);
+        two_diff_s(pp.y, r0.y, hy, ly);
+        two_diff_s(pp.z, r0.z, hz, lz);
+        float4* o = srec + kNearRec * j;
+        o[0] = make_float4(dx, dy, dz, r0.w);
+        o[1] = make_float4(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), r0.w < 0.f ? -1.f : r0.w * r0.w * 1.0001f, hx, hy);
+        o[2] = make_float4(hz, lx, ly, lz);
+        o[3] = r1;
+        o[4] = r2;
+        o[5] = make_float4(r3.x, fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz)), fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz)),
+                           fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz)));
+        o[6] = make_float4(r3.y, r3.z, r3.w, r4.x);
+    }
     __syncthreads();
     const int RR = k.R * k.R;
     for (int t = tid; t < RR; t += kNearThreads) {
@@ -281,43 +322,36 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
         const float3 d = f3(d4.x, d4.y, d4.z);
         float T = 1.f, L0 = 0.f, L1 = 0.f, L2 = 0.f, W = 0.f, Dacc = 0.f;
         for (int j = 0; j < nl; ++j) {
-            const float4 r0 = srec[5 * j];
+            const float4* q = srec + kNearRec * j;
+            const float4 c0 = q[0], c1 = q[1];
             // lossless cull: a ray that misses the alpha_min bounding sphere
-            // (radius r0.w, margin included) cannot reach alpha_min; the
-            // texels of a warp are neighbouring directions, so it is coherent
-            {
-                const float dx = r0.x - pp.x, dy = r0.y - pp.y, dz = r0.z - pp.z;
-                const float pr = fmaf(dx, d.x, fmaf(dy, d.y, dz * d.z));
-                const float q2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) - pr * pr;
-                if (r0.w < 0.f || q2 > r0.w * r0.w * 1.0001f || pr < -r0.w) continue;
-            }
-            const float4 r1 = srec[5 * j + 1], r2 = srec[5 * j + 2], r3 = srec[5 * j + 3];
-            float hx, lx, hy, ly, hz, lz;
-            two_diff_s(pp.x, r0.x, hx, lx);
-            two_diff_s(pp.y, r0.y, hy, ly);
-            two_diff_s(pp.z, r0.z, hz, lz);
-            const float u0 = fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz));
-            const float u1 = fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz));
-            const float u2 = fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz));
-            const float w0 = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
-            const float w1 = fmaf(r1.w, d.x, fmaf(r2.x, d.y, r2.y * d.z));
-            const float w2 = fmaf(r2.z, d.x, fmaf(r2.w, d.y, r3.x * d.z));
+            // (margin included) cannot reach alpha_min; the texels of a warp
+            // are neighbouring directions, so it is coherent
+            const float pr = fmaf(c0.x, d.x, fmaf(c0.y, d.y, c0.z * d.z));
+            if (c1.x - pr * pr > c1.y || pr < -c0.w) continue;
+            const float4 c2 = q[2], c3 = q[3], c4 = q[4], c5 = q[5];
+            // the response is largest at t* = -(w.u) / (w.w), w = M d
+            const float w0 = fmaf(c3.x, d.x, fmaf(c3.y, d.y, c3.z * d.z));
+            const float w1 = fmaf(c3.w, d.x, fmaf(c4.x, d.y, c4.y * d.z));
+            const float w2 = fmaf(c4.z, d.x, fmaf(c4.w, d.y, c5.x * d.z));
             const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
-            const float B = fmaf(w0, u0, fmaf(w1, u1, w2 * u2));
-            const float ts = -B / A;
+            const float B = fmaf(w0, c5.y, fmaf(w1, c5.z, w2 * c5.w));
+            const float ts = __fdividef(-B, A);
             if (!(ts > 0.f)) continue;
-            const float ex = fmaf(ts, d.x, hx) + lx, ey = fmaf(ts, d.y, hy) + ly, ez = fmaf(ts, d.z, hz) + lz;
-            const float v0 = fmaf(r1.x, ex, fmaf(r1.y, ey, r1.z * ez));
-            const float v1 = fmaf(r1.w, ex, fmaf(r2.x, ey, r2.y * ez));
-            const float v2 = fmaf(r2.z, ex, fmaf(r2.w, ey, r3.x * ez));
-            const float resp = r3.y * expf(-0.5f * fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+            // m^2 at t*: M applied to the small offset e = h + l + t* d
+            const float ex = fmaf(ts, d.x, c1.z) + c2.y, ey = fmaf(ts, d.y, c1.w) + c2.z,
+                        ez = fmaf(ts, d.z, c2.x) + c2.w;
+            const float v0 = fmaf(c3.x, ex, fmaf(c3.y, ey, c3.z * ez));
+            const float v1 = fmaf(c3.w, ex, fmaf(c4.x, ey, c4.y * ez));
+            const float v2 = fmaf(c4.z, ex, fmaf(c4.w, ey, c5.x * ez));
+            const float4 c6 = q[6];
+            const float resp = c6.x * expf(-0.5f * fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
             if (resp < k.alpha_min) continue;
             const float al = fminf(resp, k.alpha_max);
             const float w = T * al;
-            const float4 r4 = srec[5 * j + 4];
-            L0 = fmaf(w, r3.z, L0);
-            L1 = fmaf(w, r3.w, L1);
-            L2 = fmaf(w, r4.x, L2);
+            L0 = fmaf(w, c6.y, L0);
+            L1 = fmaf(w, c6.z, L1);
+            L2 = fmaf(w, c6.w, L2);
             W += w;
             Dacc = fmaf(w, ts, Dacc);
             T *= 1.f - al;
@@ -383,9 +417,10 @@ __global__ void far_bbox_kernel(sop_gaussians g, float alpha_min, int32_t* mm)
     }
 }
 
-__global__ void far_setup_kernel(const int32_t* mm, FarGrid* fg)
+__global__ void far_setup_kernel(const int32_t* mm, FarGrid* fg, unsigned long long* next_ray)
 {
     if (threadIdx.x != 0) return;
+    *next_ray = 0ull;  // the march's ray counter
     FarGrid F;
     if (mm[0] > mm[3]) {  // nothing carries mass
         for (int a = 0; a < 3; ++a) {
@@ -490,83 +525,19 @@ __device__ __forceinline__ float far_tnext(int st, int c, float lo, float h, flo
     return st == 0 ? INFINITY : (lo + (float)(c + (st > 0 ? 1 : 0)) * h - o) / d;
 }
 
-__global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict__ probe_pos, int32_t P, int32_t R,
-                                                        const float* __restrict__ t0p, const float4* __restrict__ tdirs,
-                                                        const FarGrid* __restrict__ fg,
-                                                        const float4* __restrict__ cells, float* __restrict__ feats)
+// Texel rays of a warp differ widely in length (a ray into the object stops
+// once tau > 20 within a few cells; one that leaves it crosses the box), so
+// a warp that marched 32 fixed rays would idle most lanes behind its longest
+// ray. The march is persistent instead: each lane holds one ray, and once
+// kFarRefill lanes have finished (or none is left marching) the warp fetches
+// that many new rays from a global counter. Every ray is still marched by one
+// lane from start to end with the same arithmetic, so the result does not
+// depend on which lane or warp took it.
+constexpr int kFarRefill = 16;
+
+__device__ __forceinline__ void far_write(float* __restrict__ feats, int64_t id, float tk0, float tk1, float tk2,
+                                          float tk3, float tk4, float tau, float L0, float L1, float L2)
 {
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int RR = R * R;
-    if (id >= (int64_t)P * RR) return;
-    const int p = (int)(id / RR), t = (int)(id % RR);
-    const FarGrid F = *fg;
-    const float3 o = load3(probe_pos, p);
-    const float4 d = __ldg(tdirs + t);
-    const float t0 = __ldg(t0p + p);
-    const float h = F.h;
-    const float ck0 = fmaf(2.f, h, t0), ck1 = fmaf(4.f, h, t0), ck2 = fmaf(8.f, h, t0), ck3 = fmaf(16.f, h, t0),
-                ck4 = fmaf(32.f, h, t0);
-    float tk0 = -1.f, tk1 = -1.f, tk2 = -1.f, tk3 = -1.f, tk4 = -1.f;  // tau at the checkpoints (-1: not yet)
-    float tau = 0.f, L0 = 0.f, L1 = 0.f, L2 = 0.f;
-    float ta = t0, tb = INFINITY;
-    far_slab(o.x, d.x, F.lo[0], F.lo[0] + F.dims[0] * h, ta, tb);
-    far_slab(o.y, d.y, F.lo[1], F.lo[1] + F.dims[1] * h, ta, tb);
-    far_slab(o.z, d.z, F.lo[2], F.lo[2] + F.dims[2] * h, ta, tb);
-    if (ta < tb) {
-        int cx = far_cell0(o.x, d.x, ta, F.lo[0], h, F.dims[0]);
-        int cy = far_cell0(o.y, d.y, ta, F.lo[1], h, F.dims[1]);
-        int cz = far_cell0(o.z, d.z, ta, F.lo[2], h, F.dims[2]);
-        const int sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
-        const int sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
-        const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
-        float tnx = far_tnext(sx, cx, F.lo[0], h, o.x, d.x);
-        float tny = far_tnext(sy, cy, F.lo[1], h, o.y, d.y);
-        float tnz = far_tnext(sz, cz, F.lo[2], h, o.z, d.z);
-        float tc = ta;
-        // at most one step per cell along each axis: bounded by the dims
-        const int max_steps = F.dims[0] + F.dims[1] + F.dims[2] + 3;
-        for (int it = 0; it < max_steps && tc < tb && tau <= kTauMax; ++it) {
-            const int ax = (tnx <= tny && tnx <= tnz) ? 0 : (tny <= tnz ? 1 : 2);
-            float te = fminf(ax == 0 ? tnx : (ax == 1 ? tny : tnz), tb);
-            te = fmaxf(te, tc);
-            const float4 cv = __ldg(cells + ((int64_t)cz * F.dims[1] + cy) * F.dims[0] + cx);
-            // checkpoints inside this segment take tau at their position
-            if (tk0 < 0.f && ck0 < te) tk0 = ck0 <= tc ? tau : fmaf(cv.x, ck0 - tc, tau);
-            if (tk1 < 0.f && ck1 < te) tk1 = ck1 <= tc ? tau : fmaf(cv.x, ck1 - tc, tau);
-            if (tk2 < 0.f && ck2 < te) tk2 = ck2 <= tc ? tau : fmaf(cv.x, ck2 - tc, tau);
-            if (tk3 < 0.f && ck3 < te) tk3 = ck3 <= tc ? tau : fmaf(cv.x, ck3 - tc, tau);
-            if (tk4 < 0.f && ck4 < te) tk4 = ck4 <= tc ? tau : fmaf(cv.x, ck4 - tc, tau);
-            if (cv.x > 0.f) {
-                const float dtau = cv.x * (te - tc);
-                const float a = __expf(-tau) * -expm1f(-dtau);
-                L0 = fmaf(a, cv.y, L0);
-                L1 = fmaf(a, cv.z, L1);
-                L2 = fmaf(a, cv.w, L2);
-                tau += dtau;
-            }
-            tc = te;
-            if (!(te < tb)) break;
-            if (ax == 0) {
-                cx += sx;
-                if (cx < 0 || cx >= F.dims[0]) break;
-                tnx = far_tnext(sx, cx, F.lo[0], h, o.x, d.x);
-            } else if (ax == 1) {
-                cy += sy;
-                if (cy < 0 || cy >= F.dims[1]) break;
-                tny = far_tnext(sy, cy, F.lo[1], h, o.y, d.y);
-            } else {
-                cz += sz;
-                if (cz < 0 || cz >= F.dims[2]) break;
-                tnz = far_tnext(sz, cz, F.lo[2], h, o.z, d.z);
-            }
-        }
-    }
-    // checkpoints beyond the walk take its final depth
-    if (tk0 < 0.f) tk0 = tau;
-    if (tk1 < 0.f) tk1 = tau;
-    if (tk2 < 0.f) tk2 = tau;
-    if (tk3 < 0.f) tk3 = tau;
-    if (tk4 < 0.f) tk4 = tau;
     float* f = feats + id * kIn + 9;
     f[0] = -expm1f(-tk0);
     f[1] = -expm1f(-tk1);
@@ -577,6 +548,134 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
     f[6] = L0;
     f[7] = L1;
     f[8] = L2;
+}
+
+__global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict__ probe_pos, int32_t P, int32_t R,
+                                                        const float* __restrict__ t0p, const float4* __restrict__ tdirs,
+                                                        const FarGrid* __restrict__ fg,
+                                                        const float4* __restrict__ cells, float* __restrict__ feats,
+                                                        unsigned long long* __restrict__ next_ray)
+{
+    const int lane = threadIdx.x & 31;
+    const int RR = R * R;
+    const int64_t total = (int64_t)P * RR;
+    const FarGrid F = *fg;
+    const float h = F.h;
+    // at most one step per cell along each axis: bounded by the dims
+    const int max_steps = F.dims[0] + F.dims[1] + F.dims[2] + 3;
+    // the lane's ray
+    int64_t id = -1;
+    bool live = false, retired = false;
+    float ox = 0.f, oy = 0.f, oz = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, t0 = 0.f;
+    float tc = 0.f, tb = 0.f, tau = 0.f, L0 = 0.f, L1 = 0.f, L2 = 0.f;
+    float tnx = 0.f, tny = 0.f, tnz = 0.f, ckn = 0.f;
+    float tk0 = 0.f, tk1 = 0.f, tk2 = 0.f, tk3 = 0.f, tk4 = 0.f;  // tau at the checkpoints
+    int cx = 0, cy = 0, cz = 0, sx = 0, sy = 0, sz = 0, kn = 0, it = 0;
+    for (;;) {
+        const unsigned want = __ballot_sync(0xffffffffu, !live && !retired);
+        const unsigned marching = __ballot_sync(0xffffffffu, live);
+        if (want == 0 && marching == 0) break;
+        if (want != 0 && (marching == 0 || __popc(want) >= kFarRefill)) {
+            // fetch a ray for every lane that wants one
+            const int leader = __ffs(want) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(next_ray, (unsigned long long)__popc(want));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (want & (1u << lane)) {
+                id = (int64_t)base + __popc(want & ((1u << lane) - 1u));
+                if (id >= total) {
+                    retired = true;
+                } else {
+                    const int p = (int)(id / RR), t = (int)(id % RR);
+                    const float3 o = load3(probe_pos, p);
+                    const float4 d = __ldg(tdirs + t);
+                    ox = o.x;
+                    oy = o.y;
+                    oz = o.z;
+                    dx = d.x;
+                    dy = d.y;
+                    dz = d.z;
+                    t0 = __ldg(t0p + p);
+                    tau = L0 = L1 = L2 = 0.f;
+                    tk0 = tk1 = tk2 = tk3 = tk4 = -1.f;  // -1: not reached yet
+                    kn = 0;
+                    ckn = fmaf(2.f, h, t0);
+                    it = 0;
+                    float ta = t0;
+                    tb = INFINITY;
+                    far_slab(ox, dx, F.lo[0], F.lo[0] + F.dims[0] * h, ta, tb);
+                    far_slab(oy, dy, F.lo[1], F.lo[1] + F.dims[1] * h, ta, tb);
+                    far_slab(oz, dz, F.lo[2], F.lo[2] + F.dims[2] * h, ta, tb);
+                    live = ta < tb;
+                    if (live) {
+                        cx = far_cell0(ox, dx, ta, F.lo[0], h, F.dims[0]);
+                        cy = far_cell0(oy, dy, ta, F.lo[1], h, F.dims[1]);
+                        cz = far_cell0(oz, dz, ta, F.lo[2], h, F.dims[2]);
+                        sx = dx > 0.f ? 1 : (dx < 0.f ? -1 : 0);
+                        sy = dy > 0.f ? 1 : (dy < 0.f ? -1 : 0);
+                        sz = dz > 0.f ? 1 : (dz < 0.f ? -1 : 0);
+                        tnx = far_tnext(sx, cx, F.lo[0], h, ox, dx);
+                        tny = far_tnext(sy, cy, F.lo[1], h, oy, dy);
+                        tnz = far_tnext(sz, cz, F.lo[2], h, oz, dz);
+                        tc = ta;
+                    } else {
+                        far_write(feats, id, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+            continue;
+        }
+        if (!live) continue;
+        // one cell of the walk
+        const int ax = (tnx <= tny && tnx <= tnz) ? 0 : (tny <= tnz ? 1 : 2);
+        float te = fminf(ax == 0 ? tnx : (ax == 1 ? tny : tnz), tb);
+        te = fmaxf(te, tc);
+        const float4 cv = __ldg(cells + ((int64_t)cz * F.dims[1] + cy) * F.dims[0] + cx);
+        // checkpoints inside this segment take tau at their position (they
+        // are increasing: only the next one can be due)
+        while (kn < 5 && ckn < te) {
+            const float v = ckn <= tc ? tau : fmaf(cv.x, ckn - tc, tau);
+            if (kn == 0) tk0 = v;
+            else if (kn == 1) tk1 = v;
+            else if (kn == 2) tk2 = v;
+            else if (kn == 3) tk3 = v;
+            else tk4 = v;
+            ++kn;
+            ckn = kn < 5 ? fmaf((float)(2 << kn), h, t0) : INFINITY;
+        }
+        if (cv.x > 0.f) {
+            const float dtau = cv.x * (te - tc);
+            const float a = __expf(-tau) * -expm1f(-dtau);
+            L0 = fmaf(a, cv.y, L0);
+            L1 = fmaf(a, cv.z, L1);
+            L2 = fmaf(a, cv.w, L2);
+            tau += dtau;
+        }
+        tc = te;
+        bool end = !(te < tb);
+        if (!end) {
+            if (ax == 0) {
+                cx += sx;
+                end = cx < 0 || cx >= F.dims[0];
+                if (!end) tnx = far_tnext(sx, cx, F.lo[0], h, ox, dx);
+            } else if (ax == 1) {
+                cy += sy;
+                end = cy < 0 || cy >= F.dims[1];
+                if (!end) tny = far_tnext(sy, cy, F.lo[1], h, oy, dy);
+            } else {
+                cz += sz;
+                end = cz < 0 || cz >= F.dims[2];
+                if (!end) tnz = far_tnext(sz, cz, F.lo[2], h, oz, dz);
+            }
+        }
+        ++it;
+        if (end || it >= max_steps || !(tc < tb) || tau > kTauMax) {
+            // checkpoints beyond the walk take its final depth
+            far_write(feats, id, tk0 < 0.f ? tau : tk0, tk1 < 0.f ? tau : tk1, tk2 < 0.f ? tau : tk2,
+                      tk3 < 0.f ? tau : tk3, tk4 < 0.f ? tau : tk4, tau, L0, L1, L2);
+            live = false;
+        }
+    }
 }
 
 __global__ void surr_tdirs_kernel(int R, float4* __restrict__ dirs)
@@ -776,6 +875,95 @@ __device__ __forceinline__ void texel_store(void* rgbo, int dt, int64_t ti, floa
     else reinterpret_cast<uint2*>(rgbo)[ti] = Texel<SOP_F16>::pack(v);
 }
 
+// A CTA's position in its share of the network's work: probe entry b of
+// the batch (probe p, or -1 once the CTA is done) and its first texel s0.
+struct MlpChunk {
+    int b, s0;
+    int64_t p;
+};
+
+// the first entry from c.b on (in steps of gridDim.x) with a valid probe id;
+// invalid ids are reported and skipped
+__device__ __forceinline__ void mlp_seek(const MlpK& k, MlpChunk& c, int tid)
+{
+    for (; c.b < k.B; c.b += gridDim.x) {
+        const int64_t p = k.pid ? k.pid[c.b] : c.b;
+        if (p >= 0 && p < k.P) {
+            c.p = p;
+            return;
+        }
+        if (tid == 0 && k.status) atomicOr(k.status, SOP_DEVSTAT_INDEX);
+    }
+    c.p = -1;
+}
+
+__device__ __forceinline__ void mlp_next(const MlpK& k, MlpChunk& c, int RR, int tid)
+{
+    c.s0 += kCH;
+    if (c.s0 >= RR) {
+        c.s0 = 0;
+        c.b += gridDim.x;
+        mlp_seek(k, c, tid);
+    }
+}
+
+// A chunk's features (ns rows of kIn floats, contiguous) in registers: up
+// to kFeatVec float4 a thread when the rows start on a 16-byte boundary.
+constexpr int kFeatVec = (kCH * kIn / 4 + 255) / 256;
+struct FeatRegs {
+    float4 v[kFeatVec];
+};
+
+__device__ __forceinline__ const float* chunk_feats(const MlpK& k, const MlpChunk& c, int RR, int& nf)
+{
+    nf = min(kCH, RR - c.s0) * kIn;
+    return k.feats + (c.p * RR + c.s0) * kIn;
+}
+
+__device__ __forceinline__ void feat_load(const MlpK& k, const MlpChunk& c, int RR, int tid, FeatRegs& r)
+{
+    int nf;
+    const float* fp = chunk_feats(k, c, RR, nf);
+    if ((reinterpret_cast<uintptr_t>(fp) & 15) != 0 || (nf & 3) != 0) return;  // feat_store reads them itself
+#pragma unroll
+    for (int q = 0; q < kFeatVec; ++q) {
+        const int i = tid + 256 * q;
+        if (i < nf / 4) r.v[q] = __ldg(reinterpret_cast<const float4*>(fp) + i);
+    }
+}
+
+// the chunk's features as bf16 into the tile sX ([kCH][kLDX]; rows beyond
+// the chunk zero)
+__device__ __forceinline__ void feat_store(const MlpK& k, const MlpChunk& c, int RR, int tid, const FeatRegs& r,
+                                           uint16_t* sX)
+{
+    int nf;
+    const float* fp = chunk_feats(k, c, RR, nf);
+    if ((reinterpret_cast<uintptr_t>(fp) & 15) == 0 && (nf & 3) == 0) {
+#pragma unroll
+        for (int q = 0; q < kFeatVec; ++q) {
+            const int i = tid + 256 * q;
+            if (i < nf / 4) {
+                const float f[4] = {r.v[q].x, r.v[q].y, r.v[q].z, r.v[q].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int n = 4 * i + e, s = n / kIn;
+                    sX[s * kLDX + (n - s * kIn)] = f2bf(f[e]);
+                }
+            }
+        }
+    } else {
+        for (int n = tid; n < nf; n += 256) {
+            const int s = n / kIn;
+            sX[s * kLDX + (n - s * kIn)] = f2bf(fp[n]);
+        }
+    }
+    for (int i = nf + tid; i < kCH * kIn; i += 256) {
+        const int s = i / kIn;
+        sX[s * kLDX + (i - s * kIn)] = 0;
+    }
+}
+
 template <bool TRAIN>
 __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
 {
@@ -850,21 +1038,30 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
     const int row0 = warp * 16, mt = warp & 3, nt0 = (warp >> 2) * 4, nx0 = (warp >> 2) * 2;
     __syncthreads();
 
-    for (int b = blockIdx.x; b < k.B; b += gridDim.x) {
-        int64_t p = k.pid ? k.pid[b] : b;
-        if (p < 0 || p >= k.P) {
-            if (tid == 0 && k.status) atomicOr(k.status, SOP_DEVSTAT_INDEX);
-            continue;
-        }
-        for (int s0 = 0; s0 < RR; s0 += kCH) {
-            const int ns = min(kCH, RR - s0);
-            __syncthreads();
-            const float* fp = k.feats + ((int64_t)p * RR + s0) * kIn;
-            for (int i = tid; i < kCH * kLDX; i += blockDim.x) {
-                const int s = i / kLDX, c = i % kLDX;
-                sX[i] = (s < ns && c < kIn) ? f2bf(fp[s * kIn + c]) : (uint16_t)0;
-            }
-            __syncthreads();
+    // the padding columns of the feature tile stay zero (chunks write only
+    // the first kIn columns)
+    for (int i = tid; i < kCH * (kLDX - kIn); i += blockDim.x)
+        sX[(i / (kLDX - kIn)) * kLDX + kIn + i % (kLDX - kIn)] = 0;
+    // the CTA's chunks: probe entries b = blockIdx.x, + gridDim.x, ... (each
+    // in chunks of kCH texels). Inference loads the next chunk's features
+    // into registers while the current one goes through the network.
+    MlpChunk cur;
+    cur.b = blockIdx.x;
+    cur.s0 = 0;
+    mlp_seek(k, cur, tid);
+    FeatRegs pf;
+    if (!TRAIN && cur.p >= 0) feat_load(k, cur, RR, tid, pf);
+    while (cur.p >= 0) {
+        const int64_t p = cur.p;
+        const int s0 = cur.s0;
+        const int ns = min(kCH, RR - s0);
+        __syncthreads();
+        if (TRAIN) feat_load(k, cur, RR, tid, pf);
+        feat_store(k, cur, RR, tid, pf, sX);
+        mlp_next(k, cur, RR, tid);
+        if (!TRAIN && cur.p >= 0) feat_load(k, cur, RR, tid, pf);
+        __syncthreads();
+        {
             layer_fwd<kInPad, kLDX, kLDX>(sX, sW1, sb1, sH1, row0, lane);
             __syncwarp();
             layer_fwd<kHid, kLD, kLD>(sH1, sW2, sb2, sH2, row0, lane);
@@ -873,45 +1070,41 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
             __syncwarp();
             out_fwd(sH3, sW4b, sb4, sY, row0, lane);
             __syncthreads();
-            // the loss gradient / the atlas write of the outputs
+            if (!TRAIN) {
+                // the atlas write: occupancy clamped to [0, 1], depth and
+                // radiance to >= 0
+                for (int s = tid; s < ns; s += blockDim.x) {
+                    const float* y = sY + s * 8;
+                    const int t = s0 + s;
+                    const int64_t ti = p * RS * RS + (int64_t)(t / k.R + 1) * RS + (t % k.R + 1);
+                    if (k.depth) depth_put(k.depth, k.depth_dtype, ti, fmaxf(y[1], 0.f));
+                    texel_store(k.rgbo, k.rgbo_dtype, ti,
+                                make_float4(fmaxf(y[2], 0.f), fmaxf(y[3], 0.f), fmaxf(y[4], 0.f),
+                                            fminf(fmaxf(y[0], 0.f), 1.f)));
+                }
+            } else {
+            // the loss gradient of the outputs
             for (int i = tid; i < kCH * kOut; i += blockDim.x) {
                 const int s = i / kOut, o = i % kOut;
                 const float y = sY[s * 8 + o];
                 const int t = s0 + s;
                 const int64_t ti = p * RS * RS + (int64_t)(t / k.R + 1) * RS + (t % k.R + 1);
-                if (TRAIN) {
-                    float g = 0.f;
-                    if (s < ns) {
-                        float tg;
-                        if (o == 1) {
-                            tg = k.depth ? depth_at(k.depth, k.depth_dtype, ti) : 0.f;
-                        } else {
-                            const float4 v = texel_load(k.rgbo, k.rgbo_dtype, ti);
-                            tg = o == 0 ? v.w : (o == 2 ? v.x : (o == 3 ? v.y : v.z));
-                        }
-                        const float df = y - tg;
-                        lsum += fabsf(df);
-                        g = (df > 0.f ? 1.f : (df < 0.f ? -1.f : 0.f)) * k.inv_count;
-                    }
-                    sG4[i] = g;
-                } else if (s < ns) {
+                float g = 0.f;
+                if (s < ns) {
+                    float tg;
                     if (o == 1) {
-                        if (k.depth) depth_put(k.depth, k.depth_dtype, ti, fmaxf(y, 0.f));
+                        tg = k.depth ? depth_at(k.depth, k.depth_dtype, ti) : 0.f;
                     } else {
-                        sG4[i] = o == 0 ? fminf(fmaxf(y, 0.f), 1.f) : fmaxf(y, 0.f);
+                        const float4 v = texel_load(k.rgbo, k.rgbo_dtype, ti);
+                        tg = o == 0 ? v.w : (o == 2 ? v.x : (o == 3 ? v.y : v.z));
                     }
+                    const float df = y - tg;
+                    lsum += fabsf(df);
+                    g = (df > 0.f ? 1.f : (df < 0.f ? -1.f : 0.f)) * k.inv_count;
                 }
+                sG4[i] = g;
             }
             __syncthreads();
-            if (!TRAIN) {
-                for (int s = tid; s < ns; s += blockDim.x) {
-                    const int t = s0 + s;
-                    const int64_t ti = p * RS * RS + (int64_t)(t / k.R + 1) * RS + (t % k.R + 1);
-                    texel_store(k.rgbo, k.rgbo_dtype, ti,
-                                make_float4(sG4[s * kOut + 2], sG4[s * kOut + 3], sG4[s * kOut + 4], sG4[s * kOut]));
-                }
-                continue;
-            }
             // ---- backward ----------------------------------------------------------
             // output layer: dW4 += G4^T H3, db4 += sum G4; D3 = bf16((G4 W4) * (h3 > 0))
             for (int i = tid; i < kOut * kHid; i += blockDim.x) {
@@ -967,6 +1160,7 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
                 for (int s = 0; s < ns; ++s) a += bf2f(sD3[s * kLD + tid]);
                 gb1[tid] += a;
             }
+            }  // training
         }
     }
     if (TRAIN) {
@@ -1186,6 +1380,7 @@ SurrFeatLayout surr_feat_layout(int64_t N, int32_t P, int32_t R)
     L.t0 = o;     o = align256(o + sizeof(float) * (size_t)P);
     L.fhdr = o;   o = align256(o + sizeof(FarGrid));
     L.fmm = o;    o = align256(o + 8 * sizeof(int32_t));
+    L.fctr = o;   o = align256(o + sizeof(unsigned long long));
     const size_t cells = (size_t)kFarCells * kFarCells * kFarCells;
     L.facc = o;   o = align256(o + 4 * sizeof(unsigned long long) * cells);
     L.fcells = o; o = align256(o + sizeof(float4) * cells);
@@ -1236,14 +1431,27 @@ cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_
     far_bbox_init_kernel<<<1, 32, 0, s>>>(mm);
     const unsigned nb = (unsigned)((g.n + 255) / 256);
     if (g.n > 0) far_bbox_kernel<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(g, alpha_min, mm);
-    far_setup_kernel<<<1, 32, 0, s>>>(mm, fg);
+    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(ws + L.fctr);
+    far_setup_kernel<<<1, 32, 0, s>>>(mm, fg, next_ray);
     const int64_t maxc = (int64_t)kFarCells * kFarCells * kFarCells;
     far_zero_kernel<<<(unsigned)((4 * maxc + 255) / 256), 256, 0, s>>>(fg, acc);
     if (g.n > 0) far_splat_kernel<<<nb, 256, 0, s>>>(g, alpha_min, alpha_max, fg, acc);
     far_cells_kernel<<<(unsigned)((maxc + 255) / 256), 256, 0, s>>>(fg, acc, cells);
     const int64_t rays = (int64_t)P * R * R;
-    if (rays > 0)
-        far_march_kernel<<<(unsigned)((rays + 255) / 256), 256, 0, s>>>(probe_pos, P, R, t0, tdirs, fg, cells, feats);
+    if (rays > 0) {
+        // persistent: the CTAs that fit at once, never more than the rays need
+        static int resident = 0;
+        if (!resident) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_march_kernel, 256, 0);
+            resident = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+        }
+        const int64_t need = (rays + 255) / 256;
+        far_march_kernel<<<(unsigned)(need < resident ? need : resident), 256, 0, s>>>(probe_pos, P, R, t0, tdirs, fg,
+                                                                                    cells, feats, next_ray);
+    }
     return cudaGetLastError();
 }
 
