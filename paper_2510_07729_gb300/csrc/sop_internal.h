@@ -136,7 +136,7 @@ cudaError_t surr_get_grad(const char* state, float* grad, cudaStream_t s);
 cudaError_t surr_state_io(char* state, float* master, float* m, float* v, int32_t* step, bool to_device,
                           cudaStream_t s);
 struct SurrFeatLayout {
-    size_t sites, tdirs, t0, fhdr, fmm, fctr, facc, fcells, total;
+    size_t sites, tdirs, t0, fhdr, fmm, fctr, fbrick, facc, fcells, total;
 };
 SurrFeatLayout surr_feat_layout(int64_t N, int32_t P, int32_t R);
 // features [P][R*R][18] of every texel; bake_rec: the Gaussian records of a

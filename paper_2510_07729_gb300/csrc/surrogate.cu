@@ -184,7 +184,7 @@ __device__ __forceinline__ void two_diff_s(float a, float b, float& hi, float& l
 }
 
 constexpr int kNearThreads = 256;
-constexpr int kNearRec = 7;  // staged float4 per listed Gaussian
+constexpr int kNearRec = 8;  // staged float4 per listed Gaussian
 static_assert(kNearCap * kNearRec * 16 <= kCandCap * 12, "the staged records must fit the candidate buffer");
 
 __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
@@ -297,6 +297,14 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
     //   2: h (z), the low parts l of p - mu = h + l (error-free)
     //   3, 4, 5 (x): M = diag(1/s) R^T, row by row; 5 (yzw): u = M h
     //   6: opacity, rgb
+    //   7 (x): Q, for a cheap test that a ray cannot reach alpha_min: the
+    //     smallest m^2 along the ray is |u|^2 - B^2 / A (B = w.u, A = w.w,
+    //     w = M d); above kk^2 = 2 ln(o / alpha_min) no point reaches
+    //     alpha_min. With Q = |u|^2 (1 - 1e-3) - kk^2 - 1e-2, Q A > B^2 says
+    //     so with a margin of 1e-3 |u|^2 A + 1e-2 A. The FP32 rounding of M
+    //     and h moves |u|^2 A - B^2 by at most about 2^-23 (s_max / s_min)
+    //     |u|^2 A, so the test only drops certain misses for any Gaussian
+    //     with s_max / s_min below about 10^4.
     for (int j = tid; j < nl; j += kNearThreads) {
         const float4* r = k.rec + (int64_t)s_list[j] * 5;
         const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3), r4 = __ldg(r + 4);
@@ -311,9 +319,15 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
         o[2] = make_float4(hz, lx, ly, lz);
         o[3] = r1;
         o[4] = r2;
-        o[5] = make_float4(r3.x, fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz)), fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz)),
-                           fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz)));
+        // u = M (h + l), the low part included
+        o[5] = make_float4(r3.x, fmaf(r1.x, hx, fmaf(r1.y, hy, r1.z * hz)) + fmaf(r1.x, lx, fmaf(r1.y, ly, r1.z * lz)),
+                           fmaf(r1.w, hx, fmaf(r2.x, hy, r2.y * hz)) + fmaf(r1.w, lx, fmaf(r2.x, ly, r2.y * lz)),
+                           fmaf(r2.z, hx, fmaf(r2.w, hy, r3.x * hz)) + fmaf(r2.z, lx, fmaf(r2.w, ly, r3.x * lz)));
         o[6] = make_float4(r3.y, r3.z, r3.w, r4.x);
+        const float u0 = o[5].y, u1 = o[5].z, u2 = o[5].w;
+        const float uu = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+        const float kk2 = r0.w < 0.f ? 0.f : 2.f * fmaxf(logf(r3.y / k.alpha_min), 0.f);
+        o[7] = make_float4(fmaf(uu, 1.f - 1e-3f, -kk2) - 1e-2f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     const int RR = k.R * k.R;
@@ -336,6 +350,7 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
             const float w2 = fmaf(c4.z, d.x, fmaf(c4.w, d.y, c5.x * d.z));
             const float A = fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
             const float B = fmaf(w0, c5.y, fmaf(w1, c5.z, w2 * c5.w));
+            if (q[7].x * A > B * B) continue;  // certainly below alpha_min
             const float ts = __fdividef(-B, A);
             if (!(ts > 0.f)) continue;
             // m^2 at t*: M applied to the small offset e = h + l + t* d
@@ -496,6 +511,32 @@ __global__ void far_cells_kernel(const FarGrid* fg, const unsigned long long* __
     cells[i] = v;
 }
 
+// Empty space: one bit per brick of kFarBrick^3 cells, set when a cell of
+// the brick carries mass (a warp per 32 bricks, one word each).
+constexpr int kFarBrick = 4;
+constexpr int kFarBrickWords = (kFarCells / kFarBrick) * (kFarCells / kFarBrick) * (kFarCells / kFarBrick) / 32;
+
+__global__ void far_bricks_kernel(const FarGrid* fg, const float4* __restrict__ cells, uint32_t* __restrict__ bits)
+{
+    const FarGrid F = *fg;
+    const int bdx = (F.dims[0] + kFarBrick - 1) / kFarBrick, bdy = (F.dims[1] + kFarBrick - 1) / kFarBrick,
+              bdz = (F.dims[2] + kFarBrick - 1) / kFarBrick;
+    const int nb = bdx * bdy * bdz;
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w * 32 >= nb) return;
+    const int b = w * 32 + lane;
+    bool any = false;
+    if (b < nb) {
+        const int bx = b % bdx, by = (b / bdx) % bdy, bz = b / (bdx * bdy);
+        for (int z = bz * kFarBrick; z < min((bz + 1) * kFarBrick, F.dims[2]); ++z)
+            for (int y = by * kFarBrick; y < min((by + 1) * kFarBrick, F.dims[1]); ++y)
+                for (int x = bx * kFarBrick; x < min((bx + 1) * kFarBrick, F.dims[0]); ++x)
+                    any |= __ldg(&cells[((int64_t)z * F.dims[1] + y) * F.dims[0] + x].x) > 0.f;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, any);
+    if (lane == 0) bits[w] = m;
+}
+
 // one thread per texel ray (scalars per axis and per checkpoint, so that
 // nothing is indexed at run time and the walk stays in registers)
 __device__ __forceinline__ void far_slab(float o, float d, float lo, float hi, float& ta, float& tb)
@@ -554,8 +595,10 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
                                                         const float* __restrict__ t0p, const float4* __restrict__ tdirs,
                                                         const FarGrid* __restrict__ fg,
                                                         const float4* __restrict__ cells, float* __restrict__ feats,
-                                                        unsigned long long* __restrict__ next_ray)
+                                                        unsigned long long* __restrict__ next_ray,
+                                                        const uint32_t* __restrict__ brick_bits)
 {
+    __shared__ uint32_t s_bits[kFarBrickWords];
     const int lane = threadIdx.x & 31;
     const int RR = R * R;
     const int64_t total = (int64_t)P * RR;
@@ -563,6 +606,10 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
     const float h = F.h;
     // at most one step per cell along each axis: bounded by the dims
     const int max_steps = F.dims[0] + F.dims[1] + F.dims[2] + 3;
+    const int bdx = (F.dims[0] + kFarBrick - 1) / kFarBrick, bdy = (F.dims[1] + kFarBrick - 1) / kFarBrick;
+    const int nwords = (bdx * bdy * ((F.dims[2] + kFarBrick - 1) / kFarBrick) + 31) / 32;
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) s_bits[i] = __ldg(brick_bits + i);
+    __syncthreads();
     // the lane's ray
     int64_t id = -1;
     bool live = false, retired = false;
@@ -626,6 +673,64 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
             continue;
         }
         if (!live) continue;
+        // An empty brick is crossed in one jump: its exit time is the
+        // boundary time the walk would take at the brick's last cell along
+        // the ray (the same expression), so the walk resumes in the next
+        // cell with the same entry time; tau, the colour and the checkpoints
+        // (which take tau there) do not change across empty cells.
+        {
+            const int bx = cx / kFarBrick, by = cy / kFarBrick, bz = cz / kFarBrick;
+            const int bi = (bz * bdy + by) * bdx + bx;
+            if (!((s_bits[bi >> 5] >> (bi & 31)) & 1u)) {
+                const int ex = sx > 0 ? min(bx * kFarBrick + kFarBrick - 1, F.dims[0] - 1) : bx * kFarBrick;
+                const int ey = sy > 0 ? min(by * kFarBrick + kFarBrick - 1, F.dims[1] - 1) : by * kFarBrick;
+                const int ez = sz > 0 ? min(bz * kFarBrick + kFarBrick - 1, F.dims[2] - 1) : bz * kFarBrick;
+                const float tbx = far_tnext(sx, ex, F.lo[0], h, ox, dx), tby = far_tnext(sy, ey, F.lo[1], h, oy, dy),
+                            tbz = far_tnext(sz, ez, F.lo[2], h, oz, dz);
+                const int jax = (tbx <= tby && tbx <= tbz) ? 0 : (tby <= tbz ? 1 : 2);
+                const float tex = fminf(jax == 0 ? tbx : (jax == 1 ? tby : tbz), tb);
+                if (tex > tc) {
+                    while (kn < 5 && ckn < tex) {
+                        if (kn == 0) tk0 = tau;
+                        else if (kn == 1) tk1 = tau;
+                        else if (kn == 2) tk2 = tau;
+                        else if (kn == 3) tk3 = tau;
+                        else tk4 = tau;
+                        ++kn;
+                        ckn = kn < 5 ? fmaf((float)(2 << kn), h, t0) : INFINITY;
+                    }
+                    tc = tex;
+                    bool end = !(tex < tb);
+                    if (!end) {
+                        // one cell beyond the brick along the exit axis; the
+                        // others where the ray is, kept inside the brick
+                        const int lx0 = bx * kFarBrick, ly0 = by * kFarBrick, lz0 = bz * kFarBrick;
+                        const int px = min(max(far_cell0(ox, dx, tex, F.lo[0], h, F.dims[0]), lx0),
+                                           min(lx0 + kFarBrick - 1, F.dims[0] - 1));
+                        const int py = min(max(far_cell0(oy, dy, tex, F.lo[1], h, F.dims[1]), ly0),
+                                           min(ly0 + kFarBrick - 1, F.dims[1] - 1));
+                        const int pz = min(max(far_cell0(oz, dz, tex, F.lo[2], h, F.dims[2]), lz0),
+                                           min(lz0 + kFarBrick - 1, F.dims[2] - 1));
+                        cx = jax == 0 ? ex + sx : px;
+                        cy = jax == 1 ? ey + sy : py;
+                        cz = jax == 2 ? ez + sz : pz;
+                        end = cx < 0 || cx >= F.dims[0] || cy < 0 || cy >= F.dims[1] || cz < 0 || cz >= F.dims[2];
+                        if (!end) {
+                            tnx = far_tnext(sx, cx, F.lo[0], h, ox, dx);
+                            tny = far_tnext(sy, cy, F.lo[1], h, oy, dy);
+                            tnz = far_tnext(sz, cz, F.lo[2], h, oz, dz);
+                        }
+                    }
+                    ++it;
+                    if (end || it >= max_steps || !(tc < tb)) {
+                        far_write(feats, id, tk0 < 0.f ? tau : tk0, tk1 < 0.f ? tau : tk1, tk2 < 0.f ? tau : tk2,
+                                  tk3 < 0.f ? tau : tk3, tk4 < 0.f ? tau : tk4, tau, L0, L1, L2);
+                        live = false;
+                    }
+                    continue;
+                }
+            }
+        }
         // one cell of the walk
         const int ax = (tnx <= tny && tnx <= tnz) ? 0 : (tny <= tnz ? 1 : 2);
         float te = fminf(ax == 0 ? tnx : (ax == 1 ? tny : tnz), tb);
@@ -1381,6 +1486,7 @@ SurrFeatLayout surr_feat_layout(int64_t N, int32_t P, int32_t R)
     L.fhdr = o;   o = align256(o + sizeof(FarGrid));
     L.fmm = o;    o = align256(o + 8 * sizeof(int32_t));
     L.fctr = o;   o = align256(o + sizeof(unsigned long long));
+    L.fbrick = o; o = align256(o + sizeof(uint32_t) * (size_t)kFarBrickWords);
     const size_t cells = (size_t)kFarCells * kFarCells * kFarCells;
     L.facc = o;   o = align256(o + 4 * sizeof(unsigned long long) * cells);
     L.fcells = o; o = align256(o + sizeof(float4) * cells);
@@ -1437,6 +1543,8 @@ cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_
     far_zero_kernel<<<(unsigned)((4 * maxc + 255) / 256), 256, 0, s>>>(fg, acc);
     if (g.n > 0) far_splat_kernel<<<nb, 256, 0, s>>>(g, alpha_min, alpha_max, fg, acc);
     far_cells_kernel<<<(unsigned)((maxc + 255) / 256), 256, 0, s>>>(fg, acc, cells);
+    uint32_t* bricks = reinterpret_cast<uint32_t*>(ws + L.fbrick);
+    far_bricks_kernel<<<(unsigned)((kFarBrickWords * 32 + 255) / 256), 256, 0, s>>>(fg, cells, bricks);
     const int64_t rays = (int64_t)P * R * R;
     if (rays > 0) {
         // persistent: the CTAs that fit at once, never more than the rays need
@@ -1450,7 +1558,7 @@ cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_
         }
         const int64_t need = (rays + 255) / 256;
         far_march_kernel<<<(unsigned)(need < resident ? need : resident), 256, 0, s>>>(probe_pos, P, R, t0, tdirs, fg,
-                                                                                    cells, feats, next_ray);
+                                                                                    cells, feats, next_ray, bricks);
     }
     return cudaGetLastError();
 }
