@@ -491,7 +491,53 @@ __device__ __forceinline__ void eval_batch(const TraceK& k, const float3 o, cons
 __device__ __forceinline__ void sort_hits(uint64_t* key, float* alp, const int n, const int lane)
 {
     __syncwarp();
-    if (n > 32) {
+    if (n > 32 && n <= 64) {
+        // 64 elements in registers, two a lane: element lane (a) and
+        // lane + 32 (b); a bitonic network whose j = 32 steps compare a lane's
+        // own pair and whose others exchange over the lanes
+        uint64_t ka = key[lane], kb = lane + 32 < n ? key[lane + 32] : ~0ull;
+        float aa = alp[lane], ab = lane + 32 < n ? alp[lane + 32] : 0.f;
+#pragma unroll 1
+        for (int kk = 2; kk <= 64; kk <<= 1) {
+#pragma unroll 1
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                if (j == 32) {
+                    // (kk = 64: every pair ascending)
+                    if (kb < ka) {
+                        const uint64_t tk = ka;
+                        ka = kb;
+                        kb = tk;
+                        const float ta = aa;
+                        aa = ab;
+                        ab = ta;
+                    }
+                    continue;
+                }
+                const bool lower = (lane & j) == 0;
+                // element index lane (+ 32): ascending where (index & kk) == 0
+                const bool up_a = (lane & kk) == 0;
+                const bool up_b = ((lane + 32) & kk) == 0;
+                const uint64_t koa = __shfl_xor_sync(0xffffffffu, ka, j);
+                const float aoa = __shfl_xor_sync(0xffffffffu, aa, j);
+                const uint64_t kob = __shfl_xor_sync(0xffffffffu, kb, j);
+                const float aob = __shfl_xor_sync(0xffffffffu, ab, j);
+                if ((lower == up_a) ? (koa < ka) : (koa > ka)) {
+                    ka = koa;
+                    aa = aoa;
+                }
+                if ((lower == up_b) ? (kob < kb) : (kob > kb)) {
+                    kb = kob;
+                    ab = aob;
+                }
+            }
+        }
+        key[lane] = ka;
+        alp[lane] = aa;
+        if (lane + 32 < n) {
+            key[lane + 32] = kb;
+            alp[lane + 32] = ab;
+        }
+    } else if (n > 64) {
         int P2 = 64;
         while (P2 < n) P2 <<= 1;
         for (int i = n + lane; i < P2; i += 32) {
@@ -988,16 +1034,30 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
 
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s)
 {
+    const cudaError_t e = launch_bake_prep(g, alpha_min, L, ws, s);
+    return e != cudaSuccess ? e : launch_bake_grid(g, L, ws, s);
+}
+
+cudaError_t launch_bake_prep(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s)
+{
+    int32_t* bbox = reinterpret_cast<int32_t*>(ws + L.bbox);
+    GRec* rec = reinterpret_cast<GRec*>(ws + L.rec);
+    bbox_init_kernel<<<1, 32, 0, s>>>(bbox);
+    const unsigned nb = (unsigned)((g.n + 255) / 256);
+    if (g.n > 0) gauss_prep_kernel<<<nb, 256, 0, s>>>(g, alpha_min, rec, bbox, status_word());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bake_grid(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s)
+{
     GaussGrid* grid = reinterpret_cast<GaussGrid*>(ws + L.hdr);
     int32_t* bbox = reinterpret_cast<int32_t*>(ws + L.bbox);
     GRec* rec = reinterpret_cast<GRec*>(ws + L.rec);
     int32_t* cstart = reinterpret_cast<int32_t*>(ws + L.cell_start);
     int32_t* ccnt = reinterpret_cast<int32_t*>(ws + L.cell_cnt);
     unsigned int* status = status_word();
-    bbox_init_kernel<<<1, 32, 0, s>>>(bbox);
     const int bs = 256;
     const unsigned nb = (unsigned)((g.n + bs - 1) / bs);
-    if (g.n > 0) gauss_prep_kernel<<<nb, bs, 0, s>>>(g, alpha_min, rec, bbox, status);
     // Binning attempts, decided on the device (no host read-back): the
     // requested grid; if its cell lists overflow the workspace, a grid with
     // 1/16 of the cells; then one of at most 2 cells, whose lists (at most

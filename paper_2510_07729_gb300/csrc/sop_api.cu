@@ -4,6 +4,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <stdio.h>
 #include <string.h>
@@ -535,6 +536,43 @@ sop_status check_gauss(const sop_gaussians* g)
 }
 
 // features of every probe of `atlas`-sized sets into the run workspace
+// A second stream for the rebake's spot check, which needs the Gaussian
+// records but not the features or the network, so that it runs beside them:
+// one per device, made on first use with the greatest priority (its chain of
+// small launches is short of parallelism; the features fill the GPU), with
+// a fork and a join event. The mutex keeps the event pairs of overlapping
+// calls from interleaving while they are enqueued.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    bool tried = false, ok = false;
+};
+constexpr int kMaxDevices = 64;
+std::mutex g_side_mu;
+SideStream g_side[kMaxDevices];
+
+// the current device's side stream, or NULL when it cannot be made (the
+// rebake then runs on the caller's stream alone); call with g_side_mu held
+SideStream* side_stream()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    SideStream& r = g_side[dev];
+    if (!r.tried) {
+        r.tried = true;
+        int least = 0, greatest = 0;
+        r.ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+               cudaStreamCreateWithPriority(&r.s, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+               cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&r.join, cudaEventDisableTiming) == cudaSuccess;
+        cudaGetLastError();  // a failed creation leaves no error for later calls
+    }
+    return r.ok ? &r : nullptr;
+}
+
 sop_status surr_feats_into(const sop_surrogate* net, const sop_gaussians* g, const float* probe_pos, int32_t P,
                            int32_t R, const sop_bake_params* bp, float* feats, int32_t* list, char* w,
                            const SurrRunLayout& L, cudaStream_t s, const char* what)
@@ -754,29 +792,55 @@ sop_status sop_surrogate_infer(const sop_surrogate* net, const sop_gaussians* g,
     cudaStream_t s = (cudaStream_t)stream;
     char* w = (char*)ws;
     float* feats = (float*)(w + L.feats);
-    // features (binning included) and the prediction of every probe
-    if ((st = surr_feats_into(net, g, out->probe_pos, P, R, params, feats, nullptr, w, L, s,
-                              "sop_surrogate_infer (features)")) != SOP_OK)
-        return st;
-    st = cuda_status(sop::surr_infer(net->state, feats, nullptr, P, P, *out, s), "sop_surrogate_infer (network)");
-    if (st != SOP_OK) return st;
-    if ((st = cuda_status(sop::launch_gutter_fill(*out, s), "sop_surrogate_infer (border)")) != SOP_OK) return st;
-    // spot check: trace the sample into the workspace's atlas and compare
     const int32_t n_spot = std::max(1, std::min(P, (int32_t)ceil((double)spot_frac * P)));
     int32_t* ids = (int32_t*)(w + L.spot_ids);
     float* pos = (float*)(w + L.spot_pos);
-    if ((st = cuda_status(sop::launch_spot_pick(seed, P, n_spot, out->probe_pos, ids, pos, s),
-                          "sop_surrogate_infer (sample)")) != SOP_OK)
-        return st;
     sop_atlas spot = *out;
     spot.rgbo = w + L.spot_rgbo;
     spot.depth = out->depth ? w + L.spot_depth : nullptr;
     spot.P = n_spot;
     spot.probe_pos = pos;
     spot.probe_nrm = nullptr;
-    if ((st = cuda_status(sop::launch_bake_trace(spot, *params, L.B, w + L.bake, s), "sop_surrogate_infer (spot bake)")) !=
-        SOP_OK)
+    // the Gaussian records, which both branches read
+    if ((st = cuda_status(sop::launch_bake_prep(*g, params->alpha_min, L.B, w + L.bake, s),
+                          "sop_surrogate_infer (records)")) != SOP_OK)
         return st;
+    std::unique_lock<std::mutex> lock(g_side_mu);
+    SideStream* side = side_stream();
+    if (!side) lock.unlock();
+    cudaStream_t b = side ? side->s : s;
+    if (side && (st = cuda_status(cudaEventRecord(side->fork, s) == cudaSuccess
+                                      ? cudaStreamWaitEvent(b, side->fork, 0)
+                                      : cudaGetLastError(),
+                                  "sop_surrogate_infer (fork)")) != SOP_OK)
+        return st;
+    // branch b: the binning grid, then the spot check's sample traced into
+    // the workspace's atlas
+    st = cuda_status(sop::launch_bake_grid(*g, L.B, w + L.bake, b), "sop_surrogate_infer (binning)");
+    if (st == SOP_OK) st = cuda_status(sop::launch_bake_fill(*g, L.B, w + L.bake, b), "sop_surrogate_infer (binning)");
+    if (st == SOP_OK)
+        st = cuda_status(sop::launch_spot_pick(seed, P, n_spot, out->probe_pos, ids, pos, b),
+                         "sop_surrogate_infer (sample)");
+    if (st == SOP_OK)
+        st = cuda_status(sop::launch_bake_trace(spot, *params, L.B, w + L.bake, b), "sop_surrogate_infer (spot bake)");
+    // branch s: features and the prediction of every probe
+    if (st == SOP_OK)
+        st = cuda_status(sop::surr_features(*g, out->probe_pos, P, R, net->r_near, params->alpha_min,
+                                            params->alpha_max, w + L.bake + L.B.rec, feats, nullptr, w + L.feat, s),
+                         "sop_surrogate_infer (features)");
+    if (st == SOP_OK)
+        st = cuda_status(sop::surr_infer(net->state, feats, nullptr, P, P, *out, s), "sop_surrogate_infer (network)");
+    if (st == SOP_OK) st = cuda_status(sop::launch_gutter_fill(*out, s), "sop_surrogate_infer (border)");
+    // join (also after a failed launch, so that nothing of b outlives the call)
+    if (side) {
+        const sop_status sj = cuda_status(cudaEventRecord(side->join, b) == cudaSuccess
+                                              ? cudaStreamWaitEvent(s, side->join, 0)
+                                              : cudaGetLastError(),
+                                          "sop_surrogate_infer (join)");
+        lock.unlock();
+        if (st == SOP_OK) st = sj;
+    }
+    if (st != SOP_OK) return st;
     float* sums = (float*)(w + L.sums);
     if ((st = cuda_status(sop::launch_atlas_compare(spot, nullptr, *out, ids, n_spot, sums, s),
                           "sop_surrogate_infer (compare)")) != SOP_OK)

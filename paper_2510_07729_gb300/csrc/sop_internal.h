@@ -94,6 +94,10 @@ constexpr size_t kBakeEntryBytes = 16;
 // density: grid cells per Gaussian (0: the default, 0.35)
 BakeLayout bake_layout(int64_t N, int64_t entries_cap, float density = 0.f);
 cudaError_t launch_bake_bin(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s);
+// launch_bake_bin in two parts: the Gaussian records (and the bounding box)
+// and the binning grid built from them
+cudaError_t launch_bake_prep(const sop_gaussians& g, float alpha_min, const BakeLayout& L, char* ws, cudaStream_t s);
+cudaError_t launch_bake_grid(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s);
 cudaError_t launch_bake_fill(const sop_gaussians& g, const BakeLayout& L, char* ws, cudaStream_t s);
 // run_if: when not NULL, the launches do nothing unless *run_if != 0 (device)
 // stats: the trace's counters, whose truncation bit goes to the status word

@@ -185,6 +185,8 @@ __device__ __forceinline__ void two_diff_s(float a, float b, float& hi, float& l
 
 constexpr int kNearThreads = 256;
 constexpr int kNearRec = 8;  // staged float4 per listed Gaussian
+constexpr int kSelCap = 2 * kNearCap;  // candidates sorted after the selection of the list's last key
+static_assert(kNearThreads == 256, "one histogram bin a thread");
 static_assert(kNearCap * kNearRec * 16 <= kCandCap * 12, "the staged records must fit the candidate buffer");
 
 __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
@@ -192,8 +194,14 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* ckey = reinterpret_cast<uint64_t*>(smem);                 // [kCandCap]
     int32_t* cidx = reinterpret_cast<int32_t*>(ckey + kCandCap);          // [kCandCap]
+    // the selection ([kSelCap]) in the candidate arrays' tail, used while
+    // the candidates leave it free
+    uint64_t* skey = ckey + (kCandCap - kSelCap);
+    int32_t* sidx = cidx + (kCandCap - kSelCap);
     float4* srec = reinterpret_cast<float4*>(smem);                       // [kNearCap][kNearRec], after the sort
-    __shared__ int32_t s_count, s_box[6];
+    __shared__ int32_t s_count, s_box[6], s_need, s_sel;
+    __shared__ int32_t s_hist[256];
+    __shared__ uint64_t s_prefix;
     __shared__ int32_t s_list[kNearCap];
     const int tid = threadIdx.x, p = blockIdx.x;
     const float3 pp = load3(k.probe_pos, p);
@@ -251,12 +259,92 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
     const int total = s_count;
     const int n = total < kCandCap ? total : kCandCap;
     if (total > kCandCap && tid == 0 && k.status) atomicOr(k.status, SOP_DEVSTAT_CAPACITY);
-    // bitonic sort of the candidates by (key, index), padded to a power of two
+    // The list is the first kNearCap candidates in (key, index) order. With
+    // more candidates than that, the kNearCap-th smallest key K is found
+    // first, 8 bits at a time from the top (a 256-bin histogram of the
+    // candidates that match the digits found so far), and only the
+    // candidates with key <= K are sorted: kNearCap of them, plus any others
+    // equal to K (all candidates, should more than kSelCap share the key K
+    // or more than kCandCap - kSelCap be found).
+    uint64_t* lkey = ckey;
+    int32_t* lidx = cidx;
+    int nsort = n;
+    if (n > kNearCap && n <= kCandCap - kSelCap) {
+        const int bits = 64 - __clzll((long long)(k.r2key > 0 ? k.r2key : 1));
+        if (tid == 0) {
+            s_prefix = 0;
+            s_need = kNearCap;
+        }
+        for (int sh = ((bits + 7) / 8 - 1) * 8; sh >= 0; sh -= 8) {
+            s_hist[tid] = 0;
+            __syncthreads();
+            const uint64_t pre = s_prefix;
+            for (int i = tid; i < n; i += kNearThreads) {
+                const uint64_t kv = ckey[i];
+                if (sh + 8 >= 64 || (kv >> (sh + 8)) == (pre >> (sh + 8))) atomicAdd(&s_hist[(kv >> sh) & 255], 1);
+            }
+            __syncthreads();
+            if (tid < 32) {
+                // lane l holds bins 8l .. 8l+7; the bin holding the need-th key
+                int c[8], sum = 0;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    c[b] = s_hist[8 * tid + b];
+                    sum += c[b];
+                }
+                int incl = sum;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (tid >= off) incl += v;
+                }
+                const int need = s_need, excl = incl - sum;
+                if (excl < need && need <= incl) {
+                    int r = need - excl, b = 0;
+                    bool found = false;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (!found) {
+                            if (r <= c[q]) {
+                                b = q;
+                                found = true;
+                            } else {
+                                r -= c[q];
+                            }
+                        }
+                    }
+                    s_prefix = pre | ((uint64_t)(8 * tid + b) << sh);
+                    s_need = r;
+                }
+            }
+            __syncthreads();
+        }
+        const uint64_t K = s_prefix;
+        if (tid == 0) s_sel = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += kNearThreads) {
+            const uint64_t kv = ckey[i];
+            if (kv <= K) {
+                const int pos = atomicAdd(&s_sel, 1);
+                if (pos < kSelCap) {
+                    skey[pos] = kv;
+                    sidx[pos] = cidx[i];
+                }
+            }
+        }
+        __syncthreads();
+        if (s_sel <= kSelCap) {
+            lkey = skey;
+            lidx = sidx;
+            nsort = s_sel;
+        }
+    }
+    // bitonic sort by (key, index), padded to a power of two
     int n2 = 32;
-    while (n2 < n) n2 <<= 1;
-    for (int i = n + tid; i < n2; i += kNearThreads) {
-        ckey[i] = UINT64_MAX;
-        cidx[i] = INT32_MAX;
+    while (n2 < nsort) n2 <<= 1;
+    for (int i = nsort + tid; i < n2; i += kNearThreads) {
+        lkey[i] = UINT64_MAX;
+        lidx[i] = INT32_MAX;
     }
     __syncthreads();
     for (int kk = 2; kk <= n2; kk <<= 1) {
@@ -264,14 +352,14 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
             for (int i = tid; i < n2; i += kNearThreads) {
                 const int ixj = i ^ j;
                 if (ixj > i) {
-                    const uint64_t a = ckey[i], b = ckey[ixj];
-                    const int32_t ia = cidx[i], ib = cidx[ixj];
+                    const uint64_t a = lkey[i], b = lkey[ixj];
+                    const int32_t ia = lidx[i], ib = lidx[ixj];
                     const bool gt = a > b || (a == b && ia > ib);
                     if (gt == ((i & kk) == 0)) {
-                        ckey[i] = b;
-                        ckey[ixj] = a;
-                        cidx[i] = ib;
-                        cidx[ixj] = ia;
+                        lkey[i] = b;
+                        lkey[ixj] = a;
+                        lidx[i] = ib;
+                        lidx[ixj] = ia;
                     }
                 }
             }
@@ -280,14 +368,14 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
     }
     const int nl = n < kNearCap ? n : kNearCap;
     for (int i = tid; i < kNearCap; i += kNearThreads) {
-        const int32_t g = i < nl ? cidx[i] : -1;
+        const int32_t g = i < nl ? lidx[i] : -1;
         s_list[i] = g;
         if (k.list) k.list[(int64_t)p * kNearCap + i] = g;
     }
     if (tid == 0) {
         // one square root per probe, in double, so that the far field's
         // start is the correctly rounded distance
-        k.t0[p] = nl == kNearCap ? (float)(sqrt((double)ckey[kNearCap - 1]) * (1.0 / 1048576.0)) : k.r_n;
+        k.t0[p] = nl == kNearCap ? (float)(sqrt((double)lkey[kNearCap - 1]) * (1.0 / 1048576.0)) : k.r_n;
     }
     __syncthreads();
     // stage what each listed Gaussian contributes to every texel of this
@@ -561,6 +649,19 @@ __device__ __forceinline__ int far_cell0(float o, float d, float t, float lo, fl
     return ci < 0 ? 0 : (ci >= dim ? dim - 1 : ci);
 }
 
+// the same boundary time with the reciprocal of the direction (the march:
+// one division per axis and ray instead of one per step)
+__device__ __forceinline__ float far_tn(int st, int c, float lo, float h, float o, float id)
+{
+    return st == 0 ? INFINITY : (fmaf((float)(c + (st > 0 ? 1 : 0)), h, lo) - o) * id;
+}
+
+__device__ __forceinline__ int far_cell_at(float o, float d, float t, float lo, float ih, int dim)
+{
+    const int ci = (int)floorf((fmaf(t, d, o) - lo) * ih);
+    return ci < 0 ? 0 : (ci >= dim ? dim - 1 : ci);
+}
+
 __device__ __forceinline__ float far_tnext(int st, int c, float lo, float h, float o, float d)
 {
     return st == 0 ? INFINITY : (lo + (float)(c + (st > 0 ? 1 : 0)) * h - o) / d;
@@ -603,7 +704,7 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
     const int RR = R * R;
     const int64_t total = (int64_t)P * RR;
     const FarGrid F = *fg;
-    const float h = F.h;
+    const float h = F.h, ih = 1.f / F.h;
     // at most one step per cell along each axis: bounded by the dims
     const int max_steps = F.dims[0] + F.dims[1] + F.dims[2] + 3;
     const int bdx = (F.dims[0] + kFarBrick - 1) / kFarBrick, bdy = (F.dims[1] + kFarBrick - 1) / kFarBrick;
@@ -614,6 +715,7 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
     int64_t id = -1;
     bool live = false, retired = false;
     float ox = 0.f, oy = 0.f, oz = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, t0 = 0.f;
+    float idx = 0.f, idy = 0.f, idz = 0.f;  // 1 / d (unused along an axis with d = 0)
     float tc = 0.f, tb = 0.f, tau = 0.f, L0 = 0.f, L1 = 0.f, L2 = 0.f;
     float tnx = 0.f, tny = 0.f, tnz = 0.f, ckn = 0.f;
     float tk0 = 0.f, tk1 = 0.f, tk2 = 0.f, tk3 = 0.f, tk4 = 0.f;  // tau at the checkpoints
@@ -642,6 +744,9 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
                     dx = d.x;
                     dy = d.y;
                     dz = d.z;
+                    idx = 1.f / dx;
+                    idy = 1.f / dy;
+                    idz = 1.f / dz;
                     t0 = __ldg(t0p + p);
                     tau = L0 = L1 = L2 = 0.f;
                     tk0 = tk1 = tk2 = tk3 = tk4 = -1.f;  // -1: not reached yet
@@ -655,15 +760,15 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
                     far_slab(oz, dz, F.lo[2], F.lo[2] + F.dims[2] * h, ta, tb);
                     live = ta < tb;
                     if (live) {
-                        cx = far_cell0(ox, dx, ta, F.lo[0], h, F.dims[0]);
-                        cy = far_cell0(oy, dy, ta, F.lo[1], h, F.dims[1]);
-                        cz = far_cell0(oz, dz, ta, F.lo[2], h, F.dims[2]);
+                        cx = far_cell_at(ox, dx, ta, F.lo[0], ih, F.dims[0]);
+                        cy = far_cell_at(oy, dy, ta, F.lo[1], ih, F.dims[1]);
+                        cz = far_cell_at(oz, dz, ta, F.lo[2], ih, F.dims[2]);
                         sx = dx > 0.f ? 1 : (dx < 0.f ? -1 : 0);
                         sy = dy > 0.f ? 1 : (dy < 0.f ? -1 : 0);
                         sz = dz > 0.f ? 1 : (dz < 0.f ? -1 : 0);
-                        tnx = far_tnext(sx, cx, F.lo[0], h, ox, dx);
-                        tny = far_tnext(sy, cy, F.lo[1], h, oy, dy);
-                        tnz = far_tnext(sz, cz, F.lo[2], h, oz, dz);
+                        tnx = far_tn(sx, cx, F.lo[0], h, ox, idx);
+                        tny = far_tn(sy, cy, F.lo[1], h, oy, idy);
+                        tnz = far_tn(sz, cz, F.lo[2], h, oz, idz);
                         tc = ta;
                     } else {
                         far_write(feats, id, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
@@ -679,14 +784,14 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
         // cell with the same entry time; tau, the colour and the checkpoints
         // (which take tau there) do not change across empty cells.
         {
-            const int bx = cx / kFarBrick, by = cy / kFarBrick, bz = cz / kFarBrick;
+            const int bx = (unsigned)cx / kFarBrick, by = (unsigned)cy / kFarBrick, bz = (unsigned)cz / kFarBrick;
             const int bi = (bz * bdy + by) * bdx + bx;
             if (!((s_bits[bi >> 5] >> (bi & 31)) & 1u)) {
                 const int ex = sx > 0 ? min(bx * kFarBrick + kFarBrick - 1, F.dims[0] - 1) : bx * kFarBrick;
                 const int ey = sy > 0 ? min(by * kFarBrick + kFarBrick - 1, F.dims[1] - 1) : by * kFarBrick;
                 const int ez = sz > 0 ? min(bz * kFarBrick + kFarBrick - 1, F.dims[2] - 1) : bz * kFarBrick;
-                const float tbx = far_tnext(sx, ex, F.lo[0], h, ox, dx), tby = far_tnext(sy, ey, F.lo[1], h, oy, dy),
-                            tbz = far_tnext(sz, ez, F.lo[2], h, oz, dz);
+                const float tbx = far_tn(sx, ex, F.lo[0], h, ox, idx), tby = far_tn(sy, ey, F.lo[1], h, oy, idy),
+                            tbz = far_tn(sz, ez, F.lo[2], h, oz, idz);
                 const int jax = (tbx <= tby && tbx <= tbz) ? 0 : (tby <= tbz ? 1 : 2);
                 const float tex = fminf(jax == 0 ? tbx : (jax == 1 ? tby : tbz), tb);
                 if (tex > tc) {
@@ -705,20 +810,20 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
                         // one cell beyond the brick along the exit axis; the
                         // others where the ray is, kept inside the brick
                         const int lx0 = bx * kFarBrick, ly0 = by * kFarBrick, lz0 = bz * kFarBrick;
-                        const int px = min(max(far_cell0(ox, dx, tex, F.lo[0], h, F.dims[0]), lx0),
+                        const int px = min(max(far_cell_at(ox, dx, tex, F.lo[0], ih, F.dims[0]), lx0),
                                            min(lx0 + kFarBrick - 1, F.dims[0] - 1));
-                        const int py = min(max(far_cell0(oy, dy, tex, F.lo[1], h, F.dims[1]), ly0),
+                        const int py = min(max(far_cell_at(oy, dy, tex, F.lo[1], ih, F.dims[1]), ly0),
                                            min(ly0 + kFarBrick - 1, F.dims[1] - 1));
-                        const int pz = min(max(far_cell0(oz, dz, tex, F.lo[2], h, F.dims[2]), lz0),
+                        const int pz = min(max(far_cell_at(oz, dz, tex, F.lo[2], ih, F.dims[2]), lz0),
                                            min(lz0 + kFarBrick - 1, F.dims[2] - 1));
                         cx = jax == 0 ? ex + sx : px;
                         cy = jax == 1 ? ey + sy : py;
                         cz = jax == 2 ? ez + sz : pz;
                         end = cx < 0 || cx >= F.dims[0] || cy < 0 || cy >= F.dims[1] || cz < 0 || cz >= F.dims[2];
                         if (!end) {
-                            tnx = far_tnext(sx, cx, F.lo[0], h, ox, dx);
-                            tny = far_tnext(sy, cy, F.lo[1], h, oy, dy);
-                            tnz = far_tnext(sz, cz, F.lo[2], h, oz, dz);
+                            tnx = far_tn(sx, cx, F.lo[0], h, ox, idx);
+                            tny = far_tn(sy, cy, F.lo[1], h, oy, idy);
+                            tnz = far_tn(sz, cz, F.lo[2], h, oz, idz);
                         }
                     }
                     ++it;
@@ -735,7 +840,7 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
         const int ax = (tnx <= tny && tnx <= tnz) ? 0 : (tny <= tnz ? 1 : 2);
         float te = fminf(ax == 0 ? tnx : (ax == 1 ? tny : tnz), tb);
         te = fmaxf(te, tc);
-        const float4 cv = __ldg(cells + ((int64_t)cz * F.dims[1] + cy) * F.dims[0] + cx);
+        const float4 cv = __ldg(cells + (cz * F.dims[1] + cy) * F.dims[0] + cx);  // < 2^21 cells
         // checkpoints inside this segment take tau at their position (they
         // are increasing: only the next one can be due)
         while (kn < 5 && ckn < te) {
@@ -762,15 +867,15 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
             if (ax == 0) {
                 cx += sx;
                 end = cx < 0 || cx >= F.dims[0];
-                if (!end) tnx = far_tnext(sx, cx, F.lo[0], h, ox, dx);
+                if (!end) tnx = far_tn(sx, cx, F.lo[0], h, ox, idx);
             } else if (ax == 1) {
                 cy += sy;
                 end = cy < 0 || cy >= F.dims[1];
-                if (!end) tny = far_tnext(sy, cy, F.lo[1], h, oy, dy);
+                if (!end) tny = far_tn(sy, cy, F.lo[1], h, oy, idy);
             } else {
                 cz += sz;
                 end = cz < 0 || cz >= F.dims[2];
-                if (!end) tnz = far_tnext(sz, cz, F.lo[2], h, oz, dz);
+                if (!end) tnz = far_tn(sz, cz, F.lo[2], h, oz, idz);
             }
         }
         ++it;
