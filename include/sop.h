@@ -522,7 +522,12 @@ sop_status sop_surrogate_predict(const sop_surrogate* net, const float* feats, c
  * traced maps. out_spot_err (device float) receives err, out_fell_back
  * (device int32) 1 after a fallback, else 0. 0 < spot_frac <= 1.
  * Asynchronous: no host synchronisation, the decision is taken on the
- * device. */
+ * device. The spot check runs on a second stream of the library's (made
+ * once per device, greatest priority) beside the features and the network;
+ * it waits for the work queued on `stream` before the call, and work queued
+ * on `stream` after the call waits for it. Calls from several host threads
+ * are serialised while they are queued. Not to be called across a
+ * cudaDeviceReset (the second stream does not survive it). */
 sop_status sop_surrogate_infer(const sop_surrogate* net, const sop_gaussians* g, const sop_atlas* out,
                                const sop_bake_params* params, float spot_frac, float tau, uint64_t seed,
                                float* out_spot_err, int32_t* out_fell_back, void* ws, size_t ws_bytes, void* stream);

@@ -536,15 +536,16 @@ sop_status check_gauss(const sop_gaussians* g)
 }
 
 // features of every probe of `atlas`-sized sets into the run workspace
-// A second stream for the rebake's spot check, which needs the Gaussian
-// records but not the features or the network, so that it runs beside them:
-// one per device, made on first use with the greatest priority (its chain of
-// small launches is short of parallelism; the features fill the GPU), with
-// a fork and a join event. The mutex keeps the event pairs of overlapping
-// calls from interleaving while they are enqueued.
+// Two more streams for the rebake. The spot check needs the Gaussian records
+// but not the features or the network, so it runs beside them on `s`, made
+// with the greatest priority (its chain of small launches is short of
+// parallelism; the features fill the GPU). The far field's grid and march
+// run on `far`, beside the near field's composite. One pair per device, made
+// on first use, with the events that fork and join them. The mutex keeps the
+// events of overlapping calls from interleaving while they are enqueued.
 struct SideStream {
-    cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t s = nullptr, far = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, list = nullptr, far_done = nullptr;
     bool tried = false, ok = false;
 };
 constexpr int kMaxDevices = 64;
@@ -566,8 +567,11 @@ SideStream* side_stream()
         int least = 0, greatest = 0;
         r.ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
                cudaStreamCreateWithPriority(&r.s, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+               cudaStreamCreateWithFlags(&r.far, cudaStreamNonBlocking) == cudaSuccess &&
                cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming) == cudaSuccess &&
-               cudaEventCreateWithFlags(&r.join, cudaEventDisableTiming) == cudaSuccess;
+               cudaEventCreateWithFlags(&r.join, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&r.list, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&r.far_done, cudaEventDisableTiming) == cudaSuccess;
         cudaGetLastError();  // a failed creation leaves no error for later calls
     }
     return r.ok ? &r : nullptr;
@@ -824,10 +828,14 @@ sop_status sop_surrogate_infer(const sop_surrogate* net, const sop_gaussians* g,
     if (st == SOP_OK)
         st = cuda_status(sop::launch_bake_trace(spot, *params, L.B, w + L.bake, b), "sop_surrogate_infer (spot bake)");
     // branch s: features and the prediction of every probe
-    if (st == SOP_OK)
+    if (st == SOP_OK) {
+        sop::SurrStreams ss{side ? side->far : nullptr, side ? side->fork : nullptr, side ? side->list : nullptr,
+                            side ? side->far_done : nullptr};
         st = cuda_status(sop::surr_features(*g, out->probe_pos, P, R, net->r_near, params->alpha_min,
-                                            params->alpha_max, w + L.bake + L.B.rec, feats, nullptr, w + L.feat, s),
+                                            params->alpha_max, w + L.bake + L.B.rec, feats, nullptr, w + L.feat, s,
+                                            side ? &ss : nullptr),
                          "sop_surrogate_infer (features)");
+    }
     if (st == SOP_OK)
         st = cuda_status(sop::surr_infer(net->state, feats, nullptr, P, P, *out, s), "sop_surrogate_infer (network)");
     if (st == SOP_OK) st = cuda_status(sop::launch_gutter_fill(*out, s), "sop_surrogate_infer (border)");

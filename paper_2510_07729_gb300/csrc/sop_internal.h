@@ -140,14 +140,22 @@ cudaError_t surr_get_grad(const char* state, float* grad, cudaStream_t s);
 cudaError_t surr_state_io(char* state, float* master, float* m, float* v, int32_t* step, bool to_device,
                           cudaStream_t s);
 struct SurrFeatLayout {
-    size_t sites, tdirs, t0, fhdr, fmm, fctr, fbrick, facc, fcells, total;
+    size_t sites, tdirs, t0, fhdr, fmm, fctr, list, fbrick, facc, fcells, total;
+};
+// Streams of the features' two branches: the far field (grid, march) runs on
+// `far`, after the event `fork` that the caller recorded on the main stream;
+// `list` and `far_done` are recorded by surr_features (the near list done;
+// the far march done, which the main stream then waits for).
+struct SurrStreams {
+    cudaStream_t far;
+    cudaEvent_t fork, list, far_done;
 };
 SurrFeatLayout surr_feat_layout(int64_t N, int32_t P, int32_t R);
 // features [P][R*R][18] of every texel; bake_rec: the Gaussian records of a
 // binned bake workspace; list [P][near cap] or NULL
 cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_t P, int32_t R, float r_n,
                           float alpha_min, float alpha_max, const char* bake_rec, float* feats, int32_t* list,
-                          char* ws, cudaStream_t s);
+                          char* ws, cudaStream_t s, const SurrStreams* ss = nullptr);
 // `steps` Adam steps on B probes each (pid, or drawn from seed); ws holds
 // surr_train_ws_bytes() (drawn ids, per-CTA gradient and loss sums)
 size_t surr_train_ws_bytes();

@@ -149,10 +149,13 @@ __global__ void surr_init_kernel(float* __restrict__ master, uint64_t seed)
 }
 
 // ---------------------------------------------------------------------------
-// Near field. One CTA per probe: the centres within r_n (integer keys) are
-// gathered from the site grid into shared memory, sorted by (key, index)
-// (bitonic), the first kNearCap kept; their bake records are staged in
-// shared memory and each thread composites them along its texels' rays.
+// Near field, in two launches of one CTA per probe. The list: the centres
+// within r_n (integer keys) are gathered from the site grid into shared
+// memory, the kNearCap-th key is selected and the candidates up to it are
+// sorted by (key, index); the list and t0 (where the far field starts) go to
+// memory. The composite: the listed Gaussians' terms are staged in shared
+// memory and each thread composites them along its texels' rays. Between
+// the two, the far march (which needs t0) can start.
 // ---------------------------------------------------------------------------
 struct NearK {
     const float* probe_pos;
@@ -167,7 +170,7 @@ struct NearK {
     const float4* tdirs;  // [R*R] texel directions
     float alpha_min, alpha_max;
     float* feats;         // [P][R*R][kIn]
-    int32_t* list;        // [P][kNearCap] or NULL
+    int32_t* list;        // [P][kNearCap]
     float* t0;            // [P]
     unsigned int* status;
 };
@@ -187,9 +190,8 @@ constexpr int kNearThreads = 256;
 constexpr int kNearRec = 8;  // staged float4 per listed Gaussian
 constexpr int kSelCap = 2 * kNearCap;  // candidates sorted after the selection of the list's last key
 static_assert(kNearThreads == 256, "one histogram bin a thread");
-static_assert(kNearCap * kNearRec * 16 <= kCandCap * 12, "the staged records must fit the candidate buffer");
 
-__global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
+__global__ void __launch_bounds__(kNearThreads) surr_near_list_kernel(const NearK k)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* ckey = reinterpret_cast<uint64_t*>(smem);                 // [kCandCap]
@@ -198,11 +200,9 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
     // the candidates leave it free
     uint64_t* skey = ckey + (kCandCap - kSelCap);
     int32_t* sidx = cidx + (kCandCap - kSelCap);
-    float4* srec = reinterpret_cast<float4*>(smem);                       // [kNearCap][kNearRec], after the sort
     __shared__ int32_t s_count, s_box[6], s_need, s_sel;
     __shared__ int32_t s_hist[256];
     __shared__ uint64_t s_prefix;
-    __shared__ int32_t s_list[kNearCap];
     const int tid = threadIdx.x, p = blockIdx.x;
     const float3 pp = load3(k.probe_pos, p);
     const int32_t q[3] = {quantise_s(pp.x), quantise_s(pp.y), quantise_s(pp.z)};
@@ -367,19 +367,35 @@ __global__ void __launch_bounds__(kNearThreads) surr_near_kernel(const NearK k)
         }
     }
     const int nl = n < kNearCap ? n : kNearCap;
-    for (int i = tid; i < kNearCap; i += kNearThreads) {
-        const int32_t g = i < nl ? lidx[i] : -1;
-        s_list[i] = g;
-        if (k.list) k.list[(int64_t)p * kNearCap + i] = g;
-    }
+    for (int i = tid; i < kNearCap; i += kNearThreads) k.list[(int64_t)p * kNearCap + i] = i < nl ? lidx[i] : -1;
     if (tid == 0) {
         // one square root per probe, in double, so that the far field's
         // start is the correctly rounded distance
         k.t0[p] = nl == kNearCap ? (float)(sqrt((double)lkey[kNearCap - 1]) * (1.0 / 1048576.0)) : k.r_n;
     }
+}
+
+// The near field's second part: the listed Gaussians' terms staged in
+// shared memory, then one thread per texel composites them along its ray.
+__global__ void __launch_bounds__(kNearThreads) surr_near_comp_kernel(const NearK k)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4* srec = reinterpret_cast<float4*>(smem);  // [kNearCap][kNearRec]
+    __shared__ int32_t s_list[kNearCap];
+    __shared__ int32_t s_nl;
+    const int tid = threadIdx.x, p = blockIdx.x;
+    const float3 pp = load3(k.probe_pos, p);
+    if (tid == 0) s_nl = 0;
     __syncthreads();
+    for (int i = tid; i < kNearCap; i += kNearThreads) {
+        const int32_t g = k.list[(int64_t)p * kNearCap + i];
+        s_list[i] = g;
+        if (g >= 0) atomicMax(&s_nl, i + 1);
+    }
+    __syncthreads();
+    const int nl = s_nl;
     // stage what each listed Gaussian contributes to every texel of this
-    // probe (over the candidate buffer), kNearRec float4 each:
+    // probe, kNearRec float4 each:
     //   0: mu - p, rho (the alpha_min bounding sphere; < 0: never a hit)
     //   1: |mu - p|^2, rho^2 (1 + 1e-4) (-1 when rho < 0), h = p - mu (x, y)
     //   2: h (z), the low parts l of p - mu = h + l (error-free)
@@ -1591,6 +1607,7 @@ SurrFeatLayout surr_feat_layout(int64_t N, int32_t P, int32_t R)
     L.fhdr = o;   o = align256(o + sizeof(FarGrid));
     L.fmm = o;    o = align256(o + 8 * sizeof(int32_t));
     L.fctr = o;   o = align256(o + sizeof(unsigned long long));
+    L.list = o;   o = align256(o + sizeof(int32_t) * (size_t)kNearCap * (size_t)(P > 0 ? P : 1));
     L.fbrick = o; o = align256(o + sizeof(uint32_t) * (size_t)kFarBrickWords);
     const size_t cells = (size_t)kFarCells * kFarCells * kFarCells;
     L.facc = o;   o = align256(o + 4 * sizeof(unsigned long long) * cells);
@@ -1599,14 +1616,36 @@ SurrFeatLayout surr_feat_layout(int64_t N, int32_t P, int32_t R)
     return L;
 }
 
-size_t surr_near_smem() { return (sizeof(uint64_t) + sizeof(int32_t)) * kCandCap; }
 
 cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_t P, int32_t R, float r_n,
                           float alpha_min, float alpha_max, const char* bake_rec, float* feats, int32_t* list,
-                          char* ws, cudaStream_t s)
+                          char* ws, cudaStream_t s, const SurrStreams* ss)
 {
     const SurrFeatLayout L = surr_feat_layout(g.n, P, R);
     unsigned int* status = status_word();
+    // the far field's grid on the far stream (it reads only the Gaussians),
+    // after the work queued on s before the call (ss->fork)
+    cudaStream_t sf = ss ? ss->far : s;
+    if (ss) {
+        const cudaError_t e = cudaStreamWaitEvent(sf, ss->fork, 0);
+        if (e != cudaSuccess) return e;
+    }
+    FarGrid* fg = reinterpret_cast<FarGrid*>(ws + L.fhdr);
+    int32_t* mm = reinterpret_cast<int32_t*>(ws + L.fmm);
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(ws + L.facc);
+    float4* cells = reinterpret_cast<float4*>(ws + L.fcells);
+    far_bbox_init_kernel<<<1, 32, 0, sf>>>(mm);
+    const unsigned nb = (unsigned)((g.n + 255) / 256);
+    if (g.n > 0) far_bbox_kernel<<<nb < 1024 ? nb : 1024, 256, 0, sf>>>(g, alpha_min, mm);
+    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(ws + L.fctr);
+    far_setup_kernel<<<1, 32, 0, sf>>>(mm, fg, next_ray);
+    const int64_t maxc = (int64_t)kFarCells * kFarCells * kFarCells;
+    far_zero_kernel<<<(unsigned)((4 * maxc + 255) / 256), 256, 0, sf>>>(fg, acc);
+    if (g.n > 0) far_splat_kernel<<<nb, 256, 0, sf>>>(g, alpha_min, alpha_max, fg, acc);
+    far_cells_kernel<<<(unsigned)((maxc + 255) / 256), 256, 0, sf>>>(fg, acc, cells);
+    uint32_t* bricks = reinterpret_cast<uint32_t*>(ws + L.fbrick);
+    far_bricks_kernel<<<(unsigned)((kFarBrickWords * 32 + 255) / 256), 256, 0, sf>>>(fg, cells, bricks);
+    // the near list and t0 on s
     const SitesGrid sg = launch_sites_grid(g.mean, (int32_t)g.n, ws + L.sites, s);
     float4* tdirs = reinterpret_cast<float4*>(ws + L.tdirs);
     surr_tdirs_kernel<<<(R * R + 127) / 128, 128, 0, s>>>(R, tdirs);
@@ -1627,29 +1666,24 @@ cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_
     nk.alpha_min = alpha_min;
     nk.alpha_max = alpha_max;
     nk.feats = feats;
-    nk.list = list;
+    nk.list = list ? list : reinterpret_cast<int32_t*>(ws + L.list);
     nk.t0 = t0;
     nk.status = status;
-    const size_t smem = surr_near_smem();
-    cudaError_t e = cudaFuncSetAttribute(surr_near_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem_list = (sizeof(uint64_t) + sizeof(int32_t)) * kCandCap;
+    const size_t smem_comp = sizeof(float4) * kNearRec * kNearCap;
+    cudaError_t e = cudaFuncSetAttribute(surr_near_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_list);
     if (e != cudaSuccess) return e;
-    if (P > 0) surr_near_kernel<<<P, kNearThreads, smem, s>>>(nk);
-    // far field
-    FarGrid* fg = reinterpret_cast<FarGrid*>(ws + L.fhdr);
-    int32_t* mm = reinterpret_cast<int32_t*>(ws + L.fmm);
-    unsigned long long* acc = reinterpret_cast<unsigned long long*>(ws + L.facc);
-    float4* cells = reinterpret_cast<float4*>(ws + L.fcells);
-    far_bbox_init_kernel<<<1, 32, 0, s>>>(mm);
-    const unsigned nb = (unsigned)((g.n + 255) / 256);
-    if (g.n > 0) far_bbox_kernel<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(g, alpha_min, mm);
-    unsigned long long* next_ray = reinterpret_cast<unsigned long long*>(ws + L.fctr);
-    far_setup_kernel<<<1, 32, 0, s>>>(mm, fg, next_ray);
-    const int64_t maxc = (int64_t)kFarCells * kFarCells * kFarCells;
-    far_zero_kernel<<<(unsigned)((4 * maxc + 255) / 256), 256, 0, s>>>(fg, acc);
-    if (g.n > 0) far_splat_kernel<<<nb, 256, 0, s>>>(g, alpha_min, alpha_max, fg, acc);
-    far_cells_kernel<<<(unsigned)((maxc + 255) / 256), 256, 0, s>>>(fg, acc, cells);
-    uint32_t* bricks = reinterpret_cast<uint32_t*>(ws + L.fbrick);
-    far_bricks_kernel<<<(unsigned)((kFarBrickWords * 32 + 255) / 256), 256, 0, s>>>(fg, cells, bricks);
+    if ((e = cudaFuncSetAttribute(surr_near_comp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_comp)) != cudaSuccess)
+        return e;
+    if (P > 0) surr_near_list_kernel<<<P, kNearThreads, smem_list, s>>>(nk);
+    // the far march on the far stream once t0 is known, beside the near
+    // composite on s
+    if (ss) {
+        if ((e = cudaEventRecord(ss->list, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sf, ss->list, 0)) != cudaSuccess) return e;
+    }
     const int64_t rays = (int64_t)P * R * R;
     if (rays > 0) {
         // persistent: the CTAs that fit at once, never more than the rays need
@@ -1662,8 +1696,14 @@ cudaError_t surr_features(const sop_gaussians& g, const float* probe_pos, int32_
             resident = (sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
         }
         const int64_t need = (rays + 255) / 256;
-        far_march_kernel<<<(unsigned)(need < resident ? need : resident), 256, 0, s>>>(probe_pos, P, R, t0, tdirs, fg,
-                                                                                    cells, feats, next_ray, bricks);
+        far_march_kernel<<<(unsigned)(need < resident ? need : resident), 256, 0, sf>>>(probe_pos, P, R, t0, tdirs,
+                                                                                     fg, cells, feats, next_ray,
+                                                                                     bricks);
+    }
+    if (P > 0) surr_near_comp_kernel<<<P, kNearThreads, smem_comp, s>>>(nk);
+    if (ss) {
+        if ((e = cudaEventRecord(ss->far_done, sf)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, ss->far_done, 0)) != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
