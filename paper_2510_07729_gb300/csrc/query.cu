@@ -1326,7 +1326,7 @@ __global__ void sites_fill_kernel(const float* __restrict__ pos, int32_t N, cons
 // K nearest sites (e.g. Gaussian centres) of M query points, exact, with the
 // same integer keys and tie rule as the probe search.
 // ---------------------------------------------------------------------------
-size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K)
+size_t sites_grid_bytes(int32_t N)
 {
     int g = 1;
     while ((int64_t)g * g * g < N) ++g;
@@ -1335,184 +1335,9 @@ size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K)
     o = align256(o + sizeof(int32_t) * (size_t)(cells + 1));
     o = align256(o + sizeof(int32_t) * (size_t)cells);
     o = align256(o + sizeof(int4) * (size_t)N);
-    o = align256(o + sizeof(float) * (size_t)M * K);
     o = align256(o + 8 * sizeof(int32_t));
     o = align256(o + sizeof(long long) * scan_scratch_count(cells));
     return o;
-}
-
-// ---------------------------------------------------------------------------
-// Exact K <= 32 nearest sites, one warp per query point (the surrogate's 32
-// nearest Gaussians of each probe: few points, many sites, large K, where a
-// thread per point leaves most SMs idle and keeps its list in local memory).
-// The warp holds the best 32 (key, index) pairs, one per lane, ascending
-// over the lanes. Lanes scan a cell's entries 32 at a time; entries that
-// beat the current 32nd best are queued in shared memory, and every 32
-// queued ones are sorted across the lanes (bitonic) and merged into the
-// list (the elementwise minimum of the list and the reversed batch holds
-// the 32 smallest of both, as a bitonic sequence, which five more steps
-// sort). The ring search and its stopping bound are those of knn_kernel, so
-// the K nearest, and their order, are the same.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool kv_less(uint64_t ka, int32_t ia, uint64_t kb, int32_t ib)
-{
-    return ka < kb || (ka == kb && ia < ib);
-}
-
-// one compare-exchange step of a bitonic network over the lanes: the lower
-// lane of a pair keeps the smaller pair when `up`, the larger otherwise
-__device__ __forceinline__ void kv_step(uint64_t& k, int32_t& i, int lane, int j, bool up)
-{
-    const uint64_t ko = __shfl_xor_sync(0xffffffffu, k, j);
-    const int32_t io = __shfl_xor_sync(0xffffffffu, i, j);
-    const bool lower = (lane & j) == 0;
-    const bool take = (lower == up) ? kv_less(ko, io, k, i) : kv_less(k, i, ko, io);
-    if (take) {
-        k = ko;
-        i = io;
-    }
-}
-
-constexpr int kKnnWarps = 4;
-
-// merges que[0, min(qn, 32)) into the list (bk, bi); drops them from the queue
-__device__ __forceinline__ void knn_merge(uint64_t* qk, int32_t* qi, int& qn, uint64_t& bk, int32_t& bi, int lane)
-{
-    const int take = qn < 32 ? qn : 32;
-    uint64_t ck = lane < take ? qk[lane] : UINT64_MAX;
-    int32_t ci = lane < take ? qi[lane] : INT32_MAX;
-    __syncwarp();
-    if (lane < qn - take) {
-        qk[lane] = qk[lane + take];
-        qi[lane] = qi[lane + take];
-    }
-    qn -= take;
-    __syncwarp();
-#pragma unroll
-    for (int kk = 2; kk <= 32; kk <<= 1)
-#pragma unroll
-        for (int j = kk >> 1; j > 0; j >>= 1) kv_step(ck, ci, lane, j, (lane & kk) == 0);
-    // reversed batch against the list: the smaller of each pair
-    const uint64_t rk = __shfl_sync(0xffffffffu, ck, 31 - lane);
-    const int32_t ri = __shfl_sync(0xffffffffu, ci, 31 - lane);
-    if (kv_less(rk, ri, bk, bi)) {
-        bk = rk;
-        bi = ri;
-    }
-#pragma unroll
-    for (int j = 16; j > 0; j >>= 1) kv_step(bk, bi, lane, j, true);
-}
-
-__global__ void __launch_bounds__(kKnnWarps * 32) knn_sites_warp_kernel(const float* __restrict__ x, int64_t M,
-                                                                         int32_t K,
-                                                                         const ProbeGrid* __restrict__ gridp,
-                                                                         const int32_t* __restrict__ cell_start,
-                                                                         const int4* __restrict__ entries,
-                                                                         int32_t* __restrict__ out_idx)
-{
-    __shared__ uint64_t s_qk[kKnnWarps][64];
-    __shared__ int32_t s_qi[kKnnWarps][64];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m = (int64_t)blockIdx.x * kKnnWarps + wib;
-    if (m >= M) return;  // warp-uniform
-    uint64_t* qk = s_qk[wib];
-    int32_t* qi = s_qi[wib];
-    const ProbeGrid G = *gridp;
-    const float3 xp = load3(x, m);
-    const int32_t q[3] = {quantise(xp.x), quantise(xp.y), quantise(xp.z)};
-    int c[3];
-    for (int a = 0; a < 3; ++a) {
-        const int64_t ca = floordiv((int64_t)q[a] - G.qmin[a], G.cs);
-        c[a] = (int)(ca < 0 ? 0 : (ca > G.dims[a] - 1 ? G.dims[a] - 1 : ca));
-    }
-    uint64_t bk = UINT64_MAX;  // lane l: the (l+1)-th best so far
-    int32_t bi = INT32_MAX;
-    int qn = 0;
-    for (int r = 0;; ++r) {
-        // the shell of ring r (the 24 r^2 + 2 cells at Chebyshev distance r
-        // from c: two z faces, two y faces without their z rows, two x faces
-        // without either), one cell per lane, clipped to the grid; the
-        // lanes' entries are then taken 32 at a time across the lanes
-        // (prefix sum of the lanes' counts)
-        const int64_t w = 2 * r + 1, wn = 2 * r - 1;
-        const int64_t nz = 2 * w * w, ny = 2 * w * wn, nshell = r == 0 ? 1 : nz + ny + 2 * wn * wn;
-        for (int64_t t0 = 0; t0 < nshell; t0 += 32) {
-            const int64_t t = t0 + lane;
-            int e0 = 0, cnt = 0;
-            if (t < nshell) {
-                int64_t dx = 0, dy = 0, dz = 0;
-                if (r > 0) {
-                    if (t < nz) {
-                        const int64_t u = t % (w * w);
-                        dx = u % w - r;
-                        dy = u / w - r;
-                        dz = t < w * w ? -r : r;
-                    } else if (t < nz + ny) {
-                        const int64_t t1 = t - nz, u = t1 % (w * wn);
-                        dx = u % w - r;
-                        dz = u / w - r + 1;
-                        dy = t1 < w * wn ? -r : r;
-                    } else {
-                        const int64_t t2 = t - nz - ny, u = t2 % (wn * wn);
-                        dy = u % wn - r + 1;
-                        dz = u / wn - r + 1;
-                        dx = t2 < wn * wn ? -r : r;
-                    }
-                }
-                const int64_t cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
-                if (cx >= 0 && cx < G.dims[0] && cy >= 0 && cy < G.dims[1] && cz >= 0 && cz < G.dims[2]) {
-                    const int cell = (int)((cz * G.dims[1] + cy) * G.dims[0] + cx);
-                    e0 = __ldg(cell_start + cell);
-                    cnt = __ldg(cell_start + cell + 1) - e0;
-                }
-            }
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int excl = incl - cnt;
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const uint64_t wk = __shfl_sync(0xffffffffu, bk, 31);
-            const int32_t wi = __shfl_sync(0xffffffffu, bi, 31);
-            for (int f0 = 0; f0 < total; f0 += 32) {
-                const int f = f0 + lane;
-                // owner: the last lane whose first flattened entry is <= f
-                int own = 0;
-#pragma unroll
-                for (int st = 16; st > 0; st >>= 1) {
-                    const int ex = __shfl_sync(0xffffffffu, excl, own + st);
-                    if (ex <= f) own += st;
-                }
-                const int e = __shfl_sync(0xffffffffu, e0, own) + f - __shfl_sync(0xffffffffu, excl, own);
-                bool pass = false;
-                uint64_t key = 0;
-                int32_t id = 0;
-                if (f < total) {
-                    const int4 en = __ldg(entries + e);
-                    key = qdist2(en.x, en.y, en.z, q);
-                    id = en.w;
-                    pass = kv_less(key, id, wk, wi);
-                }
-                const unsigned pm = __ballot_sync(0xffffffffu, pass);
-                if (pass) {
-                    const int j = qn + __popc(pm & ((1u << lane) - 1u));
-                    qk[j] = key;
-                    qi[j] = id;
-                }
-                qn += __popc(pm);
-                __syncwarp();
-                if (qn >= 32) knn_merge(qk, qi, qn, bk, bi, lane);
-            }
-        }
-        while (qn > 0) knn_merge(qk, qi, qn, bk, bi, lane);
-        // stop once no site outside ring r can enter the best K
-        const uint64_t kth = __shfl_sync(0xffffffffu, bk, K - 1);
-        const uint64_t bnd = unsearched_bound2(G, q, c, r);
-        if (bnd == UINT64_MAX || kth < bnd) break;
-    }
-    if (lane < K) out_idx[m * K + lane] = bi;
 }
 
 // ---------------------------------------------------------------------------
@@ -1588,18 +1413,6 @@ SitesGrid launch_sites_grid(const float* sites, int32_t N, char* ws, cudaStream_
     return r;
 }
 
-size_t sites_grid_bytes(int32_t N) { return knn_sites_bytes(N, 0, 0); }
-
-cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,
-                             char* ws, cudaStream_t s)
-{
-    const SitesGrid sg = launch_sites_grid(sites, N, ws, s);
-    if (M > 0) {
-        const unsigned nb = (unsigned)((M + kKnnWarps - 1) / kKnnWarps);
-        knn_sites_warp_kernel<<<nb, kKnnWarps * 32, 0, s>>>(pts, M, K, sg.grid, sg.cell_start, sg.entries, idx);
-    }
-    return cudaGetLastError();
-}
 
 // ===========================================================================
 // Allocation-free variant of the query + shade (sop_query_shade_noalloc).

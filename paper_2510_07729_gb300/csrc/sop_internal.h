@@ -59,8 +59,6 @@ cudaError_t launch_l1_grad(const float* C, const float* Ct, int64_t n, float* gr
 cudaError_t launch_adam_l1(float* p, const float* g, float* m, float* v, int64_t n, const sop_adam_params& a,
                            cudaStream_t s);
 
-// K nearest sites of M points
-size_t knn_sites_bytes(int32_t N, int64_t M, int32_t K);
 // the uniform grid of N sites (quantised positions and indices) that the
 // site searches use, built in ws (sites_grid_bytes(N) bytes)
 struct SitesGrid {
@@ -70,8 +68,6 @@ struct SitesGrid {
 };
 size_t sites_grid_bytes(int32_t N);
 SitesGrid launch_sites_grid(const float* sites, int32_t N, char* ws, cudaStream_t s);
-cudaError_t launch_knn_sites(const float* pts, int64_t M, const float* sites, int32_t N, int32_t K, int32_t* idx,
-                             char* ws, cudaStream_t s);
 
 // allocation-free query (static device scratch, see query.cu)
 size_t noalloc_scratch_bytes();

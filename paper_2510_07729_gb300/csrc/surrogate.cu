@@ -934,26 +934,43 @@ constexpr int kLD = 72;    // row stride of 64-wide bf16 tiles in shared memory
 constexpr int kLDX = 40;   // row stride of the 32-wide (padded) feature tile
 constexpr int kCH = 128;   // samples per chunk (8 warps x 16 rows)
 
+// four 8x8 bf16 matrices from shared memory, one per register: lane i
+// gives the address of row i % 8 of matrix i / 8 and receives, of each
+// matrix, row lane / 4, columns 2 (lane % 4) and +1 (the mma fragment layout)
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const uint16_t* row)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a)
+                 : "memory");
+}
+
 // out[16 rows of this warp] = relu(in[rows] W^T + b) in bf16: in is
-// [kCH][LDI] with KD columns, W is [64 out][LDW] with KD columns. The A
-// fragments of a k-step are loaded once and used for all 8 n-tiles.
+// [kCH][LDI] with KD columns, W is [64 out][LDW] with KD columns (row
+// strides of 16-byte multiples whose rows fall on distinct banks). Per
+// k-step one ldmatrix gives the A fragments (rows +0/+8 by matrix bit 0,
+// columns +0/+8 by bit 1) and one per pair of n-tiles the B fragments (k
+// +0/+8 by bit 0, n +0/+8 by bit 1).
 template <int KD, int LDI, int LDW>
 __device__ __forceinline__ void layer_fwd(const uint16_t* in, const uint16_t* W, const float* bias, uint16_t* out,
                                           int row0, int lane)
 {
     const int g = lane >> 2, t = lane & 3;
+    const int mr = lane & 7, m0 = (lane >> 3) & 1, m1 = lane >> 4;
     float c[8][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
 #pragma unroll
     for (int k0 = 0; k0 < KD; k0 += 16) {
-        const uint32_t a[4] = {ld2(in + (row0 + g) * LDI + k0 + 2 * t), ld2(in + (row0 + g + 8) * LDI + k0 + 2 * t),
-                               ld2(in + (row0 + g) * LDI + k0 + 8 + 2 * t),
-                               ld2(in + (row0 + g + 8) * LDI + k0 + 8 + 2 * t)};
+        uint32_t a[4];
+        ldsm_x4(a, in + (row0 + mr + 8 * m0) * LDI + k0 + 8 * m1);
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const uint32_t b[2] = {ld2(W + (nt * 8 + g) * LDW + k0 + 2 * t), ld2(W + (nt * 8 + g) * LDW + k0 + 8 + 2 * t)};
-            mma_bf16(c[nt], a, b);
+        for (int np = 0; np < 4; ++np) {
+            uint32_t b[4];
+            ldsm_x4(b, W + (16 * np + mr + 8 * m1) * LDW + k0 + 8 * m0);
+            mma_bf16(c[2 * np], a, b);
+            mma_bf16(c[2 * np + 1], a, b + 2);
         }
     }
 #pragma unroll
