@@ -1072,9 +1072,10 @@ def launches_per_step(do_bake, n_queries):
     n = 0
     if do_bake:
         # binning: bbox init, Gaussian records, 3 attempts x (grid setup,
-        # count, scan) decided on the device, fill; trace: counter reset,
-        # texel directions, trace, atlas border
-        n += 2 + 3 * 3 + 1 + 4
+        # count, and the scan's tile sums, tile offsets and apply) decided on
+        # the device, fill; trace: counter reset, texel directions, trace,
+        # atlas border
+        n += 2 + 3 * 5 + 1 + 4
     # per query: probe grid, nearest probes, environment table and
     # footprints, atlas footprints, directions, shade
     n += 7 * n_queries

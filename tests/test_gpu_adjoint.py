@@ -92,12 +92,15 @@ def diff_subset(n=4096, seed=51):
 
 def test_adjoint_rough_workload_subset(sop, orc):
     """The differentiation workload (rough HDR environment, independent
-    per-texel maps, K=8, S=128) on 4,096 points. Materials, environment and
-    probe gradients within 2e-3 relative: the same FP32 direction
-    conditioning as the forward pass (up to ~1e-4 relative there) enters
-    here multiplied by the texture slopes. Normal gradients cross bilinear
-    kinks whenever an FP32 direction lands on the other side of a texel
-    edge (the derivative is one-sided there), so they are checked by
+    per-texel maps, K=8, S=128) on 4,096 points. Material gradients within
+    1e-4 relative plus TERM_FRAC of their terms' magnitudes (measured: at
+    most 0.41 of that allowance). The environment and probe-map gradients
+    are sums of float atomics over all points and directions: 1e-4 relative
+    plus 2e-5 of the largest entry (measured: at most 0.92 of the allowance
+    with 1e-5; with 1e-6 a few entries of a million exceed it 4x, the FP32
+    accumulation of ~10^5 terms of both signs). Normal gradients cross
+    bilinear kinks whenever an FP32 direction lands on the other side of a
+    texel edge (the derivative is one-sided there), so they are checked by
     distribution: median within 1e-4, 99% within 1e-3."""
     c, sel, pts = diff_subset()
     rng = np.random.default_rng(52)
@@ -107,10 +110,10 @@ def test_adjoint_rough_workload_subset(sop, orc):
     g = gpu_grads(sop, pts, at, c["env"], 8, 128, go)
     o = orc_grads(orc, pts, c["probe_pos"], maps, c["env"], 8, 128, go)
     for k in ("albedo", "rough", "metal"):
-        assert_close(g[k], o[k], rtol=2e-3, absolute=TERM_FRAC * o["abs_" + k], what=k)
-    assert_close(g["env"], o["env"], rtol=2e-3, floor=0, absolute=1e-5 * np.abs(o["env"]).max(), what="env")
+        assert_close(g[k], o[k], rtol=1e-4, absolute=TERM_FRAC * o["abs_" + k], what=k)
+    assert_close(g["env"], o["env"], rtol=1e-4, floor=0, absolute=2e-5 * np.abs(o["env"]).max(), what="env")
     om = maps_of(o)
-    assert_close(g["maps"], om, rtol=2e-3, floor=0, absolute=1e-5 * np.abs(om).max(), what="maps")
+    assert_close(g["maps"], om, rtol=1e-4, floor=0, absolute=2e-5 * np.abs(om).max(), what="maps")
     rel = np.linalg.norm(g["normal"] - o["normal"], axis=1) / np.maximum(
         np.linalg.norm(o["normal"], axis=1), 1e-3 * np.linalg.norm(o["normal"], axis=1).mean())
     print("normal grad rel err: median %.2e p99 %.2e max %.2e" % (np.median(rel), np.percentile(rel, 99), rel.max()))
@@ -155,7 +158,7 @@ def test_adjoint_full_size_identities(sop, orc):
     sub = {k: c[k][sel] for k in KEYS}
     o = orc_grads(orc, sub, c["probe_pos"], maps, c["env"], 8, 128, go[sel].astype(np.float64))
     for k in ("albedo", "rough", "metal"):
-        assert_close(g[k].cpu().numpy()[sel], o[k], rtol=2e-3, absolute=TERM_FRAC * o["abs_" + k], what=k)
+        assert_close(g[k].cpu().numpy()[sel], o[k], rtol=1e-4, absolute=TERM_FRAC * o["abs_" + k], what=k)
 
 
 def test_autograd_function(sop):

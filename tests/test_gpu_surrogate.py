@@ -155,9 +155,13 @@ def test_train_step_matches_oracle(sop, scene):
     assert losses.item() == pytest.approx(l_o, rel=1e-4)
     gg = net.grad().cpu().numpy().astype(np.float64)
     wg, wo = mlp.unflatten(gg), mlp.unflatten(g_o)
+    # both sides round activations and deltas to bf16; an FP32 sum that
+    # differs from the FP64 one in its last bits can round to the neighbouring
+    # bf16 value (2^-8 relative), which the later layers carry on. Measured on
+    # three seeds: at most 1.9e-4 relative per block
     for name, _ in mlp.SHAPES:
         rel = np.linalg.norm(wg[name] - wo[name]) / max(np.linalg.norm(wo[name]), 1e-12)
-        assert rel < 2e-2, (name, rel)
+        assert rel < 1e-3, (name, rel)
     # the Adam update, on the GPU's own gradient (first step: lr * sign)
     th1 = net.params().cpu().numpy().astype(np.float64)
     want, _, _ = mlp.adam(th0.astype(np.float64), np.zeros_like(gg), np.zeros_like(gg), gg, 1, lr=1e-3)
