@@ -701,10 +701,13 @@ __device__ __forceinline__ void composite_hits(const TraceK& k, uint64_t* key, f
 // 32 at a time as the queue fills, and at the end while at least `least`
 // remain. Entries are loaded 32 ahead of the ones being tested: pv holds
 // entry pe + lane, and the last batch of the range loads the first one of
-// the next range [nf, ne) (the next cell's, when the walk knows it). go and
-// sp are the grid box's origin and span (the entries' fixed-point frame).
-__device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const float3 iv, const float3 go,
-                                          const float3 sp, const float t0, const int e0, const int e1,
+// the next range [nf, ne) (the next cell's, when the walk knows it). An
+// entry's centre along axis a is go_a + span_a u (u = q / 65536, decoded as
+// v = 1 + u from its bits), so its slab time (centre - o_a) / d_a is
+// v qa_a + qb_a with the ray's qa = span iv and qb = (go - o) iv - qa: one
+// FMA, the same in every cell.
+__device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const float3 iv, const float3 qa,
+                                          const float3 qb, const float t0, const int e0, const int e1,
                                           const int nf, const int ne, const float tl, const float th_e,
                                           const int least, uint4& pv, int& pe, int32_t* que, int& qn,
                                           int& pend, uint64_t* key, float* alp, int& n, const int lane,
@@ -725,9 +728,9 @@ __device__ __forceinline__ void scan_eval(const TraceK& k, const float3 o, const
             const int pl = eb < e1 ? e1 : ne;
             if (pe + lane < pl) pv = __ldg(k.ent + pe + lane);
             // box: slab entries/exits (c - o) iv -+ h |iv| per axis
-            const float px = (qdecode(en.x & 0xffffu, sp.x, go.x) - o.x) * iv.x;
-            const float py = (qdecode(en.x >> 16, sp.y, go.y) - o.y) * iv.y;
-            const float pz = (qdecode(en.y & 0xffffu, sp.z, go.z) - o.z) * iv.z;
+            const float px = fmaf(__uint_as_float(0x3f800000u | ((en.x & 0xffffu) << 7)), qa.x, qb.x);
+            const float py = fmaf(__uint_as_float(0x3f800000u | ((en.x >> 16) << 7)), qa.y, qb.y);
+            const float pz = fmaf(__uint_as_float(0x3f800000u | ((en.y & 0xffffu) << 7)), qa.z, qb.z);
             const float qx = hdecode(en.y >> 16) * fabsf(iv.x), qy = hdecode(en.z & 0xffffu) * fabsf(iv.y),
                         qz = hdecode(en.z >> 16) * fabsf(iv.z);
             const float tin = fmaxf(fmaxf(px - qx, py - qy), pz - qz);
@@ -816,6 +819,9 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
     // tiny one: the slab along that axis is then all or nothing)
     const float3 iv = f3(1.f / (fabsf(d.x) > 1e-30f ? d.x : 1e-30f), 1.f / (fabsf(d.y) > 1e-30f ? d.y : 1e-30f),
                          1.f / (fabsf(d.z) > 1e-30f ? d.z : 1e-30f));
+    // the box test's slab-time constants (see scan_eval)
+    const float3 qa = f3(sp.x * iv.x, sp.y * iv.y, sp.z * iv.z);
+    const float3 qb = f3((go.x - o.x) * iv.x - qa.x, (go.y - o.y) * iv.y - qa.y, (go.z - o.z) * iv.z - qa.z);
     RayAcc acc;
     acc.T = 1.f;
     acc.L0 = acc.L1 = acc.L2 = acc.Dacc = acc.Wacc = 0.f;
@@ -907,7 +913,7 @@ __global__ void __launch_bounds__(256, OUT == kTraceAtlas ? 4 : 3) trace_kernel(
                     const float hi_e = (mode == 2 ? sfin : last) ? FLT_MAX : (mode == 2 ? sh : t_exit);
                     const int nb = n, pb = pend;
                     // in mode 0 the walk goes on to the next cell: load its first entries
-                    scan_eval(k, o, iv, go, sp, t0, from, e1, mode == 0 ? ne0 : 0, mode == 0 ? ne1 : 0, lo, hi_e, least,
+                    scan_eval(k, o, iv, qa, qb, t0, from, e1, mode == 0 ? ne0 : 0, mode == 0 ? ne1 : 0, lo, hi_e, least,
                               pv, pe, que, qn, pend, key, alp, n, lane, acc, d);
                     if (mode == 0 && least == 32) {
                         if (!(last || nw + pend >= k.composite_at)) break;
