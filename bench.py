@@ -174,9 +174,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def traffic_for(kernel, P):
+def traffic_for(kernel, workload, P):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel (else None)."""
+    on this workload with all of its probes and on the current source of the
+    kernel (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -185,7 +186,7 @@ def traffic_for(kernel, P):
     except (OSError, ValueError):
         return None
     e = tab.get(kernel)
-    if not e:
+    if not e or e.get("workload") != workload or e.get("probes") != P:
         return None
     src = os.path.join(ROOT, "paper_2510_07729_gb300", "csrc", e["source"])
     try:
@@ -194,7 +195,7 @@ def traffic_for(kernel, P):
         return None
     if h != e.get("source_sha256_16"):
         return None
-    return round(e["bytes_per_probe"] * P) if "bytes_per_probe" in e else e.get("bytes")
+    return e.get("bytes")
 
 
 def chosen_variant(sop, g, ppos, R, pargs, env, K, S, mode, out_ref, flush, steps):
@@ -861,7 +862,7 @@ def trace_roofline(sop, state, ms_trace, peak_fp32):
     rays = state.P * state.R * state.R
     return {"kernel": "trace_kernel (sop_bake_trace)", "bound": "alu", "achieved": round(ach, 3),
             "peak": round(peak_fp32, 1), "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
-            "traffic": traffic_for("trace_kernel", state.P),
+            "traffic": traffic_for("trace_kernel", state.W["name"], state.P),
             "work": {"rays": rays, "box_tests": n_test, "exact_evaluations": n_eval, "composited_hits": n_comp,
                      "per_ray": {"box_tests": round(n_test / rays, 2), "exact_evaluations": round(n_eval / rays, 2),
                                  "composited_hits": round(n_comp / rays, 2)},
