@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
     float ox = 0.f, oy = 0.f, oz = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, t0 = 0.f;
     float idx = 0.f, idy = 0.f, idz = 0.f;  // 1 / d (unused along an axis with d = 0)
     float tc = 0.f, tb = 0.f, tau = 0.f, L0 = 0.f, L1 = 0.f, L2 = 0.f;
-    float tnx = 0.f, tny = 0.f, tnz = 0.f, ckn = 0.f;
+    float ckn = 0.f;
     float tk0 = 0.f, tk1 = 0.f, tk2 = 0.f, tk3 = 0.f, tk4 = 0.f;  // tau at the checkpoints
     int cx = 0, cy = 0, cz = 0, sx = 0, sy = 0, sz = 0, kn = 0, it = 0;
     for (;;) {
@@ -782,9 +782,6 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
                         sx = dx > 0.f ? 1 : (dx < 0.f ? -1 : 0);
                         sy = dy > 0.f ? 1 : (dy < 0.f ? -1 : 0);
                         sz = dz > 0.f ? 1 : (dz < 0.f ? -1 : 0);
-                        tnx = far_tn(sx, cx, F.lo[0], h, ox, idx);
-                        tny = far_tn(sy, cy, F.lo[1], h, oy, idy);
-                        tnz = far_tn(sz, cz, F.lo[2], h, oz, idz);
                         tc = ta;
                     } else {
                         far_write(feats, id, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
@@ -794,69 +791,29 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
             continue;
         }
         if (!live) continue;
-        // An empty brick is crossed in one jump: its exit time is the
-        // boundary time the walk would take at the brick's last cell along
-        // the ray (the same expression), so the walk resumes in the next
-        // cell with the same entry time; tau, the colour and the checkpoints
-        // (which take tau there) do not change across empty cells.
-        {
-            const int bx = (unsigned)cx / kFarBrick, by = (unsigned)cy / kFarBrick, bz = (unsigned)cz / kFarBrick;
-            const int bi = (bz * bdy + by) * bdx + bx;
-            if (!((s_bits[bi >> 5] >> (bi & 31)) & 1u)) {
-                const int ex = sx > 0 ? min(bx * kFarBrick + kFarBrick - 1, F.dims[0] - 1) : bx * kFarBrick;
-                const int ey = sy > 0 ? min(by * kFarBrick + kFarBrick - 1, F.dims[1] - 1) : by * kFarBrick;
-                const int ez = sz > 0 ? min(bz * kFarBrick + kFarBrick - 1, F.dims[2] - 1) : bz * kFarBrick;
-                const float tbx = far_tn(sx, ex, F.lo[0], h, ox, idx), tby = far_tn(sy, ey, F.lo[1], h, oy, idy),
-                            tbz = far_tn(sz, ez, F.lo[2], h, oz, idz);
-                const int jax = (tbx <= tby && tbx <= tbz) ? 0 : (tby <= tbz ? 1 : 2);
-                const float tex = fminf(jax == 0 ? tbx : (jax == 1 ? tby : tbz), tb);
-                if (tex > tc) {
-                    while (kn < 5 && ckn < tex) {
-                        if (kn == 0) tk0 = tau;
-                        else if (kn == 1) tk1 = tau;
-                        else if (kn == 2) tk2 = tau;
-                        else if (kn == 3) tk3 = tau;
-                        else tk4 = tau;
-                        ++kn;
-                        ckn = kn < 5 ? fmaf((float)(2 << kn), h, t0) : INFINITY;
-                    }
-                    tc = tex;
-                    bool end = !(tex < tb);
-                    if (!end) {
-                        // one cell beyond the brick along the exit axis; the
-                        // others where the ray is, kept inside the brick
-                        const int lx0 = bx * kFarBrick, ly0 = by * kFarBrick, lz0 = bz * kFarBrick;
-                        const int px = min(max(far_cell_at(ox, dx, tex, F.lo[0], ih, F.dims[0]), lx0),
-                                           min(lx0 + kFarBrick - 1, F.dims[0] - 1));
-                        const int py = min(max(far_cell_at(oy, dy, tex, F.lo[1], ih, F.dims[1]), ly0),
-                                           min(ly0 + kFarBrick - 1, F.dims[1] - 1));
-                        const int pz = min(max(far_cell_at(oz, dz, tex, F.lo[2], ih, F.dims[2]), lz0),
-                                           min(lz0 + kFarBrick - 1, F.dims[2] - 1));
-                        cx = jax == 0 ? ex + sx : px;
-                        cy = jax == 1 ? ey + sy : py;
-                        cz = jax == 2 ? ez + sz : pz;
-                        end = cx < 0 || cx >= F.dims[0] || cy < 0 || cy >= F.dims[1] || cz < 0 || cz >= F.dims[2];
-                        if (!end) {
-                            tnx = far_tn(sx, cx, F.lo[0], h, ox, idx);
-                            tny = far_tn(sy, cy, F.lo[1], h, oy, idy);
-                            tnz = far_tn(sz, cz, F.lo[2], h, oz, idz);
-                        }
-                    }
-                    ++it;
-                    if (end || it >= max_steps || !(tc < tb)) {
-                        far_write(feats, id, tk0 < 0.f ? tau : tk0, tk1 < 0.f ? tau : tk1, tk2 < 0.f ? tau : tk2,
-                                  tk3 < 0.f ? tau : tk3, tk4 < 0.f ? tau : tk4, tau, L0, L1, L2);
-                        live = false;
-                    }
-                    continue;
-                }
-            }
-        }
-        // one cell of the walk
+        // One advance a lane, the same steps for all: the segment ends at the
+        // boundary time of its exit cell along each axis, the current cell
+        // or, when its brick of kFarBrick^3 cells carries no mass, the
+        // brick's last cell along the ray (one jump across the brick). The
+        // times come from the cell indices (the same expression the walk
+        // takes), so the walk resumes in the next cell with the entry time
+        // it would have had; across empty cells tau, the colour and the
+        // checkpoints (which take tau there) do not change.
+        const int bx = (unsigned)cx / kFarBrick, by = (unsigned)cy / kFarBrick, bz = (unsigned)cz / kFarBrick;
+        const int bi = (bz * bdy + by) * bdx + bx;
+        const bool empty = !((s_bits[bi >> 5] >> (bi & 31)) & 1u);
+        const int lx = bx * kFarBrick, ly = by * kFarBrick, lz = bz * kFarBrick;
+        const int hx = min(lx + kFarBrick - 1, F.dims[0] - 1), hy = min(ly + kFarBrick - 1, F.dims[1] - 1),
+                  hz = min(lz + kFarBrick - 1, F.dims[2] - 1);
+        const int ex = empty ? (sx > 0 ? hx : lx) : cx, ey = empty ? (sy > 0 ? hy : ly) : cy,
+                  ez = empty ? (sz > 0 ? hz : lz) : cz;
+        const float tnx = far_tn(sx, ex, F.lo[0], h, ox, idx), tny = far_tn(sy, ey, F.lo[1], h, oy, idy),
+                    tnz = far_tn(sz, ez, F.lo[2], h, oz, idz);
         const int ax = (tnx <= tny && tnx <= tnz) ? 0 : (tny <= tnz ? 1 : 2);
         float te = fminf(ax == 0 ? tnx : (ax == 1 ? tny : tnz), tb);
         te = fmaxf(te, tc);
-        const float4 cv = __ldg(cells + (cz * F.dims[1] + cy) * F.dims[0] + cx);  // < 2^21 cells
+        float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!empty) cv = __ldg(cells + (cz * F.dims[1] + cy) * F.dims[0] + cx);  // < 2^21 cells
         // checkpoints inside this segment take tau at their position (they
         // are increasing: only the next one can be due)
         while (kn < 5 && ckn < te) {
@@ -880,19 +837,22 @@ __global__ void __launch_bounds__(256) far_march_kernel(const float* __restrict_
         tc = te;
         bool end = !(te < tb);
         if (!end) {
-            if (ax == 0) {
-                cx += sx;
-                end = cx < 0 || cx >= F.dims[0];
-                if (!end) tnx = far_tn(sx, cx, F.lo[0], h, ox, idx);
-            } else if (ax == 1) {
-                cy += sy;
-                end = cy < 0 || cy >= F.dims[1];
-                if (!end) tny = far_tn(sy, cy, F.lo[1], h, oy, idy);
-            } else {
-                cz += sz;
-                end = cz < 0 || cz >= F.dims[2];
-                if (!end) tnz = far_tn(sz, cz, F.lo[2], h, oz, idz);
+            // the next cell: one beyond the exit cell along the exit axis; the
+            // other axes stay, or after a jump follow the ray's position,
+            // kept inside the brick it leaves
+            int nx = cx, ny = cy, nz = cz;
+            if (empty) {
+                nx = min(max(far_cell_at(ox, dx, te, F.lo[0], ih, F.dims[0]), lx), hx);
+                ny = min(max(far_cell_at(oy, dy, te, F.lo[1], ih, F.dims[1]), ly), hy);
+                nz = min(max(far_cell_at(oz, dz, te, F.lo[2], ih, F.dims[2]), lz), hz);
             }
+            if (ax == 0) nx = ex + sx;
+            else if (ax == 1) ny = ey + sy;
+            else nz = ez + sz;
+            end = nx < 0 || nx >= F.dims[0] || ny < 0 || ny >= F.dims[1] || nz < 0 || nz >= F.dims[2];
+            cx = nx;
+            cy = ny;
+            cz = nz;
         }
         ++it;
         if (end || it >= max_steps || !(tc < tb) || tau > kTauMax) {
