@@ -72,6 +72,10 @@ typedef enum {
  *                              result was computed from part of its input
  *                              (the surrogate's near-field search found
  *                              more than 4,096 centres within r_near);
+ *   SOP_DEVSTAT_TIMEOUT        a kernel's bounded wait for the tensor cores
+ *                              (the surrogate network's completion
+ *                              barrier) gave up; that launch's outputs are
+ *                              not valid;
  *   SOP_DEVSTAT_GRID_COARSENED information, not an error: the bake's
  *                              binning grid was coarsened on the device
  *                              until the cell lists fit the workspace.
@@ -87,6 +91,7 @@ typedef enum {
 #define SOP_DEVSTAT_BAKE_TRUNCATED 0x2u
 #define SOP_DEVSTAT_INDEX 0x4u
 #define SOP_DEVSTAT_CAPACITY 0x8u
+#define SOP_DEVSTAT_TIMEOUT 0x10u
 #define SOP_DEVSTAT_GRID_COARSENED 0x100u
 #define SOP_DEVSTAT_ERRORS 0xffu
 sop_status sop_device_status(void* stream, uint32_t* out_bits, int32_t clear);

@@ -54,6 +54,7 @@ const char* status_bits_message(uint32_t bits)
         add("a bake ray met more hits at one depth than its hit buffer holds and stopped there");
     if (bits & SOP_DEVSTAT_INDEX) add("an index outside its range was skipped");
     if (bits & SOP_DEVSTAT_CAPACITY) add("a fixed-capacity buffer overflowed (part of the input was used)");
+    if (bits & SOP_DEVSTAT_TIMEOUT) add("a bounded wait for the tensor cores gave up (that launch's outputs are not valid)");
     if (bits & SOP_DEVSTAT_GRID_COARSENED) add("(info) the binning grid was coarsened to fit the workspace");
     return g_msg;
 }

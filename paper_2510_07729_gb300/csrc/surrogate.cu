@@ -1411,6 +1411,273 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Inference on the fifth-generation tensor cores (tcgen05). One CTA of 128
+// threads takes chunks of kCH = 128 samples: each layer is one 128 x N x K
+// product (M = 128 samples, N = 64 outputs, or 16 for the 5 outputs padded
+// with zero rows; K = 32 padded features or 64), issued by one thread as
+// K/16 tcgen05.mma of kind f16 (bf16 operands from shared memory, FP32
+// accumulators in tensor memory), completed through an mbarrier. Each warp
+// then reads its 32 samples' accumulators (tensor-memory lanes 32w..32w+31)
+// with tcgen05.ld, adds the bias, applies ReLU and writes the bf16
+// activations as the next layer's operand. The operands are K-major tiles
+// of core matrices (8 rows x 8 bf16 = 128 contiguous bytes; along K 128 B
+// apart, along the rows K/8 * 128 B apart), described to the MMA without
+// swizzling. Waits give up after kTcSpin tries and report SOP_DEVSTAT_TIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr int kTcThreads = 128;
+constexpr int kTcCols = 128;    // tensor-memory columns: hidden layers 0-63, output layer 64-79
+constexpr int kTcOutN = 16;     // the output layer's N (5 outputs and zero rows)
+constexpr int kTcSpin = 1 << 24;
+
+// element (r, k) of a K-major [rows][KK] tile of core matrices
+__device__ __forceinline__ int tc_at(int r, int k, int KK) { return ((r >> 3) * (KK >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+__device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, K-direction core-matrix step
+// (leading byte offset), row-direction step (stride byte offset), descriptor
+// version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind f16: FP32 accumulator, bf16 A and B, both
+// K-major, N and M
+__host__ __device__ constexpr uint32_t tc_idesc(int n, int m)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// D[tmem] (+)= A[128 x K] B[N x K]^T, K/16 MMAs, then a commit to the mbarrier
+// (one thread)
+__device__ __forceinline__ void tc_layer(uint32_t tmem, const uint16_t* A, const uint16_t* B, int K, uint32_t idesc,
+                                         uint64_t* mbar)
+{
+    const uint32_t a0 = tc_smem(A), b0 = tc_smem(B), sbo = (uint32_t)(K / 8) * 128u;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const uint64_t da = tc_desc(a0 + (uint32_t)k0 * 16u, 128u, sbo), db = tc_desc(b0 + (uint32_t)k0 * 16u, 128u, sbo);
+        const uint32_t acc = k0 > 0;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                     "l"(da), "l"(db), "r"(idesc), "r"(acc));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_smem(mbar))
+                 : "memory");
+}
+
+// waits for the mbarrier's phase `parity` to complete; false after kTcSpin tries
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < kTcSpin && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(tc_smem(mbar)), "r"(parity)
+                     : "memory");
+    return done != 0;
+}
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// this thread's sample row: bias, ReLU, bf16 into the K-major [128][64] tile
+__device__ __forceinline__ void tc_hidden_out(uint32_t tmem_row, const float* bias, uint16_t* H, int row)
+{
+#pragma unroll
+    for (int c0 = 0; c0 < kHid; c0 += 16) {
+        float v[16];
+        tc_ld16(tmem_row + (uint32_t)c0, v);
+        uint32_t w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            w[j] = pk(f2bf(fmaxf(v[2 * j] + bias[c0 + 2 * j], 0.f)), f2bf(fmaxf(v[2 * j + 1] + bias[c0 + 2 * j + 1], 0.f)));
+        *reinterpret_cast<uint4*>(H + tc_at(row, c0, kHid)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(H + tc_at(row, c0 + 8, kHid)) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+// orders this CTA's shared-memory writes before the tensor cores read them,
+// and the tensor-memory reads before the next MMA
+__device__ __forceinline__ void tc_sync()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// a chunk's features in registers (128 threads)
+constexpr int kTcFeatVec = (kCH * kIn / 4 + kTcThreads - 1) / kTcThreads;
+struct TcFeatRegs {
+    float4 v[kTcFeatVec];
+};
+
+__device__ __forceinline__ void tc_feat_load(const MlpK& k, const MlpChunk& c, int RR, int tid, TcFeatRegs& r)
+{
+    int nf;
+    const float* fp = chunk_feats(k, c, RR, nf);
+    if ((reinterpret_cast<uintptr_t>(fp) & 15) != 0 || (nf & 3) != 0) return;  // tc_feat_store reads them itself
+#pragma unroll
+    for (int q = 0; q < kTcFeatVec; ++q) {
+        const int i = tid + kTcThreads * q;
+        if (i < nf / 4) r.v[q] = __ldg(reinterpret_cast<const float4*>(fp) + i);
+    }
+}
+
+// the chunk's features as bf16 into the K-major [kCH][kInPad] tile X (rows
+// beyond the chunk zero; the padding columns are zero from the start)
+__device__ __forceinline__ void tc_feat_store(const MlpK& k, const MlpChunk& c, int RR, int tid, const TcFeatRegs& r,
+                                              uint16_t* X)
+{
+    int nf;
+    const float* fp = chunk_feats(k, c, RR, nf);
+    if ((reinterpret_cast<uintptr_t>(fp) & 15) == 0 && (nf & 3) == 0) {
+#pragma unroll
+        for (int q = 0; q < kTcFeatVec; ++q) {
+            const int i = tid + kTcThreads * q;
+            if (i < nf / 4) {
+                const float f[4] = {r.v[q].x, r.v[q].y, r.v[q].z, r.v[q].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int n = 4 * i + e, s = n / kIn;
+                    X[tc_at(s, n - s * kIn, kInPad)] = f2bf(f[e]);
+                }
+            }
+        }
+    } else {
+        for (int n = tid; n < nf; n += kTcThreads) {
+            const int s = n / kIn;
+            X[tc_at(s, n - s * kIn, kInPad)] = f2bf(fp[n]);
+        }
+    }
+    for (int i = nf + tid; i < kCH * kIn; i += kTcThreads) {
+        const int s = i / kIn;
+        X[tc_at(s, i - s * kIn, kInPad)] = 0;
+    }
+}
+
+constexpr size_t kTcSmem = sizeof(uint16_t) * ((size_t)kHid * kInPad + 2 * kHid * kHid + kTcOutN * kHid +
+                                               (size_t)kCH * kInPad + 2 * (size_t)kCH * kHid) +
+                           sizeof(float) * (3 * kHid + kTcOutN);
+static_assert(kCH == 128 && kTcThreads == 128, "one sample a thread and tensor-memory lane");
+
+__global__ void __launch_bounds__(kTcThreads) surr_mlp_tc_kernel(const MlpK k)
+{
+    // (unswizzled operands: 16-byte aligned starts suffice; every tile's size
+    // is a multiple of 1 KB)
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint16_t* W1 = reinterpret_cast<uint16_t*>(smem);  // [64][kInPad]
+    uint16_t* W2 = W1 + kHid * kInPad;                  // [64][64]
+    uint16_t* W3 = W2 + kHid * kHid;                    // [64][64]
+    uint16_t* W4 = W3 + kHid * kHid;                    // [kTcOutN][64], rows beyond the 5 outputs zero
+    uint16_t* X = W4 + kTcOutN * kHid;                  // [kCH][kInPad]
+    uint16_t* H0 = X + kCH * kInPad;                    // [kCH][64]
+    uint16_t* H1 = H0 + kCH * kHid;                     // [kCH][64]
+    float* bias = reinterpret_cast<float*>(H1 + kCH * kHid);  // b1 | b2 | b3 | b4 (kTcOutN)
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = 32 * warp + lane;  // this thread's sample of a chunk, and its tensor-memory lane
+    for (int i = tid; i < kHid * kInPad; i += kTcThreads) {
+        const int r = i / kInPad, c = i % kInPad;
+        W1[tc_at(r, c, kInPad)] = c < kIn ? k.wbf[oW1 + r * kIn + c] : (uint16_t)0;
+    }
+    for (int i = tid; i < kHid * kHid; i += kTcThreads) {
+        const int r = i / kHid, c = i % kHid;
+        W2[tc_at(r, c, kHid)] = k.wbf[oW2 + i];
+        W3[tc_at(r, c, kHid)] = k.wbf[oW3 + i];
+    }
+    for (int i = tid; i < kTcOutN * kHid; i += kTcThreads) {
+        const int r = i / kHid, c = i % kHid;
+        W4[tc_at(r, c, kHid)] = r < kOut ? k.wbf[oW4 + r * kHid + c] : (uint16_t)0;
+    }
+    for (int i = tid; i < kHid; i += kTcThreads) {
+        bias[i] = k.master[ob1 + i];
+        bias[kHid + i] = k.master[ob2 + i];
+        bias[2 * kHid + i] = k.master[ob3 + i];
+    }
+    if (tid < kTcOutN) bias[3 * kHid + tid] = tid < kOut ? k.master[ob4 + tid] : 0.f;
+    for (int i = tid; i < kCH * (kInPad - kIn); i += kTcThreads) {
+        const int r = i / (kInPad - kIn), c = kIn + i % (kInPad - kIn);
+        X[tc_at(r, c, kInPad)] = 0;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&s_tmem)),
+                     "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_sync();
+    const uint32_t tmem = s_tmem;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    const int RR = k.R * k.R, RS = k.R + 2;
+    uint32_t parity = 0;
+    bool ok = true;
+    MlpChunk cur;
+    cur.b = blockIdx.x;
+    cur.s0 = 0;
+    mlp_seek(k, cur, tid);
+    TcFeatRegs pf;
+    if (cur.p >= 0) tc_feat_load(k, cur, RR, tid, pf);
+    while (cur.p >= 0) {
+        const int64_t p = cur.p;
+        const int s0 = cur.s0;
+        const int ns = min(kCH, RR - s0);
+        tc_feat_store(k, cur, RR, tid, pf, X);
+        mlp_next(k, cur, RR, tid);
+        if (cur.p >= 0) tc_feat_load(k, cur, RR, tid, pf);
+        // layers 1-3 (ReLU, bf16) and the output layer
+        const uint16_t* in[4] = {X, H0, H1, H0};
+        uint16_t* outH[3] = {H0, H1, H0};
+        const uint16_t* Ws[4] = {W1, W2, W3, W4};
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            tc_sync();
+            if (tid == 0)
+                tc_layer(l < 3 ? tmem : tmem + kHid, in[l], Ws[l], l == 0 ? kInPad : kHid,
+                         l < 3 ? tc_idesc(kHid, kCH) : tc_idesc(kTcOutN, kCH), &mbar);
+            ok = __syncthreads_and(tc_wait(&mbar, parity)) && ok;
+            parity ^= 1u;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (l < 3) tc_hidden_out(trow, bias + l * kHid, outH[l], row);
+        }
+        if (!ok) break;
+        float y[16];
+        tc_ld16(trow + kHid, y);
+        if (row < ns) {
+            const int t = s0 + row;
+            const int64_t ti = p * RS * RS + (int64_t)(t / k.R + 1) * RS + (t % k.R + 1);
+            const float* b4 = bias + 3 * kHid;
+            if (k.depth) depth_put(k.depth, k.depth_dtype, ti, fmaxf(y[1] + b4[1], 0.f));
+            texel_store(k.rgbo, k.rgbo_dtype, ti,
+                        make_float4(fmaxf(y[2] + b4[2], 0.f), fmaxf(y[3] + b4[3], 0.f), fmaxf(y[4] + b4[4], 0.f),
+                                    fminf(fmaxf(y[0] + b4[0], 0.f), 1.f)));
+        }
+    }
+    if (!ok && tid == 0 && k.status) atomicOr(k.status, SOP_DEVSTAT_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
 // grad[i] = sum over the CTAs, in CTA order, of their partial sums; loss
 // likewise (thread 0)
 __global__ void surr_grad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ loss_part, int nb,
@@ -1792,7 +2059,20 @@ cudaError_t surr_infer(const char* state, const float* feats, const int32_t* pid
     k.rgbo_dtype = out.rgbo_dtype;
     k.depth_dtype = out.depth_dtype;
     k.status = status_word();
-    return mlp_launch(false, k, mlp_blocks(B), s);
+    // three CTAs an SM (64 KB of shared memory and 128 tensor-memory columns each)
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    const unsigned nb = (unsigned)(B < 3 * sms ? B : 3 * sms);
+    if (nb == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(surr_mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    surr_mlp_tc_kernel<<<nb, kTcThreads, kTcSmem, s>>>(k);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_atlas_compare(const sop_atlas& a, const int32_t* ap, const sop_atlas& b, const int32_t* bp,

@@ -21,9 +21,10 @@ ENV_EQUIRECT, ENV_OCTAHEDRAL = 0, 1
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "WORKSPACE", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "DEVICE"}
 # bits of the device status word (include/sop.h)
 DEVSTAT_NONFINITE, DEVSTAT_BAKE_TRUNCATED, DEVSTAT_INDEX, DEVSTAT_GRID_COARSENED = 0x1, 0x2, 0x4, 0x100
+DEVSTAT_CAPACITY, DEVSTAT_TIMEOUT = 0x8, 0x10
 DEVSTAT_ERRORS = 0xff
 _DEVSTAT_NAMES = {DEVSTAT_NONFINITE: "nonfinite", DEVSTAT_BAKE_TRUNCATED: "bake_truncated", DEVSTAT_INDEX: "index",
-                  DEVSTAT_GRID_COARSENED: "grid_coarsened"}
+                  DEVSTAT_CAPACITY: "capacity", DEVSTAT_TIMEOUT: "timeout", DEVSTAT_GRID_COARSENED: "grid_coarsened"}
 
 
 def devstat_names(bits):

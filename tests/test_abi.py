@@ -137,8 +137,8 @@ def test_device_status_bits_decoded_on_the_host():
     from paper_2510_07729_gb300 import sop as S
     hdr = open(os.path.join(ROOT, "include", "sop.h")).read()
     for name, val in (("NONFINITE", S.DEVSTAT_NONFINITE), ("BAKE_TRUNCATED", S.DEVSTAT_BAKE_TRUNCATED),
-                      ("INDEX", S.DEVSTAT_INDEX), ("GRID_COARSENED", S.DEVSTAT_GRID_COARSENED),
-                      ("ERRORS", S.DEVSTAT_ERRORS)):
+                      ("INDEX", S.DEVSTAT_INDEX), ("CAPACITY", S.DEVSTAT_CAPACITY), ("TIMEOUT", S.DEVSTAT_TIMEOUT),
+                      ("GRID_COARSENED", S.DEVSTAT_GRID_COARSENED), ("ERRORS", S.DEVSTAT_ERRORS)):
         m = re.search(r"#define SOP_DEVSTAT_%s (0x[0-9a-f]+)u" % name, hdr)
         assert m and int(m.group(1), 16) == val, name
     assert S.DEVSTAT_GRID_COARSENED & S.DEVSTAT_ERRORS == 0  # information, not an error
