@@ -1167,8 +1167,10 @@ __device__ __forceinline__ void feat_store(const MlpK& k, const MlpChunk& c, int
     }
 }
 
-template <bool TRAIN>
-__global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
+// Training on mma.sync: the forward pass of each chunk (activations kept),
+// the L1 loss gradient, and the backward pass (delta products and weight
+// gradients on the tensor cores), summed into this CTA's gradient slot.
+__global__ void __launch_bounds__(256) surr_mlp_train_kernel(const MlpK k)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint16_t* sW1 = reinterpret_cast<uint16_t*>(smem);  // [64][kLDX]
@@ -1177,11 +1179,10 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
     uint16_t* sX = sW3 + kHid * kLD;                    // [kCH][kLDX]
     uint16_t* sH1 = sX + kCH * kLDX;                    // [kCH][kLD]
     uint16_t* sH2 = sH1 + kCH * kLD;
-    // inference keeps two activation buffers (h3 over h1: each warp works on
-    // its own 16 rows); training keeps h1..h3 and the deltas for backward
-    uint16_t* sH3 = TRAIN ? sH2 + kCH * kLD : sH1;     // (train: later D2)
-    uint16_t* sD3 = TRAIN ? sH3 + kCH * kLD : sH2;     // (train: later D1; unused in inference)
-    uint16_t* sW4b = (TRAIN ? sD3 : sH2) + kCH * kLD;   // [8][kLD] (rows 5..7 zero)
+    // h1..h3 and the deltas for the backward pass
+    uint16_t* sH3 = sH2 + kCH * kLD;                    // (later D2)
+    uint16_t* sD3 = sH3 + kCH * kLD;                    // (later D1)
+    uint16_t* sW4b = sD3 + kCH * kLD;                   // [8][kLD] (rows 5..7 zero)
     float* fs = reinterpret_cast<float*>(sW4b + 8 * kLD);
     float* sW4 = fs;                  // [5][64]
     float* sb1 = sW4 + kOut * kHid;   // [64]
@@ -1208,7 +1209,7 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
     }
     for (int i = tid; i < kOut * kHid; i += blockDim.x) {
         sW4[i] = bf2f(k.wbf[oW4 + i]);
-        if (TRAIN) gW4[i] = 0.f;
+        gW4[i] = 0.f;
     }
     for (int i = tid; i < 8 * kLD; i += blockDim.x) {
         const int r = i / kLD, c = i % kLD;
@@ -1218,11 +1219,11 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
         sb1[i] = k.master[ob1 + i];
         sb2[i] = k.master[ob2 + i];
         sb3[i] = k.master[ob3 + i];
-        if (TRAIN) gb1[i] = gb2[i] = gb3[i] = 0.f;
+        gb1[i] = gb2[i] = gb3[i] = 0.f;
     }
     for (int i = tid; i < 8; i += blockDim.x) {
         sb4[i] = i < kOut ? k.master[ob4 + i] : 0.f;
-        if (TRAIN) gb4[i] = 0.f;
+        gb4[i] = 0.f;
     }
     // weight-gradient accumulators of layers 1-3 (tensor cores): m-tile
     // warp & 3; n-tiles (warp >> 2) * 4 .. +3 of the 64-wide inputs, and
@@ -1246,23 +1247,20 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
     for (int i = tid; i < kCH * (kLDX - kIn); i += blockDim.x)
         sX[(i / (kLDX - kIn)) * kLDX + kIn + i % (kLDX - kIn)] = 0;
     // the CTA's chunks: probe entries b = blockIdx.x, + gridDim.x, ... (each
-    // in chunks of kCH texels). Inference loads the next chunk's features
-    // into registers while the current one goes through the network.
+    // in chunks of kCH texels)
     MlpChunk cur;
     cur.b = blockIdx.x;
     cur.s0 = 0;
     mlp_seek(k, cur, tid);
     FeatRegs pf;
-    if (!TRAIN && cur.p >= 0) feat_load(k, cur, RR, tid, pf);
     while (cur.p >= 0) {
         const int64_t p = cur.p;
         const int s0 = cur.s0;
         const int ns = min(kCH, RR - s0);
         __syncthreads();
-        if (TRAIN) feat_load(k, cur, RR, tid, pf);
+        feat_load(k, cur, RR, tid, pf);
         feat_store(k, cur, RR, tid, pf, sX);
         mlp_next(k, cur, RR, tid);
-        if (!TRAIN && cur.p >= 0) feat_load(k, cur, RR, tid, pf);
         __syncthreads();
         {
             layer_fwd<kInPad, kLDX, kLDX>(sX, sW1, sb1, sH1, row0, lane);
@@ -1273,20 +1271,8 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
             __syncwarp();
             out_fwd(sH3, sW4b, sb4, sY, row0, lane);
             __syncthreads();
-            if (!TRAIN) {
-                // the atlas write: occupancy clamped to [0, 1], depth and
-                // radiance to >= 0
-                for (int s = tid; s < ns; s += blockDim.x) {
-                    const float* y = sY + s * 8;
-                    const int t = s0 + s;
-                    const int64_t ti = p * RS * RS + (int64_t)(t / k.R + 1) * RS + (t % k.R + 1);
-                    if (k.depth) depth_put(k.depth, k.depth_dtype, ti, fmaxf(y[1], 0.f));
-                    texel_store(k.rgbo, k.rgbo_dtype, ti,
-                                make_float4(fmaxf(y[2], 0.f), fmaxf(y[3], 0.f), fmaxf(y[4], 0.f),
-                                            fminf(fmaxf(y[0], 0.f), 1.f)));
-                }
-            } else {
-            // the loss gradient of the outputs
+            {
+            // the loss gradient of the outputs (one block with the backward pass)
             for (int i = tid; i < kCH * kOut; i += blockDim.x) {
                 const int s = i / kOut, o = i % kOut;
                 const float y = sY[s * 8 + o];
@@ -1363,10 +1349,10 @@ __global__ void __launch_bounds__(256) surr_mlp_kernel(const MlpK k)
                 for (int s = 0; s < ns; ++s) a += bf2f(sD3[s * kLD + tid]);
                 gb1[tid] += a;
             }
-            }  // training
+            }
         }
     }
-    if (TRAIN) {
+    {
         __syncthreads();
         // this CTA's gradient sums into its own slot (summed over the CTAs in
         // a fixed order by surr_grad_reduce_kernel: training is bit-
@@ -1696,9 +1682,9 @@ __global__ void surr_grad_reduce_kernel(const float* __restrict__ part, const fl
     }
 }
 
-size_t surr_mlp_smem(bool train)
+size_t surr_mlp_smem()
 {
-    return sizeof(uint16_t) * (kHid * kLDX + 2 * kHid * kLD + kCH * kLDX + (train ? 4 : 2) * kCH * kLD + 8 * kLD) +
+    return sizeof(uint16_t) * (kHid * kLDX + 2 * kHid * kLD + kCH * kLDX + 4 * kCH * kLD + 8 * kLD) +
            sizeof(float) * (kOut * kHid + 3 * kHid + 8 + kCH * kOut + kOut * kHid + 8 + 3 * kHid + kCH * 8);
 }
 
@@ -1969,19 +1955,13 @@ static unsigned mlp_blocks(int32_t B)
     return (unsigned)(B < nb ? B : nb);
 }
 
-static cudaError_t mlp_launch(bool train, const MlpK& k, unsigned nb, cudaStream_t s)
+static cudaError_t mlp_train_launch(const MlpK& k, unsigned nb, cudaStream_t s)
 {
-    const size_t smem = surr_mlp_smem(train);
+    const size_t smem = surr_mlp_smem();
     if (nb == 0) return cudaSuccess;
-    if (train) {
-        cudaError_t e = cudaFuncSetAttribute(surr_mlp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        surr_mlp_kernel<true><<<nb, 256, smem, s>>>(k);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(surr_mlp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        surr_mlp_kernel<false><<<nb, 256, smem, s>>>(k);
-    }
+    cudaError_t e = cudaFuncSetAttribute(surr_mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    surr_mlp_train_kernel<<<nb, 256, smem, s>>>(k);
     return cudaGetLastError();
 }
 
@@ -2029,7 +2009,7 @@ cudaError_t surr_train_steps(char* state, const float* feats, const int32_t* pid
         k.grad_part = part;
         k.loss_part = lpart;
         k.status = status_word();
-        cudaError_t e = mlp_launch(true, k, nb, s);
+        cudaError_t e = mlp_train_launch(k, nb, s);
         if (e != cudaSuccess) return e;
         surr_grad_reduce_kernel<<<(kNParam + 255) / 256, 256, 0, s>>>(part, lpart, (int)nb, grad, loss);
         if (loss_out) surr_loss_kernel<<<1, 1, 0, s>>>(loss, 1.f / ((float)B * R * R * kOut), loss_out + it);
