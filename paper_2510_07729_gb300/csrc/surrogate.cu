@@ -1557,7 +1557,7 @@ __device__ __forceinline__ void tc_feat_store(const MlpK& k, const MlpChunk& c, 
 }
 
 constexpr size_t kTcSmem = sizeof(uint16_t) * ((size_t)kHid * kInPad + 2 * kHid * kHid + kTcOutN * kHid +
-                                               (size_t)kCH * kInPad + 2 * (size_t)kCH * kHid) +
+                                               (size_t)kCH * kInPad + (size_t)kCH * kHid) +
                            sizeof(float) * (3 * kHid + kTcOutN);
 static_assert(kCH == 128 && kTcThreads == 128, "one sample a thread and tensor-memory lane");
 
@@ -1571,9 +1571,10 @@ __global__ void __launch_bounds__(kTcThreads) surr_mlp_tc_kernel(const MlpK k)
     uint16_t* W3 = W2 + kHid * kHid;                    // [64][64]
     uint16_t* W4 = W3 + kHid * kHid;                    // [kTcOutN][64], rows beyond the 5 outputs zero
     uint16_t* X = W4 + kTcOutN * kHid;                  // [kCH][kInPad]
-    uint16_t* H0 = X + kCH * kInPad;                    // [kCH][64]
-    uint16_t* H1 = H0 + kCH * kHid;                     // [kCH][64]
-    float* bias = reinterpret_cast<float*>(H1 + kCH * kHid);  // b1 | b2 | b3 | b4 (kTcOutN)
+    // [kCH][64] activations: a layer's epilogue overwrites the tile its own
+    // MMA read, which has completed by then
+    uint16_t* H = X + kCH * kInPad;
+    float* bias = reinterpret_cast<float*>(H + kCH * kHid);  // b1 | b2 | b3 | b4 (kTcOutN)
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1630,20 +1631,18 @@ __global__ void __launch_bounds__(kTcThreads) surr_mlp_tc_kernel(const MlpK k)
         mlp_next(k, cur, RR, tid);
         if (cur.p >= 0) tc_feat_load(k, cur, RR, tid, pf);
         // layers 1-3 (ReLU, bf16) and the output layer
-        const uint16_t* in[4] = {X, H0, H1, H0};
-        uint16_t* outH[3] = {H0, H1, H0};
         const uint16_t* Ws[4] = {W1, W2, W3, W4};
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
             tc_sync();
             if (tid == 0)
-                tc_layer(l < 3 ? tmem : tmem + kHid, in[l], Ws[l], l == 0 ? kInPad : kHid,
+                tc_layer(l < 3 ? tmem : tmem + kHid, l == 0 ? X : H, Ws[l], l == 0 ? kInPad : kHid,
                          l < 3 ? tc_idesc(kHid, kCH) : tc_idesc(kTcOutN, kCH), &mbar);
             ok = __syncthreads_and(tc_wait(&mbar, parity)) && ok;
             parity ^= 1u;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (l < 3) tc_hidden_out(trow, bias + l * kHid, outH[l], row);
+            if (l < 3) tc_hidden_out(trow, bias + l * kHid, H, row);
         }
         if (!ok) break;
         float y[16];
@@ -2039,7 +2038,8 @@ cudaError_t surr_infer(const char* state, const float* feats, const int32_t* pid
     k.rgbo_dtype = out.rgbo_dtype;
     k.depth_dtype = out.depth_dtype;
     k.status = status_word();
-    // three CTAs an SM (64 KB of shared memory and 128 tensor-memory columns each)
+    // four CTAs an SM (48 KB of shared memory and 128 of the 512 tensor-memory
+    // columns each)
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -2047,7 +2047,7 @@ cudaError_t surr_infer(const char* state, const float* feats, const int32_t* pid
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 152;
     }
-    const unsigned nb = (unsigned)(B < 3 * sms ? B : 3 * sms);
+    const unsigned nb = (unsigned)(B < 4 * sms ? B : 4 * sms);
     if (nb == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(surr_mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e != cudaSuccess) return e;
