@@ -1415,6 +1415,7 @@ constexpr int kTcThreads = 128;
 constexpr int kTcCols = 128;    // tensor-memory columns: hidden layers 0-63, output layer 64-79
 constexpr int kTcOutN = 16;     // the output layer's N (5 outputs and zero rows)
 constexpr int kTcSpin = 1 << 24;
+constexpr int kTcMaxCtas = 512 / kTcCols;  // CTAs an SM whose tensor memory fits
 
 // element (r, k) of a K-major [rows][KK] tile of core matrices
 __device__ __forceinline__ int tc_at(int r, int k, int KK) { return ((r >> 3) * (KK >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
@@ -1506,49 +1507,38 @@ __device__ __forceinline__ void tc_sync()
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// a chunk's features in registers (128 threads)
-constexpr int kTcFeatVec = (kCH * kIn / 4 + kTcThreads - 1) / kTcThreads;
-struct TcFeatRegs {
-    float4 v[kTcFeatVec];
-};
-
-__device__ __forceinline__ void tc_feat_load(const MlpK& k, const MlpChunk& c, int RR, int tid, TcFeatRegs& r)
+// A chunk's features (ns rows of kIn floats, contiguous in memory) come into
+// shared memory by one bulk asynchronous copy when they start on a 16-byte
+// boundary and span whole 16 bytes (cp.async.bulk, completing on an
+// mbarrier with its byte count); otherwise the threads read them.
+__device__ __forceinline__ bool tc_bulk_ok(const MlpK& k, const MlpChunk& c, int RR)
 {
     int nf;
     const float* fp = chunk_feats(k, c, RR, nf);
-    if ((reinterpret_cast<uintptr_t>(fp) & 15) != 0 || (nf & 3) != 0) return;  // tc_feat_store reads them itself
-#pragma unroll
-    for (int q = 0; q < kTcFeatVec; ++q) {
-        const int i = tid + kTcThreads * q;
-        if (i < nf / 4) r.v[q] = __ldg(reinterpret_cast<const float4*>(fp) + i);
-    }
+    return (reinterpret_cast<uintptr_t>(fp) & 15) == 0 && ((nf * 4) & 15) == 0;
 }
 
-// the chunk's features as bf16 into the K-major [kCH][kInPad] tile X (rows
-// beyond the chunk zero; the padding columns are zero from the start)
-__device__ __forceinline__ void tc_feat_store(const MlpK& k, const MlpChunk& c, int RR, int tid, const TcFeatRegs& r,
-                                              uint16_t* X)
+// (one thread) the chunk's features into F, completing on mb
+__device__ __forceinline__ void tc_bulk_issue(const MlpK& k, const MlpChunk& c, int RR, float* F, uint64_t* mb)
 {
     int nf;
     const float* fp = chunk_feats(k, c, RR, nf);
-    if ((reinterpret_cast<uintptr_t>(fp) & 15) == 0 && (nf & 3) == 0) {
-#pragma unroll
-        for (int q = 0; q < kTcFeatVec; ++q) {
-            const int i = tid + kTcThreads * q;
-            if (i < nf / 4) {
-                const float f[4] = {r.v[q].x, r.v[q].y, r.v[q].z, r.v[q].w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int n = 4 * i + e, s = n / kIn;
-                    X[tc_at(s, n - s * kIn, kInPad)] = f2bf(f[e]);
-                }
-            }
-        }
-    } else {
-        for (int n = tid; n < nf; n += kTcThreads) {
-            const int s = n / kIn;
-            X[tc_at(s, n - s * kIn, kInPad)] = f2bf(fp[n]);
-        }
+    const uint32_t bytes = (uint32_t)nf * 4u;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem(mb)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc_smem(F)),
+                 "l"(fp), "r"(bytes), "r"(tc_smem(mb))
+                 : "memory");
+}
+
+// nf features (staged or in global memory) as bf16 into the K-major
+// [kCH][kInPad] tile X; rows beyond them zero (the padding columns are
+// zero from the start)
+__device__ __forceinline__ void tc_feat_to_x(const float* src, int nf, int tid, uint16_t* X)
+{
+    for (int n = tid; n < nf; n += kTcThreads) {
+        const int s = n / kIn;
+        X[tc_at(s, n - s * kIn, kInPad)] = f2bf(src[n]);
     }
     for (int i = nf + tid; i < kCH * kIn; i += kTcThreads) {
         const int s = i / kIn;
@@ -1558,7 +1548,10 @@ __device__ __forceinline__ void tc_feat_store(const MlpK& k, const MlpChunk& c, 
 
 constexpr size_t kTcSmem = sizeof(uint16_t) * ((size_t)kHid * kInPad + 2 * kHid * kHid + kTcOutN * kHid +
                                                (size_t)kCH * kInPad + (size_t)kCH * kHid) +
-                           sizeof(float) * (3 * kHid + kTcOutN);
+                           sizeof(float) * (3 * kHid + kTcOutN + kCH * kIn);
+static_assert((sizeof(uint16_t) * ((size_t)kHid * kInPad + 2 * kHid * kHid + kTcOutN * kHid + (size_t)kCH * kInPad +
+                                   (size_t)kCH * kHid) + sizeof(float) * (3 * kHid + kTcOutN)) % 16 == 0,
+              "the staging buffer must start on a 16-byte boundary");
 static_assert(kCH == 128 && kTcThreads == 128, "one sample a thread and tensor-memory lane");
 
 __global__ void __launch_bounds__(kTcThreads) surr_mlp_tc_kernel(const MlpK k)
@@ -1575,7 +1568,9 @@ __global__ void __launch_bounds__(kTcThreads) surr_mlp_tc_kernel(const MlpK k)
     // MMA read, which has completed by then
     uint16_t* H = X + kCH * kInPad;
     float* bias = reinterpret_cast<float*>(H + kCH * kHid);  // b1 | b2 | b3 | b4 (kTcOutN)
+    float* F = bias + 3 * kHid + kTcOutN;                      // [kCH * kIn] the next chunk's features
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbf;  // completion of the bulk copy into F
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = 32 * warp + lane;  // this thread's sample of a chunk, and its tensor-memory lane
@@ -1604,6 +1599,7 @@ __global__ void __launch_bounds__(kTcThreads) surr_mlp_tc_kernel(const MlpK k)
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&mbf)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -1615,26 +1611,46 @@ __global__ void __launch_bounds__(kTcThreads) surr_mlp_tc_kernel(const MlpK k)
     const uint32_t tmem = s_tmem;
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
     const int RR = k.R * k.R, RS = k.R + 2;
-    uint32_t parity = 0;
-    bool ok = true;
+    uint32_t parity = 0, fpar = 0;  // phases of mbar and mbf
+    bool ok = true, pend = false;   // a bulk copy into F not yet waited for
     MlpChunk cur;
     cur.b = blockIdx.x;
     cur.s0 = 0;
     mlp_seek(k, cur, tid);
-    TcFeatRegs pf;
-    if (cur.p >= 0) tc_feat_load(k, cur, RR, tid, pf);
+    bool cur_bulk = cur.p >= 0 && tc_bulk_ok(k, cur, RR);
+    if (cur_bulk) {
+        if (tid == 0) tc_bulk_issue(k, cur, RR, F, &mbf);
+        pend = true;
+    }
     while (cur.p >= 0) {
         const int64_t p = cur.p;
         const int s0 = cur.s0;
         const int ns = min(kCH, RR - s0);
-        tc_feat_store(k, cur, RR, tid, pf, X);
-        mlp_next(k, cur, RR, tid);
-        if (cur.p >= 0) tc_feat_load(k, cur, RR, tid, pf);
+        int nf;
+        const float* fp = chunk_feats(k, cur, RR, nf);
+        if (cur_bulk) {
+            ok = __syncthreads_and(tc_wait(&mbf, fpar)) && ok;
+            fpar ^= 1u;
+            pend = false;
+            if (!ok) break;
+            tc_feat_to_x(F, nf, tid, X);
+        } else {
+            tc_feat_to_x(fp, nf, tid, X);
+        }
+        // the next chunk's copy into F goes out after the first barrier
+        // below (every thread has converted F by then), beside the layers
+        MlpChunk nxt = cur;
+        mlp_next(k, nxt, RR, tid);
+        const bool nxt_bulk = nxt.p >= 0 && tc_bulk_ok(k, nxt, RR);
         // layers 1-3 (ReLU, bf16) and the output layer
         const uint16_t* Ws[4] = {W1, W2, W3, W4};
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
             tc_sync();
+            if (l == 0 && nxt_bulk) {
+                if (tid == 0) tc_bulk_issue(k, nxt, RR, F, &mbf);
+                pend = true;
+            }
             if (tid == 0)
                 tc_layer(l < 3 ? tmem : tmem + kHid, l == 0 ? X : H, Ws[l], l == 0 ? kInPad : kHid,
                          l < 3 ? tc_idesc(kHid, kCH) : tc_idesc(kTcOutN, kCH), &mbar);
@@ -1656,8 +1672,14 @@ __global__ void __launch_bounds__(kTcThreads) surr_mlp_tc_kernel(const MlpK k)
                         make_float4(fmaxf(y[2] + b4[2], 0.f), fmaxf(y[3] + b4[3], 0.f), fmaxf(y[4] + b4[4], 0.f),
                                     fminf(fmaxf(y[0] + b4[0], 0.f), 1.f)));
         }
+        cur = nxt;
+        cur_bulk = nxt_bulk;
     }
-    if (!ok && tid == 0 && k.status) atomicOr(k.status, SOP_DEVSTAT_TIMEOUT);
+    if (!ok) {
+        // a copy still in flight lands before the CTA leaves (bounded wait)
+        if (pend) tc_wait(&mbf, fpar);
+        if (tid == 0 && k.status) atomicOr(k.status, SOP_DEVSTAT_TIMEOUT);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
@@ -2038,19 +2060,25 @@ cudaError_t surr_infer(const char* state, const float* feats, const int32_t* pid
     k.rgbo_dtype = out.rgbo_dtype;
     k.depth_dtype = out.depth_dtype;
     k.status = status_word();
-    // four CTAs an SM (48 KB of shared memory and 128 of the 512 tensor-memory
-    // columns each)
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-    }
-    const unsigned nb = (unsigned)(B < 4 * sms ? B : 4 * sms);
-    if (nb == 0) return cudaSuccess;
+    // the CTAs that fit at once (57 KB of shared memory and 128 of the 512
+    // tensor-memory columns each: four an SM)
     cudaError_t e = cudaFuncSetAttribute(surr_mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e != cudaSuccess) return e;
+    static int resident = 0;
+    if (!resident) {
+        // from the shared memory an SM holds (each CTA also takes 1 KB the
+        // system reserves and its static variables), at most 4 (the tensor
+        // memory's 512 columns)
+        int dev = 0, sms = 0, smem_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        int per_sm = smem_sm > 0 ? (int)((size_t)smem_sm / (kTcSmem + 1024 + 128)) : 1;
+        per_sm = per_sm < 1 ? 1 : (per_sm > kTcMaxCtas ? kTcMaxCtas : per_sm);
+        resident = (sms > 0 ? sms : 152) * per_sm;
+    }
+    const unsigned nb = (unsigned)(B < resident ? B : resident);
+    if (nb == 0) return cudaSuccess;
     surr_mlp_tc_kernel<<<nb, kTcThreads, kTcSmem, s>>>(k);
     return cudaGetLastError();
 }
