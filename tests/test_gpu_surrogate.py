@@ -216,3 +216,36 @@ def test_rebake_fallback_and_spot_check(sop, scene):
     dO = (pred.rgbo[checked, 1:R + 1, 1:R + 1, 3] - exact.rgbo[checked, 1:R + 1, 1:R + 1, 3]).abs().mean().item()
     assert err2.item() == pytest.approx(dO, rel=1e-5)
     assert sop.device_status() == 0
+
+
+def test_predict_unaligned_features(sop, scene):
+    """The network reads a chunk's features by one bulk copy only when they
+    start on a 16-byte boundary and span whole 16 bytes; other chunks are read
+    by the threads. R = 15 (225 texels a probe: chunks of 128 and 97 whose
+    starts alternate between aligned and not) and a feature array that starts
+    one texel into its allocation take both paths; both match the FP64
+    network on the same features."""
+    th = params(6)
+    net = sop.Surrogate(th, r_near=R_NEAR)
+    R = 15
+    g = {k: cuda(v) for k, v in scene["gauss"].items()}
+    pp = cuda(scene["probe_pos"])
+    P = len(scene["probe_pos"])
+    feats = net.features(g, pp, R)
+    # the same features, one texel into a larger buffer (72 bytes: not 16-aligned)
+    buf = torch.zeros(P * R * R * mlp.N_IN + mlp.N_IN, device="cuda")
+    shifted = buf[mlp.N_IN:].view(P, R * R, mlp.N_IN)
+    shifted.copy_(feats)
+    assert (shifted.data_ptr() % 16) != 0
+    x = feats.cpu().numpy().reshape(-1, mlp.N_IN).astype(np.float64)
+    y, _ = mlp.forward(th.astype(np.float64), x)
+    want_o = np.clip(y[:, 0], 0, 1).reshape(P, R, R)
+    for f in (feats, shifted):
+        out = sop.make_atlas(pp, R)
+        net.predict(f, out)
+        occ = out.interior()[1].cpu().numpy()
+        err = np.abs(occ - want_o) / np.maximum(np.abs(want_o), 1e-2)
+        assert np.median(err) < 1e-4
+        assert (err > 1e-3).mean() < 0.02
+        assert err.max() < 5e-2
+    assert sop.device_status() == 0
