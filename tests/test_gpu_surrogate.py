@@ -249,3 +249,41 @@ def test_predict_unaligned_features(sop, scene):
         assert (err > 1e-3).mean() < 0.02
         assert err.max() < 5e-2
     assert sop.device_status() == 0
+
+
+def test_rebake_from_two_host_threads(sop, scene):
+    """sop_surrogate_infer shares one pair of side streams and events per
+    device; calls from two host threads on two streams (each with its own
+    handle, hence its own workspace) must each give the atlas of a call made
+    alone, bit for bit."""
+    import threading
+    g, _ = _targets(sop, scene)
+    R = 16
+    pp = cuda(scene["probe_pos"])
+    th = params(7)
+    ref = sop.make_atlas(pp, R)
+    sop.Surrogate(th, r_near=R_NEAR).rebake(g, ref, spot_frac=0.1, tau=1e9, seed=5)
+    torch.cuda.synchronize()
+    nets = [sop.Surrogate(th, r_near=R_NEAR) for _ in range(2)]
+    outs = [sop.make_atlas(pp, R) for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    errors = []
+
+    def run(i):
+        try:
+            with torch.cuda.stream(streams[i]):
+                for _ in range(4):
+                    nets[i].rebake(g, outs[i], spot_frac=0.1, tau=1e9, seed=5)
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append(e)
+
+    ts = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    torch.cuda.synchronize()
+    assert not errors, errors
+    for o in outs:
+        assert torch.equal(o.rgbo, ref.rgbo) and torch.equal(o.depth, ref.depth)
+    assert sop.device_status() == 0
