@@ -341,7 +341,9 @@ size_t sop_query_workspace_bytes(const sop_atlas* atlas, int64_t M, const sop_sh
  *           (1 where the denominator is < 1e-20).
  * out [M,3] float32. out_idx [M,K] int32 and out_w [M,K] float32 are
  * optional (NULL to skip): the neighbour indices in increasing distance and
- * their weights. Asynchronous. */
+ * their weights. P (R+1)^2 must not exceed 2^31 - 1 (the bilinear
+ * footprints are indexed with 32-bit integers): SOP_ERR_INVALID_ARG
+ * otherwise. Asynchronous. */
 sop_status sop_query_shade(const float* x, const float* n, const float* wo, const float* albedo, const float* rough,
                            const float* metal, int64_t M, const sop_atlas* atlas, const float* env, int32_t He,
                            int32_t We, const float* dirs_local, const sop_shade_params* params, float* out,

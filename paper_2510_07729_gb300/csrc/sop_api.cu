@@ -328,6 +328,11 @@ static sop_status query_common(const float* x, const float* n, const float* wo, 
     st = check_shade(params, atlas->P);
     if (st != SOP_OK) return st;
     if (M < 0 || M > ((int64_t)1 << 36)) return fail(SOP_ERR_INVALID_ARG, "M = %lld out of range", (long long)M);
+    // the shading kernels index the probes' bilinear footprints (P (R+1)^2 of
+    // them) with 32-bit integers
+    if ((int64_t)atlas->P * (atlas->R + 1) * (atlas->R + 1) > (int64_t)INT32_MAX)
+        return fail(SOP_ERR_INVALID_ARG, "P * (R+1)^2 = %lld footprints exceeds 2^31 - 1",
+                    (long long)atlas->P * (atlas->R + 1) * (atlas->R + 1));
     if (He < 1 || We < 1 || (int64_t)He * We > ((int64_t)1 << 28))
         return fail(SOP_ERR_INVALID_ARG, "environment size %d x %d invalid", He, We);
     if (params->env_layout == SOP_ENV_OCTAHEDRAL && (He != We || He < 2))

@@ -63,6 +63,24 @@ def test_radius_checked_on_the_host():
         assert b"radius" in lib.sop_last_error()
 
 
+def test_footprint_index_range_checked_on_the_host():
+    """An atlas whose bilinear footprints (P (R+1)^2) overflow the shading
+    kernels' 32-bit index is refused before any device work; one just
+    inside the range passes the check (and then fails on the workspace)."""
+    from paper_2510_07729_gb300 import sop as S
+    lib = S.load()
+    fake = 1 << 20
+    sp = S.ShadeParams(4, 64, 0, 0.5, 1e-6, 0, 0, 0.0)
+    for P, R, refused in ((508280, 64, False), (508281, 64, True), (7430739, 16, False), (7430740, 16, True)):
+        assert (P * (R + 1) ** 2 > 2 ** 31 - 1) == refused
+        at = S.AtlasDesc(fake, None, 0, 0, P, R, 1.0, fake, None)
+        st = lib.sop_query_shade(fake, fake, fake, fake, fake, fake, 16, ctypes.byref(at), fake, 16, 32, None,
+                                 ctypes.byref(sp), fake, None, None, fake, 64, None)
+        # refused: SOP_ERR_INVALID_ARG; else the 64-byte workspace is too small
+        assert st == (1 if refused else 3), (P, R, st, lib.sop_last_error())
+        assert (b"footprints" in lib.sop_last_error()) == refused, lib.sop_last_error()
+
+
 def test_front_end_and_placement_checks_on_the_host():
     """The deferred front end and the placement entry points refuse bad
     arguments before any device work (SOP_ERR_INVALID_ARG = 1, with a

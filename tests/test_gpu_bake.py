@@ -51,6 +51,25 @@ def test_tiny_bake_parity(sop, orc, t_stop):
     assert occ.max() > 0.5  # the shell occludes
 
 
+@pytest.mark.parametrize("R", [2, 64])
+def test_tiny_bake_resolution_limits(sop, orc, R):
+    """The smallest and largest octahedral resolutions the library accepts:
+    the whole tiny scene baked (64 probes), 4 probes checked at 64 x 64."""
+    c = I.make_tiny()
+    g = c["gauss"]
+    rgb, occ, dep, at = gpu_bake(sop, g, c["probe_pos"], R)
+    probes = np.arange(64) if R == 2 else np.array([0, 17, 38, 63])
+    o_rgb, o_occ, o_dep, fl = orc.bake(g, c["probe_pos"], R, probes=probes)
+    flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, f"tiny R={R}")
+    assert flagged <= 0.01 * fl.size
+    assert occ.max() > 0.5
+    a = at.rgbo.cpu().numpy()
+    for jj in (0, 1, R, R + 1):
+        for ii in range(R + 2):
+            si, sj = orc.oct_wrap(R, ii - 1, jj - 1)
+            assert np.array_equal(a[:, jj, ii], a[:, sj + 1, si + 1])
+
+
 def test_bake_gutter_matches_interior(sop, orc):
     c = I.make_tiny()
     _, _, _, at = gpu_bake(sop, c["gauss"], c["probe_pos"], c["R"])
@@ -89,6 +108,30 @@ def test_object_full_bake_sampled(sop, orc):
     probes = np.sort(np.random.default_rng(21).choice(len(c["probe_pos"]), 16, replace=False))
     o_rgb, o_occ, o_dep, fl = orc.bake(g, c["probe_pos"], c["R"], probes=probes)
     flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, "object")
+    assert flagged <= 0.05 * fl.size
+
+
+def test_compose_full_bake_sampled(sop, orc):
+    """The 1080p composition's bake in the benchmark's launch configuration:
+    all 8,192 probes (4,096 on the object, 4,096 shadow-region probes on the
+    ground) in one call against the object's 200k Gaussians. Sampled: 8
+    random object probes, the 4 ground probes nearest the object (most of
+    their upper hemisphere sees it) and 4 random ground probes."""
+    c = I.make_compose()
+    g = c["gauss_object"]
+    po, ps = c["shade"]["probe_pos"], c["shadow"]["probe_pos"]
+    pp = np.concatenate([po, ps])
+    rgb, occ, dep, _ = gpu_bake(sop, g, pp, c["R"])
+    rng = np.random.default_rng(22)
+    centre = g["mean"].astype(np.float64).mean(0)
+    near = np.argsort(np.linalg.norm(ps - centre, axis=1), kind="stable")[:4]
+    far = rng.choice(np.setdiff1d(np.arange(len(ps)), near), 4, replace=False)
+    probes = np.sort(np.concatenate([rng.choice(len(po), 8, replace=False), len(po) + near, len(po) + far]))
+    o_rgb, o_occ, o_dep, fl = orc.bake(g, pp, c["R"], probes=probes)
+    # the nearest ground probes do see the object
+    assert o_occ[8:].max() > 0.5
+    flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, "compose",
+                      extent=float(c["object_size"]))
     assert flagged <= 0.05 * fl.size
 
 

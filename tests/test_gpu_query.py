@@ -74,7 +74,7 @@ def test_hammersley_matches_oracle(sop, orc):
         assert np.array_equal(g, o.astype(np.float32))
 
 
-@pytest.mark.parametrize("R", [2, 8, 16])
+@pytest.mark.parametrize("R", [2, 8, 16, 64])
 def test_atlas_pack_gutter_exact(sop, orc, R):
     rng = np.random.default_rng(R)
     P = 5
@@ -101,6 +101,21 @@ def test_tiny_parity(sop, orc, tiny):
     assert np.array_equal(idx, ri)  # bit-exact probe selection
     assert_close(w, rw, what="weights")
     assert_close(out, ro, what="shade")
+
+
+@pytest.mark.parametrize("R", [2, 64])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tiny_parity_resolution_limits(sop, orc, tiny, R, mode):
+    """The smallest and largest octahedral resolutions the library accepts
+    (2 and 64 texels a side), SHADE and SHADOW, on the tiny workload."""
+    c = tiny
+    maps = I.synthetic_maps(np.random.default_rng(30 + R + mode), 64, R)
+    at = atlas_from_maps(sop, c["probe_pos"], maps)
+    out, idx, w = run_gpu(sop, c, at, c["K"], c["S"], mode=mode)
+    ro, ri, rw = run_orc(orc, c, maps, c["probe_pos"], c["K"], c["S"], mode=mode)
+    assert np.array_equal(idx, ri)
+    kap = kappa(orc, c, maps, c["probe_pos"], c["K"], c["S"], mode=mode)
+    assert_close(out, ro, what=f"R={R} mode {mode}", absolute=kap)
 
 
 def test_tiny_shadow_parity(sop, orc, tiny):
