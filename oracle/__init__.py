@@ -139,33 +139,48 @@ def brdf(n, wo, wi, albedo, rough, metal, spec=0.5):
 DEFAULT_BAKE = dict(t_near=0.0, alpha_min=1.0 / 255.0, alpha_max=0.99, t_stop=1e-4)
 
 
+# angular error bound of a texel direction held in FP32 (rad): each unit
+# component rounded once from double is off by at most 2^-25, so the vector
+# by at most sqrt(3) 2^-25 < 2^-24
+FP32_TEXEL_DIR_EPS = 2.0 ** -24
+
+
 def bake_rays(gauss, probe_pos, R, probe_of, ti, tj, t_near=0.0, alpha_min=1.0 / 255.0,
-              alpha_max=0.99, t_stop=1e-4):
-    """Bake the listed texel rays. Returns rgb [n,3], occ [n], depth [n], flags [n]."""
+              alpha_max=0.99, t_stop=1e-4, eps_dir=FP32_TEXEL_DIR_EPS, with_sens=False):
+    """Bake the listed texel rays. Returns rgb [n,3], occ [n], depth [n], flags [n]
+    and, with with_sens, the test allowance [n,5] (L0, L1, L2, O, D): each
+    output's first-order bound under an angular error eps_dir of the ray
+    direction (see orc_bake_rays)."""
     mean, scale, quat, op, rgb = (_f32(gauss[k]) for k in ("mean", "scale", "quat", "opacity", "rgb"))
     pp = _f32(probe_pos)
     probe_of, ti, tj = (np.ascontiguousarray(v, dtype=np.int32) for v in (probe_of, ti, tj))
     n = len(probe_of)
     o_rgb, o_occ, o_d = np.empty((n, 3)), np.empty(n), np.empty(n)
     o_fl = np.empty(n, np.int32)
+    sens = np.empty((n, 5)) if with_sens else None
     lib().orc_bake_rays(C.c_int64(len(mean)), _p(mean), _p(scale), _p(quat), _p(op), _p(rgb), _p(pp),
                         C.c_int(R), C.c_int64(n), _p(probe_of), _p(ti), _p(tj), C.c_double(t_near),
                         C.c_double(alpha_min), C.c_double(alpha_max), C.c_double(t_stop),
-                        _p(o_rgb), _p(o_occ), _p(o_d), _p(o_fl))
+                        _p(o_rgb), _p(o_occ), _p(o_d), _p(o_fl), C.c_double(eps_dir),
+                        _p(sens) if with_sens else None)
+    if with_sens:
+        return o_rgb, o_occ, o_d, o_fl, sens
     return o_rgb, o_occ, o_d, o_fl
 
 
-def bake(gauss, probe_pos, R, probes=None, **kw):
+def bake(gauss, probe_pos, R, probes=None, with_sens=False, **kw):
     """Bake whole probes (all R*R texels). Returns maps [P',R,R,3], [P',R,R],
-    [P',R,R] and flags [P',R,R] for the probes listed (default: all)."""
+    [P',R,R] and flags [P',R,R] for the probes listed (default: all), and
+    with with_sens the allowance [P',R,R,5] of bake_rays."""
     probes = np.arange(len(probe_pos)) if probes is None else np.asarray(probes)
     jj, ii = np.meshgrid(np.arange(R), np.arange(R), indexing="ij")
     po = np.repeat(probes, R * R)
     ti = np.tile(ii.reshape(-1), len(probes))
     tj = np.tile(jj.reshape(-1), len(probes))
-    rgb, occ, dep, fl = bake_rays(gauss, probe_pos, R, po, ti, tj, **kw)
+    out = bake_rays(gauss, probe_pos, R, po, ti, tj, with_sens=with_sens, **kw)
     P = len(probes)
-    return (rgb.reshape(P, R, R, 3), occ.reshape(P, R, R), dep.reshape(P, R, R), fl.reshape(P, R, R))
+    res = (out[0].reshape(P, R, R, 3), out[1].reshape(P, R, R), out[2].reshape(P, R, R), out[3].reshape(P, R, R))
+    return res + (out[4].reshape(P, R, R, 5),) if with_sens else res
 
 
 # ----------------------------------------------------------------------------

@@ -140,6 +140,7 @@ void orc_oct_bilerp(const double* map, int R, int C, const double* uv, double* o
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double t, alpha;
+    double dalpha, Tb; /* orc_bake_rays: bound of |d alpha|; transmittance before the hit */
     int64_t idx;
 } orc_hit;
 
@@ -176,20 +177,38 @@ enum {
 /* Bake n_rays texel rays. Ray r starts at probe probe_of[r] and points at the
  * centre of texel (ti[r], tj[r]) of an R x R map. Outputs per ray: RGB
  * indirect radiance L, occlusion O = 1 - T, depth D = sum(T a t*)/sum(T a)
- * (0 when nothing is hit) and ambiguity flags. */
+ * (0 when nothing is hit) and ambiguity flags.
+ *
+ * Test allowance (out_sens [n_rays][5]: L0, L1, L2, O, D; NULL to skip): how
+ * far each output may move when the ray direction carries an angular error
+ * of up to eps_dir (an FP32 path holds the direction rounded to single
+ * precision). At the point of maximum response m^2 is stationary in t, so
+ * to first order only the rotation of the ray moves it: with e = M (p - mu
+ * + t* d) the whitened offset there, dm^2 = 2 e . (t* M dd) and |dm^2| <=
+ * 2 |e| t* |M|_2 eps_dir, |M|_2 = max 1/s; hence |d alpha| <= alpha |e| t*
+ * max(1/s) eps_dir (0 where alpha is clamped at alpha_max). Each composited
+ * hit's |d alpha| is carried to the outputs through their partial
+ * derivatives in alpha (the later hits' transmittances hold 1 - alpha) and
+ * summed in absolute value. A response within that |d alpha| of alpha_min
+ * is flagged like one within 1e-4 relative of it. */
 void orc_bake_rays(int64_t N, const float* mean, const float* scale, const float* quat,
                    const float* opacity, const float* rgb, const float* probe_pos, int R,
                    int64_t n_rays, const int32_t* probe_of, const int32_t* ti, const int32_t* tj,
                    double t_near, double alpha_min, double alpha_max, double t_stop,
-                   double* out_rgb, double* out_occ, double* out_depth, int32_t* out_flags)
+                   double* out_rgb, double* out_occ, double* out_depth, int32_t* out_flags,
+                   double eps_dir, double* out_sens)
 {
     /* Per-Gaussian M = diag(1/s) R^T, so that m^2(x) = |M (x - mu)|^2. */
     double* Mg = (double*)malloc(sizeof(double) * 9 * (size_t)(N > 0 ? N : 1));
+    double* Mn = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1)); /* |M|_2 = max 1/s */
     for (int64_t g = 0; g < N; ++g) {
         double Rm[3][3];
         quat_to_rot(quat + 4 * g, Rm);
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) Mg[9 * g + 3 * a + b] = Rm[b][a] / (double)scale[3 * g + a];
+        Mn[g] = 0.0;
+        for (int a = 0; a < 3; ++a)
+            if (1.0 / (double)scale[3 * g + a] > Mn[g]) Mn[g] = 1.0 / (double)scale[3 * g + a];
     }
 #pragma omp parallel
     {
@@ -221,7 +240,8 @@ void orc_bake_rays(int64_t N, const float* mean, const float* scale, const float
                 }
                 double resp = opacity[g] * exp(-0.5 * m2);
                 double dl = sqrt(del[0] * del[0] + del[1] * del[1] + del[2] * del[2]);
-                if (fabs(resp - alpha_min) <= 1e-4 * alpha_min && ts > t_near) flags |= ORC_FLAG_ALPHA_MIN;
+                const double da = resp * sqrt(m2) * fabs(ts) * Mn[g] * eps_dir;
+                if (fabs(resp - alpha_min) <= fmax(1e-4 * alpha_min, da) && ts > t_near) flags |= ORC_FLAG_ALPHA_MIN;
                 if (resp >= alpha_min && fabs(ts - t_near) <= 1e-5 * (dl + 1e-3)) flags |= ORC_FLAG_TNEAR;
                 if (ts <= t_near) continue;
                 if (resp < alpha_min) continue;
@@ -231,14 +251,18 @@ void orc_bake_rays(int64_t N, const float* mean, const float* scale, const float
                 }
                 hits[nh].t = ts;
                 hits[nh].alpha = resp < alpha_max ? resp : alpha_max;
+                hits[nh].dalpha = resp < alpha_max ? da : 0.0;
                 hits[nh].idx = g;
                 ++nh;
             }
             qsort(hits, nh, sizeof(orc_hit), hit_cmp);
             double T = 1.0, L[3] = {0, 0, 0}, Dacc = 0.0, W = 0.0;
+            size_t nc = 0; /* hits composited */
             for (size_t k = 0; k < nh; ++k) {
+                nc = k + 1;
                 if (k + 1 < nh && hits[k + 1].t - hits[k].t <= 1e-6 * fabs(hits[k + 1].t)) flags |= ORC_FLAG_ORDER;
                 double wk = T * hits[k].alpha;
+                hits[k].Tb = T;
                 const float* c = rgb + 3 * hits[k].idx;
                 L[0] += wk * c[0];
                 L[1] += wk * c[1];
@@ -255,9 +279,33 @@ void orc_bake_rays(int64_t N, const float* mean, const float* scale, const float
             out_occ[r] = 1.0 - T;
             out_depth[r] = (W > 1e-8) ? Dacc / W : 0.0;
             out_flags[r] = flags;
+            if (out_sens) {
+                /* X = sum_k T_k a_k x_k with T_k = prod_{j<k} (1 - a_j):
+                 * dX/da_k = T_k x_k - (sum_{j>k} T_j a_j x_j) / (1 - a_k);
+                 * O = 1 - prod (1 - a_j): dO/da_k = T_end / (1 - a_k). The
+                 * suffix sums run from the last composited hit down. */
+                double sL[3] = {0, 0, 0}, sD = 0.0, sW = 0.0, sens[5] = {0, 0, 0, 0, 0};
+                const double Dv = (W > 1e-8) ? Dacc / W : 0.0;
+                for (size_t k = nc; k-- > 0;) {
+                    const double a = hits[k].alpha, om = 1.0 - a, Tk = hits[k].Tb;
+                    const double wk = Tk * a;
+                    const float* c = rgb + 3 * hits[k].idx;
+                    double dX[5];
+                    for (int q = 0; q < 3; ++q) dX[q] = Tk * c[q] - sL[q] / om;
+                    dX[3] = T / om;
+                    const double dDacc = Tk * hits[k].t - sD / om, dW = Tk - sW / om;
+                    dX[4] = (W > 1e-8) ? (dDacc - Dv * dW) / W : 0.0;
+                    for (int q = 0; q < 5; ++q) sens[q] += fabs(dX[q]) * hits[k].dalpha;
+                    for (int q = 0; q < 3; ++q) sL[q] += wk * c[q];
+                    sD += wk * hits[k].t;
+                    sW += wk;
+                }
+                for (int q = 0; q < 5; ++q) out_sens[5 * r + q] = sens[q];
+            }
         }
         free(hits);
     }
+    free(Mn);
     free(Mg);
 }
 

@@ -29,14 +29,16 @@ def gpu_bake(sop, g, probe_pos, R, **kw):
     return rgb.cpu().numpy(), occ.cpu().numpy(), dep.cpu().numpy(), at
 
 
-def compare(orc, g_rgb, g_occ, g_dep, o_rgb, o_occ, o_dep, flags, what, extent=2.0):
+def compare(orc, g_rgb, g_occ, g_dep, o_rgb, o_occ, o_dep, flags, sens, what, extent=2.0):
+    """Element-wise parity; `sens` is the oracle's allowance [..., 5] for
+    the FP32 rounding of each texel direction (orc.bake with_sens)."""
     order_ok = (flags & orc.FLAG_ORDER) == 0
     dec_ok = (flags & (orc.FLAG_ALPHA_MIN | orc.FLAG_TNEAR | orc.FLAG_TSTOP)) == 0
     # occlusion is a product over hits: order-independent
-    assert_close(g_occ[dec_ok], o_occ[dec_ok], what=what + " O")
+    assert_close(g_occ[dec_ok], o_occ[dec_ok], what=what + " O", absolute=sens[..., 3][dec_ok])
     ok = order_ok & dec_ok
-    assert_close(g_rgb[ok], o_rgb[ok], what=what + " L_in")
-    assert_close(g_dep[ok], o_dep[ok], what=what + " D", absolute=4 * 2.0 ** -24 * extent)
+    assert_close(g_rgb[ok], o_rgb[ok], what=what + " L_in", absolute=sens[..., :3][ok])
+    assert_close(g_dep[ok], o_dep[ok], what=what + " D", absolute=4 * 2.0 ** -24 * extent + sens[..., 4][ok])
     return int((~ok).sum())
 
 
@@ -45,8 +47,8 @@ def test_tiny_bake_parity(sop, orc, t_stop):
     c = I.make_tiny()
     g = c["gauss"]
     rgb, occ, dep, at = gpu_bake(sop, g, c["probe_pos"], c["R"], t_stop=t_stop)
-    o_rgb, o_occ, o_dep, fl = orc.bake(g, c["probe_pos"], c["R"], t_stop=t_stop)
-    flagged = compare(orc, rgb, occ, dep, o_rgb, o_occ, o_dep, fl, "tiny")
+    o_rgb, o_occ, o_dep, fl, sens = orc.bake(g, c["probe_pos"], c["R"], t_stop=t_stop, with_sens=True)
+    flagged = compare(orc, rgb, occ, dep, o_rgb, o_occ, o_dep, fl, sens, "tiny")
     assert flagged <= 0.01 * fl.size
     assert occ.max() > 0.5  # the shell occludes
 
@@ -59,8 +61,8 @@ def test_tiny_bake_resolution_limits(sop, orc, R):
     g = c["gauss"]
     rgb, occ, dep, at = gpu_bake(sop, g, c["probe_pos"], R)
     probes = np.arange(64) if R == 2 else np.array([0, 17, 38, 63])
-    o_rgb, o_occ, o_dep, fl = orc.bake(g, c["probe_pos"], R, probes=probes)
-    flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, f"tiny R={R}")
+    o_rgb, o_occ, o_dep, fl, sens = orc.bake(g, c["probe_pos"], R, probes=probes, with_sens=True)
+    flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, sens, f"tiny R={R}")
     assert flagged <= 0.01 * fl.size
     assert occ.max() > 0.5
     a = at.rgbo.cpu().numpy()
@@ -93,9 +95,9 @@ def test_empty_and_single_gaussian(sop, orc):
                quat=np.array([[0.9, 0.1, -0.3, 0.2]], np.float32), opacity=np.array([0.8], np.float32),
                rgb=np.array([[0.1, 0.5, 0.9]], np.float32))
     rgb, occ, dep, _ = gpu_bake(sop, one, pp, 8)
-    o_rgb, o_occ, o_dep, fl = orc.bake(one, pp, 8)
+    o_rgb, o_occ, o_dep, fl, sens = orc.bake(one, pp, 8, with_sens=True)
     assert (occ > 0).sum() >= 1
-    compare(orc, rgb, occ, dep, o_rgb, o_occ, o_dep, fl, "single")
+    compare(orc, rgb, occ, dep, o_rgb, o_occ, o_dep, fl, sens, "single")
 
 
 def test_object_full_bake_sampled(sop, orc):
@@ -106,8 +108,8 @@ def test_object_full_bake_sampled(sop, orc):
     g = c["gauss"]
     rgb, occ, dep, _ = gpu_bake(sop, g, c["probe_pos"], c["R"])
     probes = np.sort(np.random.default_rng(21).choice(len(c["probe_pos"]), 16, replace=False))
-    o_rgb, o_occ, o_dep, fl = orc.bake(g, c["probe_pos"], c["R"], probes=probes)
-    flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, "object")
+    o_rgb, o_occ, o_dep, fl, sens = orc.bake(g, c["probe_pos"], c["R"], probes=probes, with_sens=True)
+    flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, sens, "object")
     assert flagged <= 0.05 * fl.size
 
 
@@ -127,10 +129,10 @@ def test_compose_full_bake_sampled(sop, orc):
     near = np.argsort(np.linalg.norm(ps - centre, axis=1), kind="stable")[:4]
     far = rng.choice(np.setdiff1d(np.arange(len(ps)), near), 4, replace=False)
     probes = np.sort(np.concatenate([rng.choice(len(po), 8, replace=False), len(po) + near, len(po) + far]))
-    o_rgb, o_occ, o_dep, fl = orc.bake(g, pp, c["R"], probes=probes)
+    o_rgb, o_occ, o_dep, fl, sens = orc.bake(g, pp, c["R"], probes=probes, with_sens=True)
     # the nearest ground probes do see the object
     assert o_occ[8:].max() > 0.5
-    flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, "compose",
+    flagged = compare(orc, rgb[probes], occ[probes], dep[probes], o_rgb, o_occ, o_dep, fl, sens, "compose",
                       extent=float(c["object_size"]))
     assert flagged <= 0.05 * fl.size
 

@@ -148,3 +148,52 @@ def test_flags_mark_near_ties(orc):
     g = gset([1.0 * d, 1.5 * d], [[0.05] * 3] * 2, opacity=[0.5, 0.5])
     _, _, _, fl = one_texel(orc, g, i=3, j=3)
     assert fl == 0
+
+
+def test_direction_allowance_matches_finite_differences(orc):
+    """The bake's test allowance (bake_rays with_sens) bounds each output's
+    change under an angular error eps of the ray direction by the sum, over
+    the composited hits, of the change that moving that hit alone by the
+    worst first-order amount causes. For an isotropic Gaussian, turning the
+    ray by eps about the probe moves the ray's closest point to the centre by
+    t* eps, the same as moving the centre by t* eps towards the ray. So each
+    hit's term is a central difference of the oracle's own outputs with that
+    centre moved; their sum must reproduce the allowance. A Gaussian
+    saturated at alpha_max contributes nothing of its own but scales the
+    hits behind it."""
+    R, i, j = 8, 3, 5
+    d = ray(orc, R, i, j)
+    rng = np.random.default_rng(7)
+    ts, ms = [0.6, 0.9, 1.0, 1.3], [0.8, 1.4, 0.0, 2.1]
+    ss, ops = [0.03, 0.05, 0.04, 0.02], [0.5, 0.7, 1.0, 0.9]
+    mus = []
+    for t, m, s in zip(ts, ms, ss):
+        perp = np.cross(d, rng.standard_normal(3))
+        perp /= np.linalg.norm(perp)
+        mus.append(t * d + m * s * perp)
+    rgb = rng.uniform(0.1, 1.0, (4, 3))
+    eps = 1e-4
+
+    def outs(means):
+        g = gset(means, [[s, s, s] for s in ss], opacity=ops, rgb=rgb)
+        o_rgb, o_occ, o_dep, fl, sens = orc.bake_rays(g, np.zeros((1, 3), np.float32), R, [0], [i], [j],
+                                                     eps_dir=eps, with_sens=True)
+        return np.concatenate([o_rgb[0], [o_occ[0], o_dep[0]]]), sens[0], fl[0]
+
+    base, sens, fl = outs(mus)
+    assert fl == 0
+    assert base[3] > 0.99  # the saturated Gaussian is composited
+    fd = np.zeros(5)
+    for k in range(4):
+        mu32 = np.asarray(mus[k], np.float32).astype(np.float64)
+        tk = mu32 @ d
+        off = mu32 - tk * d
+        if np.linalg.norm(off) == 0:
+            continue
+        e_hat = off / np.linalg.norm(off)
+        step = tk * eps * e_hat
+        plus = [m if q != k else mu32 + step for q, m in enumerate(mus)]
+        minus = [m if q != k else mu32 - step for q, m in enumerate(mus)]
+        fd += np.abs(outs(plus)[0] - outs(minus)[0]) / 2
+    assert sens[3] > 0 and sens[4] > 0
+    np.testing.assert_allclose(sens, fd, rtol=1e-3)

@@ -14,6 +14,11 @@ Two derived allowances are added where the arithmetic requires them:
   - bake depth: 4 ulp of the scene extent, because t* of a Gaussian next to
     the probe cannot be resolved better than the FP32 coordinates it comes
     from;
+  - bake outputs: their first-order change under the FP32 rounding of the
+    texel direction (2^-24 rad; oracle.bake with_sens), large only where a
+    small Gaussian far from the probe decides a texel: turning the ray by
+    eps moves its closest point to the centre by t* eps, i.e. t* eps / s in
+    units of the Gaussian's scale;
   - surrogate far field: the march's conditioning (oracle.surr_far with
     with_sens), sigma times the FP32 rounding of each cell boundary time,
     summed over the segments.
