@@ -232,7 +232,7 @@ __device__ __forceinline__ uint64_t unsearched_bound2(const ProbeGrid& G, const 
 // Exact K nearest probes + blend weights. One thread per point.
 // ---------------------------------------------------------------------------
 template <int KMAX>
-__global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float* __restrict__ x, const float* __restrict__ nrm, int64_t M,
+__global__ void __launch_bounds__(128, KMAX <= 8 ? 8 : 1) knn_kernel(const float* __restrict__ x, const float* __restrict__ nrm, int64_t M,
                                                    int32_t K, uint64_t snap_key, uint64_t r2_key,
                                                    const ProbeGrid* __restrict__ gridp,
                                                    const int32_t* __restrict__ cell_start,
@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
                     if (xx < 0 || xx >= G.dims[0]) continue;
                     const int cell = (z * G.dims[1] + y) * G.dims[0] + xx;
                     const int e1 = __ldg(cell_start + cell + 1);
+#pragma unroll 2
                     for (int e = __ldg(cell_start + cell); e < e1; ++e) {
                         const int4 en = __ldg(entries + e);
                         const uint64_t key = qdist2(en.x, en.y, en.z, q);
@@ -303,10 +304,11 @@ __global__ void __launch_bounds__(128, KMAX <= 8 ? 5 : 1) knn_kernel(const float
             }
         // stop once no probe outside ring r can enter the best K, nor lie
         // within the radius
+        // the K-th best key as a chain of selects: picking bk[K - 1] by the
+        // run-time K would put bk in local memory
         uint64_t kth = bk[0];
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k == K - 1) kth = bk[k];
+        for (int k = 1; k < KMAX; ++k) kth = k < K ? bk[k] : kth;
         const uint64_t bnd = unsearched_bound2(G, q, c, r);
         if (bnd == UINT64_MAX || kth < bnd || r2_key < bnd) break;
     }
