@@ -84,6 +84,28 @@ def test_adjoint_smooth_inputs_strict(sop, orc):
     assert_close(g["maps"], om, rtol=1e-4, floor=0, absolute=1e-6 * np.abs(om).max(), what="maps")
 
 
+def test_adjoint_direction_count_limit(sop, orc):
+    """The adjoint at S = 4096 (the most directions the library accepts) on
+    101 tilted points with smooth maps: per-point gradients as in the strict
+    test; the environment and probe-map gradients are float-atomic sums of
+    about 4e5 terms, held to 1e-4 relative plus 2e-5 of the largest entry as
+    on the differentiation workload."""
+    c = I.make_tiny()
+    rng = np.random.default_rng(53)
+    pts = tilted({k: c[k][:101] for k in KEYS}, rng)
+    maps = I.smooth_maps(rng, 64, 8)
+    go = rng.standard_normal((101, 3))
+    at = atlas(sop, c["probe_pos"], maps)
+    g = gpu_grads(sop, pts, at, c["env"], 4, 4096, go)
+    o = orc_grads(orc, pts, c["probe_pos"], maps, c["env"], 4, 4096, go)
+    for k in ("albedo", "rough", "metal"):
+        assert_close(g[k], o[k], rtol=1e-4, absolute=TERM_FRAC * o["abs_" + k], what=k)
+    assert_close(g["normal"], o["normal"], rtol=1e-4, absolute=TERM_FRAC * o["abs_normal"][:, None], what="normal")
+    assert_close(g["env"], o["env"], rtol=1e-4, floor=0, absolute=2e-5 * np.abs(o["env"]).max(), what="env")
+    om = maps_of(o)
+    assert_close(g["maps"], om, rtol=1e-4, floor=0, absolute=2e-5 * np.abs(om).max(), what="maps")
+
+
 def diff_subset(n=4096, seed=51):
     c = I.make_diff()
     sel, pts = I.subsample(np.random.default_rng(seed), c, list(KEYS), n)

@@ -53,6 +53,18 @@ def _check(sop, orc, pts, probe_pos, maps, env_oct, K, S, mode, sample=None):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
+def test_importance_direction_count_limit(sop, orc, mode):
+    """4,096 importance-sampled world directions (the library's maximum S;
+    the world-direction kernel's table is 192 KB of shared memory) on 101
+    points of the tiny workload."""
+    c = I.make_tiny()
+    pts = {k: c[k][:101] for k in PTS}
+    env_oct = orc.env_to_octahedral(c["env"], 32).astype(np.float32)
+    maps = I.synthetic_maps(np.random.default_rng(44 + mode), 64, 8)
+    _check(sop, orc, pts, c["probe_pos"], maps, env_oct, c["K"], 4096, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
 def test_tiny_importance_sampled(sop, orc, mode):
     c = I.make_tiny()
     env_oct = orc.env_to_octahedral(c["env"], 32).astype(np.float32)

@@ -68,7 +68,7 @@ def kappa(orc, c, maps, probe_pos, K, S, mode=0, pts=None, env=None):
 
 
 def test_hammersley_matches_oracle(sop, orc):
-    for S in (1, 7, 64, 128, 1000):
+    for S in (1, 7, 64, 128, 1000, 4096):
         g = sop.hammersley(S).cpu().numpy()
         o = orc.hammersley(S)
         assert np.array_equal(g, o.astype(np.float32))
@@ -116,6 +116,22 @@ def test_tiny_parity_resolution_limits(sop, orc, tiny, R, mode):
     assert np.array_equal(idx, ri)
     kap = kappa(orc, c, maps, c["probe_pos"], c["K"], c["S"], mode=mode)
     assert_close(out, ro, what=f"R={R} mode {mode}", absolute=kap)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_direction_count_limit(sop, orc, tiny, mode):
+    """S = 4096, the most light directions the library accepts (a 64 KB
+    direction table in shared memory), on 101 points of the tiny workload."""
+    c = tiny
+    M, S = 101, 4096
+    pts = {k: c[k][:M] for k in ("x", "n", "wo", "albedo", "rough", "metal")}
+    maps = I.synthetic_maps(np.random.default_rng(50 + mode), 64, 8)
+    at = atlas_from_maps(sop, c["probe_pos"], maps)
+    out, idx, _ = run_gpu(sop, c, at, 4, S, mode=mode, pts=pts)
+    ro, ri, _ = run_orc(orc, c, maps, c["probe_pos"], 4, S, mode=mode, pts=pts)
+    assert np.array_equal(idx, ri)
+    kap = kappa(orc, c, maps, c["probe_pos"], 4, S, mode=mode, pts=pts)
+    assert_close(out, ro, what=f"S={S} mode {mode}", absolute=kap)
 
 
 def test_tiny_shadow_parity(sop, orc, tiny):
