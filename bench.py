@@ -8,7 +8,9 @@ texel rays traced through the object's Gaussians: binning, grid walk,
 compositing, atlas border) followed by the frame's two sop_query_shade
 calls: the 21,907 object pixels in SHADE mode against the object probes and
 the 2,051,693 scene pixels in SHADOW mode against the shadow-region probes
-(K=8, S=64, 256x512 HDR environment). `value` is shaded point-directions per
+(K=8, S=64, 256x512 HDR environment). The two queries are independent and
+are issued on two streams: the small SHADE call's launches run beside the
+SHADOW call instead of before it. `value` is shaded point-directions per
 second of that step; the bake's texels/s is reported beside it. The
 object-reconstruction workload (4,096 probes, 418,111 points, K=8, S=128) is
 timed the same way as a secondary line (`object_step`).
@@ -776,6 +778,10 @@ class StepState:
         self.atlas = sop.make_atlas(self.ppos, self.R, rgbo_dtype=rgbo_dtype, depth_dtype=depth_dtype,
                                     depth_scale=W["depth_scale"])
         self.bws = sop.BakeWorkspace(len(W["gauss"]["mean"]), dev)
+        # the frame's queries are independent (own points, atlas slice,
+        # output and workspace; the atlas and environment are read-only):
+        # the smaller ones run on a second stream beside the largest
+        self.side = torch.cuda.Stream(device=dev)
         self.parts = []
         for part in W["parts"]:
             q = dict(name=part["name"], mode=part["mode"], M=len(part["pts"]["x"]))
@@ -808,8 +814,16 @@ class StepState:
             evs[1].record(st)
         if do_query:
             evs[2].record(st)
-            for q in self.parts:
-                self.query(q)
+            big = max(self.parts, key=lambda q: q["M"])
+            rest = [q for q in self.parts if q is not big]
+            if rest:
+                self.side.wait_stream(st)
+                with torch.cuda.stream(self.side):
+                    for q in rest:
+                        self.query(q)
+            self.query(big)
+            if rest:
+                st.wait_stream(self.side)
             evs[3].record(st)
 
 
@@ -1119,10 +1133,16 @@ def measure_e2e(args, W, dev, sop, flush):
         at = sop.make_atlas(dbuf["probe_pos"], R, depth_scale=W["depth_scale"])
         sop.bake(g, at)
         main.wait_stream(side)
+        # as in the device-timed step: the smaller queries on the side
+        # stream (after the bake), the largest on the main one
+        big = int(np.argmax([len(part["pts"]["x"]) for part in W["parts"]]))
+        side.wait_stream(main)
         for i, part in enumerate(W["parts"]):
-            o = sop.query_shade(*[dbuf[f"p{i}_{k}"] for k in ("x", "n", "wo", "albedo", "rough", "metal")],
-                                atlas_view(sop, at, *part["probes"]), dbuf["env"], K, S, mode=part["mode"])
-            outs_h[i].copy_(o, non_blocking=True)
+            with torch.cuda.stream(main if i == big else side):
+                o = sop.query_shade(*[dbuf[f"p{i}_{k}"] for k in ("x", "n", "wo", "albedo", "rough", "metal")],
+                                    atlas_view(sop, at, *part["probes"]), dbuf["env"], K, S, mode=part["mode"])
+                outs_h[i].copy_(o, non_blocking=True)
+        main.wait_stream(side)
 
     for _ in range(2):
         one()

@@ -298,3 +298,46 @@ def test_reduced_precision_atlas_error(sop, orc, obj, dtype, bound):
     assert np.array_equal(idx[sel], ri)
     rel = np.abs(out[sel] - ro).mean() / np.abs(ro).mean()
     assert rel < bound
+
+
+def test_concurrent_queries_on_two_streams(sop, tiny):
+    """Two independent queries (own points, atlas, output and workspace; the
+    environment shared and read-only), a SHADE and a SHADOW call as in the
+    composition frame, issued on two streams at once: each output is
+    bit-identical to the same call issued alone (the library keeps no
+    scratch of its own across sop_query_shade calls)."""
+    c = tiny
+    keys = ("x", "n", "wo", "albedo", "rough", "metal")
+    env = cuda(c["env"])
+    calls = []
+    for seed, mode, sl in ((60, 0, slice(0, 2049)), (61, 1, slice(2049, 4096))):
+        maps = I.synthetic_maps(np.random.default_rng(seed), 64, 8)
+        at = atlas_from_maps(sop, c["probe_pos"], maps)
+        pts = [cuda(c[k][sl]) for k in keys]
+        M = pts[0].shape[0]
+        ws = torch.empty(sop.query_workspace_bytes(at, M, 8, 256, env.shape[0], env.shape[1], mode),
+                         dtype=torch.uint8, device="cuda")
+        calls.append((pts, at, mode, ws, M))
+
+    def run(pts, at, mode, ws, M, out):
+        sop.query_shade(*pts, at, env, 8, 256, mode=mode, out=out, workspace=ws)
+
+    alone = []
+    for pts, at, mode, ws, M in calls:
+        out = torch.empty((M, 3), dtype=torch.float32, device="cuda")
+        run(pts, at, mode, ws, M, out)
+        torch.cuda.synchronize()
+        alone.append(out.clone())
+    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+    for _ in range(3):
+        outs = [torch.full((M, 3), float("nan"), device="cuda") for _, _, _, _, M in calls]
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            run(*calls[0], outs[0])
+        run(*calls[1], outs[1])
+        main.wait_stream(side)
+        torch.cuda.synchronize()
+        for a, b in zip(alone, outs):
+            assert torch.equal(a, b)
+    assert sop.device_status() == 0
